@@ -1,0 +1,215 @@
+"""ctypes loader for the TRSTMI CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
+baseline leg may import this package.  The product path (the CUDA library and
+its binding) never imports or calls it.  See ``trstmi_oracle.c`` for what the
+oracle computes and the passages of arXiv 2207.06374 each part follows.
+
+Frames are numpy complex128 arrays of shape (d, N) here; the C side stores
+them column-major with interleaved (re, im), which is the memory layout of
+``np.asfortranarray(phi)`` viewed as float64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "trstmi_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no fast-math) into _build/."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC",
+                               "-shared", "-ffp-contract=off", "-o", tmp, _SRC,
+                               "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OracleOpts(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("T", ctypes.c_int),
+                ("delta0", ctypes.c_double), ("gamma_inc", ctypes.c_double),
+                ("gamma_dec", ctypes.c_double), ("delta_min", ctypes.c_double),
+                ("delta_max", ctypes.c_double), ("target_mu", ctypes.c_double)]
+
+
+class TraceRow(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_uint32), ("cstar", ctypes.c_uint32),
+                ("mu2_best", ctypes.c_double), ("mu2_cur", ctypes.c_double),
+                ("delta_used", ctypes.c_double), ("delta_next", ctypes.c_double),
+                ("accepted", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+TRACE_DTYPE = np.dtype([("t", "<u4"), ("cstar", "<u4"), ("mu2_best", "<f8"),
+                        ("mu2_cur", "<f8"), ("delta_used", "<f8"),
+                        ("delta_next", "<f8"), ("accepted", "<i4"), ("pad", "<i4")])
+assert TRACE_DTYPE.itemsize == ctypes.sizeof(TraceRow)
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.oracle_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+            L.oracle_gauss_entry.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.c_uint32, _dp, _dp]
+            L.oracle_mu2.argtypes = [ctypes.c_int, ctypes.c_int, _dp]
+            L.oracle_mu2.restype = ctypes.c_double
+            L.oracle_gram_abs2.argtypes = [ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int]
+            L.oracle_gram_abs2.restype = ctypes.c_double
+            L.oracle_welch.argtypes = [ctypes.c_int, ctypes.c_int]
+            L.oracle_welch.restype = ctypes.c_double
+            L.oracle_init.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _dp]
+            L.oracle_candidate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _dp,
+                                           ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32, _dp]
+            L.oracle_score.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _dp,
+                                       ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_int, _dp, ctypes.c_int]
+            L.oracle_search.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                        ctypes.POINTER(OracleOpts), _dp, _dp, _dp,
+                                        ctypes.c_uint32, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.c_void_p, ctypes.c_int]
+            L.oracle_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                     ctypes.POINTER(OracleOpts), _dp, _dp, _dp,
+                                     ctypes.POINTER(ctypes.c_int), ctypes.c_void_p, ctypes.c_int]
+            L.oracle_replay.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                        ctypes.POINTER(OracleOpts), _dp, _dp, _dp,
+                                        ctypes.c_uint32, ctypes.c_int, _u32p, ctypes.c_void_p]
+            for f in ("oracle_init", "oracle_candidate", "oracle_score", "oracle_search",
+                      "oracle_run", "oracle_replay"):
+                getattr(L, f).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _flat(phi: np.ndarray) -> np.ndarray:
+    """(d, N) complex -> contiguous float64 buffer, column-major interleaved."""
+    a = np.asarray(phi, dtype=np.complex128)
+    return np.ascontiguousarray(a.T).view(np.float64).reshape(-1).copy()
+
+
+def _unflat(buf: np.ndarray, d: int, N: int) -> np.ndarray:
+    return buf.view(np.complex128).reshape(N, d).T.copy()
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise ValueError(f"oracle {what} failed with status {st}")
+
+
+def philox4x32_10(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*[int(x) & 0xffffffff for x in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xffffffff for x in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().oracle_philox4x32_10(c, k, o)
+    return [int(x) for x in o]
+
+
+def gauss_entry(seed, d, i, j, c, t, tag):
+    re, im = ctypes.c_double(), ctypes.c_double()
+    lib().oracle_gauss_entry(seed, d, i, j, c, t, tag, ctypes.byref(re), ctypes.byref(im))
+    return complex(re.value, im.value)
+
+
+def mu2(phi: np.ndarray) -> float:
+    d, N = phi.shape
+    b = _flat(phi)
+    return float(lib().oracle_mu2(N, d, _ptr(b)))
+
+
+def mu(phi: np.ndarray) -> float:
+    return float(np.sqrt(mu2(phi)))
+
+
+def welch(N: int, d: int) -> float:
+    return float(lib().oracle_welch(N, d))
+
+
+def init(N: int, d: int, seed: int) -> np.ndarray:
+    b = np.zeros(2 * d * N)
+    _check(lib().oracle_init(N, d, seed, _ptr(b)), "init")
+    return _unflat(b, d, N)
+
+
+def candidate(phi: np.ndarray, seed: int, delta: float, t: int, c: int) -> np.ndarray:
+    d, N = phi.shape
+    b = _flat(phi)
+    o = np.zeros_like(b)
+    _check(lib().oracle_candidate(N, d, seed, _ptr(b), delta, t, c, _ptr(o)), "candidate")
+    return _unflat(o, d, N)
+
+
+def score(phi: np.ndarray, seed: int, delta: float, t: int, c0: int, K: int,
+          nthreads: int = 1) -> np.ndarray:
+    """mu^2 of candidates c0..c0+K-1 of iteration t (float64 array of K)."""
+    d, N = phi.shape
+    b = _flat(phi)
+    out = np.zeros(K)
+    _check(lib().oracle_score(N, d, seed, _ptr(b), delta, t, c0, K, _ptr(out), nthreads),
+           "score")
+    return out
+
+
+def make_opts(K=256, T=100, delta0=0.1, gamma_inc=2.0, gamma_dec=0.25,
+              delta_min=1e-9, delta_max=1.0, target_mu=0.0) -> OracleOpts:
+    return OracleOpts(K, T, delta0, gamma_inc, gamma_dec, delta_min, delta_max, target_mu)
+
+
+def run(N: int, d: int, seed: int, opts: OracleOpts, nthreads: int = 1):
+    """Whole search from the seeded init.  Returns (phi, mu2, delta, trace)."""
+    b = np.zeros(2 * d * N)
+    m2, dl = ctypes.c_double(), ctypes.c_double()
+    it = ctypes.c_int()
+    tr = np.zeros(max(opts.T, 1), dtype=TRACE_DTYPE)
+    _check(lib().oracle_run(N, d, seed, ctypes.byref(opts), _ptr(b), ctypes.byref(m2),
+                            ctypes.byref(dl), ctypes.byref(it), tr.ctypes.data, nthreads),
+           "run")
+    return _unflat(b, d, N), m2.value, dl.value, tr[: it.value]
+
+
+def search(phi: np.ndarray, seed: int, opts: OracleOpts, delta: float, mu2_cur: float,
+           t0: int, nthreads: int = 1):
+    """Continue a search from a given state.  Returns (phi, mu2, delta, trace)."""
+    d, N = phi.shape
+    b = _flat(phi)
+    m2, dl = ctypes.c_double(mu2_cur), ctypes.c_double(delta)
+    it = ctypes.c_int()
+    tr = np.zeros(max(opts.T, 1), dtype=TRACE_DTYPE)
+    _check(lib().oracle_search(N, d, seed, ctypes.byref(opts), _ptr(b), ctypes.byref(dl),
+                               ctypes.byref(m2), t0, ctypes.byref(it), tr.ctypes.data,
+                               nthreads), "search")
+    return _unflat(b, d, N), m2.value, dl.value, tr[: it.value]
+
+
+def replay(phi: np.ndarray, seed: int, opts: OracleOpts, delta: float, mu2_cur: float,
+           t0: int, cstar_seq):
+    """Re-run the accept/radius rule on a given candidate choice per iteration."""
+    d, N = phi.shape
+    b = _flat(phi)
+    cs = np.ascontiguousarray(np.asarray(cstar_seq, dtype=np.uint32))
+    m2, dl = ctypes.c_double(mu2_cur), ctypes.c_double(delta)
+    tr = np.zeros(max(len(cs), 1), dtype=TRACE_DTYPE)
+    _check(lib().oracle_replay(N, d, seed, ctypes.byref(opts), _ptr(b), ctypes.byref(dl),
+                               ctypes.byref(m2), t0, len(cs),
+                               cs.ctypes.data_as(_u32p), tr.ctypes.data), "replay")
+    return _unflat(b, d, N), m2.value, dl.value, tr[: len(cs)]

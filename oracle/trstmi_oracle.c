@@ -1,0 +1,364 @@
+/*
+ * TRSTMI CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, double-precision restatement of the stochastic trust-region
+ * coherence search (Park, Saltijeral, Zhong, "Grassmannian packings:
+ * Trust-region stochastic tuning for matrix incoherence", arXiv 2207.06374).
+ * Only the test suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load this file's library.  It shares no code, header, table
+ * or constant generator with the CUDA path; its Philox generator and
+ * Box-Muller transform are written here from their published definitions.
+ *
+ * What is computed (notation of the paper, Sec. "Introduction"):
+ *   Phi in C^{d x N} with unit-norm columns phi_j, stored column-major with
+ *   interleaved (re, im): phi[2*(j*d + i) + 0] = Re Phi_ij, [.. + 1] = Im.
+ *   G = Phi^* Phi,  G_jk = sum_i conj(Phi_ij) Phi_ik  (Gram matrix, Sec. 1).
+ *   mu(Phi) = max_{j != k} |G_jk|  (coherence, Sec. 1); by the symmetry
+ *   |G_jk| = |G_kj| only j < k is visited (Sec. "Optimization procedure":
+ *   the upper-triangular part suffices).  Everything is reduced in |G|^2 and
+ *   one square root is taken at the end.
+ *   Welch bound mu >= sqrt((N-d)/(d(N-1))) (Sec. "Welch bound ...").
+ *
+ * The search (Algorithm "TRSTMI optimization steps", step 1 = random unit
+ * vectors; the Monte-Carlo sampling of Sec. "Optimization procedure") is read
+ * as a derivative-free trust-region iteration.  The paper prints no
+ * candidate step or radius rule; the reading used here is:
+ *   init:    Phi = normalise_cols(Z_init),  Z_init ~ CN(0,1) entrywise
+ *   iter t:  for c < K:  Phi_c = normalise_cols(Phi + Delta * Z_{t,c})
+ *            c* = argmin_c mu^2(Phi_c)   (lowest c on ties)
+ *            accept iff mu^2(Phi_c*) < mu^2(Phi)   (strict)
+ *            accept: Phi <- Phi_c*, Delta <- min(gamma_inc*Delta, Delta_max)
+ *            reject: Delta <- max(gamma_dec*Delta, Delta_min)
+ *            stop when mu(Phi) <= target or after T iterations.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
+ * random numbers: as easy as 1, 2, 3", SC'11), key = (seed lo32, seed hi32),
+ * counter = (e, c, t, tag) with e = j*ceil(d/2) + (i/2) the index of the pair
+ * of entries (i even, i+1) of column j; tag 0 = perturbation, 1 = init (c=t=0).
+ * One call gives u0..u3; U = (u + 1/2) 2^-32 in (0,1).  Entry i even uses
+ * (u0,u1), i odd uses (u2,u3): Z = sqrt(-ln U_a) * exp(2 pi i U_b), which is
+ * the Box-Muller pair (z, z') / sqrt(2), i.e. complex normal CN(0,1).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_EINVAL (-1)
+
+/* ---------------------------------------------------------------- Philox */
+
+/* Philox4x32 round constants as published (SC'11, Sec. 4.2 and Table 2). */
+static const uint32_t PHX_M0 = 0xD2511F53u, PHX_M1 = 0xCD9E8D57u;
+static const uint32_t PHX_W0 = 0x9E3779B9u, PHX_W1 = 0xBB67AE85u;
+
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                          uint32_t out[4])
+{
+    uint32_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += PHX_W0; k1 += PHX_W1; }
+        uint64_t p0 = (uint64_t)PHX_M0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)PHX_M1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* ------------------------------------------------------- Gaussian entries */
+
+static double u32_to_open01(uint32_t u)
+{
+    return ((double)u + 0.5) * (1.0 / 4294967296.0);
+}
+
+/* Z_ij for the counter slot (c, t, tag); see the header comment. */
+void oracle_gauss_entry(uint64_t seed, int d, int i, int j, uint32_t c,
+                        uint32_t t, uint32_t tag, double *re, double *im)
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t pairs_per_col = (uint32_t)((d + 1) / 2);
+    uint32_t ctr[4] = {(uint32_t)j * pairs_per_col + (uint32_t)(i / 2), c, t, tag};
+    uint32_t u[4];
+    oracle_philox4x32_10(ctr, key, u);
+    double ua = (i % 2 == 0) ? u32_to_open01(u[0]) : u32_to_open01(u[2]);
+    double ub = (i % 2 == 0) ? u32_to_open01(u[1]) : u32_to_open01(u[3]);
+    double r = sqrt(-log(ua));
+    double theta = 2.0 * M_PI * ub;
+    *re = r * cos(theta);
+    *im = r * sin(theta);
+}
+
+/* ------------------------------------------------------ columns and Gram */
+
+/* Divide every column by its 2-norm; a zero column is an error (the Remark
+ * on normalisation excludes zero columns). */
+static int normalise_columns(int N, int d, double *phi)
+{
+    for (int j = 0; j < N; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double a = phi[2 * (j * d + i)], b = phi[2 * (j * d + i) + 1];
+            s += a * a + b * b;
+        }
+        if (!(s > 0.0)) return ORACLE_EINVAL;
+        double nrm = sqrt(s);
+        for (int i = 0; i < d; ++i) {
+            phi[2 * (j * d + i)] /= nrm;
+            phi[2 * (j * d + i) + 1] /= nrm;
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* |G_jk|^2 with G_jk = sum_i conj(Phi_ij) Phi_ik. */
+double oracle_gram_abs2(int d, const double *phi, int j, int k)
+{
+    double re = 0.0, im = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double a = phi[2 * (j * d + i)], b = phi[2 * (j * d + i) + 1];
+        double x = phi[2 * (k * d + i)], y = phi[2 * (k * d + i) + 1];
+        /* (a - ib)(x + iy) = (ax + by) + i(ay - bx) */
+        re += a * x + b * y;
+        im += a * y - b * x;
+    }
+    return re * re + im * im;
+}
+
+/* mu(Phi)^2 = max_{j<k} |G_jk|^2 by enumerating every pair; 0 if N < 2. */
+double oracle_mu2(int N, int d, const double *phi)
+{
+    double m = 0.0;
+    for (int j = 0; j < N; ++j)
+        for (int k = j + 1; k < N; ++k) {
+            double g = oracle_gram_abs2(d, phi, j, k);
+            if (g > m) m = g;
+        }
+    return m;
+}
+
+/* Welch bound sqrt((N-d)/(d(N-1))), clamped at 0 for N <= d. */
+double oracle_welch(int N, int d)
+{
+    if (N <= d || N < 2) return 0.0;
+    return sqrt((double)(N - d) / ((double)d * (double)(N - 1)));
+}
+
+/* ------------------------------------------------ init and one candidate */
+
+int oracle_init(int N, int d, uint64_t seed, double *phi)
+{
+    if (N < 1 || d < 1 || !phi) return ORACLE_EINVAL;
+    for (int j = 0; j < N; ++j)
+        for (int i = 0; i < d; ++i)
+            oracle_gauss_entry(seed, d, i, j, 0, 0, 1, &phi[2 * (j * d + i)],
+                               &phi[2 * (j * d + i) + 1]);
+    return normalise_columns(N, d, phi);
+}
+
+/* Phi_c = normalise_cols(Phi + delta * Z_{t,c}). */
+int oracle_candidate(int N, int d, uint64_t seed, const double *phi,
+                     double delta, uint32_t t, uint32_t c, double *out)
+{
+    if (N < 1 || d < 1 || !phi || !out) return ORACLE_EINVAL;
+    for (int j = 0; j < N; ++j)
+        for (int i = 0; i < d; ++i) {
+            double zr, zi;
+            oracle_gauss_entry(seed, d, i, j, c, t, 0, &zr, &zi);
+            out[2 * (j * d + i)] = phi[2 * (j * d + i)] + delta * zr;
+            out[2 * (j * d + i) + 1] = phi[2 * (j * d + i) + 1] + delta * zi;
+        }
+    return normalise_columns(N, d, out);
+}
+
+/* ------------------------------------------- scoring many candidates */
+
+typedef struct {
+    int N, d;
+    uint64_t seed;
+    const double *phi;
+    double delta;
+    uint32_t t, c0;
+    int begin, end;
+    double *mu2;
+    int status;
+} score_job;
+
+static void *score_worker(void *arg)
+{
+    score_job *jb = (score_job *)arg;
+    double *buf = (double *)malloc(sizeof(double) * 2 * (size_t)jb->d * (size_t)jb->N);
+    jb->status = ORACLE_OK;
+    if (!buf) { jb->status = ORACLE_EINVAL; return NULL; }
+    for (int k = jb->begin; k < jb->end; ++k) {
+        int st = oracle_candidate(jb->N, jb->d, jb->seed, jb->phi, jb->delta,
+                                  jb->t, jb->c0 + (uint32_t)k, buf);
+        if (st != ORACLE_OK) { jb->status = st; break; }
+        jb->mu2[k] = oracle_mu2(jb->N, jb->d, buf);
+    }
+    free(buf);
+    return NULL;
+}
+
+/* mu^2 of candidates c0 .. c0+K-1 of iteration t, split over nthreads. */
+int oracle_score(int N, int d, uint64_t seed, const double *phi, double delta,
+                 uint32_t t, uint32_t c0, int K, double *mu2, int nthreads)
+{
+    if (N < 1 || d < 1 || K < 0 || !phi || (K > 0 && !mu2)) return ORACLE_EINVAL;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > K) nthreads = K > 0 ? K : 1;
+    score_job *jobs = (score_job *)calloc((size_t)nthreads, sizeof(score_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return ORACLE_EINVAL; }
+    for (int w = 0; w < nthreads; ++w) {
+        jobs[w] = (score_job){N, d, seed, phi, delta, t, c0,
+                              (int)((long long)K * w / nthreads),
+                              (int)((long long)K * (w + 1) / nthreads), mu2, 0};
+    }
+    for (int w = 1; w < nthreads; ++w) pthread_create(&th[w], NULL, score_worker, &jobs[w]);
+    score_worker(&jobs[0]);
+    for (int w = 1; w < nthreads; ++w) pthread_join(th[w], NULL);
+    int st = ORACLE_OK;
+    for (int w = 0; w < nthreads; ++w) if (jobs[w].status != ORACLE_OK) st = jobs[w].status;
+    free(jobs); free(th);
+    return st;
+}
+
+/* -------------------------------------------------------- the search */
+
+typedef struct {
+    int K;             /* candidates per iteration */
+    int T;             /* iteration budget */
+    double delta0;     /* initial trust radius */
+    double gamma_inc;  /* expansion factor on accept */
+    double gamma_dec;  /* contraction factor on reject */
+    double delta_min, delta_max;
+    double target_mu;  /* stop once mu <= target (<= 0: never) */
+} oracle_opts;
+
+typedef struct {
+    uint32_t t;        /* iteration counter used for the candidates */
+    uint32_t cstar;    /* best candidate */
+    double mu2_best;   /* its mu^2 */
+    double mu2_cur;    /* mu^2 of Phi after the decision */
+    double delta_used; /* radius the candidates were drawn with */
+    double delta_next; /* radius after the update */
+    int32_t accepted;
+    int32_t pad;
+} oracle_trace_row;
+
+static void apply_rule(const oracle_opts *o, int accept, double *delta)
+{
+    if (accept) {
+        double v = o->gamma_inc * *delta;
+        *delta = v < o->delta_max ? v : o->delta_max;
+    } else {
+        double v = o->gamma_dec * *delta;
+        *delta = v > o->delta_min ? v : o->delta_min;
+    }
+}
+
+/*
+ * Runs iterations t = t0+1 .. t0+T from the state (phi, delta, mu2) in place.
+ * Returns the number of iterations done through *iters.  trace may be NULL,
+ * else it has room for T rows.
+ */
+int oracle_search(int N, int d, uint64_t seed, const oracle_opts *o,
+                  double *phi, double *delta, double *mu2_cur, uint32_t t0,
+                  int *iters, oracle_trace_row *trace, int nthreads)
+{
+    if (!o || !phi || !delta || !mu2_cur || !iters || o->K < 1 || o->T < 0)
+        return ORACLE_EINVAL;
+    size_t n = 2 * (size_t)d * (size_t)N;
+    double *mu2 = (double *)malloc(sizeof(double) * (size_t)o->K);
+    double *cand = (double *)malloc(sizeof(double) * n);
+    if (!mu2 || !cand) { free(mu2); free(cand); return ORACLE_EINVAL; }
+    double target2 = o->target_mu > 0 ? o->target_mu * o->target_mu : -1.0;
+    int done = 0, st = ORACLE_OK;
+    for (int it = 0; it < o->T; ++it) {
+        if (*mu2_cur <= target2) break;
+        uint32_t t = t0 + (uint32_t)it + 1u;
+        st = oracle_score(N, d, seed, phi, *delta, t, 0, o->K, mu2, nthreads);
+        if (st != ORACLE_OK) break;
+        int cstar = 0;
+        for (int c = 1; c < o->K; ++c) if (mu2[c] < mu2[cstar]) cstar = c;
+        int accept = mu2[cstar] < *mu2_cur;
+        double dused = *delta;
+        if (accept) {
+            st = oracle_candidate(N, d, seed, phi, dused, t, (uint32_t)cstar, cand);
+            if (st != ORACLE_OK) break;
+            memcpy(phi, cand, sizeof(double) * n);
+            *mu2_cur = mu2[cstar];
+        }
+        apply_rule(o, accept, delta);
+        if (trace) {
+            trace[it].t = t; trace[it].cstar = (uint32_t)cstar;
+            trace[it].mu2_best = mu2[cstar]; trace[it].mu2_cur = *mu2_cur;
+            trace[it].delta_used = dused; trace[it].delta_next = *delta;
+            trace[it].accepted = accept; trace[it].pad = 0;
+        }
+        ++done;
+    }
+    *iters = done;
+    free(mu2); free(cand);
+    return st;
+}
+
+/* Whole run from the seeded initialisation. */
+int oracle_run(int N, int d, uint64_t seed, const oracle_opts *o, double *phi,
+               double *mu2_out, double *delta_out, int *iters,
+               oracle_trace_row *trace, int nthreads)
+{
+    if (!o || !phi || !mu2_out || !delta_out || !iters) return ORACLE_EINVAL;
+    int st = oracle_init(N, d, seed, phi);
+    if (st != ORACLE_OK) return st;
+    *mu2_out = oracle_mu2(N, d, phi);
+    *delta_out = o->delta0;
+    return oracle_search(N, d, seed, o, phi, delta_out, mu2_out, 0, iters, trace,
+                         nthreads);
+}
+
+/*
+ * Replays a given sequence of chosen candidates (one per iteration t0+1 ..
+ * t0+T): each is regenerated in double precision, scored exactly and put
+ * through the accept/radius rule.  Used to check a run whose candidate
+ * selection was made elsewhere (e.g. by a reduced-precision screen).
+ */
+int oracle_replay(int N, int d, uint64_t seed, const oracle_opts *o,
+                  double *phi, double *delta, double *mu2_cur, uint32_t t0,
+                  int T, const uint32_t *cstar_seq, oracle_trace_row *trace)
+{
+    if (!o || !phi || !delta || !mu2_cur || T < 0 || (T > 0 && !cstar_seq))
+        return ORACLE_EINVAL;
+    size_t n = 2 * (size_t)d * (size_t)N;
+    double *cand = (double *)malloc(sizeof(double) * n);
+    if (!cand) return ORACLE_EINVAL;
+    int st = ORACLE_OK;
+    for (int it = 0; it < T; ++it) {
+        uint32_t t = t0 + (uint32_t)it + 1u;
+        double dused = *delta;
+        st = oracle_candidate(N, d, seed, phi, dused, t, cstar_seq[it], cand);
+        if (st != ORACLE_OK) break;
+        double m2 = oracle_mu2(N, d, cand);
+        int accept = m2 < *mu2_cur;
+        if (accept) { memcpy(phi, cand, sizeof(double) * n); *mu2_cur = m2; }
+        apply_rule(o, accept, delta);
+        if (trace) {
+            trace[it].t = t; trace[it].cstar = cstar_seq[it];
+            trace[it].mu2_best = m2; trace[it].mu2_cur = *mu2_cur;
+            trace[it].delta_used = dused; trace[it].delta_next = *delta;
+            trace[it].accepted = accept; trace[it].pad = 0;
+        }
+    }
+    free(cand);
+    return st;
+}
