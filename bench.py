@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""Benchmark: off-diagonal Gram pairs scored per second by the TRSTMI search.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision bf16|fp32|fp64] [--workload NAME]
+
+A step is one iteration of the whole search on one instance: K candidates
+perturbed, renormalised and scored by their exact coherence, the best one
+selected (screen modes: top-k re-scored in fp32, the winner certified in
+fp64) and the accept/radius rule applied.  Default workload: complex d = 32,
+N = 1024, 1024 candidates per iteration, bf16 tensor-core screen + fp32 top-8
+re-score + fp64 certification; the plain fp32 path on the same workload is
+reported beside it.
+
+Timing: each timed step is bracketed by CUDA events on the library's stream;
+between steps a 512 MiB device buffer is rewritten (L2 flush, outside the
+events).  Multi-GPU (torchrun): every rank runs an independent instance
+(seed + rank; weak scaling, no collective on the data path); the reported
+time is the max over ranks.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (d, N, K, precision, description)
+    "precision_d32_n1024": (32, 1024, 1024, "bf16",
+                            "complex d=32 N=1024, 1024 candidates/iteration, bf16 screen + "
+                            "fp32 top-8 re-score + fp64 certify"),
+    "plain_d32_n1024_fp32": (32, 1024, 1024, "fp32",
+                             "complex d=32 N=1024, 1024 candidates/iteration, plain fp32"),
+    "plain_d8_n64": (8, 64, 4096, "fp32",
+                     "complex d=8 N=64, 4096 candidates/iteration, plain fp32"),
+    "plain_d2_n4_fp64": (2, 4, 256, "fp64",
+                         "complex d=2 N=4, 256 candidates/iteration, fp64"),
+}
+L2_FLUSH_BYTES = 512 << 20
+SEED = 1
+
+
+def pairs_per_step(d, N, K):
+    return K * N * (N - 1) // 2
+
+
+def flops_per_pair(d):
+    # Re and Im of <phi_j, phi_k>: 2 real dot products of length 2d, 2 flops each
+    return 8 * d
+
+
+def kernels_per_step(precision):
+    # one k_set_stop per trstmi_step call plus the iteration's kernels
+    return 1 + {"fp64": 4, "fp32": 4, "bf16": 11}[precision]
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """Samples nvidia-smi clocks/throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.dev = device_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        except OSError:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def cpu_baseline(d, N, K, steps=1):
+    """The oracle, as it stands, scoring one full iteration's candidates (a2-a6)
+    on the host cores.  Returns a dict for the JSON line."""
+    import oracle as O
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    phi = O.init(N, d, SEED)
+    # bounded sample: at most ~10-30 s of CPU work
+    per_cand = pairs_per_step(d, N, 1)
+    budget_pairs = 60_000_000 * cores * 4
+    count = int(max(cores, min(K, budget_pairs // max(per_cand, 1))))
+    t0 = time.perf_counter()
+    for s in range(steps):
+        O.score(phi, SEED, 0.1, 1 + s, 0, count, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = steps * count * per_cand / dt
+    return {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+            "sample": f"{count} of the {K} candidates of iteration t=1..{steps} (d={d}, N={N}) "
+                      f"scored by the fp64 oracle (generation + all-pairs |G|^2 max), "
+                      f"{steps} step(s), {dt:.2f} s"}
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    d, N, K, prec, desc = WORKLOADS[wl]
+    steps, warm = args.steps, args.warmup
+    import oracle as O
+    cores = len(os.sched_getaffinity(0))
+    phi = O.init(N, d, SEED)
+    per_cand = pairs_per_step(d, N, 1)
+    count = int(max(cores, min(K, (30_000_000 * cores) // max(per_cand, 1))))
+    for w in range(warm):
+        O.score(phi, SEED, 0.1, 1 + w, 0, min(count, cores), nthreads=cores)
+    t0 = time.perf_counter()
+    for s in range(steps):
+        O.score(phi, SEED, 0.1, 1 + s, 0, count, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = steps * count * per_cand / dt
+    line = {"impl": "reference", "metric": "off-diagonal Gram pairs scored per second",
+            "value": value, "unit": "pairs/s", "n_gpus": 1, "steps": steps, "warmup": warm,
+            "ms_per_step": dt / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox frames)",
+            "config": {"workload": wl, "d": d, "N": N, "K": K, "precision": "fp64 oracle",
+                       "sample_candidates_per_step": count},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{count} of {K} candidates per step, d={d}, N={N}"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="precision_d32_n1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side", action="store_true", help="skip the fp32 side-by-side run")
+    args = ap.parse_args()
+    wl = args.workload
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2207_06374_gb300 import trstmi as T
+
+    d, N, K, prec, desc = WORKLOADS[wl]
+    if prec == "bf16":
+        probe = T.lib()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_run(precision, steps, warmup, seed):
+        s = T.Search(N, d, seed, K=K, precision=precision, device=local, trace_cap=64)
+        for _ in range(warmup):
+            s.step(1)
+        times = []
+        barrier()
+        t_wall = time.perf_counter()
+        for _ in range(steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            info = s.step(1)
+            times.append(info.elapsed_ns * 1e-9)
+        barrier()
+        wall = time.perf_counter() - t_wall
+        return s, times, wall
+
+    seed = SEED + rank
+    with Clocks(local) as clk:
+        s, times, wall = timed_run(prec, args.steps, args.warmup, seed)
+        # live per-kernel timing of the dominant (scoring) kernel on the same stream
+        kernel_ms = s.profile_score(prec, launches=5, delta=0.1, flush_bytes=L2_FLUSH_BYTES)
+    clocks = clk.summary()
+    t_dev = sum(times)
+    if dist:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    pps = pairs_per_step(d, N, K)
+    value = ws * args.steps * pps / t_dev
+
+    # end to end through the public API: host frame in (pinned), one iteration,
+    # frame and mu out, per step
+    phi_host = torch.empty(2 * d * N, dtype=torch.float64, pin_memory=True)
+    phi_host.copy_(torch.from_numpy(T._flat(s.get_phi())))
+    out_host = torch.empty(2 * d * N, dtype=torch.float64, pin_memory=True)
+    L = T.lib()
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    e2e_steps = max(3, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        T._check(L.trstmi_set_phi(s._h, ctypes.cast(phi_host.data_ptr(), dp)), "set_phi")
+        s.step(1)
+        T._check(L.trstmi_get_phi(s._h, ctypes.cast(out_host.data_ptr(), dp)), "get_phi")
+        mu = ctypes.c_double()
+        T._check(L.trstmi_coherence(s._h, ctypes.byref(mu), None), "coherence")
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": ws * e2e_steps * pps / t_e2e, "unit": "pairs/s",
+           "h2d_bytes_per_step": 16 * d * N, "d2h_bytes_per_step": 16 * d * N + 8,
+           "call": "trstmi_set_phi + trstmi_step(1) + trstmi_get_phi + trstmi_coherence"}
+
+    peaks, peak_kind = measured_peaks()
+    flops_launch = pps * flops_per_pair(d)
+    if prec == "bf16":
+        peak = peaks.get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "unit": "TFLOP/s"}
+        peak_note = f"bf16_tflops burst ({peak_kind})"
+    else:
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = fp32_alu_peak_tflops(sm_mhz) if prec == "fp32" else fp32_alu_peak_tflops(sm_mhz) / 64
+        roof = {"bound": "alu", "unit": "TFLOP/s"}
+        peak_note = (f"{prec} FMA peak derived: 152 SMs x "
+                     f"{'128' if prec == 'fp32' else '2'} lanes x 2 flops x {sm_mhz} MHz")
+    achieved = flops_launch / (kernel_ms * 1e-3) / 1e12
+    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                 "traffic": None, "kernel": "tc_screen_bf16" if prec == "bf16" else "k_gram_tile",
+                 "kernel_ms": kernel_ms, "flops_per_launch": flops_launch, "peak_source": peak_note})
+
+    side = None
+    if prec == "bf16" and not args.no_side:
+        s2, times2, _ = timed_run("fp32", max(2, args.steps // 4), 1, seed)
+        side = {"precision": "fp32 plain", "value": ws * len(times2) * pps / sum(times2),
+                "unit": "pairs/s", "ms_per_step": 1e3 * sum(times2) / len(times2)}
+        s2.close()
+
+    line = {"metric": "off-diagonal Gram pairs scored per second (K*N(N-1)/2 per iteration)",
+            "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16": "bf16", "fp32": "f32", "fp64": "f64"}[prec],
+            "data": "synthetic (seeded Philox complex-Gaussian frames)",
+            "config": {"workload": wl, "description": desc, "d": d, "N": N, "K": K,
+                       "precision": prec, "seed": SEED, "l2": "flushed between steps "
+                       f"({L2_FLUSH_BYTES >> 20} MiB write outside the timed events)",
+                       "parallelism": f"independent instance per GPU x{ws}"},
+            "roofline": roof, "gpu_launches": kernels_per_step(prec) * args.steps,
+            "e2e": e2e, "clocks": clocks, "mu_after": s.coherence()[0]}
+    if side:
+        line["side_by_side_fp32"] = side
+    s.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(d, N, K)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

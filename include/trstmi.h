@@ -1,0 +1,209 @@
+/*
+ * trstmi.h -- C ABI of the GB300 (sm_103a) TRSTMI coherence-search library.
+ *
+ * The library searches for complex frames Phi in C^{d x N} with unit-norm
+ * columns and low coherence mu(Phi) = max_{j != k} |<phi_j, phi_k>|
+ * (arXiv 2207.06374, Sec. "Introduction", definition of mu_{N,d}).  Each
+ * iteration of the stochastic trust-region search scores K random candidates
+ *     Phi_c = normalise_columns(Phi + Delta * Z_{t,c}),  Z ~ CN(0,1) entrywise
+ * by their exact coherence, keeps the best one if it lowers mu, and expands or
+ * contracts the trust radius Delta (the Monte-Carlo sampling and trust-region
+ * framework of Sec. "Optimization procedure"; the candidate step and the radius
+ * rule are this library's reading of that section, stated with each field).
+ *
+ * Conventions
+ *   - Every function returns an int status: TRSTMI_OK (0), TRSTMI_PENDING (1)
+ *     or a negative error code; trstmi_strerror() names it.
+ *   - Frames crossing the ABI are HOST buffers owned by the caller: 2*d*N
+ *     doubles, column-major with interleaved (re, im), i.e. element (i, j) at
+ *     [2*(j*d + i)] (real) and [2*(j*d + i) + 1] (imaginary).
+ *   - Handles are opaque and owned by the library.  One handle must not be
+ *     used from two threads at once.
+ *   - All device work is issued on the stream given in the options (NULL =
+ *     a stream the library creates); calls that return host data synchronise
+ *     that stream.  There is no CPU fallback: without a usable CUDA device
+ *     every call that needs one returns TRSTMI_ECUDA.
+ */
+#ifndef TRSTMI_H
+#define TRSTMI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- statuses */
+#define TRSTMI_OK 0
+#define TRSTMI_PENDING 1
+#define TRSTMI_EINVAL (-1)       /* bad argument (sizes, NULL pointers, options) */
+#define TRSTMI_ENOMEM (-2)       /* device allocation failed or budget exceeded */
+#define TRSTMI_ECUDA (-3)        /* CUDA runtime error or no device */
+#define TRSTMI_ETIMEOUT (-4)     /* a device-side wait hit its time limit */
+#define TRSTMI_ECANCELLED (-5)   /* request cancelled */
+#define TRSTMI_EBUSY (-6)        /* queue full */
+#define TRSTMI_EUNSUPPORTED (-7) /* shape/precision combination not built */
+#define TRSTMI_ENOTFOUND (-8)    /* unknown ticket */
+
+/* ----------------------------------------------------- precision modes */
+typedef enum trstmi_precision {
+  /* candidates generated, scored and accepted in binary64 */
+  TRSTMI_FP64 = 0,
+  /* complex64 storage, binary32 Gram; acceptance on the binary32 mu */
+  TRSTMI_FP32 = 1,
+  /* candidates screened by a bf16 tensor-core Gram (fp32 accumulation), the
+     top-k survivors re-scored in binary32, the best survivor regenerated,
+     renormalised and certified in binary64; acceptance on the binary64 mu */
+  TRSTMI_BF16_SCREEN = 2
+} trstmi_precision;
+
+/* ---------------------------------------------------------- options */
+typedef struct trstmi_options {
+  int32_t K;            /* candidates per iteration (default 256), >= 1 */
+  int32_t precision;    /* trstmi_precision (default TRSTMI_FP64) */
+  int32_t topk;         /* BF16_SCREEN: survivors re-scored in fp32 (default 8, 1..64) */
+  int32_t trace_cap;    /* rows of the per-iteration trace ring (default 4096, >= 0) */
+  double delta0;        /* initial trust radius (default 0.1), > 0 */
+  double gamma_inc;     /* radius factor on accept (default 2.0), >= 1 */
+  double gamma_dec;     /* radius factor on reject (default 0.25), in (0, 1] */
+  double delta_min;     /* radius floor (default 1e-9) */
+  double delta_max;     /* radius cap (default 1.0) */
+  double target_mu;     /* stop once mu <= target_mu (default 0 = never) */
+  void *stream;         /* cudaStream_t to issue on, or NULL */
+  int32_t device;       /* CUDA device ordinal (default 0) */
+  int32_t reserved0;
+} trstmi_options;
+
+/* Fills *opt with the defaults listed above. */
+void trstmi_default_options(trstmi_options *opt);
+
+typedef struct trstmi_instance *trstmi_handle;
+
+/* One row per iteration (binary64 values are mu^2, not mu). */
+typedef struct trstmi_trace_row {
+  uint32_t t;           /* iteration counter (1-based) */
+  uint32_t cstar;       /* chosen candidate index */
+  double mu2_best;      /* mu^2 of the chosen candidate in the deciding precision */
+  double mu2_screen;    /* its screen (bf16) or fp32 score; = mu2_best otherwise */
+  double mu2_cur;       /* mu^2 of the current frame after the decision */
+  double delta_used;    /* radius the candidates were drawn with */
+  double delta_next;    /* radius after the update */
+  int32_t accepted;     /* 1 if the candidate replaced the frame */
+  int32_t reserved;
+} trstmi_trace_row;
+
+typedef struct trstmi_step_info {
+  int32_t iters_done;   /* iterations run by this call */
+  int32_t accepts;      /* accepted candidates in this call */
+  double mu;            /* mu of the current frame (deciding precision) */
+  double delta;         /* current radius */
+  uint64_t pairs_scored;/* K * N(N-1)/2 per iteration run (screen pairs in BF16 mode) */
+  uint64_t elapsed_ns;  /* device time of the call (CUDA events) */
+  int32_t done;         /* 1 once mu <= target_mu */
+  int32_t reserved;
+} trstmi_step_info;
+
+/*
+ * Creates a search instance for N >= 2 columns in C^d, d >= 1 (N <= d is
+ * allowed; its optimum is mu = 0).  Allocates the device state, draws the
+ * seeded initial frame (Algorithm "TRSTMI optimization steps", step 1: random
+ * unit vectors; Philox counter tag 1) and scores it in the deciding precision.
+ * opt may be NULL for the defaults.  On error *out is set to NULL.
+ */
+int trstmi_create(int N, int d, uint64_t seed, const trstmi_options *opt,
+                  trstmi_handle *out);
+
+/*
+ * Runs up to iters >= 0 iterations (fewer if mu reaches target_mu).  Issues
+ * them as replays of a captured CUDA graph with no host synchronisation
+ * between iterations; synchronises the stream once at the end.  info may be
+ * NULL.
+ */
+int trstmi_step(trstmi_handle h, int iters, trstmi_step_info *info);
+
+/*
+ * Certified coherence of the current frame: the frame is renormalised in
+ * binary64 and mu computed in binary64 over all pairs j < k (a binary32
+ * pass preselects the pairs within its rounding-error bound of the max, the
+ * maximum over those is taken in binary64 -- exact by that bound).
+ * welch (nullable) receives sqrt((N-d)/(d(N-1))) (Sec. "Welch bound and
+ * equiangular lines"), 0 for N <= d.
+ */
+int trstmi_coherence(trstmi_handle h, double *mu, double *welch);
+
+/* Copies the current binary64 frame to out (2*d*N doubles, host). */
+int trstmi_get_phi(trstmi_handle h, double *out);
+
+/* Replaces the frame (host buffer, 2*d*N doubles); columns are renormalised
+ * in binary64 and the frame rescored.  A zero column is TRSTMI_EINVAL. */
+int trstmi_set_phi(trstmi_handle h, const double *in);
+
+/*
+ * Checkpoint: the whole search state (frame, radius, iteration counter,
+ * current mu, accept count, options, seed) as a self-describing blob.  With
+ * blob == NULL, *size receives the size needed.  Because every random draw
+ * is a pure function of (seed, t, c), restoring a blob and running m
+ * iterations gives bit-identical results to running them without the
+ * interruption.
+ */
+int trstmi_get_state(trstmi_handle h, void *blob, size_t *size);
+int trstmi_set_state(trstmi_handle h, const void *blob, size_t size);
+
+/* Copies the last min(n, trace_cap, iterations run) trace rows, oldest
+ * first, to rows; *n_out receives the count. */
+int trstmi_get_trace(trstmi_handle h, trstmi_trace_row *rows, int n, int *n_out);
+
+/* Frees everything.  Safe on NULL. */
+void trstmi_destroy(trstmi_handle h);
+
+/* Static string for a status code. */
+const char *trstmi_strerror(int status);
+
+/* ---------------------------------------------- scoring entry points
+ * These run one stage of the iteration on the current frame without
+ * changing the search state; the tests use them to compare the kernels with
+ * an independent implementation on identical seeded candidates.
+ */
+
+/*
+ * mu^2 of candidates c0 .. c0+count-1 of iteration t (t >= 1) drawn with
+ * radius delta around the current frame, scored by the kernel of the given
+ * precision: TRSTMI_FP64 (binary64 generation and Gram), TRSTMI_FP32
+ * (binary32) or TRSTMI_BF16_SCREEN (the tensor-core screen alone, before
+ * any re-scoring).  mu2 is a host array of count doubles.
+ */
+int trstmi_score(trstmi_handle h, uint32_t t, uint32_t c0, int count, double delta,
+                 int precision, double *mu2);
+
+/* Candidate c of iteration t as generated on the device in binary64
+ * (precision TRSTMI_FP64) or binary32 (TRSTMI_FP32, widened), host out. */
+int trstmi_candidate(trstmi_handle h, uint32_t t, uint32_t c, double delta,
+                     int precision, double *out);
+
+/*
+ * mu^2 of a caller frame (host, 2*d*N doubles, columns used as given) by the
+ * Gram kernel of the given precision (TRSTMI_FP64 or TRSTMI_FP32; the frame
+ * is rounded to the precision first).  Stateless; device 0, default stream.
+ */
+int trstmi_mu2_frame(int N, int d, const double *phi, int precision, double *mu2);
+
+/* ------------------------------------------------- measurement entry point */
+
+/*
+ * Times the candidate-scoring kernel of the instance alone: `launches`
+ * launches over the instance's K candidates (iteration t = 1, 2, ...; radius
+ * delta around the current frame), each bracketed by CUDA events on the
+ * instance's stream.  Between launches, outside the timed spans, flush_bytes
+ * of device scratch (0 = none) are overwritten so each launch starts with a
+ * cold L2.  *avg_ms receives the mean device time of one launch.  The
+ * precision selects the kernel: TRSTMI_FP64 / TRSTMI_FP32 (SIMT Gram) or
+ * TRSTMI_BF16_SCREEN (tensor-core screen).  Does not change the search state.
+ */
+int trstmi_profile_score(trstmi_handle h, int precision, int launches, double delta,
+                         size_t flush_bytes, double *avg_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRSTMI_H */

@@ -1,0 +1,753 @@
+// Host runtime and C ABI of the TRSTMI library (see include/trstmi.h).
+//
+// One instance = one search: its frame (binary64 master + binary32 copy),
+// radius, counters and scratch live in one device allocation.  An iteration
+// is a fixed sequence of kernels that read and write the device-resident
+// state (DevState), so `iters` iterations are captured once as a CUDA graph
+// and replayed with no host round trip; the host synchronises once per call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/trstmi.h"
+#include "kernels.h"
+
+using namespace trstmi;
+
+namespace {
+
+constexpr uint32_t kBlobMagic = 0x54525354u;  // "TRST"
+constexpr uint32_t kBlobVersion = 1u;
+constexpr uint32_t kPairCap = 1u << 16;
+constexpr int kGraphChunk = 32;
+
+std::mutex g_attr_mu;
+bool g_attr_done[64] = {false};
+
+int ensure_device(int device, int* num_sms) {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0) return TRSTMI_ECUDA;
+  if (device < 0 || device >= n || device >= 64) return TRSTMI_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return TRSTMI_ECUDA;
+  {
+    std::lock_guard<std::mutex> g(g_attr_mu);
+    if (!g_attr_done[device]) {
+      if (init_kernel_attributes() != cudaSuccess) return TRSTMI_ECUDA;
+      g_attr_done[device] = true;
+    }
+  }
+  if (cudaDeviceGetAttribute(num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    return TRSTMI_ECUDA;
+  return TRSTMI_OK;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct trstmi_instance {
+  int N = 0, d = 0;
+  uint64_t seed = 0;
+  trstmi_options opt{};
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* block = nullptr;
+  size_t block_bytes = 0;
+  // carved from block
+  DevState* st = nullptr;
+  double2* phi64 = nullptr;
+  float2* phi32 = nullptr;
+  double2* cand64 = nullptr;
+  float2* cand32 = nullptr;
+  double2* scratch64 = nullptr;
+  unsigned int* mu2_k32 = nullptr;         // K
+  unsigned long long* mu2_k64 = nullptr;   // K
+  unsigned int* mu2_top = nullptr;         // topk
+  uint32_t* topk = nullptr;                // topk
+  unsigned int* cert32 = nullptr;          // 1
+  unsigned long long* cert64 = nullptr;    // 1
+  uint32_t* misc = nullptr;                // [0] npairs, [1] overflow (standalone certify)
+  uint2* pairs = nullptr;                  // kPairCap
+  TraceRowDev* trace = nullptr;            // trace_cap
+  std::map<int, cudaGraphExec_t> graphs;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+double welch_of(int N, int d) {
+  if (N <= d || N < 2) return 0.0;
+  return std::sqrt((double)(N - d) / ((double)d * (double)(N - 1)));
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? TRSTMI_OK : TRSTMI_ECUDA; }
+
+#define TRY_CUDA(expr)                                   \
+  do {                                                   \
+    cudaError_t _e = (expr);                             \
+    if (_e != cudaSuccess) return TRSTMI_ECUDA;          \
+  } while (0)
+
+float certify_margin(int d) {
+  // |G| in binary32 of a frame rounded from binary64 differs from the
+  // binary64 |G| by at most ~(2 + 2*(2d) ) u, u = 2^-24 (rounding of the
+  // entries plus a 2d-term dot product per part); twice a generous 4x of
+  // that bound separates "can be the max" from "cannot".
+  return (float)(8.0 * (2.0 * d + 2.0) * std::ldexp(1.0, -24));
+}
+
+// binary64 mu^2 of a normalised binary64 frame (with its binary32 rounding)
+// into out64: binary32 max, binary32 preselection of the pairs within the
+// error bound, binary64 over those pairs, full binary64 pass on overflow.
+int enqueue_certify(trstmi_instance* h, const double2* f64, const float2* f32,
+                    unsigned long long* out64, const uint32_t* active, uint32_t* npairs,
+                    uint32_t* overflow, cudaStream_t s) {
+  GramSource src{};
+  src.perturb = false;
+  src.phi = f32;
+  src.normalize = false;
+  src.gate = active;
+  TRY_CUDA(launch_gram_f32(h->N, h->d, 1, src, h->cert32, nullptr, h->num_sms, s));
+  PairFilter pf{h->cert32, certify_margin(h->d), h->pairs, npairs, kPairCap, overflow};
+  TRY_CUDA(launch_gram_f32(h->N, h->d, 1, src, h->cert32 + 1, &pf, h->num_sms, s));
+  TRY_CUDA(launch_pairs64(active, npairs, h->pairs, kPairCap, h->d, f64, out64, s));
+  GramSource full{};
+  full.perturb = false;
+  full.phi = f64;
+  full.normalize = false;
+  full.gate = overflow;  // reset every iteration, so 0 when the iteration is inactive
+  TRY_CUDA(launch_gram_f64(h->N, h->d, 1, full, out64, h->num_sms, s));
+  return TRSTMI_OK;
+}
+
+__global__ void k_set_mu2cur(DevState* st, const unsigned int* b32, const unsigned long long* b64) {
+  st->mu2_cur = b64 ? nonneg_from_bits(*b64) : (double)nonneg_from_bits(*b32);
+  st->done = (st->mu2_cur <= st->target2) ? 1u : 0u;
+}
+
+__global__ void k_set_stop(DevState* st, uint32_t iters) {
+  const unsigned long long stop = (unsigned long long)st->t + iters;
+  st->t_stop = stop > 0xffffffffull ? 0xffffffffu : (uint32_t)stop;
+}
+
+// Score the current frame in the deciding precision into st->mu2_cur.
+int enqueue_rescore_current(trstmi_instance* h) {
+  cudaStream_t s = h->stream;
+  const int prec = h->opt.precision;
+  if (prec == TRSTMI_FP32) {
+    TRY_CUDA(cudaMemsetAsync(h->cert32, 0, 2 * sizeof(unsigned int), s));
+    GramSource src{};
+    src.perturb = false;
+    src.phi = h->phi32;
+    TRY_CUDA(launch_gram_f32(h->N, h->d, 1, src, h->cert32, nullptr, h->num_sms, s));
+    k_set_mu2cur<<<1, 1, 0, s>>>(h->st, h->cert32, nullptr);
+  } else if (prec == TRSTMI_FP64) {
+    TRY_CUDA(cudaMemsetAsync(h->cert64, 0, sizeof(unsigned long long), s));
+    GramSource src{};
+    src.perturb = false;
+    src.phi = h->phi64;
+    TRY_CUDA(launch_gram_f64(h->N, h->d, 1, src, h->cert64, h->num_sms, s));
+    k_set_mu2cur<<<1, 1, 0, s>>>(h->st, nullptr, h->cert64);
+  } else {
+    TRY_CUDA(cudaMemsetAsync(h->cert32, 0, 2 * sizeof(unsigned int), s));
+    TRY_CUDA(cudaMemsetAsync(h->cert64, 0, sizeof(unsigned long long), s));
+    TRY_CUDA(cudaMemsetAsync(h->misc, 0, 2 * sizeof(uint32_t), s));
+    int rc = enqueue_certify(h, h->phi64, h->phi32, h->cert64, nullptr, h->misc, h->misc + 1, s);
+    if (rc) return rc;
+    k_set_mu2cur<<<1, 1, 0, s>>>(h->st, nullptr, h->cert64);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+// One iteration of the search, enqueued on s (captured into the graph).
+int enqueue_iteration(trstmi_instance* h, cudaStream_t s) {
+  const int N = h->N, d = h->d, K = h->opt.K;
+  DevState* st = h->st;
+  const int prec = h->opt.precision;
+  if (prec == TRSTMI_FP64) {
+    TRY_CUDA(launch_iter_begin(st, h->mu2_k64, sizeof(unsigned long long) * K, nullptr, 0,
+                               nullptr, 0, s));
+    GramSource src{};
+    src.perturb = true;
+    src.phi = h->phi64;
+    src.seed = h->seed;
+    src.st = st;
+    TRY_CUDA(launch_gram_f64(N, d, K, src, h->mu2_k64, h->num_sms, s));
+    TRY_CUDA(launch_select_decide_f64(st, h->mu2_k64, K, h->trace, s));
+    TRY_CUDA(launch_commit_f64(N, d, h->seed, st, h->phi64, h->phi32, s));
+  } else if (prec == TRSTMI_FP32) {
+    TRY_CUDA(launch_iter_begin(st, h->mu2_k32, sizeof(unsigned int) * K, nullptr, 0, nullptr,
+                               0, s));
+    GramSource src{};
+    src.perturb = true;
+    src.phi = h->phi32;
+    src.seed = h->seed;
+    src.st = st;
+    TRY_CUDA(launch_gram_f32(N, d, K, src, h->mu2_k32, nullptr, h->num_sms, s));
+    TRY_CUDA(launch_select_decide_f32(st, h->mu2_k32, K, h->trace, s));
+    TRY_CUDA(launch_commit_f32(N, d, h->seed, st, h->phi32, h->phi64, s));
+  } else {
+    const int k = h->opt.topk;
+    TRY_CUDA(launch_iter_begin(st, h->mu2_k32, sizeof(unsigned int) * K, h->mu2_top,
+                               sizeof(unsigned int) * k, h->cert32,
+                               2 * sizeof(unsigned int) + sizeof(unsigned long long), s));
+    TRY_CUDA(launch_screen_bf16(N, d, h->seed, h->phi32, K, 0u, 0u, 0.0, st, h->mu2_k32,
+                                &st->error, h->num_sms, s));
+    TRY_CUDA(launch_topk(st, h->mu2_k32, K, k, h->topk, s));
+    GramSource src{};
+    src.perturb = true;
+    src.phi = h->phi32;
+    src.seed = h->seed;
+    src.cand_list = h->topk;
+    src.st = st;
+    TRY_CUDA(launch_gram_f32(N, d, k, src, h->mu2_top, nullptr, h->num_sms, s));
+    TRY_CUDA(launch_materialize64(N, d, h->seed, st, h->topk, h->mu2_top, k, h->phi64,
+                                  h->cand64, h->cand32, s));
+    // cert32[0..1] and cert64 were zeroed by iter_begin (contiguous block)
+    int rc = enqueue_certify(h, h->cand64, h->cand32, h->cert64, &st->active, &st->npairs,
+                             &st->overflow, s);
+    if (rc) return rc;
+    TRY_CUDA(launch_decide_certified(st, h->cert64, h->trace, s));
+    TRY_CUDA(launch_commit_copy(N, d, st, h->cand64, h->cand32, h->phi64, h->phi32, s));
+  }
+  return TRSTMI_OK;
+}
+
+int get_graph(trstmi_instance* h, int iters, cudaGraphExec_t* out) {
+  auto it = h->graphs.find(iters);
+  if (it != h->graphs.end()) { *out = it->second; return TRSTMI_OK; }
+  cudaGraph_t g = nullptr;
+  TRY_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = TRSTMI_OK;
+  for (int i = 0; i < iters && rc == TRSTMI_OK; ++i) rc = enqueue_iteration(h, h->stream);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (rc != TRSTMI_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc != TRSTMI_OK ? rc : TRSTMI_ECUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return TRSTMI_ECUDA;
+  h->graphs[iters] = ex;
+  *out = ex;
+  return TRSTMI_OK;
+}
+
+int read_state(trstmi_instance* h, DevState* out) {
+  TRY_CUDA(cudaMemcpyAsync(out, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  TRY_CUDA(cudaStreamSynchronize(h->stream));
+  return TRSTMI_OK;
+}
+
+int device_error_status(const DevState& s) {
+  if (s.error & kErrTimeout) return TRSTMI_ETIMEOUT;
+  if (s.error & kErrZeroColumn) return TRSTMI_EINVAL;
+  return TRSTMI_OK;
+}
+
+int validate_options(int N, int d, const trstmi_options& o) {
+  if (N < 2 || d < 1 || d > kMaxD) return TRSTMI_EINVAL;
+  if ((long long)N * ((d + 1) / 2) >= (1ll << 32)) return TRSTMI_EINVAL;
+  if (o.K < 1 || o.trace_cap < 0) return TRSTMI_EINVAL;
+  if (o.precision < TRSTMI_FP64 || o.precision > TRSTMI_BF16_SCREEN) return TRSTMI_EINVAL;
+  if (o.precision == TRSTMI_BF16_SCREEN && (o.topk < 1 || o.topk > 64 || o.topk > o.K))
+    return TRSTMI_EINVAL;
+  if (!(o.delta0 > 0) || !(o.gamma_inc >= 1) || !(o.gamma_dec > 0 && o.gamma_dec <= 1))
+    return TRSTMI_EINVAL;
+  if (!(o.delta_min >= 0) || !(o.delta_max >= o.delta_min)) return TRSTMI_EINVAL;
+  if (o.precision == TRSTMI_BF16_SCREEN && !screen_supported(N, d)) return TRSTMI_EUNSUPPORTED;
+  return TRSTMI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void trstmi_default_options(trstmi_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->K = 256;
+  o->precision = TRSTMI_FP64;
+  o->topk = 8;
+  o->trace_cap = 4096;
+  o->delta0 = 0.1;
+  o->gamma_inc = 2.0;
+  o->gamma_dec = 0.25;
+  o->delta_min = 1e-9;
+  o->delta_max = 1.0;
+  o->target_mu = 0.0;
+  o->stream = nullptr;
+  o->device = 0;
+}
+
+const char* trstmi_strerror(int s) {
+  switch (s) {
+    case TRSTMI_OK: return "ok";
+    case TRSTMI_PENDING: return "pending";
+    case TRSTMI_EINVAL: return "invalid argument";
+    case TRSTMI_ENOMEM: return "out of device memory or over budget";
+    case TRSTMI_ECUDA: return "CUDA error or no CUDA device";
+    case TRSTMI_ETIMEOUT: return "device-side wait timed out";
+    case TRSTMI_ECANCELLED: return "cancelled";
+    case TRSTMI_EBUSY: return "queue full";
+    case TRSTMI_EUNSUPPORTED: return "shape/precision combination not supported";
+    case TRSTMI_ENOTFOUND: return "unknown ticket";
+    default: return "unknown status";
+  }
+}
+
+void trstmi_destroy(trstmi_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->opt.device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->block) cudaFree(h->block);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi_handle* out) {
+  if (!out) return TRSTMI_EINVAL;
+  *out = nullptr;
+  trstmi_options o;
+  if (opt) o = *opt; else trstmi_default_options(&o);
+  if (o.precision != TRSTMI_BF16_SCREEN) o.topk = std::max(1, std::min(o.topk, o.K));
+  int num_sms = 0;
+  int rc = ensure_device(o.device, &num_sms);
+  if (rc) return rc;
+  rc = validate_options(N, d, o);
+  if (rc) return rc;
+
+  trstmi_instance* h = new (std::nothrow) trstmi_instance();
+  if (!h) return TRSTMI_ENOMEM;
+  h->N = N; h->d = d; h->seed = seed; h->opt = o; h->num_sms = num_sms;
+  if (o.stream) {
+    h->stream = (cudaStream_t)o.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return TRSTMI_ECUDA;
+    }
+    h->own_stream = true;
+  }
+  // carve one allocation
+  const size_t nd = (size_t)N * d;
+  const int K = o.K, k = std::max(1, o.topk);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t at = off; off = align_up(off + bytes, 256); return at; };
+  const size_t o_st = take(sizeof(DevState));
+  const size_t o_phi64 = take(nd * sizeof(double2));
+  const size_t o_phi32 = take(nd * sizeof(float2));
+  const size_t o_c64 = take(nd * sizeof(double2));
+  const size_t o_c32 = take(nd * sizeof(float2));
+  const size_t o_s64 = take(nd * sizeof(double2));
+  const size_t o_k32 = take((size_t)K * sizeof(unsigned int));
+  const size_t o_k64 = take((size_t)K * sizeof(unsigned long long));
+  const size_t o_top = take((size_t)k * sizeof(unsigned int));
+  const size_t o_topk = take((size_t)k * sizeof(uint32_t));
+  // cert32[2] followed by cert64 in one 16-byte span (zeroed together)
+  const size_t o_cert = take(2 * sizeof(unsigned int) + sizeof(unsigned long long));
+  const size_t o_misc = take(2 * sizeof(uint32_t));
+  const size_t o_pairs = take((size_t)kPairCap * sizeof(uint2));
+  const size_t o_trace = take((size_t)std::max(o.trace_cap, 1) * sizeof(TraceRowDev));
+  h->block_bytes = off;
+  if (cudaMalloc(&h->block, off) != cudaSuccess) {
+    cudaGetLastError();
+    trstmi_destroy(h);
+    return TRSTMI_ENOMEM;
+  }
+  char* b = (char*)h->block;
+  h->st = (DevState*)(b + o_st);
+  h->phi64 = (double2*)(b + o_phi64);
+  h->phi32 = (float2*)(b + o_phi32);
+  h->cand64 = (double2*)(b + o_c64);
+  h->cand32 = (float2*)(b + o_c32);
+  h->scratch64 = (double2*)(b + o_s64);
+  h->mu2_k32 = (unsigned int*)(b + o_k32);
+  h->mu2_k64 = (unsigned long long*)(b + o_k64);
+  h->mu2_top = (unsigned int*)(b + o_top);
+  h->topk = (uint32_t*)(b + o_topk);
+  h->cert32 = (unsigned int*)(b + o_cert);
+  h->cert64 = (unsigned long long*)(b + o_cert + 2 * sizeof(unsigned int));
+  h->misc = (uint32_t*)(b + o_misc);
+  h->pairs = (uint2*)(b + o_pairs);
+  h->trace = (TraceRowDev*)(b + o_trace);
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    trstmi_destroy(h);
+    return TRSTMI_ECUDA;
+  }
+  DevState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.delta = o.delta0;
+  s0.delta_used = o.delta0;
+  s0.target2 = o.target_mu > 0 ? o.target_mu * o.target_mu : -1.0;
+  s0.gamma_inc = o.gamma_inc;
+  s0.gamma_dec = o.gamma_dec;
+  s0.delta_min = o.delta_min;
+  s0.delta_max = o.delta_max;
+  s0.trace_cap = (uint32_t)o.trace_cap;
+  cudaStream_t s = h->stream;
+  if (cudaMemsetAsync(h->block, 0, off, s) != cudaSuccess ||
+      cudaMemcpyAsync(h->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      launch_init_frame(N, d, seed, h->phi64, h->phi32, h->st, s) != cudaSuccess) {
+    trstmi_destroy(h);
+    return TRSTMI_ECUDA;
+  }
+  rc = enqueue_rescore_current(h);
+  DevState chk;
+  if (!rc) rc = read_state(h, &chk);
+  if (!rc) rc = device_error_status(chk);
+  if (rc) { trstmi_destroy(h); return rc; }
+  *out = h;
+  return TRSTMI_OK;
+}
+
+int trstmi_step(trstmi_handle h, int iters, trstmi_step_info* info) {
+  if (!h || iters < 0) return TRSTMI_EINVAL;
+  TRY_CUDA(cudaSetDevice(h->opt.device));
+  DevState before;
+  int rc = read_state(h, &before);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  TRY_CUDA(cudaEventRecord(h->ev0, s));
+  k_set_stop<<<1, 1, 0, s>>>(h->st, (uint32_t)iters);
+  TRY_CUDA(cudaGetLastError());
+  const int full = iters / kGraphChunk, rem = iters % kGraphChunk;
+  if (full > 0) {
+    cudaGraphExec_t g;
+    rc = get_graph(h, kGraphChunk, &g);
+    if (rc) return rc;
+    for (int r = 0; r < full; ++r) TRY_CUDA(cudaGraphLaunch(g, s));
+  }
+  if (rem > 0) {
+    cudaGraphExec_t g;
+    rc = get_graph(h, rem, &g);
+    if (rc) return rc;
+    TRY_CUDA(cudaGraphLaunch(g, s));
+  }
+  TRY_CUDA(cudaEventRecord(h->ev1, s));
+  DevState after;
+  rc = read_state(h, &after);
+  if (rc) return rc;
+  if (info) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    info->iters_done = (int32_t)(after.t - before.t);
+    info->accepts = (int32_t)(after.accepts - before.accepts);
+    info->mu = std::sqrt(after.mu2_cur);
+    info->delta = after.delta;
+    info->pairs_scored = (uint64_t)info->iters_done * (uint64_t)h->opt.K *
+                         ((uint64_t)h->N * (uint64_t)(h->N - 1) / 2);
+    info->elapsed_ns = (uint64_t)((double)ms * 1e6);
+    info->done = (int32_t)after.done;
+    info->reserved = 0;
+  }
+  return device_error_status(after);
+}
+
+int trstmi_coherence(trstmi_handle h, double* mu, double* welch) {
+  if (!h || !mu) return TRSTMI_EINVAL;
+  TRY_CUDA(cudaSetDevice(h->opt.device));
+  cudaStream_t s = h->stream;
+  TRY_CUDA(cudaMemsetAsync(h->cert32, 0, 2 * sizeof(unsigned int) + sizeof(unsigned long long), s));
+  TRY_CUDA(cudaMemsetAsync(h->misc, 0, 2 * sizeof(uint32_t), s));
+  TRY_CUDA(launch_normalize64(h->N, h->d, h->phi64, h->scratch64, h->cand32, nullptr, s));
+  int rc = enqueue_certify(h, h->scratch64, h->cand32, h->cert64, nullptr, h->misc, h->misc + 1, s);
+  if (rc) return rc;
+  unsigned long long bits = 0;
+  TRY_CUDA(cudaMemcpyAsync(&bits, h->cert64, sizeof(bits), cudaMemcpyDeviceToHost, s));
+  TRY_CUDA(cudaStreamSynchronize(s));
+  double m2;
+  std::memcpy(&m2, &bits, sizeof(m2));
+  *mu = std::sqrt(m2);
+  if (welch) *welch = welch_of(h->N, h->d);
+  return TRSTMI_OK;
+}
+
+int trstmi_get_phi(trstmi_handle h, double* out) {
+  if (!h || !out) return TRSTMI_EINVAL;
+  TRY_CUDA(cudaSetDevice(h->opt.device));
+  TRY_CUDA(cudaMemcpyAsync(out, h->phi64, (size_t)h->N * h->d * sizeof(double2),
+                           cudaMemcpyDeviceToHost, h->stream));
+  TRY_CUDA(cudaStreamSynchronize(h->stream));
+  return TRSTMI_OK;
+}
+
+int trstmi_set_phi(trstmi_handle h, const double* in) {
+  if (!h || !in) return TRSTMI_EINVAL;
+  TRY_CUDA(cudaSetDevice(h->opt.device));
+  cudaStream_t s = h->stream;
+  const size_t bytes = (size_t)h->N * h->d * sizeof(double2);
+  // reject zero columns on the host before touching the device state
+  for (int j = 0; j < h->N; ++j) {
+    double acc = 0.0;
+    for (int i = 0; i < 2 * h->d; ++i) acc += in[(size_t)j * 2 * h->d + i] * in[(size_t)j * 2 * h->d + i];
+    if (!(acc > 0.0) || !std::isfinite(acc)) return TRSTMI_EINVAL;
+  }
+  TRY_CUDA(cudaMemcpyAsync(h->scratch64, in, bytes, cudaMemcpyHostToDevice, s));
+  TRY_CUDA(launch_normalize64(h->N, h->d, h->scratch64, h->phi64, h->phi32, h->st, s));
+  int rc = enqueue_rescore_current(h);
+  if (rc) return rc;
+  DevState chk;
+  rc = read_state(h, &chk);
+  if (rc) return rc;
+  return device_error_status(chk);
+}
+
+namespace {
+struct BlobHeader {
+  uint32_t magic, version;
+  int32_t N, d;
+  uint64_t seed;
+  int32_t precision, K, topk, pad;
+  DevState st;
+};
+}  // namespace
+
+int trstmi_get_state(trstmi_handle h, void* blob, size_t* size) {
+  if (!h || !size) return TRSTMI_EINVAL;
+  const size_t nd = (size_t)h->N * h->d;
+  const size_t need = sizeof(BlobHeader) + nd * sizeof(double2) + nd * sizeof(float2);
+  if (!blob) { *size = need; return TRSTMI_OK; }
+  if (*size < need) { *size = need; return TRSTMI_EINVAL; }
+  TRY_CUDA(cudaSetDevice(h->opt.device));
+  BlobHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  hd.magic = kBlobMagic; hd.version = kBlobVersion; hd.N = h->N; hd.d = h->d; hd.seed = h->seed;
+  hd.precision = h->opt.precision; hd.K = h->opt.K; hd.topk = h->opt.topk;
+  char* p = (char*)blob;
+  TRY_CUDA(cudaMemcpyAsync(&hd.st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  TRY_CUDA(cudaMemcpyAsync(p + sizeof(BlobHeader), h->phi64, nd * sizeof(double2),
+                           cudaMemcpyDeviceToHost, h->stream));
+  TRY_CUDA(cudaMemcpyAsync(p + sizeof(BlobHeader) + nd * sizeof(double2), h->phi32,
+                           nd * sizeof(float2), cudaMemcpyDeviceToHost, h->stream));
+  TRY_CUDA(cudaStreamSynchronize(h->stream));
+  std::memcpy(p, &hd, sizeof(hd));
+  *size = need;
+  return TRSTMI_OK;
+}
+
+int trstmi_set_state(trstmi_handle h, const void* blob, size_t size) {
+  if (!h || !blob || size < sizeof(BlobHeader)) return TRSTMI_EINVAL;
+  BlobHeader hd;
+  std::memcpy(&hd, blob, sizeof(hd));
+  const size_t nd = (size_t)h->N * h->d;
+  if (hd.magic != kBlobMagic || hd.version != kBlobVersion || hd.N != h->N || hd.d != h->d ||
+      hd.seed != h->seed || hd.precision != h->opt.precision || hd.K != h->opt.K ||
+      size < sizeof(BlobHeader) + nd * (sizeof(double2) + sizeof(float2)))
+    return TRSTMI_EINVAL;
+  TRY_CUDA(cudaSetDevice(h->opt.device));
+  DevState st = hd.st;
+  st.trace_cap = (uint32_t)h->opt.trace_cap;
+  const char* p = (const char*)blob;
+  TRY_CUDA(cudaMemcpyAsync(h->st, &st, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+  TRY_CUDA(cudaMemcpyAsync(h->phi64, p + sizeof(BlobHeader), nd * sizeof(double2),
+                           cudaMemcpyHostToDevice, h->stream));
+  TRY_CUDA(cudaMemcpyAsync(h->phi32, p + sizeof(BlobHeader) + nd * sizeof(double2),
+                           nd * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
+  TRY_CUDA(cudaStreamSynchronize(h->stream));
+  return TRSTMI_OK;
+}
+
+int trstmi_get_trace(trstmi_handle h, trstmi_trace_row* rows, int n, int* n_out) {
+  if (!h || n < 0 || !n_out || (n > 0 && !rows)) return TRSTMI_EINVAL;
+  static_assert(sizeof(trstmi_trace_row) == sizeof(TraceRowDev), "trace row layout");
+  DevState s;
+  int rc = read_state(h, &s);
+  if (rc) return rc;
+  const uint32_t cap = s.trace_cap;
+  const uint32_t avail = std::min<uint32_t>(cap, s.t);
+  const uint32_t cnt = std::min<uint32_t>(avail, (uint32_t)n);
+  std::vector<TraceRowDev> all(cap ? cap : 1);
+  if (cap) {
+    TRY_CUDA(cudaMemcpyAsync(all.data(), h->trace, cap * sizeof(TraceRowDev),
+                             cudaMemcpyDeviceToHost, h->stream));
+    TRY_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  for (uint32_t q = 0; q < cnt; ++q) {
+    const uint32_t t = s.t - cnt + 1 + q;  // 1-based iteration
+    std::memcpy(&rows[q], &all[(t - 1) % cap], sizeof(TraceRowDev));
+  }
+  *n_out = (int)cnt;
+  return TRSTMI_OK;
+}
+
+int trstmi_score(trstmi_handle h, uint32_t t, uint32_t c0, int count, double delta,
+                 int precision, double* mu2) {
+  if (!h || count < 0 || (count > 0 && !mu2) || t < 1 || !(delta >= 0)) return TRSTMI_EINVAL;
+  if (count == 0) return TRSTMI_OK;
+  TRY_CUDA(cudaSetDevice(h->opt.device));
+  cudaStream_t s = h->stream;
+  void* tmp = nullptr;
+  const size_t bytes = (size_t)count * sizeof(unsigned long long);
+  TRY_CUDA(cudaMalloc(&tmp, bytes));
+  int rc = TRSTMI_OK;
+  std::vector<double> outv(count);
+  do {
+    if (cudaMemsetAsync(tmp, 0, bytes, s) != cudaSuccess) { rc = TRSTMI_ECUDA; break; }
+    GramSource src{};
+    src.perturb = true;
+    src.seed = h->seed;
+    src.c0 = c0;
+    src.t = t;
+    src.delta = delta;
+    if (precision == TRSTMI_FP64) {
+      src.phi = h->phi64;
+      if (launch_gram_f64(h->N, h->d, count, src, (unsigned long long*)tmp, h->num_sms, s)) {
+        rc = TRSTMI_ECUDA; break;
+      }
+      std::vector<unsigned long long> b(count);
+      if (cudaMemcpyAsync(b.data(), tmp, bytes, cudaMemcpyDeviceToHost, s) ||
+          cudaStreamSynchronize(s)) { rc = TRSTMI_ECUDA; break; }
+      for (int q = 0; q < count; ++q) std::memcpy(&outv[q], &b[q], sizeof(double));
+    } else if (precision == TRSTMI_FP32 || precision == TRSTMI_BF16_SCREEN) {
+      cudaError_t e;
+      if (precision == TRSTMI_FP32) {
+        src.phi = h->phi32;
+        e = launch_gram_f32(h->N, h->d, count, src, (unsigned int*)tmp, nullptr, h->num_sms, s);
+      } else {
+        if (!screen_supported(h->N, h->d)) { rc = TRSTMI_EUNSUPPORTED; break; }
+        e = launch_screen_bf16(h->N, h->d, h->seed, h->phi32, count, c0, t, delta, nullptr,
+                               (unsigned int*)tmp, &h->misc[1], h->num_sms, s);
+      }
+      if (e != cudaSuccess) { rc = TRSTMI_ECUDA; break; }
+      std::vector<unsigned int> b(count);
+      if (cudaMemcpyAsync(b.data(), tmp, (size_t)count * sizeof(unsigned int),
+                          cudaMemcpyDeviceToHost, s) ||
+          cudaStreamSynchronize(s)) { rc = TRSTMI_ECUDA; break; }
+      for (int q = 0; q < count; ++q) {
+        float f;
+        std::memcpy(&f, &b[q], sizeof(float));
+        outv[q] = (double)f;
+      }
+    } else {
+      rc = TRSTMI_EINVAL;
+    }
+  } while (0);
+  cudaFree(tmp);
+  if (rc == TRSTMI_OK) std::memcpy(mu2, outv.data(), sizeof(double) * count);
+  return rc;
+}
+
+int trstmi_candidate(trstmi_handle h, uint32_t t, uint32_t c, double delta, int precision,
+                     double* out) {
+  if (!h || !out || t < 1 || !(delta >= 0)) return TRSTMI_EINVAL;
+  if (precision != TRSTMI_FP64 && precision != TRSTMI_FP32) return TRSTMI_EINVAL;
+  TRY_CUDA(cudaSetDevice(h->opt.device));
+  cudaStream_t s = h->stream;
+  TRY_CUDA(launch_gen_candidate(h->N, h->d, h->seed, t, c, delta, precision == TRSTMI_FP64,
+                                h->phi64, h->phi32, h->scratch64, s));
+  TRY_CUDA(cudaMemcpyAsync(out, h->scratch64, (size_t)h->N * h->d * sizeof(double2),
+                           cudaMemcpyDeviceToHost, s));
+  TRY_CUDA(cudaStreamSynchronize(s));
+  return TRSTMI_OK;
+}
+
+int trstmi_mu2_frame(int N, int d, const double* phi, int precision, double* mu2) {
+  if (N < 1 || d < 1 || d > kMaxD || !phi || !mu2) return TRSTMI_EINVAL;
+  if (precision != TRSTMI_FP64 && precision != TRSTMI_FP32) return TRSTMI_EINVAL;
+  int num_sms = 0;
+  int rc = ensure_device(0, &num_sms);
+  if (rc) return rc;
+  const size_t nd = (size_t)N * d;
+  void* buf = nullptr;
+  const size_t bytes = nd * sizeof(double2) + 256;
+  TRY_CUDA(cudaMalloc(&buf, bytes));
+  std::vector<float> f32;
+  do {
+    GramSource src{};
+    src.perturb = false;
+    src.phi = (char*)buf + 256;
+    if (cudaMemset(buf, 0, 256) != cudaSuccess) { rc = TRSTMI_ECUDA; break; }
+    if (precision == TRSTMI_FP64) {
+      if (cudaMemcpy((char*)buf + 256, phi, nd * sizeof(double2), cudaMemcpyHostToDevice) ||
+          launch_gram_f64(N, d, 1, src, (unsigned long long*)buf, num_sms, 0)) {
+        rc = TRSTMI_ECUDA; break;
+      }
+      unsigned long long b = 0;
+      if (cudaMemcpy(&b, buf, sizeof(b), cudaMemcpyDeviceToHost)) { rc = TRSTMI_ECUDA; break; }
+      std::memcpy(mu2, &b, sizeof(double));
+    } else {
+      f32.resize(2 * nd);
+      for (size_t e = 0; e < 2 * nd; ++e) f32[e] = (float)phi[e];
+      if (cudaMemcpy((char*)buf + 256, f32.data(), nd * sizeof(float2), cudaMemcpyHostToDevice) ||
+          launch_gram_f32(N, d, 1, src, (unsigned int*)buf, nullptr, num_sms, 0)) {
+        rc = TRSTMI_ECUDA; break;
+      }
+      unsigned int b = 0;
+      if (cudaMemcpy(&b, buf, sizeof(b), cudaMemcpyDeviceToHost)) { rc = TRSTMI_ECUDA; break; }
+      float f;
+      std::memcpy(&f, &b, sizeof(f));
+      *mu2 = (double)f;
+    }
+  } while (0);
+  cudaFree(buf);
+  return rc;
+}
+
+int trstmi_profile_score(trstmi_handle h, int precision, int launches, double delta,
+                         size_t flush_bytes, double* avg_ms) {
+  if (!h || launches < 1 || !avg_ms || !(delta >= 0)) return TRSTMI_EINVAL;
+  if (precision < TRSTMI_FP64 || precision > TRSTMI_BF16_SCREEN) return TRSTMI_EINVAL;
+  if (precision == TRSTMI_BF16_SCREEN && !screen_supported(h->N, h->d)) return TRSTMI_EUNSUPPORTED;
+  TRY_CUDA(cudaSetDevice(h->opt.device));
+  cudaStream_t s = h->stream;
+  const int K = h->opt.K;
+  void* flush = nullptr;
+  if (flush_bytes) TRY_CUDA(cudaMalloc(&flush, flush_bytes));
+  std::vector<cudaEvent_t> ev(2 * launches, nullptr);
+  int rc = TRSTMI_OK;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) rc = TRSTMI_ECUDA;
+  for (int l = 0; l < launches && rc == TRSTMI_OK; ++l) {
+    if (flush && cudaMemsetAsync(flush, l & 0xff, flush_bytes, s) != cudaSuccess) { rc = TRSTMI_ECUDA; break; }
+    if (cudaMemsetAsync(h->mu2_k64, 0, (size_t)K * sizeof(unsigned long long), s) ||
+        cudaMemsetAsync(h->mu2_k32, 0, (size_t)K * sizeof(unsigned int), s)) { rc = TRSTMI_ECUDA; break; }
+    GramSource src{};
+    src.perturb = true;
+    src.seed = h->seed;
+    src.t = (uint32_t)(l + 1);
+    src.delta = delta;
+    cudaEventRecord(ev[2 * l], s);
+    cudaError_t e;
+    if (precision == TRSTMI_FP64) {
+      src.phi = h->phi64;
+      e = launch_gram_f64(h->N, h->d, K, src, h->mu2_k64, h->num_sms, s);
+    } else if (precision == TRSTMI_FP32) {
+      src.phi = h->phi32;
+      e = launch_gram_f32(h->N, h->d, K, src, h->mu2_k32, nullptr, h->num_sms, s);
+    } else {
+      e = launch_screen_bf16(h->N, h->d, h->seed, h->phi32, K, 0u, (uint32_t)(l + 1), delta,
+                             nullptr, h->mu2_k32, &h->misc[1], h->num_sms, s);
+    }
+    cudaEventRecord(ev[2 * l + 1], s);
+    if (e != cudaSuccess) rc = TRSTMI_ECUDA;
+  }
+  if (rc == TRSTMI_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = TRSTMI_ECUDA;
+  double total = 0.0;
+  if (rc == TRSTMI_OK) {
+    for (int l = 0; l < launches; ++l) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[2 * l], ev[2 * l + 1]) != cudaSuccess) rc = TRSTMI_ECUDA;
+      total += ms;
+    }
+  }
+  for (auto& e : ev) if (e) cudaEventDestroy(e);
+  if (flush) cudaFree(flush);
+  if (rc == TRSTMI_OK) *avg_ms = total / launches;
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Counter-based Gaussian draws for the candidate perturbation (device side).
+//
+// Philox4x32-10 is implemented here from its published definition (Salmon,
+// Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11):
+// ten rounds of two 32x32->64 multiplies with Weyl-sequence key bumps.
+//
+// Counter layout of this library (TRSTMI candidate step, the Monte-Carlo
+// sampling of arXiv 2207.06374, Sec. "Optimization procedure"):
+//   key = (seed lo32, seed hi32)
+//   ctr = (e, c, t, tag),  e = j*ceil(d/2) + i/2  (entries i, i+1 of column j)
+//   tag 0 = perturbation of iteration t, candidate c; tag 1 = initial frame.
+// Each call yields u0..u3; U = (u + 1/2) 2^-32; entry i even uses (u0,u1),
+// i odd (u2,u3); Z = sqrt(-ln Ua) * exp(2 pi i Ub) is complex normal CN(0,1)
+// (the Box-Muller pair divided by sqrt 2).
+#pragma once
+#include <cstdint>
+
+namespace trstmi {
+
+struct PhiloxOut { uint32_t x[4]; };
+
+__device__ __forceinline__ PhiloxOut philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                   uint32_t c3, uint32_t k0, uint32_t k1) {
+  constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+  constexpr uint32_t kBumpA = 0x9E3779B9u, kBumpB = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hiA = __umulhi(kMulA, c0), loA = kMulA * c0;
+    const uint32_t hiB = __umulhi(kMulB, c2), loB = kMulB * c2;
+    const uint32_t n0 = hiB ^ c1 ^ k0;
+    const uint32_t n2 = hiA ^ c3 ^ k1;
+    c0 = n0; c1 = loB; c2 = n2; c3 = loA;
+    k0 += kBumpA; k1 += kBumpB;
+  }
+  PhiloxOut o;
+  o.x[0] = c0; o.x[1] = c1; o.x[2] = c2; o.x[3] = c3;
+  return o;
+}
+
+// --- uniform -> complex normal, three precisions -------------------------
+
+// Double precision: U = (u + 0.5) * 2^-32 is exact in binary64.
+__device__ __forceinline__ void cn_from_u32_f64(uint32_t ua, uint32_t ub, double& re, double& im) {
+  const double Ua = __dmul_rn(__dadd_rn((double)ua, 0.5), 0x1.0p-32);
+  const double Ub = __dmul_rn(__dadd_rn((double)ub, 0.5), 0x1.0p-32);
+  const double r = sqrt(-log(Ua));
+  double s, c;
+  sincospi(__dmul_rn(2.0, Ub), &s, &c);
+  re = __dmul_rn(r, c);
+  im = __dmul_rn(r, s);
+}
+
+// Single precision with the accurate library functions (plain FP32 path and
+// the FP32 re-score of the screen survivors).
+__device__ __forceinline__ void cn_from_u32_f32(uint32_t ua, uint32_t ub, float& re, float& im) {
+  const float Ua = __fmaf_rn(__uint2float_rn(ua), 0x1.0p-32f, 0x1.0p-33f);
+  const float Ub = __fmaf_rn(__uint2float_rn(ub), 0x1.0p-32f, 0x1.0p-33f);
+  const float r = sqrtf(-logf(Ua));
+  float s, c;
+  sincospif(__fmul_rn(2.0f, Ub), &s, &c);
+  re = __fmul_rn(r, c);
+  im = __fmul_rn(r, s);
+}
+
+// Single precision with the hardware approximations; used only by the
+// reduced-precision (bf16) screen, whose own rounding (2^-9) dominates.
+// The angle is shifted into [-pi, pi) where the approximate sine/cosine are
+// accurate: cos(2 pi U) = -cos(2 pi U - pi), likewise for the sine.
+__device__ __forceinline__ void cn_from_u32_fast(uint32_t ua, uint32_t ub, float& re, float& im) {
+  const float Ua = __fmaf_rn(__uint2float_rn(ua), 0x1.0p-32f, 0x1.0p-33f);
+  const float Ub = __uint2float_rn(ub) * 0x1.0p-32f;
+  // -ln U = -log2(U) * ln 2
+  const float r = __fsqrt_rn(fmaxf(__log2f(Ua) * -0.69314718055994531f, 0.0f));
+  const float th = __fmaf_rn(Ub, 6.28318530717958648f, -3.14159265358979324f);
+  float s, c;
+  __sincosf(th, &s, &c);
+  re = -r * c;
+  im = -r * s;
+}
+
+__device__ __forceinline__ uint32_t seed_lo(uint64_t s) { return (uint32_t)(s & 0xffffffffull); }
+__device__ __forceinline__ uint32_t seed_hi(uint64_t s) { return (uint32_t)(s >> 32); }
+
+}  // namespace trstmi

@@ -1,0 +1,648 @@
+// SIMT kernels of the TRSTMI search: candidate generation, the tiled
+// upper-triangle Gram with a fused |G|^2 / max epilogue (binary32 and
+// binary64), and the per-iteration select / accept / commit kernels.
+//
+// Method (arXiv 2207.06374): coherence mu(Phi) = max_{j != k} |<phi_j, phi_k>|
+// (Sec. "Introduction"); only the upper triangle j < k is formed (Sec.
+// "Optimization procedure"); columns are renormalised after every
+// perturbation so the search is unconstrained (Remark on normalisation).
+#include <algorithm>
+
+#include "kernels.h"
+#include "philox.cuh"
+
+namespace trstmi {
+
+// ----------------------------------------------------- rounding helpers
+// Generation uses explicitly rounded operations so that the same candidate
+// is bit-identical wherever it is regenerated (scoring, commit, copies).
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
+
+template <typename T> __device__ __forceinline__ void cn_draw(uint32_t ua, uint32_t ub, T& re, T& im);
+template <> __device__ __forceinline__ void cn_draw<float>(uint32_t ua, uint32_t ub, float& re, float& im) {
+  cn_from_u32_f32(ua, ub, re, im);
+}
+template <> __device__ __forceinline__ void cn_draw<double>(uint32_t ua, uint32_t ub, double& re, double& im) {
+  cn_from_u32_f64(ua, ub, re, im);
+}
+
+// Column j of normalise(Phi + delta * Z_{t,c}) (tag 0), or of the initial
+// draw normalise(Z_init) (tag 1, phi == nullptr), written to
+// out_re[i*stride], out_im[i*stride].  Returns false for a zero column.
+// Entry i of phi is read before out[i] is written and never again, so the
+// output may alias the input column (in-place commit).
+template <typename T>
+__device__ bool gen_column(const typename Cplx<T>::type* phi, int d, int j,
+                           uint64_t seed, uint32_t c, uint32_t t, uint32_t tag, T delta,
+                           T* out_re, T* out_im, int stride) {
+  const uint32_t k0 = seed_lo(seed), k1 = seed_hi(seed);
+  const int P = (d + 1) >> 1;
+  const typename Cplx<T>::type* col = phi ? phi + (size_t)j * d : nullptr;
+  T s = T(0);
+  for (int p = 0; p < P; ++p) {
+    const PhiloxOut u = philox4x32_10((uint32_t)j * (uint32_t)P + (uint32_t)p, c, t, tag, k0, k1);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * p + h;
+      if (i < d) {
+        T zr, zi;
+        cn_draw<T>(u.x[2 * h], u.x[2 * h + 1], zr, zi);
+        T xr = zr, xi = zi;
+        if (col) {
+          const auto v = col[i];
+          xr = add_rn(v.x, mul_rn(delta, zr));
+          xi = add_rn(v.y, mul_rn(delta, zi));
+        }
+        out_re[i * stride] = xr;
+        out_im[i * stride] = xi;
+        s = add_rn(s, add_rn(mul_rn(xr, xr), mul_rn(xi, xi)));
+      }
+    }
+  }
+  if (!(s > T(0))) {
+    for (int i = 0; i < d; ++i) { out_re[i * stride] = T(0); out_im[i * stride] = T(0); }
+    return false;
+  }
+  const T nrm = sqrt_rn(s);
+  for (int i = 0; i < d; ++i) {
+    out_re[i * stride] = div_rn(out_re[i * stride], nrm);
+    out_im[i * stride] = div_rn(out_im[i * stride], nrm);
+  }
+  return true;
+}
+
+// Column j of a stored frame, optionally renormalised.
+template <typename T>
+__device__ bool load_column(const typename Cplx<T>::type* __restrict__ frame, int d, int j,
+                            bool normalize, T* out_re, T* out_im, int stride) {
+  const typename Cplx<T>::type* col = frame + (size_t)j * d;
+  T s = T(0);
+  for (int i = 0; i < d; ++i) {
+    const auto v = col[i];
+    out_re[i * stride] = v.x;
+    out_im[i * stride] = v.y;
+    s = add_rn(s, add_rn(mul_rn(v.x, v.x), mul_rn(v.y, v.y)));
+  }
+  if (!normalize) return true;
+  if (!(s > T(0))) return false;
+  const T nrm = sqrt_rn(s);
+  for (int i = 0; i < d; ++i) {
+    out_re[i * stride] = div_rn(out_re[i * stride], nrm);
+    out_im[i * stride] = div_rn(out_im[i * stride], nrm);
+  }
+  return true;
+}
+
+// Upper-triangle tile tau (column-major over tiles with I <= J) -> (I, J).
+__device__ __forceinline__ void tile_coords(int tau, int& I, int& J) {
+  int j = (int)((sqrtf(8.0f * (float)tau + 1.0f) - 1.0f) * 0.5f);
+  while ((j + 1) * (j + 2) / 2 <= tau) ++j;
+  while (j * (j + 1) / 2 > tau) --j;
+  J = j;
+  I = tau - j * (j + 1) / 2;
+}
+
+template <typename T> struct GramArgs {
+  int N, d, nb, ntiles, nslots;
+  GramSource src;
+  typename Mu2Bits<T>::type* out;
+  PairFilter filter;
+  bool has_filter;
+};
+
+template <typename T> __device__ __forceinline__ T block_max(T v, T* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;  // valid in thread 0
+}
+
+// One CTA (256 threads, 16 x 16) per work item (slot, tile I <= J) of width
+// BT = 16 R columns.  Column blocks I and J are generated (or loaded) into
+// shared memory as [i][column] planes of real and imaginary parts; each
+// thread accumulates an R x R micro-tile of
+//   Re G_jk = sum_i a_ij a_ik + b_ij b_ik,  Im G_jk = sum_i a_ij b_ik - b_ij a_ik
+// and the CTA reduces max |G_jk|^2 over j < k < N.
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_gram_tile(const GramArgs<T> a) {
+  constexpr int BT = 16 * R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T red[8];
+  __shared__ int zero_col;
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int d = a.d, N = a.N;
+  T* sIre = sm;
+  T* sIim = sm + (size_t)d * BT;
+  T* sJre = sm + (size_t)2 * d * BT;
+  T* sJim = sm + (size_t)3 * d * BT;
+
+  const GramSource& src = a.src;
+  if (src.gate && *src.gate == 0u) return;
+  uint32_t t = src.t;
+  T delta = (T)src.delta;
+  if (src.st) {
+    if (!src.st->active) return;
+    t = src.st->t + 1u;
+    delta = (T)src.st->delta_used;
+  }
+  T thr = T(-1);
+  if (a.has_filter) {
+    const float ref = sqrtf(__uint_as_float(*a.filter.mu2_ref));
+    const float lo = fmaxf(ref - a.filter.margin, 0.0f);
+    thr = (T)(lo * lo);
+  }
+  using C = typename Cplx<T>::type;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const long long nitems = (long long)a.nslots * a.ntiles;
+  for (long long w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int slot = (int)(w / a.ntiles);
+    const int tau = (int)(w - (long long)slot * a.ntiles);
+    int I, J;
+    tile_coords(tau, I, J);
+    const bool diag = (I == J);
+    if (threadIdx.x == 0) zero_col = 0;
+    __syncthreads();
+    const int ncols = diag ? BT : 2 * BT;
+    for (int q = threadIdx.x; q < ncols; q += blockDim.x) {
+      const int blk = q / BT, loc = q - blk * BT;
+      const int gj = (blk == 0 ? I : J) * BT + loc;
+      T* ore = (blk == 0 ? sIre : sJre) + loc;
+      T* oim = (blk == 0 ? sIim : sJim) + loc;
+      bool ok = true;
+      if (gj < N) {
+        if (src.perturb) {
+          const uint32_t c = src.cand_list ? src.cand_list[slot] : src.c0 + (uint32_t)slot;
+          ok = gen_column<T>(reinterpret_cast<const C*>(src.phi), d, gj, src.seed, c, t, 0u,
+                             delta, ore, oim, BT);
+        } else {
+          const C* frame = reinterpret_cast<const C*>(src.phi) + (size_t)slot * d * N;
+          ok = load_column<T>(frame, d, gj, src.normalize, ore, oim, BT);
+        }
+      } else {
+        for (int i = 0; i < d; ++i) { ore[i * BT] = T(0); oim[i * BT] = T(0); }
+      }
+      if (!ok) zero_col = 1;
+    }
+    __syncthreads();
+    if (zero_col && src.st && threadIdx.x == 0)
+      atomicOr(&const_cast<DevState*>(src.st)->error, (uint32_t)kErrZeroColumn);
+    const T* bRe = diag ? sIre : sJre;
+    const T* bIm = diag ? sIim : sJim;
+    T accR[R][R], accI[R][R];
+#pragma unroll
+    for (int x = 0; x < R; ++x)
+#pragma unroll
+      for (int y = 0; y < R; ++y) { accR[x][y] = T(0); accI[x][y] = T(0); }
+#pragma unroll 2
+    for (int i = 0; i < d; ++i) {
+      T ar[R], ai[R], br[R], bi[R];
+#pragma unroll
+      for (int x = 0; x < R; ++x) {
+        ar[x] = sIre[i * BT + ty + 16 * x];
+        ai[x] = sIim[i * BT + ty + 16 * x];
+        br[x] = bRe[i * BT + tx + 16 * x];
+        bi[x] = bIm[i * BT + tx + 16 * x];
+      }
+#pragma unroll
+      for (int x = 0; x < R; ++x)
+#pragma unroll
+        for (int y = 0; y < R; ++y) {
+          accR[x][y] = fma(ar[x], br[y], fma(ai[x], bi[y], accR[x][y]));
+          accI[x][y] = fma(ar[x], bi[y], fma(-ai[x], br[y], accI[x][y]));
+        }
+    }
+    T m = T(0);
+#pragma unroll
+    for (int x = 0; x < R; ++x)
+#pragma unroll
+      for (int y = 0; y < R; ++y) {
+        const int gj = I * BT + ty + 16 * x, gk = J * BT + tx + 16 * y;
+        const T v = accR[x][y] * accR[x][y] + accI[x][y] * accI[x][y];
+        if (gj < gk && gk < N) {
+          m = fmax(m, v);
+          if (a.has_filter && v >= thr) {
+            const uint32_t idx = atomicAdd(a.filter.npairs, 1u);
+            if (idx < a.filter.cap) a.filter.pairs[idx] = make_uint2((unsigned)gj, (unsigned)gk);
+            else atomicExch(a.filter.overflow, 1u);
+          }
+        }
+      }
+    m = block_max<T>(m, red);
+    if (threadIdx.x == 0) atomic_max_nonneg(a.out + slot, m);
+    __syncthreads();
+  }
+}
+
+template <typename T> static size_t gram_smem(int d, int R) {
+  return (size_t)4 * d * 16 * R * sizeof(T);
+}
+
+template <typename T> static int pick_R(int N, int d) {
+  int R = 4;
+  while (R > 1 && 16 * R >= 2 * N) R >>= 1;          // do not pad tiny N
+  while (R > 1 && gram_smem<T>(d, R) > 200 * 1024) R >>= 1;
+  return R;
+}
+
+template <typename T>
+static cudaError_t launch_gram(int N, int d, int nslots, const GramSource& src,
+                               typename Mu2Bits<T>::type* out, const PairFilter* filter,
+                               int num_sms, cudaStream_t s) {
+  if (N < 1 || d < 1 || d > kMaxD || nslots < 0) return cudaErrorInvalidValue;
+  if (nslots == 0) return cudaSuccess;
+  const int R = pick_R<T>(N, d);
+  const int BT = 16 * R;
+  GramArgs<T> a;
+  a.N = N; a.d = d; a.nb = (N + BT - 1) / BT; a.ntiles = a.nb * (a.nb + 1) / 2;
+  a.nslots = nslots; a.src = src; a.out = out;
+  a.has_filter = filter != nullptr;
+  if (filter) a.filter = *filter; else a.filter = PairFilter{};
+  const size_t smem = gram_smem<T>(d, R);
+  const long long items = (long long)nslots * a.ntiles;
+  const int per_sm = smem <= 100 * 1024 ? 2 : 1;
+  const int grid = (int)std::min<long long>(items, (long long)num_sms * per_sm * 4);
+  switch (R) {
+    case 4: k_gram_tile<T, 4><<<grid, 256, smem, s>>>(a); break;
+    case 2: k_gram_tile<T, 2><<<grid, 256, smem, s>>>(a); break;
+    default: k_gram_tile<T, 1><<<grid, 256, smem, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_f32(int N, int d, int nslots, const GramSource& src, unsigned int* out,
+                            const PairFilter* filter, int num_sms, cudaStream_t s) {
+  return launch_gram<float>(N, d, nslots, src, out, filter, num_sms, s);
+}
+cudaError_t launch_gram_f64(int N, int d, int nslots, const GramSource& src,
+                            unsigned long long* out, int num_sms, cudaStream_t s) {
+  return launch_gram<double>(N, d, nslots, src, out, nullptr, num_sms, s);
+}
+
+// ------------------------------------------------------------- init
+
+__global__ void k_init_frame(int N, int d, uint64_t seed, double2* phi64, float2* phi32,
+                             DevState* st) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double* base = reinterpret_cast<double*>(phi64 + (size_t)j * d);
+  const bool ok = gen_column<double>(nullptr, d, j, seed, 0u, 0u, 1u, 0.0, base, base + 1, 2);
+  if (!ok && st) atomicOr(&st->error, (uint32_t)kErrZeroColumn);
+  for (int i = 0; i < d; ++i) {
+    const double2 v = phi64[(size_t)j * d + i];
+    phi32[(size_t)j * d + i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+cudaError_t launch_init_frame(int N, int d, uint64_t seed, double2* phi64, float2* phi32,
+                              DevState* st, cudaStream_t s) {
+  k_init_frame<<<(N + 127) / 128, 128, 0, s>>>(N, d, seed, phi64, phi32, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------- iteration start
+
+__global__ void k_iter_begin(DevState* st, void* z0, size_t b0, void* z1, size_t b1, void* z2,
+                             size_t b2) {
+  __shared__ uint32_t act;
+  if (threadIdx.x == 0) {
+    act = (!st->done && st->t < st->t_stop) ? 1u : 0u;
+    st->active = act;
+    st->npairs = 0u;
+    st->overflow = 0u;
+    if (act) {
+      st->delta_used = st->delta;
+      st->accepted = 0u;
+    }
+  }
+  __syncthreads();
+  if (!act) return;
+  void* ptrs[3] = {z0, z1, z2};
+  size_t bytes[3] = {b0, b1, b2};
+  for (int q = 0; q < 3; ++q) {
+    if (!ptrs[q]) continue;
+    uint32_t* p = reinterpret_cast<uint32_t*>(ptrs[q]);
+    const size_t n = bytes[q] / 4;
+    for (size_t e = threadIdx.x; e < n; e += blockDim.x) p[e] = 0u;
+  }
+}
+
+cudaError_t launch_iter_begin(DevState* st, void* zero0, size_t bytes0, void* zero1,
+                              size_t bytes1, void* zero2, size_t bytes2, cudaStream_t s) {
+  k_iter_begin<<<1, 1024, 0, s>>>(st, zero0, bytes0, zero1, bytes1, zero2, bytes2);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ the accept/radius rule
+
+__device__ void apply_rule_and_trace(DevState* st, uint32_t cstar, double mu2_best,
+                                     double mu2_screen, TraceRowDev* trace) {
+  const uint32_t t = st->t + 1u;
+  const double dused = st->delta_used;
+  const bool accept = mu2_best < st->mu2_cur;
+  double dl;
+  if (accept) {
+    st->mu2_cur = mu2_best;
+    dl = fmin(st->gamma_inc * dused, st->delta_max);
+    st->accepts += 1u;
+  } else {
+    dl = fmax(st->gamma_dec * dused, st->delta_min);
+  }
+  st->delta = dl;
+  st->accepted = accept ? 1u : 0u;
+  st->cstar = cstar;
+  st->mu2_best = mu2_best;
+  st->mu2_screen = mu2_screen;
+  st->t = t;
+  if (st->mu2_cur <= st->target2) st->done = 1u;
+  if (trace && st->trace_cap) {
+    TraceRowDev& r = trace[(t - 1u) % st->trace_cap];
+    r.t = t; r.cstar = cstar; r.mu2_best = mu2_best; r.mu2_screen = mu2_screen;
+    r.mu2_cur = st->mu2_cur; r.delta_used = dused; r.delta_next = dl;
+    r.accepted = accept ? 1 : 0; r.reserved = 0;
+  }
+}
+
+// argmin over candidates (lowest c on ties) then the rule; one CTA.
+template <typename B>
+__global__ void k_select_decide(DevState* st, const B* mu2, int K, TraceRowDev* trace) {
+  if (!st->active) return;
+  __shared__ B sv[32];
+  __shared__ int sc[32];
+  B bv = ~B(0);
+  int bc = 0x7fffffff;
+  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    const B v = mu2[c];
+    if (v < bv || (v == bv && c < bc)) { bv = v; bc = c; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const B ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+    if (ov < bv || (ov == bv && oc < bc)) { bv = ov; bc = oc; }
+  }
+  if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = bv; sc[threadIdx.x >> 5] = bc; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (sv[w] < bv || (sv[w] == bv && sc[w] < bc)) { bv = sv[w]; bc = sc[w]; }
+    const double m = (double)nonneg_from_bits(bv);
+    apply_rule_and_trace(st, (uint32_t)bc, m, m, trace);
+  }
+}
+
+cudaError_t launch_select_decide_f32(DevState* st, const unsigned int* mu2, int K,
+                                     TraceRowDev* trace, cudaStream_t s) {
+  k_select_decide<unsigned int><<<1, 1024, 0, s>>>(st, mu2, K, trace);
+  return cudaGetLastError();
+}
+cudaError_t launch_select_decide_f64(DevState* st, const unsigned long long* mu2, int K,
+                                     TraceRowDev* trace, cudaStream_t s) {
+  k_select_decide<unsigned long long><<<1, 1024, 0, s>>>(st, mu2, K, trace);
+  return cudaGetLastError();
+}
+
+// Regenerate the accepted candidate in place (one thread per column).  The
+// counters are those of the iteration just decided: t = st->t.
+template <typename T, typename O>
+__global__ void k_commit(int N, int d, uint64_t seed, DevState* st,
+                         typename Cplx<T>::type* phi, typename Cplx<O>::type* other) {
+  if (!st->active || !st->accepted) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  T* base = reinterpret_cast<T*>(phi + (size_t)j * d);
+  gen_column<T>(phi, d, j, seed, st->cstar, st->t, 0u, (T)st->delta_used, base, base + 1, 2);
+  for (int i = 0; i < d; ++i) {
+    const auto v = phi[(size_t)j * d + i];
+    other[(size_t)j * d + i].x = (O)v.x;
+    other[(size_t)j * d + i].y = (O)v.y;
+  }
+}
+
+cudaError_t launch_commit_f32(int N, int d, uint64_t seed, DevState* st, float2* phi32,
+                              double2* phi64, cudaStream_t s) {
+  k_commit<float, double><<<(N + 127) / 128, 128, 0, s>>>(N, d, seed, st, phi32, phi64);
+  return cudaGetLastError();
+}
+cudaError_t launch_commit_f64(int N, int d, uint64_t seed, DevState* st, double2* phi64,
+                              float2* phi32, cudaStream_t s) {
+  k_commit<double, float><<<(N + 127) / 128, 128, 0, s>>>(N, d, seed, st, phi64, phi32);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- screen mode
+
+// The k smallest screen scores, ordered by (mu^2, c); one CTA.
+__global__ void k_topk(DevState* st, const unsigned int* mu2, int K, int k, uint32_t* topk) {
+  if (!st->active) return;
+  __shared__ unsigned long long sk[32];
+  __shared__ unsigned long long last;
+  if (threadIdx.x == 0) last = 0ull;
+  __syncthreads();
+  for (int r = 0; r < k; ++r) {
+    const unsigned long long floor_key = last;
+    unsigned long long best = ~0ull;
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+      const unsigned long long key = ((unsigned long long)mu2[c] << 32) | (unsigned)c;
+      if ((r == 0 || key > floor_key) && key < best) best = key;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+      best = ov < best ? ov : best;
+    }
+    if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = sk[w] < best ? sk[w] : best;
+      topk[r] = (uint32_t)(best & 0xffffffffull);
+      last = best;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_topk(DevState* st, const unsigned int* mu2_screen, int K, int k,
+                        uint32_t* topk, cudaStream_t s) {
+  k_topk<<<1, 1024, 0, s>>>(st, mu2_screen, K, k, topk);
+  return cudaGetLastError();
+}
+
+// Best survivor by its binary32 score (ties: lowest c), regenerated in
+// binary64 from the binary64 frame, plus its binary32 rounding.
+__global__ void k_materialize64(int N, int d, uint64_t seed, DevState* st,
+                                const uint32_t* topk, const unsigned int* mu2_top, int k,
+                                const double2* phi64, double2* cand64, float2* cand32) {
+  if (!st->active) return;
+  unsigned int bv = mu2_top[0];
+  uint32_t bc = topk[0];
+  for (int s = 1; s < k; ++s) {
+    const unsigned int v = mu2_top[s];
+    if (v < bv || (v == bv && topk[s] < bc)) { bv = v; bc = topk[s]; }
+  }
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j == 0) {
+    st->cstar = bc;
+    st->mu2_screen = (double)__uint_as_float(bv);
+  }
+  if (j >= N) return;
+  double* base = reinterpret_cast<double*>(cand64 + (size_t)j * d);
+  const bool ok = gen_column<double>(phi64, d, j, seed, bc, st->t + 1u, 0u, st->delta_used,
+                                     base, base + 1, 2);
+  if (!ok) atomicOr(&st->error, (uint32_t)kErrZeroColumn);
+  for (int i = 0; i < d; ++i) {
+    const double2 v = cand64[(size_t)j * d + i];
+    cand32[(size_t)j * d + i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+cudaError_t launch_materialize64(int N, int d, uint64_t seed, DevState* st,
+                                 const uint32_t* topk, const unsigned int* mu2_top, int k,
+                                 const double2* phi64, double2* cand64, float2* cand32,
+                                 cudaStream_t s) {
+  k_materialize64<<<(N + 127) / 128, 128, 0, s>>>(N, d, seed, st, topk, mu2_top, k, phi64,
+                                                   cand64, cand32);
+  return cudaGetLastError();
+}
+
+// binary64 |G_jk|^2 of the preselected pairs.
+__global__ void k_pairs64(const uint32_t* active, const uint32_t* npairs, const uint2* pairs,
+                          uint32_t cap, int d, const double2* f, unsigned long long* out) {
+  if (active && !*active) return;
+  const uint32_t n = min(*npairs, cap);
+  double m = 0.0;
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const uint2 jk = pairs[p];
+    const double2* x = f + (size_t)jk.x * d;
+    const double2* y = f + (size_t)jk.y * d;
+    double re = 0.0, im = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double2 u = x[i], v = y[i];
+      re = fma(u.x, v.x, fma(u.y, v.y, re));
+      im = fma(u.x, v.y, fma(-u.y, v.x, im));
+    }
+    m = fmax(m, re * re + im * im);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_nonneg(out, m);
+}
+
+cudaError_t launch_pairs64(const uint32_t* active, const uint32_t* npairs, const uint2* pairs,
+                           uint32_t cap, int d, const double2* frame64, unsigned long long* out,
+                           cudaStream_t s) {
+  k_pairs64<<<64, 256, 0, s>>>(active, npairs, pairs, cap, d, frame64, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_decide_certified(DevState* st, const unsigned long long* mu2_64,
+                                   TraceRowDev* trace) {
+  if (!st->active) return;
+  apply_rule_and_trace(st, st->cstar, nonneg_from_bits(*mu2_64), st->mu2_screen, trace);
+}
+
+cudaError_t launch_decide_certified(DevState* st, const unsigned long long* mu2_64,
+                                    TraceRowDev* trace, cudaStream_t s) {
+  k_decide_certified<<<1, 1, 0, s>>>(st, mu2_64, trace);
+  return cudaGetLastError();
+}
+
+__global__ void k_commit_copy(size_t n, DevState* st, const double2* cand64,
+                              const float2* cand32, double2* phi64, float2* phi32) {
+  if (!st->active || !st->accepted) return;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    phi64[e] = cand64[e];
+    phi32[e] = cand32[e];
+  }
+}
+
+cudaError_t launch_commit_copy(int N, int d, DevState* st, const double2* cand64,
+                               const float2* cand32, double2* phi64, float2* phi32,
+                               cudaStream_t s) {
+  const size_t n = (size_t)N * d;
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 1024);
+  k_commit_copy<<<grid, 256, 0, s>>>(n, st, cand64, cand32, phi64, phi32);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- utilities
+
+__global__ void k_normalize64(int N, int d, const double2* in, double2* out64, float2* out32,
+                              DevState* st) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double* base = reinterpret_cast<double*>(out64 + (size_t)j * d);
+  const bool ok = load_column<double>(in, d, j, true, base, base + 1, 2);
+  if (!ok && st) atomicOr(&st->error, (uint32_t)kErrZeroColumn);
+  for (int i = 0; i < d; ++i) {
+    const double2 v = out64[(size_t)j * d + i];
+    out32[(size_t)j * d + i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+cudaError_t launch_normalize64(int N, int d, const double2* in, double2* out64, float2* out32,
+                               DevState* st, cudaStream_t s) {
+  k_normalize64<<<(N + 127) / 128, 128, 0, s>>>(N, d, in, out64, out32, st);
+  return cudaGetLastError();
+}
+
+__global__ void k_gen_candidate(int N, int d, uint64_t seed, uint32_t t, uint32_t c,
+                                double delta, bool f64, const double2* phi64,
+                                const float2* phi32, double2* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double* base = reinterpret_cast<double*>(out + (size_t)j * d);
+  if (f64) {
+    gen_column<double>(phi64, d, j, seed, c, t, 0u, delta, base, base + 1, 2);
+  } else {
+    // binary32 generation into a scratch of the output, then widened
+    float* fb = reinterpret_cast<float*>(base);
+    gen_column<float>(phi32, d, j, seed, c, t, 0u, (float)delta, fb, fb + 1, 2);
+    for (int i = d - 1; i >= 0; --i) {
+      const float re = fb[2 * i], im = fb[2 * i + 1];
+      base[2 * i] = (double)re;
+      base[2 * i + 1] = (double)im;
+    }
+  }
+}
+
+cudaError_t launch_gen_candidate(int N, int d, uint64_t seed, uint32_t t, uint32_t c,
+                                 double delta, bool f64, const double2* phi64,
+                                 const float2* phi32, double2* out, cudaStream_t s) {
+  k_gen_candidate<<<(N + 127) / 128, 128, 0, s>>>(N, d, seed, t, c, delta, f64, phi64, phi32,
+                                                   out);
+  return cudaGetLastError();
+}
+
+cudaError_t init_kernel_attributes() {
+  const int maxs = 227 * 1024;
+  cudaError_t e;
+  e = cudaFuncSetAttribute(k_gram_tile<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gram_tile<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gram_tile<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gram_tile<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gram_tile<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gram_tile<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+  return e;
+}
+
+}  // namespace trstmi

@@ -1,0 +1,210 @@
+"""CUDA path vs the CPU oracle, element by element on identical seeded inputs.
+
+Tolerances: binary64 paths agree with the oracle to 1e-12 (relative on mu^2,
+i.e. rounding-order differences only); binary32 coherence agrees to 1e-6
+absolute on mu.  Shapes span several Gram tiles with a ragged tail, odd d,
+N = 2, d = 1 and N <= d.
+"""
+import numpy as np
+import pytest
+
+import frames as F
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+T = pytest.importorskip("paper_2207_06374_gb300.trstmi")
+
+
+def _mu_err(a2, b2):
+    return abs(np.sqrt(a2) - np.sqrt(b2))
+
+
+# ---------------------------------------------------------- coherence of frames
+
+@pytest.mark.parametrize("name,make", [
+    ("tetrahedral(2,4)", F.tetrahedral_2_4), ("harmonic(3,7)", F.harmonic_3_7),
+    ("hesse(3,9)", F.hesse_sic_3_9), ("mubs(3)", lambda: F.mubs(3)),
+    ("naimark(9,6)", lambda: F.naimark_complement(F.hesse_sic_3_9())),
+])
+def test_frame_mu_closed_forms(name, make):
+    phi = make()
+    ref = O.mu2(phi)
+    assert abs(T.mu2_frame(phi, "fp64") - ref) <= 1e-12 * ref
+    assert _mu_err(T.mu2_frame(phi, "fp32"), ref) < 1e-6
+
+
+@pytest.mark.parametrize("d,N", [(1, 5), (2, 2), (3, 17), (7, 130), (8, 64), (5, 301), (32, 200),
+                                 (16, 3), (64, 70)])
+def test_frame_mu_random(d, N):
+    rng = np.random.default_rng(100 * d + N)
+    phi = F.random_frame(d, N, rng)
+    ref = O.mu2(phi)
+    assert abs(T.mu2_frame(phi, "fp64") - ref) <= 1e-12 * max(ref, 1e-300)
+    assert _mu_err(T.mu2_frame(phi, "fp32"), ref) < 1e-6
+
+
+def test_frame_mu_orthonormal_is_zero():
+    rng = np.random.default_rng(9)
+    U = F.haar_unitary(12, rng)
+    assert T.mu2_frame(U, "fp64") < 1e-28
+    assert T.mu2_frame(U, "fp32") < 1e-12
+
+
+# ------------------------------------------------------- init and candidates
+
+@pytest.mark.parametrize("d,N,seed", [(2, 4, 1), (3, 9, 5), (7, 45, 12345678901), (32, 150, 3)])
+def test_init_matches_oracle(d, N, seed):
+    with T.Search(N, d, seed) as s:
+        phi = s.get_phi()
+    assert np.abs(phi - O.init(N, d, seed)).max() < 1e-14
+
+
+@pytest.mark.parametrize("d,N", [(2, 4), (5, 33), (8, 64)])
+def test_candidates_match_oracle(d, N):
+    seed = 77
+    with T.Search(N, d, seed) as s:
+        phi0 = s.get_phi()
+        for (t, c, delta) in [(1, 0, 0.1), (5, 300, 0.7), (123456, 4095, 1e-6)]:
+            ref = O.candidate(phi0, seed, delta, t, c)
+            assert np.abs(s.candidate(t, c, delta, "fp64") - ref).max() < 1e-13
+            assert np.abs(s.candidate(t, c, delta, "fp32") - ref).max() < 2e-6
+
+
+# ----------------------------------------------------------------- scoring
+
+@pytest.mark.parametrize("d,N,K", [(2, 4, 256), (3, 7, 64), (8, 64, 96), (5, 130, 12), (1, 3, 8),
+                                   (6, 4, 16)])
+def test_scores_match_oracle(d, N, K):
+    seed = 2024
+    with T.Search(N, d, seed) as s:
+        phi0 = s.get_phi()
+        for (t, c0, delta) in [(1, 0, 0.1), (17, 1000, 0.02)]:
+            ref = O.score(phi0, seed, delta, t, c0, K, nthreads=4)
+            g64 = s.score(t, c0, K, delta, "fp64")
+            g32 = s.score(t, c0, K, delta, "fp32")
+            assert np.all(np.abs(g64 - ref) <= 1e-12 * np.maximum(ref, 1e-300))
+            assert np.max(np.abs(np.sqrt(g32) - np.sqrt(ref))) < 1e-6
+            # the argmin the fp64 path picks is the oracle's (lowest c on ties)
+            assert int(np.argmin(g64)) == int(np.argmin(ref))
+
+
+def test_scores_full_size_sampled():
+    """d=8, N=64, K=4096 and d=32, N=1024: sampled candidates, fp32 vs oracle."""
+    for d, N, c0, cnt in ((8, 64, 4000, 16), (32, 1024, 1020, 2)):
+        with T.Search(N, d, 5, precision="fp32", K=cnt) as s:
+            phi0 = s.get_phi()
+            ref = O.score(phi0, 5, 0.1, 9, c0, cnt, nthreads=4)
+            g32 = s.score(9, c0, cnt, 0.1, "fp32")
+            assert np.max(np.abs(np.sqrt(g32) - np.sqrt(ref))) < 1e-6
+
+
+# ------------------------------------------------------------- trajectories
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_fp64_trajectory_matches_oracle_tetrahedral(seed):
+    """Config d=2, N=4, K=256, Delta0=0.1, 2000 iterations, binary64: identical
+    argmin and accept sequence, final mu equal to 1e-12 and within 1e-5 of
+    1/sqrt(3)."""
+    opts = O.make_opts(K=256, T=2000)
+    ophi, om2, odl, otr = O.run(4, 2, seed, opts)
+    with T.Search(4, 2, seed, K=256, precision="fp64", trace_cap=2000) as s:
+        info = s.step(2000)
+        tr = s.trace()
+        mu_cert, welch = s.coherence()
+    assert info.iters_done == 2000 and len(tr) == 2000
+    assert np.array_equal(tr["cstar"], otr["cstar"])
+    assert np.array_equal(tr["accepted"], otr["accepted"])
+    assert np.allclose(tr["mu2_cur"], otr["mu2_cur"], rtol=1e-12, atol=0)
+    assert np.allclose(tr["delta_next"], otr["delta_next"], rtol=1e-12, atol=0)
+    assert abs(info.mu - np.sqrt(om2)) < 1e-12
+    assert abs(mu_cert - 1 / np.sqrt(3)) < 1e-5 and abs(welch - 1 / np.sqrt(3)) < 1e-15
+
+
+@pytest.mark.parametrize("d,N,K,iters", [(3, 7, 128, 150), (5, 17, 64, 100), (3, 2, 8, 20)])
+def test_fp64_trajectory_matches_oracle_other_shapes(d, N, K, iters):
+    seed = 31
+    opts = O.make_opts(K=K, T=iters)
+    ophi, om2, odl, otr = O.run(N, d, seed, opts, nthreads=4)
+    with T.Search(N, d, seed, K=K, precision="fp64") as s:
+        s.step(iters)
+        tr = s.trace()
+        phi = s.get_phi()
+    assert np.array_equal(tr["cstar"], otr["cstar"])
+    assert np.array_equal(tr["accepted"], otr["accepted"])
+    assert np.abs(phi - ophi).max() < 1e-12
+
+
+def test_fp32_run_decisions_replay_in_fp64():
+    """The fp32 path's choices, replayed by the oracle in binary64, give the
+    same accept decisions while the improvements exceed fp32 resolution."""
+    d, N, K, iters, seed = 4, 12, 256, 40, 8
+    with T.Search(N, d, seed, K=K, precision="fp32") as s:
+        phi0 = s.get_phi()
+        s.step(iters)
+        tr = s.trace()
+        mu_cert, _ = s.coherence()
+        phi = s.get_phi()
+    opts = O.make_opts(K=K, T=iters)
+    rphi, rm2, rdl, rtr = O.replay(phi0, seed, opts, 0.1, O.mu2(phi0), 0, tr["cstar"])
+    gaps = np.abs(np.sqrt(rtr["mu2_best"]) - np.sqrt(np.maximum(rtr["mu2_cur"], 0)))
+    clear = gaps > 1e-5
+    assert np.array_equal(tr["accepted"][clear], rtr["accepted"][clear])
+    assert np.max(np.abs(np.sqrt(tr["mu2_best"]) - np.sqrt(rtr["mu2_best"]))) < 1e-6
+    assert abs(mu_cert - O.mu(phi)) < 1e-12
+
+
+def test_checkpoint_resume_is_bitwise():
+    for prec in ("fp64", "fp32"):
+        with T.Search(9, 3, 4, K=64, precision=prec) as a:
+            a.step(30)
+            blob = a.get_state()
+            a.step(25)
+            pa = a.get_phi()
+            ta = a.trace(25)
+        with T.Search(9, 3, 4, K=64, precision=prec) as b:
+            b.set_state(blob)
+            b.step(25)
+            pb = b.get_phi()
+            tb = b.trace(25)
+        with T.Search(9, 3, 4, K=64, precision=prec) as c:
+            c.step(55)
+            pc = c.get_phi()
+        assert np.array_equal(pa, pb) and np.array_equal(pa, pc)
+        assert np.array_equal(ta, tb)
+
+
+def test_set_phi_and_coherence():
+    phi = F.hesse_sic_3_9()
+    with T.Search(9, 3, 1) as s:
+        s.set_phi(phi * 3.0)             # renormalised on the way in
+        mu, w = s.coherence()
+        assert abs(mu - 0.5) < 1e-12 and abs(w - 0.5) < 1e-15
+        assert np.abs(s.get_phi() - phi).max() < 1e-14
+        bad = phi.copy()
+        bad[:, 4] = 0
+        with pytest.raises(T.TrstmiError):
+            s.set_phi(bad)
+
+
+def test_target_stops_early():
+    with T.Search(4, 2, 1, K=128, target_mu=0.6) as s:
+        info = s.step(2000)
+        assert info.done == 1 and info.iters_done < 2000 and info.mu <= 0.6
+        more = s.step(10)
+        assert more.iters_done == 0
+
+
+def test_degenerate_shapes():
+    with T.Search(5, 1, 3, K=16) as s:          # C^1: mu = 1 always
+        s.step(5)
+        assert abs(s.coherence()[0] - 1.0) < 1e-15
+    with T.Search(3, 6, 3, K=64) as s:          # N <= d: optimum is 0
+        s.step(300)
+        assert s.coherence()[0] < 1e-3
+    with pytest.raises(T.TrstmiError):
+        T.Search(1, 3, 0)
+    with pytest.raises(T.TrstmiError):
+        T.Search(4, 0, 0)
+    with pytest.raises(T.TrstmiError):
+        T.Search(4, 2, 0, K=0)
