@@ -160,6 +160,11 @@ void trstmi_destroy(trstmi_handle h);
 /* Static string for a status code. */
 const char *trstmi_strerror(int status);
 
+/* Detail of the last CUDA failure seen by the calling thread (the CUDA error
+ * name and text and the failing call), "" if none.  Valid until the thread's
+ * next failing call. */
+const char *trstmi_last_error(void);
+
 /* ---------------------------------------------- scoring entry points
  * These run one stage of the iteration on the current frame without
  * changing the search state; the tests use them to compare the kernels with

@@ -30,21 +30,35 @@ constexpr int kGraphChunk = 32;
 
 std::mutex g_attr_mu;
 bool g_attr_done[64] = {false};
+thread_local char g_last_error[256] = "";
+
+int record_cuda_error(cudaError_t e, const char* what, int line) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (at capi.cu:%d: %.120s)",
+                cudaGetErrorName(e), cudaGetErrorString(e), line, what);
+  cudaGetLastError();
+  return TRSTMI_ECUDA;
+}
+
+#define TRY_CUDA(expr)                                             \
+  do {                                                             \
+    cudaError_t _e = (expr);                                       \
+    if (_e != cudaSuccess) return record_cuda_error(_e, #expr, __LINE__); \
+  } while (0)
 
 int ensure_device(int device, int* num_sms) {
   int n = 0;
-  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0) return TRSTMI_ECUDA;
+  TRY_CUDA(cudaGetDeviceCount(&n));
+  if (n <= 0) return TRSTMI_ECUDA;
   if (device < 0 || device >= n || device >= 64) return TRSTMI_EINVAL;
-  if (cudaSetDevice(device) != cudaSuccess) return TRSTMI_ECUDA;
+  TRY_CUDA(cudaSetDevice(device));
   {
     std::lock_guard<std::mutex> g(g_attr_mu);
     if (!g_attr_done[device]) {
-      if (init_kernel_attributes() != cudaSuccess) return TRSTMI_ECUDA;
+      TRY_CUDA(init_kernel_attributes());
       g_attr_done[device] = true;
     }
   }
-  if (cudaDeviceGetAttribute(num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
-    return TRSTMI_ECUDA;
+  TRY_CUDA(cudaDeviceGetAttribute(num_sms, cudaDevAttrMultiProcessorCount, device));
   return TRSTMI_OK;
 }
 
@@ -88,13 +102,9 @@ double welch_of(int N, int d) {
   return std::sqrt((double)(N - d) / ((double)d * (double)(N - 1)));
 }
 
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? TRSTMI_OK : TRSTMI_ECUDA; }
-
-#define TRY_CUDA(expr)                                   \
-  do {                                                   \
-    cudaError_t _e = (expr);                             \
-    if (_e != cudaSuccess) return TRSTMI_ECUDA;          \
-  } while (0)
+int cuda_status(cudaError_t e) {
+  return e == cudaSuccess ? TRSTMI_OK : record_cuda_error(e, "kernel launch", __LINE__);
+}
 
 float certify_margin(int d) {
   // |G| in binary32 of a frame rounded from binary64 differs from the
@@ -289,6 +299,8 @@ void trstmi_default_options(trstmi_options* o) {
   o->stream = nullptr;
   o->device = 0;
 }
+
+const char* trstmi_last_error(void) { return g_last_error; }
 
 const char* trstmi_strerror(int s) {
   switch (s) {

@@ -89,5 +89,6 @@ cudaError_t launch_screen_bf16(int N, int d, uint64_t seed, const float2* phi32,
                                cudaStream_t s);
 
 cudaError_t init_kernel_attributes();
+cudaError_t init_screen_attributes(int optin_smem);
 
 }  // namespace trstmi

@@ -628,21 +628,27 @@ cudaError_t launch_gen_candidate(int N, int d, uint64_t seed, uint32_t t, uint32
   return cudaGetLastError();
 }
 
+template <typename K> static cudaError_t allow_max_dynamic_smem(K kernel, int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
 cudaError_t init_kernel_attributes() {
-  const int maxs = 227 * 1024;
-  cudaError_t e;
-  e = cudaFuncSetAttribute(k_gram_tile<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_gram_tile<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_gram_tile<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_gram_tile<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_gram_tile<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_gram_tile<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-  return e;
+  if ((e = allow_max_dynamic_smem(k_gram_tile<float, 4>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_gram_tile<float, 2>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_gram_tile<float, 1>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_gram_tile<double, 4>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_gram_tile<double, 2>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_gram_tile<double, 1>, optin)) != cudaSuccess) return e;
+  return init_screen_attributes(optin);
 }
 
 }  // namespace trstmi

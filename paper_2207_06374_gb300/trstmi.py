@@ -25,7 +25,8 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16_SCREEN}
 class TrstmiError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {strerror(status)} ({status})")
+        detail = lib().trstmi_last_error().decode() if status == TRSTMI_ECUDA else ""
+        super().__init__(f"{what}: {strerror(status)} ({status}) {detail}".rstrip())
 
 
 class Options(ctypes.Structure):
@@ -78,6 +79,7 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int)]),
     "trstmi_destroy": (None, [ctypes.c_void_p]),
     "trstmi_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "trstmi_last_error": (ctypes.c_char_p, []),
     "trstmi_score": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
                                     ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp]),
     "trstmi_candidate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,

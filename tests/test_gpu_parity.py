@@ -85,8 +85,12 @@ def test_scores_match_oracle(d, N, K):
             g32 = s.score(t, c0, K, delta, "fp32")
             assert np.all(np.abs(g64 - ref) <= 1e-12 * np.maximum(ref, 1e-300))
             assert np.max(np.abs(np.sqrt(g32) - np.sqrt(ref))) < 1e-6
-            # the argmin the fp64 path picks is the oracle's (lowest c on ties)
-            assert int(np.argmin(g64)) == int(np.argmin(ref))
+            # the fp64 path's argmin is a valid argmin of the oracle's scores
+            # (equal to rounding: several candidates can tie, e.g. d = 1)
+            c = int(np.argmin(g64))
+            assert ref[c] <= ref.min() * (1 + 1e-12)
+            if np.sort(ref)[1] > ref.min() * (1 + 1e-9):   # unique minimum
+                assert c == int(np.argmin(ref))
 
 
 def test_scores_full_size_sampled():
@@ -151,7 +155,8 @@ def test_fp32_run_decisions_replay_in_fp64():
     clear = gaps > 1e-5
     assert np.array_equal(tr["accepted"][clear], rtr["accepted"][clear])
     assert np.max(np.abs(np.sqrt(tr["mu2_best"]) - np.sqrt(rtr["mu2_best"]))) < 1e-6
-    assert abs(mu_cert - O.mu(phi)) < 1e-12
+    # coherence() certifies the frame after renormalising it in binary64
+    assert abs(mu_cert - O.mu(phi / np.linalg.norm(phi, axis=0))) < 1e-12
 
 
 def test_checkpoint_resume_is_bitwise():
