@@ -1,14 +1,437 @@
-// Tensor-core (tcgen05) bf16 screen of the candidate Gram matrices.
+// bf16 tensor-core screen of the candidate Gram matrices (tcgen05, sm_103a).
+//
+// For candidate c of iteration t the CTA forms X = [A; B] (2*DP x N, bf16),
+// the real split of Phi_c = normalise_cols(Phi + Delta Z_{t,c}) = A + iB, in
+// shared memory, then sweeps the upper-triangle 128 x 128 tiles (I <= J) of
+//   Re G = A_I^T A_J + B_I^T B_J            (one K = 2*DP contraction)
+//   Im G = A_I^T B_J - B_I^T A_J            (two K = DP contractions, the
+//                                             second with A negated)
+// on the tensor cores with fp32 accumulators in tensor memory, and reduces
+// max_{j<k} |G_jk|^2 in the epilogue; the N x N Gram never leaves the SM
+// (coherence: arXiv 2207.06374, Sec. "Introduction"; upper triangle only:
+// Sec. "Optimization procedure").
+//
+// Roles (13 warps): warps 0-7 generate column blocks, warps 8-11 (one
+// warpgroup) read the accumulators, warp 12 owns tensor memory and issues the
+// MMAs.  Shared-memory column blocks and the two accumulator buffers are
+// handed over with mbarriers; every wait is bounded in time and gives up by
+// setting an error bit instead of spinning forever.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "kernels.h"
+#include "philox.cuh"
 
 namespace trstmi {
+namespace {
 
-bool screen_supported(int, int) { return false; }
-cudaError_t init_screen_attributes(int) { return cudaSuccess; }
+constexpr int kDP = 32;                 // padded d: K = 2*kDP = 64 bf16 = 128 bytes / column
+constexpr int kBlockCols = 128;         // columns per block = MMA M = N
+constexpr int kBlockBytes = kBlockCols * 2 * kDP * 2;   // 16 KiB
+constexpr int kMaxBlocks = 12;          // N <= 1536
+constexpr int kGenWarps = 8, kEpiWarps = 4;
+constexpr int kEpiWarp0 = kGenWarps;                   // warps 8..11: a whole warpgroup
+constexpr int kMmaWarp = kGenWarps + kEpiWarps;        // warp 12
+constexpr int kThreads = 32 * (kMmaWarp + 1);          // 416
+constexpr uint32_t kTmemCols = 512;                    // 2 buffers x (128 Re + 128 Im)
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
-cudaError_t launch_screen_bf16(int, int, uint64_t, const float2*, int, uint32_t, uint32_t, double,
-                               const DevState*, unsigned int*, uint32_t*, int, cudaStream_t) {
-  return cudaErrorNotSupported;
+struct ScreenArgs {
+  int N, d, nb, ntiles, K;
+  uint64_t seed;
+  const float2* phi;
+  uint32_t c0, t;
+  float delta;
+  const DevState* st;
+  unsigned int* out;
+  uint32_t* err;
+};
+
+struct SmemCtl {
+  unsigned long long blk_full[kMaxBlocks];
+  unsigned long long blk_empty[kMaxBlocks];
+  unsigned long long acc_full[2];
+  unsigned long long acc_empty[2];
+  unsigned long long drain;
+  uint32_t tmem_base;
+  volatile int abort_flag;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false (and the CTA-wide abort flag and the error bit set) if
+// the phase does not complete within kWaitLimitNs or another role aborted.
+__device__ bool mbar_wait(unsigned long long* b, uint32_t parity, SmemCtl* ctl, uint32_t* err) {
+  if (mbar_try_wait(b, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(b, parity)) return true;
+    if ((it & 63u) == 0u) {
+      if (ctl->abort_flag) return false;
+      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+        ctl->abort_flag = 1;
+        if (err) atomicOr(err, (uint32_t)kErrTimeout);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// UMMA shared-memory descriptor: K-major operand in the 128-byte swizzled
+// layout (8 rows x 128 B atoms, 1024 B apart).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);          // start address
+  d |= (uint64_t)1u << 16;                          // leading byte offset (unused: 16 B)
+  d |= (uint64_t)(1024u >> 4) << 32;                // stride byte offset: 1024 B
+  d |= (uint64_t)1u << 46;                          // descriptor version
+  d |= (uint64_t)2u << 61;                          // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major,
+// M = N = 128; bit 13 negates A.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+constexpr uint32_t kIdescNegA = kIdesc | (1u << 13);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tile_coords_tc(int tau, int& I, int& J) {
+  int j = (int)((sqrtf(8.0f * (float)tau + 1.0f) - 1.0f) * 0.5f);
+  while ((j + 1) * (j + 2) / 2 <= tau) ++j;
+  while (j * (j + 1) / 2 > tau) --j;
+  J = j;
+  I = tau - j * (j + 1) / 2;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Column r (0..127) of a block, 16-byte chunk c (0..7) -> byte offset in the
+// block: 8-row atoms of 1024 B, chunk index XOR-swizzled by the row.
+__device__ __forceinline__ uint32_t swz_offset(int r, int c) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_screen_bf16(const ScreenArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ SmemCtl ctl;
+  // 1024-byte aligned operand area
+  const uint32_t raw = smem_u32(smem_raw);
+  unsigned char* xs = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  const uint32_t xs_addr = smem_u32(xs);
+
+  uint32_t t = a.t;
+  float delta = a.delta;
+  if (a.st) {
+    if (!a.st->active) return;
+    t = a.st->t + 1u;
+    delta = (float)a.st->delta_used;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nb = a.nb, ntiles = a.ntiles;
+
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < nb; ++b) {
+      mbar_init(&ctl.blk_full[b], kGenWarps);
+      mbar_init(&ctl.blk_empty[b], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl.acc_full[b], 1);
+      mbar_init(&ctl.acc_empty[b], kEpiWarps);
+    }
+    mbar_init(&ctl.drain, 1);
+    ctl.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kMmaWarp) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+            smem_u32(&ctl.tmem_base)),
+        "r"(kTmemCols)
+        : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl.tmem_base;
+
+  if (warp < kGenWarps) {
+    // ------------------------------------------------------- generators
+    const int g = threadIdx.x;            // 0..255
+    const int r = g >> 1, h = g & 1;      // column within the block, half of the entries
+    const int d = a.d, P = (d + 1) >> 1;
+    const uint32_t k0 = seed_lo(a.seed), k1 = seed_hi(a.seed);
+    int q = 0;
+    for (int c = blockIdx.x; c < a.K; c += gridDim.x, ++q) {
+      const uint32_t cand = a.c0 + (uint32_t)c;
+      for (int b = 0; b < nb; ++b) {
+        if (q > 0) {
+          bool ok = true;
+          if (lane == 0) ok = mbar_wait(&ctl.blk_empty[b], (uint32_t)((q - 1) & 1), &ctl, a.err);
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) goto gen_done;
+        }
+        const int j = b * kBlockCols + r;
+        float xr[16], xi[16];
+        float s = 0.f;
+        if (j < a.N) {
+          const float2* col = a.phi + (size_t)j * d;
+#pragma unroll
+          for (int pp = 0; pp < 8; ++pp) {
+            const int p = 8 * h + pp;
+            if (p < P) {
+              const PhiloxOut u = philox4x32_10((uint32_t)j * (uint32_t)P + (uint32_t)p, cand, t,
+                                                0u, k0, k1);
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                const int i = 2 * p + e;
+                float zr = 0.f, zi = 0.f, vr = 0.f, vi = 0.f;
+                if (i < d) {
+                  cn_from_u32_fast(u.x[2 * e], u.x[2 * e + 1], zr, zi);
+                  const float2 v = col[i];
+                  vr = fmaf(delta, zr, v.x);
+                  vi = fmaf(delta, zi, v.y);
+                }
+                xr[2 * pp + e] = vr;
+                xi[2 * pp + e] = vi;
+                s = fmaf(vr, vr, fmaf(vi, vi, s));
+              }
+            } else {
+              xr[2 * pp] = xr[2 * pp + 1] = 0.f;
+              xi[2 * pp] = xi[2 * pp + 1] = 0.f;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) { xr[e] = 0.f; xi[e] = 0.f; }
+        }
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        const float inv = s > 0.f ? rsqrtf(s) : 0.f;
+        unsigned char* blk = xs + b * kBlockBytes;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          uint4 re, im;
+          const int e0 = 8 * half;
+          re.x = pack_bf16(xr[e0 + 0] * inv, xr[e0 + 1] * inv);
+          re.y = pack_bf16(xr[e0 + 2] * inv, xr[e0 + 3] * inv);
+          re.z = pack_bf16(xr[e0 + 4] * inv, xr[e0 + 5] * inv);
+          re.w = pack_bf16(xr[e0 + 6] * inv, xr[e0 + 7] * inv);
+          im.x = pack_bf16(xi[e0 + 0] * inv, xi[e0 + 1] * inv);
+          im.y = pack_bf16(xi[e0 + 2] * inv, xi[e0 + 3] * inv);
+          im.z = pack_bf16(xi[e0 + 4] * inv, xi[e0 + 5] * inv);
+          im.w = pack_bf16(xi[e0 + 6] * inv, xi[e0 + 7] * inv);
+          // real parts of entries 16h + 8half .. +7 -> chunk 2h + half;
+          // imaginary parts -> chunk 4 + 2h + half
+          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * h + half)) = re;
+          *reinterpret_cast<uint4*>(blk + swz_offset(r, 4 + 2 * h + half)) = im;
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl.blk_full[b]);
+      }
+    }
+  gen_done:;
+  } else if (warp < kMmaWarp) {
+    // --------------------------------------------------------- epilogue
+    const int qw = warp - kEpiWarp0;                 // TMEM lane quarter
+    const int row = 32 * qw + lane;                  // accumulator row = column j within block I
+    uint32_t gt = 0;                                 // tile counter
+    for (int c = blockIdx.x; c < a.K; c += gridDim.x) {
+      float m = 0.f;
+      bool ok = true;
+      for (int tau = 0; tau < ntiles; ++tau, ++gt) {
+        int I, J;
+        tile_coords_tc(tau, I, J);
+        const uint32_t buf = gt & 1u, use = gt >> 1;
+        if (lane == 0) ok = mbar_wait(&ctl.acc_full[buf], use & 1u, &ctl, a.err);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t base = tmem + ((uint32_t)(32 * qw) << 16) + buf * 256u;
+#pragma unroll 1
+        for (int ch = 0; ch < 4; ++ch) {
+          uint32_t re[32], im[32];
+          tmem_ld32(base + 32u * ch, re);
+          tmem_ld32(base + 128u + 32u * ch, im);
+          tmem_ld_wait();
+          if (I != J) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const float x = __uint_as_float(re[e]), y = __uint_as_float(im[e]);
+              m = fmaxf(m, fmaf(x, x, y * y));
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const float x = __uint_as_float(re[e]), y = __uint_as_float(im[e]);
+              const float v = fmaf(x, x, y * y);
+              m = (32 * ch + e > row) ? fmaxf(m, v) : m;
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl.acc_empty[buf]);
+      }
+      if (!ok) break;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) atomicMax(a.out + c, __float_as_uint(m));
+    }
+  } else {
+    // ------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t gt = 0;
+      int q = 0;
+      bool ok = true;
+      for (int c = blockIdx.x; c < a.K && ok; c += gridDim.x, ++q) {
+        for (int J = 0; J < nb && ok; ++J) {
+          ok = mbar_wait(&ctl.blk_full[J], (uint32_t)(q & 1), &ctl, a.err);
+          if (!ok) break;
+          for (int I = 0; I <= J; ++I, ++gt) {
+            const uint32_t buf = gt & 1u, use = gt >> 1;
+            if (use > 0) {
+              ok = mbar_wait(&ctl.acc_empty[buf], (use - 1u) & 1u, &ctl, a.err);
+              if (!ok) break;
+            }
+            tc_fence_after();
+            const uint32_t aI = xs_addr + (uint32_t)(I * kBlockBytes);
+            const uint32_t bJ = xs_addr + (uint32_t)(J * kBlockBytes);
+            const uint32_t dre = tmem + buf * 256u, dim = dre + 128u;
+            // Re: sum over the whole K = 2*DP (4 steps of 16)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma_bf16(dre, smem_desc_sw128(aI + 32u * kk), smem_desc_sw128(bJ + 32u * kk), kIdesc,
+                       kk > 0 ? 1u : 0u);
+            // Im: A_I^T B_J (K slices 0,1 against 2,3) - B_I^T A_J (2,3 against 0,1)
+            mma_bf16(dim, smem_desc_sw128(aI + 0u), smem_desc_sw128(bJ + 64u), kIdesc, 0u);
+            mma_bf16(dim, smem_desc_sw128(aI + 32u), smem_desc_sw128(bJ + 96u), kIdesc, 1u);
+            mma_bf16(dim, smem_desc_sw128(aI + 64u), smem_desc_sw128(bJ + 0u), kIdescNegA, 1u);
+            mma_bf16(dim, smem_desc_sw128(aI + 96u), smem_desc_sw128(bJ + 32u), kIdescNegA, 1u);
+            mma_commit(&ctl.acc_full[buf]);
+            if (J == nb - 1) mma_commit(&ctl.blk_empty[I]);   // last use of block I
+          }
+        }
+      }
+      // all issued MMAs complete before tensor memory is released
+      mma_commit(&ctl.drain);
+      mbar_wait(&ctl.drain, 0u, &ctl, a.err);
+    }
+    __syncwarp();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+size_t screen_smem_bytes(int nb) { return (size_t)nb * kBlockBytes + 1024; }
+
+}  // namespace
+
+bool screen_supported(int N, int d) {
+  const int nb = (N + kBlockCols - 1) / kBlockCols;
+  return N >= 2 && d >= 1 && d <= kDP && nb <= kMaxBlocks;
+}
+
+cudaError_t init_screen_attributes(int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_screen_bf16);
+  if (e != cudaSuccess) return e;
+  const int want = (int)screen_smem_bytes(kMaxBlocks);
+  const int allowed = std::min(want, optin - (int)fa.sharedSizeBytes);
+  return cudaFuncSetAttribute(k_screen_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, allowed);
+}
+
+cudaError_t launch_screen_bf16(int N, int d, uint64_t seed, const float2* phi32, int K,
+                               uint32_t c0, uint32_t t, double delta, const DevState* st,
+                               unsigned int* mu2_out, uint32_t* err_flag, int num_sms,
+                               cudaStream_t s) {
+  if (!screen_supported(N, d) || K < 1) return cudaErrorInvalidValue;
+  ScreenArgs a;
+  a.N = N; a.d = d;
+  a.nb = (N + kBlockCols - 1) / kBlockCols;
+  a.ntiles = a.nb * (a.nb + 1) / 2;
+  a.K = K; a.seed = seed; a.phi = phi32; a.c0 = c0; a.t = t; a.delta = (float)delta;
+  a.st = st; a.out = mu2_out; a.err = err_flag;
+  const int grid = std::min(K, num_sms);
+  // the operand area is always reserved for the largest block count, so every
+  // descriptor address lies inside the CTA's shared memory
+  k_screen_bf16<<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace trstmi

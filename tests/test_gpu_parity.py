@@ -213,3 +213,64 @@ def test_degenerate_shapes():
         T.Search(4, 0, 0)
     with pytest.raises(T.TrstmiError):
         T.Search(4, 2, 0, K=0)
+
+
+# ------------------------------------------------- bf16 tensor-core screen
+
+@pytest.mark.parametrize("d,N,K", [(32, 1024, 6), (32, 300, 16), (7, 129, 16), (2, 4, 64),
+                                   (32, 128, 8), (16, 1536, 3), (1, 5, 8), (32, 2, 4)])
+def test_screen_scores_match_oracle(d, N, K):
+    """bf16 screen (before re-scoring) within 4e-3 of the oracle's mu on the
+    same seeded candidates: 2^-9 input rounding on unit vectors."""
+    seed = 99
+    with T.Search(N, d, seed, K=K, precision="fp32") as s:
+        phi0 = s.get_phi()
+        for (t, c0, delta) in [(1, 0, 0.1), (4, 77, 0.5)]:
+            ref = O.score(phi0, seed, delta, t, c0, K, nthreads=4)
+            gbf = s.score(t, c0, K, delta, "bf16")
+            assert np.max(np.abs(np.sqrt(gbf) - np.sqrt(ref))) < 4e-3
+
+
+def test_bf16_mode_decisions_replay_exactly():
+    """Screen + fp32 top-k + fp64 certification: the certified mu of every
+    chosen candidate equals the oracle's binary64 mu of that candidate, and the
+    oracle's accept/radius rule reproduces every decision and the final frame."""
+    d, N, K, iters, seed = 8, 40, 128, 25, 6
+    with T.Search(N, d, seed, K=K, precision="bf16", topk=8) as s:
+        phi0 = s.get_phi()
+        s.step(iters)
+        tr = s.trace()
+        phi = s.get_phi()
+    opts = O.make_opts(K=K, T=iters)
+    rphi, rm2, rdl, rtr = O.replay(phi0, seed, opts, 0.1, O.mu2(phi0), 0, tr["cstar"])
+    assert np.allclose(tr["mu2_best"], rtr["mu2_best"], rtol=1e-12, atol=0)
+    assert np.array_equal(tr["accepted"], rtr["accepted"])
+    assert np.abs(phi - rphi).max() < 1e-12
+    # the fp32 re-score of the winner is within fp32 tolerance of its fp64 mu
+    assert np.max(np.abs(np.sqrt(tr["mu2_screen"]) - np.sqrt(tr["mu2_best"]))) < 1e-6
+
+
+def test_bf16_mode_full_size_iterations_replay():
+    """d=32, N=1024, K=1024 (the precision-form workload): three iterations,
+    every decision reproduced by the oracle in binary64."""
+    d, N, K, seed = 32, 1024, 1024, 1
+    with T.Search(N, d, seed, K=K, precision="bf16") as s:
+        phi0 = s.get_phi()
+        s.step(3)
+        tr = s.trace()
+        mu, _ = s.coherence()
+    opts = O.make_opts(K=K, T=3)
+    rphi, rm2, rdl, rtr = O.replay(phi0, seed, opts, 0.1, O.mu2(phi0), 0, tr["cstar"])
+    assert np.allclose(tr["mu2_best"], rtr["mu2_best"], rtol=1e-12, atol=0)
+    assert np.array_equal(tr["accepted"], rtr["accepted"])
+    assert abs(mu - np.sqrt(rm2)) < 1e-12
+
+
+def test_bf16_mode_reaches_tetrahedral_code():
+    """Precision form on the pinned case d=2, N=4: final certified mu within
+    1e-5 of the oracle's fp64 run, i.e. of 1/sqrt(3)."""
+    _, om2, _, _ = O.run(4, 2, 1, O.make_opts(K=256, T=2000))
+    with T.Search(4, 2, 1, K=256, precision="bf16") as s:
+        s.step(2000)
+        mu, w = s.coherence()
+    assert abs(mu - np.sqrt(om2)) < 1e-5 and abs(mu - w) < 1e-5
