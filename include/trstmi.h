@@ -55,7 +55,11 @@ typedef enum trstmi_precision {
   /* candidates screened by a bf16 tensor-core Gram (fp32 accumulation), the
      top-k survivors re-scored in binary32, the best survivor regenerated,
      renormalised and certified in binary64; acceptance on the binary64 mu */
-  TRSTMI_BF16_SCREEN = 2
+  TRSTMI_BF16_SCREEN = 2,
+  /* as TRSTMI_BF16_SCREEN with fp16 screen operands: same tensor rate and
+     storage, 2^-11 instead of 2^-9 input rounding (screen error on mu <= 1e-3
+     instead of <= 4e-3 for unit vectors) */
+  TRSTMI_FP16_SCREEN = 3
 } trstmi_precision;
 
 /* ---------------------------------------------------------- options */
@@ -70,6 +74,11 @@ typedef struct trstmi_options {
   double delta_min;     /* radius floor (default 1e-9) */
   double delta_max;     /* radius cap (default 1.0) */
   double target_mu;     /* stop once mu <= target_mu (default 0 = never) */
+  /* screen modes: an iteration ranks its candidates with the tensor-core
+     screen while its radius is >= screen_min_delta, and with the binary32
+     Gram of every candidate below it, where candidate coherences differ by
+     less than the screen's resolution (default 0.01; 0 = always screen) */
+  double screen_min_delta;
   void *stream;         /* cudaStream_t to issue on, or NULL */
   int32_t device;       /* CUDA device ordinal (default 0) */
   int32_t reserved0;
@@ -90,7 +99,7 @@ typedef struct trstmi_trace_row {
   double delta_used;    /* radius the candidates were drawn with */
   double delta_next;    /* radius after the update */
   int32_t accepted;     /* 1 if the candidate replaced the frame */
-  int32_t reserved;
+  int32_t flags;        /* bit 0: candidates ranked by the tensor-core screen */
 } trstmi_trace_row;
 
 typedef struct trstmi_step_info {

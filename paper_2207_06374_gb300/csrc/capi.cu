@@ -97,6 +97,8 @@ struct trstmi_instance {
 
 namespace {
 
+bool is_screen(int p) { return p == TRSTMI_BF16_SCREEN || p == TRSTMI_FP16_SCREEN; }
+
 double welch_of(int N, int d) {
   if (N <= d || N < 2) return 0.0;
   return std::sqrt((double)(N - d) / ((double)d * (double)(N - 1)));
@@ -209,8 +211,18 @@ int enqueue_iteration(trstmi_instance* h, cudaStream_t s) {
     TRY_CUDA(launch_iter_begin(st, h->mu2_k32, sizeof(unsigned int) * K, h->mu2_top,
                                sizeof(unsigned int) * k, h->cert32,
                                2 * sizeof(unsigned int) + sizeof(unsigned long long), s));
-    TRY_CUDA(launch_screen_bf16(N, d, h->seed, h->phi32, K, 0u, 0u, 0.0, st, h->mu2_k32,
-                                &st->error, h->num_sms, s));
+    // rank the K candidates: tensor-core screen while delta >= screen_min_delta,
+    // else the fp32 Gram of every candidate (each kernel returns at once when
+    // the other one is selected for this iteration)
+    TRY_CUDA(launch_screen(prec == TRSTMI_FP16_SCREEN, N, d, h->seed, h->phi32, K, 0u, 0u, 0.0,
+                           st, h->mu2_k32, &st->error, h->num_sms, s));
+    GramSource full{};
+    full.perturb = true;
+    full.phi = h->phi32;
+    full.seed = h->seed;
+    full.st = st;
+    full.gate = &st->use_full;
+    TRY_CUDA(launch_gram_f32(N, d, K, full, h->mu2_k32, nullptr, h->num_sms, s));
     TRY_CUDA(launch_topk(st, h->mu2_k32, K, k, h->topk, s));
     GramSource src{};
     src.perturb = true;
@@ -269,13 +281,14 @@ int validate_options(int N, int d, const trstmi_options& o) {
   if (N < 2 || d < 1 || d > kMaxD) return TRSTMI_EINVAL;
   if ((long long)N * ((d + 1) / 2) >= (1ll << 32)) return TRSTMI_EINVAL;
   if (o.K < 1 || o.trace_cap < 0) return TRSTMI_EINVAL;
-  if (o.precision < TRSTMI_FP64 || o.precision > TRSTMI_BF16_SCREEN) return TRSTMI_EINVAL;
-  if (o.precision == TRSTMI_BF16_SCREEN && (o.topk < 1 || o.topk > 64 || o.topk > o.K))
+  if (o.precision < TRSTMI_FP64 || o.precision > TRSTMI_FP16_SCREEN) return TRSTMI_EINVAL;
+  if (is_screen(o.precision) && (o.topk < 1 || o.topk > 64 || o.topk > o.K))
     return TRSTMI_EINVAL;
   if (!(o.delta0 > 0) || !(o.gamma_inc >= 1) || !(o.gamma_dec > 0 && o.gamma_dec <= 1))
     return TRSTMI_EINVAL;
   if (!(o.delta_min >= 0) || !(o.delta_max >= o.delta_min)) return TRSTMI_EINVAL;
-  if (o.precision == TRSTMI_BF16_SCREEN && !screen_supported(N, d)) return TRSTMI_EUNSUPPORTED;
+  if (!(o.screen_min_delta >= 0)) return TRSTMI_EINVAL;
+  if (is_screen(o.precision) && !screen_supported(N, d)) return TRSTMI_EUNSUPPORTED;
   return TRSTMI_OK;
 }
 
@@ -296,6 +309,7 @@ void trstmi_default_options(trstmi_options* o) {
   o->delta_min = 1e-9;
   o->delta_max = 1.0;
   o->target_mu = 0.0;
+  o->screen_min_delta = 0.01;
   o->stream = nullptr;
   o->device = 0;
 }
@@ -335,7 +349,7 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   *out = nullptr;
   trstmi_options o;
   if (opt) o = *opt; else trstmi_default_options(&o);
-  if (o.precision != TRSTMI_BF16_SCREEN) o.topk = std::max(1, std::min(o.topk, o.K));
+  if (!is_screen(o.precision)) o.topk = std::max(1, std::min(o.topk, o.K));
   int num_sms = 0;
   int rc = ensure_device(o.device, &num_sms);
   if (rc) return rc;
@@ -409,6 +423,7 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   s0.gamma_dec = o.gamma_dec;
   s0.delta_min = o.delta_min;
   s0.delta_max = o.delta_max;
+  s0.screen_min_delta = o.screen_min_delta;
   s0.trace_cap = (uint32_t)o.trace_cap;
   cudaStream_t s = h->stream;
   if (cudaMemsetAsync(h->block, 0, off, s) != cudaSuccess ||
@@ -624,15 +639,15 @@ int trstmi_score(trstmi_handle h, uint32_t t, uint32_t c0, int count, double del
       if (cudaMemcpyAsync(b.data(), tmp, bytes, cudaMemcpyDeviceToHost, s) ||
           cudaStreamSynchronize(s)) { rc = TRSTMI_ECUDA; break; }
       for (int q = 0; q < count; ++q) std::memcpy(&outv[q], &b[q], sizeof(double));
-    } else if (precision == TRSTMI_FP32 || precision == TRSTMI_BF16_SCREEN) {
+    } else if (precision == TRSTMI_FP32 || is_screen(precision)) {
       cudaError_t e;
       if (precision == TRSTMI_FP32) {
         src.phi = h->phi32;
         e = launch_gram_f32(h->N, h->d, count, src, (unsigned int*)tmp, nullptr, h->num_sms, s);
       } else {
         if (!screen_supported(h->N, h->d)) { rc = TRSTMI_EUNSUPPORTED; break; }
-        e = launch_screen_bf16(h->N, h->d, h->seed, h->phi32, count, c0, t, delta, nullptr,
-                               (unsigned int*)tmp, &h->misc[1], h->num_sms, s);
+        e = launch_screen(precision == TRSTMI_FP16_SCREEN, h->N, h->d, h->seed, h->phi32, count,
+                          c0, t, delta, nullptr, (unsigned int*)tmp, &h->misc[1], h->num_sms, s);
       }
       if (e != cudaSuccess) { rc = TRSTMI_ECUDA; break; }
       std::vector<unsigned int> b(count);
@@ -712,8 +727,8 @@ int trstmi_mu2_frame(int N, int d, const double* phi, int precision, double* mu2
 int trstmi_profile_score(trstmi_handle h, int precision, int launches, double delta,
                          size_t flush_bytes, double* avg_ms) {
   if (!h || launches < 1 || !avg_ms || !(delta >= 0)) return TRSTMI_EINVAL;
-  if (precision < TRSTMI_FP64 || precision > TRSTMI_BF16_SCREEN) return TRSTMI_EINVAL;
-  if (precision == TRSTMI_BF16_SCREEN && !screen_supported(h->N, h->d)) return TRSTMI_EUNSUPPORTED;
+  if (precision < TRSTMI_FP64 || precision > TRSTMI_FP16_SCREEN) return TRSTMI_EINVAL;
+  if (is_screen(precision) && !screen_supported(h->N, h->d)) return TRSTMI_EUNSUPPORTED;
   TRY_CUDA(cudaSetDevice(h->opt.device));
   cudaStream_t s = h->stream;
   const int K = h->opt.K;
@@ -741,8 +756,8 @@ int trstmi_profile_score(trstmi_handle h, int precision, int launches, double de
       src.phi = h->phi32;
       e = launch_gram_f32(h->N, h->d, K, src, h->mu2_k32, nullptr, h->num_sms, s);
     } else {
-      e = launch_screen_bf16(h->N, h->d, h->seed, h->phi32, K, 0u, (uint32_t)(l + 1), delta,
-                             nullptr, h->mu2_k32, &h->misc[1], h->num_sms, s);
+      e = launch_screen(precision == TRSTMI_FP16_SCREEN, h->N, h->d, h->seed, h->phi32, K, 0u,
+                        (uint32_t)(l + 1), delta, nullptr, h->mu2_k32, &h->misc[1], h->num_sms, s);
     }
     cudaEventRecord(ev[2 * l + 1], s);
     if (e != cudaSuccess) rc = TRSTMI_ECUDA;

@@ -21,6 +21,10 @@ struct DevState {
   double mu2_screen;  // its screen / fp32 score
   double target2;     // stop once mu2_cur <= target2 (negative: never)
   double gamma_inc, gamma_dec, delta_min, delta_max;
+  double screen_min_delta;  // screen modes: rank with the tensor-core screen only while
+                            // delta_used >= this; below it, with the fp32 Gram of all K
+  uint32_t use_screen;      // this iteration ranks with the screen
+  uint32_t use_full;        // this iteration ranks with the fp32 Gram of every candidate
   uint32_t t;         // iterations completed
   uint32_t t_stop;    // no iteration starts with t >= t_stop
   uint32_t cstar;     // chosen candidate of the iteration in progress
@@ -38,7 +42,7 @@ struct DevState {
 struct TraceRowDev {
   uint32_t t, cstar;
   double mu2_best, mu2_screen, mu2_cur, delta_used, delta_next;
-  int32_t accepted, reserved;
+  int32_t accepted, flags;  // flags bit 0: ranked by the tensor-core screen
 };
 
 template <typename T> struct Cplx;

@@ -83,10 +83,12 @@ cudaError_t launch_gen_candidate(int N, int d, uint64_t seed, uint32_t t, uint32
 
 // tensor-core screen (tc_screen.cu)
 bool screen_supported(int N, int d);
-cudaError_t launch_screen_bf16(int N, int d, uint64_t seed, const float2* phi32, int K,
-                               uint32_t c0, uint32_t t, double delta, const DevState* st,
-                               unsigned int* mu2_out, uint32_t* err_flag, int num_sms,
-                               cudaStream_t s);
+// fp16 = false: bf16 operands; true: fp16 operands.  With st, runs only when
+// st->active && st->use_screen.
+cudaError_t launch_screen(bool fp16, int N, int d, uint64_t seed, const float2* phi32, int K,
+                          uint32_t c0, uint32_t t, double delta, const DevState* st,
+                          unsigned int* mu2_out, uint32_t* err_flag, int num_sms,
+                          cudaStream_t s);
 
 cudaError_t init_kernel_attributes();
 cudaError_t init_screen_attributes(int optin_smem);

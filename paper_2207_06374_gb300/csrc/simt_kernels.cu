@@ -323,9 +323,14 @@ __global__ void k_iter_begin(DevState* st, void* z0, size_t b0, void* z1, size_t
     st->active = act;
     st->npairs = 0u;
     st->overflow = 0u;
+    st->use_screen = 0u;
+    st->use_full = 0u;
     if (act) {
       st->delta_used = st->delta;
       st->accepted = 0u;
+      const bool scr = st->delta >= st->screen_min_delta;
+      st->use_screen = scr ? 1u : 0u;
+      st->use_full = scr ? 0u : 1u;
     }
   }
   __syncthreads();
@@ -372,7 +377,7 @@ __device__ void apply_rule_and_trace(DevState* st, uint32_t cstar, double mu2_be
     TraceRowDev& r = trace[(t - 1u) % st->trace_cap];
     r.t = t; r.cstar = cstar; r.mu2_best = mu2_best; r.mu2_screen = mu2_screen;
     r.mu2_cur = st->mu2_cur; r.delta_used = dused; r.delta_next = dl;
-    r.accepted = accept ? 1 : 0; r.reserved = 0;
+    r.accepted = accept ? 1 : 0; r.flags = (int32_t)(st->use_screen & 1u);
   }
 }
 

@@ -17,6 +17,7 @@
 // handed over with mbarriers; every wait is bounded in time and gives up by
 // setting an error bit instead of spinning forever.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -121,11 +122,14 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major,
-// M = N = 128; bit 13 negates A.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
-                            ((128u >> 4) << 24);
-constexpr uint32_t kIdescNegA = kIdesc | (1u << 13);
+// Instruction descriptor, kind::f16: D fp32, A and B both bf16 (format 1)
+// or both fp16 (format 0), both K-major, M = N = 128; bit 13 negates A.
+template <bool kHalf> struct Idesc {
+  static constexpr uint32_t fmt = kHalf ? 0u : 1u;
+  static constexpr uint32_t pos = (1u << 4) | (fmt << 7) | (fmt << 10) | ((128u >> 3) << 17) |
+                                  ((128u >> 4) << 24);
+  static constexpr uint32_t neg_a = pos | (1u << 13);
+};
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate) {
@@ -168,9 +172,14 @@ __device__ __forceinline__ void tile_coords_tc(int tau, int& I, int& J) {
   I = tau - j * (j + 1) / 2;
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&v);
+template <bool kHalf> __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  if constexpr (kHalf) {
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+  } else {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+  }
 }
 
 // Column r (0..127) of a block, 16-byte chunk c (0..7) -> byte offset in the
@@ -179,7 +188,8 @@ __device__ __forceinline__ uint32_t swz_offset(int r, int c) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_screen_bf16(const ScreenArgs a) {
+template <bool kHalf>
+__global__ void __launch_bounds__(kThreads, 1) k_screen(const ScreenArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ SmemCtl ctl;
   // 1024-byte aligned operand area
@@ -190,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_screen_bf16(const ScreenArgs a)
   uint32_t t = a.t;
   float delta = a.delta;
   if (a.st) {
-    if (!a.st->active) return;
+    if (!a.st->active || !a.st->use_screen) return;
     t = a.st->t + 1u;
     delta = (float)a.st->delta_used;
   }
@@ -280,14 +290,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_screen_bf16(const ScreenArgs a)
         for (int half = 0; half < 2; ++half) {
           uint4 re, im;
           const int e0 = 8 * half;
-          re.x = pack_bf16(xr[e0 + 0] * inv, xr[e0 + 1] * inv);
-          re.y = pack_bf16(xr[e0 + 2] * inv, xr[e0 + 3] * inv);
-          re.z = pack_bf16(xr[e0 + 4] * inv, xr[e0 + 5] * inv);
-          re.w = pack_bf16(xr[e0 + 6] * inv, xr[e0 + 7] * inv);
-          im.x = pack_bf16(xi[e0 + 0] * inv, xi[e0 + 1] * inv);
-          im.y = pack_bf16(xi[e0 + 2] * inv, xi[e0 + 3] * inv);
-          im.z = pack_bf16(xi[e0 + 4] * inv, xi[e0 + 5] * inv);
-          im.w = pack_bf16(xi[e0 + 6] * inv, xi[e0 + 7] * inv);
+          re.x = pack2<kHalf>(xr[e0 + 0] * inv, xr[e0 + 1] * inv);
+          re.y = pack2<kHalf>(xr[e0 + 2] * inv, xr[e0 + 3] * inv);
+          re.z = pack2<kHalf>(xr[e0 + 4] * inv, xr[e0 + 5] * inv);
+          re.w = pack2<kHalf>(xr[e0 + 6] * inv, xr[e0 + 7] * inv);
+          im.x = pack2<kHalf>(xi[e0 + 0] * inv, xi[e0 + 1] * inv);
+          im.y = pack2<kHalf>(xi[e0 + 2] * inv, xi[e0 + 3] * inv);
+          im.z = pack2<kHalf>(xi[e0 + 4] * inv, xi[e0 + 5] * inv);
+          im.w = pack2<kHalf>(xi[e0 + 6] * inv, xi[e0 + 7] * inv);
           // real parts of entries 16h + 8half .. +7 -> chunk 2h + half;
           // imaginary parts -> chunk 4 + 2h + half
           *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * h + half)) = re;
@@ -369,13 +379,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_screen_bf16(const ScreenArgs a)
             // Re: sum over the whole K = 2*DP (4 steps of 16)
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-              mma_bf16(dre, smem_desc_sw128(aI + 32u * kk), smem_desc_sw128(bJ + 32u * kk), kIdesc,
+              mma_bf16(dre, smem_desc_sw128(aI + 32u * kk), smem_desc_sw128(bJ + 32u * kk), Idesc<kHalf>::pos,
                        kk > 0 ? 1u : 0u);
             // Im: A_I^T B_J (K slices 0,1 against 2,3) - B_I^T A_J (2,3 against 0,1)
-            mma_bf16(dim, smem_desc_sw128(aI + 0u), smem_desc_sw128(bJ + 64u), kIdesc, 0u);
-            mma_bf16(dim, smem_desc_sw128(aI + 32u), smem_desc_sw128(bJ + 96u), kIdesc, 1u);
-            mma_bf16(dim, smem_desc_sw128(aI + 64u), smem_desc_sw128(bJ + 0u), kIdescNegA, 1u);
-            mma_bf16(dim, smem_desc_sw128(aI + 96u), smem_desc_sw128(bJ + 32u), kIdescNegA, 1u);
+            mma_bf16(dim, smem_desc_sw128(aI + 0u), smem_desc_sw128(bJ + 64u), Idesc<kHalf>::pos, 0u);
+            mma_bf16(dim, smem_desc_sw128(aI + 32u), smem_desc_sw128(bJ + 96u), Idesc<kHalf>::pos, 1u);
+            mma_bf16(dim, smem_desc_sw128(aI + 64u), smem_desc_sw128(bJ + 0u), Idesc<kHalf>::neg_a, 1u);
+            mma_bf16(dim, smem_desc_sw128(aI + 96u), smem_desc_sw128(bJ + 32u), Idesc<kHalf>::neg_a, 1u);
             mma_commit(&ctl.acc_full[buf]);
             if (J == nb - 1) mma_commit(&ctl.blk_empty[I]);   // last use of block I
           }
@@ -409,17 +419,22 @@ bool screen_supported(int N, int d) {
 
 cudaError_t init_screen_attributes(int optin) {
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, k_screen_bf16);
-  if (e != cudaSuccess) return e;
   const int want = (int)screen_smem_bytes(kMaxBlocks);
-  const int allowed = std::min(want, optin - (int)fa.sharedSizeBytes);
-  return cudaFuncSetAttribute(k_screen_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, allowed);
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_screen<false>);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_screen<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           std::min(want, optin - (int)fa.sharedSizeBytes));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncGetAttributes(&fa, k_screen<true>);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_screen<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              std::min(want, optin - (int)fa.sharedSizeBytes));
 }
 
-cudaError_t launch_screen_bf16(int N, int d, uint64_t seed, const float2* phi32, int K,
-                               uint32_t c0, uint32_t t, double delta, const DevState* st,
-                               unsigned int* mu2_out, uint32_t* err_flag, int num_sms,
-                               cudaStream_t s) {
+cudaError_t launch_screen(bool fp16, int N, int d, uint64_t seed, const float2* phi32, int K,
+                          uint32_t c0, uint32_t t, double delta, const DevState* st,
+                          unsigned int* mu2_out, uint32_t* err_flag, int num_sms,
+                          cudaStream_t s) {
   if (!screen_supported(N, d) || K < 1) return cudaErrorInvalidValue;
   ScreenArgs a;
   a.N = N; a.d = d;
@@ -430,7 +445,8 @@ cudaError_t launch_screen_bf16(int N, int d, uint64_t seed, const float2* phi32,
   const int grid = std::min(K, num_sms);
   // the operand area is always reserved for the largest block count, so every
   // descriptor address lies inside the CTA's shared memory
-  k_screen_bf16<<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(a);
+  if (fp16) k_screen<true><<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(a);
+  else k_screen<false><<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -18,8 +18,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtrstmi.so")
 TRSTMI_OK, TRSTMI_PENDING = 0, 1
 TRSTMI_EINVAL, TRSTMI_ENOMEM, TRSTMI_ECUDA, TRSTMI_ETIMEOUT = -1, -2, -3, -4
 TRSTMI_ECANCELLED, TRSTMI_EBUSY, TRSTMI_EUNSUPPORTED, TRSTMI_ENOTFOUND = -5, -6, -7, -8
-FP64, FP32, BF16_SCREEN = 0, 1, 2
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16_SCREEN}
+FP64, FP32, BF16_SCREEN, FP16_SCREEN = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16_SCREEN, "fp16": FP16_SCREEN}
 
 
 class TrstmiError(RuntimeError):
@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
                 ("trace_cap", ctypes.c_int32), ("delta0", ctypes.c_double),
                 ("gamma_inc", ctypes.c_double), ("gamma_dec", ctypes.c_double),
                 ("delta_min", ctypes.c_double), ("delta_max", ctypes.c_double),
-                ("target_mu", ctypes.c_double), ("stream", ctypes.c_void_p),
+                ("target_mu", ctypes.c_double), ("screen_min_delta", ctypes.c_double),
+                ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
@@ -43,12 +44,12 @@ class TraceRow(ctypes.Structure):
                 ("mu2_best", ctypes.c_double), ("mu2_screen", ctypes.c_double),
                 ("mu2_cur", ctypes.c_double), ("delta_used", ctypes.c_double),
                 ("delta_next", ctypes.c_double), ("accepted", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32)]
 
 
 TRACE_DTYPE = np.dtype([("t", "<u4"), ("cstar", "<u4"), ("mu2_best", "<f8"),
                         ("mu2_screen", "<f8"), ("mu2_cur", "<f8"), ("delta_used", "<f8"),
-                        ("delta_next", "<f8"), ("accepted", "<i4"), ("reserved", "<i4")])
+                        ("delta_next", "<f8"), ("accepted", "<i4"), ("flags", "<i4")])
 assert TRACE_DTYPE.itemsize == ctypes.sizeof(TraceRow)
 
 

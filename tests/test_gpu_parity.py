@@ -273,4 +273,34 @@ def test_bf16_mode_reaches_tetrahedral_code():
     with T.Search(4, 2, 1, K=256, precision="bf16") as s:
         s.step(2000)
         mu, w = s.coherence()
+        tr = s.trace()
     assert abs(mu - np.sqrt(om2)) < 1e-5 and abs(mu - w) < 1e-5
+    # the screen ranked the iterations with delta >= screen_min_delta
+    assert np.array_equal(tr["flags"] & 1, (tr["delta_used"] >= 0.01).astype(np.int32))
+
+
+@pytest.mark.parametrize("d,N,K", [(32, 1024, 4), (7, 129, 16), (2, 4, 64), (16, 1536, 3)])
+def test_fp16_screen_scores_match_oracle(d, N, K):
+    """fp16 screen within 1e-3 of the oracle's mu (2^-11 input rounding)."""
+    seed = 98
+    with T.Search(N, d, seed, K=K, precision="fp32") as s:
+        phi0 = s.get_phi()
+        ref = O.score(phi0, seed, 0.1, 2, 5, K, nthreads=4)
+        g16 = s.score(2, 5, K, 0.1, "fp16")
+        assert np.max(np.abs(np.sqrt(g16) - np.sqrt(ref))) < 1e-3
+
+
+def test_screen_gate_by_radius():
+    """screen_min_delta = 0: every iteration screened; huge: none screened
+    (fp32 Gram of all candidates); decisions replay in binary64 either way."""
+    d, N, K, iters, seed = 6, 50, 64, 12, 3
+    for smd, expect in ((0.0, 1), (1e9, 0)):
+        with T.Search(N, d, seed, K=K, precision="fp16", screen_min_delta=smd) as s:
+            phi0 = s.get_phi()
+            s.step(iters)
+            tr = s.trace()
+        assert np.all((tr["flags"] & 1) == expect)
+        rphi, rm2, _, rtr = O.replay(phi0, seed, O.make_opts(K=K, T=iters), 0.1, O.mu2(phi0), 0,
+                                     tr["cstar"])
+        assert np.array_equal(tr["accepted"], rtr["accepted"])
+        assert np.allclose(tr["mu2_best"], rtr["mu2_best"], rtol=1e-12, atol=0)
