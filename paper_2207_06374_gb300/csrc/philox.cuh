@@ -25,11 +25,14 @@ __device__ __forceinline__ PhiloxOut philox4x32_10(uint32_t c0, uint32_t c1, uin
   constexpr uint32_t kBumpA = 0x9E3779B9u, kBumpB = 0xBB67AE85u;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hiA = __umulhi(kMulA, c0), loA = kMulA * c0;
-    const uint32_t hiB = __umulhi(kMulB, c2), loB = kMulB * c2;
-    const uint32_t n0 = hiB ^ c1 ^ k0;
-    const uint32_t n2 = hiA ^ c3 ^ k1;
-    c0 = n0; c1 = loB; c2 = n2; c3 = loA;
+    // one 32x32 -> 64-bit product per multiplier gives both halves
+    const uint64_t pA = (uint64_t)kMulA * (uint64_t)c0;
+    const uint64_t pB = (uint64_t)kMulB * (uint64_t)c2;
+    const uint32_t n0 = (uint32_t)(pB >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = (uint32_t)(pA >> 32) ^ c3 ^ k1;
+    c1 = (uint32_t)pB;
+    c3 = (uint32_t)pA;
+    c0 = n0; c2 = n2;
     k0 += kBumpA; k1 += kBumpB;
   }
   PhiloxOut o;
@@ -76,6 +79,28 @@ __device__ __forceinline__ void cn_from_u32_fast(uint32_t ua, uint32_t ub, float
   __sincosf(th, &s, &c);
   re = -r * c;
   im = -r * s;
+}
+
+// Screen form of one perturbed entry: returns phi + delta * Z for the pair of
+// words (ua, ub), with Z as in cn_from_u32_fast but cheaper: Ua by one
+// conversion, the angle fraction Ub from the top 23 bits of ub placed in a
+// float mantissa (f in [1, 2), Ub = f - 1, resolution 2^-23), and
+// approximate lg2 / sqrt / sin / cos.
+__device__ __forceinline__ void perturb_fast(uint32_t ua, uint32_t ub, float delta, float vr,
+                                             float vi, float& xr, float& xi) {
+  const float Ua = __fmaf_rn(__uint2float_rn(ua), 0x1.0p-32f, 0x1.0p-33f);
+  float l2, r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(Ua));
+  const float e = fmaxf(l2 * -0.69314718055994531f, 0.0f);  // -ln Ua
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e));
+  const float f = __int_as_float(0x3f800000u | (ub >> 9));
+  // 2 pi Ub - pi = 2 pi f - 3 pi, in [-pi, pi); cos/sin(2 pi Ub) = -cos/sin of it
+  const float th = __fmaf_rn(f, 6.28318530717958648f, -9.42477796076937972f);
+  float s, c;
+  __sincosf(th, &s, &c);
+  const float dr = delta * r;
+  xr = __fmaf_rn(-dr, c, vr);
+  xi = __fmaf_rn(-dr, s, vi);
 }
 
 __device__ __forceinline__ uint32_t seed_lo(uint64_t s) { return (uint32_t)(s & 0xffffffffull); }

@@ -78,6 +78,51 @@ __device__ bool gen_column(const typename Cplx<T>::type* phi, int d, int j,
   return true;
 }
 
+// Warp-cooperative form of gen_column for an interleaved column in global
+// memory: lane l draws the entry pairs p = l, l + 32, ...; the squared norm
+// is reduced across the warp.  All 32 lanes must call it.
+template <typename T>
+__device__ bool gen_column_warp(const typename Cplx<T>::type* phi, int d, int j, uint64_t seed,
+                                uint32_t c, uint32_t t, uint32_t tag, T delta,
+                                typename Cplx<T>::type* out, int lane) {
+  const uint32_t k0 = seed_lo(seed), k1 = seed_hi(seed);
+  const int P = (d + 1) >> 1;
+  const typename Cplx<T>::type* col = phi ? phi + (size_t)j * d : nullptr;
+  typename Cplx<T>::type* o = out + (size_t)j * d;
+  T s = T(0);
+  for (int p = lane; p < P; p += 32) {
+    const PhiloxOut u = philox4x32_10((uint32_t)j * (uint32_t)P + (uint32_t)p, c, t, tag, k0, k1);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * p + h;
+      if (i < d) {
+        T zr, zi;
+        cn_draw<T>(u.x[2 * h], u.x[2 * h + 1], zr, zi);
+        T xr = zr, xi = zi;
+        if (col) {
+          const auto v = col[i];
+          xr = add_rn(v.x, mul_rn(delta, zr));
+          xi = add_rn(v.y, mul_rn(delta, zi));
+        }
+        o[i].x = xr;
+        o[i].y = xi;
+        s = add_rn(s, add_rn(mul_rn(xr, xr), mul_rn(xi, xi)));
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (!(s > T(0))) return false;
+  const T nrm = sqrt_rn(s);
+  for (int p = lane; p < P; p += 32)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * p + h;
+      if (i < d) { o[i].x = div_rn(o[i].x, nrm); o[i].y = div_rn(o[i].y, nrm); }
+    }
+  return true;
+}
+
 // Column j of a stored frame, optionally renormalised.
 template <typename T>
 __device__ bool load_column(const typename Cplx<T>::type* __restrict__ frame, int d, int j,
@@ -498,17 +543,19 @@ __global__ void k_materialize64(int N, int d, uint64_t seed, DevState* st,
     const unsigned int v = mu2_top[s];
     if (v < bv || (v == bv && topk[s] < bc)) { bv = v; bc = topk[s]; }
   }
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j == 0) {
+  // one warp per column
+  const int lane = threadIdx.x & 31;
+  const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->cstar = bc;
     st->mu2_screen = (double)__uint_as_float(bv);
   }
   if (j >= N) return;
-  double* base = reinterpret_cast<double*>(cand64 + (size_t)j * d);
-  const bool ok = gen_column<double>(phi64, d, j, seed, bc, st->t + 1u, 0u, st->delta_used,
-                                     base, base + 1, 2);
-  if (!ok) atomicOr(&st->error, (uint32_t)kErrZeroColumn);
-  for (int i = 0; i < d; ++i) {
+  const bool ok = gen_column_warp<double>(phi64, d, j, seed, bc, st->t + 1u, 0u, st->delta_used,
+                                          cand64, lane);
+  if (!ok && lane == 0) atomicOr(&st->error, (uint32_t)kErrZeroColumn);
+  __syncwarp();
+  for (int i = lane; i < d; i += 32) {
     const double2 v = cand64[(size_t)j * d + i];
     cand32[(size_t)j * d + i] = make_float2((float)v.x, (float)v.y);
   }
@@ -518,8 +565,9 @@ cudaError_t launch_materialize64(int N, int d, uint64_t seed, DevState* st,
                                  const uint32_t* topk, const unsigned int* mu2_top, int k,
                                  const double2* phi64, double2* cand64, float2* cand32,
                                  cudaStream_t s) {
-  k_materialize64<<<(N + 127) / 128, 128, 0, s>>>(N, d, seed, st, topk, mu2_top, k, phi64,
-                                                   cand64, cand32);
+  const size_t threads = (size_t)N * 32;
+  k_materialize64<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(N, d, seed, st, topk, mu2_top,
+                                                                   k, phi64, cand64, cand32);
   return cudaGetLastError();
 }
 
@@ -588,20 +636,32 @@ cudaError_t launch_commit_copy(int N, int d, DevState* st, const double2* cand64
 
 __global__ void k_normalize64(int N, int d, const double2* in, double2* out64, float2* out32,
                               DevState* st) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per column; in and out64 may alias
+  const int lane = threadIdx.x & 31;
+  const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (j >= N) return;
-  double* base = reinterpret_cast<double*>(out64 + (size_t)j * d);
-  const bool ok = load_column<double>(in, d, j, true, base, base + 1, 2);
-  if (!ok && st) atomicOr(&st->error, (uint32_t)kErrZeroColumn);
-  for (int i = 0; i < d; ++i) {
-    const double2 v = out64[(size_t)j * d + i];
-    out32[(size_t)j * d + i] = make_float2((float)v.x, (float)v.y);
+  const double2* col = in + (size_t)j * d;
+  double s = 0.0;
+  for (int i = lane; i < d; i += 32) s += col[i].x * col[i].x + col[i].y * col[i].y;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (!(s > 0.0)) {
+    if (st && lane == 0) atomicOr(&st->error, (uint32_t)kErrZeroColumn);
+    return;
+  }
+  const double nrm = sqrt(s);
+  for (int i = lane; i < d; i += 32) {
+    const double2 v = col[i];
+    const double2 w = make_double2(v.x / nrm, v.y / nrm);
+    out64[(size_t)j * d + i] = w;
+    out32[(size_t)j * d + i] = make_float2((float)w.x, (float)w.y);
   }
 }
 
 cudaError_t launch_normalize64(int N, int d, const double2* in, double2* out64, float2* out32,
                                DevState* st, cudaStream_t s) {
-  k_normalize64<<<(N + 127) / 128, 128, 0, s>>>(N, d, in, out64, out32, st);
+  const size_t threads = (size_t)N * 32;
+  k_normalize64<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(N, d, in, out64, out32, st);
   return cudaGetLastError();
 }
 

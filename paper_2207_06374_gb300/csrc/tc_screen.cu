@@ -182,6 +182,12 @@ template <bool kHalf> __device__ __forceinline__ uint32_t pack2(float lo, float 
   }
 }
 
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
 // Column r (0..127) of a block, 16-byte chunk c (0..7) -> byte offset in the
 // block: 8-row atoms of 1024 B, chunk index XOR-swizzled by the row.
 __device__ __forceinline__ uint32_t swz_offset(int r, int c) {
@@ -252,7 +258,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_screen(const ScreenArgs a) {
         const int j = b * kBlockCols + r;
         float xr[16], xi[16];
         float s = 0.f;
-        if (j < a.N) {
+        if (j < a.N && d == kDP) {
+          // full width: entries 16h .. 16h+15 are 128 contiguous bytes of phi
+          const float4* col4 = reinterpret_cast<const float4*>(a.phi + (size_t)j * kDP + 16 * h);
+          float4 v[8];
+#pragma unroll
+          for (int pp = 0; pp < 8; ++pp) v[pp] = __ldg(col4 + pp);
+#pragma unroll
+          for (int pp = 0; pp < 8; ++pp) {
+            const uint32_t p = (uint32_t)(8 * h + pp);
+            const PhiloxOut u = philox4x32_10((uint32_t)j * (uint32_t)(kDP / 2) + p, cand, t, 0u,
+                                              k0, k1);
+            perturb_fast(u.x[0], u.x[1], delta, v[pp].x, v[pp].y, xr[2 * pp], xi[2 * pp]);
+            perturb_fast(u.x[2], u.x[3], delta, v[pp].z, v[pp].w, xr[2 * pp + 1], xi[2 * pp + 1]);
+          }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) s = fmaf(xr[e], xr[e], fmaf(xi[e], xi[e], s));
+        } else if (j < a.N) {
           const float2* col = a.phi + (size_t)j * d;
 #pragma unroll
           for (int pp = 0; pp < 8; ++pp) {
@@ -263,12 +285,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_screen(const ScreenArgs a) {
 #pragma unroll
               for (int e = 0; e < 2; ++e) {
                 const int i = 2 * p + e;
-                float zr = 0.f, zi = 0.f, vr = 0.f, vi = 0.f;
+                float vr = 0.f, vi = 0.f;
                 if (i < d) {
-                  cn_from_u32_fast(u.x[2 * e], u.x[2 * e + 1], zr, zi);
                   const float2 v = col[i];
-                  vr = fmaf(delta, zr, v.x);
-                  vi = fmaf(delta, zi, v.y);
+                  perturb_fast(u.x[2 * e], u.x[2 * e + 1], delta, v.x, v.y, vr, vi);
                 }
                 xr[2 * pp + e] = vr;
                 xi[2 * pp + e] = vi;
@@ -333,10 +353,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_screen(const ScreenArgs a) {
           tmem_ld32(base + 128u + 32u * ch, im);
           tmem_ld_wait();
           if (I != J) {
+            // two pairs per packed multiply / fma, one three-input max
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const float x = __uint_as_float(re[e]), y = __uint_as_float(im[e]);
-              m = fmaxf(m, fmaf(x, x, y * y));
+            for (int e = 0; e < 32; e += 2) {
+              const float2 x = make_float2(__uint_as_float(re[e]), __uint_as_float(re[e + 1]));
+              const float2 y = make_float2(__uint_as_float(im[e]), __uint_as_float(im[e + 1]));
+              const float2 v = __ffma2_rn(y, y, __fmul2_rn(x, x));
+              m = fmax3(m, v.x, v.y);
             }
           } else {
 #pragma unroll
