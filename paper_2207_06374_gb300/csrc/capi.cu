@@ -148,6 +148,8 @@ __global__ void k_set_mu2cur(DevState* st, const unsigned int* b32, const unsign
 __global__ void k_set_stop(DevState* st, uint32_t iters) {
   const unsigned long long stop = (unsigned long long)st->t + iters;
   st->t_stop = stop > 0xffffffffull ? 0xffffffffu : (uint32_t)stop;
+  st->t_call = st->t;
+  st->accepts_call = st->accepts;
 }
 
 // Score the current frame in the deciding precision into st->mu2_cur.
@@ -444,26 +446,20 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
 int trstmi_step(trstmi_handle h, int iters, trstmi_step_info* info) {
   if (!h || iters < 0) return TRSTMI_EINVAL;
   TRY_CUDA(cudaSetDevice(h->opt.device));
-  DevState before;
-  int rc = read_state(h, &before);
-  if (rc) return rc;
   cudaStream_t s = h->stream;
+  // graphs are captured (host work only) before the timed span starts
+  const int full = iters / kGraphChunk, rem = iters % kGraphChunk;
+  cudaGraphExec_t g_full = nullptr, g_rem = nullptr;
+  int rc = TRSTMI_OK;
+  if (full > 0 && (rc = get_graph(h, kGraphChunk, &g_full)) != TRSTMI_OK) return rc;
+  if (rem > 0 && (rc = get_graph(h, rem, &g_rem)) != TRSTMI_OK) return rc;
+  // no host synchronisation until the end: the start counters are snapshot
+  // on the device by the first kernel
   TRY_CUDA(cudaEventRecord(h->ev0, s));
   k_set_stop<<<1, 1, 0, s>>>(h->st, (uint32_t)iters);
   TRY_CUDA(cudaGetLastError());
-  const int full = iters / kGraphChunk, rem = iters % kGraphChunk;
-  if (full > 0) {
-    cudaGraphExec_t g;
-    rc = get_graph(h, kGraphChunk, &g);
-    if (rc) return rc;
-    for (int r = 0; r < full; ++r) TRY_CUDA(cudaGraphLaunch(g, s));
-  }
-  if (rem > 0) {
-    cudaGraphExec_t g;
-    rc = get_graph(h, rem, &g);
-    if (rc) return rc;
-    TRY_CUDA(cudaGraphLaunch(g, s));
-  }
+  for (int r = 0; r < full; ++r) TRY_CUDA(cudaGraphLaunch(g_full, s));
+  if (g_rem) TRY_CUDA(cudaGraphLaunch(g_rem, s));
   TRY_CUDA(cudaEventRecord(h->ev1, s));
   DevState after;
   rc = read_state(h, &after);
@@ -471,8 +467,8 @@ int trstmi_step(trstmi_handle h, int iters, trstmi_step_info* info) {
   if (info) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-    info->iters_done = (int32_t)(after.t - before.t);
-    info->accepts = (int32_t)(after.accepts - before.accepts);
+    info->iters_done = (int32_t)(after.t - after.t_call);
+    info->accepts = (int32_t)(after.accepts - after.accepts_call);
     info->mu = std::sqrt(after.mu2_cur);
     info->delta = after.delta;
     info->pairs_scored = (uint64_t)info->iters_done * (uint64_t)h->opt.K *
@@ -649,7 +645,7 @@ int trstmi_score(trstmi_handle h, uint32_t t, uint32_t c0, int count, double del
         e = launch_screen(precision == TRSTMI_FP16_SCREEN, h->N, h->d, h->seed, h->phi32, count,
                           c0, t, delta, nullptr, (unsigned int*)tmp, &h->misc[1], h->num_sms, s);
       }
-      if (e != cudaSuccess) { rc = TRSTMI_ECUDA; break; }
+      if (e != cudaSuccess) { rc = record_cuda_error(e, "score kernel launch", __LINE__); break; }
       std::vector<unsigned int> b(count);
       if (cudaMemcpyAsync(b.data(), tmp, (size_t)count * sizeof(unsigned int),
                           cudaMemcpyDeviceToHost, s) ||
@@ -760,7 +756,7 @@ int trstmi_profile_score(trstmi_handle h, int precision, int launches, double de
                         (uint32_t)(l + 1), delta, nullptr, h->mu2_k32, &h->misc[1], h->num_sms, s);
     }
     cudaEventRecord(ev[2 * l + 1], s);
-    if (e != cudaSuccess) rc = TRSTMI_ECUDA;
+    if (e != cudaSuccess) rc = record_cuda_error(e, "profiled kernel launch", __LINE__);
   }
   if (rc == TRSTMI_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = TRSTMI_ECUDA;
   double total = 0.0;

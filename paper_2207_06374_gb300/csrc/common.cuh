@@ -36,6 +36,8 @@ struct DevState {
   uint32_t npairs;    // certification pair list fill
   uint32_t overflow;  // certification pair list overflowed -> full binary64 pass
   uint32_t trace_cap;
+  uint32_t t_call;        // t when the current trstmi_step call started
+  uint32_t accepts_call;  // accepts when the current trstmi_step call started
   uint32_t pad0;
 };
 

@@ -40,6 +40,39 @@ __device__ __forceinline__ PhiloxOut philox4x32_10(uint32_t c0, uint32_t c1, uin
   return o;
 }
 
+// The ten round keys of one seed, (k0 + r W0, k1 + r W1), r = 0..9.
+struct PhiloxKeys { uint32_t k0[10], k1[10]; };
+
+__host__ __device__ inline PhiloxKeys philox_round_keys(uint64_t seed) {
+  PhiloxKeys k;
+  uint32_t a = (uint32_t)(seed & 0xffffffffull), b = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    k.k0[r] = a; k.k1[r] = b;
+    a += 0x9E3779B9u; b += 0xBB67AE85u;
+  }
+  return k;
+}
+
+// Same generator with the round keys given (e.g. from kernel parameters,
+// which the instructions can read directly).
+__device__ __forceinline__ PhiloxOut philox4x32_10_keys(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                        uint32_t c3, const PhiloxKeys& k) {
+  constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t pA = (uint64_t)kMulA * (uint64_t)c0;
+    const uint64_t pB = (uint64_t)kMulB * (uint64_t)c2;
+    const uint32_t n0 = (uint32_t)(pB >> 32) ^ c1 ^ k.k0[r];
+    const uint32_t n2 = (uint32_t)(pA >> 32) ^ c3 ^ k.k1[r];
+    c1 = (uint32_t)pB;
+    c3 = (uint32_t)pA;
+    c0 = n0; c2 = n2;
+  }
+  PhiloxOut o;
+  o.x[0] = c0; o.x[1] = c1; o.x[2] = c2; o.x[3] = c3;
+  return o;
+}
+
 // --- uniform -> complex normal, three precisions -------------------------
 
 // Double precision: U = (u + 0.5) * 2^-32 is exact in binary64.

@@ -31,16 +31,17 @@ constexpr int kDP = 32;                 // padded d: K = 2*kDP = 64 bf16 = 128 b
 constexpr int kBlockCols = 128;         // columns per block = MMA M = N
 constexpr int kBlockBytes = kBlockCols * 2 * kDP * 2;   // 16 KiB
 constexpr int kMaxBlocks = 12;          // N <= 1536
-constexpr int kGenWarps = 8, kEpiWarps = 4;
-constexpr int kEpiWarp0 = kGenWarps;                   // warps 8..11: a whole warpgroup
-constexpr int kMmaWarp = kGenWarps + kEpiWarps;        // warp 12
-constexpr int kThreads = 32 * (kMmaWarp + 1);          // 416
+constexpr int kGenWarps = 8, kEpiWarps = 8;
+constexpr int kEpiWarp0 = kGenWarps;                   // warps 8..15: two whole warpgroups
+constexpr int kMmaWarp = kGenWarps + kEpiWarps;        // warp 16
+constexpr int kThreads = 32 * (kMmaWarp + 1);          // 544
 constexpr uint32_t kTmemCols = 512;                    // 2 buffers x (128 Re + 128 Im)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
 struct ScreenArgs {
   int N, d, nb, ntiles, K;
   uint64_t seed;
+  PhiloxKeys keys;  // round keys of the seed, read straight from the parameter bank
   const float2* phi;
   uint32_t c0, t;
   float delta;
@@ -57,6 +58,11 @@ struct SmemCtl {
   unsigned long long drain;
   uint32_t tmem_base;
   volatile int abort_flag;
+  // Decision of a group's elected waiter for one barrier episode, read by the
+  // whole group after the named barrier.  Two slots alternate: slot e & 1 is
+  // rewritten only after every member has passed barrier e + 1, i.e. after
+  // it has read slot e & 1, so all members always act on the same value.
+  int gen_go[2], epi_go[2];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -73,23 +79,29 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
 
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, uint32_t parity) {
   uint32_t ok;
+  // the thread may sleep in hardware up to the hint (ns) while the phase is
+  // pending, so waiting warps do not take issue slots from working ones
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
+      : "r"(smem_u32(b)), "r"(parity), "r"(1000000u)
       : "memory");
   return ok != 0;
 }
 
 // Bounded wait: false (and the CTA-wide abort flag and the error bit set) if
 // the phase does not complete within kWaitLimitNs or another role aborted.
-__device__ bool mbar_wait(unsigned long long* b, uint32_t parity, SmemCtl* ctl, uint32_t* err) {
+// Between unsuccessful polls the thread sleeps backoff_ns, so a waiting warp
+// leaves the issue slots to the working ones.
+__device__ bool mbar_wait(unsigned long long* b, uint32_t parity, SmemCtl* ctl, uint32_t* err,
+                          unsigned backoff_ns = 0) {
   if (mbar_try_wait(b, parity)) return true;
   const unsigned long long t0 = globaltimer_ns();
   for (uint32_t it = 1;; ++it) {
+    if (backoff_ns) __nanosleep(backoff_ns);
     if (mbar_try_wait(b, parity)) return true;
-    if ((it & 63u) == 0u) {
+    if ((it & 7u) == 0u) {
       if (ctl->abort_flag) return false;
       if (globaltimer_ns() - t0 > kWaitLimitNs) {
         ctl->abort_flag = 1;
@@ -99,6 +111,12 @@ __device__ bool mbar_wait(unsigned long long* b, uint32_t parity, SmemCtl* ctl, 
     }
   }
 }
+
+// Hardware named barrier over a role group: blocked warps issue nothing.
+__device__ __forceinline__ void group_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+constexpr int kBarGen = 1, kBarEpi = 2;
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -164,14 +182,6 @@ __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tile_coords_tc(int tau, int& I, int& J) {
-  int j = (int)((sqrtf(8.0f * (float)tau + 1.0f) - 1.0f) * 0.5f);
-  while ((j + 1) * (j + 2) / 2 <= tau) ++j;
-  while (j * (j + 1) / 2 > tau) --j;
-  J = j;
-  I = tau - j * (j + 1) / 2;
-}
-
 template <bool kHalf> __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   if constexpr (kHalf) {
     __half2 v = __floats2half2_rn(lo, hi);
@@ -195,7 +205,9 @@ __device__ __forceinline__ uint32_t swz_offset(int r, int c) {
 }
 
 template <bool kHalf>
-__global__ void __launch_bounds__(kThreads, 1) k_screen(const ScreenArgs a) {
+// 17 warps: one SM sub-partition (16K registers) holds 5 of them, so a
+// thread may use at most 16384 / (5 * 32) -> 96 registers
+__global__ void __maxnreg__(96) k_screen(const ScreenArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ SmemCtl ctl;
   // 1024-byte aligned operand area
@@ -244,16 +256,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_screen(const ScreenArgs a) {
     const int g = threadIdx.x;            // 0..255
     const int r = g >> 1, h = g & 1;      // column within the block, half of the entries
     const int d = a.d, P = (d + 1) >> 1;
-    const uint32_t k0 = seed_lo(a.seed), k1 = seed_hi(a.seed);
     int q = 0;
     for (int c = blockIdx.x; c < a.K; c += gridDim.x, ++q) {
       const uint32_t cand = a.c0 + (uint32_t)c;
       for (int b = 0; b < nb; ++b) {
         if (q > 0) {
-          bool ok = true;
-          if (lane == 0) ok = mbar_wait(&ctl.blk_empty[b], (uint32_t)((q - 1) & 1), &ctl, a.err);
-          ok = __shfl_sync(0xffffffffu, ok, 0);
-          if (!ok) goto gen_done;
+          // one thread polls; the other generator warps block in hardware
+          const int slot = (q * nb + b) & 1;
+          if (g == 0)
+            ctl.gen_go[slot] =
+                mbar_wait(&ctl.blk_empty[b], (uint32_t)((q - 1) & 1), &ctl, a.err, 64) ? 1 : 0;
+          group_sync(kBarGen, 32 * kGenWarps);
+          if (!ctl.gen_go[slot]) goto gen_done;
         }
         const int j = b * kBlockCols + r;
         float xr[16], xi[16];
@@ -267,8 +281,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_screen(const ScreenArgs a) {
 #pragma unroll
           for (int pp = 0; pp < 8; ++pp) {
             const uint32_t p = (uint32_t)(8 * h + pp);
-            const PhiloxOut u = philox4x32_10((uint32_t)j * (uint32_t)(kDP / 2) + p, cand, t, 0u,
-                                              k0, k1);
+            const PhiloxOut u =
+                philox4x32_10_keys((uint32_t)j * (uint32_t)(kDP / 2) + p, cand, t, 0u, a.keys);
             perturb_fast(u.x[0], u.x[1], delta, v[pp].x, v[pp].y, xr[2 * pp], xi[2 * pp]);
             perturb_fast(u.x[2], u.x[3], delta, v[pp].z, v[pp].w, xr[2 * pp + 1], xi[2 * pp + 1]);
           }
@@ -280,8 +294,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_screen(const ScreenArgs a) {
           for (int pp = 0; pp < 8; ++pp) {
             const int p = 8 * h + pp;
             if (p < P) {
-              const PhiloxOut u = philox4x32_10((uint32_t)j * (uint32_t)P + (uint32_t)p, cand, t,
-                                                0u, k0, k1);
+              const PhiloxOut u =
+                  philox4x32_10_keys((uint32_t)j * (uint32_t)P + (uint32_t)p, cand, t, 0u, a.keys);
 #pragma unroll
               for (int e = 0; e < 2; ++e) {
                 const int i = 2 * p + e;
@@ -331,42 +345,69 @@ __global__ void __launch_bounds__(kThreads, 1) k_screen(const ScreenArgs a) {
   gen_done:;
   } else if (warp < kMmaWarp) {
     // --------------------------------------------------------- epilogue
-    const int qw = warp - kEpiWarp0;                 // TMEM lane quarter
-    const int row = 32 * qw + lane;                  // accumulator row = column j within block I
+    // warps 8..11 take accumulator columns 0..63 of every tile, warps 12..15
+    // columns 64..127; within a warpgroup, warp w reads TMEM lanes 32(w%4)..
+    const int ew = warp - kEpiWarp0;
+    const int qw = ew & 3;                           // TMEM lane quarter
+    const int colh = 64 * (ew >> 2);                 // first accumulator column of this warp
     uint32_t gt = 0;                                 // tile counter
     for (int c = blockIdx.x; c < a.K; c += gridDim.x) {
-      float m = 0.f;
+      // four independent running maxima keep the max chain off the critical path
+      float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
       bool ok = true;
-      for (int tau = 0; tau < ntiles; ++tau, ++gt) {
-        int I, J;
-        tile_coords_tc(tau, I, J);
+      // tiles in the MMA issuer's row-major order: I = 0..nb-1, J = I..nb-1
+      int I = 0, J = 0;
+      for (int tau = 0; tau < ntiles; ++tau, ++gt, J = (J + 1 < nb) ? J + 1 : ++I) {
         const uint32_t buf = gt & 1u, use = gt >> 1;
-        if (lane == 0) ok = mbar_wait(&ctl.acc_full[buf], use & 1u, &ctl, a.err);
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) break;
+        // one thread polls; the other epilogue warps block in hardware
+        if (ew == 0 && lane == 0)
+          ctl.epi_go[gt & 1u] = mbar_wait(&ctl.acc_full[buf], use & 1u, &ctl, a.err, 32) ? 1 : 0;
+        group_sync(kBarEpi, 32 * kEpiWarps);
+        if (!ctl.epi_go[gt & 1u]) { ok = false; break; }
         tc_fence_after();
-        const uint32_t base = tmem + ((uint32_t)(32 * qw) << 16) + buf * 256u;
+        const uint32_t base = tmem + ((uint32_t)(32 * qw) << 16) + buf * 256u + (uint32_t)colh;
 #pragma unroll 1
-        for (int ch = 0; ch < 4; ++ch) {
+        for (int ch = 0; ch < 2; ++ch) {
+          // On a diagonal tile only k > j counts: this warp's rows are
+          // 32qw..32qw+31 and the chunk's columns n0..n0+31, so the chunk is
+          // entirely below the diagonal (skip), entirely above (no mask) or
+          // straddles it (n0 == 32qw: mask column e against row lane).
+          const int n0 = colh + 32 * ch;
+          const bool diag = (I == J);
+          if (diag && n0 < 32 * qw) continue;
           uint32_t re[32], im[32];
           tmem_ld32(base + 32u * ch, re);
           tmem_ld32(base + 128u + 32u * ch, im);
           tmem_ld_wait();
-          if (I != J) {
+          if (!diag || n0 > 32 * qw) {
             // two pairs per packed multiply / fma, one three-input max
 #pragma unroll
-            for (int e = 0; e < 32; e += 2) {
-              const float2 x = make_float2(__uint_as_float(re[e]), __uint_as_float(re[e + 1]));
-              const float2 y = make_float2(__uint_as_float(im[e]), __uint_as_float(im[e + 1]));
-              const float2 v = __ffma2_rn(y, y, __fmul2_rn(x, x));
-              m = fmax3(m, v.x, v.y);
+            for (int e = 0; e < 32; e += 8) {
+              float2 x, y, v;
+              x = make_float2(__uint_as_float(re[e]), __uint_as_float(re[e + 1]));
+              y = make_float2(__uint_as_float(im[e]), __uint_as_float(im[e + 1]));
+              v = __ffma2_rn(y, y, __fmul2_rn(x, x));
+              m0 = fmax3(m0, v.x, v.y);
+              x = make_float2(__uint_as_float(re[e + 2]), __uint_as_float(re[e + 3]));
+              y = make_float2(__uint_as_float(im[e + 2]), __uint_as_float(im[e + 3]));
+              v = __ffma2_rn(y, y, __fmul2_rn(x, x));
+              m1 = fmax3(m1, v.x, v.y);
+              x = make_float2(__uint_as_float(re[e + 4]), __uint_as_float(re[e + 5]));
+              y = make_float2(__uint_as_float(im[e + 4]), __uint_as_float(im[e + 5]));
+              v = __ffma2_rn(y, y, __fmul2_rn(x, x));
+              m2 = fmax3(m2, v.x, v.y);
+              x = make_float2(__uint_as_float(re[e + 6]), __uint_as_float(re[e + 7]));
+              y = make_float2(__uint_as_float(im[e + 6]), __uint_as_float(im[e + 7]));
+              v = __ffma2_rn(y, y, __fmul2_rn(x, x));
+              m3 = fmax3(m3, v.x, v.y);
             }
           } else {
+            // straddling chunk: column n0 + e against row 32qw + lane
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
               const float x = __uint_as_float(re[e]), y = __uint_as_float(im[e]);
               const float v = fmaf(x, x, y * y);
-              m = (32 * ch + e > row) ? fmaxf(m, v) : m;
+              m0 = (e > lane) ? fmaxf(m0, v) : m0;
             }
           }
         }
@@ -375,6 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_screen(const ScreenArgs a) {
         if (lane == 0) mbar_arrive(&ctl.acc_empty[buf]);
       }
       if (!ok) break;
+      float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
       if (lane == 0) atomicMax(a.out + c, __float_as_uint(m));
@@ -385,11 +427,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_screen(const ScreenArgs a) {
       uint32_t gt = 0;
       int q = 0;
       bool ok = true;
+      // Row-major sweep: block I is last read in row I (as A for J >= I, as B
+      // in rows I' <= I), so it is released right after its row and the next
+      // candidate's block I is generated while rows I+1.. still run.  Row 0
+      // reads every block; it waits for each one as it first needs it.
       for (int c = blockIdx.x; c < a.K && ok; c += gridDim.x, ++q) {
-        for (int J = 0; J < nb && ok; ++J) {
-          ok = mbar_wait(&ctl.blk_full[J], (uint32_t)(q & 1), &ctl, a.err);
-          if (!ok) break;
-          for (int I = 0; I <= J; ++I, ++gt) {
+        for (int I = 0; I < nb && ok; ++I) {
+          for (int J = I; J < nb; ++J, ++gt) {
+            if (I == 0) {
+              ok = mbar_wait(&ctl.blk_full[J], (uint32_t)(q & 1), &ctl, a.err);
+              if (!ok) break;
+            }
             const uint32_t buf = gt & 1u, use = gt >> 1;
             if (use > 0) {
               ok = mbar_wait(&ctl.acc_empty[buf], (use - 1u) & 1u, &ctl, a.err);
@@ -410,8 +458,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_screen(const ScreenArgs a) {
             mma_bf16(dim, smem_desc_sw128(aI + 64u), smem_desc_sw128(bJ + 0u), Idesc<kHalf>::neg_a, 1u);
             mma_bf16(dim, smem_desc_sw128(aI + 96u), smem_desc_sw128(bJ + 32u), Idesc<kHalf>::neg_a, 1u);
             mma_commit(&ctl.acc_full[buf]);
-            if (J == nb - 1) mma_commit(&ctl.blk_empty[I]);   // last use of block I
           }
+          if (ok) mma_commit(&ctl.blk_empty[I]);   // row I done: block I is free
         }
       }
       // all issued MMAs complete before tensor memory is released
@@ -464,8 +512,15 @@ cudaError_t launch_screen(bool fp16, int N, int d, uint64_t seed, const float2* 
   a.nb = (N + kBlockCols - 1) / kBlockCols;
   a.ntiles = a.nb * (a.nb + 1) / 2;
   a.K = K; a.seed = seed; a.phi = phi32; a.c0 = c0; a.t = t; a.delta = (float)delta;
+  a.keys = philox_round_keys(seed);
   a.st = st; a.out = mu2_out; a.err = err_flag;
   const int grid = std::min(K, num_sms);
+  // refuse (without launching) a configuration the SM cannot hold
+  int fit = 0;
+  cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &fit, fp16 ? k_screen<true> : k_screen<false>, kThreads, screen_smem_bytes(kMaxBlocks));
+  if (oe != cudaSuccess) return oe;
+  if (fit < 1) return cudaErrorLaunchOutOfResources;
   // the operand area is always reserved for the largest block count, so every
   // descriptor address lies inside the CTA's shared memory
   if (fp16) k_screen<true><<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(a);
