@@ -45,6 +45,7 @@ extern "C" {
 #define TRSTMI_EBUSY (-6)        /* queue full */
 #define TRSTMI_EUNSUPPORTED (-7) /* shape/precision combination not built */
 #define TRSTMI_ENOTFOUND (-8)    /* unknown ticket */
+#define TRSTMI_ESIZE (-9)        /* size beyond a fixed built-in limit */
 
 /* ----------------------------------------------------- precision modes */
 typedef enum trstmi_precision {
@@ -201,6 +202,37 @@ int trstmi_candidate(trstmi_handle h, uint32_t t, uint32_t c, double delta,
  * is rounded to the precision first).  Stateless; device 0, default stream.
  */
 int trstmi_mu2_frame(int N, int d, const double *phi, int precision, double *mu2);
+
+/*
+ * Allocation-free binary64 mu^2 of a caller frame that is already in device
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that may not allocate device memory -- their device memory belongs to an
+ * allocator they must not bypass (a framework's caching allocator), or they
+ * run in loops where cudaMalloc / cudaFree would stall on an implicit device
+ * synchronisation.  It calls no allocating routine.
+ *
+ * phi_dev: DEVICE pointer, 2*d*N doubles in the frame layout above, columns
+ *          used as given.  mu2_dev: DEVICE pointer to one double, written
+ *          with max_{j<k} |G_jk|^2 (certified: binary32 preselection of the
+ *          pairs within its rounding-error bound of the max, binary64 over
+ *          those, a full binary64 pass if more than 65536 pairs qualify).
+ * stream:  cudaStream_t to issue on (NULL = the legacy default stream).  The
+ *          call only enqueues work; the result is ready when the stream is.
+ * Limit:   N * d <= 131072 complex entries, d <= 256; larger sizes return
+ *          TRSTMI_ESIZE without touching the device.
+ * Scratch: one static device array of about 1.5 MiB per GPU (the binary32
+ *          copy of the frame, the pair list and its counters), held by every
+ *          GPU that loads the library until the process exits.  Each call
+ *          clears what accumulates; the array otherwise keeps the last
+ *          call's contents.  All calls share it, so calls whose work overlaps
+ *          on a GPU (different streams, or different host threads) race and
+ *          must be serialised by the caller.
+ * The first call on a device looks up the array's device address (and sets
+ * kernel attributes) for that device; make that first call before any stream
+ * capture on the device.
+ */
+int trstmi_mu2_frame_noalloc(int N, int d, const double *phi_dev, double *mu2_dev,
+                             void *stream);
 
 /* ------------------------------------------------- measurement entry point */
 

@@ -330,6 +330,7 @@ const char* trstmi_strerror(int s) {
     case TRSTMI_EBUSY: return "queue full";
     case TRSTMI_EUNSUPPORTED: return "shape/precision combination not supported";
     case TRSTMI_ENOTFOUND: return "unknown ticket";
+    case TRSTMI_ESIZE: return "size beyond the built-in limit of this entry point";
     default: return "unknown status";
   }
 }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtrstmi.so")
 TRSTMI_OK, TRSTMI_PENDING = 0, 1
 TRSTMI_EINVAL, TRSTMI_ENOMEM, TRSTMI_ECUDA, TRSTMI_ETIMEOUT = -1, -2, -3, -4
 TRSTMI_ECANCELLED, TRSTMI_EBUSY, TRSTMI_EUNSUPPORTED, TRSTMI_ENOTFOUND = -5, -6, -7, -8
+TRSTMI_ESIZE = -9
 FP64, FP32, BF16_SCREEN, FP16_SCREEN = 0, 1, 2, 3
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16_SCREEN, "fp16": FP16_SCREEN}
 
@@ -88,6 +89,8 @@ SIGNATURES = {
     "trstmi_mu2_frame": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp]),
     "trstmi_profile_score": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_size_t, _dp]),
+    "trstmi_mu2_frame_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
