@@ -138,6 +138,46 @@ def measured_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
+PROFILES = os.path.join(ROOT, "profiles")
+KERNEL_SOURCES = {
+    "bf16": ["paper_2207_06374_gb300/csrc/tc_screen.cu", "paper_2207_06374_gb300/csrc/philox.cuh",
+             "paper_2207_06374_gb300/csrc/common.cuh"],
+    "fp32": ["paper_2207_06374_gb300/csrc/simt_kernels.cu", "paper_2207_06374_gb300/csrc/philox.cuh",
+             "paper_2207_06374_gb300/csrc/common.cuh"],
+}
+KERNEL_PROFILE = {"bf16": "k_screen_bf16_d32_n1024.txt", "fp32": "k_gram_tile_f32_d32_n1024.txt"}
+
+
+def kernel_source_sha1(precision):
+    import hashlib
+    h = hashlib.sha1()
+    for rel in KERNEL_SOURCES.get(precision, []):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(precision):
+    """DRAM bytes per launch from the committed ncu summary of the dominant
+    kernel, or None if there is none or the kernel source changed since."""
+    name = KERNEL_PROFILE.get(precision)
+    path = os.path.join(PROFILES, name) if name else None
+    if not path or not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+    if fields.get("source_sha1") != kernel_source_sha1(precision):
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def fp32_alu_peak_tflops(sm_mhz):
     # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -304,7 +344,8 @@ def main():
                      f"{'128' if prec == 'fp32' else '2'} lanes x 2 flops x {sm_mhz} MHz")
     achieved = flops_launch / (kernel_ms * 1e-3) / 1e12
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
-                 "traffic": None, "kernel": "tc_screen_bf16" if prec == "bf16" else "k_gram_tile",
+                 "traffic": profiled_traffic(prec),
+                 "kernel": "k_screen (bf16)" if prec == "bf16" else "k_gram_tile",
                  "kernel_ms": kernel_ms, "flops_per_launch": flops_launch, "peak_source": peak_note})
 
     side = None
