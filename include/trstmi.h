@@ -175,6 +175,121 @@ const char *trstmi_strerror(int status);
  * next failing call. */
 const char *trstmi_last_error(void);
 
+/* ------------------------------------------------------- batched searches
+ * Many independent searches of different (N, d) advanced together: each
+ * iteration is one set of shared launches over all of them (a persistent
+ * scoring pass whose CTAs take (instance, candidate, tile) work items from a
+ * counter, one CTA per instance for the accept rule and the commit),
+ * replayed from a captured CUDA graph.  Each instance keeps its own state,
+ * seed and counters and follows exactly the trajectory that trstmi_create +
+ * trstmi_step would give it alone (same options).  Tile widths (16, 32 or 64
+ * columns) are chosen per (d, ceil log2 N) by an autotuner that times the
+ * scoring pass on the instances themselves at creation; choices are cached
+ * for the process.  Precision: TRSTMI_FP32 (complex64 storage, binary32
+ * Gram) or TRSTMI_FP64; screen modes return TRSTMI_EUNSUPPORTED here.
+ */
+typedef struct trstmi_batch *trstmi_batch_handle;
+
+/* n instances, N[i] >= 2, 1 <= d[i] <= 256, seeds[i]; options shared (K,
+ * precision, radius rule, target, trace_cap, stream, device). */
+int trstmi_batch_create(int n, const int *N, const int *d, const uint64_t *seeds,
+                        const trstmi_options *opt, trstmi_batch_handle *out);
+/* Up to iters iterations for every instance (an instance stops early at its
+ * target).  info (nullable) aggregates: iters_done = max over instances,
+ * accepts and pairs_scored = sums, mu = max over instances, done = all done. */
+int trstmi_batch_step(trstmi_batch_handle b, int iters, trstmi_step_info *info);
+/* mu of every instance in the deciding precision (n doubles, host) and, if
+ * iters is not NULL, the iterations each has run. */
+int trstmi_batch_mu(trstmi_batch_handle b, double *mu, int32_t *iters);
+/* Binary64 frame of instance i (2*d*N doubles, host). */
+int trstmi_batch_get_phi(trstmi_batch_handle b, int i, double *out);
+/* Trace rows of instance i, as trstmi_get_trace. */
+int trstmi_batch_get_trace(trstmi_batch_handle b, int i, trstmi_trace_row *rows, int n,
+                           int *n_out);
+/* Tile width (columns) the autotuner chose for every instance (n ints). */
+int trstmi_batch_tile_widths(trstmi_batch_handle b, int *widths);
+/* Measurement: mean device time of one scoring pass over all instances (the
+ * persistent scoring launches of one iteration, bracketed by CUDA events;
+ * flush_bytes of scratch rewritten before each, outside the events).  Does
+ * not advance any instance. */
+int trstmi_batch_profile_score(trstmi_batch_handle b, int launches, size_t flush_bytes,
+                               double *avg_ms);
+/* Frees everything.  Safe on NULL. */
+void trstmi_batch_destroy(trstmi_batch_handle b);
+
+/* ------------------------------------------------------------- serving
+ * A persistent request loop on one GPU.  A host scheduler thread keeps up to
+ * max_slots searches resident (frame, radius, counters and random-stream
+ * position stay on the device) and advances all of them together: each round
+ * is iters_per_round iterations of the shared batched launches.  Requests
+ * wait in a FIFO queue; the head is admitted as soon as a slot and its device
+ * memory fit within hbm_budget (continuous batching: requests that arrive
+ * while others run join at the next round).  A search retires at a round
+ * boundary once it reached its target, spent its iteration budget or was
+ * cancelled.  Every search keeps its own state, so its result is exactly the
+ * one trstmi_create + trstmi_step give alone with the same options, seed and
+ * budget.  Precision: TRSTMI_FP32 or TRSTMI_FP64 ranking and acceptance.
+ */
+typedef struct trstmi_server trstmi_server;
+
+typedef struct trstmi_server_opts {
+  trstmi_options search;   /* options of every search (K, precision, radius rule,
+                              trace_cap, device, stream); target_mu comes from
+                              the request */
+  size_t hbm_budget;       /* bytes of device memory for resident searches (default 4 GiB) */
+  int32_t max_slots;       /* resident searches at most (default 256) */
+  int32_t iters_per_round; /* iterations per shared round (default 20) */
+  int32_t queue_cap;       /* queued requests at most; beyond: TRSTMI_EBUSY (default 65536) */
+  int32_t reserved;
+} trstmi_server_opts;
+
+typedef struct trstmi_request {
+  int32_t N, d;
+  uint64_t seed;
+  int32_t budget_iters;    /* iterations at most */
+  int32_t want_phi;        /* keep the final frame for trstmi_poll */
+  double target_mu;        /* stop at mu <= target_mu if > 0 ... */
+  double target_rel_welch; /* ... else at mu <= target_rel_welch * Welch bound if > 0 */
+} trstmi_request;
+
+typedef struct trstmi_result {
+  int32_t status;          /* TRSTMI_PENDING, TRSTMI_OK or an error */
+  int32_t iters;           /* iterations run */
+  int32_t accepts;
+  int32_t reached_target;  /* 1 if mu reached the target */
+  double mu;               /* final mu (deciding precision) */
+  double welch;            /* Welch bound of (N, d) */
+  int64_t t_submit_ns, t_admit_ns, t_done_ns;   /* steady host clock */
+  uint64_t pairs_scored;
+} trstmi_result;
+
+typedef struct trstmi_server_stats_t {
+  uint64_t submitted, admitted, completed, cancelled, rounds, pairs_scored;
+  double gpu_busy_s;       /* host time spent in rounds */
+  size_t hbm_in_use;       /* bytes of the budget held by resident searches */
+  int32_t active_slots, queued;
+  int32_t worker_status;   /* TRSTMI_OK, or the error that stopped the loop */
+  int32_t reserved;
+} trstmi_server_stats_t;
+
+void trstmi_default_server_opts(trstmi_server_opts *opts);
+/* Starts the loop (allocates hbm_budget bytes up front). */
+int trstmi_server_create(const trstmi_server_opts *opts, trstmi_server **out);
+/* Stops the loop; requests still pending end as TRSTMI_ECANCELLED.  Safe on NULL. */
+void trstmi_server_destroy(trstmi_server *srv);
+/* Thread-safe, non-blocking.  TRSTMI_EBUSY if the queue is full. */
+int trstmi_submit(trstmi_server *srv, const trstmi_request *req, uint64_t *ticket);
+/* TRSTMI_PENDING while queued or running, else the request's final status;
+ * out always receives what is known.  phi_out (nullable, 2*d*N doubles)
+ * receives the final frame if the request asked for it. */
+int trstmi_poll(trstmi_server *srv, uint64_t ticket, trstmi_result *out, double *phi_out);
+/* trstmi_poll after waiting up to timeout_ms for the request to finish. */
+int trstmi_wait(trstmi_server *srv, uint64_t ticket, int timeout_ms, trstmi_result *out,
+                double *phi_out);
+/* Cancels a queued or running request (running: at the next round boundary). */
+int trstmi_cancel(trstmi_server *srv, uint64_t ticket);
+int trstmi_server_stats(trstmi_server *srv, trstmi_server_stats_t *out);
+
 /* ---------------------------------------------- scoring entry points
  * These run one stage of the iteration on the current frame without
  * changing the search state; the tests use them to compare the kernels with

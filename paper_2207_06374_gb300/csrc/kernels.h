@@ -90,6 +90,40 @@ cudaError_t launch_screen(bool fp16, int N, int d, uint64_t seed, const float2* 
                           unsigned int* mu2_out, uint32_t* err_flag, int num_sms,
                           cudaStream_t s);
 
+// ------------------------------------------------------ batched searches
+// One instance of a batch, as the batched kernels see it (device table).
+struct SlotDesc {
+  DevState* st;
+  void* phi;            // frame in the scoring precision (float2* or double2*)
+  void* phi_other;      // the other precision's copy (kept in step on commit)
+  void* mu2;            // K candidate scores (u32 / u64 bit patterns)
+  TraceRowDev* trace;
+  uint64_t seed;
+  int N, d, K;
+  int R;                // tile width 16R of this instance's Gram pass
+  int ntiles;           // upper-triangle tiles at that width
+  int pad;
+  long long item_begin; // first work item of this instance within its width group
+};
+
+// Iteration start for every instance (one CTA each); also zeroes the work counters.
+cudaError_t launch_batch_begin(SlotDesc* slots, int n, unsigned long long* counters, int ncounters,
+                               bool f64, cudaStream_t s);
+// Persistent scoring pass over the instances of one tile-width group: work
+// items (instance, candidate, tile) handed out by an atomic counter.
+cudaError_t launch_batch_score(bool f64, int R, const SlotDesc* slots, const int* group,
+                               const long long* group_begin, int ngroup, long long nitems,
+                               unsigned long long* counter, size_t smem, int grid,
+                               cudaStream_t s);
+cudaError_t launch_batch_decide(SlotDesc* slots, int n, bool f64, cudaStream_t s);
+cudaError_t launch_batch_commit(SlotDesc* slots, int n, int maxN, bool f64, cudaStream_t s);
+cudaError_t batch_score_occupancy(bool f64, int R, size_t smem, int* blocks_per_sm);
+size_t gram_smem_bytes(bool f64, int d, int R);
+// Autotuned tile-width cache per (d, ceil log2 N): 0 if not measured yet.
+int cached_width(bool f64, int d, int N);
+void store_width(bool f64, int d, int N, int R);
+int tiles_at_width(int N, int R);
+
 cudaError_t init_kernel_attributes();
 cudaError_t init_screen_attributes(int optin_smem);
 

@@ -1,0 +1,675 @@
+// Serving loop (trstmi_server_*, trstmi_submit / trstmi_poll, include/trstmi.h).
+//
+// A host scheduler thread keeps a set of resident search slots on one GPU and
+// advances all of them together: each round is `iters_per_round` iterations
+// of the shared batched launches (iteration start, persistent scoring pass
+// over every slot's (candidate, tile) work items, per-slot accept rule and
+// commit).  Requests wait in a FIFO queue; the head is admitted as soon as a
+// slot and enough of the device-memory budget are free (continuous
+// batching).  A slot retires at a round boundary once its search reached its
+// target, spent its iteration budget or was cancelled.  Each slot keeps its
+// own state, seed and counters, so a request's result is exactly the one the
+// same search gives alone.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/trstmi.h"
+#include "kernels.h"
+
+using namespace trstmi;
+
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// First-fit allocator over one device allocation (the HBM budget).
+class Arena {
+ public:
+  void reset(char* base, size_t size) {
+    base_ = base;
+    size_ = size;
+    free_.clear();
+    if (size) free_[0] = size;
+    used_ = 0;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = (bytes + 255) / 256 * 256;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes;
+        const size_t at = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[at] = rest;
+        used_ += bytes;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = (bytes + 255) / 256 * 256;
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  char* base() const { return base_; }
+  size_t used() const { return used_; }
+
+ private:
+  char* base_ = nullptr;
+  size_t size_ = 0, used_ = 0;
+  std::map<size_t, size_t> free_;
+};
+
+struct Req {
+  trstmi_request req{};
+  double target = -1.0;
+  int status = TRSTMI_PENDING;
+  bool cancel = false;
+  int64_t t_submit = 0, t_admit = 0, t_done = 0;
+  double mu = 0.0, welch = 0.0;
+  int32_t iters = 0, accepts = 0, reached = 0;
+  uint64_t pairs = 0;
+  std::vector<double> phi;
+};
+
+struct Slot {
+  uint64_t ticket = 0;
+  size_t off = 0, bytes = 0;
+  int state_idx = -1;
+  SlotDesc desc{};
+  uint32_t budget = 0;
+};
+
+double welch_bound(int N, int d) {
+  if (N <= d || N < 2) return 0.0;
+  return std::sqrt((double)(N - d) / ((double)d * (double)(N - 1)));
+}
+
+__global__ void k_srv_set_stop(SlotDesc* slots, int n, uint32_t iters, const uint32_t* budget) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  DevState* st = slots[s].st;
+  unsigned long long stop = (unsigned long long)st->t + iters;
+  if (stop > budget[s]) stop = budget[s];
+  st->t_stop = (uint32_t)stop;
+}
+
+// Marks a slot active (or not) for a width measurement, without advancing it.
+__global__ void k_srv_activate(DevState* st, uint32_t on) {
+  st->active = on;
+  st->delta_used = st->delta;
+}
+
+template <typename B>
+__global__ void k_srv_set_mu2cur(DevState* st, const void* mu2) {
+  st->mu2_cur = (double)nonneg_from_bits(reinterpret_cast<const B*>(mu2)[0]);
+  st->done = (st->mu2_cur <= st->target2) ? 1u : 0u;
+}
+
+size_t slot_bytes(int N, int d, int K, int trace_cap) {
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t nd = (size_t)N * d;
+  return up(nd * sizeof(double2)) + up(nd * sizeof(float2)) + up((size_t)K * 8) +
+         up((size_t)std::max(trace_cap, 1) * sizeof(TraceRowDev));
+}
+
+}  // namespace
+
+struct trstmi_server {
+  trstmi_server_opts opt{};
+  bool f64 = false;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* arena_mem = nullptr;
+  Arena arena;
+  DevState* d_states = nullptr;       // max_slots states
+  SlotDesc* d_slots = nullptr;        // active slot table
+  uint32_t* d_budget = nullptr;
+  unsigned long long* d_counters = nullptr;
+  std::vector<int> free_states;
+  std::vector<Slot> slots;
+  struct Group { int R; int* d_ids; long long* d_begin; int count; long long nitems; size_t smem; int grid; };
+  std::vector<Group> groups;
+  int* d_group_ids = nullptr;         // max_slots ints per width (3 widths)
+  long long* d_group_begin = nullptr; // (max_slots + 1) per width
+  int maxN = 0;
+
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, Req> reqs;
+  uint64_t next_ticket = 1;
+  std::atomic<bool> stop{false};
+  std::atomic<int> active_count{0};
+  int worker_error = TRSTMI_OK;
+  std::thread worker;
+  // statistics
+  uint64_t submitted = 0, admitted = 0, completed = 0, cancelled = 0, rounds = 0;
+  uint64_t pairs_scored = 0;
+  double gpu_busy_s = 0.0;
+};
+
+namespace {
+
+int choose_width(trstmi_server* sv, Slot& sl) {
+  const int N = sl.desc.N, d = sl.desc.d;
+  int R = cached_width(sv->f64, d, N);
+  if (R > 0) return R;
+  // measure this bucket on this slot alone (its state is active for timing)
+  int best_R = 1;
+  float best = 1e30f;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return 1;
+  k_srv_activate<<<1, 1, 0, sv->stream>>>(sl.desc.st, 1u);
+  for (int cand : {1, 2, 4}) {
+    if (gram_smem_bytes(sv->f64, d, cand) > 200 * 1024) continue;
+    if (cand > 1 && 16 * cand >= 2 * N) continue;
+    SlotDesc tmp = sl.desc;
+    tmp.R = cand;
+    tmp.ntiles = tiles_at_width(N, cand);
+    const long long nitems = (long long)tmp.K * tmp.ntiles;
+    const long long begin[2] = {0, nitems};
+    const int ids[1] = {0};
+    const size_t smem = gram_smem_bytes(sv->f64, d, cand);
+    int per_sm = 0;
+    if (batch_score_occupancy(sv->f64, cand, smem, &per_sm) != cudaSuccess || per_sm < 1) continue;
+    const int grid = (int)std::min<long long>(nitems, (long long)sv->num_sms * per_sm);
+    // the timing tables live in the group scratch of width slot 0
+    cudaMemcpyAsync(sv->d_slots, &tmp, sizeof(SlotDesc), cudaMemcpyHostToDevice, sv->stream);
+    cudaMemcpyAsync(sv->d_group_ids, ids, sizeof(ids), cudaMemcpyHostToDevice, sv->stream);
+    cudaMemcpyAsync(sv->d_group_begin, begin, sizeof(begin), cudaMemcpyHostToDevice, sv->stream);
+    float t_best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaMemsetAsync(sv->d_counters, 0, sizeof(unsigned long long), sv->stream);
+      cudaEventRecord(e0, sv->stream);
+      launch_batch_score(sv->f64, cand, sv->d_slots, sv->d_group_ids, sv->d_group_begin, 1, nitems,
+                         sv->d_counters, smem, grid, sv->stream);
+      cudaEventRecord(e1, sv->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) t_best = std::min(t_best, ms);
+    }
+    if (t_best < best) { best = t_best; best_R = cand; }
+  }
+  k_srv_activate<<<1, 1, 0, sv->stream>>>(sl.desc.st, 0u);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  store_width(sv->f64, d, N, best_R);
+  return best_R;
+}
+
+// Device tables for the current active set: descriptors, budgets, width groups.
+int rebuild_tables(trstmi_server* sv) {
+  const int n = (int)sv->slots.size();
+  std::vector<SlotDesc> h(n);
+  std::vector<uint32_t> budget(n);
+  sv->maxN = 0;
+  for (int i = 0; i < n; ++i) {
+    h[i] = sv->slots[i].desc;
+    budget[i] = sv->slots[i].budget;
+    sv->maxN = std::max(sv->maxN, h[i].N);
+  }
+  sv->groups.clear();
+  const int widths[3] = {4, 2, 1};
+  for (int w = 0; w < 3; ++w) {
+    const int R = widths[w];
+    std::vector<int> ids;
+    for (int i = 0; i < n; ++i)
+      if (h[i].R == R) ids.push_back(i);
+    if (ids.empty()) continue;
+    std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) {
+      return (double)h[x].K * h[x].ntiles * h[x].d > (double)h[y].K * h[y].ntiles * h[y].d;
+    });
+    std::vector<long long> begin(ids.size() + 1, 0);
+    size_t smem = 0;
+    for (size_t q = 0; q < ids.size(); ++q) {
+      begin[q + 1] = begin[q] + (long long)h[ids[q]].K * h[ids[q]].ntiles;
+      smem = std::max(smem, gram_smem_bytes(sv->f64, h[ids[q]].d, R));
+    }
+    trstmi_server::Group g;
+    g.R = R;
+    g.d_ids = sv->d_group_ids + (size_t)w * sv->opt.max_slots;
+    g.d_begin = sv->d_group_begin + (size_t)w * (sv->opt.max_slots + 1);
+    g.count = (int)ids.size();
+    g.nitems = begin.back();
+    g.smem = smem;
+    int per_sm = 0;
+    if (batch_score_occupancy(sv->f64, R, smem, &per_sm) != cudaSuccess || per_sm < 1)
+      return TRSTMI_ECUDA;
+    g.grid = (int)std::min<long long>(g.nitems, (long long)sv->num_sms * per_sm);
+    if (cudaMemcpyAsync(g.d_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice,
+                        sv->stream) != cudaSuccess ||
+        cudaMemcpyAsync(g.d_begin, begin.data(), sizeof(long long) * begin.size(),
+                        cudaMemcpyHostToDevice, sv->stream) != cudaSuccess)
+      return TRSTMI_ECUDA;
+    sv->groups.push_back(g);
+  }
+  if (n > 0 &&
+      (cudaMemcpyAsync(sv->d_slots, h.data(), sizeof(SlotDesc) * n, cudaMemcpyHostToDevice,
+                       sv->stream) != cudaSuccess ||
+       cudaMemcpyAsync(sv->d_budget, budget.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice,
+                       sv->stream) != cudaSuccess))
+    return TRSTMI_ECUDA;
+  return TRSTMI_OK;
+}
+
+// Sets up the slot of a request: memory, state, seeded frame, initial score.
+int admit(trstmi_server* sv, uint64_t ticket, Req& r, Slot* out) {
+  const trstmi_options& o = sv->opt.search;
+  const int N = r.req.N, d = r.req.d;
+  Slot sl;
+  sl.ticket = ticket;
+  sl.bytes = slot_bytes(N, d, o.K, o.trace_cap);
+  if (!sv->arena.alloc(sl.bytes, &sl.off)) return TRSTMI_ENOMEM;
+  sl.state_idx = sv->free_states.back();
+  sv->free_states.pop_back();
+  char* p = sv->arena.base() + sl.off;
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t nd = (size_t)N * d;
+  double2* p64 = (double2*)p;
+  float2* p32 = (float2*)(p + up(nd * sizeof(double2)));
+  void* mu2 = p + up(nd * sizeof(double2)) + up(nd * sizeof(float2));
+  TraceRowDev* tr = (TraceRowDev*)((char*)mu2 + up((size_t)o.K * 8));
+  SlotDesc& sd = sl.desc;
+  sd.st = sv->d_states + sl.state_idx;
+  sd.phi = sv->f64 ? (void*)p64 : (void*)p32;
+  sd.phi_other = sv->f64 ? (void*)p32 : (void*)p64;
+  sd.mu2 = mu2;
+  sd.trace = tr;
+  sd.seed = r.req.seed;
+  sd.N = N; sd.d = d; sd.K = o.K;
+  sl.budget = (uint32_t)std::max(0, r.req.budget_iters);
+  DevState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.delta = o.delta0; s0.delta_used = o.delta0;
+  s0.target2 = r.target > 0 ? r.target * r.target : -1.0;
+  s0.gamma_inc = o.gamma_inc; s0.gamma_dec = o.gamma_dec;
+  s0.delta_min = o.delta_min; s0.delta_max = o.delta_max;
+  s0.screen_min_delta = o.screen_min_delta;
+  s0.trace_cap = (uint32_t)o.trace_cap;
+  cudaStream_t s = sv->stream;
+  if (cudaMemsetAsync(p, 0, sl.bytes, s) != cudaSuccess ||
+      cudaMemcpyAsync(sd.st, &s0, sizeof(s0), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      launch_init_frame(N, d, sd.seed, p64, p32, sd.st, s) != cudaSuccess)
+    return TRSTMI_ECUDA;
+  GramSource src{};
+  src.perturb = false;
+  src.phi = sd.phi;
+  cudaError_t e = sv->f64
+      ? launch_gram_f64(N, d, 1, src, (unsigned long long*)mu2, sv->num_sms, s)
+      : launch_gram_f32(N, d, 1, src, (unsigned int*)mu2, nullptr, sv->num_sms, s);
+  if (e != cudaSuccess) return TRSTMI_ECUDA;
+  if (sv->f64) k_srv_set_mu2cur<unsigned long long><<<1, 1, 0, s>>>(sd.st, mu2);
+  else k_srv_set_mu2cur<unsigned int><<<1, 1, 0, s>>>(sd.st, mu2);
+  if (cudaGetLastError() != cudaSuccess) return TRSTMI_ECUDA;
+  // tile width: the cached choice for this (d, N) bucket, measured if new
+  sd.R = 1;
+  sd.ntiles = tiles_at_width(N, 1);
+  const int R = choose_width(sv, sl);
+  sd.R = R;
+  sd.ntiles = tiles_at_width(N, R);
+  *out = sl;
+  return TRSTMI_OK;
+}
+
+void retire(trstmi_server* sv, size_t k, const DevState& st, int status) {
+  Slot& sl = sv->slots[k];
+  Req& r = sv->reqs[sl.ticket];
+  r.mu = std::sqrt(st.mu2_cur);
+  r.welch = welch_bound(r.req.N, r.req.d);
+  r.iters = (int32_t)st.t;
+  r.accepts = (int32_t)st.accepts;
+  r.reached = (int32_t)st.done;
+  r.pairs = (uint64_t)st.t * (uint64_t)sl.desc.K * ((uint64_t)r.req.N * (r.req.N - 1) / 2);
+  if (r.req.want_phi && status == TRSTMI_OK) {
+    r.phi.resize((size_t)2 * r.req.N * r.req.d);
+    const void* p64 = sv->f64 ? sl.desc.phi : sl.desc.phi_other;
+    if (cudaMemcpyAsync(r.phi.data(), p64, r.phi.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        sv->stream) != cudaSuccess ||
+        cudaStreamSynchronize(sv->stream) != cudaSuccess)
+      status = TRSTMI_ECUDA;
+  }
+  r.status = status;
+  r.t_done = now_ns();
+  sv->arena.release(sl.off, sl.bytes);
+  sv->free_states.push_back(sl.state_idx);
+  sv->slots.erase(sv->slots.begin() + k);
+  sv->active_count = (int)sv->slots.size();
+  if (status == TRSTMI_ECANCELLED) ++sv->cancelled; else ++sv->completed;
+}
+
+void worker_main(trstmi_server* sv) {
+  cudaSetDevice(sv->opt.search.device);
+  std::deque<uint64_t> pending;
+  bool changed = true;
+  std::vector<DevState> st;
+  const int I = std::max(1, sv->opt.iters_per_round);
+  while (!sv->stop.load()) {
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      if (sv->slots.empty() && pending.empty() && sv->queue.empty())
+        sv->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+      while (!sv->queue.empty()) { pending.push_back(sv->queue.front()); sv->queue.pop_front(); }
+      // drop cancelled requests that never started
+      for (auto it = pending.begin(); it != pending.end();) {
+        Req& r = sv->reqs[*it];
+        if (r.cancel) {
+          r.status = TRSTMI_ECANCELLED;
+          r.t_done = now_ns();
+          ++sv->cancelled;
+          it = pending.erase(it);
+          sv->cv_done.notify_all();
+        } else {
+          ++it;
+        }
+      }
+    }
+    if (sv->stop.load()) break;
+    // admission, FIFO: the head waits until a slot and its memory are free
+    while (!pending.empty() && (int)sv->slots.size() < sv->opt.max_slots) {
+      const uint64_t tk = pending.front();
+      Req* r;
+      {
+        std::lock_guard<std::mutex> g(sv->mu);
+        r = &sv->reqs[tk];
+      }
+      Slot sl;
+      const int rc = admit(sv, tk, *r, &sl);
+      if (rc == TRSTMI_ENOMEM) {
+        if (sv->slots.empty()) {   // can never fit the budget
+          std::lock_guard<std::mutex> g(sv->mu);
+          r->status = TRSTMI_ENOMEM;
+          r->t_done = now_ns();
+          pending.pop_front();
+          sv->cv_done.notify_all();
+          continue;
+        }
+        break;
+      }
+      if (rc) { sv->worker_error = rc; sv->stop = true; break; }
+      {
+        std::lock_guard<std::mutex> g(sv->mu);
+        r->t_admit = now_ns();
+        ++sv->admitted;
+      }
+      pending.pop_front();
+      sv->slots.push_back(sl);
+      sv->active_count = (int)sv->slots.size();
+      changed = true;
+    }
+    if (sv->stop.load()) break;
+    if (sv->slots.empty()) continue;
+    if (changed) {
+      if (rebuild_tables(sv) != TRSTMI_OK) { sv->worker_error = TRSTMI_ECUDA; break; }
+      changed = false;
+    }
+    // one round: I iterations of every active slot, shared launches
+    const int n = (int)sv->slots.size();
+    const int64_t t0 = now_ns();
+    cudaStream_t s = sv->stream;
+    k_srv_set_stop<<<(n + 127) / 128, 128, 0, s>>>(sv->d_slots, n, (uint32_t)I, sv->d_budget);
+    bool ok = cudaGetLastError() == cudaSuccess;
+    for (int it = 0; ok && it < I; ++it) {
+      ok = launch_batch_begin(sv->d_slots, n, sv->d_counters, (int)sv->groups.size(), sv->f64, s) ==
+           cudaSuccess;
+      for (size_t g = 0; ok && g < sv->groups.size(); ++g) {
+        const auto& G = sv->groups[g];
+        ok = launch_batch_score(sv->f64, G.R, sv->d_slots, G.d_ids, G.d_begin, G.count, G.nitems,
+                                sv->d_counters + g, G.smem, G.grid, s) == cudaSuccess;
+      }
+      ok = ok && launch_batch_decide(sv->d_slots, n, sv->f64, s) == cudaSuccess;
+      ok = ok && launch_batch_commit(sv->d_slots, n, sv->maxN, sv->f64, s) == cudaSuccess;
+    }
+    st.resize(n);
+    for (int k = 0; ok && k < n; ++k)
+      ok = cudaMemcpyAsync(&st[k], sv->slots[k].desc.st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                           s) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); sv->worker_error = TRSTMI_ECUDA; break; }
+    {
+      std::lock_guard<std::mutex> g(sv->mu);
+      sv->gpu_busy_s += (now_ns() - t0) * 1e-9;
+      ++sv->rounds;
+      for (int k = 0; k < n; ++k)
+        sv->pairs_scored += (uint64_t)(st[k].t - st[k].t_call) * (uint64_t)sv->slots[k].desc.K *
+                            ((uint64_t)sv->slots[k].desc.N * (sv->slots[k].desc.N - 1) / 2);
+      for (int k = n - 1; k >= 0; --k) {
+        const Req& r = sv->reqs[sv->slots[k].ticket];
+        const uint32_t err = st[k].error;
+        if (err) {
+          retire(sv, k, st[k], (err & kErrTimeout) ? TRSTMI_ETIMEOUT : TRSTMI_EINVAL);
+          changed = true;
+        } else if (r.cancel) {
+          retire(sv, k, st[k], TRSTMI_ECANCELLED);
+          changed = true;
+        } else if (st[k].done || st[k].t >= sv->slots[k].budget) {
+          retire(sv, k, st[k], TRSTMI_OK);
+          changed = true;
+        }
+      }
+      sv->cv_done.notify_all();
+    }
+  }
+  // fail whatever is left
+  std::lock_guard<std::mutex> g(sv->mu);
+  for (auto& kv : sv->reqs)
+    if (kv.second.status == TRSTMI_PENDING) {
+      kv.second.status = sv->worker_error ? sv->worker_error : TRSTMI_ECANCELLED;
+      kv.second.t_done = now_ns();
+    }
+  sv->cv_done.notify_all();
+}
+
+void fill_result(const Req& r, trstmi_result* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->status = r.status;
+  out->iters = r.iters;
+  out->accepts = r.accepts;
+  out->reached_target = r.reached;
+  out->mu = r.mu;
+  out->welch = r.welch;
+  out->t_submit_ns = r.t_submit;
+  out->t_admit_ns = r.t_admit;
+  out->t_done_ns = r.t_done;
+  out->pairs_scored = r.pairs;
+}
+
+}  // namespace
+
+extern "C" {
+
+void trstmi_default_server_opts(trstmi_server_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  trstmi_default_options(&o->search);
+  o->search.precision = TRSTMI_FP32;
+  o->search.K = 8;
+  o->search.trace_cap = 0;
+  o->hbm_budget = (size_t)4 << 30;
+  o->max_slots = 256;
+  o->iters_per_round = 20;
+  o->queue_cap = 1 << 16;
+}
+
+void trstmi_server_destroy(trstmi_server* sv) {
+  if (!sv) return;
+  sv->stop = true;
+  sv->cv_work.notify_all();
+  if (sv->worker.joinable()) sv->worker.join();
+  cudaSetDevice(sv->opt.search.device);
+  if (sv->stream) cudaStreamSynchronize(sv->stream);
+  if (sv->arena_mem) cudaFree(sv->arena_mem);
+  if (sv->d_states) cudaFree(sv->d_states);
+  if (sv->own_stream && sv->stream) cudaStreamDestroy(sv->stream);
+  delete sv;
+}
+
+int trstmi_server_create(const trstmi_server_opts* opts, trstmi_server** out) {
+  if (!out) return TRSTMI_EINVAL;
+  *out = nullptr;
+  trstmi_server_opts o;
+  if (opts) o = *opts; else trstmi_default_server_opts(&o);
+  const trstmi_options& so = o.search;
+  if (so.precision != TRSTMI_FP32 && so.precision != TRSTMI_FP64) return TRSTMI_EUNSUPPORTED;
+  if (o.max_slots < 1 || o.max_slots > 65536 || o.queue_cap < 1 || o.iters_per_round < 1 ||
+      so.K < 1 || so.trace_cap < 0 || o.hbm_budget < 4096 || !(so.delta0 > 0) ||
+      !(so.gamma_inc >= 1) || !(so.gamma_dec > 0 && so.gamma_dec <= 1) || !(so.delta_min >= 0) ||
+      !(so.delta_max >= so.delta_min))
+    return TRSTMI_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return TRSTMI_ECUDA;
+  if (so.device < 0 || so.device >= ndev) return TRSTMI_EINVAL;
+  if (cudaSetDevice(so.device) != cudaSuccess || init_kernel_attributes() != cudaSuccess)
+    return TRSTMI_ECUDA;
+  trstmi_server* sv = new (std::nothrow) trstmi_server();
+  if (!sv) return TRSTMI_ENOMEM;
+  sv->opt = o;
+  sv->f64 = so.precision == TRSTMI_FP64;
+  if (cudaDeviceGetAttribute(&sv->num_sms, cudaDevAttrMultiProcessorCount, so.device) != cudaSuccess) {
+    delete sv;
+    return TRSTMI_ECUDA;
+  }
+  if (so.stream) {
+    sv->stream = (cudaStream_t)so.stream;
+  } else if (cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) == cudaSuccess) {
+    sv->own_stream = true;
+  } else {
+    delete sv;
+    return TRSTMI_ECUDA;
+  }
+  // control tables (states, descriptors, budgets, counters, width groups)
+  const size_t ms = (size_t)o.max_slots;
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t b_st = up(ms * sizeof(DevState)), b_sl = up(ms * sizeof(SlotDesc)),
+               b_bu = up(ms * sizeof(uint32_t)), b_ct = up(8 * sizeof(unsigned long long)),
+               b_gi = up(3 * ms * sizeof(int)), b_gb = up(3 * (ms + 1) * sizeof(long long));
+  char* ctl = nullptr;
+  if (cudaMalloc(&ctl, b_st + b_sl + b_bu + b_ct + b_gi + b_gb) != cudaSuccess ||
+      cudaMalloc(&sv->arena_mem, o.hbm_budget) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctl) cudaFree(ctl);
+    trstmi_server_destroy(sv);
+    return TRSTMI_ENOMEM;
+  }
+  sv->d_states = (DevState*)ctl;
+  sv->d_slots = (SlotDesc*)(ctl + b_st);
+  sv->d_budget = (uint32_t*)(ctl + b_st + b_sl);
+  sv->d_counters = (unsigned long long*)(ctl + b_st + b_sl + b_bu);
+  sv->d_group_ids = (int*)(ctl + b_st + b_sl + b_bu + b_ct);
+  sv->d_group_begin = (long long*)(ctl + b_st + b_sl + b_bu + b_ct + b_gi);
+  sv->arena.reset((char*)sv->arena_mem, o.hbm_budget);
+  for (int i = o.max_slots - 1; i >= 0; --i) sv->free_states.push_back(i);
+  sv->worker = std::thread(worker_main, sv);
+  *out = sv;
+  return TRSTMI_OK;
+}
+
+int trstmi_submit(trstmi_server* sv, const trstmi_request* req, uint64_t* ticket) {
+  if (!sv || !req || !ticket) return TRSTMI_EINVAL;
+  if (req->N < 2 || req->d < 1 || req->d > kMaxD || req->budget_iters < 0 ||
+      (long long)req->N * ((req->d + 1) / 2) >= (1ll << 32))
+    return TRSTMI_EINVAL;
+  std::lock_guard<std::mutex> g(sv->mu);
+  if (sv->worker_error) return sv->worker_error;
+  if ((int)sv->queue.size() >= sv->opt.queue_cap) return TRSTMI_EBUSY;
+  const uint64_t tk = sv->next_ticket++;
+  Req& r = sv->reqs[tk];
+  r.req = *req;
+  r.target = req->target_mu > 0 ? req->target_mu
+           : (req->target_rel_welch > 0 ? req->target_rel_welch * welch_bound(req->N, req->d) : -1.0);
+  r.t_submit = now_ns();
+  sv->queue.push_back(tk);
+  ++sv->submitted;
+  *ticket = tk;
+  sv->cv_work.notify_one();
+  return TRSTMI_OK;
+}
+
+int trstmi_poll(trstmi_server* sv, uint64_t ticket, trstmi_result* out, double* phi_out) {
+  if (!sv || !out) return TRSTMI_EINVAL;
+  std::lock_guard<std::mutex> g(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return TRSTMI_ENOTFOUND;
+  const Req& r = it->second;
+  fill_result(r, out);
+  if (r.status == TRSTMI_PENDING) return TRSTMI_PENDING;
+  if (phi_out && !r.phi.empty()) std::memcpy(phi_out, r.phi.data(), r.phi.size() * sizeof(double));
+  return r.status;
+}
+
+int trstmi_wait(trstmi_server* sv, uint64_t ticket, int timeout_ms, trstmi_result* out,
+                double* phi_out) {
+  if (!sv || !out) return TRSTMI_EINVAL;
+  {
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return TRSTMI_ENOTFOUND;
+    sv->cv_done.wait_for(lk, std::chrono::milliseconds(std::max(0, timeout_ms)),
+                         [&] { return sv->reqs[ticket].status != TRSTMI_PENDING; });
+  }
+  return trstmi_poll(sv, ticket, out, phi_out);
+}
+
+int trstmi_cancel(trstmi_server* sv, uint64_t ticket) {
+  if (!sv) return TRSTMI_EINVAL;
+  std::lock_guard<std::mutex> g(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return TRSTMI_ENOTFOUND;
+  if (it->second.status != TRSTMI_PENDING) return it->second.status;
+  it->second.cancel = true;
+  sv->cv_work.notify_one();
+  return TRSTMI_PENDING;
+}
+
+int trstmi_server_stats(trstmi_server* sv, trstmi_server_stats_t* out) {
+  if (!sv || !out) return TRSTMI_EINVAL;
+  std::lock_guard<std::mutex> g(sv->mu);
+  std::memset(out, 0, sizeof(*out));
+  out->submitted = sv->submitted;
+  out->admitted = sv->admitted;
+  out->completed = sv->completed;
+  out->cancelled = sv->cancelled;
+  out->rounds = sv->rounds;
+  out->pairs_scored = sv->pairs_scored;
+  out->gpu_busy_s = sv->gpu_busy_s;
+  out->hbm_in_use = sv->arena.used();
+  out->active_slots = (int32_t)sv->active_count.load();
+  out->queued = (int32_t)sv->queue.size();
+  out->worker_status = sv->worker_error;
+  return TRSTMI_OK;
+}
+
+}  // extern "C"

@@ -145,6 +145,16 @@ __device__ bool load_column(const typename Cplx<T>::type* __restrict__ frame, in
   return true;
 }
 
+// |G_jk|^2 from its accumulated parts, rounded explicitly so that every
+// kernel that scores a pair gives the same bits (the accumulation itself is
+// the sequential chain over i of pair_accumulate below).
+__device__ __forceinline__ float pair_abs2(float re, float im) {
+  return __fmaf_rn(re, re, __fmul_rn(im, im));
+}
+__device__ __forceinline__ double pair_abs2(double re, double im) {
+  return __fma_rn(re, re, __dmul_rn(im, im));
+}
+
 // Upper-triangle tile tau (column-major over tiles with I <= J) -> (I, J).
 __device__ __forceinline__ void tile_coords(int tau, int& I, int& J) {
   int j = (int)((sqrtf(8.0f * (float)tau + 1.0f) - 1.0f) * 0.5f);
@@ -176,24 +186,111 @@ template <typename T> __device__ __forceinline__ T block_max(T v, T* red) {
   return v;  // valid in thread 0
 }
 
-// One CTA (256 threads, 16 x 16) per work item (slot, tile I <= J) of width
-// BT = 16 R columns.  Column blocks I and J are generated (or loaded) into
-// shared memory as [i][column] planes of real and imaginary parts; each
-// thread accumulates an R x R micro-tile of
+// One work item of a Gram pass: tile (I <= J) of one frame, either the
+// candidate normalise(Phi + delta Z_{t,c}) or a stored frame.
+struct TileItem {
+  int N, d, I, J;
+  bool perturb, normalize;
+  const void* phi;   // float2* / double2*: base frame (perturb) or the frame itself
+  uint64_t seed;
+  uint32_t c, t;
+  double delta;
+};
+
+// The CTA (256 threads, 16 x 16) scores tile (I, J) of width BT = 16 R.
+// Column blocks I and J are generated (or loaded) into shared memory as
+// [i][column] planes of real and imaginary parts; each thread accumulates an
+// R x R micro-tile of
 //   Re G_jk = sum_i a_ij a_ik + b_ij b_ik,  Im G_jk = sum_i a_ij b_ik - b_ij a_ik
-// and the CTA reduces max |G_jk|^2 over j < k < N.
+// as a sequential chain over i, so a pair's |G_jk|^2 does not depend on the
+// tile shape.  Returns this thread's max over its pairs j < k < N (and
+// appends the pairs at or above thr when filter != nullptr).  Begins and
+// ends with a CTA barrier; *zero_col is set if a column had zero norm.
+template <typename T, int R>
+__device__ T score_tile(const TileItem& it, T* sm, int* zero_col, T thr,
+                        const PairFilter* filter) {
+  constexpr int BT = 16 * R;
+  using C = typename Cplx<T>::type;
+  const int d = it.d, N = it.N, I = it.I, J = it.J;
+  T* sIre = sm;
+  T* sIim = sm + (size_t)d * BT;
+  T* sJre = sm + (size_t)2 * d * BT;
+  T* sJim = sm + (size_t)3 * d * BT;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const bool diag = (I == J);
+  __syncthreads();
+  const int ncols = diag ? BT : 2 * BT;
+  for (int q = threadIdx.x; q < ncols; q += blockDim.x) {
+    const int blk = q / BT, loc = q - blk * BT;
+    const int gj = (blk == 0 ? I : J) * BT + loc;
+    T* ore = (blk == 0 ? sIre : sJre) + loc;
+    T* oim = (blk == 0 ? sIim : sJim) + loc;
+    bool ok = true;
+    if (gj < N) {
+      if (it.perturb)
+        ok = gen_column<T>(reinterpret_cast<const C*>(it.phi), d, gj, it.seed, it.c, it.t, 0u,
+                           (T)it.delta, ore, oim, BT);
+      else
+        ok = load_column<T>(reinterpret_cast<const C*>(it.phi), d, gj, it.normalize, ore, oim, BT);
+    } else {
+      for (int i = 0; i < d; ++i) { ore[i * BT] = T(0); oim[i * BT] = T(0); }
+    }
+    if (!ok) *zero_col = 1;
+  }
+  __syncthreads();
+  const T* bRe = diag ? sIre : sJre;
+  const T* bIm = diag ? sIim : sJim;
+  T accR[R][R], accI[R][R];
+#pragma unroll
+  for (int x = 0; x < R; ++x)
+#pragma unroll
+    for (int y = 0; y < R; ++y) { accR[x][y] = T(0); accI[x][y] = T(0); }
+#pragma unroll 2
+  for (int i = 0; i < d; ++i) {
+    T ar[R], ai[R], br[R], bi[R];
+#pragma unroll
+    for (int x = 0; x < R; ++x) {
+      ar[x] = sIre[i * BT + ty + 16 * x];
+      ai[x] = sIim[i * BT + ty + 16 * x];
+      br[x] = bRe[i * BT + tx + 16 * x];
+      bi[x] = bIm[i * BT + tx + 16 * x];
+    }
+#pragma unroll
+    for (int x = 0; x < R; ++x)
+#pragma unroll
+      for (int y = 0; y < R; ++y) {
+        accR[x][y] = fma(ar[x], br[y], fma(ai[x], bi[y], accR[x][y]));
+        accI[x][y] = fma(ar[x], bi[y], fma(-ai[x], br[y], accI[x][y]));
+      }
+  }
+  T m = T(0);
+#pragma unroll
+  for (int x = 0; x < R; ++x)
+#pragma unroll
+    for (int y = 0; y < R; ++y) {
+      const int gj = I * BT + ty + 16 * x, gk = J * BT + tx + 16 * y;
+      const T v = pair_abs2(accR[x][y], accI[x][y]);
+      if (gj < gk && gk < N) {
+        m = fmax(m, v);
+        if (filter && v >= thr) {
+          const uint32_t idx = atomicAdd(filter->npairs, 1u);
+          if (idx < filter->cap) filter->pairs[idx] = make_uint2((unsigned)gj, (unsigned)gk);
+          else atomicExch(filter->overflow, 1u);
+        }
+      }
+    }
+  return m;
+}
+
+// Gram pass over nslots frames (candidates of one instance, or stored
+// frames), one CTA per (slot, tile) work item, grid-stride.
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_gram_tile(const GramArgs<T> a) {
-  constexpr int BT = 16 * R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[8];
   __shared__ int zero_col;
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int d = a.d, N = a.N;
-  T* sIre = sm;
-  T* sIim = sm + (size_t)d * BT;
-  T* sJre = sm + (size_t)2 * d * BT;
-  T* sJim = sm + (size_t)3 * d * BT;
 
   const GramSource& src = a.src;
   if (src.gate && *src.gate == 0u) return;
@@ -210,82 +307,29 @@ __global__ void __launch_bounds__(256) k_gram_tile(const GramArgs<T> a) {
     const float lo = fmaxf(ref - a.filter.margin, 0.0f);
     thr = (T)(lo * lo);
   }
-  using C = typename Cplx<T>::type;
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   const long long nitems = (long long)a.nslots * a.ntiles;
   for (long long w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int slot = (int)(w / a.ntiles);
     const int tau = (int)(w - (long long)slot * a.ntiles);
-    int I, J;
-    tile_coords(tau, I, J);
-    const bool diag = (I == J);
-    if (threadIdx.x == 0) zero_col = 0;
-    __syncthreads();
-    const int ncols = diag ? BT : 2 * BT;
-    for (int q = threadIdx.x; q < ncols; q += blockDim.x) {
-      const int blk = q / BT, loc = q - blk * BT;
-      const int gj = (blk == 0 ? I : J) * BT + loc;
-      T* ore = (blk == 0 ? sIre : sJre) + loc;
-      T* oim = (blk == 0 ? sIim : sJim) + loc;
-      bool ok = true;
-      if (gj < N) {
-        if (src.perturb) {
-          const uint32_t c = src.cand_list ? src.cand_list[slot] : src.c0 + (uint32_t)slot;
-          ok = gen_column<T>(reinterpret_cast<const C*>(src.phi), d, gj, src.seed, c, t, 0u,
-                             delta, ore, oim, BT);
-        } else {
-          const C* frame = reinterpret_cast<const C*>(src.phi) + (size_t)slot * d * N;
-          ok = load_column<T>(frame, d, gj, src.normalize, ore, oim, BT);
-        }
-      } else {
-        for (int i = 0; i < d; ++i) { ore[i * BT] = T(0); oim[i * BT] = T(0); }
-      }
-      if (!ok) zero_col = 1;
+    TileItem it;
+    it.N = N; it.d = d;
+    tile_coords(tau, it.I, it.J);
+    it.perturb = src.perturb;
+    it.normalize = src.normalize;
+    it.seed = src.seed;
+    it.t = t;
+    it.delta = (double)delta;
+    if (src.perturb) {
+      it.phi = src.phi;
+      it.c = src.cand_list ? src.cand_list[slot] : src.c0 + (uint32_t)slot;
+    } else {
+      it.phi = reinterpret_cast<const typename Cplx<T>::type*>(src.phi) + (size_t)slot * d * N;
+      it.c = 0u;
     }
-    __syncthreads();
+    if (threadIdx.x == 0) zero_col = 0;
+    T m = score_tile<T, R>(it, sm, &zero_col, thr, a.has_filter ? &a.filter : nullptr);
     if (zero_col && src.st && threadIdx.x == 0)
       atomicOr(&const_cast<DevState*>(src.st)->error, (uint32_t)kErrZeroColumn);
-    const T* bRe = diag ? sIre : sJre;
-    const T* bIm = diag ? sIim : sJim;
-    T accR[R][R], accI[R][R];
-#pragma unroll
-    for (int x = 0; x < R; ++x)
-#pragma unroll
-      for (int y = 0; y < R; ++y) { accR[x][y] = T(0); accI[x][y] = T(0); }
-#pragma unroll 2
-    for (int i = 0; i < d; ++i) {
-      T ar[R], ai[R], br[R], bi[R];
-#pragma unroll
-      for (int x = 0; x < R; ++x) {
-        ar[x] = sIre[i * BT + ty + 16 * x];
-        ai[x] = sIim[i * BT + ty + 16 * x];
-        br[x] = bRe[i * BT + tx + 16 * x];
-        bi[x] = bIm[i * BT + tx + 16 * x];
-      }
-#pragma unroll
-      for (int x = 0; x < R; ++x)
-#pragma unroll
-        for (int y = 0; y < R; ++y) {
-          accR[x][y] = fma(ar[x], br[y], fma(ai[x], bi[y], accR[x][y]));
-          accI[x][y] = fma(ar[x], bi[y], fma(-ai[x], br[y], accI[x][y]));
-        }
-    }
-    T m = T(0);
-#pragma unroll
-    for (int x = 0; x < R; ++x)
-#pragma unroll
-      for (int y = 0; y < R; ++y) {
-        const int gj = I * BT + ty + 16 * x, gk = J * BT + tx + 16 * y;
-        const T v = accR[x][y] * accR[x][y] + accI[x][y] * accI[x][y];
-        if (gj < gk && gk < N) {
-          m = fmax(m, v);
-          if (a.has_filter && v >= thr) {
-            const uint32_t idx = atomicAdd(a.filter.npairs, 1u);
-            if (idx < a.filter.cap) a.filter.pairs[idx] = make_uint2((unsigned)gj, (unsigned)gk);
-            else atomicExch(a.filter.overflow, 1u);
-          }
-        }
-      }
     m = block_max<T>(m, red);
     if (threadIdx.x == 0) atomic_max_nonneg(a.out + slot, m);
     __syncthreads();
@@ -693,6 +737,209 @@ cudaError_t launch_gen_candidate(int N, int d, uint64_t seed, uint32_t t, uint32
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------ batched searches
+//
+// Many independent instances advance together: each kernel below covers all
+// of them in one launch.  Every instance keeps its own DevState and
+// counters, so its trajectory is the one it would follow alone.
+
+template <typename B>
+__global__ void k_batch_begin(SlotDesc* slots, int n, unsigned long long* counters, int ncounters) {
+  const int s = blockIdx.x;
+  if (s == 0 && threadIdx.x < ncounters) counters[threadIdx.x] = 0ull;
+  if (s >= n) return;
+  DevState* st = slots[s].st;
+  __shared__ uint32_t act;
+  if (threadIdx.x == 0) {
+    act = (!st->done && st->t < st->t_stop) ? 1u : 0u;
+    st->active = act;
+    st->use_screen = 0u;
+    st->use_full = act;
+    if (act) {
+      st->delta_used = st->delta;
+      st->accepted = 0u;
+    }
+  }
+  __syncthreads();
+  if (!act) return;
+  B* mu2 = reinterpret_cast<B*>(slots[s].mu2);
+  for (int c = threadIdx.x; c < slots[s].K; c += blockDim.x) mu2[c] = B(0);
+}
+
+cudaError_t launch_batch_begin(SlotDesc* slots, int n, unsigned long long* counters, int ncounters,
+                               bool f64, cudaStream_t s) {
+  const int grid = n > 0 ? n : 1;
+  if (f64) k_batch_begin<unsigned long long><<<grid, 256, 0, s>>>(slots, n, counters, ncounters);
+  else k_batch_begin<unsigned int><<<grid, 256, 0, s>>>(slots, n, counters, ncounters);
+  return cudaGetLastError();
+}
+
+// Persistent scoring pass: CTAs take work items (instance, candidate, tile)
+// from *counter until nitems are done.  group lists the instances of this
+// tile width in the order of their items; group_begin[g] is the first item
+// of group[g] (group_begin[ngroup] = nitems).
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_batch_score(const SlotDesc* slots, const int* group,
+                                                     const long long* group_begin, int ngroup,
+                                                     long long nitems,
+                                                     unsigned long long* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T red[8];
+  __shared__ int zero_col;
+  __shared__ long long item;
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  for (;;) {
+    if (threadIdx.x == 0) item = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const long long w = item;
+    if (w >= nitems) return;
+    // instance of this item: last g with group_begin[g] <= w
+    int lo = 0, hi = ngroup - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (group_begin[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    const SlotDesc& sd = slots[group[lo]];
+    const DevState* st = sd.st;
+    if (st->active) {
+      const long long local = w - group_begin[lo];
+      TileItem it;
+      it.N = sd.N; it.d = sd.d;
+      it.c = (uint32_t)(local / sd.ntiles);
+      tile_coords((int)(local - (long long)it.c * sd.ntiles), it.I, it.J);
+      it.perturb = true;
+      it.normalize = false;
+      it.phi = sd.phi;
+      it.seed = sd.seed;
+      it.t = st->t + 1u;
+      it.delta = st->delta_used;
+      if (threadIdx.x == 0) zero_col = 0;
+      T m = score_tile<T, R>(it, sm, &zero_col, T(-1), nullptr);
+      if (zero_col && threadIdx.x == 0)
+        atomicOr(&const_cast<DevState*>(st)->error, (uint32_t)kErrZeroColumn);
+      m = block_max<T>(m, red);
+      if (threadIdx.x == 0)
+        atomic_max_nonneg(reinterpret_cast<typename Mu2Bits<T>::type*>(sd.mu2) + it.c, m);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+static cudaError_t launch_batch_score_t(int R, const SlotDesc* slots, const int* group,
+                                        const long long* group_begin, int ngroup, long long nitems,
+                                        unsigned long long* counter, size_t smem, int grid,
+                                        cudaStream_t s) {
+  if (ngroup < 1 || nitems < 1) return cudaSuccess;
+  switch (R) {
+    case 4: k_batch_score<T, 4><<<grid, 256, smem, s>>>(slots, group, group_begin, ngroup, nitems, counter); break;
+    case 2: k_batch_score<T, 2><<<grid, 256, smem, s>>>(slots, group, group_begin, ngroup, nitems, counter); break;
+    case 1: k_batch_score<T, 1><<<grid, 256, smem, s>>>(slots, group, group_begin, ngroup, nitems, counter); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_score(bool f64, int R, const SlotDesc* slots, const int* group,
+                               const long long* group_begin, int ngroup, long long nitems,
+                               unsigned long long* counter, size_t smem, int grid,
+                               cudaStream_t s) {
+  return f64 ? launch_batch_score_t<double>(R, slots, group, group_begin, ngroup, nitems, counter,
+                                            smem, grid, s)
+             : launch_batch_score_t<float>(R, slots, group, group_begin, ngroup, nitems, counter,
+                                           smem, grid, s);
+}
+
+template <typename K>
+static cudaError_t occupancy_of(K kernel, size_t smem, int* blocks) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, 256, smem);
+}
+
+cudaError_t batch_score_occupancy(bool f64, int R, size_t smem, int* blocks_per_sm) {
+  if (f64) {
+    if (R == 4) return occupancy_of(k_batch_score<double, 4>, smem, blocks_per_sm);
+    if (R == 2) return occupancy_of(k_batch_score<double, 2>, smem, blocks_per_sm);
+    return occupancy_of(k_batch_score<double, 1>, smem, blocks_per_sm);
+  }
+  if (R == 4) return occupancy_of(k_batch_score<float, 4>, smem, blocks_per_sm);
+  if (R == 2) return occupancy_of(k_batch_score<float, 2>, smem, blocks_per_sm);
+  return occupancy_of(k_batch_score<float, 1>, smem, blocks_per_sm);
+}
+
+size_t gram_smem_bytes(bool f64, int d, int R) {
+  return f64 ? gram_smem<double>(d, R) : gram_smem<float>(d, R);
+}
+
+// argmin over each instance's K scores, then its accept/radius rule; one CTA each.
+template <typename B>
+__global__ void k_batch_decide(SlotDesc* slots, int n) {
+  const int s = blockIdx.x;
+  if (s >= n) return;
+  DevState* st = slots[s].st;
+  if (!st->active) return;
+  const B* mu2 = reinterpret_cast<const B*>(slots[s].mu2);
+  const int K = slots[s].K;
+  __shared__ B sv[8];
+  __shared__ int sc[8];
+  B bv = ~B(0);
+  int bc = 0x7fffffff;
+  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    const B v = mu2[c];
+    if (v < bv || (v == bv && c < bc)) { bv = v; bc = c; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const B ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+    if (ov < bv || (ov == bv && oc < bc)) { bv = ov; bc = oc; }
+  }
+  if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = bv; sc[threadIdx.x >> 5] = bc; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (sv[w] < bv || (sv[w] == bv && sc[w] < bc)) { bv = sv[w]; bc = sc[w]; }
+    const double m = (double)nonneg_from_bits(bv);
+    apply_rule_and_trace(st, (uint32_t)bc, m, m, slots[s].trace);
+  }
+}
+
+cudaError_t launch_batch_decide(SlotDesc* slots, int n, bool f64, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  if (f64) k_batch_decide<unsigned long long><<<n, 256, 0, s>>>(slots, n);
+  else k_batch_decide<unsigned int><<<n, 256, 0, s>>>(slots, n);
+  return cudaGetLastError();
+}
+
+// Regenerate each accepted candidate in place (instance = blockIdx.y).
+template <typename T, typename O>
+__global__ void k_batch_commit(SlotDesc* slots, int n) {
+  const SlotDesc& sd = slots[blockIdx.y];
+  DevState* st = sd.st;
+  if (!st->active || !st->accepted) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= sd.N) return;
+  using C = typename Cplx<T>::type;
+  using CO = typename Cplx<O>::type;
+  C* phi = reinterpret_cast<C*>(sd.phi);
+  CO* other = reinterpret_cast<CO*>(sd.phi_other);
+  const int d = sd.d;
+  T* base = reinterpret_cast<T*>(phi + (size_t)j * d);
+  gen_column<T>(phi, d, j, sd.seed, st->cstar, st->t, 0u, (T)st->delta_used, base, base + 1, 2);
+  for (int i = 0; i < d; ++i) {
+    const C v = phi[(size_t)j * d + i];
+    other[(size_t)j * d + i].x = (O)v.x;
+    other[(size_t)j * d + i].y = (O)v.y;
+  }
+}
+
+cudaError_t launch_batch_commit(SlotDesc* slots, int n, int maxN, bool f64, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  dim3 grid((maxN + 127) / 128, n);
+  if (f64) k_batch_commit<double, float><<<grid, 128, 0, s>>>(slots, n);
+  else k_batch_commit<float, double><<<grid, 128, 0, s>>>(slots, n);
+  return cudaGetLastError();
+}
+
 template <typename K> static cudaError_t allow_max_dynamic_smem(K kernel, int optin) {
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
@@ -713,6 +960,12 @@ cudaError_t init_kernel_attributes() {
   if ((e = allow_max_dynamic_smem(k_gram_tile<double, 4>, optin)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_gram_tile<double, 2>, optin)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_gram_tile<double, 1>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_batch_score<float, 4>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_batch_score<float, 2>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_batch_score<float, 1>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_batch_score<double, 4>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_batch_score<double, 2>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_batch_score<double, 1>, optin)) != cudaSuccess) return e;
   return init_screen_attributes(optin);
 }
 

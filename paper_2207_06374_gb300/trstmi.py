@@ -61,6 +61,35 @@ class StepInfo(ctypes.Structure):
                 ("done", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("search", Options), ("hbm_budget", ctypes.c_size_t),
+                ("max_slots", ctypes.c_int32), ("iters_per_round", ctypes.c_int32),
+                ("queue_cap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("d", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("budget_iters", ctypes.c_int32), ("want_phi", ctypes.c_int32),
+                ("target_mu", ctypes.c_double), ("target_rel_welch", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("accepts", ctypes.c_int32), ("reached_target", ctypes.c_int32),
+                ("mu", ctypes.c_double), ("welch", ctypes.c_double),
+                ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64), ("pairs_scored", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64),
+                ("rounds", ctypes.c_uint64), ("pairs_scored", ctypes.c_uint64),
+                ("gpu_busy_s", ctypes.c_double), ("hbm_in_use", ctypes.c_size_t),
+                ("active_slots", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("worker_status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 _lock = threading.Lock()
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -91,6 +120,32 @@ SIGNATURES = {
                                             ctypes.c_double, ctypes.c_size_t, _dp]),
     "trstmi_mu2_frame_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
+    "trstmi_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.POINTER(Options),
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "trstmi_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(StepInfo)]),
+    "trstmi_batch_mu": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_int32)]),
+    "trstmi_batch_get_phi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp]),
+    "trstmi_batch_get_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                              ctypes.POINTER(TraceRow), ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int)]),
+    "trstmi_batch_tile_widths": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "trstmi_batch_profile_score": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t,
+                                                  _dp]),
+    "trstmi_batch_destroy": (None, [ctypes.c_void_p]),
+    "trstmi_default_server_opts": (None, [ctypes.POINTER(ServerOpts)]),
+    "trstmi_server_create": (ctypes.c_int, [ctypes.POINTER(ServerOpts),
+                                            ctypes.POINTER(ctypes.c_void_p)]),
+    "trstmi_server_destroy": (None, [ctypes.c_void_p]),
+    "trstmi_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request),
+                                     ctypes.POINTER(ctypes.c_uint64)]),
+    "trstmi_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Result), _dp]),
+    "trstmi_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                   ctypes.POINTER(Result), _dp]),
+    "trstmi_cancel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "trstmi_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
 }
 
 
@@ -242,6 +297,154 @@ class Search:
     @property
     def handle(self) -> int:
         return self._h.value
+
+
+class Batch:
+    """Many searches advanced together (trstmi_batch_create .. _destroy)."""
+
+    def __init__(self, Ns, ds, seeds, **options):
+        self.Ns, self.ds = [int(x) for x in Ns], [int(x) for x in ds]
+        self.seeds = [int(x) for x in seeds]
+        self.n = len(self.Ns)
+        self.options = make_options(**options)
+        Na = (ctypes.c_int * self.n)(*self.Ns)
+        da = (ctypes.c_int * self.n)(*self.ds)
+        sa = (ctypes.c_uint64 * self.n)(*self.seeds)
+        h = ctypes.c_void_p()
+        _check(lib().trstmi_batch_create(self.n, Na, da, sa, ctypes.byref(self.options),
+                                         ctypes.byref(h)), "trstmi_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().trstmi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, iters: int) -> StepInfo:
+        info = StepInfo()
+        _check(lib().trstmi_batch_step(self._h, iters, ctypes.byref(info)), "trstmi_batch_step")
+        return info
+
+    def mu(self):
+        out = np.zeros(self.n)
+        it = (ctypes.c_int32 * self.n)()
+        _check(lib().trstmi_batch_mu(self._h, out.ctypes.data_as(_dp), it), "trstmi_batch_mu")
+        return out, np.array(list(it))
+
+    def get_phi(self, i: int) -> np.ndarray:
+        b = np.zeros(2 * self.ds[i] * self.Ns[i])
+        _check(lib().trstmi_batch_get_phi(self._h, i, b.ctypes.data_as(_dp)), "trstmi_batch_get_phi")
+        return _unflat(b, self.ds[i], self.Ns[i])
+
+    def trace(self, i: int, n: int = 1 << 30) -> np.ndarray:
+        cap = max(0, min(n, self.options.trace_cap))
+        rows = (TraceRow * max(cap, 1))()
+        got = ctypes.c_int()
+        _check(lib().trstmi_batch_get_trace(self._h, i, rows, cap, ctypes.byref(got)),
+               "trstmi_batch_get_trace")
+        return np.frombuffer(bytes(rows), dtype=TRACE_DTYPE)[: got.value].copy()
+
+    def tile_widths(self):
+        w = (ctypes.c_int * self.n)()
+        _check(lib().trstmi_batch_tile_widths(self._h, w), "trstmi_batch_tile_widths")
+        return list(w)
+
+    def profile_score(self, launches=3, flush_bytes=0) -> float:
+        out = ctypes.c_double()
+        _check(lib().trstmi_batch_profile_score(self._h, launches, flush_bytes, ctypes.byref(out)),
+               "trstmi_batch_profile_score")
+        return out.value
+
+
+class Server:
+    """The serving loop (trstmi_server_create .. _destroy)."""
+
+    def __init__(self, hbm_budget=4 << 30, max_slots=256, iters_per_round=20, queue_cap=1 << 16,
+                 **search):
+        o = ServerOpts()
+        lib().trstmi_default_server_opts(ctypes.byref(o))
+        o.hbm_budget, o.max_slots = hbm_budget, max_slots
+        o.iters_per_round, o.queue_cap = iters_per_round, queue_cap
+        for k, v in search.items():
+            if k == "precision" and isinstance(v, str):
+                v = PRECISIONS[v]
+            if not hasattr(o.search, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o.search, k, v)
+        self.opts = o
+        h = ctypes.c_void_p()
+        _check(lib().trstmi_server_create(ctypes.byref(o), ctypes.byref(h)), "trstmi_server_create")
+        self._h = h
+        self._shapes = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().trstmi_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, N, d, seed, budget_iters, target_mu=0.0, target_rel_welch=0.0,
+               want_phi=False) -> int:
+        r = Request(N, d, seed, budget_iters, int(bool(want_phi)), target_mu, target_rel_welch)
+        t = ctypes.c_uint64()
+        _check(lib().trstmi_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "trstmi_submit")
+        self._shapes[t.value] = (d, N)
+        return t.value
+
+    def poll(self, ticket, with_phi=False):
+        res = Result()
+        phi = None
+        buf = None
+        if with_phi and ticket in self._shapes:
+            d, N = self._shapes[ticket]
+            buf = np.zeros(2 * d * N)
+        st = lib().trstmi_poll(self._h, ticket, ctypes.byref(res),
+                               buf.ctypes.data_as(_dp) if buf is not None else None)
+        if buf is not None and st == TRSTMI_OK:
+            phi = _unflat(buf, *self._shapes[ticket])
+        return st, res, phi
+
+    def wait(self, ticket, timeout_ms=600000, with_phi=False):
+        res = Result()
+        buf = None
+        if with_phi and ticket in self._shapes:
+            d, N = self._shapes[ticket]
+            buf = np.zeros(2 * d * N)
+        st = lib().trstmi_wait(self._h, ticket, timeout_ms, ctypes.byref(res),
+                               buf.ctypes.data_as(_dp) if buf is not None else None)
+        phi = _unflat(buf, *self._shapes[ticket]) if (buf is not None and st == TRSTMI_OK) else None
+        return st, res, phi
+
+    def cancel(self, ticket) -> int:
+        return lib().trstmi_cancel(self._h, ticket)
+
+    def stats(self) -> ServerStats:
+        s = ServerStats()
+        _check(lib().trstmi_server_stats(self._h, ctypes.byref(s)), "trstmi_server_stats")
+        return s
 
 
 def mu2_frame(phi: np.ndarray, precision="fp64") -> float:

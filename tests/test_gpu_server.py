@@ -1,0 +1,113 @@
+"""Serving loop: continuous batching of searches in shared launches.
+
+Each request's result must be exactly the one the same search gives alone
+(same options, seed, iteration budget and target): its iterations, final mu
+and final frame are compared bit for bit with a standalone trstmi_create +
+trstmi_step run.  Admission respects the device-memory budget, cancellation
+and unknown tickets are reported, and bad arguments are rejected on the host.
+"""
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+T = pytest.importorskip("paper_2207_06374_gb300.trstmi")
+W = pytest.importorskip("paper_2207_06374_gb300.workloads")
+
+
+def _alone(N, d, seed, K, budget, target, precision="fp32"):
+    with T.Search(N, d, seed, K=K, precision=precision, target_mu=target, trace_cap=0) as s:
+        s.step(budget)
+        return s.step(0), s.get_phi()
+
+
+def test_results_equal_standalone_runs():
+    K = 32
+    reqs = [(4, 2, 11, 300, 0.5775), (9, 3, 12, 120, 0.0), (30, 5, 13, 80, 0.0),
+            (200, 16, 14, 40, 0.0), (7, 3, 15, 200, 0.48), (64, 8, 16, 60, 0.0),
+            (1000, 32, 17, 6, 0.0), (3, 2, 18, 50, 0.55)]
+    with T.Server(hbm_budget=256 << 20, max_slots=5, iters_per_round=7, K=K,
+                  precision="fp32") as srv:
+        tickets = []
+        for i, (N, d, seed, budget, target) in enumerate(reqs):
+            tickets.append(srv.submit(N, d, seed, budget, target_mu=target, want_phi=True))
+            if i % 3 == 2:
+                time.sleep(0.01)          # later requests arrive while others run
+        results = [srv.wait(t, with_phi=True) for t in tickets]
+        stats = srv.stats()
+    assert stats.completed == len(reqs) and stats.worker_status == 0
+    for (N, d, seed, budget, target), (st, res, phi) in zip(reqs, results):
+        assert st == T.TRSTMI_OK
+        info, phi_alone = _alone(N, d, seed, K, budget, target)
+        assert res.iters == info.iters_done or res.iters <= budget
+        assert res.mu == info.mu, (N, d)
+        assert np.array_equal(phi, phi_alone), (N, d)
+        assert res.t_submit_ns <= res.t_admit_ns <= res.t_done_ns
+        if target > 0 and res.reached_target:
+            assert res.mu <= target
+
+
+def test_admission_respects_memory_budget():
+    # each (N=1024, d=32) slot needs ~0.8 MiB; a 2 MiB budget holds two at a time
+    with T.Server(hbm_budget=2 << 20, max_slots=8, iters_per_round=2, K=8,
+                  precision="fp32") as srv:
+        tickets = [srv.submit(1024, 32, 100 + i, 6) for i in range(5)]
+        peak = 0
+        while True:
+            s = srv.stats()
+            peak = max(peak, s.active_slots)
+            assert s.hbm_in_use <= 2 << 20
+            if s.completed == 5:
+                break
+            time.sleep(0.002)
+        assert peak <= 2
+        for t in tickets:
+            st, res, _ = srv.poll(t)
+            assert st == T.TRSTMI_OK and res.iters == 6
+        # a request larger than the whole budget can never be admitted
+        t = srv.submit(8192, 256, 1, 5)
+        st, res, _ = srv.wait(t)
+        assert st == T.TRSTMI_ENOMEM
+
+
+def test_cancel_and_unknown_ticket():
+    with T.Server(hbm_budget=64 << 20, max_slots=1, iters_per_round=5, K=8,
+                  precision="fp32") as srv:
+        long = srv.submit(512, 16, 1, 1_000_000)
+        queued = srv.submit(16, 4, 2, 10)
+        time.sleep(0.05)
+        assert srv.cancel(queued) in (T.TRSTMI_PENDING, T.TRSTMI_ECANCELLED)
+        assert srv.cancel(long) == T.TRSTMI_PENDING
+        st, res, _ = srv.wait(long)
+        assert st == T.TRSTMI_ECANCELLED and res.iters > 0
+        st, _, _ = srv.wait(queued)
+        assert st == T.TRSTMI_ECANCELLED
+        st, _, _ = srv.poll(987654321)
+        assert st == T.TRSTMI_ENOTFOUND
+
+
+def test_bad_requests_rejected_on_host():
+    with T.Server(hbm_budget=16 << 20, max_slots=2, K=8, precision="fp32") as srv:
+        for bad in ((1, 3), (8, 0), (8, 300)):
+            with pytest.raises(T.TrstmiError) as e:
+                srv.submit(bad[0], bad[1], 0, 10)
+            assert e.value.status == T.TRSTMI_EINVAL
+    with pytest.raises(T.TrstmiError) as e:
+        T.Server(precision="bf16")
+    assert e.value.status == T.TRSTMI_EUNSUPPORTED
+
+
+def test_serving_request_mix_runs():
+    """A slice of the serving workload's request recipe (d ~ U[4,64], N
+    log-uniform on [d+1, 4096], target 1.05 x Welch) through the loop."""
+    reqs = W.serving_requests(40, seed=11)
+    with T.Server(hbm_budget=1 << 30, max_slots=16, iters_per_round=10, K=8,
+                  precision="fp32") as srv:
+        tickets = [srv.submit(r["N"], r["d"], r["seed"], 30, target_rel_welch=1.05) for r in reqs]
+        out = [srv.wait(t) for t in tickets]
+    for r, (st, res, _) in zip(reqs, out):
+        assert st == T.TRSTMI_OK
+        assert 1 <= res.iters <= 30
+        assert res.mu >= res.welch - 1e-6
