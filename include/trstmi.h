@@ -78,7 +78,9 @@ typedef struct trstmi_options {
   /* screen modes: an iteration ranks its candidates with the tensor-core
      screen while its radius is >= screen_min_delta, and with the binary32
      Gram of every candidate below it, where candidate coherences differ by
-     less than the screen's resolution (default 0.01; 0 = always screen) */
+     less than the screen's resolution (default 0.01; 0 = always screen).
+     Shapes the screen kernel does not take (d > 32 or N > 1536) always rank
+     with the binary32 Gram; the re-score and certification are unchanged. */
   double screen_min_delta;
   void *stream;         /* cudaStream_t to issue on, or NULL */
   int32_t device;       /* CUDA device ordinal (default 0) */
@@ -185,8 +187,10 @@ const char *trstmi_last_error(void);
  * trstmi_step would give it alone (same options).  Tile widths (16, 32 or 64
  * columns) are chosen per (d, ceil log2 N) by an autotuner that times the
  * scoring pass on the instances themselves at creation; choices are cached
- * for the process.  Precision: TRSTMI_FP32 (complex64 storage, binary32
- * Gram) or TRSTMI_FP64; screen modes return TRSTMI_EUNSUPPORTED here.
+ * for the process.  Every precision mode is accepted; in the screen modes the
+ * tensor-core screen of every instance it takes runs as one shared launch
+ * over all (instance, candidate) pairs, then re-score, certification, accept
+ * rule and commit run as shared launches too.
  */
 typedef struct trstmi_batch *trstmi_batch_handle;
 
@@ -208,10 +212,11 @@ int trstmi_batch_get_trace(trstmi_batch_handle b, int i, trstmi_trace_row *rows,
                            int *n_out);
 /* Tile width (columns) the autotuner chose for every instance (n ints). */
 int trstmi_batch_tile_widths(trstmi_batch_handle b, int *widths);
-/* Measurement: mean device time of one scoring pass over all instances (the
- * persistent scoring launches of one iteration, bracketed by CUDA events;
- * flush_bytes of scratch rewritten before each, outside the events).  Does
- * not advance any instance. */
+/* Measurement: mean device time of one ranking pass over all instances (the
+ * persistent scoring launches of one iteration, or in the screen modes the
+ * shared tensor-core screen launch, bracketed by CUDA events; flush_bytes of
+ * scratch rewritten before each, outside the events).  Does not advance any
+ * instance. */
 int trstmi_batch_profile_score(trstmi_batch_handle b, int launches, size_t flush_bytes,
                                double *avg_ms);
 /* Frees everything.  Safe on NULL. */
@@ -228,7 +233,10 @@ void trstmi_batch_destroy(trstmi_batch_handle b);
  * boundary once it reached its target, spent its iteration budget or was
  * cancelled.  Every search keeps its own state, so its result is exactly the
  * one trstmi_create + trstmi_step give alone with the same options, seed and
- * budget.  Precision: TRSTMI_FP32 or TRSTMI_FP64 ranking and acceptance.
+ * budget.  Every precision mode is accepted; in the screen modes each slot
+ * also holds its top-k, certification scratch and a pair list of up to 65536
+ * pairs,
+ * and the slot's device memory grows accordingly.
  */
 typedef struct trstmi_server trstmi_server;
 

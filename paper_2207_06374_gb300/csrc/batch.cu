@@ -1,15 +1,17 @@
 // Batched searches (trstmi_batch_*, include/trstmi.h): many independent
 // instances of different (N, d) advanced together, each iteration one set of
-// shared launches for all of them, replayed from a captured CUDA graph.
+// shared launches for all of them (BatchPlan), replayed from a captured CUDA
+// graph.
 //
 // Every instance keeps its own device state, seed and counters, and a pair's
 // |G|^2 is computed by the same sequential chain whatever the tile width, so
-// an instance follows exactly the trajectory it follows alone.
+// an instance follows exactly the trajectory it follows alone (the screen
+// scores one candidate per CTA in either form, so the same holds there).
 //
-// Tile widths: the scoring kernel is instantiated for tiles of 16, 32 and 64
-// columns.  The autotuner times the persistent scoring pass on the actual
-// instances of each (d, ceil log2 N) bucket at every feasible width and
-// keeps the fastest; the choice is cached for the process.
+// Tile widths: the fp32/fp64 scoring kernel is instantiated for tiles of 16,
+// 32 and 64 columns.  The autotuner times the persistent scoring pass on the
+// actual instances of each (d, ceil log2 N) bucket at every feasible width
+// and keeps the fastest; the choice is cached for the process.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,6 +31,13 @@ using namespace trstmi;
 namespace {
 
 constexpr int kBatchGraphChunk = 16;
+// Pair list of the certification: the standalone instance's 65536 pairs, or
+// every pair when there are fewer, so that the list overflows exactly when a
+// standalone run's does.
+uint32_t slot_pair_cap(int N) {
+  const unsigned long long all = (unsigned long long)N * (unsigned long long)(N - 1) / 2;
+  return (uint32_t)std::min<unsigned long long>(all, 1ull << 16);
+}
 
 __global__ void k_batch_set_stop(SlotDesc* slots, int n, uint32_t iters) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -49,6 +58,16 @@ __global__ void k_batch_set_mu2cur(SlotDesc* slots, int n) {
   st->done = (st->mu2_cur <= st->target2) ? 1u : 0u;
 }
 
+// Screen modes: the initial frame is certified in binary64 like every later
+// one, here simply by its binary64 mu^2 over all pairs (cert64 of the slot).
+__global__ void k_batch_set_mu2cur_cert(SlotDesc* slots, int n) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  DevState* st = slots[s].st;
+  st->mu2_cur = nonneg_from_bits(*slots[s].cert64);
+  st->done = (st->mu2_cur <= st->target2) ? 1u : 0u;
+}
+
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, int> g_tuned_R[2];   // [f64] (d, ceil log2 N) -> R
 
@@ -62,6 +81,8 @@ int ntiles_for(int N, int R) {
   const int nb = (N + 16 * R - 1) / (16 * R);
   return nb * (nb + 1) / 2;
 }
+
+bool is_screen_prec(int p) { return p == TRSTMI_BF16_SCREEN || p == TRSTMI_FP16_SCREEN; }
 
 }  // namespace
 
@@ -77,12 +98,66 @@ void store_width(bool f64, int d, int N, int R) {
   g_tuned_R[f64][{d, ceil_log2(N)}] = R;
 }
 int tiles_at_width(int N, int R) { return ntiles_for(N, R); }
+
+bool width_feasible(bool f64, int d, int N, int R) {
+  if (gram_smem_bytes(f64, d, R) > 200 * 1024) return false;
+  return R == 1 || 16 * R < 2 * N;     // do not pad tiny N
+}
+
+// Times one full scoring pass of the given instances at width R (ms); the
+// instances must be active with use_full set.  ids/begin scratch of at least
+// ids.size() (+1) entries is passed in.
+int time_width(const std::vector<SlotDesc>& h, SlotDesc* d_slots, const std::vector<int>& ids,
+               bool f64, int R, int num_sms, int* d_ids, long long* d_begin,
+               unsigned long long* d_counter, cudaStream_t s, float* ms) {
+  std::vector<SlotDesc> tmp = h;
+  std::vector<long long> begin(ids.size() + 1, 0);
+  size_t smem = 0;
+  for (size_t q = 0; q < ids.size(); ++q) {
+    SlotDesc& sd = tmp[ids[q]];
+    sd.R = R;
+    sd.ntiles = ntiles_for(sd.N, R);
+    begin[q + 1] = begin[q] + (long long)sd.K * sd.ntiles;
+    smem = std::max(smem, gram_smem_bytes(f64, sd.d, R));
+  }
+  int per_sm = 0;
+  if (batch_score_occupancy(f64, R, smem, &per_sm) != cudaSuccess || per_sm < 1) return TRSTMI_ECUDA;
+  const int grid = (int)std::min<long long>(begin.back(), (long long)num_sms * per_sm);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TRSTMI_ECUDA;
+  int rc = TRSTMI_OK;
+  if (cudaMemcpyAsync(d_slots, tmp.data(), sizeof(SlotDesc) * tmp.size(), cudaMemcpyHostToDevice, s) ||
+      cudaMemcpyAsync(d_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice, s) ||
+      cudaMemcpyAsync(d_begin, begin.data(), sizeof(long long) * begin.size(), cudaMemcpyHostToDevice, s))
+    rc = TRSTMI_ECUDA;
+  float best = 1e30f;
+  for (int rep = 0; rep < 3 && rc == TRSTMI_OK; ++rep) {
+    float t = 0.f;
+    if (cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s) ||
+        cudaEventRecord(e0, s) ||
+        launch_batch_score(f64, R, d_slots, d_ids, d_begin, (int)ids.size(), begin.back(),
+                           d_counter, smem, grid, s, kPassFull) ||
+        cudaEventRecord(e1, s) || cudaEventSynchronize(e1) || cudaEventElapsedTime(&t, e0, e1)) {
+      rc = TRSTMI_ECUDA;
+      break;
+    }
+    if (rep > 0) best = std::min(best, t);   // the first launch warms up
+  }
+  // restore the table
+  if (cudaMemcpyAsync(d_slots, h.data(), sizeof(SlotDesc) * h.size(), cudaMemcpyHostToDevice, s))
+    rc = TRSTMI_ECUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  *ms = best;
+  return rc;
+}
 }  // namespace trstmi
 
 struct trstmi_batch {
   int n = 0;
   trstmi_options opt{};
-  bool f64 = false;
+  bool f64 = false, screen = false;
   int num_sms = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -91,163 +166,57 @@ struct trstmi_batch {
   std::vector<uint64_t> seed;
   std::vector<SlotDesc> h_slots;
   SlotDesc* d_slots = nullptr;
-  int maxN = 0;
-  struct Group {
-    int R = 1;
-    int* d_ids = nullptr;
-    long long* d_begin = nullptr;
-    int count = 0;
-    long long nitems = 0;
-    size_t smem = 0;
-    int grid = 0;
-  };
-  std::vector<Group> groups;
-  unsigned long long* d_counters = nullptr;
+  uint32_t* d_err = nullptr;
+  int* d_scratch_ids = nullptr;
+  long long* d_scratch_begin = nullptr;
+  BatchPlan plan;
   std::map<int, cudaGraphExec_t> graphs;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  std::vector<void*> extra;   // group tables (cudaMalloc'd)
 };
 
 namespace {
 
-#define BTRY(expr)                                     \
-  do {                                                 \
+#define BTRY(expr)                                                          \
+  do {                                                                      \
     if ((expr) != cudaSuccess) { cudaGetLastError(); return TRSTMI_ECUDA; } \
   } while (0)
-
-int build_group(trstmi_batch* b, int R, std::vector<int> ids, trstmi_batch::Group* g) {
-  // heaviest instances first: their items are handed out first
-  auto cost = [&](int i) {
-    return (double)b->h_slots[i].K * ntiles_for(b->N[i], R) * (16.0 * R) * (16.0 * R) * b->d[i];
-  };
-  std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) { return cost(x) > cost(y); });
-  std::vector<long long> begin(ids.size() + 1, 0);
-  size_t smem = 0;
-  for (size_t q = 0; q < ids.size(); ++q) {
-    const int i = ids[q];
-    const long long items = (long long)b->h_slots[i].K * ntiles_for(b->N[i], R);
-    begin[q + 1] = begin[q] + items;
-    smem = std::max(smem, gram_smem_bytes(b->f64, b->d[i], R));
-  }
-  g->R = R;
-  g->count = (int)ids.size();
-  g->nitems = begin.back();
-  g->smem = smem;
-  int per_sm = 0;
-  BTRY(batch_score_occupancy(b->f64, R, smem, &per_sm));
-  if (per_sm < 1) return TRSTMI_EUNSUPPORTED;
-  g->grid = (int)std::min<long long>(g->nitems, (long long)b->num_sms * per_sm);
-  BTRY(cudaMalloc(&g->d_ids, sizeof(int) * std::max<size_t>(ids.size(), 1)));
-  BTRY(cudaMalloc(&g->d_begin, sizeof(long long) * begin.size()));
-  b->extra.push_back(g->d_ids);
-  b->extra.push_back(g->d_begin);
-  BTRY(cudaMemcpy(g->d_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice));
-  BTRY(cudaMemcpy(g->d_begin, begin.data(), sizeof(long long) * begin.size(),
-                  cudaMemcpyHostToDevice));
-  return TRSTMI_OK;
-}
-
-bool width_feasible(bool f64, int d, int N, int R) {
-  if (gram_smem_bytes(f64, d, R) > 200 * 1024) return false;
-  return R == 1 || 16 * R < 2 * N;     // do not pad tiny N
-}
-
-int apply_widths(trstmi_batch* b, const std::vector<int>& R_of) {
-  for (int i = 0; i < b->n; ++i) {
-    b->h_slots[i].R = R_of[i];
-    b->h_slots[i].ntiles = ntiles_for(b->N[i], R_of[i]);
-  }
-  b->groups.clear();
-  for (int R : {4, 2, 1}) {
-    std::vector<int> ids;
-    for (int i = 0; i < b->n; ++i)
-      if (R_of[i] == R) ids.push_back(i);
-    if (ids.empty()) continue;
-    trstmi_batch::Group g;
-    int rc = build_group(b, R, ids, &g);
-    if (rc) return rc;
-    b->groups.push_back(g);
-  }
-  BTRY(cudaMemcpy(b->d_slots, b->h_slots.data(), sizeof(SlotDesc) * b->n, cudaMemcpyHostToDevice));
-  return TRSTMI_OK;
-}
-
-// Times one scoring pass of the given instances at width R (ms, CUDA events).
-int time_width(trstmi_batch* b, const std::vector<int>& ids, int R, float* ms) {
-  // the descriptors must carry this width while it is timed
-  std::vector<SlotDesc> saved = b->h_slots;
-  for (int i : ids) { b->h_slots[i].R = R; b->h_slots[i].ntiles = ntiles_for(b->N[i], R); }
-  BTRY(cudaMemcpy(b->d_slots, b->h_slots.data(), sizeof(SlotDesc) * b->n, cudaMemcpyHostToDevice));
-  trstmi_batch::Group g;
-  int rc = build_group(b, R, ids, &g);
-  if (rc) { b->h_slots = saved; return rc; }
-  cudaStream_t s = b->stream;
-  float best = 1e30f;
-  for (int rep = 0; rep < 3 && rc == TRSTMI_OK; ++rep) {
-    if (cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned long long), s) != cudaSuccess ||
-        cudaEventRecord(b->ev0, s) != cudaSuccess ||
-        launch_batch_score(b->f64, R, b->d_slots, g.d_ids, g.d_begin, g.count, g.nitems,
-                           b->d_counters, g.smem, g.grid, s) != cudaSuccess ||
-        cudaEventRecord(b->ev1, s) != cudaSuccess || cudaEventSynchronize(b->ev1) != cudaSuccess) {
-      rc = TRSTMI_ECUDA;
-      break;
-    }
-    float t = 0.f;
-    cudaEventElapsedTime(&t, b->ev0, b->ev1);
-    if (rep > 0) best = std::min(best, t);   // first launch warms up
-  }
-  b->h_slots = saved;
-  *ms = best;
-  return rc;
-}
 
 // Chooses every instance's tile width: cached per (d, ceil log2 N), measured
 // on the instances of a bucket when it is first seen.
 int autotune(trstmi_batch* b) {
+  const bool f64s = b->f64;   // width of the fp32 (or fp64) full pass
   std::map<std::pair<int, int>, std::vector<int>> buckets;
   for (int i = 0; i < b->n; ++i) buckets[{b->d[i], ceil_log2(b->N[i])}].push_back(i);
-  std::vector<int> R_of(b->n, 1);
-  // instances must be active (and not advance) while widths are timed
+  // instances active with use_full while widths are timed (not advanced)
   k_batch_set_stop<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->d_slots, b->n, 1u);
   BTRY(cudaGetLastError());
-  BTRY(launch_batch_begin(b->d_slots, b->n, b->d_counters, 1, b->f64, b->stream));
+  BTRY(launch_batch_begin(b->d_slots, b->n, b->plan.d_counters, BatchPlan::kCounters, f64s, false,
+                          b->stream));
   for (auto& kv : buckets) {
-    int R = -1;
-    {
-      std::lock_guard<std::mutex> g(g_tune_mu);
-      auto it = g_tuned_R[b->f64].find(kv.first);
-      if (it != g_tuned_R[b->f64].end()) R = it->second;
-    }
-    if (R < 0) {
+    int R = cached_width(f64s, kv.first.first, b->N[kv.second[0]]);
+    if (R <= 0) {
       float best = 1e30f;
       for (int cand : {1, 2, 4}) {
         bool ok = true;
-        for (int i : kv.second) ok = ok && width_feasible(b->f64, b->d[i], b->N[i], cand);
+        for (int i : kv.second) ok = ok && width_feasible(f64s, b->d[i], b->N[i], cand);
         if (!ok) continue;
         float ms = 0.f;
-        int rc = time_width(b, kv.second, cand, &ms);
+        int rc = time_width(b->h_slots, b->d_slots, kv.second, f64s, cand, b->num_sms,
+                            b->d_scratch_ids, b->d_scratch_begin, b->plan.d_counters, b->stream, &ms);
         if (rc) return rc;
         if (ms < best) { best = ms; R = cand; }
       }
-      if (R < 0) R = 1;
-      std::lock_guard<std::mutex> g(g_tune_mu);
-      g_tuned_R[b->f64][kv.first] = R;
+      if (R <= 0) R = 1;
+      store_width(f64s, kv.first.first, b->N[kv.second[0]], R);
     }
-    for (int i : kv.second) R_of[i] = R;
+    for (int i : kv.second) {
+      b->h_slots[i].R = R;
+      b->h_slots[i].ntiles = ntiles_for(b->N[i], R);
+    }
   }
-  return apply_widths(b, R_of);
-}
-
-int enqueue_batch_iteration(trstmi_batch* b, cudaStream_t s) {
-  BTRY(launch_batch_begin(b->d_slots, b->n, b->d_counters, (int)b->groups.size(), b->f64, s));
-  for (size_t g = 0; g < b->groups.size(); ++g) {
-    const auto& G = b->groups[g];
-    BTRY(launch_batch_score(b->f64, G.R, b->d_slots, G.d_ids, G.d_begin, G.count, G.nitems,
-                            b->d_counters + g, G.smem, G.grid, s));
-  }
-  BTRY(launch_batch_decide(b->d_slots, b->n, b->f64, s));
-  BTRY(launch_batch_commit(b->d_slots, b->n, b->maxN, b->f64, s));
-  return TRSTMI_OK;
+  BTRY(cudaMemcpyAsync(b->d_slots, b->h_slots.data(), sizeof(SlotDesc) * b->n,
+                       cudaMemcpyHostToDevice, b->stream));
+  return b->plan.rebuild(b->h_slots, b->opt.precision, b->stream);
 }
 
 int batch_graph(trstmi_batch* b, int iters, cudaGraphExec_t* out) {
@@ -256,7 +225,8 @@ int batch_graph(trstmi_batch* b, int iters, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   BTRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   int rc = TRSTMI_OK;
-  for (int i = 0; i < iters && rc == TRSTMI_OK; ++i) rc = enqueue_batch_iteration(b, b->stream);
+  for (int i = 0; i < iters && rc == TRSTMI_OK; ++i)
+    rc = b->plan.enqueue_iteration(b->d_slots, b->n, b->d_err, b->stream);
   cudaError_t e = cudaStreamEndCapture(b->stream, &g);
   if (rc || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -290,7 +260,7 @@ void trstmi_batch_destroy(trstmi_batch_handle b) {
   cudaSetDevice(b->opt.device);
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
-  for (void* p : b->extra) cudaFree(p);
+  b->plan.destroy();
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
   if (b->block) cudaFree(b->block);
@@ -305,22 +275,25 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
   if (n < 1 || !N || !d || !seeds) return TRSTMI_EINVAL;
   trstmi_options o;
   if (opt) o = *opt; else trstmi_default_options(&o);
-  if (o.precision != TRSTMI_FP32 && o.precision != TRSTMI_FP64) return TRSTMI_EUNSUPPORTED;
+  if (o.precision < TRSTMI_FP64 || o.precision > TRSTMI_FP16_SCREEN) return TRSTMI_EINVAL;
+  const bool screen = is_screen_prec(o.precision);
   if (o.K < 1 || o.trace_cap < 0 || !(o.delta0 > 0) || !(o.gamma_inc >= 1) ||
-      !(o.gamma_dec > 0 && o.gamma_dec <= 1) || !(o.delta_min >= 0) || !(o.delta_max >= o.delta_min))
+      !(o.gamma_dec > 0 && o.gamma_dec <= 1) || !(o.delta_min >= 0) ||
+      !(o.delta_max >= o.delta_min) || !(o.screen_min_delta >= 0))
     return TRSTMI_EINVAL;
+  if (screen && (o.topk < 1 || o.topk > 64 || o.topk > o.K)) return TRSTMI_EINVAL;
   for (int i = 0; i < n; ++i)
     if (N[i] < 2 || d[i] < 1 || d[i] > kMaxD || (long long)N[i] * ((d[i] + 1) / 2) >= (1ll << 32))
       return TRSTMI_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return TRSTMI_ECUDA;
   if (o.device < 0 || o.device >= ndev) return TRSTMI_EINVAL;
-  if (cudaSetDevice(o.device) != cudaSuccess) return TRSTMI_ECUDA;
-  if (init_kernel_attributes() != cudaSuccess) return TRSTMI_ECUDA;
+  if (cudaSetDevice(o.device) != cudaSuccess || init_kernel_attributes() != cudaSuccess)
+    return TRSTMI_ECUDA;
 
   trstmi_batch* b = new (std::nothrow) trstmi_batch();
   if (!b) return TRSTMI_ENOMEM;
-  b->n = n; b->opt = o; b->f64 = (o.precision == TRSTMI_FP64);
+  b->n = n; b->opt = o; b->f64 = (o.precision == TRSTMI_FP64); b->screen = screen;
   b->N.assign(N, N + n); b->d.assign(d, d + n); b->seed.assign(seeds, seeds + n);
   if (cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess) {
     delete b;
@@ -328,30 +301,39 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
   }
   if (o.stream) {
     b->stream = (cudaStream_t)o.stream;
-  } else {
-    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      delete b;
-      return TRSTMI_ECUDA;
-    }
+  } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess) {
     b->own_stream = true;
+  } else {
+    delete b;
+    return TRSTMI_ECUDA;
   }
-  // one arena: states, descriptors, counters, then per instance frames, scores, trace
+  // one arena: states, descriptors, error word, scratch tables, then per
+  // instance frames, scores, trace and (screen modes) the certification scratch
   auto up = [](size_t x) { return (x + 255) / 256 * 256; };
   const size_t K = (size_t)o.K, tcap = (size_t)std::max(o.trace_cap, 1);
+  const size_t tk = screen ? (size_t)o.topk : 0;
   size_t off = 0;
   const size_t o_st = off; off = up(off + sizeof(DevState) * n);
   const size_t o_sl = off; off = up(off + sizeof(SlotDesc) * n);
-  const size_t o_ct = off; off = up(off + sizeof(unsigned long long) * 8);
-  std::vector<size_t> o_phi64(n), o_phi32(n), o_mu2(n), o_tr(n);
+  const size_t o_er = off; off = up(off + sizeof(uint32_t));
+  const size_t o_ids = off; off = up(off + sizeof(int) * n);
+  const size_t o_beg = off; off = up(off + sizeof(long long) * (n + 1));
+  std::vector<size_t> o_phi64(n), o_phi32(n), o_mu2(n), o_tr(n), o_scr(n);
   for (int i = 0; i < n; ++i) {
     const size_t nd = (size_t)N[i] * d[i];
     o_phi64[i] = off; off = up(off + nd * sizeof(double2));
     o_phi32[i] = off; off = up(off + nd * sizeof(float2));
     o_mu2[i] = off; off = up(off + K * sizeof(unsigned long long));
     o_tr[i] = off; off = up(off + tcap * sizeof(TraceRowDev));
-    b->maxN = std::max(b->maxN, N[i]);
+    if (screen) {
+      o_scr[i] = off;
+      off += 2 * up(tk * sizeof(uint32_t)) + up(nd * sizeof(double2)) +
+            up(nd * sizeof(float2)) + up(4 * sizeof(uint32_t)) + up(sizeof(unsigned long long)) +
+            up((size_t)slot_pair_cap(N[i]) * sizeof(uint2));
+    }
   }
-  if (cudaMalloc(&b->block, off) != cudaSuccess) {
+  if (cudaMalloc(&b->block, off) != cudaSuccess ||
+      b->plan.init(n, screen ? (long long)n * o.K : 0, b->num_sms) != TRSTMI_OK) {
     cudaGetLastError();
     trstmi_batch_destroy(b);
     return TRSTMI_ENOMEM;
@@ -359,11 +341,15 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
   char* base = (char*)b->block;
   DevState* states = (DevState*)(base + o_st);
   b->d_slots = (SlotDesc*)(base + o_sl);
-  b->d_counters = (unsigned long long*)(base + o_ct);
+  b->d_err = (uint32_t*)(base + o_er);
+  b->d_scratch_ids = (int*)(base + o_ids);
+  b->d_scratch_begin = (long long*)(base + o_beg);
   b->h_slots.resize(n);
   std::vector<DevState> s0(n);
   for (int i = 0; i < n; ++i) {
+    const size_t nd = (size_t)N[i] * d[i];
     SlotDesc& sd = b->h_slots[i];
+    std::memset(&sd, 0, sizeof(sd));
     sd.st = states + i;
     double2* p64 = (double2*)(base + o_phi64[i]);
     float2* p32 = (float2*)(base + o_phi32[i]);
@@ -372,8 +358,20 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
     sd.mu2 = base + o_mu2[i];
     sd.trace = (TraceRowDev*)(base + o_tr[i]);
     sd.seed = seeds[i];
-    sd.N = N[i]; sd.d = d[i]; sd.K = o.K; sd.R = 1; sd.ntiles = ntiles_for(N[i], 1); sd.pad = 0;
-    sd.item_begin = 0;
+    sd.N = N[i]; sd.d = d[i]; sd.K = o.K; sd.R = 1; sd.ntiles = ntiles_for(N[i], 1);
+    if (screen) {
+      char* q = base + o_scr[i];
+      sd.screen = screen_supported(N[i], d[i]) ? 1 : 0;
+      sd.topk = (uint32_t*)q; q += up(tk * sizeof(uint32_t));
+      sd.mu2_top = (unsigned int*)q; q += up(tk * sizeof(uint32_t));
+      sd.cand64 = (double2*)q; q += up(nd * sizeof(double2));
+      sd.cand32 = (float2*)q; q += up(nd * sizeof(float2));
+      sd.cert32 = (unsigned int*)q; q += up(4 * sizeof(uint32_t));
+      sd.cert64 = (unsigned long long*)q; q += up(sizeof(unsigned long long));
+      sd.pairs = (uint2*)q;
+      sd.topk_n = o.topk;
+      sd.pair_cap = slot_pair_cap(sd.N);
+    }
     DevState& s = s0[i];
     std::memset(&s, 0, sizeof(s));
     s.delta = o.delta0; s.delta_used = o.delta0;
@@ -398,14 +396,20 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
     if (launch_init_frame(N[i], d[i], seeds[i], p64, p32, sd.st, s) != cudaSuccess) rc = TRSTMI_ECUDA;
     GramSource src{};
     src.perturb = false;
-    src.phi = sd.phi;
-    cudaError_t e = b->f64
-        ? launch_gram_f64(N[i], d[i], 1, src, (unsigned long long*)sd.mu2, b->num_sms, s)
-        : launch_gram_f32(N[i], d[i], 1, src, (unsigned int*)sd.mu2, nullptr, b->num_sms, s);
+    cudaError_t e;
+    if (screen) {          // binary64 over all pairs of the initial frame
+      src.phi = p64;
+      e = launch_gram_f64(N[i], d[i], 1, src, sd.cert64, b->num_sms, s);
+    } else {
+      src.phi = sd.phi;
+      e = b->f64 ? launch_gram_f64(N[i], d[i], 1, src, (unsigned long long*)sd.mu2, b->num_sms, s)
+                 : launch_gram_f32(N[i], d[i], 1, src, (unsigned int*)sd.mu2, nullptr, b->num_sms, s);
+    }
     if (e != cudaSuccess) rc = TRSTMI_ECUDA;
   }
   if (rc == TRSTMI_OK) {
-    if (b->f64) k_batch_set_mu2cur<unsigned long long><<<(n + 127) / 128, 128, 0, s>>>(b->d_slots, n);
+    if (screen) k_batch_set_mu2cur_cert<<<(n + 127) / 128, 128, 0, s>>>(b->d_slots, n);
+    else if (b->f64) k_batch_set_mu2cur<unsigned long long><<<(n + 127) / 128, 128, 0, s>>>(b->d_slots, n);
     else k_batch_set_mu2cur<unsigned int><<<(n + 127) / 128, 128, 0, s>>>(b->d_slots, n);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = TRSTMI_ECUDA;
   }
@@ -441,6 +445,7 @@ int trstmi_batch_step(trstmi_batch_handle b, int iters, trstmi_step_info* info) 
   rc = read_states(b, &st);
   if (rc) return rc;
   uint32_t err = 0;
+  BTRY(cudaMemcpy(&err, b->d_err, sizeof(err), cudaMemcpyDeviceToHost));
   if (info) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, b->ev0, b->ev1);
@@ -522,19 +527,21 @@ int trstmi_batch_profile_score(trstmi_batch_handle b, int launches, size_t flush
   double total = 0.0;
   int rc = TRSTMI_OK;
   for (int l = 0; l < launches && rc == TRSTMI_OK; ++l) {
-    // make every instance active for one iteration without advancing it
+    // every instance active for one iteration, not advanced; the screen modes
+    // time the screen (all instances screened), the others the full pass
     k_batch_set_stop<<<(b->n + 127) / 128, 128, 0, s>>>(b->d_slots, b->n, 1u);
     if (cudaGetLastError() != cudaSuccess ||
-        launch_batch_begin(b->d_slots, b->n, b->d_counters, (int)b->groups.size(), b->f64, s) ||
+        launch_batch_begin(b->d_slots, b->n, b->plan.d_counters, BatchPlan::kCounters, b->f64,
+                           b->screen, s) ||
         (flush && cudaMemsetAsync(flush, l & 0xff, flush_bytes, s)) ||
         cudaEventRecord(b->ev0, s) != cudaSuccess) { rc = TRSTMI_ECUDA; break; }
-    for (size_t g = 0; g < b->groups.size(); ++g) {
-      const auto& G = b->groups[g];
-      if (launch_batch_score(b->f64, G.R, b->d_slots, G.d_ids, G.d_begin, G.count, G.nitems,
-                             b->d_counters + g, G.smem, G.grid, s) != cudaSuccess) rc = TRSTMI_ECUDA;
-    }
+    cudaError_t e = b->screen
+        ? launch_screen_batched(b->opt.precision == TRSTMI_FP16_SCREEN, b->plan.d_screen_slots,
+                                b->plan.d_items, b->plan.n_items, b->d_err, b->num_sms, s)
+        : b->plan.launch_pass(kPassFull, b->d_slots, s);
     float ms = 0.f;
-    if (rc || cudaEventRecord(b->ev1, s) != cudaSuccess || cudaEventSynchronize(b->ev1) != cudaSuccess ||
+    if (e != cudaSuccess || cudaEventRecord(b->ev1, s) != cudaSuccess ||
+        cudaEventSynchronize(b->ev1) != cudaSuccess ||
         cudaEventElapsedTime(&ms, b->ev0, b->ev1) != cudaSuccess) { rc = TRSTMI_ECUDA; break; }
     total += ms;
   }

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <mutex>
 #include <new>
@@ -216,8 +217,9 @@ int enqueue_iteration(trstmi_instance* h, cudaStream_t s) {
     // rank the K candidates: tensor-core screen while delta >= screen_min_delta,
     // else the fp32 Gram of every candidate (each kernel returns at once when
     // the other one is selected for this iteration)
-    TRY_CUDA(launch_screen(prec == TRSTMI_FP16_SCREEN, N, d, h->seed, h->phi32, K, 0u, 0u, 0.0,
-                           st, h->mu2_k32, &st->error, h->num_sms, s));
+    if (screen_supported(N, d))
+      TRY_CUDA(launch_screen(prec == TRSTMI_FP16_SCREEN, N, d, h->seed, h->phi32, K, 0u, 0u, 0.0,
+                             st, h->mu2_k32, &st->error, h->num_sms, s));
     GramSource full{};
     full.perturb = true;
     full.phi = h->phi32;
@@ -290,7 +292,6 @@ int validate_options(int N, int d, const trstmi_options& o) {
     return TRSTMI_EINVAL;
   if (!(o.delta_min >= 0) || !(o.delta_max >= o.delta_min)) return TRSTMI_EINVAL;
   if (!(o.screen_min_delta >= 0)) return TRSTMI_EINVAL;
-  if (is_screen(o.precision) && !screen_supported(N, d)) return TRSTMI_EUNSUPPORTED;
   return TRSTMI_OK;
 }
 
@@ -426,7 +427,10 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   s0.gamma_dec = o.gamma_dec;
   s0.delta_min = o.delta_min;
   s0.delta_max = o.delta_max;
-  s0.screen_min_delta = o.screen_min_delta;
+  // a shape outside the screen kernel's range ranks with the binary32 Gram
+  s0.screen_min_delta = (is_screen(o.precision) && !screen_supported(N, d))
+                            ? std::numeric_limits<double>::infinity()
+                            : o.screen_min_delta;
   s0.trace_cap = (uint32_t)o.trace_cap;
   cudaStream_t s = h->stream;
   if (cudaMemsetAsync(h->block, 0, off, s) != cudaSuccess ||

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 #include "common.cuh"
 
 namespace trstmi {
@@ -83,6 +84,19 @@ cudaError_t launch_gen_candidate(int N, int d, uint64_t seed, uint32_t t, uint32
 
 // tensor-core screen (tc_screen.cu)
 bool screen_supported(int N, int d);
+// One instance as the batched screen sees it (device table).
+struct ScreenSlot {
+  const float2* phi32;
+  unsigned int* mu2;     // K screen scores
+  const DevState* st;
+  uint64_t seed;
+  int N, d;
+};
+// Screen of (instance, candidate) items of many instances; an instance's items
+// are skipped unless it is active and ranks with the screen this iteration.
+cudaError_t launch_screen_batched(bool fp16, const ScreenSlot* slots, const uint2* items,
+                                  int n_items, uint32_t* err_flag, int num_sms, cudaStream_t s);
+
 // fp16 = false: bf16 operands; true: fp16 operands.  With st, runs only when
 // st->active && st->use_screen.
 cudaError_t launch_screen(bool fp16, int N, int d, uint64_t seed, const float2* phi32, int K,
@@ -102,19 +116,46 @@ struct SlotDesc {
   int N, d, K;
   int R;                // tile width 16R of this instance's Gram pass
   int ntiles;           // upper-triangle tiles at that width
-  int pad;
-  long long item_begin; // first work item of this instance within its width group
+  int screen;           // screen modes: 1 if the tensor-core screen handles this shape
+  // screen modes only: top-k survivors, their fp32 scores, the binary64
+  // winner and its binary32 rounding, certification scratch
+  uint32_t* topk;
+  unsigned int* mu2_top;
+  int topk_n;
+  uint32_t pair_cap;
+  double2* cand64;
+  float2* cand32;
+  unsigned int* cert32;          // [0] fp32 max of the winner, [1] filter pass's own max
+  unsigned long long* cert64;    // certified binary64 mu^2 of the winner
+  uint2* pairs;                  // preselected pairs (pair_cap)
 };
 
-// Iteration start for every instance (one CTA each); also zeroes the work counters.
+// Passes of the batched scoring kernel.
+enum BatchPassMode : int {
+  kPassFull = 0,      // every candidate, binary32/64 (ranking when not screened)
+  kPassRescore = 1,   // the top-k survivors, binary32, into mu2_top
+  kPassFrameMax = 2,  // the winner's binary32 rounding: max |G|^2 into cert32[0]
+  kPassFilter = 3,    // same frame: pairs within the bound of cert32[0] into pairs
+  kPassFrame64 = 4,   // the binary64 winner, all pairs, only after a pair-list overflow
+};
+
+// Iteration start for every instance (one CTA each); also zeroes the work
+// counters.  screen_mode: instances with SlotDesc::screen rank with the
+// tensor-core screen while their radius is >= screen_min_delta.
 cudaError_t launch_batch_begin(SlotDesc* slots, int n, unsigned long long* counters, int ncounters,
-                               bool f64, cudaStream_t s);
+                               bool f64, bool screen_mode, cudaStream_t s);
 // Persistent scoring pass over the instances of one tile-width group: work
-// items (instance, candidate, tile) handed out by an atomic counter.
+// items (instance, candidate-or-frame, tile) handed out by an atomic counter.
 cudaError_t launch_batch_score(bool f64, int R, const SlotDesc* slots, const int* group,
                                const long long* group_begin, int ngroup, long long nitems,
                                unsigned long long* counter, size_t smem, int grid,
-                               cudaStream_t s);
+                               cudaStream_t s, int mode = kPassFull);
+// Screen modes, one CTA (or column warps) per instance.
+cudaError_t launch_batch_topk(SlotDesc* slots, int n, cudaStream_t s);
+cudaError_t launch_batch_materialize64(SlotDesc* slots, int n, int maxN, cudaStream_t s);
+cudaError_t launch_batch_pairs64(SlotDesc* slots, int n, cudaStream_t s);
+cudaError_t launch_batch_decide_certified(SlotDesc* slots, int n, cudaStream_t s);
+cudaError_t launch_batch_commit_copy(SlotDesc* slots, int n, int maxN, int maxd, cudaStream_t s);
 cudaError_t launch_batch_decide(SlotDesc* slots, int n, bool f64, cudaStream_t s);
 cudaError_t launch_batch_commit(SlotDesc* slots, int n, int maxN, bool f64, cudaStream_t s);
 cudaError_t batch_score_occupancy(bool f64, int R, size_t smem, int* blocks_per_sm);
@@ -123,6 +164,47 @@ size_t gram_smem_bytes(bool f64, int d, int R);
 int cached_width(bool f64, int d, int N);
 void store_width(bool f64, int d, int N, int R);
 int tiles_at_width(int N, int R);
+
+// Launch plan of one iteration over many instances (plan.cu): width-group
+// tables of every scoring pass and the screen's work items, in device buffers
+// allocated once for a capacity and refilled by rebuild().
+struct BatchPlan {
+  static constexpr int kPasses = 5;
+  static constexpr int kCounters = 16;
+  struct Group {
+    int R = 1;
+    bool f64 = false;
+    int* d_ids = nullptr;
+    long long* d_begin = nullptr;
+    int count = 0;
+    long long nitems = 0;
+    size_t smem = 0;
+    int grid = 0;
+    int counter = 0;
+  };
+  struct Table { int* d_ids = nullptr; long long* d_begin = nullptr; };
+  void* mem = nullptr;
+  int cap_slots = 0;
+  long long cap_items = 0;
+  int num_sms = 0;
+  int precision = 0;
+  int maxN = 0, maxd = 0;
+  int ncounters = 0;
+  Table tables[kPasses][3];
+  std::vector<Group> groups[kPasses];
+  ScreenSlot* d_screen_slots = nullptr;
+  uint2* d_items = nullptr;
+  int n_items = 0;
+  unsigned long long* d_counters = nullptr;
+
+  int init(int capacity_slots, long long capacity_items, int num_sms);
+  void destroy();
+  // h: host copy of the device slot table (R of every slot chosen)
+  int rebuild(const std::vector<SlotDesc>& h, int precision, cudaStream_t s);
+  int enqueue_iteration(SlotDesc* d_slots, int n, uint32_t* err, cudaStream_t s) const;
+  cudaError_t launch_pass(int pass, SlotDesc* d_slots, cudaStream_t s) const;
+  int kernels_per_iteration() const;
+};
 
 cudaError_t init_kernel_attributes();
 cudaError_t init_screen_attributes(int optin_smem);

@@ -1,0 +1,186 @@
+// Launch plan of one iteration over many instances (batched searches and the
+// serving loop): the width-group tables of every scoring pass, the work items
+// of the tensor-core screen, and the enqueue of the iteration's kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/trstmi.h"
+#include "kernels.h"
+
+namespace trstmi {
+
+namespace {
+constexpr int kWidths[3] = {4, 2, 1};
+
+bool is_screen_prec(int p) { return p == TRSTMI_BF16_SCREEN || p == TRSTMI_FP16_SCREEN; }
+
+// Widest tile usable for a binary64 frame pass of this shape (<= R).
+int frame64_width(int d, int N, int R) {
+  while (R > 1 && (gram_smem_bytes(true, d, R) > 200 * 1024 || 16 * R >= 2 * N)) R >>= 1;
+  return R;
+}
+}  // namespace
+
+int BatchPlan::init(int capacity_slots, long long capacity_items, int num_sms_) {
+  cap_slots = capacity_slots;
+  cap_items = capacity_items;
+  num_sms = num_sms_;
+  const size_t ids_b = sizeof(int) * (size_t)cap_slots;
+  const size_t beg_b = sizeof(long long) * ((size_t)cap_slots + 1);
+  size_t total = 0;
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  total += kPasses * 3 * (up(ids_b) + up(beg_b));
+  total += up(sizeof(ScreenSlot) * (size_t)cap_slots);
+  total += up(sizeof(uint2) * (size_t)std::max<long long>(cap_items, 1));
+  total += up(sizeof(unsigned long long) * kCounters);
+  if (cudaMalloc(&mem, total) != cudaSuccess) { cudaGetLastError(); return TRSTMI_ENOMEM; }
+  char* p = (char*)mem;
+  for (int pass = 0; pass < kPasses; ++pass)
+    for (int w = 0; w < 3; ++w) {
+      tables[pass][w].d_ids = (int*)p; p += up(ids_b);
+      tables[pass][w].d_begin = (long long*)p; p += up(beg_b);
+    }
+  d_screen_slots = (ScreenSlot*)p; p += up(sizeof(ScreenSlot) * (size_t)cap_slots);
+  d_items = (uint2*)p; p += up(sizeof(uint2) * (size_t)std::max<long long>(cap_items, 1));
+  d_counters = (unsigned long long*)p;
+  return TRSTMI_OK;
+}
+
+void BatchPlan::destroy() {
+  if (mem) cudaFree(mem);
+  mem = nullptr;
+}
+
+int BatchPlan::rebuild(const std::vector<SlotDesc>& h, int precision_, cudaStream_t s) {
+  precision = precision_;
+  const int n = (int)h.size();
+  if (n > cap_slots) return TRSTMI_EINVAL;
+  const bool f64 = precision == TRSTMI_FP64;
+  const bool screen = is_screen_prec(precision);
+  maxN = 0; maxd = 0;
+  for (const auto& sd : h) { maxN = std::max(maxN, sd.N); maxd = std::max(maxd, sd.d); }
+  ncounters = 0;
+  for (int pass = 0; pass < kPasses; ++pass) {
+    groups[pass].clear();
+    if (!screen && pass != kPassFull) continue;
+    for (int w = 0; w < 3; ++w) {
+      const int R = kWidths[w];
+      const bool pass64 = (pass == kPassFrame64) || (pass == kPassFull && f64);
+      std::vector<int> ids;
+      for (int i = 0; i < n; ++i) {
+        const int r_i = pass == kPassFrame64 ? frame64_width(h[i].d, h[i].N, h[i].R) : h[i].R;
+        if (r_i == R) ids.push_back(i);
+      }
+      if (ids.empty()) continue;
+      auto keff = [&](int i) {
+        return pass == kPassFull ? h[i].K : pass == kPassRescore ? h[i].topk_n : 1;
+      };
+      auto cost = [&](int i) { return (double)keff(i) * tiles_at_width(h[i].N, R) * h[i].d; };
+      std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) { return cost(x) > cost(y); });
+      std::vector<long long> begin(ids.size() + 1, 0);
+      size_t smem = 0;
+      for (size_t q = 0; q < ids.size(); ++q) {
+        begin[q + 1] = begin[q] + (long long)keff(ids[q]) * tiles_at_width(h[ids[q]].N, R);
+        smem = std::max(smem, gram_smem_bytes(pass64, h[ids[q]].d, R));
+      }
+      Group g;
+      g.R = R;
+      g.f64 = pass64;
+      g.d_ids = tables[pass][w].d_ids;
+      g.d_begin = tables[pass][w].d_begin;
+      g.count = (int)ids.size();
+      g.nitems = begin.back();
+      g.smem = smem;
+      g.counter = ncounters++;
+      int per_sm = 0;
+      if (batch_score_occupancy(pass64, R, smem, &per_sm) != cudaSuccess || per_sm < 1)
+        return TRSTMI_ECUDA;
+      g.grid = (int)std::min<long long>(g.nitems, (long long)num_sms * per_sm);
+      if (cudaMemcpyAsync(g.d_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+          cudaMemcpyAsync(g.d_begin, begin.data(), sizeof(long long) * begin.size(),
+                          cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return TRSTMI_ECUDA;
+      groups[pass].push_back(g);
+    }
+  }
+  // screen work items (instance, candidate), heaviest instances first
+  n_items = 0;
+  if (screen) {
+    std::vector<ScreenSlot> ss(n);
+    std::vector<int> order;
+    for (int i = 0; i < n; ++i) {
+      ss[i].phi32 = reinterpret_cast<const float2*>(h[i].phi);
+      ss[i].mu2 = reinterpret_cast<unsigned int*>(h[i].mu2);
+      ss[i].st = h[i].st;
+      ss[i].seed = h[i].seed;
+      ss[i].N = h[i].N;
+      ss[i].d = h[i].d;
+      if (h[i].screen) order.push_back(i);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      const long long nx = (h[x].N + 127) / 128, ny = (h[y].N + 127) / 128;
+      return nx * (nx + 1) > ny * (ny + 1);
+    });
+    std::vector<uint2> items;
+    for (int i : order)
+      for (int c = 0; c < h[i].K; ++c) items.push_back(make_uint2((unsigned)i, (unsigned)c));
+    if ((long long)items.size() > cap_items) return TRSTMI_EINVAL;
+    n_items = (int)items.size();
+    if (cudaMemcpyAsync(d_screen_slots, ss.data(), sizeof(ScreenSlot) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        (n_items && cudaMemcpyAsync(d_items, items.data(), sizeof(uint2) * items.size(),
+                                    cudaMemcpyHostToDevice, s) != cudaSuccess))
+      return TRSTMI_ECUDA;
+  }
+  return TRSTMI_OK;
+}
+
+cudaError_t BatchPlan::launch_pass(int pass, SlotDesc* d_slots, cudaStream_t s) const {
+  for (const auto& g : groups[pass]) {
+    cudaError_t e = launch_batch_score(g.f64, g.R, d_slots, g.d_ids, g.d_begin, g.count, g.nitems,
+                                       d_counters + g.counter, g.smem, g.grid, s, pass);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int BatchPlan::enqueue_iteration(SlotDesc* d_slots, int n, uint32_t* err, cudaStream_t s) const {
+  const bool f64 = precision == TRSTMI_FP64;
+  const bool screen = is_screen_prec(precision);
+  if (launch_batch_begin(d_slots, n, d_counters, kCounters, f64, screen, s) != cudaSuccess)
+    return TRSTMI_ECUDA;
+  if (!screen) {
+    if (launch_pass(kPassFull, d_slots, s) != cudaSuccess ||
+        launch_batch_decide(d_slots, n, f64, s) != cudaSuccess ||
+        launch_batch_commit(d_slots, n, maxN, f64, s) != cudaSuccess)
+      return TRSTMI_ECUDA;
+    return TRSTMI_OK;
+  }
+  // rank (screen, or fp32 below the screen radius), keep the top-k, re-score
+  // them in fp32, regenerate the winner in fp64 and certify it, decide, commit
+  if (launch_screen_batched(precision == TRSTMI_FP16_SCREEN, d_screen_slots, d_items, n_items, err,
+                            num_sms, s) != cudaSuccess ||
+      launch_pass(kPassFull, d_slots, s) != cudaSuccess ||
+      launch_batch_topk(d_slots, n, s) != cudaSuccess ||
+      launch_pass(kPassRescore, d_slots, s) != cudaSuccess ||
+      launch_batch_materialize64(d_slots, n, maxN, s) != cudaSuccess ||
+      launch_pass(kPassFrameMax, d_slots, s) != cudaSuccess ||
+      launch_pass(kPassFilter, d_slots, s) != cudaSuccess ||
+      launch_batch_pairs64(d_slots, n, s) != cudaSuccess ||
+      launch_pass(kPassFrame64, d_slots, s) != cudaSuccess ||
+      launch_batch_decide_certified(d_slots, n, s) != cudaSuccess ||
+      launch_batch_commit_copy(d_slots, n, maxN, maxd, s) != cudaSuccess)
+    return TRSTMI_ECUDA;
+  return TRSTMI_OK;
+}
+
+int BatchPlan::kernels_per_iteration() const {
+  int k = 1;   // begin
+  for (int p = 0; p < kPasses; ++p) k += (int)groups[p].size();
+  if (is_screen_prec(precision)) k += (n_items ? 1 : 0) + 6;
+  else k += 2;
+  return k;
+}
+
+}  // namespace trstmi

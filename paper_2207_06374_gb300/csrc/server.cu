@@ -2,9 +2,10 @@
 //
 // A host scheduler thread keeps a set of resident search slots on one GPU and
 // advances all of them together: each round is `iters_per_round` iterations
-// of the shared batched launches (iteration start, persistent scoring pass
-// over every slot's (candidate, tile) work items, per-slot accept rule and
-// commit).  Requests wait in a FIFO queue; the head is admitted as soon as a
+// of the shared batched launches of BatchPlan (iteration start, the
+// tensor-core screen in the screen modes, persistent scoring passes over
+// every slot's (candidate, tile) work items, per-slot certification, accept
+// rule and commit).  Requests wait in a FIFO queue; the head is admitted as soon as a
 // slot and enough of the device-memory budget are free (continuous
 // batching).  A slot retires at a round boundary once its search reached its
 // target, spent its iteration budget or was cancelled.  Each slot keeps its
@@ -127,6 +128,7 @@ __global__ void k_srv_set_stop(SlotDesc* slots, int n, uint32_t iters, const uin
 // Marks a slot active (or not) for a width measurement, without advancing it.
 __global__ void k_srv_activate(DevState* st, uint32_t on) {
   st->active = on;
+  st->use_full = on;
   st->delta_used = st->delta;
 }
 
@@ -136,18 +138,40 @@ __global__ void k_srv_set_mu2cur(DevState* st, const void* mu2) {
   st->done = (st->mu2_cur <= st->target2) ? 1u : 0u;
 }
 
-size_t slot_bytes(int N, int d, int K, int trace_cap) {
-  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+// Pair list of the certification: the standalone instance's 65536 pairs, or
+// every pair when there are fewer, so that the list overflows exactly when a
+// standalone run's does.
+uint32_t slot_pair_cap(int N) {
+  const unsigned long long all = (unsigned long long)N * (unsigned long long)(N - 1) / 2;
+  return (uint32_t)std::min<unsigned long long>(all, 1ull << 16);
+}
+
+bool is_screen_prec(int p) { return p == TRSTMI_BF16_SCREEN || p == TRSTMI_FP16_SCREEN; }
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Screen modes: top-k indices and scores, the binary64 winner and its binary32
+// rounding, the certification words and the preselected pair list.
+size_t screen_bytes(int N, int d, int topk) {
   const size_t nd = (size_t)N * d;
-  return up(nd * sizeof(double2)) + up(nd * sizeof(float2)) + up((size_t)K * 8) +
-         up((size_t)std::max(trace_cap, 1) * sizeof(TraceRowDev));
+  return 2 * up256((size_t)topk * sizeof(uint32_t)) + up256(nd * sizeof(double2)) +
+         up256(nd * sizeof(float2)) + up256(4 * sizeof(uint32_t)) +
+         up256(sizeof(unsigned long long)) + up256((size_t)slot_pair_cap(N) * sizeof(uint2));
+}
+
+size_t slot_bytes(int N, int d, const trstmi_options& o) {
+  const size_t nd = (size_t)N * d;
+  size_t b = up256(nd * sizeof(double2)) + up256(nd * sizeof(float2)) + up256((size_t)o.K * 8) +
+             up256((size_t)std::max(o.trace_cap, 1) * sizeof(TraceRowDev));
+  if (is_screen_prec(o.precision)) b += screen_bytes(N, d, o.topk);
+  return b;
 }
 
 }  // namespace
 
 struct trstmi_server {
   trstmi_server_opts opt{};
-  bool f64 = false;
+  bool f64 = false, screen = false;
   int num_sms = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -156,14 +180,12 @@ struct trstmi_server {
   DevState* d_states = nullptr;       // max_slots states
   SlotDesc* d_slots = nullptr;        // active slot table
   uint32_t* d_budget = nullptr;
-  unsigned long long* d_counters = nullptr;
+  uint32_t* d_err = nullptr;          // screen kernel's abort word
+  int* d_tune_ids = nullptr;          // width measurement: one-slot group table
+  long long* d_tune_begin = nullptr;
   std::vector<int> free_states;
   std::vector<Slot> slots;
-  struct Group { int R; int* d_ids; long long* d_begin; int count; long long nitems; size_t smem; int grid; };
-  std::vector<Group> groups;
-  int* d_group_ids = nullptr;         // max_slots ints per width (3 widths)
-  long long* d_group_begin = nullptr; // (max_slots + 1) per width
-  int maxN = 0;
+  BatchPlan plan;
 
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -184,7 +206,7 @@ namespace {
 
 int choose_width(trstmi_server* sv, Slot& sl) {
   const int N = sl.desc.N, d = sl.desc.d;
-  int R = cached_width(sv->f64, d, N);
+  int R = cached_width(sv->f64, d, N);   // the binary32 pass in the screen modes
   if (R > 0) return R;
   // measure this bucket on this slot alone (its state is active for timing)
   int best_R = 1;
@@ -205,16 +227,16 @@ int choose_width(trstmi_server* sv, Slot& sl) {
     int per_sm = 0;
     if (batch_score_occupancy(sv->f64, cand, smem, &per_sm) != cudaSuccess || per_sm < 1) continue;
     const int grid = (int)std::min<long long>(nitems, (long long)sv->num_sms * per_sm);
-    // the timing tables live in the group scratch of width slot 0
+    // slot table entry 0 is rewritten by rebuild_tables before the next round
     cudaMemcpyAsync(sv->d_slots, &tmp, sizeof(SlotDesc), cudaMemcpyHostToDevice, sv->stream);
-    cudaMemcpyAsync(sv->d_group_ids, ids, sizeof(ids), cudaMemcpyHostToDevice, sv->stream);
-    cudaMemcpyAsync(sv->d_group_begin, begin, sizeof(begin), cudaMemcpyHostToDevice, sv->stream);
+    cudaMemcpyAsync(sv->d_tune_ids, ids, sizeof(ids), cudaMemcpyHostToDevice, sv->stream);
+    cudaMemcpyAsync(sv->d_tune_begin, begin, sizeof(begin), cudaMemcpyHostToDevice, sv->stream);
     float t_best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
-      cudaMemsetAsync(sv->d_counters, 0, sizeof(unsigned long long), sv->stream);
+      cudaMemsetAsync(sv->plan.d_counters, 0, sizeof(unsigned long long), sv->stream);
       cudaEventRecord(e0, sv->stream);
-      launch_batch_score(sv->f64, cand, sv->d_slots, sv->d_group_ids, sv->d_group_begin, 1, nitems,
-                         sv->d_counters, smem, grid, sv->stream);
+      launch_batch_score(sv->f64, cand, sv->d_slots, sv->d_tune_ids, sv->d_tune_begin, 1, nitems,
+                         sv->plan.d_counters, smem, grid, sv->stream, kPassFull);
       cudaEventRecord(e1, sv->stream);
       cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -231,52 +253,17 @@ int choose_width(trstmi_server* sv, Slot& sl) {
   return best_R;
 }
 
-// Device tables for the current active set: descriptors, budgets, width groups.
+// Device tables for the current active set: descriptors, budgets, launch plan.
 int rebuild_tables(trstmi_server* sv) {
   const int n = (int)sv->slots.size();
   std::vector<SlotDesc> h(n);
   std::vector<uint32_t> budget(n);
-  sv->maxN = 0;
   for (int i = 0; i < n; ++i) {
     h[i] = sv->slots[i].desc;
     budget[i] = sv->slots[i].budget;
-    sv->maxN = std::max(sv->maxN, h[i].N);
   }
-  sv->groups.clear();
-  const int widths[3] = {4, 2, 1};
-  for (int w = 0; w < 3; ++w) {
-    const int R = widths[w];
-    std::vector<int> ids;
-    for (int i = 0; i < n; ++i)
-      if (h[i].R == R) ids.push_back(i);
-    if (ids.empty()) continue;
-    std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) {
-      return (double)h[x].K * h[x].ntiles * h[x].d > (double)h[y].K * h[y].ntiles * h[y].d;
-    });
-    std::vector<long long> begin(ids.size() + 1, 0);
-    size_t smem = 0;
-    for (size_t q = 0; q < ids.size(); ++q) {
-      begin[q + 1] = begin[q] + (long long)h[ids[q]].K * h[ids[q]].ntiles;
-      smem = std::max(smem, gram_smem_bytes(sv->f64, h[ids[q]].d, R));
-    }
-    trstmi_server::Group g;
-    g.R = R;
-    g.d_ids = sv->d_group_ids + (size_t)w * sv->opt.max_slots;
-    g.d_begin = sv->d_group_begin + (size_t)w * (sv->opt.max_slots + 1);
-    g.count = (int)ids.size();
-    g.nitems = begin.back();
-    g.smem = smem;
-    int per_sm = 0;
-    if (batch_score_occupancy(sv->f64, R, smem, &per_sm) != cudaSuccess || per_sm < 1)
-      return TRSTMI_ECUDA;
-    g.grid = (int)std::min<long long>(g.nitems, (long long)sv->num_sms * per_sm);
-    if (cudaMemcpyAsync(g.d_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice,
-                        sv->stream) != cudaSuccess ||
-        cudaMemcpyAsync(g.d_begin, begin.data(), sizeof(long long) * begin.size(),
-                        cudaMemcpyHostToDevice, sv->stream) != cudaSuccess)
-      return TRSTMI_ECUDA;
-    sv->groups.push_back(g);
-  }
+  int rc = sv->plan.rebuild(h, sv->opt.search.precision, sv->stream);
+  if (rc) return rc;
   if (n > 0 &&
       (cudaMemcpyAsync(sv->d_slots, h.data(), sizeof(SlotDesc) * n, cudaMemcpyHostToDevice,
                        sv->stream) != cudaSuccess ||
@@ -292,18 +279,31 @@ int admit(trstmi_server* sv, uint64_t ticket, Req& r, Slot* out) {
   const int N = r.req.N, d = r.req.d;
   Slot sl;
   sl.ticket = ticket;
-  sl.bytes = slot_bytes(N, d, o.K, o.trace_cap);
+  sl.bytes = slot_bytes(N, d, o);
   if (!sv->arena.alloc(sl.bytes, &sl.off)) return TRSTMI_ENOMEM;
   sl.state_idx = sv->free_states.back();
   sv->free_states.pop_back();
   char* p = sv->arena.base() + sl.off;
-  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
   const size_t nd = (size_t)N * d;
   double2* p64 = (double2*)p;
-  float2* p32 = (float2*)(p + up(nd * sizeof(double2)));
-  void* mu2 = p + up(nd * sizeof(double2)) + up(nd * sizeof(float2));
-  TraceRowDev* tr = (TraceRowDev*)((char*)mu2 + up((size_t)o.K * 8));
+  float2* p32 = (float2*)(p + up256(nd * sizeof(double2)));
+  void* mu2 = p + up256(nd * sizeof(double2)) + up256(nd * sizeof(float2));
+  TraceRowDev* tr = (TraceRowDev*)((char*)mu2 + up256((size_t)o.K * 8));
   SlotDesc& sd = sl.desc;
+  std::memset(&sd, 0, sizeof(sd));
+  if (sv->screen) {
+    char* q = (char*)tr + up256((size_t)std::max(o.trace_cap, 1) * sizeof(TraceRowDev));
+    sd.screen = screen_supported(N, d) ? 1 : 0;
+    sd.topk = (uint32_t*)q; q += up256((size_t)o.topk * sizeof(uint32_t));
+    sd.mu2_top = (unsigned int*)q; q += up256((size_t)o.topk * sizeof(uint32_t));
+    sd.cand64 = (double2*)q; q += up256(nd * sizeof(double2));
+    sd.cand32 = (float2*)q; q += up256(nd * sizeof(float2));
+    sd.cert32 = (unsigned int*)q; q += up256(4 * sizeof(uint32_t));
+    sd.cert64 = (unsigned long long*)q; q += up256(sizeof(unsigned long long));
+    sd.pairs = (uint2*)q;
+    sd.topk_n = o.topk;
+    sd.pair_cap = slot_pair_cap(sd.N);
+  }
   sd.st = sv->d_states + sl.state_idx;
   sd.phi = sv->f64 ? (void*)p64 : (void*)p32;
   sd.phi_other = sv->f64 ? (void*)p32 : (void*)p64;
@@ -325,15 +325,17 @@ int admit(trstmi_server* sv, uint64_t ticket, Req& r, Slot* out) {
       cudaMemcpyAsync(sd.st, &s0, sizeof(s0), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       launch_init_frame(N, d, sd.seed, p64, p32, sd.st, s) != cudaSuccess)
     return TRSTMI_ECUDA;
+  // initial score in the deciding precision (binary64 in the screen modes)
   GramSource src{};
   src.perturb = false;
-  src.phi = sd.phi;
-  cudaError_t e = sv->f64
-      ? launch_gram_f64(N, d, 1, src, (unsigned long long*)mu2, sv->num_sms, s)
-      : launch_gram_f32(N, d, 1, src, (unsigned int*)mu2, nullptr, sv->num_sms, s);
+  src.phi = sv->screen ? (const void*)p64 : sd.phi;
+  void* init_out = sv->screen ? (void*)sd.cert64 : mu2;
+  cudaError_t e = (sv->f64 || sv->screen)
+      ? launch_gram_f64(N, d, 1, src, (unsigned long long*)init_out, sv->num_sms, s)
+      : launch_gram_f32(N, d, 1, src, (unsigned int*)init_out, nullptr, sv->num_sms, s);
   if (e != cudaSuccess) return TRSTMI_ECUDA;
-  if (sv->f64) k_srv_set_mu2cur<unsigned long long><<<1, 1, 0, s>>>(sd.st, mu2);
-  else k_srv_set_mu2cur<unsigned int><<<1, 1, 0, s>>>(sd.st, mu2);
+  if (sv->f64 || sv->screen) k_srv_set_mu2cur<unsigned long long><<<1, 1, 0, s>>>(sd.st, init_out);
+  else k_srv_set_mu2cur<unsigned int><<<1, 1, 0, s>>>(sd.st, init_out);
   if (cudaGetLastError() != cudaSuccess) return TRSTMI_ECUDA;
   // tile width: the cached choice for this (d, N) bucket, measured if new
   sd.R = 1;
@@ -442,22 +444,21 @@ void worker_main(trstmi_server* sv) {
     cudaStream_t s = sv->stream;
     k_srv_set_stop<<<(n + 127) / 128, 128, 0, s>>>(sv->d_slots, n, (uint32_t)I, sv->d_budget);
     bool ok = cudaGetLastError() == cudaSuccess;
-    for (int it = 0; ok && it < I; ++it) {
-      ok = launch_batch_begin(sv->d_slots, n, sv->d_counters, (int)sv->groups.size(), sv->f64, s) ==
-           cudaSuccess;
-      for (size_t g = 0; ok && g < sv->groups.size(); ++g) {
-        const auto& G = sv->groups[g];
-        ok = launch_batch_score(sv->f64, G.R, sv->d_slots, G.d_ids, G.d_begin, G.count, G.nitems,
-                                sv->d_counters + g, G.smem, G.grid, s) == cudaSuccess;
-      }
-      ok = ok && launch_batch_decide(sv->d_slots, n, sv->f64, s) == cudaSuccess;
-      ok = ok && launch_batch_commit(sv->d_slots, n, sv->maxN, sv->f64, s) == cudaSuccess;
-    }
+    for (int it = 0; ok && it < I; ++it)
+      ok = sv->plan.enqueue_iteration(sv->d_slots, n, sv->d_err, s) == TRSTMI_OK;
     st.resize(n);
     for (int k = 0; ok && k < n; ++k)
       ok = cudaMemcpyAsync(&st[k], sv->slots[k].desc.st, sizeof(DevState), cudaMemcpyDeviceToHost,
                            s) == cudaSuccess;
+    uint32_t screen_err = 0;
+    ok = ok && cudaMemcpyAsync(&screen_err, sv->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                               s) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+    // a screen launch that gave up waiting aborts every slot of the round
+    if (ok && screen_err) {
+      for (int k = 0; k < n; ++k) st[k].error |= screen_err;
+      ok = cudaMemsetAsync(sv->d_err, 0, sizeof(uint32_t), s) == cudaSuccess;
+    }
     if (!ok) { cudaGetLastError(); sv->worker_error = TRSTMI_ECUDA; break; }
     {
       std::lock_guard<std::mutex> g(sv->mu);
@@ -531,6 +532,7 @@ void trstmi_server_destroy(trstmi_server* sv) {
   if (sv->worker.joinable()) sv->worker.join();
   cudaSetDevice(sv->opt.search.device);
   if (sv->stream) cudaStreamSynchronize(sv->stream);
+  sv->plan.destroy();
   if (sv->arena_mem) cudaFree(sv->arena_mem);
   if (sv->d_states) cudaFree(sv->d_states);
   if (sv->own_stream && sv->stream) cudaStreamDestroy(sv->stream);
@@ -543,11 +545,13 @@ int trstmi_server_create(const trstmi_server_opts* opts, trstmi_server** out) {
   trstmi_server_opts o;
   if (opts) o = *opts; else trstmi_default_server_opts(&o);
   const trstmi_options& so = o.search;
-  if (so.precision != TRSTMI_FP32 && so.precision != TRSTMI_FP64) return TRSTMI_EUNSUPPORTED;
+  if (so.precision < TRSTMI_FP64 || so.precision > TRSTMI_FP16_SCREEN) return TRSTMI_EINVAL;
   if (o.max_slots < 1 || o.max_slots > 65536 || o.queue_cap < 1 || o.iters_per_round < 1 ||
       so.K < 1 || so.trace_cap < 0 || o.hbm_budget < 4096 || !(so.delta0 > 0) ||
       !(so.gamma_inc >= 1) || !(so.gamma_dec > 0 && so.gamma_dec <= 1) || !(so.delta_min >= 0) ||
-      !(so.delta_max >= so.delta_min))
+      !(so.delta_max >= so.delta_min) || !(so.screen_min_delta >= 0))
+    return TRSTMI_EINVAL;
+  if (is_screen_prec(so.precision) && (so.topk < 1 || so.topk > 64 || so.topk > so.K))
     return TRSTMI_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return TRSTMI_ECUDA;
@@ -558,6 +562,7 @@ int trstmi_server_create(const trstmi_server_opts* opts, trstmi_server** out) {
   if (!sv) return TRSTMI_ENOMEM;
   sv->opt = o;
   sv->f64 = so.precision == TRSTMI_FP64;
+  sv->screen = is_screen_prec(so.precision);
   if (cudaDeviceGetAttribute(&sv->num_sms, cudaDevAttrMultiProcessorCount, so.device) != cudaSuccess) {
     delete sv;
     return TRSTMI_ECUDA;
@@ -570,26 +575,28 @@ int trstmi_server_create(const trstmi_server_opts* opts, trstmi_server** out) {
     delete sv;
     return TRSTMI_ECUDA;
   }
-  // control tables (states, descriptors, budgets, counters, width groups)
+  // control tables (states, descriptors, budgets, error word, width measurement)
   const size_t ms = (size_t)o.max_slots;
-  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-  const size_t b_st = up(ms * sizeof(DevState)), b_sl = up(ms * sizeof(SlotDesc)),
-               b_bu = up(ms * sizeof(uint32_t)), b_ct = up(8 * sizeof(unsigned long long)),
-               b_gi = up(3 * ms * sizeof(int)), b_gb = up(3 * (ms + 1) * sizeof(long long));
+  const size_t b_st = up256(ms * sizeof(DevState)), b_sl = up256(ms * sizeof(SlotDesc)),
+               b_bu = up256(ms * sizeof(uint32_t)), b_er = up256(sizeof(uint32_t)),
+               b_ti = up256(sizeof(int)), b_tb = up256(2 * sizeof(long long));
   char* ctl = nullptr;
-  if (cudaMalloc(&ctl, b_st + b_sl + b_bu + b_ct + b_gi + b_gb) != cudaSuccess ||
-      cudaMalloc(&sv->arena_mem, o.hbm_budget) != cudaSuccess) {
+  if (cudaMalloc(&ctl, b_st + b_sl + b_bu + b_er + b_ti + b_tb) != cudaSuccess ||
+      cudaMemset(ctl, 0, b_st + b_sl + b_bu + b_er + b_ti + b_tb) != cudaSuccess ||
+      cudaMalloc(&sv->arena_mem, o.hbm_budget) != cudaSuccess ||
+      sv->plan.init(o.max_slots, sv->screen ? (long long)o.max_slots * so.K : 0, sv->num_sms) !=
+          TRSTMI_OK) {
     cudaGetLastError();
-    if (ctl) cudaFree(ctl);
+    sv->d_states = (DevState*)ctl;   // freed by destroy
     trstmi_server_destroy(sv);
     return TRSTMI_ENOMEM;
   }
   sv->d_states = (DevState*)ctl;
   sv->d_slots = (SlotDesc*)(ctl + b_st);
   sv->d_budget = (uint32_t*)(ctl + b_st + b_sl);
-  sv->d_counters = (unsigned long long*)(ctl + b_st + b_sl + b_bu);
-  sv->d_group_ids = (int*)(ctl + b_st + b_sl + b_bu + b_ct);
-  sv->d_group_begin = (long long*)(ctl + b_st + b_sl + b_bu + b_ct + b_gi);
+  sv->d_err = (uint32_t*)(ctl + b_st + b_sl + b_bu);
+  sv->d_tune_ids = (int*)(ctl + b_st + b_sl + b_bu + b_er);
+  sv->d_tune_begin = (long long*)(ctl + b_st + b_sl + b_bu + b_er + b_ti);
   sv->arena.reset((char*)sv->arena_mem, o.hbm_budget);
   for (int i = o.max_slots - 1; i >= 0; --i) sv->free_states.push_back(i);
   sv->worker = std::thread(worker_main, sv);

@@ -631,7 +631,7 @@ __global__ void k_pairs64(const uint32_t* active, const uint32_t* npairs, const 
       re = fma(u.x, v.x, fma(u.y, v.y, re));
       im = fma(u.x, v.y, fma(-u.y, v.x, im));
     }
-    m = fmax(m, re * re + im * im);
+    m = fmax(m, pair_abs2(re, im));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -744,17 +744,22 @@ cudaError_t launch_gen_candidate(int N, int d, uint64_t seed, uint32_t t, uint32
 // counters, so its trajectory is the one it would follow alone.
 
 template <typename B>
-__global__ void k_batch_begin(SlotDesc* slots, int n, unsigned long long* counters, int ncounters) {
+__global__ void k_batch_begin(SlotDesc* slots, int n, unsigned long long* counters, int ncounters,
+                              int screen_mode) {
   const int s = blockIdx.x;
   if (s == 0 && threadIdx.x < ncounters) counters[threadIdx.x] = 0ull;
   if (s >= n) return;
-  DevState* st = slots[s].st;
+  const SlotDesc& sd = slots[s];
+  DevState* st = sd.st;
   __shared__ uint32_t act;
   if (threadIdx.x == 0) {
     act = (!st->done && st->t < st->t_stop) ? 1u : 0u;
     st->active = act;
-    st->use_screen = 0u;
-    st->use_full = act;
+    st->npairs = 0u;
+    st->overflow = 0u;
+    const bool scr = act && screen_mode && sd.screen && st->delta >= st->screen_min_delta;
+    st->use_screen = scr ? 1u : 0u;
+    st->use_full = (act && !scr) ? 1u : 0u;
     if (act) {
       st->delta_used = st->delta;
       st->accepted = 0u;
@@ -762,27 +767,34 @@ __global__ void k_batch_begin(SlotDesc* slots, int n, unsigned long long* counte
   }
   __syncthreads();
   if (!act) return;
-  B* mu2 = reinterpret_cast<B*>(slots[s].mu2);
-  for (int c = threadIdx.x; c < slots[s].K; c += blockDim.x) mu2[c] = B(0);
+  B* mu2 = reinterpret_cast<B*>(sd.mu2);
+  for (int c = threadIdx.x; c < sd.K; c += blockDim.x) mu2[c] = B(0);
+  if (screen_mode) {
+    for (int c = threadIdx.x; c < sd.topk_n; c += blockDim.x) sd.mu2_top[c] = 0u;
+    if (threadIdx.x == 0) { sd.cert32[0] = 0u; sd.cert32[1] = 0u; *sd.cert64 = 0ull; }
+  }
 }
 
 cudaError_t launch_batch_begin(SlotDesc* slots, int n, unsigned long long* counters, int ncounters,
-                               bool f64, cudaStream_t s) {
+                               bool f64, bool screen_mode, cudaStream_t s) {
   const int grid = n > 0 ? n : 1;
-  if (f64) k_batch_begin<unsigned long long><<<grid, 256, 0, s>>>(slots, n, counters, ncounters);
-  else k_batch_begin<unsigned int><<<grid, 256, 0, s>>>(slots, n, counters, ncounters);
+  if (f64) k_batch_begin<unsigned long long><<<grid, 256, 0, s>>>(slots, n, counters, ncounters, screen_mode);
+  else k_batch_begin<unsigned int><<<grid, 256, 0, s>>>(slots, n, counters, ncounters, screen_mode);
   return cudaGetLastError();
 }
 
-// Persistent scoring pass: CTAs take work items (instance, candidate, tile)
-// from *counter until nitems are done.  group lists the instances of this
-// tile width in the order of their items; group_begin[g] is the first item
-// of group[g] (group_begin[ngroup] = nitems).
+// Persistent scoring pass: CTAs take work items (instance, k, tile) from
+// *counter until nitems are done.  group lists the instances of this tile
+// width in the order of their items; group_begin[g] is the first item of
+// group[g] (group_begin[ngroup] = nitems).  What an item is depends on the
+// pass (BatchPassMode): a candidate (k = candidate index, or the k-th top-k
+// survivor) generated around the instance's frame, or the instance's stored
+// winner frame (one item per tile).
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_batch_score(const SlotDesc* slots, const int* group,
                                                      const long long* group_begin, int ngroup,
                                                      long long nitems,
-                                                     unsigned long long* counter) {
+                                                     unsigned long long* counter, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[8];
   __shared__ int zero_col;
@@ -801,25 +813,66 @@ __global__ void __launch_bounds__(256) k_batch_score(const SlotDesc* slots, cons
     }
     const SlotDesc& sd = slots[group[lo]];
     const DevState* st = sd.st;
-    if (st->active) {
+    bool run;
+    switch (mode) {
+      case kPassFull: run = st->active && st->use_full; break;
+      case kPassFrame64: run = st->active && st->overflow; break;
+      default: run = st->active; break;
+    }
+    if (run) {
+      // tiles at this launch's width (the binary64 frame pass may run an
+      // instance narrower than its ranking width)
+      const int nbw = (sd.N + 16 * R - 1) / (16 * R);
+      const long long ntw = (long long)nbw * (nbw + 1) / 2;
       const long long local = w - group_begin[lo];
+      const int k = (int)(local / ntw);
       TileItem it;
       it.N = sd.N; it.d = sd.d;
-      it.c = (uint32_t)(local / sd.ntiles);
-      tile_coords((int)(local - (long long)it.c * sd.ntiles), it.I, it.J);
-      it.perturb = true;
+      tile_coords((int)(local - (long long)k * ntw), it.I, it.J);
       it.normalize = false;
-      it.phi = sd.phi;
       it.seed = sd.seed;
       it.t = st->t + 1u;
       it.delta = st->delta_used;
+      T thr = T(-1);
+      PairFilter pf;
+      const PairFilter* filter = nullptr;
+      if (mode == kPassFull || mode == kPassRescore) {
+        it.perturb = true;
+        it.phi = sd.phi;
+        it.c = mode == kPassFull ? (uint32_t)k : sd.topk[k];
+      } else {
+        it.perturb = false;
+        it.c = 0u;
+        it.phi = mode == kPassFrame64 ? (const void*)sd.cand64 : (const void*)sd.cand32;
+        if (mode == kPassFilter) {
+          pf.mu2_ref = &sd.cert32[0];
+          pf.margin = (float)(8.0 * (2.0 * sd.d + 2.0) / 16777216.0);
+          pf.pairs = sd.pairs;
+          pf.npairs = &const_cast<DevState*>(st)->npairs;
+          pf.cap = sd.pair_cap;
+          pf.overflow = &const_cast<DevState*>(st)->overflow;
+          const float ref = sqrtf(__uint_as_float(sd.cert32[0]));
+          const float lo2 = fmaxf(ref - pf.margin, 0.0f);
+          thr = (T)(lo2 * lo2);
+          filter = &pf;
+        }
+      }
       if (threadIdx.x == 0) zero_col = 0;
-      T m = score_tile<T, R>(it, sm, &zero_col, T(-1), nullptr);
+      T m = score_tile<T, R>(it, sm, &zero_col, thr, filter);
       if (zero_col && threadIdx.x == 0)
         atomicOr(&const_cast<DevState*>(st)->error, (uint32_t)kErrZeroColumn);
       m = block_max<T>(m, red);
-      if (threadIdx.x == 0)
-        atomic_max_nonneg(reinterpret_cast<typename Mu2Bits<T>::type*>(sd.mu2) + it.c, m);
+      if (threadIdx.x == 0) {
+        typename Mu2Bits<T>::type* out;
+        switch (mode) {
+          case kPassFull: out = reinterpret_cast<typename Mu2Bits<T>::type*>(sd.mu2) + k; break;
+          case kPassRescore: out = reinterpret_cast<typename Mu2Bits<T>::type*>(sd.mu2_top) + k; break;
+          case kPassFrameMax: out = reinterpret_cast<typename Mu2Bits<T>::type*>(sd.cert32); break;
+          case kPassFilter: out = reinterpret_cast<typename Mu2Bits<T>::type*>(sd.cert32 + 1); break;
+          default: out = reinterpret_cast<typename Mu2Bits<T>::type*>(sd.cert64); break;
+        }
+        atomic_max_nonneg(out, m);
+      }
     }
     __syncthreads();
   }
@@ -829,12 +882,12 @@ template <typename T>
 static cudaError_t launch_batch_score_t(int R, const SlotDesc* slots, const int* group,
                                         const long long* group_begin, int ngroup, long long nitems,
                                         unsigned long long* counter, size_t smem, int grid,
-                                        cudaStream_t s) {
+                                        cudaStream_t s, int mode) {
   if (ngroup < 1 || nitems < 1) return cudaSuccess;
   switch (R) {
-    case 4: k_batch_score<T, 4><<<grid, 256, smem, s>>>(slots, group, group_begin, ngroup, nitems, counter); break;
-    case 2: k_batch_score<T, 2><<<grid, 256, smem, s>>>(slots, group, group_begin, ngroup, nitems, counter); break;
-    case 1: k_batch_score<T, 1><<<grid, 256, smem, s>>>(slots, group, group_begin, ngroup, nitems, counter); break;
+    case 4: k_batch_score<T, 4><<<grid, 256, smem, s>>>(slots, group, group_begin, ngroup, nitems, counter, mode); break;
+    case 2: k_batch_score<T, 2><<<grid, 256, smem, s>>>(slots, group, group_begin, ngroup, nitems, counter, mode); break;
+    case 1: k_batch_score<T, 1><<<grid, 256, smem, s>>>(slots, group, group_begin, ngroup, nitems, counter, mode); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -843,11 +896,155 @@ static cudaError_t launch_batch_score_t(int R, const SlotDesc* slots, const int*
 cudaError_t launch_batch_score(bool f64, int R, const SlotDesc* slots, const int* group,
                                const long long* group_begin, int ngroup, long long nitems,
                                unsigned long long* counter, size_t smem, int grid,
-                               cudaStream_t s) {
+                               cudaStream_t s, int mode) {
   return f64 ? launch_batch_score_t<double>(R, slots, group, group_begin, ngroup, nitems, counter,
-                                            smem, grid, s)
+                                            smem, grid, s, mode)
              : launch_batch_score_t<float>(R, slots, group, group_begin, ngroup, nitems, counter,
-                                           smem, grid, s);
+                                           smem, grid, s, mode);
+}
+
+// Screen modes: the top_n smallest screen (or fp32) scores of each instance,
+// ordered by (mu^2, c); one CTA per instance.
+__global__ void k_batch_topk(SlotDesc* slots, int n) {
+  const SlotDesc& sd = slots[blockIdx.x];
+  if (!sd.st->active) return;
+  const unsigned int* mu2 = reinterpret_cast<const unsigned int*>(sd.mu2);
+  __shared__ unsigned long long sk[8];
+  __shared__ unsigned long long last;
+  if (threadIdx.x == 0) last = 0ull;
+  __syncthreads();
+  for (int r = 0; r < sd.topk_n; ++r) {
+    const unsigned long long floor_key = last;
+    unsigned long long best = ~0ull;
+    for (int c = threadIdx.x; c < sd.K; c += blockDim.x) {
+      const unsigned long long key = ((unsigned long long)mu2[c] << 32) | (unsigned)c;
+      if ((r == 0 || key > floor_key) && key < best) best = key;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+      best = ov < best ? ov : best;
+    }
+    if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = sk[w] < best ? sk[w] : best;
+      sd.topk[r] = (uint32_t)(best & 0xffffffffull);
+      last = best;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_batch_topk(SlotDesc* slots, int n, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  k_batch_topk<<<n, 256, 0, s>>>(slots, n);
+  return cudaGetLastError();
+}
+
+// The best survivor of each instance regenerated in binary64 (one warp per
+// column, instance = blockIdx.y), plus its binary32 rounding.
+__global__ void k_batch_materialize64(SlotDesc* slots, int n) {
+  const SlotDesc& sd = slots[blockIdx.y];
+  DevState* st = sd.st;
+  if (!st->active) return;
+  unsigned int bv = sd.mu2_top[0];
+  uint32_t bc = sd.topk[0];
+  for (int q = 1; q < sd.topk_n; ++q) {
+    const unsigned int v = sd.mu2_top[q];
+    if (v < bv || (v == bv && sd.topk[q] < bc)) { bv = v; bc = sd.topk[q]; }
+  }
+  const int lane = threadIdx.x & 31;
+  const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->cstar = bc;
+    st->mu2_screen = (double)__uint_as_float(bv);
+  }
+  if (j >= sd.N) return;
+  const double2* phi64 = reinterpret_cast<const double2*>(sd.phi_other);
+  const bool ok = gen_column_warp<double>(phi64, sd.d, j, sd.seed, bc, st->t + 1u, 0u,
+                                          st->delta_used, sd.cand64, lane);
+  if (!ok && lane == 0) atomicOr(&st->error, (uint32_t)kErrZeroColumn);
+  __syncwarp();
+  for (int i = lane; i < sd.d; i += 32) {
+    const double2 v = sd.cand64[(size_t)j * sd.d + i];
+    sd.cand32[(size_t)j * sd.d + i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+cudaError_t launch_batch_materialize64(SlotDesc* slots, int n, int maxN, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  dim3 grid((unsigned)(((size_t)maxN * 32 + 255) / 256), n);
+  k_batch_materialize64<<<grid, 256, 0, s>>>(slots, n);
+  return cudaGetLastError();
+}
+
+// binary64 |G|^2 over each instance's preselected pairs (one CTA per instance).
+__global__ void k_batch_pairs64(SlotDesc* slots, int n) {
+  const SlotDesc& sd = slots[blockIdx.x];
+  const DevState* st = sd.st;
+  if (!st->active) return;
+  const uint32_t np = min(st->npairs, sd.pair_cap);
+  const int d = sd.d;
+  double m = 0.0;
+  for (uint32_t p = threadIdx.x; p < np; p += blockDim.x) {
+    const uint2 jk = sd.pairs[p];
+    const double2* x = sd.cand64 + (size_t)jk.x * d;
+    const double2* y = sd.cand64 + (size_t)jk.y * d;
+    double re = 0.0, im = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double2 u = x[i], v = y[i];
+      re = fma(u.x, v.x, fma(u.y, v.y, re));
+      im = fma(u.x, v.y, fma(-u.y, v.x, im));
+    }
+    m = fmax(m, pair_abs2(re, im));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_nonneg(sd.cert64, m);
+}
+
+cudaError_t launch_batch_pairs64(SlotDesc* slots, int n, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  k_batch_pairs64<<<n, 256, 0, s>>>(slots, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_batch_decide_certified(SlotDesc* slots, int n) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const SlotDesc& sd = slots[s];
+  DevState* st = sd.st;
+  if (!st->active) return;
+  apply_rule_and_trace(st, st->cstar, nonneg_from_bits(*sd.cert64), st->mu2_screen, sd.trace);
+}
+
+cudaError_t launch_batch_decide_certified(SlotDesc* slots, int n, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  k_batch_decide_certified<<<(n + 127) / 128, 128, 0, s>>>(slots, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_batch_commit_copy(SlotDesc* slots, int n) {
+  const SlotDesc& sd = slots[blockIdx.y];
+  DevState* st = sd.st;
+  if (!st->active || !st->accepted) return;
+  const size_t nd = (size_t)sd.N * sd.d;
+  double2* phi64 = reinterpret_cast<double2*>(sd.phi_other);
+  float2* phi32 = reinterpret_cast<float2*>(sd.phi);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nd;
+       e += (size_t)gridDim.x * blockDim.x) {
+    phi64[e] = sd.cand64[e];
+    phi32[e] = sd.cand32[e];
+  }
+}
+
+cudaError_t launch_batch_commit_copy(SlotDesc* slots, int n, int maxN, int maxd, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  const size_t nd = (size_t)maxN * maxd;
+  dim3 grid((unsigned)std::min<size_t>((nd + 255) / 256, 64), n);
+  k_batch_commit_copy<<<grid, 256, 0, s>>>(slots, n);
+  return cudaGetLastError();
 }
 
 template <typename K>

@@ -37,6 +37,10 @@ constexpr int kMmaWarp = kGenWarps + kEpiWarps;        // warp 16
 constexpr int kThreads = 32 * (kMmaWarp + 1);          // 544
 constexpr uint32_t kTmemCols = 512;                    // 2 buffers x (128 Re + 128 Im)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+#ifndef TRSTMI_MMA_BACKOFF_NS
+#define TRSTMI_MMA_BACKOFF_NS 20
+#endif
+constexpr unsigned kMmaBackoffNs = TRSTMI_MMA_BACKOFF_NS;  // sleep between MMA-issuer polls
 
 struct ScreenArgs {
   int N, d, nb, ntiles, K;
@@ -204,10 +208,78 @@ __device__ __forceinline__ uint32_t swz_offset(int r, int c) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
 }
 
-template <bool kHalf>
+// One candidate to screen.
+struct ScreenItem {
+  int N, d, nb, ntiles;
+  const float2* phi;
+  uint64_t seed;
+  uint32_t cand, t;
+  float delta;
+  unsigned int* out;   // receives its mu^2 (atomic max of non-negative float bits)
+};
+
+// Work source: candidates c0 .. c0+K-1 of one instance; the Philox round keys
+// come from the kernel parameters, which the instructions read directly.
+struct OneInstance {
+  ScreenArgs a;
+  __device__ bool launch(uint32_t& t, float& delta) const {
+    t = a.t;
+    delta = a.delta;
+    if (a.st) {
+      if (!a.st->active || !a.st->use_screen) return false;
+      t = a.st->t + 1u;
+      delta = (float)a.st->delta_used;
+    }
+    return true;
+  }
+  __device__ int count() const { return a.K; }
+  __device__ bool item(int idx, uint32_t t, float delta, ScreenItem& it) const {
+    it.N = a.N; it.d = a.d; it.nb = a.nb; it.ntiles = a.ntiles;
+    it.phi = a.phi; it.seed = a.seed;
+    it.cand = a.c0 + (uint32_t)idx; it.t = t; it.delta = delta;
+    it.out = a.out + idx;
+    return true;
+  }
+  __device__ PhiloxOut philox(uint32_t e, const ScreenItem& it) const {
+    return philox4x32_10_keys(e, it.cand, it.t, 0u, a.keys);
+  }
+  __device__ uint32_t* err() const { return a.err; }
+};
+
+// Work source: (instance, candidate) items of many instances; every instance
+// brings its own frame, seed, iteration counter and radius (its DevState),
+// and is skipped unless it is active and ranks with the screen this
+// iteration (all roles read the same, unchanging state, so they agree).
+struct ManyInstances {
+  const ScreenSlot* slots;
+  const uint2* items;
+  int n_items;
+  uint32_t* error;
+  __device__ bool launch(uint32_t&, float&) const { return true; }
+  __device__ int count() const { return n_items; }
+  __device__ bool item(int idx, uint32_t, float, ScreenItem& it) const {
+    const uint2 w = items[idx];
+    const ScreenSlot& s = slots[w.x];
+    const DevState* st = s.st;
+    if (!st->active || !st->use_screen) return false;
+    it.N = s.N; it.d = s.d;
+    it.nb = (s.N + kBlockCols - 1) / kBlockCols;
+    it.ntiles = it.nb * (it.nb + 1) / 2;
+    it.phi = s.phi32; it.seed = s.seed;
+    it.cand = w.y; it.t = st->t + 1u; it.delta = (float)st->delta_used;
+    it.out = s.mu2 + w.y;
+    return true;
+  }
+  __device__ PhiloxOut philox(uint32_t e, const ScreenItem& it) const {
+    return philox4x32_10(e, it.cand, it.t, 0u, seed_lo(it.seed), seed_hi(it.seed));
+  }
+  __device__ uint32_t* err() const { return error; }
+};
+
 // 17 warps: one SM sub-partition (16K registers) holds 5 of them, so a
 // thread may use at most 16384 / (5 * 32) -> 96 registers
-__global__ void __maxnreg__(96) k_screen(const ScreenArgs a) {
+template <bool kHalf, class Src>
+__global__ void __maxnreg__(96) k_screen(const Src src) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ SmemCtl ctl;
   // 1024-byte aligned operand area
@@ -215,18 +287,15 @@ __global__ void __maxnreg__(96) k_screen(const ScreenArgs a) {
   unsigned char* xs = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   const uint32_t xs_addr = smem_u32(xs);
 
-  uint32_t t = a.t;
-  float delta = a.delta;
-  if (a.st) {
-    if (!a.st->active || !a.st->use_screen) return;
-    t = a.st->t + 1u;
-    delta = (float)a.st->delta_used;
-  }
+  uint32_t t0;
+  float delta0;
+  if (!src.launch(t0, delta0)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nb = a.nb, ntiles = a.ntiles;
+  uint32_t* err = src.err();
+  const int nitems = src.count();
 
   if (threadIdx.x == 0) {
-    for (int b = 0; b < nb; ++b) {
+    for (int b = 0; b < kMaxBlocks; ++b) {
       mbar_init(&ctl.blk_full[b], kGenWarps);
       mbar_init(&ctl.blk_empty[b], 1);
     }
@@ -255,54 +324,56 @@ __global__ void __maxnreg__(96) k_screen(const ScreenArgs a) {
     // ------------------------------------------------------- generators
     const int g = threadIdx.x;            // 0..255
     const int r = g >> 1, h = g & 1;      // column within the block, half of the entries
-    const int d = a.d, P = (d + 1) >> 1;
-    int q = 0;
-    for (int c = blockIdx.x; c < a.K; c += gridDim.x, ++q) {
-      const uint32_t cand = a.c0 + (uint32_t)c;
-      for (int b = 0; b < nb; ++b) {
-        if (q > 0) {
-          // one thread polls; the other generator warps block in hardware
-          const int slot = (q * nb + b) & 1;
+    // block b has been filled before (bit b of filled) and the parity of its
+    // fill count (bit b of fillpar); the named-barrier episode counter
+    uint32_t filled = 0u, fillpar = 0u, ep = 0u;
+    for (int idx = blockIdx.x; idx < nitems; idx += gridDim.x) {
+      ScreenItem it;
+      if (!src.item(idx, t0, delta0, it)) continue;
+      const int d = it.d, P = (d + 1) >> 1;
+      for (int b = 0; b < it.nb; ++b) {
+        if ((filled >> b) & 1u) {
+          // one thread polls for the previous fill's release; the other
+          // generator warps block in hardware
+          const int slot = (int)(ep++ & 1u);
           if (g == 0)
-            ctl.gen_go[slot] =
-                mbar_wait(&ctl.blk_empty[b], (uint32_t)((q - 1) & 1), &ctl, a.err, 64) ? 1 : 0;
+            ctl.gen_go[slot] = mbar_wait(&ctl.blk_empty[b], ((fillpar >> b) & 1u) ^ 1u, &ctl, err,
+                                         64) ? 1 : 0;
           group_sync(kBarGen, 32 * kGenWarps);
           if (!ctl.gen_go[slot]) goto gen_done;
         }
         const int j = b * kBlockCols + r;
         float xr[16], xi[16];
         float s = 0.f;
-        if (j < a.N && d == kDP) {
+        if (j < it.N && d == kDP) {
           // full width: entries 16h .. 16h+15 are 128 contiguous bytes of phi
-          const float4* col4 = reinterpret_cast<const float4*>(a.phi + (size_t)j * kDP + 16 * h);
+          const float4* col4 = reinterpret_cast<const float4*>(it.phi + (size_t)j * kDP + 16 * h);
           float4 v[8];
 #pragma unroll
           for (int pp = 0; pp < 8; ++pp) v[pp] = __ldg(col4 + pp);
 #pragma unroll
           for (int pp = 0; pp < 8; ++pp) {
             const uint32_t p = (uint32_t)(8 * h + pp);
-            const PhiloxOut u =
-                philox4x32_10_keys((uint32_t)j * (uint32_t)(kDP / 2) + p, cand, t, 0u, a.keys);
-            perturb_fast(u.x[0], u.x[1], delta, v[pp].x, v[pp].y, xr[2 * pp], xi[2 * pp]);
-            perturb_fast(u.x[2], u.x[3], delta, v[pp].z, v[pp].w, xr[2 * pp + 1], xi[2 * pp + 1]);
+            const PhiloxOut u = src.philox((uint32_t)j * (uint32_t)(kDP / 2) + p, it);
+            perturb_fast(u.x[0], u.x[1], it.delta, v[pp].x, v[pp].y, xr[2 * pp], xi[2 * pp]);
+            perturb_fast(u.x[2], u.x[3], it.delta, v[pp].z, v[pp].w, xr[2 * pp + 1], xi[2 * pp + 1]);
           }
 #pragma unroll
           for (int e = 0; e < 16; ++e) s = fmaf(xr[e], xr[e], fmaf(xi[e], xi[e], s));
-        } else if (j < a.N) {
-          const float2* col = a.phi + (size_t)j * d;
+        } else if (j < it.N) {
+          const float2* col = it.phi + (size_t)j * d;
 #pragma unroll
           for (int pp = 0; pp < 8; ++pp) {
             const int p = 8 * h + pp;
             if (p < P) {
-              const PhiloxOut u =
-                  philox4x32_10_keys((uint32_t)j * (uint32_t)P + (uint32_t)p, cand, t, 0u, a.keys);
+              const PhiloxOut u = src.philox((uint32_t)j * (uint32_t)P + (uint32_t)p, it);
 #pragma unroll
               for (int e = 0; e < 2; ++e) {
                 const int i = 2 * p + e;
                 float vr = 0.f, vi = 0.f;
                 if (i < d) {
                   const float2 v = col[i];
-                  perturb_fast(u.x[2 * e], u.x[2 * e + 1], delta, v.x, v.y, vr, vi);
+                  perturb_fast(u.x[2 * e], u.x[2 * e + 1], it.delta, v.x, v.y, vr, vi);
                 }
                 xr[2 * pp + e] = vr;
                 xi[2 * pp + e] = vi;
@@ -340,6 +411,8 @@ __global__ void __maxnreg__(96) k_screen(const ScreenArgs a) {
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&ctl.blk_full[b]);
+        filled |= 1u << b;
+        fillpar ^= 1u << b;
       }
     }
   gen_done:;
@@ -351,17 +424,20 @@ __global__ void __maxnreg__(96) k_screen(const ScreenArgs a) {
     const int qw = ew & 3;                           // TMEM lane quarter
     const int colh = 64 * (ew >> 2);                 // first accumulator column of this warp
     uint32_t gt = 0;                                 // tile counter
-    for (int c = blockIdx.x; c < a.K; c += gridDim.x) {
+    for (int idx = blockIdx.x; idx < nitems; idx += gridDim.x) {
+      ScreenItem it;
+      if (!src.item(idx, t0, delta0, it)) continue;
+      const int nb = it.nb;
       // four independent running maxima keep the max chain off the critical path
       float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
       bool ok = true;
       // tiles in the MMA issuer's row-major order: I = 0..nb-1, J = I..nb-1
       int I = 0, J = 0;
-      for (int tau = 0; tau < ntiles; ++tau, ++gt, J = (J + 1 < nb) ? J + 1 : ++I) {
+      for (int tau = 0; tau < it.ntiles; ++tau, ++gt, J = (J + 1 < nb) ? J + 1 : ++I) {
         const uint32_t buf = gt & 1u, use = gt >> 1;
         // one thread polls; the other epilogue warps block in hardware
         if (ew == 0 && lane == 0)
-          ctl.epi_go[gt & 1u] = mbar_wait(&ctl.acc_full[buf], use & 1u, &ctl, a.err, 32) ? 1 : 0;
+          ctl.epi_go[gt & 1u] = mbar_wait(&ctl.acc_full[buf], use & 1u, &ctl, err, 32) ? 1 : 0;
         group_sync(kBarEpi, 32 * kEpiWarps);
         if (!ctl.epi_go[gt & 1u]) { ok = false; break; }
         tc_fence_after();
@@ -419,28 +495,32 @@ __global__ void __maxnreg__(96) k_screen(const ScreenArgs a) {
       float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0) atomicMax(a.out + c, __float_as_uint(m));
+      if (lane == 0) atomicMax(it.out, __float_as_uint(m));
     }
   } else {
     // ------------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t gt = 0;
-      int q = 0;
+      uint32_t usepar = 0u;   // parity of the next fill of block b to consume (bit b)
       bool ok = true;
       // Row-major sweep: block I is last read in row I (as A for J >= I, as B
       // in rows I' <= I), so it is released right after its row and the next
       // candidate's block I is generated while rows I+1.. still run.  Row 0
       // reads every block; it waits for each one as it first needs it.
-      for (int c = blockIdx.x; c < a.K && ok; c += gridDim.x, ++q) {
+      for (int idx = blockIdx.x; idx < nitems && ok; idx += gridDim.x) {
+        ScreenItem it;
+        if (!src.item(idx, t0, delta0, it)) continue;
+        const int nb = it.nb;
         for (int I = 0; I < nb && ok; ++I) {
           for (int J = I; J < nb; ++J, ++gt) {
             if (I == 0) {
-              ok = mbar_wait(&ctl.blk_full[J], (uint32_t)(q & 1), &ctl, a.err);
+              ok = mbar_wait(&ctl.blk_full[J], (usepar >> J) & 1u, &ctl, err, kMmaBackoffNs);
               if (!ok) break;
+              usepar ^= 1u << J;
             }
             const uint32_t buf = gt & 1u, use = gt >> 1;
             if (use > 0) {
-              ok = mbar_wait(&ctl.acc_empty[buf], (use - 1u) & 1u, &ctl, a.err);
+              ok = mbar_wait(&ctl.acc_empty[buf], (use - 1u) & 1u, &ctl, err, kMmaBackoffNs);
               if (!ok) break;
             }
             tc_fence_after();
@@ -450,8 +530,8 @@ __global__ void __maxnreg__(96) k_screen(const ScreenArgs a) {
             // Re: sum over the whole K = 2*DP (4 steps of 16)
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-              mma_bf16(dre, smem_desc_sw128(aI + 32u * kk), smem_desc_sw128(bJ + 32u * kk), Idesc<kHalf>::pos,
-                       kk > 0 ? 1u : 0u);
+              mma_bf16(dre, smem_desc_sw128(aI + 32u * kk), smem_desc_sw128(bJ + 32u * kk),
+                       Idesc<kHalf>::pos, kk > 0 ? 1u : 0u);
             // Im: A_I^T B_J (K slices 0,1 against 2,3) - B_I^T A_J (2,3 against 0,1)
             mma_bf16(dim, smem_desc_sw128(aI + 0u), smem_desc_sw128(bJ + 64u), Idesc<kHalf>::pos, 0u);
             mma_bf16(dim, smem_desc_sw128(aI + 32u), smem_desc_sw128(bJ + 96u), Idesc<kHalf>::pos, 1u);
@@ -464,7 +544,7 @@ __global__ void __maxnreg__(96) k_screen(const ScreenArgs a) {
       }
       // all issued MMAs complete before tensor memory is released
       mma_commit(&ctl.drain);
-      mbar_wait(&ctl.drain, 0u, &ctl, a.err);
+      mbar_wait(&ctl.drain, 0u, &ctl, err);
     }
     __syncwarp();
   }
@@ -481,6 +561,24 @@ __global__ void __maxnreg__(96) k_screen(const ScreenArgs a) {
 
 size_t screen_smem_bytes(int nb) { return (size_t)nb * kBlockBytes + 1024; }
 
+template <class K> cudaError_t allow_screen_smem(K kernel, int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              std::min((int)screen_smem_bytes(kMaxBlocks),
+                                       optin - (int)fa.sharedSizeBytes));
+}
+
+// refuse (without launching) a configuration the SM cannot hold
+template <class K> cudaError_t screen_fits(K kernel) {
+  int fit = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, kThreads,
+                                                                screen_smem_bytes(kMaxBlocks));
+  if (e != cudaSuccess) return e;
+  return fit < 1 ? cudaErrorLaunchOutOfResources : cudaSuccess;
+}
+
 }  // namespace
 
 bool screen_supported(int N, int d) {
@@ -489,17 +587,11 @@ bool screen_supported(int N, int d) {
 }
 
 cudaError_t init_screen_attributes(int optin) {
-  cudaFuncAttributes fa;
-  const int want = (int)screen_smem_bytes(kMaxBlocks);
-  cudaError_t e = cudaFuncGetAttributes(&fa, k_screen<false>);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_screen<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           std::min(want, optin - (int)fa.sharedSizeBytes));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncGetAttributes(&fa, k_screen<true>);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_screen<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              std::min(want, optin - (int)fa.sharedSizeBytes));
+  cudaError_t e;
+  if ((e = allow_screen_smem(k_screen<false, OneInstance>, optin)) != cudaSuccess) return e;
+  if ((e = allow_screen_smem(k_screen<true, OneInstance>, optin)) != cudaSuccess) return e;
+  if ((e = allow_screen_smem(k_screen<false, ManyInstances>, optin)) != cudaSuccess) return e;
+  return allow_screen_smem(k_screen<true, ManyInstances>, optin);
 }
 
 cudaError_t launch_screen(bool fp16, int N, int d, uint64_t seed, const float2* phi32, int K,
@@ -507,7 +599,8 @@ cudaError_t launch_screen(bool fp16, int N, int d, uint64_t seed, const float2* 
                           unsigned int* mu2_out, uint32_t* err_flag, int num_sms,
                           cudaStream_t s) {
   if (!screen_supported(N, d) || K < 1) return cudaErrorInvalidValue;
-  ScreenArgs a;
+  OneInstance src;
+  ScreenArgs& a = src.a;
   a.N = N; a.d = d;
   a.nb = (N + kBlockCols - 1) / kBlockCols;
   a.ntiles = a.nb * (a.nb + 1) / 2;
@@ -515,16 +608,30 @@ cudaError_t launch_screen(bool fp16, int N, int d, uint64_t seed, const float2* 
   a.keys = philox_round_keys(seed);
   a.st = st; a.out = mu2_out; a.err = err_flag;
   const int grid = std::min(K, num_sms);
-  // refuse (without launching) a configuration the SM cannot hold
-  int fit = 0;
-  cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &fit, fp16 ? k_screen<true> : k_screen<false>, kThreads, screen_smem_bytes(kMaxBlocks));
-  if (oe != cudaSuccess) return oe;
-  if (fit < 1) return cudaErrorLaunchOutOfResources;
+  cudaError_t e = fp16 ? screen_fits(k_screen<true, OneInstance>)
+                       : screen_fits(k_screen<false, OneInstance>);
+  if (e != cudaSuccess) return e;
   // the operand area is always reserved for the largest block count, so every
   // descriptor address lies inside the CTA's shared memory
-  if (fp16) k_screen<true><<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(a);
-  else k_screen<false><<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(a);
+  if (fp16) k_screen<true, OneInstance><<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(src);
+  else k_screen<false, OneInstance><<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(src);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_screen_batched(bool fp16, const ScreenSlot* slots, const uint2* items,
+                                  int n_items, uint32_t* err_flag, int num_sms, cudaStream_t s) {
+  if (n_items < 1) return cudaSuccess;
+  ManyInstances src;
+  src.slots = slots;
+  src.items = items;
+  src.n_items = n_items;
+  src.error = err_flag;
+  const int grid = std::min(n_items, num_sms);
+  cudaError_t e = fp16 ? screen_fits(k_screen<true, ManyInstances>)
+                       : screen_fits(k_screen<false, ManyInstances>);
+  if (e != cudaSuccess) return e;
+  if (fp16) k_screen<true, ManyInstances><<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(src);
+  else k_screen<false, ManyInstances><<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(src);
   return cudaGetLastError();
 }
 

@@ -88,5 +88,64 @@ def test_batch_rejects_bad_arguments():
     with pytest.raises(T.TrstmiError):
         T.Batch([1], [2], [0])
     with pytest.raises(T.TrstmiError) as e:
-        T.Batch([4], [2], [0], precision="bf16")
-    assert e.value.status == T.TRSTMI_EUNSUPPORTED
+        T.Batch([4], [2], [0], precision="bf16", K=4, topk=8)
+    assert e.value.status == T.TRSTMI_EINVAL
+
+
+# shapes of the screen modes: inside the tensor-core screen's range (d <= 32,
+# N <= 1536) and outside it (d = 40; N = 1600), which rank in binary32
+SCREEN_MIX = [(4, 2), (9, 3), (40, 8), (129, 13), (200, 16), (17, 16), (300, 32), (1024, 32),
+              (50, 40), (1600, 4)]
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_batch_screen_modes_match_single_runs_bitwise(precision):
+    """Precision form in the batch: the shared screen launch over all
+    (instance, candidate) items, shared top-k re-score and certification.
+    With the default radius gate both regimes occur (screen while delta >=
+    0.01, binary32 ranking below), and every instance's decisions, certified
+    scores and final frame equal its standalone run."""
+    Ns = [n for n, _ in SCREEN_MIX]
+    ds = [d for _, d in SCREEN_MIX]
+    seeds = [300 + i for i in range(len(SCREEN_MIX))]
+    K, iters = 48, 14
+    with T.Batch(Ns, ds, seeds, K=K, precision=precision, topk=6, trace_cap=64) as b:
+        info = b.step(iters)
+        assert info.iters_done == iters
+        mus, its = b.mu()
+        assert np.all(its == iters)
+        screened = 0
+        for i, (N, d) in enumerate(SCREEN_MIX):
+            with T.Search(N, d, seeds[i], K=K, precision=precision, topk=6, trace_cap=64) as s:
+                s.step(iters)
+                tr_single = s.trace()
+                phi_single = s.get_phi()
+                mu_single = s.step(0).mu
+            tr = b.trace(i)
+            for f in ("cstar", "accepted", "flags", "mu2_best", "mu2_screen", "delta_used"):
+                assert np.array_equal(tr[f], tr_single[f]), (f, i, N, d)
+            assert np.array_equal(b.get_phi(i), phi_single), (i, N, d)
+            assert mus[i] == mu_single
+            if d > 32 or N > 1536:
+                assert np.all(tr["flags"] & 1 == 0)
+            screened += int(np.sum(tr["flags"] & 1))
+        assert screened > 0
+
+
+def test_batch_bf16_decisions_replay_in_fp64():
+    """Independent check of the batched precision form: the oracle replays the
+    chosen candidates of each instance in binary64 and reproduces every
+    certified score, decision and the final frame."""
+    Ns, ds, seeds = [6, 30, 300], [3, 5, 24], [41, 42, 43]
+    K, iters = 64, 12
+    with T.Batch(Ns, ds, seeds, K=K, precision="bf16", screen_min_delta=0.0, trace_cap=32) as b:
+        phi0 = [b.get_phi(i) for i in range(3)]
+        b.step(iters)
+        for i in range(3):
+            tr = b.trace(i)
+            assert np.all(tr["flags"] & 1 == 1)
+            rphi, rm2, _, rtr = O.replay(phi0[i], seeds[i], O.make_opts(K=K, T=iters), 0.1,
+                                         O.mu2(phi0[i]), 0, tr["cstar"])
+            assert np.allclose(tr["mu2_best"], rtr["mu2_best"], rtol=1e-12, atol=0)
+            assert np.array_equal(tr["accepted"], rtr["accepted"])
+            assert np.abs(b.get_phi(i) - rphi).max() < 1e-12

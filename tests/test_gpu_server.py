@@ -49,6 +49,32 @@ def test_results_equal_standalone_runs():
             assert res.mu <= target
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_screen_mode_results_equal_standalone_runs(precision):
+    """Precision form through the serving loop (screen, fp32 top-k re-score,
+    fp64 certification as shared launches over the resident slots): each
+    result equals the standalone run of the same request bit for bit."""
+    K = 32
+    reqs = [(4, 2, 21, 120, 0.5775), (40, 6, 22, 30, 0.0), (300, 24, 23, 10, 0.0),
+            (50, 40, 24, 12, 0.0), (1024, 32, 25, 4, 0.0), (12, 4, 26, 40, 0.0)]
+    with T.Server(hbm_budget=256 << 20, max_slots=4, iters_per_round=5, K=K, topk=4,
+                  precision=precision) as srv:
+        tickets = [srv.submit(N, d, seed, budget, target_mu=target, want_phi=True)
+                   for N, d, seed, budget, target in reqs]
+        results = [srv.wait(t, with_phi=True) for t in tickets]
+        stats = srv.stats()
+    assert stats.completed == len(reqs) and stats.worker_status == 0
+    for (N, d, seed, budget, target), (st, res, phi) in zip(reqs, results):
+        assert st == T.TRSTMI_OK
+        with T.Search(N, d, seed, K=K, topk=4, precision=precision, target_mu=target,
+                      trace_cap=0) as s:
+            s.step(budget)
+            info = s.step(0)
+            phi_alone = s.get_phi()
+        assert res.mu == info.mu, (N, d)
+        assert np.array_equal(phi, phi_alone), (N, d)
+
+
 def test_admission_respects_memory_budget():
     # each (N=1024, d=32) slot needs ~0.8 MiB; a 2 MiB budget holds two at a time
     with T.Server(hbm_budget=2 << 20, max_slots=8, iters_per_round=2, K=8,
@@ -95,8 +121,8 @@ def test_bad_requests_rejected_on_host():
                 srv.submit(bad[0], bad[1], 0, 10)
             assert e.value.status == T.TRSTMI_EINVAL
     with pytest.raises(T.TrstmiError) as e:
-        T.Server(precision="bf16")
-    assert e.value.status == T.TRSTMI_EUNSUPPORTED
+        T.Server(precision="bf16", K=4, topk=8)
+    assert e.value.status == T.TRSTMI_EINVAL
 
 
 def test_serving_request_mix_runs():
