@@ -43,7 +43,7 @@ WORKLOADS = {
     "plain_d8_n64": (8, 64, 4096, "fp32",
                      "complex d=8 N=64, 4096 candidates/iteration, plain fp32"),
     "batched_512": (None, None, 512, "fp32", "512 uneven instances in shared launches"),
-    "serving": (None, None, 8, "fp32", "Poisson request stream through the serving loop"),
+    "serving": (None, None, 8, "bf16", "Poisson request stream through the serving loop"),
     "plain_d2_n4_fp64": (2, 4, 256, "fp64",
                          "complex d=2 N=4, 256 candidates/iteration, fp64"),
 }
@@ -499,20 +499,22 @@ def run_batched(args, ws, rank, local, dist, torch, T):
 
 def run_serving(args, ws, rank, local, dist, torch, T):
     """Seeded Poisson stream of search requests (d ~ U{4..64}, N log-uniform on
-    [d+1, 4096], target 1.05 x Welch, K = 8) replayed into the serving loop;
-    every request runs to its target or its iteration budget.  Reported: p50 /
-    p99 latency (submit -> done) and pairs scored per second of wall time; next
-    to it, the same requests served one at a time by the plain fp32
+    [d+1, 4096], target 1.05 x Welch, K = 8) replayed into the serving loop in
+    the precision form (bf16 screen, fp32 re-score of the top 2, fp64
+    certification; shapes outside the screen's range rank in fp32); every
+    request runs to its target or its iteration budget.  Reported: p50 / p99
+    latency (submit -> done) and pairs scored per second of wall time; next to
+    it, the same requests served one at a time by the plain fp32
     single-instance path (measured standalone run times, FIFO on the same
     arrival times)."""
     import threading
     from paper_2207_06374_gb300 import workloads as W
-    K = 8
+    K, prec, topk = 8, WORKLOADS["serving"][3], 2
     reqs = W.serving_requests(args.requests, seed=11 + rank, rate_hz=args.rate)
     budget = args.budget
     with Clocks(local) as clk:
         srv = T.Server(hbm_budget=8 << 30, max_slots=256, iters_per_round=10, K=K,
-                       precision="fp32", device=local, trace_cap=0)
+                       precision=prec, topk=topk, device=local, trace_cap=0)
         tickets = [None] * len(reqs)
         t0 = time.perf_counter()
 
@@ -534,6 +536,7 @@ def run_serving(args, ws, rank, local, dist, torch, T):
     lat = np.array([(res.t_done_ns - res.t_submit_ns) * 1e-9 for _, res, _ in results])
     ok = sum(1 for st, _, _ in results if st == T.TRSTMI_OK)
     pairs = sum(res.pairs_scored for _, res, _ in results)
+    n_screened = sum(1 for r in reqs if r["d"] <= 32 and r["N"] <= 1536)
     reached = sum(res.reached_target for _, res, _ in results)
     # plain fp32 single-instance path, one request at a time (same requests)
     run_s = []
@@ -554,19 +557,23 @@ def run_serving(args, ws, rank, local, dist, torch, T):
     line = {"metric": "serving: p50/p99 solve latency and off-diagonal Gram pairs scored per second",
             "value": pairs / wall, "unit": "pairs/s", "n_gpus": ws, "steps": len(reqs),
             "warmup": 0, "ms_per_step": 1e3 * wall / max(len(reqs), 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec == "bf16" else "f32",
             "data": "synthetic (seeded Poisson request stream, seeded Philox frames)",
             "config": {"workload": "serving",
                        "description": f"{len(reqs)} requests, Poisson {args.rate}/s, d ~ U{{4..64}}, "
                                       f"N log-uniform [d+1, 4096], target 1.05 x Welch, budget "
-                                      f"{budget} iterations, K={K}, fp32 ranking and acceptance",
+                                      f"{budget} iterations, K={K}, "
+                                      + ("bf16 screen + fp32 top-2 re-score + fp64 certify"
+                                         if prec == "bf16" else "fp32 ranking and acceptance"),
                        "deviation": "the recipe's 10k requests x 2000 iterations exceed the GPU's "
                                     "capacity many times over; request count and budget are scaled "
                                     "down (CLI) and the run drains the whole stream",
                        "requests": len(reqs), "rate_hz": args.rate, "budget_iters": budget, "K": K,
+                       "precision": prec, "topk": topk,
                        "max_slots": 256, "iters_per_round": 10},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "max": float(lat.max())},
+            "requests_in_screen_range": n_screened,
             "sequential_single_instance_fp32": {
                 "p50": float(np.percentile(seq_lat, 50)), "p99": float(np.percentile(seq_lat, 99)),
                 "sum_run_s": float(sum(run_s))},

@@ -73,6 +73,58 @@ __device__ __forceinline__ PhiloxOut philox4x32_10_keys(uint32_t c0, uint32_t c1
   return o;
 }
 
+// Candidate-constant part of the first two rounds.  Within one candidate the
+// counter words (c, t, 0) are fixed and only e varies, so round 1's product
+// of the t word and round 2's product of the resulting word do not depend on
+// e: they are formed once per candidate and each draw starts from them.
+struct PhiloxCand {
+  uint32_t c1k;   // round 2: low half of round 1's t product, xor round key k0[1]
+  uint32_t c2k;   // round 2: high half of (mulA x round 1's first word) xor k1[1]
+  uint32_t c3;    // round 2: low half of that product
+};
+
+__host__ __device__ inline PhiloxCand philox_cand(uint32_t c, uint32_t t, uint32_t k0_0,
+                                                  uint32_t k0_1, uint32_t k1_1) {
+  const uint64_t pB = (uint64_t)0xCD9E8D57u * (uint64_t)t;
+  const uint32_t w0 = (uint32_t)(pB >> 32) ^ c ^ k0_0;       // round 1, first word
+  const uint64_t pA = (uint64_t)0xD2511F53u * (uint64_t)w0;  // round 2 product of it
+  PhiloxCand pc;
+  pc.c1k = (uint32_t)pB ^ k0_1;
+  pc.c2k = (uint32_t)(pA >> 32) ^ k1_1;
+  pc.c3 = (uint32_t)pA;
+  return pc;
+}
+
+// Philox4x32-10 of the counter (e, c, t, 0) from its candidate constants;
+// k1_0 is the round-1 key k1, K0(r) / K1(r) give the keys of rounds r = 2..9.
+template <class KeyFn>
+__device__ __forceinline__ PhiloxOut philox_from_cand(uint32_t e, const PhiloxCand& pc,
+                                                      uint32_t k1_0, KeyFn keys) {
+  constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+  const uint64_t p1 = (uint64_t)kMulA * (uint64_t)e;
+  const uint32_t w2 = (uint32_t)(p1 >> 32) ^ k1_0;           // round 1, third word
+  const uint64_t p2 = (uint64_t)kMulB * (uint64_t)w2;
+  uint32_t c0 = (uint32_t)(p2 >> 32) ^ pc.c1k;
+  uint32_t c1 = (uint32_t)p2;
+  uint32_t c2 = pc.c2k ^ (uint32_t)p1;
+  uint32_t c3 = pc.c3;
+#pragma unroll
+  for (int r = 2; r < 10; ++r) {
+    uint32_t k0, k1;
+    keys(r, k0, k1);
+    const uint64_t pA = (uint64_t)kMulA * (uint64_t)c0;
+    const uint64_t pB = (uint64_t)kMulB * (uint64_t)c2;
+    const uint32_t n0 = (uint32_t)(pB >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = (uint32_t)(pA >> 32) ^ c3 ^ k1;
+    c1 = (uint32_t)pB;
+    c3 = (uint32_t)pA;
+    c0 = n0; c2 = n2;
+  }
+  PhiloxOut o;
+  o.x[0] = c0; o.x[1] = c1; o.x[2] = c2; o.x[3] = c3;
+  return o;
+}
+
 // --- uniform -> complex normal, three precisions -------------------------
 
 // Double precision: U = (u + 0.5) * 2^-32 is exact in binary64.
@@ -134,6 +186,36 @@ __device__ __forceinline__ void perturb_fast(uint32_t ua, uint32_t ub, float del
   const float dr = delta * r;
   xr = __fmaf_rn(-dr, c, vr);
   xi = __fmaf_rn(-dr, s, vi);
+}
+
+// Both entries of one draw (u0..u3) perturbed at once with paired binary32
+// arithmetic, same approximations as perturb_fast: x0 = v0 + delta Z(u0, u1),
+// x1 = v1 + delta Z(u2, u3).
+__device__ __forceinline__ void perturb2_fast(const uint32_t (&u)[4], float delta, float2 v0,
+                                              float2 v1, float2& x0, float2& x1) {
+  const float2 Ua = __ffma2_rn(make_float2(__uint2float_rn(u[0]), __uint2float_rn(u[2])),
+                               make_float2(0x1.0p-32f, 0x1.0p-32f),
+                               make_float2(0x1.0p-33f, 0x1.0p-33f));
+  float2 l2;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2.x) : "f"(Ua.x));
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2.y) : "f"(Ua.y));
+  // sqrt(-ln U) = sqrt(ln 2) sqrt(|log2 U|); the factor sqrt(ln 2) joins the
+  // radius below, and the magnitude guards a tiny positive approximation of
+  // log2 near U = 1
+  float2 r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(fabsf(l2.x)));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(fabsf(l2.y)));
+  const float2 f = make_float2(__int_as_float(0x3f800000u | (u[1] >> 9)),
+                               __int_as_float(0x3f800000u | (u[3] >> 9)));
+  const float2 th = __ffma2_rn(f, make_float2(6.28318530717958648f, 6.28318530717958648f),
+                               make_float2(-9.42477796076937972f, -9.42477796076937972f));
+  float s0, c0, s1, c1;
+  __sincosf(th.x, &s0, &c0);
+  __sincosf(th.y, &s1, &c1);
+  const float ds = -delta * 0.83255461115769776f;   // -delta sqrt(ln 2)
+  const float2 dr = __fmul2_rn(r, make_float2(ds, ds));
+  x0 = __ffma2_rn(make_float2(dr.x, dr.x), make_float2(c0, s0), v0);
+  x1 = __ffma2_rn(make_float2(dr.y, dr.y), make_float2(c1, s1), v1);
 }
 
 __device__ __forceinline__ uint32_t seed_lo(uint64_t s) { return (uint32_t)(s & 0xffffffffull); }

@@ -11,11 +11,12 @@
 // (coherence: arXiv 2207.06374, Sec. "Introduction"; upper triangle only:
 // Sec. "Optimization procedure").
 //
-// Roles (13 warps): warps 0-7 generate column blocks, warps 8-11 (one
-// warpgroup) read the accumulators, warp 12 owns tensor memory and issues the
-// MMAs.  Shared-memory column blocks and the two accumulator buffers are
-// handed over with mbarriers; every wait is bounded in time and gives up by
-// setting an error bit instead of spinning forever.
+// Roles (20 warps): ten generator warps fill column blocks into a ring of
+// shared-memory slots, eight epilogue warps read the accumulators, warp 0
+// owns tensor memory and issues the MMAs.  Slots and
+// the two accumulator buffers are handed over with mbarriers; every wait is
+// bounded in time and gives up by setting an error bit instead of spinning
+// forever.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -31,10 +32,27 @@ constexpr int kDP = 32;                 // padded d: K = 2*kDP = 64 bf16 = 128 b
 constexpr int kBlockCols = 128;         // columns per block = MMA M = N
 constexpr int kBlockBytes = kBlockCols * 2 * kDP * 2;   // 16 KiB
 constexpr int kMaxBlocks = 12;          // N <= 1536
-constexpr int kGenWarps = 8, kEpiWarps = 8;
-constexpr int kEpiWarp0 = kGenWarps;                   // warps 8..15: two whole warpgroups
-constexpr int kMmaWarp = kGenWarps + kEpiWarps;        // warp 16
-constexpr int kThreads = 32 * (kMmaWarp + 1);          // 544
+constexpr int kRing = kMaxBlocks;       // block slots, used as a ring across candidates
+// Warp roles.  A warp runs on SM sub-partition (warp % 4), and reads only
+// the tensor-memory lanes 32 (warp % 4) .. +31.  Sub-partition 0 holds the MMA
+// issuer (warp 0), two epilogue warps (4 and 8) and a single generator (12),
+// so the long integer-multiply streams of the random draws rarely delay an
+// MMA issue; the other nine generators (warps 1-3, 13-15, 17-19) share
+// sub-partitions 1-3 with the other epilogue warps; warp 16 idles.
+constexpr int kWarps = 20;
+constexpr int kThreads = 32 * kWarps;                  // 640
+constexpr int kMmaWarp = 0;
+constexpr int kEpiWarp0 = 4, kEpiWarps = 8;            // warps 4..11: two warpgroups
+constexpr int kGenWarps = 10;
+constexpr int kOctets = 16;                            // 8-column units of a block
+__host__ __device__ constexpr int gen_index(int w) {
+  return w == 12 ? 9
+         : (w % 4 == 0 || (w >= kEpiWarp0 && w < kEpiWarp0 + kEpiWarps)) ? -1
+         : w < 4 ? w - 1 : w < 16 ? w - 13 + 3 : w - 17 + 6;
+}
+static_assert(gen_index(1) == 0 && gen_index(15) == 5 && gen_index(19) == 8 &&
+                  gen_index(12) == kGenWarps - 1 && gen_index(16) == -1 && gen_index(0) == -1,
+              "roles");
 constexpr uint32_t kTmemCols = 512;                    // 2 buffers x (128 Re + 128 Im)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 #ifndef TRSTMI_MMA_BACKOFF_NS
@@ -55,18 +73,13 @@ struct ScreenArgs {
 };
 
 struct SmemCtl {
-  unsigned long long blk_full[kMaxBlocks];
-  unsigned long long blk_empty[kMaxBlocks];
-  unsigned long long acc_full[2];
-  unsigned long long acc_empty[2];
+  unsigned long long blk_full[kRing];    // slot filled (8 generator warps arrive)
+  unsigned long long blk_empty[kRing];   // slot's last MMA done (tcgen05.commit)
+  unsigned long long acc_full[2];        // accumulator buffer ready (tcgen05.commit)
+  unsigned long long acc_empty[2];       // buffer read (the 8 epilogue warps)
   unsigned long long drain;
   uint32_t tmem_base;
   volatile int abort_flag;
-  // Decision of a group's elected waiter for one barrier episode, read by the
-  // whole group after the named barrier.  Two slots alternate: slot e & 1 is
-  // rewritten only after every member has passed barrier e + 1, i.e. after
-  // it has read slot e & 1, so all members always act on the same value.
-  int gen_go[2], epi_go[2];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -116,12 +129,6 @@ __device__ bool mbar_wait(unsigned long long* b, uint32_t parity, SmemCtl* ctl, 
   }
 }
 
-// Hardware named barrier over a role group: blocked warps issue nothing.
-__device__ __forceinline__ void group_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-constexpr int kBarGen = 1, kBarEpi = 2;
-
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -132,18 +139,11 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// UMMA shared-memory descriptor: K-major operand in the 128-byte swizzled
-// layout (8 rows x 128 B atoms, 1024 B apart).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFFu);          // start address
-  d |= (uint64_t)1u << 16;                          // leading byte offset (unused: 16 B)
-  d |= (uint64_t)(1024u >> 4) << 32;                // stride byte offset: 1024 B
-  d |= (uint64_t)1u << 46;                          // descriptor version
-  d |= (uint64_t)2u << 61;                          // 128-byte swizzle
-  return d;
-}
-
+// UMMA shared-memory descriptor of a K-major operand in the 128-byte
+// swizzled layout (8 rows x 128 B atoms, 1024 B apart): start address >> 4 in
+// bits 0-13, leading byte offset 1 (unused) in bits 16-29, stride byte offset
+// 1024 >> 4 in bits 32-45, version 1 in bits 46-47, swizzle mode 2 in bits
+// 61-63.  A step of 16 bf16 along K is 32 bytes, i.e. +2 in the low word.
 // Instruction descriptor, kind::f16: D fp32, A and B both bf16 (format 1)
 // or both fp16 (format 0), both K-major, M = N = 128; bit 13 negates A.
 template <bool kHalf> struct Idesc {
@@ -153,12 +153,21 @@ template <bool kHalf> struct Idesc {
   static constexpr uint32_t neg_a = pos | (1u << 13);
 };
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
+// High word of every operand descriptor (stride byte offset 1024 B, version
+// bit, 128-byte swizzle); the low word carries the start address.
+constexpr uint32_t kDescHi = (1024u >> 4) | (1u << 14) | (2u << 29);
+__device__ __forceinline__ uint32_t desc_lo(uint32_t addr) {
+  return ((addr >> 4) & 0x3FFFu) | (1u << 16);
+}
+
+// One MMA from the low descriptor words (the high word is kDescHi).
+__device__ __forceinline__ void mma_lo(uint32_t tmem_d, uint32_t alo, uint32_t blo,
+                                       uint32_t idesc, uint32_t accumulate, uint32_t hi) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      "{\n .reg .pred p;\n .reg .b64 da, db;\n setp.ne.b32 p, %4, 0;\n"
+      " mov.b64 da, {%1, %5};\n mov.b64 db, {%2, %5};\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(alo), "r"(blo), "r"(idesc), "r"(accumulate), "r"(hi)
       : "memory");
 }
 
@@ -167,23 +176,6 @@ __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
       : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_ld_wait() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 template <bool kHalf> __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
@@ -240,8 +232,15 @@ struct OneInstance {
     it.out = a.out + idx;
     return true;
   }
-  __device__ PhiloxOut philox(uint32_t e, const ScreenItem& it) const {
-    return philox4x32_10_keys(e, it.cand, it.t, 0u, a.keys);
+  __device__ PhiloxCand cand(const ScreenItem& it) const {
+    return philox_cand(it.cand, it.t, a.keys.k0[0], a.keys.k0[1], a.keys.k1[1]);
+  }
+  __device__ PhiloxOut philox(uint32_t e, const PhiloxCand& pc, const ScreenItem&) const {
+    const PhiloxKeys& k = a.keys;
+    return philox_from_cand(e, pc, k.k1[0], [&](int r, uint32_t& k0, uint32_t& k1) {
+      k0 = k.k0[r];
+      k1 = k.k1[r];
+    });
   }
   __device__ uint32_t* err() const { return a.err; }
 };
@@ -270,13 +269,103 @@ struct ManyInstances {
     it.out = s.mu2 + w.y;
     return true;
   }
-  __device__ PhiloxOut philox(uint32_t e, const ScreenItem& it) const {
-    return philox4x32_10(e, it.cand, it.t, 0u, seed_lo(it.seed), seed_hi(it.seed));
+  __device__ PhiloxCand cand(const ScreenItem& it) const {
+    const uint32_t lo = seed_lo(it.seed), hi = seed_hi(it.seed);
+    return philox_cand(it.cand, it.t, lo, lo + 0x9E3779B9u, hi + 0xBB67AE85u);
+  }
+  __device__ PhiloxOut philox(uint32_t e, const PhiloxCand& pc, const ScreenItem& it) const {
+    const uint32_t lo = seed_lo(it.seed), hi = seed_hi(it.seed);
+    return philox_from_cand(e, pc, hi, [&](int r, uint32_t& k0, uint32_t& k1) {
+      k0 = lo + (uint32_t)r * 0x9E3779B9u;
+      k1 = hi + (uint32_t)r * 0xBB67AE85u;
+    });
   }
   __device__ uint32_t* err() const { return error; }
 };
 
-// 17 warps: one SM sub-partition (16K registers) holds 5 of them, so a
+// Bounded wait by every lane of a warp; the warp acts on the unanimous result.
+__device__ __forceinline__ bool warp_wait(unsigned long long* b, uint32_t parity, SmemCtl* ctl,
+                                          uint32_t* err, unsigned backoff_ns) {
+  const bool ok = mbar_wait(b, parity, ctl, err, backoff_ns);
+  return __all_sync(0xffffffffu, ok);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+}
+
+// Waits for the thread's outstanding tensor-memory loads.  The destination
+// registers of the awaited loads are passed through, so no use of them can be
+// placed before the wait.
+template <int W>
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&a)[W], uint32_t (&b)[W]);
+
+template <>
+__device__ __forceinline__ void tmem_wait_ld<16>(uint32_t (&a)[16], uint32_t (&b)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]),
+                 "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]),
+                 "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]), "+r"(b[0]), "+r"(b[1]),
+                 "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
+                 "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]),
+                 "+r"(b[14]), "+r"(b[15])
+               :
+               : "memory");
+}
+
+template <>
+__device__ __forceinline__ void tmem_wait_ld<32>(uint32_t (&a)[32], uint32_t (&b)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]),
+                 "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]),
+                 "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]), "+r"(a[16]), "+r"(a[17]),
+                 "+r"(a[18]), "+r"(a[19]), "+r"(a[20]), "+r"(a[21]), "+r"(a[22]), "+r"(a[23]),
+                 "+r"(a[24]), "+r"(a[25]), "+r"(a[26]), "+r"(a[27]), "+r"(a[28]), "+r"(a[29]),
+                 "+r"(a[30]), "+r"(a[31]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]),
+                 "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]), "+r"(b[8]), "+r"(b[9]),
+                 "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15]),
+                 "+r"(b[16]), "+r"(b[17]), "+r"(b[18]), "+r"(b[19]), "+r"(b[20]), "+r"(b[21]),
+                 "+r"(b[22]), "+r"(b[23]), "+r"(b[24]), "+r"(b[25]), "+r"(b[26]), "+r"(b[27]),
+                 "+r"(b[28]), "+r"(b[29]), "+r"(b[30]), "+r"(b[31])
+               :
+               : "memory");
+}
+
+// max of |G|^2 over W accumulator columns (Re in re, Im in im): two pairs per
+// packed multiply / fma, one three-input max per two pairs, spread over
+// eight running maxima so no max chain sits on the critical path.
+template <int W>
+__device__ __forceinline__ void absmax(const uint32_t (&re)[W], const uint32_t (&im)[W],
+                                       float (&m)[8]) {
+#pragma unroll
+  for (int e = 0; e < W; e += 2) {
+    const float2 x = make_float2(__uint_as_float(re[e]), __uint_as_float(re[e + 1]));
+    const float2 y = make_float2(__uint_as_float(im[e]), __uint_as_float(im[e + 1]));
+    const float2 v = __ffma2_rn(y, y, __fmul2_rn(x, x));
+    m[(e >> 1) & 7] = fmax3(m[(e >> 1) & 7], v.x, v.y);
+  }
+}
+
+// 20 warps: one SM sub-partition (16K registers) holds 5 of them, so a
 // thread may use at most 16384 / (5 * 32) -> 96 registers
 template <bool kHalf, class Src>
 __global__ void __maxnreg__(96) k_screen(const Src src) {
@@ -295,8 +384,8 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
   const int nitems = src.count();
 
   if (threadIdx.x == 0) {
-    for (int b = 0; b < kMaxBlocks; ++b) {
-      mbar_init(&ctl.blk_full[b], kGenWarps);
+    for (int b = 0; b < kRing; ++b) {
+      mbar_init(&ctl.blk_full[b], kOctets);
       mbar_init(&ctl.blk_empty[b], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -320,170 +409,163 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
   tc_fence_after();
   const uint32_t tmem = ctl.tmem_base;
 
-  if (warp < kGenWarps) {
+  const int gi = gen_index(warp);
+  if (gi >= 0) {
     // ------------------------------------------------------- generators
-    const int g = threadIdx.x;            // 0..255
-    const int r = g >> 1, h = g & 1;      // column within the block, half of the entries
-    // block b has been filled before (bit b of filled) and the parity of its
-    // fill count (bit b of fillpar); the named-barrier episode counter
-    uint32_t filled = 0u, fillpar = 0u, ep = 0u;
+    // The column blocks of successive candidates go round a ring of kRing
+    // slots (global block number gb -> slot gb % kRing, fill gb / kRing), so
+    // the next candidate's first blocks are generated into free slots while
+    // the current one is still being swept.  The work is cut into 8-column
+    // units (octets), numbered consecutively over all blocks of this CTA;
+    // generator gi takes the units u = gi (mod kGenWarps).  In a unit, lane l
+    // takes column 8o + (l & 7) and the quarter q = l >> 3 of its entries
+    // (8q .. 8q+7, four draws); the eight lanes of one quarter write eight
+    // different 16-byte chunks of a swizzled row group, so the stores are
+    // free of bank conflicts.  Each unit's warp arrives once on the slot's
+    // fill barrier (kOctets arrivals complete a fill).
+    const int q = lane >> 3;
+    uint32_t gb0 = 0;
     for (int idx = blockIdx.x; idx < nitems; idx += gridDim.x) {
       ScreenItem it;
       if (!src.item(idx, t0, delta0, it)) continue;
       const int d = it.d, P = (d + 1) >> 1;
-      for (int b = 0; b < it.nb; ++b) {
-        if ((filled >> b) & 1u) {
-          // one thread polls for the previous fill's release; the other
-          // generator warps block in hardware
-          const int slot = (int)(ep++ & 1u);
-          if (g == 0)
-            ctl.gen_go[slot] = mbar_wait(&ctl.blk_empty[b], ((fillpar >> b) & 1u) ^ 1u, &ctl, err,
-                                         64) ? 1 : 0;
-          group_sync(kBarGen, 32 * kGenWarps);
-          if (!ctl.gen_go[slot]) goto gen_done;
-        }
+      const PhiloxCand pc = src.cand(it);
+      const uint32_t u0 = gb0 * (uint32_t)kOctets;
+      const uint32_t u1 = u0 + (uint32_t)(it.nb * kOctets);
+      uint32_t u = u0 + ((uint32_t)gi + (uint32_t)kGenWarps - u0 % (uint32_t)kGenWarps) %
+                            (uint32_t)kGenWarps;
+      for (; u < u1; u += (uint32_t)kGenWarps) {
+        const uint32_t gb = u / (uint32_t)kOctets;
+        const int b = (int)(gb - gb0), o = (int)(u % (uint32_t)kOctets);
+        const uint32_t slot = gb % (uint32_t)kRing, fill = gb / (uint32_t)kRing;
+        if (fill > 0 && !warp_wait(&ctl.blk_empty[slot], (fill - 1u) & 1u, &ctl, err, 64))
+          goto gen_done;
+        unsigned char* blk = xs + slot * (uint32_t)kBlockBytes;
+        const int r = 8 * o + (lane & 7);        // row of the block (column of Phi)
         const int j = b * kBlockCols + r;
-        float xr[16], xi[16];
-        float s = 0.f;
+        float2 x[8];
+        float2 ss = make_float2(0.f, 0.f);
         if (j < it.N && d == kDP) {
-          // full width: entries 16h .. 16h+15 are 128 contiguous bytes of phi
-          const float4* col4 = reinterpret_cast<const float4*>(it.phi + (size_t)j * kDP + 16 * h);
-          float4 v[8];
+          // full width: entries 8q .. 8q+7 are 64 contiguous bytes of phi
+          const float4* col4 = reinterpret_cast<const float4*>(it.phi + (size_t)j * kDP + 8 * q);
+          float4 v[4];
 #pragma unroll
-          for (int pp = 0; pp < 8; ++pp) v[pp] = __ldg(col4 + pp);
+          for (int pp = 0; pp < 4; ++pp) v[pp] = __ldg(col4 + pp);
 #pragma unroll
-          for (int pp = 0; pp < 8; ++pp) {
-            const uint32_t p = (uint32_t)(8 * h + pp);
-            const PhiloxOut u = src.philox((uint32_t)j * (uint32_t)(kDP / 2) + p, it);
-            perturb_fast(u.x[0], u.x[1], it.delta, v[pp].x, v[pp].y, xr[2 * pp], xi[2 * pp]);
-            perturb_fast(u.x[2], u.x[3], it.delta, v[pp].z, v[pp].w, xr[2 * pp + 1], xi[2 * pp + 1]);
+          for (int pp = 0; pp < 4; ++pp) {
+            const PhiloxOut w =
+                src.philox((uint32_t)j * (uint32_t)(kDP / 2) + (uint32_t)(4 * q + pp), pc, it);
+            perturb2_fast(w.x, it.delta, make_float2(v[pp].x, v[pp].y),
+                          make_float2(v[pp].z, v[pp].w), x[2 * pp], x[2 * pp + 1]);
           }
-#pragma unroll
-          for (int e = 0; e < 16; ++e) s = fmaf(xr[e], xr[e], fmaf(xi[e], xi[e], s));
         } else if (j < it.N) {
           const float2* col = it.phi + (size_t)j * d;
 #pragma unroll
-          for (int pp = 0; pp < 8; ++pp) {
-            const int p = 8 * h + pp;
+          for (int pp = 0; pp < 4; ++pp) {
+            const int p = 4 * q + pp;
+            x[2 * pp] = x[2 * pp + 1] = make_float2(0.f, 0.f);
             if (p < P) {
-              const PhiloxOut u = src.philox((uint32_t)j * (uint32_t)P + (uint32_t)p, it);
-#pragma unroll
-              for (int e = 0; e < 2; ++e) {
-                const int i = 2 * p + e;
-                float vr = 0.f, vi = 0.f;
-                if (i < d) {
-                  const float2 v = col[i];
-                  perturb_fast(u.x[2 * e], u.x[2 * e + 1], it.delta, v.x, v.y, vr, vi);
-                }
-                xr[2 * pp + e] = vr;
-                xi[2 * pp + e] = vi;
-                s = fmaf(vr, vr, fmaf(vi, vi, s));
-              }
-            } else {
-              xr[2 * pp] = xr[2 * pp + 1] = 0.f;
-              xi[2 * pp] = xi[2 * pp + 1] = 0.f;
+              const PhiloxOut w = src.philox((uint32_t)j * (uint32_t)P + (uint32_t)p, pc, it);
+              const int i = 2 * p;
+              const float2 v0 = col[i];
+              const float2 v1 = (i + 1 < d) ? col[i + 1] : make_float2(0.f, 0.f);
+              float2 y0, y1;
+              perturb2_fast(w.x, it.delta, v0, v1, y0, y1);
+              x[2 * pp] = y0;
+              if (i + 1 < d) x[2 * pp + 1] = y1;
             }
           }
         } else {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) { xr[e] = 0.f; xi[e] = 0.f; }
+          for (int e = 0; e < 8; ++e) x[e] = make_float2(0.f, 0.f);
         }
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        const float inv = s > 0.f ? rsqrtf(s) : 0.f;
-        unsigned char* blk = xs + b * kBlockBytes;
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          uint4 re, im;
-          const int e0 = 8 * half;
-          re.x = pack2<kHalf>(xr[e0 + 0] * inv, xr[e0 + 1] * inv);
-          re.y = pack2<kHalf>(xr[e0 + 2] * inv, xr[e0 + 3] * inv);
-          re.z = pack2<kHalf>(xr[e0 + 4] * inv, xr[e0 + 5] * inv);
-          re.w = pack2<kHalf>(xr[e0 + 6] * inv, xr[e0 + 7] * inv);
-          im.x = pack2<kHalf>(xi[e0 + 0] * inv, xi[e0 + 1] * inv);
-          im.y = pack2<kHalf>(xi[e0 + 2] * inv, xi[e0 + 3] * inv);
-          im.z = pack2<kHalf>(xi[e0 + 4] * inv, xi[e0 + 5] * inv);
-          im.w = pack2<kHalf>(xi[e0 + 6] * inv, xi[e0 + 7] * inv);
-          // real parts of entries 16h + 8half .. +7 -> chunk 2h + half;
-          // imaginary parts -> chunk 4 + 2h + half
-          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * h + half)) = re;
-          *reinterpret_cast<uint4*>(blk + swz_offset(r, 4 + 2 * h + half)) = im;
-        }
+        for (int e = 0; e < 8; ++e) ss = __ffma2_rn(x[e], x[e], ss);
+        float sn = ss.x + ss.y;
+        sn += __shfl_xor_sync(0xffffffffu, sn, 8);
+        sn += __shfl_xor_sync(0xffffffffu, sn, 16);
+        const float inv = sn > 0.f ? rsqrtf(sn) : 0.f;
+        const float2 inv2 = make_float2(inv, inv);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = __fmul2_rn(x[e], inv2);
+        uint4 re, im;
+        re.x = pack2<kHalf>(x[0].x, x[1].x);
+        re.y = pack2<kHalf>(x[2].x, x[3].x);
+        re.z = pack2<kHalf>(x[4].x, x[5].x);
+        re.w = pack2<kHalf>(x[6].x, x[7].x);
+        im.x = pack2<kHalf>(x[0].y, x[1].y);
+        im.y = pack2<kHalf>(x[2].y, x[3].y);
+        im.z = pack2<kHalf>(x[4].y, x[5].y);
+        im.w = pack2<kHalf>(x[6].y, x[7].y);
+        // real parts of entries 8q .. 8q+7 -> chunk q; imaginary -> chunk 4 + q
+        *reinterpret_cast<uint4*>(blk + swz_offset(r, q)) = re;
+        *reinterpret_cast<uint4*>(blk + swz_offset(r, 4 + q)) = im;
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&ctl.blk_full[b]);
-        filled |= 1u << b;
-        fillpar ^= 1u << b;
+        if (lane == 0) mbar_arrive(&ctl.blk_full[slot]);
       }
+      gb0 += (uint32_t)it.nb;
     }
   gen_done:;
-  } else if (warp < kMmaWarp) {
+  } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
     // --------------------------------------------------------- epilogue
-    // warps 8..11 take accumulator columns 0..63 of every tile, warps 12..15
-    // columns 64..127; within a warpgroup, warp w reads TMEM lanes 32(w%4)..
-    const int ew = warp - kEpiWarp0;
-    const int qw = ew & 3;                           // TMEM lane quarter
-    const int colh = 64 * (ew >> 2);                 // first accumulator column of this warp
-    uint32_t gt = 0;                                 // tile counter
+    // All eight warps read every tile: warp w takes TMEM lanes 32(w%4) .. +31
+    // (its rows of the tile) and the accumulator columns 64h .. 64h+63,
+    // h = (w - 4) / 4, in two rounds of 32 Re and 32 Im columns (few, large
+    // loads).  With two accumulator buffers the reading of tile t has to end
+    // within the MMAs of tile t+1, so the tile is split as finely as the
+    // warps allow rather than handed to alternating groups.
+    const int qw = warp & 3;
+    const int colh = 64 * ((warp - kEpiWarp0) >> 2);
+    uint32_t gt = 0;
     for (int idx = blockIdx.x; idx < nitems; idx += gridDim.x) {
       ScreenItem it;
       if (!src.item(idx, t0, delta0, it)) continue;
       const int nb = it.nb;
-      // four independent running maxima keep the max chain off the critical path
-      float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+      float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bool ok = true;
-      // tiles in the MMA issuer's row-major order: I = 0..nb-1, J = I..nb-1
       int I = 0, J = 0;
       for (int tau = 0; tau < it.ntiles; ++tau, ++gt, J = (J + 1 < nb) ? J + 1 : ++I) {
         const uint32_t buf = gt & 1u, use = gt >> 1;
-        // one thread polls; the other epilogue warps block in hardware
-        if (ew == 0 && lane == 0)
-          ctl.epi_go[gt & 1u] = mbar_wait(&ctl.acc_full[buf], use & 1u, &ctl, err, 32) ? 1 : 0;
-        group_sync(kBarEpi, 32 * kEpiWarps);
-        if (!ctl.epi_go[gt & 1u]) { ok = false; break; }
+        if (!warp_wait(&ctl.acc_full[buf], use & 1u, &ctl, err, 32)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t base = tmem + ((uint32_t)(32 * qw) << 16) + buf * 256u + (uint32_t)colh;
+        // the base is re-materialised per tile so the chunk addresses are
+        // formed next to their loads instead of being held across the loop
+        uint32_t base;
+        asm volatile("mov.b32 %0, %1;" : "=r"(base) : "r"(tmem + ((uint32_t)(32 * qw) << 16) +
+                                                          buf * 256u + (uint32_t)colh));
+        if (I != J) {
+          uint32_t ra[32], ia[32];
 #pragma unroll 1
-        for (int ch = 0; ch < 2; ++ch) {
-          // On a diagonal tile only k > j counts: this warp's rows are
-          // 32qw..32qw+31 and the chunk's columns n0..n0+31, so the chunk is
-          // entirely below the diagonal (skip), entirely above (no mask) or
-          // straddles it (n0 == 32qw: mask column e against row lane).
-          const int n0 = colh + 32 * ch;
-          const bool diag = (I == J);
-          if (diag && n0 < 32 * qw) continue;
-          uint32_t re[32], im[32];
-          tmem_ld32(base + 32u * ch, re);
-          tmem_ld32(base + 128u + 32u * ch, im);
-          tmem_ld_wait();
-          if (!diag || n0 > 32 * qw) {
-            // two pairs per packed multiply / fma, one three-input max
+          for (int ch = 0; ch < 2; ++ch) {
+            tmem_ld32(base + 32u * ch, ra);
+            tmem_ld32(base + 128u + 32u * ch, ia);
+            tmem_wait_ld<32>(ra, ia);
+            absmax<32>(ra, ia, m);
+          }
+        } else {
+          // diagonal tile: only column k > row j counts.  This warp's rows
+          // are 32qw .. 32qw+31; a 16-column chunk n0 .. n0+15 lies entirely
+          // at or below the diagonal (skip), entirely above it (no mask), or
+          // straddles it (mask column n0 + e against row 32qw + lane).
+          uint32_t ra[16], ia[16];
+#pragma unroll 1
+          for (int ch = 0; ch < 4; ++ch) {
+            const int n0 = colh + 16 * ch;
+            if (n0 + 16 <= 32 * qw) continue;
+            tmem_ld16(base + 16u * ch, ra);
+            tmem_ld16(base + 128u + 16u * ch, ia);
+            tmem_wait_ld<16>(ra, ia);
+            if (n0 >= 32 * qw + 32) {
+              absmax<16>(ra, ia, m);
+            } else {
+              const int lim = 32 * qw + lane - n0;   // mask e <= lim
 #pragma unroll
-            for (int e = 0; e < 32; e += 8) {
-              float2 x, y, v;
-              x = make_float2(__uint_as_float(re[e]), __uint_as_float(re[e + 1]));
-              y = make_float2(__uint_as_float(im[e]), __uint_as_float(im[e + 1]));
-              v = __ffma2_rn(y, y, __fmul2_rn(x, x));
-              m0 = fmax3(m0, v.x, v.y);
-              x = make_float2(__uint_as_float(re[e + 2]), __uint_as_float(re[e + 3]));
-              y = make_float2(__uint_as_float(im[e + 2]), __uint_as_float(im[e + 3]));
-              v = __ffma2_rn(y, y, __fmul2_rn(x, x));
-              m1 = fmax3(m1, v.x, v.y);
-              x = make_float2(__uint_as_float(re[e + 4]), __uint_as_float(re[e + 5]));
-              y = make_float2(__uint_as_float(im[e + 4]), __uint_as_float(im[e + 5]));
-              v = __ffma2_rn(y, y, __fmul2_rn(x, x));
-              m2 = fmax3(m2, v.x, v.y);
-              x = make_float2(__uint_as_float(re[e + 6]), __uint_as_float(re[e + 7]));
-              y = make_float2(__uint_as_float(im[e + 6]), __uint_as_float(im[e + 7]));
-              v = __ffma2_rn(y, y, __fmul2_rn(x, x));
-              m3 = fmax3(m3, v.x, v.y);
-            }
-          } else {
-            // straddling chunk: column n0 + e against row 32qw + lane
-#pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const float x = __uint_as_float(re[e]), y = __uint_as_float(im[e]);
-              const float v = fmaf(x, x, y * y);
-              m0 = (e > lane) ? fmaxf(m0, v) : m0;
+              for (int e = 0; e < 16; ++e) {
+                const float x = __uint_as_float(ra[e]), y = __uint_as_float(ia[e]);
+                const float v = fmaf(x, x, y * y);
+                m[e & 7] = (e > lim) ? fmaxf(m[e & 7], v) : m[e & 7];
+              }
             }
           }
         }
@@ -492,31 +574,37 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
         if (lane == 0) mbar_arrive(&ctl.acc_empty[buf]);
       }
       if (!ok) break;
-      float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+      float mx = fmaxf(fmax3(m[0], m[1], m[2]), fmax3(m[3], m[4], m[5]));
+      mx = fmax3(mx, m[6], m[7]);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0) atomicMax(it.out, __float_as_uint(m));
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) atomicMax(it.out, __float_as_uint(mx));
     }
-  } else {
+  } else if (warp == kMmaWarp) {
     // ------------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t gt = 0;
-      uint32_t usepar = 0u;   // parity of the next fill of block b to consume (bit b)
+      uint32_t slot0 = 0, par0 = 0;    // ring slot and fill parity of the item's block 0
+      const uint32_t hi = kDescHi;
+      const uint32_t xs_lo = desc_lo(xs_addr);
       bool ok = true;
       // Row-major sweep: block I is last read in row I (as A for J >= I, as B
-      // in rows I' <= I), so it is released right after its row and the next
-      // candidate's block I is generated while rows I+1.. still run.  Row 0
+      // in rows I' <= I), so its slot is released right after its row.  Row 0
       // reads every block; it waits for each one as it first needs it.
       for (int idx = blockIdx.x; idx < nitems && ok; idx += gridDim.x) {
         ScreenItem it;
         if (!src.item(idx, t0, delta0, it)) continue;
         const int nb = it.nb;
         for (int I = 0; I < nb && ok; ++I) {
+          uint32_t sI = slot0 + (uint32_t)I;
+          if (sI >= (uint32_t)kRing) sI -= (uint32_t)kRing;
+          const uint32_t alo = xs_lo + sI * (uint32_t)(kBlockBytes >> 4);
           for (int J = I; J < nb; ++J, ++gt) {
+            uint32_t sJ = slot0 + (uint32_t)J, parJ = par0;
+            if (sJ >= (uint32_t)kRing) { sJ -= (uint32_t)kRing; parJ ^= 1u; }
             if (I == 0) {
-              ok = mbar_wait(&ctl.blk_full[J], (usepar >> J) & 1u, &ctl, err, kMmaBackoffNs);
+              ok = mbar_wait(&ctl.blk_full[sJ], parJ, &ctl, err, kMmaBackoffNs);
               if (!ok) break;
-              usepar ^= 1u << J;
             }
             const uint32_t buf = gt & 1u, use = gt >> 1;
             if (use > 0) {
@@ -524,23 +612,24 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
               if (!ok) break;
             }
             tc_fence_after();
-            const uint32_t aI = xs_addr + (uint32_t)(I * kBlockBytes);
-            const uint32_t bJ = xs_addr + (uint32_t)(J * kBlockBytes);
+            const uint32_t blo = xs_lo + sJ * (uint32_t)(kBlockBytes >> 4);
             const uint32_t dre = tmem + buf * 256u, dim = dre + 128u;
-            // Re: sum over the whole K = 2*DP (4 steps of 16)
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              mma_bf16(dre, smem_desc_sw128(aI + 32u * kk), smem_desc_sw128(bJ + 32u * kk),
-                       Idesc<kHalf>::pos, kk > 0 ? 1u : 0u);
+            // Re: sum over the whole K = 2*DP (4 steps of 16 = +2 in the low word)
+            mma_lo(dre, alo + 0u, blo + 0u, Idesc<kHalf>::pos, 0u, hi);
+            mma_lo(dre, alo + 2u, blo + 2u, Idesc<kHalf>::pos, 1u, hi);
+            mma_lo(dre, alo + 4u, blo + 4u, Idesc<kHalf>::pos, 1u, hi);
+            mma_lo(dre, alo + 6u, blo + 6u, Idesc<kHalf>::pos, 1u, hi);
             // Im: A_I^T B_J (K slices 0,1 against 2,3) - B_I^T A_J (2,3 against 0,1)
-            mma_bf16(dim, smem_desc_sw128(aI + 0u), smem_desc_sw128(bJ + 64u), Idesc<kHalf>::pos, 0u);
-            mma_bf16(dim, smem_desc_sw128(aI + 32u), smem_desc_sw128(bJ + 96u), Idesc<kHalf>::pos, 1u);
-            mma_bf16(dim, smem_desc_sw128(aI + 64u), smem_desc_sw128(bJ + 0u), Idesc<kHalf>::neg_a, 1u);
-            mma_bf16(dim, smem_desc_sw128(aI + 96u), smem_desc_sw128(bJ + 32u), Idesc<kHalf>::neg_a, 1u);
+            mma_lo(dim, alo + 0u, blo + 4u, Idesc<kHalf>::pos, 0u, hi);
+            mma_lo(dim, alo + 2u, blo + 6u, Idesc<kHalf>::pos, 1u, hi);
+            mma_lo(dim, alo + 4u, blo + 0u, Idesc<kHalf>::neg_a, 1u, hi);
+            mma_lo(dim, alo + 6u, blo + 2u, Idesc<kHalf>::neg_a, 1u, hi);
             mma_commit(&ctl.acc_full[buf]);
           }
-          if (ok) mma_commit(&ctl.blk_empty[I]);   // row I done: block I is free
+          if (ok) mma_commit(&ctl.blk_empty[sI]);   // row I done: block I's slot is free
         }
+        slot0 += (uint32_t)nb;
+        if (slot0 >= (uint32_t)kRing) { slot0 -= (uint32_t)kRing; par0 ^= 1u; }
       }
       // all issued MMAs complete before tensor memory is released
       mma_commit(&ctl.drain);
