@@ -250,6 +250,10 @@ def main():
     ap.add_argument("--requests", type=int, default=100, help="serving: requests in the stream")
     ap.add_argument("--budget", type=int, default=200, help="serving: iterations per request")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--shard", action="store_true",
+                    help="N>1: one search with its candidates split over the ranks (strong "
+                         "scaling, MAX all-reduce of the score vector per iteration) instead of "
+                         "one independent search per rank")
     args = ap.parse_args()
     wl = args.workload
     if args.impl == "reference":
@@ -291,13 +295,38 @@ def main():
     # the flush also covers the host's enqueue latency of the step
     stream = torch.cuda.Stream()
 
+    sharded = bool(args.shard and dist)
+    ctx = {}
+
     def timed_run(precision, steps, warmup, seed):
         # screen modes: the workload screens every iteration (screen_min_delta = 0)
         s = T.Search(N, d, seed, K=K, precision=precision, device=local, trace_cap=64,
                      stream=stream.cuda_stream, screen_min_delta=0.0)
+        times = []
+        if sharded:
+            # every rank holds the same search and scores its share of the K
+            # candidates; the step is timed on the shared stream around the
+            # whole sharded iteration (score, all-reduce, finish)
+            from paper_2207_06374_gb300.shard import ShardedSearch
+            with torch.cuda.stream(stream):
+                sh = ShardedSearch(s, K, torch, dist, device="cuda")
+                ctx["sharded"] = sh
+                for _ in range(warmup):
+                    sh.step(1)
+                barrier()
+                t_wall = time.perf_counter()
+                for _ in range(steps):
+                    flush.fill_(1)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    sh.step(1)
+                    e1.record(stream)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1) * 1e-3)
+                barrier()
+            return s, times, time.perf_counter() - t_wall
         for _ in range(warmup):
             s.step(1)
-        times = []
         barrier()
         t_wall = time.perf_counter()
         for _ in range(steps):
@@ -309,7 +338,7 @@ def main():
         wall = time.perf_counter() - t_wall
         return s, times, wall
 
-    seed = SEED + rank
+    seed = SEED if sharded else SEED + rank
     with Clocks(local) as clk:
         s, times, wall = timed_run(prec, args.steps, args.warmup, seed)
         # live per-kernel timing of the dominant (scoring) kernel on the same stream
@@ -321,7 +350,10 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_dev = float(tt.item())
     pps = pairs_per_step(d, N, K)
-    value = ws * args.steps * pps / t_dev
+    # independent searches: every rank scores K candidates per step; sharded:
+    # the ranks together score the K candidates of one search
+    units = 1 if sharded else ws
+    value = units * args.steps * pps / t_dev
 
     # end to end through the public API: host frame in (pinned), one iteration,
     # frame and mu out, per step
@@ -336,15 +368,21 @@ def main():
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         T._check(L.trstmi_set_phi(s._h, ctypes.cast(phi_host.data_ptr(), dp)), "set_phi")
-        s.step(1)
+        if sharded:
+            with torch.cuda.stream(stream):
+                ctx["sharded"].step(1)
+        else:
+            s.step(1)
         T._check(L.trstmi_get_phi(s._h, ctypes.cast(out_host.data_ptr(), dp)), "get_phi")
         mu = ctypes.c_double()
         T._check(L.trstmi_coherence(s._h, ctypes.byref(mu), None), "coherence")
     barrier()
     t_e2e = time.perf_counter() - t0
-    e2e = {"value": ws * e2e_steps * pps / t_e2e, "unit": "pairs/s",
+    e2e = {"value": units * e2e_steps * pps / t_e2e, "unit": "pairs/s",
            "h2d_bytes_per_step": 16 * d * N, "d2h_bytes_per_step": 16 * d * N + 8,
-           "call": "trstmi_set_phi + trstmi_step(1) + trstmi_get_phi + trstmi_coherence"}
+           "call": ("trstmi_set_phi + trstmi_shard_score / all-reduce / trstmi_shard_finish + "
+                    "trstmi_get_phi + trstmi_coherence") if sharded else
+                   "trstmi_set_phi + trstmi_step(1) + trstmi_get_phi + trstmi_coherence"}
 
     peaks, peak_kind = measured_peaks()
     flops_launch = pps * flops_per_pair(d)
@@ -365,7 +403,7 @@ def main():
                  "kernel_ms": kernel_ms, "flops_per_launch": flops_launch, "peak_source": peak_note})
 
     side = None
-    if prec == "bf16" and not args.no_side:
+    if prec == "bf16" and not args.no_side and not sharded:
         s2, times2, _ = timed_run("fp32", max(2, args.steps // 4), 1, seed)
         side = {"precision": "fp32 plain", "value": ws * len(times2) * pps / sum(times2),
                 "unit": "pairs/s", "ms_per_step": 1e3 * sum(times2) / len(times2)}
@@ -374,14 +412,17 @@ def main():
     line = {"metric": "off-diagonal Gram pairs scored per second (K*N(N-1)/2 per iteration)",
             "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if sharded else "weak",
+            "vs_baseline": None,
             "dtype": {"bf16": "bf16", "fp32": "f32", "fp64": "f64"}[prec],
             "data": "synthetic (seeded Philox complex-Gaussian frames)",
             "config": {"workload": wl, "description": desc, "d": d, "N": N, "K": K,
                        "precision": prec, "seed": SEED, "screen_min_delta": 0.0,
                        "l2": "flushed between steps "
                        f"({L2_FLUSH_BYTES >> 20} MiB write outside the timed events)",
-                       "parallelism": f"independent instance per GPU x{ws}"},
+                       "parallelism": (f"one search, candidates split over {ws} GPUs "
+                                       "(MAX all-reduce of the K-entry score vector)")
+                                      if sharded else f"independent instance per GPU x{ws}"},
             "roofline": roof, "gpu_launches": kernels_per_step(prec) * args.steps,
             "e2e": e2e, "clocks": clocks, "mu_after": s.coherence()[0]}
     if side:

@@ -134,6 +134,44 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options *opt,
  */
 int trstmi_step(trstmi_handle h, int iters, trstmi_step_info *info);
 
+/* ------------------------------------------------ candidate sharding
+ * One search spread over G processes (one GPU each): the K candidates of an
+ * iteration are independent and each is a pure function of (seed, t, c, Phi)
+ * (Sec. "Optimization procedure", Monte-Carlo sampling of the trust region),
+ * so rank r scores its own range c_lo .. c_hi-1 and the ranks exchange only
+ * the K-entry score vector.  An iteration on every rank is:
+ *
+ *   trstmi_shard_score(h, c_lo, c_hi, scores);    scores: device, K entries
+ *   element-wise MAX all-reduce of scores over the ranks (caller: NCCL,
+ *     torch.distributed, ...; entries are non-negative, so signed integer
+ *     MAX of the bit patterns is exact)
+ *   trstmi_shard_finish(h, scores, info);
+ *
+ * Every rank holds the same state (same N, d, seed and options, same calls),
+ * takes the same decisions from the reduced vector and keeps an identical
+ * frame; the result is bit-identical to trstmi_step on one GPU.  In the
+ * screen modes the top-k re-score and the binary64 certification run on
+ * every rank (they are a small part of the iteration).
+ */
+
+/* Bytes of the score vector: K x 4 (uint32 bit patterns of the binary32
+ * scores: TRSTMI_FP32 and the screen modes) or K x 8 (binary64 bit patterns:
+ * TRSTMI_FP64). */
+int trstmi_shard_score_bytes(trstmi_handle h, size_t *bytes);
+
+/* Starts the next iteration and writes the ranking score of candidates
+ * c_lo .. c_hi-1 (0 <= c_lo <= c_hi <= K) into the caller's device array
+ * scores (trstmi_shard_score_bytes bytes), zero everywhere else.  The copy is
+ * ordered on the instance's stream; with a library-owned stream the call
+ * returns after it completed.  TRSTMI_EINVAL on a bad range or NULL. */
+int trstmi_shard_score(trstmi_handle h, int c_lo, int c_hi, void *scores);
+
+/* Completes the iteration started by trstmi_shard_score from the reduced
+ * score vector (device, read on the instance's stream: when the exchange ran
+ * on another stream the caller orders or synchronises it first); info as in
+ * trstmi_step for one iteration.  Synchronises the stream. */
+int trstmi_shard_finish(trstmi_handle h, const void *scores, trstmi_step_info *info);
+
 /*
  * Certified coherence of the current frame: the frame is renormalised in
  * binary64 and mu computed in binary64 over all pairs j < k (a binary32

@@ -182,51 +182,81 @@ int enqueue_rescore_current(trstmi_instance* h) {
   return cuda_status(cudaGetLastError());
 }
 
-// One iteration of the search, enqueued on s (captured into the graph).
-int enqueue_iteration(trstmi_instance* h, cudaStream_t s) {
+// First part of an iteration, enqueued on s: its start (score buffers zeroed,
+// whether it runs and how it ranks decided on the device) and the ranking
+// scores of candidates c_lo .. c_hi-1 into the K-entry score vector
+// (mu2_k64 in binary64, mu2_k32 otherwise).  A whole iteration scores
+// 0 .. K-1; a candidate-sharded one scores its rank's range.
+int enqueue_iteration_score(trstmi_instance* h, cudaStream_t s, int c_lo, int c_hi) {
   const int N = h->N, d = h->d, K = h->opt.K;
+  const int count = c_hi - c_lo;
   DevState* st = h->st;
   const int prec = h->opt.precision;
   if (prec == TRSTMI_FP64) {
     TRY_CUDA(launch_iter_begin(st, h->mu2_k64, sizeof(unsigned long long) * K, nullptr, 0,
                                nullptr, 0, s));
-    GramSource src{};
-    src.perturb = true;
-    src.phi = h->phi64;
-    src.seed = h->seed;
-    src.st = st;
-    TRY_CUDA(launch_gram_f64(N, d, K, src, h->mu2_k64, h->num_sms, s));
-    TRY_CUDA(launch_select_decide_f64(st, h->mu2_k64, K, h->trace, s));
-    TRY_CUDA(launch_commit_f64(N, d, h->seed, st, h->phi64, h->phi32, s));
+    if (count > 0) {
+      GramSource src{};
+      src.perturb = true;
+      src.phi = h->phi64;
+      src.seed = h->seed;
+      src.c0 = (uint32_t)c_lo;
+      src.st = st;
+      TRY_CUDA(launch_gram_f64(N, d, count, src, h->mu2_k64 + c_lo, h->num_sms, s));
+    }
   } else if (prec == TRSTMI_FP32) {
     TRY_CUDA(launch_iter_begin(st, h->mu2_k32, sizeof(unsigned int) * K, nullptr, 0, nullptr,
                                0, s));
-    GramSource src{};
-    src.perturb = true;
-    src.phi = h->phi32;
-    src.seed = h->seed;
-    src.st = st;
-    TRY_CUDA(launch_gram_f32(N, d, K, src, h->mu2_k32, nullptr, h->num_sms, s));
-    TRY_CUDA(launch_select_decide_f32(st, h->mu2_k32, K, h->trace, s));
-    TRY_CUDA(launch_commit_f32(N, d, h->seed, st, h->phi32, h->phi64, s));
+    if (count > 0) {
+      GramSource src{};
+      src.perturb = true;
+      src.phi = h->phi32;
+      src.seed = h->seed;
+      src.c0 = (uint32_t)c_lo;
+      src.st = st;
+      TRY_CUDA(launch_gram_f32(N, d, count, src, h->mu2_k32 + c_lo, nullptr, h->num_sms, s));
+    }
   } else {
     const int k = h->opt.topk;
     TRY_CUDA(launch_iter_begin(st, h->mu2_k32, sizeof(unsigned int) * K, h->mu2_top,
                                sizeof(unsigned int) * k, h->cert32,
                                2 * sizeof(unsigned int) + sizeof(unsigned long long), s));
-    // rank the K candidates: tensor-core screen while delta >= screen_min_delta,
-    // else the fp32 Gram of every candidate (each kernel returns at once when
-    // the other one is selected for this iteration)
-    if (screen_supported(N, d))
-      TRY_CUDA(launch_screen(prec == TRSTMI_FP16_SCREEN, N, d, h->seed, h->phi32, K, 0u, 0u, 0.0,
-                             st, h->mu2_k32, &st->error, h->num_sms, s));
-    GramSource full{};
-    full.perturb = true;
-    full.phi = h->phi32;
-    full.seed = h->seed;
-    full.st = st;
-    full.gate = &st->use_full;
-    TRY_CUDA(launch_gram_f32(N, d, K, full, h->mu2_k32, nullptr, h->num_sms, s));
+    if (count > 0) {
+      // rank the candidates: tensor-core screen while delta >= screen_min_delta,
+      // else the fp32 Gram of every candidate (each kernel returns at once when
+      // the other one is selected for this iteration)
+      if (screen_supported(N, d))
+        TRY_CUDA(launch_screen(prec == TRSTMI_FP16_SCREEN, N, d, h->seed, h->phi32, count,
+                               (uint32_t)c_lo, 0u, 0.0, st, h->mu2_k32 + c_lo, &st->error,
+                               h->num_sms, s));
+      GramSource full{};
+      full.perturb = true;
+      full.phi = h->phi32;
+      full.seed = h->seed;
+      full.c0 = (uint32_t)c_lo;
+      full.st = st;
+      full.gate = &st->use_full;
+      TRY_CUDA(launch_gram_f32(N, d, count, full, h->mu2_k32 + c_lo, nullptr, h->num_sms, s));
+    }
+  }
+  return TRSTMI_OK;
+}
+
+// Second part: selection from the full score vector, and in the screen modes
+// the fp32 re-score of the top-k and the binary64 certification of the best
+// survivor; then the accept/radius rule, the trace row and the commit.
+int enqueue_iteration_finish(trstmi_instance* h, cudaStream_t s) {
+  const int N = h->N, d = h->d, K = h->opt.K;
+  DevState* st = h->st;
+  const int prec = h->opt.precision;
+  if (prec == TRSTMI_FP64) {
+    TRY_CUDA(launch_select_decide_f64(st, h->mu2_k64, K, h->trace, s));
+    TRY_CUDA(launch_commit_f64(N, d, h->seed, st, h->phi64, h->phi32, s));
+  } else if (prec == TRSTMI_FP32) {
+    TRY_CUDA(launch_select_decide_f32(st, h->mu2_k32, K, h->trace, s));
+    TRY_CUDA(launch_commit_f32(N, d, h->seed, st, h->phi32, h->phi64, s));
+  } else {
+    const int k = h->opt.topk;
     TRY_CUDA(launch_topk(st, h->mu2_k32, K, k, h->topk, s));
     GramSource src{};
     src.perturb = true;
@@ -245,6 +275,12 @@ int enqueue_iteration(trstmi_instance* h, cudaStream_t s) {
     TRY_CUDA(launch_commit_copy(N, d, st, h->cand64, h->cand32, h->phi64, h->phi32, s));
   }
   return TRSTMI_OK;
+}
+
+// One iteration of the search, enqueued on s (captured into the graph).
+int enqueue_iteration(trstmi_instance* h, cudaStream_t s) {
+  const int rc = enqueue_iteration_score(h, s, 0, h->opt.K);
+  return rc ? rc : enqueue_iteration_finish(h, s);
 }
 
 int get_graph(trstmi_instance* h, int iters, cudaGraphExec_t* out) {
@@ -465,6 +501,62 @@ int trstmi_step(trstmi_handle h, int iters, trstmi_step_info* info) {
   TRY_CUDA(cudaGetLastError());
   for (int r = 0; r < full; ++r) TRY_CUDA(cudaGraphLaunch(g_full, s));
   if (g_rem) TRY_CUDA(cudaGraphLaunch(g_rem, s));
+  TRY_CUDA(cudaEventRecord(h->ev1, s));
+  DevState after;
+  rc = read_state(h, &after);
+  if (rc) return rc;
+  if (info) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    info->iters_done = (int32_t)(after.t - after.t_call);
+    info->accepts = (int32_t)(after.accepts - after.accepts_call);
+    info->mu = std::sqrt(after.mu2_cur);
+    info->delta = after.delta;
+    info->pairs_scored = (uint64_t)info->iters_done * (uint64_t)h->opt.K *
+                         ((uint64_t)h->N * (uint64_t)(h->N - 1) / 2);
+    info->elapsed_ns = (uint64_t)((double)ms * 1e6);
+    info->done = (int32_t)after.done;
+    info->reserved = 0;
+  }
+  return device_error_status(after);
+}
+
+int trstmi_shard_score_bytes(trstmi_handle h, size_t* bytes) {
+  if (!h || !bytes) return TRSTMI_EINVAL;
+  *bytes = (size_t)h->opt.K *
+           (h->opt.precision == TRSTMI_FP64 ? sizeof(unsigned long long) : sizeof(unsigned int));
+  return TRSTMI_OK;
+}
+
+int trstmi_shard_score(trstmi_handle h, int c_lo, int c_hi, void* scores) {
+  if (!h || !scores || c_lo < 0 || c_hi < c_lo || c_hi > h->opt.K) return TRSTMI_EINVAL;
+  TRY_CUDA(cudaSetDevice(h->opt.device));
+  cudaStream_t s = h->stream;
+  k_set_stop<<<1, 1, 0, s>>>(h->st, 1u);
+  TRY_CUDA(cudaGetLastError());
+  int rc = enqueue_iteration_score(h, s, c_lo, c_hi);
+  if (rc) return rc;
+  const bool f64 = h->opt.precision == TRSTMI_FP64;
+  size_t bytes = 0;
+  trstmi_shard_score_bytes(h, &bytes);
+  TRY_CUDA(cudaMemcpyAsync(scores, f64 ? (const void*)h->mu2_k64 : (const void*)h->mu2_k32, bytes,
+                           cudaMemcpyDeviceToDevice, s));
+  if (h->own_stream) TRY_CUDA(cudaStreamSynchronize(s));
+  return TRSTMI_OK;
+}
+
+int trstmi_shard_finish(trstmi_handle h, const void* scores, trstmi_step_info* info) {
+  if (!h || !scores) return TRSTMI_EINVAL;
+  TRY_CUDA(cudaSetDevice(h->opt.device));
+  cudaStream_t s = h->stream;
+  const bool f64 = h->opt.precision == TRSTMI_FP64;
+  size_t bytes = 0;
+  trstmi_shard_score_bytes(h, &bytes);
+  TRY_CUDA(cudaEventRecord(h->ev0, s));
+  TRY_CUDA(cudaMemcpyAsync(f64 ? (void*)h->mu2_k64 : (void*)h->mu2_k32, scores, bytes,
+                           cudaMemcpyDeviceToDevice, s));
+  int rc = enqueue_iteration_finish(h, s);
+  if (rc) return rc;
   TRY_CUDA(cudaEventRecord(h->ev1, s));
   DevState after;
   rc = read_state(h, &after);

@@ -100,6 +100,11 @@ SIGNATURES = {
     "trstmi_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                      ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_void_p)]),
     "trstmi_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(StepInfo)]),
+    "trstmi_shard_score_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "trstmi_shard_score": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_void_p]),
+    "trstmi_shard_finish": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.POINTER(StepInfo)]),
     "trstmi_coherence": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
     "trstmi_get_phi": (ctypes.c_int, [ctypes.c_void_p, _dp]),
     "trstmi_set_phi": (ctypes.c_int, [ctypes.c_void_p, _dp]),
@@ -235,6 +240,23 @@ class Search:
     def step(self, iters: int) -> StepInfo:
         info = StepInfo()
         _check(lib().trstmi_step(self._h, iters, ctypes.byref(info)), "trstmi_step")
+        return info
+
+    # candidate sharding (include/trstmi.h): scores is a device buffer of
+    # shard_score_bytes() bytes given by its address (e.g. tensor.data_ptr())
+    def shard_score_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().trstmi_shard_score_bytes(self._h, ctypes.byref(n)), "trstmi_shard_score_bytes")
+        return n.value
+
+    def shard_score(self, c_lo: int, c_hi: int, scores_ptr: int) -> None:
+        _check(lib().trstmi_shard_score(self._h, c_lo, c_hi, ctypes.c_void_p(scores_ptr)),
+               "trstmi_shard_score")
+
+    def shard_finish(self, scores_ptr: int) -> StepInfo:
+        info = StepInfo()
+        _check(lib().trstmi_shard_finish(self._h, ctypes.c_void_p(scores_ptr), ctypes.byref(info)),
+               "trstmi_shard_finish")
         return info
 
     def coherence(self):
