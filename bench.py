@@ -553,9 +553,10 @@ def run_serving(args, ws, rank, local, dist, torch, T):
     K, prec, topk = 8, WORKLOADS["serving"][3], 2
     reqs = W.serving_requests(args.requests, seed=11 + rank, rate_hz=args.rate)
     budget = args.budget
-    with Clocks(local) as clk:
+
+    def serve(precision):
         srv = T.Server(hbm_budget=8 << 30, max_slots=256, iters_per_round=10, K=K,
-                       precision=prec, topk=topk, device=local, trace_cap=0)
+                       precision=precision, topk=topk, device=local, trace_cap=0)
         tickets = [None] * len(reqs)
         t0 = time.perf_counter()
 
@@ -573,7 +574,15 @@ def run_serving(args, ws, rank, local, dist, torch, T):
         wall = time.perf_counter() - t0
         stats = srv.stats()
         srv.close()
+        return results, wall, stats
+
+    with Clocks(local) as clk:
+        results, wall, stats = serve(prec)
     clocks = clk.summary()
+    # the same stream through the serving loop with plain fp32 ranking and
+    # acceptance: the continuous-batching effect without the precision form
+    res32, wall32, stats32 = serve("fp32")
+    lat32 = np.array([(res.t_done_ns - res.t_submit_ns) * 1e-9 for _, res, _ in res32])
     lat = np.array([(res.t_done_ns - res.t_submit_ns) * 1e-9 for _, res, _ in results])
     ok = sum(1 for st, _, _ in results if st == T.TRSTMI_OK)
     pairs = sum(res.pairs_scored for _, res, _ in results)
@@ -615,6 +624,10 @@ def run_serving(args, ws, rank, local, dist, torch, T):
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "max": float(lat.max())},
             "requests_in_screen_range": n_screened,
+            "served_fp32": {"p50": float(np.percentile(lat32, 50)),
+                            "p99": float(np.percentile(lat32, 99)),
+                            "wall_s": wall32, "gpu_busy_s": stats32.gpu_busy_s,
+                            "pairs_per_s": sum(r.pairs_scored for _, r, _ in res32) / wall32},
             "sequential_single_instance_fp32": {
                 "p50": float(np.percentile(seq_lat, 50)), "p99": float(np.percentile(seq_lat, 99)),
                 "sum_run_s": float(sum(run_s))},

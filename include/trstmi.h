@@ -102,7 +102,14 @@ typedef struct trstmi_trace_row {
   double delta_used;    /* radius the candidates were drawn with */
   double delta_next;    /* radius after the update */
   int32_t accepted;     /* 1 if the candidate replaced the frame */
-  int32_t flags;        /* bit 0: candidates ranked by the tensor-core screen */
+  int32_t flags;        /* bit 0: candidates ranked by the tensor-core screen;
+                           bit 1 (screen modes): the best survivor was rejected on
+                           its binary32 mu^2, which exceeded the current mu^2 by
+                           more than twice the fp32/fp64 error bound
+                           2 (2d + 18) 2^-24, so the exact rule rejects it too; no
+                           binary64 certification ran and mu2_best holds that
+                           binary32 value; bit 2: the certification's pair list
+                           overflowed and the binary64 pass covered every pair */
 } trstmi_trace_row;
 
 typedef struct trstmi_step_info {
@@ -287,6 +294,12 @@ typedef struct trstmi_server_opts {
   int32_t iters_per_round; /* iterations per shared round (default 20) */
   int32_t queue_cap;       /* queued requests at most; beyond: TRSTMI_EBUSY (default 65536) */
   int32_t reserved;
+  /* resident work cap: the queue head is admitted only while the resident
+     searches' pairs per iteration, sum of K N(N-1)/2, stay within it (an empty
+     server always admits the head); it keeps enough work resident to fill the
+     GPU without spreading it over every queued request, so requests finish
+     close to arrival order (default 2^28; 0 = no cap) */
+  uint64_t max_resident_pairs;
 } trstmi_server_opts;
 
 typedef struct trstmi_request {

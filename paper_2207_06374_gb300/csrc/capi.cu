@@ -257,18 +257,22 @@ int enqueue_iteration_finish(trstmi_instance* h, cudaStream_t s) {
     TRY_CUDA(launch_commit_f32(N, d, h->seed, st, h->phi32, h->phi64, s));
   } else {
     const int k = h->opt.topk;
-    TRY_CUDA(launch_topk(st, h->mu2_k32, K, k, h->topk, s));
+    TRY_CUDA(launch_topk(st, h->mu2_k32, K, k, h->topk, h->mu2_top, s));
+    // re-score the survivors in binary32 when the screen ranked them (ranked by
+    // the binary32 Gram of every candidate, k_topk copied their scores)
     GramSource src{};
     src.perturb = true;
     src.phi = h->phi32;
     src.seed = h->seed;
     src.cand_list = h->topk;
     src.st = st;
+    src.gate = &st->use_screen;
     TRY_CUDA(launch_gram_f32(N, d, k, src, h->mu2_top, nullptr, h->num_sms, s));
     TRY_CUDA(launch_materialize64(N, d, h->seed, st, h->topk, h->mu2_top, k, h->phi64,
                                   h->cand64, h->cand32, s));
-    // cert32[0..1] and cert64 were zeroed by iter_begin (contiguous block)
-    int rc = enqueue_certify(h, h->cand64, h->cand32, h->cert64, &st->active, &st->npairs,
+    // cert32[0..1] and cert64 were zeroed by iter_begin (contiguous block);
+    // the passes run only for a survivor the rule could accept (st->certify)
+    int rc = enqueue_certify(h, h->cand64, h->cand32, h->cert64, &st->certify, &st->npairs,
                              &st->overflow, s);
     if (rc) return rc;
     TRY_CUDA(launch_decide_certified(st, h->cert64, h->trace, s));

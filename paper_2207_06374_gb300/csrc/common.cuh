@@ -38,13 +38,26 @@ struct DevState {
   uint32_t trace_cap;
   uint32_t t_call;        // t when the current trstmi_step call started
   uint32_t accepts_call;  // accepts when the current trstmi_step call started
-  uint32_t pad0;
+  uint32_t certify;   // screen modes: the best survivor is certified in binary64 (else it
+                      // is rejected on its binary32 score, see certify_margin_mu2)
 };
+
+// Screen modes: the best survivor's binary32 mu^2 (fp32 generation from the
+// binary32 frame, fp32 Gram) and its binary64 mu^2 differ by less than
+// 2 (2d + 18) 2^-24 for unit columns: the entries differ by at most 8 ulp
+// (frame rounding, fp32 Box-Muller, normalisation), a Gram entry by at most
+// (2d + 2) ulp more (its 2d-term dot products), and |G| <= 1.  A survivor whose
+// binary32 mu^2 exceeds the current mu^2 by twice that bound is rejected by the
+// exact rule as well, so it is rejected without the binary64 certification.
+__host__ __device__ inline double certify_margin_mu2(int d) {
+  return 4.0 * (2.0 * d + 18.0) * 5.9604644775390625e-8;
+}
 
 struct TraceRowDev {
   uint32_t t, cstar;
   double mu2_best, mu2_screen, mu2_cur, delta_used, delta_next;
-  int32_t accepted, flags;  // flags bit 0: ranked by the tensor-core screen
+  int32_t accepted, flags;  // flags bit 0: ranked by the tensor-core screen;
+                            // bit 1: rejected on the binary32 bound (no binary64 certification)
 };
 
 template <typename T> struct Cplx;

@@ -62,7 +62,7 @@ cudaError_t launch_commit_f64(int N, int d, uint64_t seed, DevState* st, double2
                               float2* phi32, cudaStream_t s);
 // screen mode
 cudaError_t launch_topk(DevState* st, const unsigned int* mu2_screen, int K, int k,
-                        uint32_t* topk, cudaStream_t s);
+                        uint32_t* topk, unsigned int* mu2_top, cudaStream_t s);
 cudaError_t launch_materialize64(int N, int d, uint64_t seed, DevState* st,
                                  const uint32_t* topk, const unsigned int* mu2_top, int k,
                                  const double2* phi64, double2* cand64, float2* cand32,

@@ -109,7 +109,12 @@ struct Slot {
   int state_idx = -1;
   SlotDesc desc{};
   uint32_t budget = 0;
+  uint64_t pairs = 0;   // pairs scored per iteration, K N(N-1)/2
 };
+
+uint64_t pairs_per_iteration(int K, int N) {
+  return (uint64_t)K * ((uint64_t)N * (uint64_t)(N - 1) / 2);
+}
 
 double welch_bound(int N, int d) {
   if (N <= d || N < 2) return 0.0;
@@ -185,6 +190,7 @@ struct trstmi_server {
   long long* d_tune_begin = nullptr;
   std::vector<int> free_states;
   std::vector<Slot> slots;
+  uint64_t resident_pairs = 0;
   BatchPlan plan;
 
   std::mutex mu;
@@ -312,6 +318,7 @@ int admit(trstmi_server* sv, uint64_t ticket, Req& r, Slot* out) {
   sd.seed = r.req.seed;
   sd.N = N; sd.d = d; sd.K = o.K;
   sl.budget = (uint32_t)std::max(0, r.req.budget_iters);
+  sl.pairs = pairs_per_iteration(o.K, N);
   DevState s0;
   std::memset(&s0, 0, sizeof(s0));
   s0.delta = o.delta0; s0.delta_used = o.delta0;
@@ -367,6 +374,7 @@ void retire(trstmi_server* sv, size_t k, const DevState& st, int status) {
   r.status = status;
   r.t_done = now_ns();
   sv->arena.release(sl.off, sl.bytes);
+  sv->resident_pairs -= sl.pairs;
   sv->free_states.push_back(sl.state_idx);
   sv->slots.erase(sv->slots.begin() + k);
   sv->active_count = (int)sv->slots.size();
@@ -408,6 +416,11 @@ void worker_main(trstmi_server* sv) {
         std::lock_guard<std::mutex> g(sv->mu);
         r = &sv->reqs[tk];
       }
+      // resident work cap: the head waits for running searches to retire
+      const uint64_t cap = sv->opt.max_resident_pairs;
+      if (cap && !sv->slots.empty() &&
+          sv->resident_pairs + pairs_per_iteration(sv->opt.search.K, r->req.N) > cap)
+        break;
       Slot sl;
       const int rc = admit(sv, tk, *r, &sl);
       if (rc == TRSTMI_ENOMEM) {
@@ -428,6 +441,7 @@ void worker_main(trstmi_server* sv) {
         ++sv->admitted;
       }
       pending.pop_front();
+      sv->resident_pairs += sl.pairs;
       sv->slots.push_back(sl);
       sv->active_count = (int)sv->slots.size();
       changed = true;
@@ -523,6 +537,7 @@ void trstmi_default_server_opts(trstmi_server_opts* o) {
   o->max_slots = 256;
   o->iters_per_round = 20;
   o->queue_cap = 1 << 16;
+  o->max_resident_pairs = 1ull << 28;
 }
 
 void trstmi_server_destroy(trstmi_server* sv) {

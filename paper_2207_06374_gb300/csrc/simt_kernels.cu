@@ -414,6 +414,7 @@ __global__ void k_iter_begin(DevState* st, void* z0, size_t b0, void* z1, size_t
     st->overflow = 0u;
     st->use_screen = 0u;
     st->use_full = 0u;
+    st->certify = 0u;
     if (act) {
       st->delta_used = st->delta;
       st->accepted = 0u;
@@ -443,7 +444,8 @@ cudaError_t launch_iter_begin(DevState* st, void* zero0, size_t bytes0, void* ze
 // ------------------------------------------------ the accept/radius rule
 
 __device__ void apply_rule_and_trace(DevState* st, uint32_t cstar, double mu2_best,
-                                     double mu2_screen, TraceRowDev* trace) {
+                                     double mu2_screen, TraceRowDev* trace,
+                                     uint32_t extra_flags = 0u) {
   const uint32_t t = st->t + 1u;
   const double dused = st->delta_used;
   const bool accept = mu2_best < st->mu2_cur;
@@ -466,7 +468,7 @@ __device__ void apply_rule_and_trace(DevState* st, uint32_t cstar, double mu2_be
     TraceRowDev& r = trace[(t - 1u) % st->trace_cap];
     r.t = t; r.cstar = cstar; r.mu2_best = mu2_best; r.mu2_screen = mu2_screen;
     r.mu2_cur = st->mu2_cur; r.delta_used = dused; r.delta_next = dl;
-    r.accepted = accept ? 1 : 0; r.flags = (int32_t)(st->use_screen & 1u);
+    r.accepted = accept ? 1 : 0; r.flags = (int32_t)((st->use_screen & 1u) | extra_flags);
   }
 }
 
@@ -540,7 +542,12 @@ cudaError_t launch_commit_f64(int N, int d, uint64_t seed, DevState* st, double2
 // ----------------------------------------------------------- screen mode
 
 // The k smallest screen scores, ordered by (mu^2, c); one CTA.
-__global__ void k_topk(DevState* st, const unsigned int* mu2, int K, int k, uint32_t* topk) {
+// Ranked by the binary32 Gram of every candidate (not the screen), the
+// survivors' binary32 scores are known already and are copied into mu2_top
+// (the re-score pass, gated on use_screen, then does not run): the values are
+// bit-identical to a re-score, which runs the same pair arithmetic.
+__global__ void k_topk(DevState* st, const unsigned int* mu2, int K, int k, uint32_t* topk,
+                       unsigned int* mu2_top) {
   if (!st->active) return;
   __shared__ unsigned long long sk[32];
   __shared__ unsigned long long last;
@@ -563,6 +570,7 @@ __global__ void k_topk(DevState* st, const unsigned int* mu2, int K, int k, uint
     if (threadIdx.x == 0) {
       for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = sk[w] < best ? sk[w] : best;
       topk[r] = (uint32_t)(best & 0xffffffffull);
+      if (!st->use_screen) mu2_top[r] = (unsigned int)(best >> 32);
       last = best;
     }
     __syncthreads();
@@ -570,8 +578,8 @@ __global__ void k_topk(DevState* st, const unsigned int* mu2, int K, int k, uint
 }
 
 cudaError_t launch_topk(DevState* st, const unsigned int* mu2_screen, int K, int k,
-                        uint32_t* topk, cudaStream_t s) {
-  k_topk<<<1, 1024, 0, s>>>(st, mu2_screen, K, k, topk);
+                        uint32_t* topk, unsigned int* mu2_top, cudaStream_t s) {
+  k_topk<<<1, 1024, 0, s>>>(st, mu2_screen, K, k, topk, mu2_top);
   return cudaGetLastError();
 }
 
@@ -587,14 +595,18 @@ __global__ void k_materialize64(int N, int d, uint64_t seed, DevState* st,
     const unsigned int v = mu2_top[s];
     if (v < bv || (v == bv && topk[s] < bc)) { bv = v; bc = topk[s]; }
   }
+  // certify only a survivor the exact rule could accept
+  const double m32 = (double)__uint_as_float(bv);
+  const bool cert = !(m32 > st->mu2_cur + certify_margin_mu2(d));
   // one warp per column
   const int lane = threadIdx.x & 31;
   const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->cstar = bc;
-    st->mu2_screen = (double)__uint_as_float(bv);
+    st->mu2_screen = m32;
+    st->certify = cert ? 1u : 0u;
   }
-  if (j >= N) return;
+  if (!cert || j >= N) return;
   const bool ok = gen_column_warp<double>(phi64, d, j, seed, bc, st->t + 1u, 0u, st->delta_used,
                                           cand64, lane);
   if (!ok && lane == 0) atomicOr(&st->error, (uint32_t)kErrZeroColumn);
@@ -648,7 +660,11 @@ cudaError_t launch_pairs64(const uint32_t* active, const uint32_t* npairs, const
 __global__ void k_decide_certified(DevState* st, const unsigned long long* mu2_64,
                                    TraceRowDev* trace) {
   if (!st->active) return;
-  apply_rule_and_trace(st, st->cstar, nonneg_from_bits(*mu2_64), st->mu2_screen, trace);
+  // uncertified: the survivor's binary32 score is above the current mu^2 by
+  // more than the error bound, and the rule rejects it on that value
+  const bool cert = st->certify != 0u;
+  apply_rule_and_trace(st, st->cstar, cert ? nonneg_from_bits(*mu2_64) : st->mu2_screen,
+                       st->mu2_screen, trace, (cert ? 0u : 2u) | (st->overflow ? 4u : 0u));
 }
 
 cudaError_t launch_decide_certified(DevState* st, const unsigned long long* mu2_64,
@@ -757,6 +773,7 @@ __global__ void k_batch_begin(SlotDesc* slots, int n, unsigned long long* counte
     st->active = act;
     st->npairs = 0u;
     st->overflow = 0u;
+    st->certify = 0u;
     const bool scr = act && screen_mode && sd.screen && st->delta >= st->screen_min_delta;
     st->use_screen = scr ? 1u : 0u;
     st->use_full = (act && !scr) ? 1u : 0u;
@@ -816,8 +833,9 @@ __global__ void __launch_bounds__(256) k_batch_score(const SlotDesc* slots, cons
     bool run;
     switch (mode) {
       case kPassFull: run = st->active && st->use_full; break;
+      case kPassRescore: run = st->active && st->use_screen; break;
       case kPassFrame64: run = st->active && st->overflow; break;
-      default: run = st->active; break;
+      default: run = st->active && st->certify; break;   // FrameMax, Filter
     }
     if (run) {
       // tiles at this launch's width (the binary64 frame pass may run an
@@ -930,6 +948,7 @@ __global__ void k_batch_topk(SlotDesc* slots, int n) {
     if (threadIdx.x == 0) {
       for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = sk[w] < best ? sk[w] : best;
       sd.topk[r] = (uint32_t)(best & 0xffffffffull);
+      if (!sd.st->use_screen) sd.mu2_top[r] = (unsigned int)(best >> 32);
       last = best;
     }
     __syncthreads();
@@ -954,13 +973,16 @@ __global__ void k_batch_materialize64(SlotDesc* slots, int n) {
     const unsigned int v = sd.mu2_top[q];
     if (v < bv || (v == bv && sd.topk[q] < bc)) { bv = v; bc = sd.topk[q]; }
   }
+  const double m32 = (double)__uint_as_float(bv);
+  const bool cert = !(m32 > st->mu2_cur + certify_margin_mu2(sd.d));
   const int lane = threadIdx.x & 31;
   const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->cstar = bc;
-    st->mu2_screen = (double)__uint_as_float(bv);
+    st->mu2_screen = m32;
+    st->certify = cert ? 1u : 0u;
   }
-  if (j >= sd.N) return;
+  if (!cert || j >= sd.N) return;
   const double2* phi64 = reinterpret_cast<const double2*>(sd.phi_other);
   const bool ok = gen_column_warp<double>(phi64, sd.d, j, sd.seed, bc, st->t + 1u, 0u,
                                           st->delta_used, sd.cand64, lane);
@@ -983,7 +1005,7 @@ cudaError_t launch_batch_materialize64(SlotDesc* slots, int n, int maxN, cudaStr
 __global__ void k_batch_pairs64(SlotDesc* slots, int n) {
   const SlotDesc& sd = slots[blockIdx.x];
   const DevState* st = sd.st;
-  if (!st->active) return;
+  if (!st->active || !st->certify) return;
   const uint32_t np = min(st->npairs, sd.pair_cap);
   const int d = sd.d;
   double m = 0.0;
@@ -1016,7 +1038,9 @@ __global__ void k_batch_decide_certified(SlotDesc* slots, int n) {
   const SlotDesc& sd = slots[s];
   DevState* st = sd.st;
   if (!st->active) return;
-  apply_rule_and_trace(st, st->cstar, nonneg_from_bits(*sd.cert64), st->mu2_screen, sd.trace);
+  const bool cert = st->certify != 0u;
+  apply_rule_and_trace(st, st->cstar, cert ? nonneg_from_bits(*sd.cert64) : st->mu2_screen,
+                       st->mu2_screen, sd.trace, (cert ? 0u : 2u) | (st->overflow ? 4u : 0u));
 }
 
 cudaError_t launch_batch_decide_certified(SlotDesc* slots, int n, cudaStream_t s) {

@@ -64,7 +64,8 @@ class StepInfo(ctypes.Structure):
 class ServerOpts(ctypes.Structure):
     _fields_ = [("search", Options), ("hbm_budget", ctypes.c_size_t),
                 ("max_slots", ctypes.c_int32), ("iters_per_round", ctypes.c_int32),
-                ("queue_cap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("queue_cap", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_resident_pairs", ctypes.c_uint64)]
 
 
 class Request(ctypes.Structure):
@@ -394,11 +395,13 @@ class Server:
     """The serving loop (trstmi_server_create .. _destroy)."""
 
     def __init__(self, hbm_budget=4 << 30, max_slots=256, iters_per_round=20, queue_cap=1 << 16,
-                 **search):
+                 max_resident_pairs=None, **search):
         o = ServerOpts()
         lib().trstmi_default_server_opts(ctypes.byref(o))
         o.hbm_budget, o.max_slots = hbm_budget, max_slots
         o.iters_per_round, o.queue_cap = iters_per_round, queue_cap
+        if max_resident_pairs is not None:
+            o.max_resident_pairs = max_resident_pairs
         for k, v in search.items():
             if k == "precision" and isinstance(v, str):
                 v = PRECISIONS[v]

@@ -146,6 +146,9 @@ def test_batch_bf16_decisions_replay_in_fp64():
             assert np.all(tr["flags"] & 1 == 1)
             rphi, rm2, _, rtr = O.replay(phi0[i], seeds[i], O.make_opts(K=K, T=iters), 0.1,
                                          O.mu2(phi0[i]), 0, tr["cstar"])
-            assert np.allclose(tr["mu2_best"], rtr["mu2_best"], rtol=1e-12, atol=0)
+            cert = (tr["flags"] & 2) == 0
+            assert np.allclose(tr["mu2_best"][cert], rtr["mu2_best"][cert], rtol=1e-12, atol=0)
+            assert np.all(np.abs(tr["mu2_best"][~cert] - rtr["mu2_best"][~cert])
+                          <= 2.0 * (2 * ds[i] + 18) * 2.0 ** -24)
             assert np.array_equal(tr["accepted"], rtr["accepted"])
             assert np.abs(b.get_phi(i) - rphi).max() < 1e-12

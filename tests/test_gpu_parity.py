@@ -22,6 +22,24 @@ def _mu_err(a2, b2):
 
 # ---------------------------------------------------------- coherence of frames
 
+
+def check_precision_form_rows(tr, rtr, d, mu2_0):
+    """Rows of a precision-form trace against the oracle's binary64 replay of
+    the same choices: a certified row (flags bit 1 clear) carries the binary64
+    mu^2 of the chosen candidate to 1e-12; an uncertified row was rejected on
+    its binary32 score, which lies within the fp32/fp64 bound 2 (2d + 18) 2^-24
+    of the binary64 value and above the current mu^2 by twice that bound."""
+    cert = (tr["flags"] & 2) == 0
+    assert np.allclose(tr["mu2_best"][cert], rtr["mu2_best"][cert], rtol=1e-12, atol=0)
+    bound = 2.0 * (2 * d + 18) * 2.0 ** -24
+    unc = ~cert
+    assert np.all(tr["accepted"][unc] == 0)
+    assert np.all(np.abs(tr["mu2_best"][unc] - rtr["mu2_best"][unc]) <= bound)
+    prev = np.concatenate([[mu2_0], rtr["mu2_cur"][:-1]])
+    assert np.all(rtr["mu2_best"][unc] >= prev[unc])
+    return int(unc.sum())
+
+
 @pytest.mark.parametrize("name,make", [
     ("tetrahedral(2,4)", F.tetrahedral_2_4), ("harmonic(3,7)", F.harmonic_3_7),
     ("hesse(3,9)", F.hesse_sic_3_9), ("mubs(3)", lambda: F.mubs(3)),
@@ -243,11 +261,11 @@ def test_bf16_mode_decisions_replay_exactly():
         phi = s.get_phi()
     opts = O.make_opts(K=K, T=iters)
     rphi, rm2, rdl, rtr = O.replay(phi0, seed, opts, 0.1, O.mu2(phi0), 0, tr["cstar"])
-    assert np.allclose(tr["mu2_best"], rtr["mu2_best"], rtol=1e-12, atol=0)
+    check_precision_form_rows(tr, rtr, d, O.mu2(phi0))
     assert np.array_equal(tr["accepted"], rtr["accepted"])
     assert np.abs(phi - rphi).max() < 1e-12
     # the fp32 re-score of the winner is within fp32 tolerance of its fp64 mu
-    assert np.max(np.abs(np.sqrt(tr["mu2_screen"]) - np.sqrt(tr["mu2_best"]))) < 1e-6
+    assert np.max(np.abs(np.sqrt(tr["mu2_screen"]) - np.sqrt(rtr["mu2_best"]))) < 1e-6
 
 
 def test_bf16_mode_full_size_iterations_replay():
@@ -261,7 +279,7 @@ def test_bf16_mode_full_size_iterations_replay():
         mu, _ = s.coherence()
     opts = O.make_opts(K=K, T=3)
     rphi, rm2, rdl, rtr = O.replay(phi0, seed, opts, 0.1, O.mu2(phi0), 0, tr["cstar"])
-    assert np.allclose(tr["mu2_best"], rtr["mu2_best"], rtol=1e-12, atol=0)
+    check_precision_form_rows(tr, rtr, d, O.mu2(phi0))
     assert np.array_equal(tr["accepted"], rtr["accepted"])
     assert abs(mu - np.sqrt(rm2)) < 1e-12
 
@@ -303,4 +321,21 @@ def test_screen_gate_by_radius():
         rphi, rm2, _, rtr = O.replay(phi0, seed, O.make_opts(K=K, T=iters), 0.1, O.mu2(phi0), 0,
                                      tr["cstar"])
         assert np.array_equal(tr["accepted"], rtr["accepted"])
-        assert np.allclose(tr["mu2_best"], rtr["mu2_best"], rtol=1e-12, atol=0)
+        check_precision_form_rows(tr, rtr, d, O.mu2(phi0))
+
+
+def test_precision_form_rejects_on_fp32_bound_late_in_a_run():
+    """Late in a run most survivors are worse than the current frame: those
+    are rejected on their binary32 score (no binary64 work), and every
+    decision still matches the oracle's binary64 replay."""
+    d, N, K, iters, seed = 4, 16, 64, 150, 8
+    with T.Search(N, d, seed, K=K, precision="bf16", topk=4) as s:
+        phi0 = s.get_phi()
+        s.step(iters)
+        tr = s.trace()
+        phi = s.get_phi()
+    rphi, rm2, _, rtr = O.replay(phi0, seed, O.make_opts(K=K, T=iters), 0.1, O.mu2(phi0), 0,
+                                 tr["cstar"])
+    assert np.array_equal(tr["accepted"], rtr["accepted"])
+    assert check_precision_form_rows(tr, rtr, d, O.mu2(phi0)) > 0
+    assert np.abs(phi - rphi).max() < 1e-12

@@ -98,6 +98,30 @@ def test_admission_respects_memory_budget():
         assert st == T.TRSTMI_ENOMEM
 
 
+def test_resident_work_cap_limits_admission():
+    """max_resident_pairs: with room for two (N=512, K=8) searches at a time,
+    at most two are resident; a request larger than the cap is still served
+    once the server is empty."""
+    K, N = 8, 512
+    cap = 2 * K * N * (N - 1) // 2
+    with T.Server(hbm_budget=256 << 20, max_slots=16, iters_per_round=2, K=K, precision="fp32",
+                  max_resident_pairs=cap) as srv:
+        tickets = [srv.submit(N, 16, 300 + i, 8) for i in range(5)]
+        big = srv.submit(1024, 16, 400, 4)
+        peak = 0
+        while True:
+            st = srv.stats()
+            peak = max(peak, st.active_slots)
+            if st.completed == 6:
+                break
+            time.sleep(0.001)
+        assert 1 <= peak <= 2
+        for t in tickets:
+            assert srv.poll(t)[0] == T.TRSTMI_OK
+        st, res, _ = srv.poll(big)
+        assert st == T.TRSTMI_OK and res.iters == 4
+
+
 def test_cancel_and_unknown_ticket():
     with T.Server(hbm_budget=64 << 20, max_slots=1, iters_per_round=5, K=8,
                   precision="fp32") as srv:
