@@ -9,9 +9,11 @@
 // scores one candidate per CTA in either form, so the same holds there).
 //
 // Tile widths: the fp32/fp64 scoring kernel is instantiated for tiles of 16,
-// 32 and 64 columns.  The autotuner times the persistent scoring pass on the
-// actual instances of each (d, ceil log2 N) bucket at every feasible width
-// and keeps the fastest; the choice is cached for the process.
+// 32 and 64 columns, and small instances can instead be scored whole (the
+// candidate drawn once into shared memory, kResident).  The autotuner times
+// the persistent scoring pass on the actual instances of each (d, ceil log2 N)
+// bucket at every feasible choice and keeps the fastest; the choice is cached
+// for the process.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -91,15 +93,17 @@ namespace trstmi {
 int cached_width(bool f64, int d, int N) {
   std::lock_guard<std::mutex> g(g_tune_mu);
   auto it = g_tuned_R[f64].find({d, ceil_log2(N)});
-  return it == g_tuned_R[f64].end() ? 0 : it->second;
+  return it == g_tuned_R[f64].end() ? -1 : it->second;
 }
 void store_width(bool f64, int d, int N, int R) {
   std::lock_guard<std::mutex> g(g_tune_mu);
   g_tuned_R[f64][{d, ceil_log2(N)}] = R;
 }
-int tiles_at_width(int N, int R) { return ntiles_for(N, R); }
+int tiles_at_width(int N, int R) { return R == kResident ? 1 : ntiles_for(N, R); }
 
 bool width_feasible(bool f64, int d, int N, int R) {
+  // whole candidates up to 48 KiB of shared memory (four CTAs per SM or more)
+  if (R == kResident) return resident_smem_bytes(f64, d, N) <= 48 * 1024;
   if (gram_smem_bytes(f64, d, R) > 200 * 1024) return false;
   return R == 1 || 16 * R < 2 * N;     // do not pad tiny N
 }
@@ -116,12 +120,15 @@ int time_width(const std::vector<SlotDesc>& h, SlotDesc* d_slots, const std::vec
   for (size_t q = 0; q < ids.size(); ++q) {
     SlotDesc& sd = tmp[ids[q]];
     sd.R = R;
-    sd.ntiles = ntiles_for(sd.N, R);
+    sd.ntiles = tiles_at_width(sd.N, R);
     begin[q + 1] = begin[q] + (long long)sd.K * sd.ntiles;
-    smem = std::max(smem, gram_smem_bytes(f64, sd.d, R));
+    smem = std::max(smem, R == kResident ? resident_smem_bytes(f64, sd.d, sd.N)
+                                         : gram_smem_bytes(f64, sd.d, R));
   }
   int per_sm = 0;
-  if (batch_score_occupancy(f64, R, smem, &per_sm) != cudaSuccess || per_sm < 1) return TRSTMI_ECUDA;
+  const cudaError_t oe = R == kResident ? batch_resident_occupancy(f64, smem, &per_sm)
+                                        : batch_score_occupancy(f64, R, smem, &per_sm);
+  if (oe != cudaSuccess || per_sm < 1) return TRSTMI_ECUDA;
   const int grid = (int)std::min<long long>(begin.back(), (long long)num_sms * per_sm);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TRSTMI_ECUDA;
@@ -135,8 +142,11 @@ int time_width(const std::vector<SlotDesc>& h, SlotDesc* d_slots, const std::vec
     float t = 0.f;
     if (cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s) ||
         cudaEventRecord(e0, s) ||
-        launch_batch_score(f64, R, d_slots, d_ids, d_begin, (int)ids.size(), begin.back(),
-                           d_counter, smem, grid, s, kPassFull) ||
+        (R == kResident
+             ? launch_batch_resident(f64, d_slots, d_ids, d_begin, (int)ids.size(), begin.back(),
+                                     d_counter, smem, grid, s, kPassFull)
+             : launch_batch_score(f64, R, d_slots, d_ids, d_begin, (int)ids.size(), begin.back(),
+                                  d_counter, smem, grid, s, kPassFull)) ||
         cudaEventRecord(e1, s) || cudaEventSynchronize(e1) || cudaEventElapsedTime(&t, e0, e1)) {
       rc = TRSTMI_ECUDA;
       break;
@@ -194,9 +204,9 @@ int autotune(trstmi_batch* b) {
                           b->stream));
   for (auto& kv : buckets) {
     int R = cached_width(f64s, kv.first.first, b->N[kv.second[0]]);
-    if (R <= 0) {
+    if (R < 0) {
       float best = 1e30f;
-      for (int cand : {1, 2, 4}) {
+      for (int cand : {kResident, 1, 2, 4}) {
         bool ok = true;
         for (int i : kv.second) ok = ok && width_feasible(f64s, b->d[i], b->N[i], cand);
         if (!ok) continue;
@@ -206,12 +216,12 @@ int autotune(trstmi_batch* b) {
         if (rc) return rc;
         if (ms < best) { best = ms; R = cand; }
       }
-      if (R <= 0) R = 1;
+      if (R < 0) R = 1;
       store_width(f64s, kv.first.first, b->N[kv.second[0]], R);
     }
     for (int i : kv.second) {
       b->h_slots[i].R = R;
-      b->h_slots[i].ntiles = ntiles_for(b->N[i], R);
+      b->h_slots[i].ntiles = tiles_at_width(b->N[i], R);
     }
   }
   BTRY(cudaMemcpyAsync(b->d_slots, b->h_slots.data(), sizeof(SlotDesc) * b->n,
@@ -242,11 +252,11 @@ int batch_graph(trstmi_batch* b, int iters, cudaGraphExec_t* out) {
   return TRSTMI_OK;
 }
 
+// The instances' states are one contiguous array at the start of the arena.
 int read_states(trstmi_batch* b, std::vector<DevState>* out) {
   out->resize(b->n);
-  for (int i = 0; i < b->n; ++i)
-    BTRY(cudaMemcpyAsync(&(*out)[i], b->h_slots[i].st, sizeof(DevState), cudaMemcpyDeviceToHost,
-                         b->stream));
+  BTRY(cudaMemcpyAsync(out->data(), b->h_slots[0].st, sizeof(DevState) * b->n,
+                       cudaMemcpyDeviceToHost, b->stream));
   BTRY(cudaStreamSynchronize(b->stream));
   return TRSTMI_OK;
 }
@@ -552,7 +562,7 @@ int trstmi_batch_profile_score(trstmi_batch_handle b, int launches, size_t flush
 
 int trstmi_batch_tile_widths(trstmi_batch_handle b, int* widths) {
   if (!b || !widths) return TRSTMI_EINVAL;
-  for (int i = 0; i < b->n; ++i) widths[i] = 16 * b->h_slots[i].R;
+  for (int i = 0; i < b->n; ++i) widths[i] = 16 * b->h_slots[i].R;   // 0: whole candidate
   return TRSTMI_OK;
 }
 

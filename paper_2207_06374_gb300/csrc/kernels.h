@@ -114,7 +114,8 @@ struct SlotDesc {
   TraceRowDev* trace;
   uint64_t seed;
   int N, d, K;
-  int R;                // tile width 16R of this instance's Gram pass
+  int R;                // tile width 16R of this instance's Gram pass (kResident: whole
+                        // candidate in shared memory)
   int ntiles;           // upper-triangle tiles at that width
   int screen;           // screen modes: 1 if the tensor-core screen handles this shape
   // screen modes only: top-k survivors, their fp32 scores, the binary64
@@ -160,17 +161,29 @@ cudaError_t launch_batch_decide(SlotDesc* slots, int n, bool f64, cudaStream_t s
 cudaError_t launch_batch_commit(SlotDesc* slots, int n, int maxN, bool f64, cudaStream_t s);
 cudaError_t batch_score_occupancy(bool f64, int R, size_t smem, int* blocks_per_sm);
 size_t gram_smem_bytes(bool f64, int d, int R);
-// Autotuned tile-width cache per (d, ceil log2 N): 0 if not measured yet.
+// Whole-candidate scoring of small instances (SlotDesc::R == kResident):
+// one CTA per (instance, candidate), the candidate drawn once into shared
+// memory; modes kPassFull and kPassRescore.
+constexpr int kResident = 0;
+cudaError_t launch_batch_resident(bool f64, const SlotDesc* slots, const int* group,
+                                  const long long* group_begin, int ngroup, long long nitems,
+                                  unsigned long long* counter, size_t smem, int grid,
+                                  cudaStream_t s, int mode);
+cudaError_t batch_resident_occupancy(bool f64, size_t smem, int* blocks_per_sm);
+size_t resident_smem_bytes(bool f64, int d, int N);
+// Autotuned tile-width cache per (d, ceil log2 N): -1 if not measured yet,
+// else R in {kResident, 1, 2, 4}.
 int cached_width(bool f64, int d, int N);
 void store_width(bool f64, int d, int N, int R);
 int tiles_at_width(int N, int R);
+bool width_feasible(bool f64, int d, int N, int R);
 
 // Launch plan of one iteration over many instances (plan.cu): width-group
 // tables of every scoring pass and the screen's work items, in device buffers
 // allocated once for a capacity and refilled by rebuild().
 struct BatchPlan {
   static constexpr int kPasses = 5;
-  static constexpr int kCounters = 16;
+  static constexpr int kCounters = 24;
   struct Group {
     int R = 1;
     bool f64 = false;
@@ -190,7 +203,7 @@ struct BatchPlan {
   int precision = 0;
   int maxN = 0, maxd = 0;
   int ncounters = 0;
-  Table tables[kPasses][3];
+  Table tables[kPasses][4];
   std::vector<Group> groups[kPasses];
   ScreenSlot* d_screen_slots = nullptr;
   uint2* d_items = nullptr;

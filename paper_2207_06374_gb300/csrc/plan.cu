@@ -12,7 +12,9 @@
 namespace trstmi {
 
 namespace {
-constexpr int kWidths[3] = {4, 2, 1};
+// tile widths of the groups; kResident = whole candidate in shared memory
+constexpr int kWidths[4] = {4, 2, 1, kResident};
+constexpr int kNumWidths = 4;
 
 bool is_screen_prec(int p) { return p == TRSTMI_BF16_SCREEN || p == TRSTMI_FP16_SCREEN; }
 
@@ -31,14 +33,14 @@ int BatchPlan::init(int capacity_slots, long long capacity_items, int num_sms_) 
   const size_t beg_b = sizeof(long long) * ((size_t)cap_slots + 1);
   size_t total = 0;
   auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-  total += kPasses * 3 * (up(ids_b) + up(beg_b));
+  total += kPasses * kNumWidths * (up(ids_b) + up(beg_b));
   total += up(sizeof(ScreenSlot) * (size_t)cap_slots);
   total += up(sizeof(uint2) * (size_t)std::max<long long>(cap_items, 1));
   total += up(sizeof(unsigned long long) * kCounters);
   if (cudaMalloc(&mem, total) != cudaSuccess) { cudaGetLastError(); return TRSTMI_ENOMEM; }
   char* p = (char*)mem;
   for (int pass = 0; pass < kPasses; ++pass)
-    for (int w = 0; w < 3; ++w) {
+    for (int w = 0; w < kNumWidths; ++w) {
       tables[pass][w].d_ids = (int*)p; p += up(ids_b);
       tables[pass][w].d_begin = (long long*)p; p += up(beg_b);
     }
@@ -65,25 +67,37 @@ int BatchPlan::rebuild(const std::vector<SlotDesc>& h, int precision_, cudaStrea
   for (int pass = 0; pass < kPasses; ++pass) {
     groups[pass].clear();
     if (!screen && pass != kPassFull) continue;
-    for (int w = 0; w < 3; ++w) {
+    for (int w = 0; w < kNumWidths; ++w) {
       const int R = kWidths[w];
       const bool pass64 = (pass == kPassFrame64) || (pass == kPassFull && f64);
+      const bool cand_pass = pass == kPassFull || pass == kPassRescore;
+      if (R == kResident && !cand_pass) continue;
       std::vector<int> ids;
       for (int i = 0; i < n; ++i) {
-        const int r_i = pass == kPassFrame64 ? frame64_width(h[i].d, h[i].N, h[i].R) : h[i].R;
+        // resident instances score their frames (certification passes) in
+        // tiles of 16 columns
+        const int r_tile = h[i].R == kResident ? 1 : h[i].R;
+        const int r_i = pass == kPassFrame64 ? frame64_width(h[i].d, h[i].N, r_tile)
+                        : cand_pass ? h[i].R : r_tile;
         if (r_i == R) ids.push_back(i);
       }
       if (ids.empty()) continue;
       auto keff = [&](int i) {
         return pass == kPassFull ? h[i].K : pass == kPassRescore ? h[i].topk_n : 1;
       };
-      auto cost = [&](int i) { return (double)keff(i) * tiles_at_width(h[i].N, R) * h[i].d; };
+      // work items: one per candidate (resident) or per (candidate, tile)
+      auto units = [&](int i) { return R == kResident ? 1 : tiles_at_width(h[i].N, R); };
+      auto cost = [&](int i) {
+        return (double)keff(i) * (R == kResident ? (double)h[i].N * h[i].N / 256.0 : units(i)) *
+               h[i].d;
+      };
       std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) { return cost(x) > cost(y); });
       std::vector<long long> begin(ids.size() + 1, 0);
       size_t smem = 0;
       for (size_t q = 0; q < ids.size(); ++q) {
-        begin[q + 1] = begin[q] + (long long)keff(ids[q]) * tiles_at_width(h[ids[q]].N, R);
-        smem = std::max(smem, gram_smem_bytes(pass64, h[ids[q]].d, R));
+        begin[q + 1] = begin[q] + (long long)keff(ids[q]) * units(ids[q]);
+        smem = std::max(smem, R == kResident ? resident_smem_bytes(pass64, h[ids[q]].d, h[ids[q]].N)
+                                             : gram_smem_bytes(pass64, h[ids[q]].d, R));
       }
       Group g;
       g.R = R;
@@ -95,8 +109,9 @@ int BatchPlan::rebuild(const std::vector<SlotDesc>& h, int precision_, cudaStrea
       g.smem = smem;
       g.counter = ncounters++;
       int per_sm = 0;
-      if (batch_score_occupancy(pass64, R, smem, &per_sm) != cudaSuccess || per_sm < 1)
-        return TRSTMI_ECUDA;
+      const cudaError_t oe = R == kResident ? batch_resident_occupancy(pass64, smem, &per_sm)
+                                            : batch_score_occupancy(pass64, R, smem, &per_sm);
+      if (oe != cudaSuccess || per_sm < 1) return TRSTMI_ECUDA;
       g.grid = (int)std::min<long long>(g.nitems, (long long)num_sms * per_sm);
       if (cudaMemcpyAsync(g.d_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
           cudaMemcpyAsync(g.d_begin, begin.data(), sizeof(long long) * begin.size(),
@@ -138,8 +153,12 @@ int BatchPlan::rebuild(const std::vector<SlotDesc>& h, int precision_, cudaStrea
 
 cudaError_t BatchPlan::launch_pass(int pass, SlotDesc* d_slots, cudaStream_t s) const {
   for (const auto& g : groups[pass]) {
-    cudaError_t e = launch_batch_score(g.f64, g.R, d_slots, g.d_ids, g.d_begin, g.count, g.nitems,
-                                       d_counters + g.counter, g.smem, g.grid, s, pass);
+    cudaError_t e =
+        g.R == kResident
+            ? launch_batch_resident(g.f64, d_slots, g.d_ids, g.d_begin, g.count, g.nitems,
+                                    d_counters + g.counter, g.smem, g.grid, s, pass)
+            : launch_batch_score(g.f64, g.R, d_slots, g.d_ids, g.d_begin, g.count, g.nitems,
+                                 d_counters + g.counter, g.smem, g.grid, s, pass);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -128,6 +128,8 @@ __global__ void k_srv_set_stop(SlotDesc* slots, int n, uint32_t iters, const uin
   unsigned long long stop = (unsigned long long)st->t + iters;
   if (stop > budget[s]) stop = budget[s];
   st->t_stop = (uint32_t)stop;
+  st->t_call = st->t;   // iterations of this round = t - t_call
+  st->accepts_call = st->accepts;
 }
 
 // Marks a slot active (or not) for a width measurement, without advancing it.
@@ -213,25 +215,27 @@ namespace {
 int choose_width(trstmi_server* sv, Slot& sl) {
   const int N = sl.desc.N, d = sl.desc.d;
   int R = cached_width(sv->f64, d, N);   // the binary32 pass in the screen modes
-  if (R > 0) return R;
+  if (R >= 0) return R;
   // measure this bucket on this slot alone (its state is active for timing)
   int best_R = 1;
   float best = 1e30f;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return 1;
   k_srv_activate<<<1, 1, 0, sv->stream>>>(sl.desc.st, 1u);
-  for (int cand : {1, 2, 4}) {
-    if (gram_smem_bytes(sv->f64, d, cand) > 200 * 1024) continue;
-    if (cand > 1 && 16 * cand >= 2 * N) continue;
+  for (int cand : {kResident, 1, 2, 4}) {
+    if (!width_feasible(sv->f64, d, N, cand)) continue;
     SlotDesc tmp = sl.desc;
     tmp.R = cand;
     tmp.ntiles = tiles_at_width(N, cand);
     const long long nitems = (long long)tmp.K * tmp.ntiles;
     const long long begin[2] = {0, nitems};
     const int ids[1] = {0};
-    const size_t smem = gram_smem_bytes(sv->f64, d, cand);
+    const size_t smem = cand == kResident ? resident_smem_bytes(sv->f64, d, N)
+                                          : gram_smem_bytes(sv->f64, d, cand);
     int per_sm = 0;
-    if (batch_score_occupancy(sv->f64, cand, smem, &per_sm) != cudaSuccess || per_sm < 1) continue;
+    const cudaError_t oe = cand == kResident ? batch_resident_occupancy(sv->f64, smem, &per_sm)
+                                             : batch_score_occupancy(sv->f64, cand, smem, &per_sm);
+    if (oe != cudaSuccess || per_sm < 1) continue;
     const int grid = (int)std::min<long long>(nitems, (long long)sv->num_sms * per_sm);
     // slot table entry 0 is rewritten by rebuild_tables before the next round
     cudaMemcpyAsync(sv->d_slots, &tmp, sizeof(SlotDesc), cudaMemcpyHostToDevice, sv->stream);
@@ -241,8 +245,12 @@ int choose_width(trstmi_server* sv, Slot& sl) {
     for (int rep = 0; rep < 3; ++rep) {
       cudaMemsetAsync(sv->plan.d_counters, 0, sizeof(unsigned long long), sv->stream);
       cudaEventRecord(e0, sv->stream);
-      launch_batch_score(sv->f64, cand, sv->d_slots, sv->d_tune_ids, sv->d_tune_begin, 1, nitems,
-                         sv->plan.d_counters, smem, grid, sv->stream, kPassFull);
+      if (cand == kResident)
+        launch_batch_resident(sv->f64, sv->d_slots, sv->d_tune_ids, sv->d_tune_begin, 1, nitems,
+                              sv->plan.d_counters, smem, grid, sv->stream, kPassFull);
+      else
+        launch_batch_score(sv->f64, cand, sv->d_slots, sv->d_tune_ids, sv->d_tune_begin, 1, nitems,
+                           sv->plan.d_counters, smem, grid, sv->stream, kPassFull);
       cudaEventRecord(e1, sv->stream);
       cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -385,7 +393,7 @@ void worker_main(trstmi_server* sv) {
   cudaSetDevice(sv->opt.search.device);
   std::deque<uint64_t> pending;
   bool changed = true;
-  std::vector<DevState> st;
+  std::vector<DevState> st, all_st;
   const int I = std::max(1, sv->opt.iters_per_round);
   while (!sv->stop.load()) {
     {
@@ -460,14 +468,16 @@ void worker_main(trstmi_server* sv) {
     bool ok = cudaGetLastError() == cudaSuccess;
     for (int it = 0; ok && it < I; ++it)
       ok = sv->plan.enqueue_iteration(sv->d_slots, n, sv->d_err, s) == TRSTMI_OK;
-    st.resize(n);
-    for (int k = 0; ok && k < n; ++k)
-      ok = cudaMemcpyAsync(&st[k], sv->slots[k].desc.st, sizeof(DevState), cudaMemcpyDeviceToHost,
-                           s) == cudaSuccess;
+    // one copy of the whole state array, then each slot's entry
+    all_st.resize(sv->opt.max_slots);
+    ok = ok && cudaMemcpyAsync(all_st.data(), sv->d_states, sizeof(DevState) * all_st.size(),
+                               cudaMemcpyDeviceToHost, s) == cudaSuccess;
     uint32_t screen_err = 0;
     ok = ok && cudaMemcpyAsync(&screen_err, sv->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                s) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+    st.resize(n);
+    for (int k = 0; ok && k < n; ++k) st[k] = all_st[sv->slots[k].state_idx];
     // a screen launch that gave up waiting aborts every slot of the round
     if (ok && screen_err) {
       for (int k = 0; k < n; ++k) st[k].error |= screen_err;

@@ -896,6 +896,145 @@ __global__ void __launch_bounds__(256) k_batch_score(const SlotDesc* slots, cons
   }
 }
 
+// Whole-candidate scoring for small instances (batched form).  The CTA draws
+// all N columns of candidate c once into shared memory as [i][column] planes
+// (the tile path draws every column block once per tile of its row and
+// column), then reduces every pair j < k with 4 x 4 micro-tiles spread over
+// the threads.  Generation (gen_column), the sequential chain over i and the
+// explicit rounding of |G|^2 are those of score_tile, so the scores are the
+// same bits.  Np = N rounded up to a multiple of 4; padded columns are zero.
+template <typename T>
+__device__ T score_resident(int N, int d, const void* phi, uint64_t seed, uint32_t c, uint32_t t,
+                            double delta, T* sm, int* zero_col) {
+  using C = typename Cplx<T>::type;
+  const int Np = (N + 3) & ~3;
+  T* sRe = sm;
+  T* sIm = sm + (size_t)d * Np;
+  __syncthreads();
+  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
+    if (j < N) {
+      if (!gen_column<T>(reinterpret_cast<const C*>(phi), d, j, seed, c, t, 0u, (T)delta, sRe + j,
+                         sIm + j, Np))
+        *zero_col = 1;
+    } else {
+      for (int i = 0; i < d; ++i) { sRe[i * Np + j] = T(0); sIm[i * Np + j] = T(0); }
+    }
+  }
+  __syncthreads();
+  const int nq = Np >> 2;
+  const int nmt = nq * (nq + 1) / 2;
+  T m = T(0);
+  for (int w = threadIdx.x; w < nmt; w += blockDim.x) {
+    int a, b;
+    tile_coords(w, a, b);   // a <= b: rows 4a.., columns 4b..
+    T accR[4][4], accI[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) { accR[x][y] = T(0); accI[x][y] = T(0); }
+    for (int i = 0; i < d; ++i) {
+      const T* ri = sRe + (size_t)i * Np;
+      const T* ii = sIm + (size_t)i * Np;
+      T ar[4], ai[4], br[4], bi[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        ar[x] = ri[4 * a + x];
+        ai[x] = ii[4 * a + x];
+        br[x] = ri[4 * b + x];
+        bi[x] = ii[4 * b + x];
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          accR[x][y] = fma(ar[x], br[y], fma(ai[x], bi[y], accR[x][y]));
+          accI[x][y] = fma(ar[x], bi[y], fma(-ai[x], br[y], accI[x][y]));
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int j = 4 * a + x, k = 4 * b + y;
+        if (j < k && k < N) m = fmax(m, pair_abs2(accR[x][y], accI[x][y]));
+      }
+  }
+  return m;
+}
+
+template <typename T>
+size_t resident_smem(int d, int N) {
+  return (size_t)2 * d * (size_t)((N + 3) & ~3) * sizeof(T);
+}
+
+// Persistent whole-candidate pass over the resident instances of a batch:
+// work items (instance, k) from *counter; k indexes the candidates (full
+// ranking) or the top-k survivors (re-score), as in k_batch_score.
+template <typename T>
+__global__ void __launch_bounds__(128) k_batch_resident(const SlotDesc* slots, const int* group,
+                                                        const long long* group_begin, int ngroup,
+                                                        long long nitems,
+                                                        unsigned long long* counter, int mode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T red[4];
+  __shared__ int zero_col;
+  __shared__ long long item;
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  for (;;) {
+    if (threadIdx.x == 0) item = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const long long w = item;
+    if (w >= nitems) return;
+    int lo = 0, hi = ngroup - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (group_begin[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    const SlotDesc& sd = slots[group[lo]];
+    const DevState* st = sd.st;
+    const bool run = st->active && (mode == kPassFull ? st->use_full : st->use_screen);
+    if (run) {
+      const int k = (int)(w - group_begin[lo]);
+      const uint32_t c = mode == kPassFull ? (uint32_t)k : sd.topk[k];
+      if (threadIdx.x == 0) zero_col = 0;
+      T m = score_resident<T>(sd.N, sd.d, sd.phi, sd.seed, c, st->t + 1u, st->delta_used, sm,
+                              &zero_col);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) m = fmax(m, red[q]);
+        if (zero_col) atomicOr(&const_cast<DevState*>(st)->error, (uint32_t)kErrZeroColumn);
+        typename Mu2Bits<T>::type* out =
+            mode == kPassFull ? reinterpret_cast<typename Mu2Bits<T>::type*>(sd.mu2) + k
+                              : reinterpret_cast<typename Mu2Bits<T>::type*>(sd.mu2_top) + k;
+        atomic_max_nonneg(out, m);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_batch_resident(bool f64, const SlotDesc* slots, const int* group,
+                                  const long long* group_begin, int ngroup, long long nitems,
+                                  unsigned long long* counter, size_t smem, int grid,
+                                  cudaStream_t s, int mode) {
+  if (ngroup < 1 || nitems < 1) return cudaSuccess;
+  if (mode != kPassFull && mode != kPassRescore) return cudaErrorInvalidValue;
+  if (f64)
+    k_batch_resident<double><<<grid, 128, smem, s>>>(slots, group, group_begin, ngroup, nitems,
+                                                     counter, mode);
+  else
+    k_batch_resident<float><<<grid, 128, smem, s>>>(slots, group, group_begin, ngroup, nitems,
+                                                    counter, mode);
+  return cudaGetLastError();
+}
+
+size_t resident_smem_bytes(bool f64, int d, int N) {
+  return f64 ? resident_smem<double>(d, N) : resident_smem<float>(d, N);
+}
+
 template <typename T>
 static cudaError_t launch_batch_score_t(int R, const SlotDesc* slots, const int* group,
                                         const long long* group_begin, int ngroup, long long nitems,
@@ -1076,6 +1215,13 @@ static cudaError_t occupancy_of(K kernel, size_t smem, int* blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, 256, smem);
 }
 
+cudaError_t batch_resident_occupancy(bool f64, size_t smem, int* blocks_per_sm) {
+  return f64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_resident<double>,
+                                                             128, smem)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_resident<float>,
+                                                             128, smem);
+}
+
 cudaError_t batch_score_occupancy(bool f64, int R, size_t smem, int* blocks_per_sm) {
   if (f64) {
     if (R == 4) return occupancy_of(k_batch_score<double, 4>, smem, blocks_per_sm);
@@ -1187,6 +1333,8 @@ cudaError_t init_kernel_attributes() {
   if ((e = allow_max_dynamic_smem(k_batch_score<double, 4>, optin)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_batch_score<double, 2>, optin)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_batch_score<double, 1>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_batch_resident<float>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_batch_resident<double>, optin)) != cudaSuccess) return e;
   return init_screen_attributes(optin);
 }
 

@@ -38,6 +38,7 @@ def test_results_equal_standalone_runs():
         results = [srv.wait(t, with_phi=True) for t in tickets]
         stats = srv.stats()
     assert stats.completed == len(reqs) and stats.worker_status == 0
+    assert stats.pairs_scored == sum(res.pairs_scored for _, res, _ in results)
     for (N, d, seed, budget, target), (st, res, phi) in zip(reqs, results):
         assert st == T.TRSTMI_OK
         info, phi_alone = _alone(N, d, seed, K, budget, target)
