@@ -62,7 +62,7 @@ def flops_per_pair(d):
 
 def kernels_per_step(precision):
     # one k_set_stop per trstmi_step call plus the iteration's kernels
-    return 1 + {"fp64": 4, "fp32": 4, "bf16": 11}[precision]
+    return 1 + {"fp64": 4, "fp32": 5, "bf16": 11}[precision]
 
 
 def dist_env():
@@ -399,7 +399,7 @@ def main():
     achieved = flops_launch / (kernel_ms * 1e-3) / 1e12
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
                  "traffic": profiled_traffic(prec),
-                 "kernel": "k_screen (bf16)" if prec == "bf16" else "k_gram_tile",
+                 "kernel": "k_screen (bf16)" if prec == "bf16" else ("k_gen_planes_f32 + k_gram_tile (one fp32 scoring pass)" if prec == "fp32" else "k_gram_tile"),
                  "kernel_ms": kernel_ms, "flops_per_launch": flops_launch, "peak_source": peak_note})
 
     side = None

@@ -92,6 +92,8 @@ struct trstmi_instance {
   uint32_t* misc = nullptr;                // [0] npairs, [1] overflow (standalone certify)
   uint2* pairs = nullptr;                  // kPairCap
   TraceRowDev* trace = nullptr;            // trace_cap
+  float* planes = nullptr;                 // TRSTMI_FP32: the K candidates of an iteration,
+                                           // drawn once as [i][column] planes (2dN floats each)
   std::map<int, cudaGraphExec_t> graphs;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -214,6 +216,11 @@ int enqueue_iteration_score(trstmi_instance* h, cudaStream_t s, int c_lo, int c_
       src.seed = h->seed;
       src.c0 = (uint32_t)c_lo;
       src.st = st;
+      if (h->planes) {
+        TRY_CUDA(launch_gen_planes_f32(N, d, count, h->phi32, h->seed, (uint32_t)c_lo, st, 0u,
+                                       0.0, h->planes, s));
+        src.planes = h->planes;
+      }
       TRY_CUDA(launch_gram_f32(N, d, count, src, h->mu2_k32 + c_lo, nullptr, h->num_sms, s));
     }
   } else {
@@ -432,6 +439,12 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   const size_t o_misc = take(2 * sizeof(uint32_t));
   const size_t o_pairs = take((size_t)kPairCap * sizeof(uint2));
   const size_t o_trace = take((size_t)std::max(o.trace_cap, 1) * sizeof(TraceRowDev));
+  // TRSTMI_FP32: room for the iteration's K candidates (up to 1 GiB), so each
+  // is drawn once and its tiles read it, instead of every tile redrawing its
+  // two column blocks
+  const size_t planes_bytes = (size_t)K * 2 * nd * sizeof(float);
+  const size_t o_planes = (o.precision == TRSTMI_FP32 && planes_bytes <= ((size_t)1 << 30))
+                              ? take(planes_bytes) : (size_t)-1;
   h->block_bytes = off;
   if (cudaMalloc(&h->block, off) != cudaSuccess) {
     cudaGetLastError();
@@ -454,6 +467,7 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   h->misc = (uint32_t*)(b + o_misc);
   h->pairs = (uint2*)(b + o_pairs);
   h->trace = (TraceRowDev*)(b + o_trace);
+  if (o_planes != (size_t)-1) h->planes = (float*)(b + o_planes);
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
     trstmi_destroy(h);
     return TRSTMI_ECUDA;
@@ -850,8 +864,17 @@ int trstmi_profile_score(trstmi_handle h, int precision, int launches, double de
       src.phi = h->phi64;
       e = launch_gram_f64(h->N, h->d, K, src, h->mu2_k64, h->num_sms, s);
     } else if (precision == TRSTMI_FP32) {
+      // the scoring pass of the binary32 iteration: the candidates drawn once
+      // (when the instance has room for them), then the tile pass
       src.phi = h->phi32;
-      e = launch_gram_f32(h->N, h->d, K, src, h->mu2_k32, nullptr, h->num_sms, s);
+      e = cudaSuccess;
+      if (h->planes) {
+        e = launch_gen_planes_f32(h->N, h->d, K, h->phi32, h->seed, 0u, nullptr, src.t, delta,
+                                  h->planes, s);
+        src.planes = h->planes;
+      }
+      if (e == cudaSuccess)
+        e = launch_gram_f32(h->N, h->d, K, src, h->mu2_k32, nullptr, h->num_sms, s);
     } else {
       e = launch_screen(precision == TRSTMI_FP16_SCREEN, h->N, h->d, h->seed, h->phi32, K, 0u,
                         (uint32_t)(l + 1), delta, nullptr, h->mu2_k32, &h->misc[1], h->num_sms, s);

@@ -23,7 +23,20 @@ struct GramSource {
   const DevState* st;           // nullable: t = st->t + 1, delta = st->delta_used, skip unless active
   bool normalize;               // frame source only
   const uint32_t* gate;         // nullable: skip the pass unless *gate != 0
+  // perturb with planes != nullptr: slot s's candidate was drawn already (by
+  // launch_gen_planes) into planes + s * 2dN as [i][column] planes of real then
+  // imaginary parts; the pass reads it instead of drawing it per tile
+  const void* planes;
 };
+
+// Draws candidates c0 .. c0+count-1 (with st: of the next iteration, t + 1
+// and the radius in use, nothing unless st->active, zero columns set
+// kErrZeroColumn; without: of iteration t with radius delta) around the
+// binary32 frame into [i][column] planes, slot s at planes + s * 2dN floats.
+// One thread per column, the arithmetic of the tile pass.
+cudaError_t launch_gen_planes_f32(int N, int d, int count, const float2* phi, uint64_t seed,
+                                  uint32_t c0, DevState* st, uint32_t t, double delta,
+                                  float* planes, cudaStream_t s);
 
 // Optional pair filter of the binary32 certification pass.
 struct PairFilter {

@@ -186,6 +186,27 @@ template <typename T> __device__ __forceinline__ T block_max(T v, T* red) {
   return v;  // valid in thread 0
 }
 
+// R consecutive shared-memory values (R * sizeof(T)-aligned) in vector loads.
+template <typename T, int R>
+__device__ __forceinline__ void load_run(const T* p, T (&v)[R]) {
+  if constexpr (sizeof(T) == 4 && R == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else if constexpr (sizeof(T) == 4 && R == 2) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  } else if constexpr (sizeof(T) == 8 && R >= 2) {
+#pragma unroll
+    for (int h = 0; h < R; h += 2) {
+      const double2 q = *reinterpret_cast<const double2*>(p + h);
+      v[h] = q.x; v[h + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int x = 0; x < R; ++x) v[x] = p[x];
+  }
+}
+
 // One work item of a Gram pass: tile (I <= J) of one frame, either the
 // candidate normalise(Phi + delta Z_{t,c}) or a stored frame.
 struct TileItem {
@@ -195,6 +216,7 @@ struct TileItem {
   uint64_t seed;
   uint32_t c, t;
   double delta;
+  const void* planes = nullptr;   // candidate drawn already: [i][column] re, then im planes
 };
 
 // The CTA (256 threads, 16 x 16) scores tile (I, J) of width BT = 16 R.
@@ -220,6 +242,24 @@ __device__ T score_tile(const TileItem& it, T* sm, int* zero_col, T thr,
   const bool diag = (I == J);
   __syncthreads();
   const int ncols = diag ? BT : 2 * BT;
+  if (it.planes) {
+    // coalesced copy of the two column blocks out of the drawn candidate
+    // (BT is a compile-time power of two: the index split is shifts)
+    const T* pre = reinterpret_cast<const T*>(it.planes);
+    const T* pim = pre + (size_t)d * N;
+    for (int blk = 0; blk < (diag ? 1 : 2); ++blk) {
+      const int c0 = (blk == 0 ? I : J) * BT;
+      T* ore = blk == 0 ? sIre : sJre;
+      T* oim = blk == 0 ? sIim : sJim;
+      for (int q = threadIdx.x; q < d * BT; q += blockDim.x) {
+        const int i = q / BT, loc = q % BT;
+        const int gj = c0 + loc;
+        const size_t g = (size_t)i * N + gj;
+        ore[q] = gj < N ? pre[g] : T(0);
+        oim[q] = gj < N ? pim[g] : T(0);
+      }
+    }
+  } else
   for (int q = threadIdx.x; q < ncols; q += blockDim.x) {
     const int blk = q / BT, loc = q - blk * BT;
     const int gj = (blk == 0 ? I : J) * BT + loc;
@@ -245,16 +285,15 @@ __device__ T score_tile(const TileItem& it, T* sm, int* zero_col, T thr,
   for (int x = 0; x < R; ++x)
 #pragma unroll
     for (int y = 0; y < R; ++y) { accR[x][y] = T(0); accI[x][y] = T(0); }
+  // thread (ty, tx) owns rows R ty .. R ty + R-1 and columns R tx .. R tx + R-1
+  // of the tile: R consecutive values per plane, one vector load each
 #pragma unroll 2
   for (int i = 0; i < d; ++i) {
     T ar[R], ai[R], br[R], bi[R];
-#pragma unroll
-    for (int x = 0; x < R; ++x) {
-      ar[x] = sIre[i * BT + ty + 16 * x];
-      ai[x] = sIim[i * BT + ty + 16 * x];
-      br[x] = bRe[i * BT + tx + 16 * x];
-      bi[x] = bIm[i * BT + tx + 16 * x];
-    }
+    load_run<T, R>(sIre + i * BT + R * ty, ar);
+    load_run<T, R>(sIim + i * BT + R * ty, ai);
+    load_run<T, R>(bRe + i * BT + R * tx, br);
+    load_run<T, R>(bIm + i * BT + R * tx, bi);
 #pragma unroll
     for (int x = 0; x < R; ++x)
 #pragma unroll
@@ -268,7 +307,7 @@ __device__ T score_tile(const TileItem& it, T* sm, int* zero_col, T thr,
   for (int x = 0; x < R; ++x)
 #pragma unroll
     for (int y = 0; y < R; ++y) {
-      const int gj = I * BT + ty + 16 * x, gk = J * BT + tx + 16 * y;
+      const int gj = I * BT + R * ty + x, gk = J * BT + R * tx + y;
       const T v = pair_abs2(accR[x][y], accI[x][y]);
       if (gj < gk && gk < N) {
         m = fmax(m, v);
@@ -284,8 +323,13 @@ __device__ T score_tile(const TileItem& it, T* sm, int* zero_col, T thr,
 
 // Gram pass over nslots frames (candidates of one instance, or stored
 // frames), one CTA per (slot, tile) work item, grid-stride.
+// binary32: at most 85 registers, so three 256-thread CTAs per SM hide the
+// loads of one CTA's next tile behind the others' arithmetic; binary64 keeps
+// its larger micro-tile in registers
+template <typename T> struct TileCtas { static constexpr int value = sizeof(T) == 4 ? 3 : 1; };
+
 template <typename T, int R>
-__global__ void __launch_bounds__(256) k_gram_tile(const GramArgs<T> a) {
+__global__ void __launch_bounds__(256, TileCtas<T>::value) k_gram_tile(const GramArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[8];
   __shared__ int zero_col;
@@ -322,6 +366,8 @@ __global__ void __launch_bounds__(256) k_gram_tile(const GramArgs<T> a) {
     if (src.perturb) {
       it.phi = src.phi;
       it.c = src.cand_list ? src.cand_list[slot] : src.c0 + (uint32_t)slot;
+      if (src.planes)
+        it.planes = reinterpret_cast<const T*>(src.planes) + (size_t)slot * 2 * d * N;
     } else {
       it.phi = reinterpret_cast<const typename Cplx<T>::type*>(src.phi) + (size_t)slot * d * N;
       it.c = 0u;
@@ -334,6 +380,35 @@ __global__ void __launch_bounds__(256) k_gram_tile(const GramArgs<T> a) {
     if (threadIdx.x == 0) atomic_max_nonneg(a.out + slot, m);
     __syncthreads();
   }
+}
+
+// Candidates drawn once for the tile pass (see launch_gen_planes_f32).
+__global__ void k_gen_planes_f32(int N, int d, int count, const float2* phi, uint64_t seed,
+                                 uint32_t c0, DevState* st, uint32_t t, float delta,
+                                 float* planes) {
+  if (st) {
+    if (!st->active) return;
+    t = st->t + 1u;
+    delta = (float)st->delta_used;
+  }
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= (long long)count * N) return;
+  const int slot = (int)(g / N), j = (int)(g - (long long)slot * N);
+  float* pre = planes + (size_t)slot * 2 * d * N;
+  float* pim = pre + (size_t)d * N;
+  if (!gen_column<float>(phi, d, j, seed, c0 + (uint32_t)slot, t, 0u, delta, pre + j, pim + j,
+                         N) && st)
+    atomicOr(&st->error, (uint32_t)kErrZeroColumn);
+}
+
+cudaError_t launch_gen_planes_f32(int N, int d, int count, const float2* phi, uint64_t seed,
+                                  uint32_t c0, DevState* st, uint32_t t, double delta,
+                                  float* planes, cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  const long long threads = (long long)count * N;
+  k_gen_planes_f32<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+      N, d, count, phi, seed, c0, st, t, (float)delta, planes);
+  return cudaGetLastError();
 }
 
 template <typename T> static size_t gram_smem(int d, int R) {
@@ -362,7 +437,12 @@ static cudaError_t launch_gram(int N, int d, int nslots, const GramSource& src,
   if (filter) a.filter = *filter; else a.filter = PairFilter{};
   const size_t smem = gram_smem<T>(d, R);
   const long long items = (long long)nslots * a.ntiles;
-  const int per_sm = smem <= 100 * 1024 ? 2 : 1;
+  int per_sm = 1;
+  cudaError_t oe = R == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_tile<T, 4>, 256, smem)
+                 : R == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_tile<T, 2>, 256, smem)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_tile<T, 1>, 256, smem);
+  if (oe != cudaSuccess) return oe;
+  per_sm = std::max(per_sm, 1);
   const int grid = (int)std::min<long long>(items, (long long)num_sms * per_sm * 4);
   switch (R) {
     case 4: k_gram_tile<T, 4><<<grid, 256, smem, s>>>(a); break;
@@ -808,7 +888,7 @@ cudaError_t launch_batch_begin(SlotDesc* slots, int n, unsigned long long* count
 // survivor) generated around the instance's frame, or the instance's stored
 // winner frame (one item per tile).
 template <typename T, int R>
-__global__ void __launch_bounds__(256) k_batch_score(const SlotDesc* slots, const int* group,
+__global__ void __launch_bounds__(256, TileCtas<T>::value) k_batch_score(const SlotDesc* slots, const int* group,
                                                      const long long* group_begin, int ngroup,
                                                      long long nitems,
                                                      unsigned long long* counter, int mode) {
