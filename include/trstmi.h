@@ -60,7 +60,11 @@ typedef enum trstmi_precision {
   /* as TRSTMI_BF16_SCREEN with fp16 screen operands: same tensor rate and
      storage, 2^-11 instead of 2^-9 input rounding (screen error on mu <= 1e-3
      instead of <= 4e-3 for unit vectors) */
-  TRSTMI_FP16_SCREEN = 3
+  TRSTMI_FP16_SCREEN = 3,
+  /* as TRSTMI_BF16_SCREEN with tf32 screen operands (fp32 values rounded to
+     10 mantissa bits; kind::tf32 MMAs at half the bf16 tensor rate, twice the
+     shared memory per column block: the screen takes N <= 768) */
+  TRSTMI_TF32_SCREEN = 4
 } trstmi_precision;
 
 /* ---------------------------------------------------------- options */
@@ -79,8 +83,9 @@ typedef struct trstmi_options {
      screen while its radius is >= screen_min_delta, and with the binary32
      Gram of every candidate below it, where candidate coherences differ by
      less than the screen's resolution (default 0.01; 0 = always screen).
-     Shapes the screen kernel does not take (d > 32 or N > 1536) always rank
-     with the binary32 Gram; the re-score and certification are unchanged. */
+     Shapes the screen kernel does not take (d > 32, or N > 1536; N > 768
+     with tf32 operands) always rank with the binary32 Gram; the re-score and
+     certification are unchanged. */
   double screen_min_delta;
   void *stream;         /* cudaStream_t to issue on, or NULL */
   int32_t device;       /* CUDA device ordinal (default 0) */

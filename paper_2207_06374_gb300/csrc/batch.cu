@@ -84,7 +84,7 @@ int ntiles_for(int N, int R) {
   return nb * (nb + 1) / 2;
 }
 
-bool is_screen_prec(int p) { return p == TRSTMI_BF16_SCREEN || p == TRSTMI_FP16_SCREEN; }
+bool is_screen_prec(int p) { return is_screen_precision(p); }
 
 }  // namespace
 
@@ -285,7 +285,7 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
   if (n < 1 || !N || !d || !seeds) return TRSTMI_EINVAL;
   trstmi_options o;
   if (opt) o = *opt; else trstmi_default_options(&o);
-  if (o.precision < TRSTMI_FP64 || o.precision > TRSTMI_FP16_SCREEN) return TRSTMI_EINVAL;
+  if (o.precision < TRSTMI_FP64 || o.precision > TRSTMI_TF32_SCREEN) return TRSTMI_EINVAL;
   const bool screen = is_screen_prec(o.precision);
   if (o.K < 1 || o.trace_cap < 0 || !(o.delta0 > 0) || !(o.gamma_inc >= 1) ||
       !(o.gamma_dec > 0 && o.gamma_dec <= 1) || !(o.delta_min >= 0) ||
@@ -371,7 +371,7 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
     sd.N = N[i]; sd.d = d[i]; sd.K = o.K; sd.R = 1; sd.ntiles = ntiles_for(N[i], 1);
     if (screen) {
       char* q = base + o_scr[i];
-      sd.screen = screen_supported(N[i], d[i]) ? 1 : 0;
+      sd.screen = screen_supported(N[i], d[i], screen_fmt_of(o.precision)) ? 1 : 0;
       sd.topk = (uint32_t*)q; q += up(tk * sizeof(uint32_t));
       sd.mu2_top = (unsigned int*)q; q += up(tk * sizeof(uint32_t));
       sd.cand64 = (double2*)q; q += up(nd * sizeof(double2));
@@ -546,7 +546,7 @@ int trstmi_batch_profile_score(trstmi_batch_handle b, int launches, size_t flush
         (flush && cudaMemsetAsync(flush, l & 0xff, flush_bytes, s)) ||
         cudaEventRecord(b->ev0, s) != cudaSuccess) { rc = TRSTMI_ECUDA; break; }
     cudaError_t e = b->screen
-        ? launch_screen_batched(b->opt.precision == TRSTMI_FP16_SCREEN, b->plan.d_screen_slots,
+        ? launch_screen_batched(screen_fmt_of(b->opt.precision), b->plan.d_screen_slots,
                                 b->plan.d_items, b->plan.n_items, b->d_err, b->num_sms, s)
         : b->plan.launch_pass(kPassFull, b->d_slots, s);
     float ms = 0.f;

@@ -100,7 +100,7 @@ struct trstmi_instance {
 
 namespace {
 
-bool is_screen(int p) { return p == TRSTMI_BF16_SCREEN || p == TRSTMI_FP16_SCREEN; }
+bool is_screen(int p) { return is_screen_precision(p); }
 
 double welch_of(int N, int d) {
   if (N <= d || N < 2) return 0.0;
@@ -232,8 +232,8 @@ int enqueue_iteration_score(trstmi_instance* h, cudaStream_t s, int c_lo, int c_
       // rank the candidates: tensor-core screen while delta >= screen_min_delta,
       // else the fp32 Gram of every candidate (each kernel returns at once when
       // the other one is selected for this iteration)
-      if (screen_supported(N, d))
-        TRY_CUDA(launch_screen(prec == TRSTMI_FP16_SCREEN, N, d, h->seed, h->phi32, count,
+      if (screen_supported(N, d, screen_fmt_of(prec)))
+        TRY_CUDA(launch_screen(screen_fmt_of(prec), N, d, h->seed, h->phi32, count,
                                (uint32_t)c_lo, 0u, 0.0, st, h->mu2_k32 + c_lo, &st->error,
                                h->num_sms, s));
       GramSource full{};
@@ -332,7 +332,7 @@ int validate_options(int N, int d, const trstmi_options& o) {
   if (N < 2 || d < 1 || d > kMaxD) return TRSTMI_EINVAL;
   if ((long long)N * ((d + 1) / 2) >= (1ll << 32)) return TRSTMI_EINVAL;
   if (o.K < 1 || o.trace_cap < 0) return TRSTMI_EINVAL;
-  if (o.precision < TRSTMI_FP64 || o.precision > TRSTMI_FP16_SCREEN) return TRSTMI_EINVAL;
+  if (o.precision < TRSTMI_FP64 || o.precision > TRSTMI_TF32_SCREEN) return TRSTMI_EINVAL;
   if (is_screen(o.precision) && (o.topk < 1 || o.topk > 64 || o.topk > o.K))
     return TRSTMI_EINVAL;
   if (!(o.delta0 > 0) || !(o.gamma_inc >= 1) || !(o.gamma_dec > 0 && o.gamma_dec <= 1))
@@ -482,7 +482,7 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   s0.delta_min = o.delta_min;
   s0.delta_max = o.delta_max;
   // a shape outside the screen kernel's range ranks with the binary32 Gram
-  s0.screen_min_delta = (is_screen(o.precision) && !screen_supported(N, d))
+  s0.screen_min_delta = (is_screen(o.precision) && !screen_supported(N, d, screen_fmt_of(o.precision)))
                             ? std::numeric_limits<double>::infinity()
                             : o.screen_min_delta;
   s0.trace_cap = (uint32_t)o.trace_cap;
@@ -756,8 +756,8 @@ int trstmi_score(trstmi_handle h, uint32_t t, uint32_t c0, int count, double del
         src.phi = h->phi32;
         e = launch_gram_f32(h->N, h->d, count, src, (unsigned int*)tmp, nullptr, h->num_sms, s);
       } else {
-        if (!screen_supported(h->N, h->d)) { rc = TRSTMI_EUNSUPPORTED; break; }
-        e = launch_screen(precision == TRSTMI_FP16_SCREEN, h->N, h->d, h->seed, h->phi32, count,
+        if (!screen_supported(h->N, h->d, screen_fmt_of(precision))) { rc = TRSTMI_EUNSUPPORTED; break; }
+        e = launch_screen(screen_fmt_of(precision), h->N, h->d, h->seed, h->phi32, count,
                           c0, t, delta, nullptr, (unsigned int*)tmp, &h->misc[1], h->num_sms, s);
       }
       if (e != cudaSuccess) { rc = record_cuda_error(e, "score kernel launch", __LINE__); break; }
@@ -838,8 +838,9 @@ int trstmi_mu2_frame(int N, int d, const double* phi, int precision, double* mu2
 int trstmi_profile_score(trstmi_handle h, int precision, int launches, double delta,
                          size_t flush_bytes, double* avg_ms) {
   if (!h || launches < 1 || !avg_ms || !(delta >= 0)) return TRSTMI_EINVAL;
-  if (precision < TRSTMI_FP64 || precision > TRSTMI_FP16_SCREEN) return TRSTMI_EINVAL;
-  if (is_screen(precision) && !screen_supported(h->N, h->d)) return TRSTMI_EUNSUPPORTED;
+  if (precision < TRSTMI_FP64 || precision > TRSTMI_TF32_SCREEN) return TRSTMI_EINVAL;
+  if (is_screen(precision) && !screen_supported(h->N, h->d, screen_fmt_of(precision)))
+    return TRSTMI_EUNSUPPORTED;
   TRY_CUDA(cudaSetDevice(h->opt.device));
   cudaStream_t s = h->stream;
   const int K = h->opt.K;
@@ -876,7 +877,7 @@ int trstmi_profile_score(trstmi_handle h, int precision, int launches, double de
       if (e == cudaSuccess)
         e = launch_gram_f32(h->N, h->d, K, src, h->mu2_k32, nullptr, h->num_sms, s);
     } else {
-      e = launch_screen(precision == TRSTMI_FP16_SCREEN, h->N, h->d, h->seed, h->phi32, K, 0u,
+      e = launch_screen(screen_fmt_of(precision), h->N, h->d, h->seed, h->phi32, K, 0u,
                         (uint32_t)(l + 1), delta, nullptr, h->mu2_k32, &h->misc[1], h->num_sms, s);
     }
     cudaEventRecord(ev[2 * l + 1], s);

@@ -4,8 +4,19 @@
 #include <cstdint>
 #include <vector>
 #include "common.cuh"
+#include "../../include/trstmi.h"
 
 namespace trstmi {
+
+// Operand format of the tensor-core screen.
+enum ScreenFmt : int { kScreenBF16 = 0, kScreenFP16 = 1, kScreenTF32 = 2 };
+inline bool is_screen_precision(int p) {
+  return p == TRSTMI_BF16_SCREEN || p == TRSTMI_FP16_SCREEN || p == TRSTMI_TF32_SCREEN;
+}
+inline int screen_fmt_of(int precision) {
+  return precision == TRSTMI_FP16_SCREEN ? kScreenFP16
+         : precision == TRSTMI_TF32_SCREEN ? kScreenTF32 : kScreenBF16;
+}
 
 // Which frame a Gram pass reads.
 struct GramSource {
@@ -96,7 +107,8 @@ cudaError_t launch_gen_candidate(int N, int d, uint64_t seed, uint32_t t, uint32
                                  const float2* phi32, double2* out, cudaStream_t s);
 
 // tensor-core screen (tc_screen.cu)
-bool screen_supported(int N, int d);
+// d <= 32 and N <= 1536 (bf16, fp16) or N <= 768 (tf32)
+bool screen_supported(int N, int d, int fmt);
 // One instance as the batched screen sees it (device table).
 struct ScreenSlot {
   const float2* phi32;
@@ -107,12 +119,12 @@ struct ScreenSlot {
 };
 // Screen of (instance, candidate) items of many instances; an instance's items
 // are skipped unless it is active and ranks with the screen this iteration.
-cudaError_t launch_screen_batched(bool fp16, const ScreenSlot* slots, const uint2* items,
+cudaError_t launch_screen_batched(int fmt, const ScreenSlot* slots, const uint2* items,
                                   int n_items, uint32_t* err_flag, int num_sms, cudaStream_t s);
 
-// fp16 = false: bf16 operands; true: fp16 operands.  With st, runs only when
-// st->active && st->use_screen.
-cudaError_t launch_screen(bool fp16, int N, int d, uint64_t seed, const float2* phi32, int K,
+// fmt: ScreenFmt of the operands.  With st, runs only when st->active &&
+// st->use_screen.
+cudaError_t launch_screen(int fmt, int N, int d, uint64_t seed, const float2* phi32, int K,
                           uint32_t c0, uint32_t t, double delta, const DevState* st,
                           unsigned int* mu2_out, uint32_t* err_flag, int num_sms,
                           cudaStream_t s);

@@ -16,7 +16,7 @@ namespace {
 constexpr int kWidths[4] = {4, 2, 1, kResident};
 constexpr int kNumWidths = 4;
 
-bool is_screen_prec(int p) { return p == TRSTMI_BF16_SCREEN || p == TRSTMI_FP16_SCREEN; }
+bool is_screen_prec(int p) { return is_screen_precision(p); }
 
 // Widest tile usable for a binary64 frame pass of this shape (<= R).
 int frame64_width(int d, int N, int R) {
@@ -178,7 +178,7 @@ int BatchPlan::enqueue_iteration(SlotDesc* d_slots, int n, uint32_t* err, cudaSt
   }
   // rank (screen, or fp32 below the screen radius), keep the top-k, re-score
   // them in fp32, regenerate the winner in fp64 and certify it, decide, commit
-  if (launch_screen_batched(precision == TRSTMI_FP16_SCREEN, d_screen_slots, d_items, n_items, err,
+  if (launch_screen_batched(screen_fmt_of(precision), d_screen_slots, d_items, n_items, err,
                             num_sms, s) != cudaSuccess ||
       launch_pass(kPassFull, d_slots, s) != cudaSuccess ||
       launch_batch_topk(d_slots, n, s) != cudaSuccess ||

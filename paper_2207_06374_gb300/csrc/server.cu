@@ -153,7 +153,7 @@ uint32_t slot_pair_cap(int N) {
   return (uint32_t)std::min<unsigned long long>(all, 1ull << 16);
 }
 
-bool is_screen_prec(int p) { return p == TRSTMI_BF16_SCREEN || p == TRSTMI_FP16_SCREEN; }
+bool is_screen_prec(int p) { return is_screen_precision(p); }
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -307,7 +307,7 @@ int admit(trstmi_server* sv, uint64_t ticket, Req& r, Slot* out) {
   std::memset(&sd, 0, sizeof(sd));
   if (sv->screen) {
     char* q = (char*)tr + up256((size_t)std::max(o.trace_cap, 1) * sizeof(TraceRowDev));
-    sd.screen = screen_supported(N, d) ? 1 : 0;
+    sd.screen = screen_supported(N, d, screen_fmt_of(o.precision)) ? 1 : 0;
     sd.topk = (uint32_t*)q; q += up256((size_t)o.topk * sizeof(uint32_t));
     sd.mu2_top = (unsigned int*)q; q += up256((size_t)o.topk * sizeof(uint32_t));
     sd.cand64 = (double2*)q; q += up256(nd * sizeof(double2));
@@ -570,7 +570,7 @@ int trstmi_server_create(const trstmi_server_opts* opts, trstmi_server** out) {
   trstmi_server_opts o;
   if (opts) o = *opts; else trstmi_default_server_opts(&o);
   const trstmi_options& so = o.search;
-  if (so.precision < TRSTMI_FP64 || so.precision > TRSTMI_FP16_SCREEN) return TRSTMI_EINVAL;
+  if (so.precision < TRSTMI_FP64 || so.precision > TRSTMI_TF32_SCREEN) return TRSTMI_EINVAL;
   if (o.max_slots < 1 || o.max_slots > 65536 || o.queue_cap < 1 || o.iters_per_round < 1 ||
       so.K < 1 || so.trace_cap < 0 || o.hbm_budget < 4096 || !(so.delta0 > 0) ||
       !(so.gamma_inc >= 1) || !(so.gamma_dec > 0 && so.gamma_dec <= 1) || !(so.delta_min >= 0) ||

@@ -30,9 +30,19 @@ namespace {
 
 constexpr int kDP = 32;                 // padded d: K = 2*kDP = 64 bf16 = 128 bytes / column
 constexpr int kBlockCols = 128;         // columns per block = MMA M = N
-constexpr int kBlockBytes = kBlockCols * 2 * kDP * 2;   // 16 KiB
-constexpr int kMaxBlocks = 12;          // N <= 1536
-constexpr int kRing = kMaxBlocks;       // block slots, used as a ring across candidates
+// Operand formats (ScreenFmt): a column block is 128 columns x 2 DP values.
+// bf16 / fp16: one 128-byte swizzle atom per column (Re 0..31 then Im 0..31),
+// 16 KiB per block, twelve slots (N <= 1536).  tf32: two atoms per column,
+// Re in the first 16 KiB of the block and Im in the second, 32 KiB per block,
+// six slots (N <= 768).  Either way the slots fill the same 192 KiB.
+template <int F> struct FmtTraits {
+  static constexpr int kBlockBytes = F == kScreenTF32 ? 32768 : 16384;
+  static constexpr int kSlots = F == kScreenTF32 ? 6 : 12;
+  // instruction-descriptor operand format: fp16 0, bf16 1 (kind::f16), tf32 2 (kind::tf32)
+  static constexpr uint32_t kAB = F == kScreenFP16 ? 0u : F == kScreenBF16 ? 1u : 2u;
+};
+constexpr int kOperandBytes = 12 * 16384;
+constexpr int kRing = 12;               // barrier slots: the largest ring
 // Warp roles.  A warp runs on SM sub-partition (warp % 4), and reads only
 // the tensor-memory lanes 32 (warp % 4) .. +31.  Sub-partition 0 holds the MMA
 // issuer (warp 0), two epilogue warps (4 and 8) and a single generator (12),
@@ -144,10 +154,11 @@ __device__ __forceinline__ void tc_fence_after() {
 // bits 0-13, leading byte offset 1 (unused) in bits 16-29, stride byte offset
 // 1024 >> 4 in bits 32-45, version 1 in bits 46-47, swizzle mode 2 in bits
 // 61-63.  A step of 16 bf16 along K is 32 bytes, i.e. +2 in the low word.
-// Instruction descriptor, kind::f16: D fp32, A and B both bf16 (format 1)
-// or both fp16 (format 0), both K-major, M = N = 128; bit 13 negates A.
-template <bool kHalf> struct Idesc {
-  static constexpr uint32_t fmt = kHalf ? 0u : 1u;
+// Instruction descriptor: D fp32, A and B of the same format (fp16 0 or
+// bf16 1 with kind::f16, tf32 2 with kind::tf32), both K-major,
+// M = N = 128; bit 13 negates A.
+template <int F> struct Idesc {
+  static constexpr uint32_t fmt = FmtTraits<F>::kAB;
   static constexpr uint32_t pos = (1u << 4) | (fmt << 7) | (fmt << 10) | ((128u >> 3) << 17) |
                                   ((128u >> 4) << 24);
   static constexpr uint32_t neg_a = pos | (1u << 13);
@@ -161,14 +172,24 @@ __device__ __forceinline__ uint32_t desc_lo(uint32_t addr) {
 }
 
 // One MMA from the low descriptor words (the high word is kDescHi).
+template <int F>
 __device__ __forceinline__ void mma_lo(uint32_t tmem_d, uint32_t alo, uint32_t blo,
                                        uint32_t idesc, uint32_t accumulate, uint32_t hi) {
-  asm volatile(
-      "{\n .reg .pred p;\n .reg .b64 da, db;\n setp.ne.b32 p, %4, 0;\n"
-      " mov.b64 da, {%1, %5};\n mov.b64 db, {%2, %5};\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n}\n" ::"r"(tmem_d),
-      "r"(alo), "r"(blo), "r"(idesc), "r"(accumulate), "r"(hi)
-      : "memory");
+  if constexpr (F == kScreenTF32) {
+    asm volatile(
+        "{\n .reg .pred p;\n .reg .b64 da, db;\n setp.ne.b32 p, %4, 0;\n"
+        " mov.b64 da, {%1, %5};\n mov.b64 db, {%2, %5};\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], da, db, %3, p;\n}\n" ::"r"(tmem_d),
+        "r"(alo), "r"(blo), "r"(idesc), "r"(accumulate), "r"(hi)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n .reg .b64 da, db;\n setp.ne.b32 p, %4, 0;\n"
+        " mov.b64 da, {%1, %5};\n mov.b64 db, {%2, %5};\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n}\n" ::"r"(tmem_d),
+        "r"(alo), "r"(blo), "r"(idesc), "r"(accumulate), "r"(hi)
+        : "memory");
+  }
 }
 
 __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
@@ -178,8 +199,15 @@ __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
       : "memory");
 }
 
-template <bool kHalf> __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-  if constexpr (kHalf) {
+// fp32 value rounded to tf32 (nearest, ties away), as the 32-bit word the MMA reads
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+template <int F> __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  if constexpr (F == kScreenFP16) {
     __half2 v = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
   } else {
@@ -367,8 +395,10 @@ __device__ __forceinline__ void absmax(const uint32_t (&re)[W], const uint32_t (
 
 // 20 warps: one SM sub-partition (16K registers) holds 5 of them, so a
 // thread may use at most 16384 / (5 * 32) -> 96 registers
-template <bool kHalf, class Src>
+template <int F, class Src>
 __global__ void __maxnreg__(96) k_screen(const Src src) {
+  constexpr int kSlots = FmtTraits<F>::kSlots;
+  constexpr int kBlockBytes = FmtTraits<F>::kBlockBytes;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ SmemCtl ctl;
   // 1024-byte aligned operand area
@@ -437,7 +467,7 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
       for (; u < u1; u += (uint32_t)kGenWarps) {
         const uint32_t gb = u / (uint32_t)kOctets;
         const int b = (int)(gb - gb0), o = (int)(u % (uint32_t)kOctets);
-        const uint32_t slot = gb % (uint32_t)kRing, fill = gb / (uint32_t)kRing;
+        const uint32_t slot = gb % (uint32_t)kSlots, fill = gb / (uint32_t)kSlots;
         if (fill > 0 && !warp_wait(&ctl.blk_empty[slot], (fill - 1u) & 1u, &ctl, err, 64))
           goto gen_done;
         unsigned char* blk = xs + slot * (uint32_t)kBlockBytes;
@@ -488,18 +518,31 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
         const float2 inv2 = make_float2(inv, inv);
 #pragma unroll
         for (int e = 0; e < 8; ++e) x[e] = __fmul2_rn(x[e], inv2);
-        uint4 re, im;
-        re.x = pack2<kHalf>(x[0].x, x[1].x);
-        re.y = pack2<kHalf>(x[2].x, x[3].x);
-        re.z = pack2<kHalf>(x[4].x, x[5].x);
-        re.w = pack2<kHalf>(x[6].x, x[7].x);
-        im.x = pack2<kHalf>(x[0].y, x[1].y);
-        im.y = pack2<kHalf>(x[2].y, x[3].y);
-        im.z = pack2<kHalf>(x[4].y, x[5].y);
-        im.w = pack2<kHalf>(x[6].y, x[7].y);
-        // real parts of entries 8q .. 8q+7 -> chunk q; imaginary -> chunk 4 + q
-        *reinterpret_cast<uint4*>(blk + swz_offset(r, q)) = re;
-        *reinterpret_cast<uint4*>(blk + swz_offset(r, 4 + q)) = im;
+        if constexpr (F == kScreenTF32) {
+          // real parts of entries 8q .. 8q+7 -> chunks 2q, 2q+1 of the first
+          // atom; imaginary parts -> the same chunks of the second
+          const uint4 r0 = make_uint4(to_tf32(x[0].x), to_tf32(x[1].x), to_tf32(x[2].x), to_tf32(x[3].x));
+          const uint4 r1 = make_uint4(to_tf32(x[4].x), to_tf32(x[5].x), to_tf32(x[6].x), to_tf32(x[7].x));
+          const uint4 i0 = make_uint4(to_tf32(x[0].y), to_tf32(x[1].y), to_tf32(x[2].y), to_tf32(x[3].y));
+          const uint4 i1 = make_uint4(to_tf32(x[4].y), to_tf32(x[5].y), to_tf32(x[6].y), to_tf32(x[7].y));
+          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q)) = r0;
+          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q + 1)) = r1;
+          *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q)) = i0;
+          *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q + 1)) = i1;
+        } else {
+          uint4 re, im;
+          re.x = pack2<F>(x[0].x, x[1].x);
+          re.y = pack2<F>(x[2].x, x[3].x);
+          re.z = pack2<F>(x[4].x, x[5].x);
+          re.w = pack2<F>(x[6].x, x[7].x);
+          im.x = pack2<F>(x[0].y, x[1].y);
+          im.y = pack2<F>(x[2].y, x[3].y);
+          im.z = pack2<F>(x[4].y, x[5].y);
+          im.w = pack2<F>(x[6].y, x[7].y);
+          // real parts of entries 8q .. 8q+7 -> chunk q; imaginary -> chunk 4 + q
+          *reinterpret_cast<uint4*>(blk + swz_offset(r, q)) = re;
+          *reinterpret_cast<uint4*>(blk + swz_offset(r, 4 + q)) = im;
+        }
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&ctl.blk_full[slot]);
@@ -597,11 +640,11 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
         const int nb = it.nb;
         for (int I = 0; I < nb && ok; ++I) {
           uint32_t sI = slot0 + (uint32_t)I;
-          if (sI >= (uint32_t)kRing) sI -= (uint32_t)kRing;
+          if (sI >= (uint32_t)kSlots) sI -= (uint32_t)kSlots;
           const uint32_t alo = xs_lo + sI * (uint32_t)(kBlockBytes >> 4);
           for (int J = I; J < nb; ++J, ++gt) {
             uint32_t sJ = slot0 + (uint32_t)J, parJ = par0;
-            if (sJ >= (uint32_t)kRing) { sJ -= (uint32_t)kRing; parJ ^= 1u; }
+            if (sJ >= (uint32_t)kSlots) { sJ -= (uint32_t)kSlots; parJ ^= 1u; }
             if (I == 0) {
               ok = mbar_wait(&ctl.blk_full[sJ], parJ, &ctl, err, kMmaBackoffNs);
               if (!ok) break;
@@ -614,22 +657,39 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
             tc_fence_after();
             const uint32_t blo = xs_lo + sJ * (uint32_t)(kBlockBytes >> 4);
             const uint32_t dre = tmem + buf * 256u, dim = dre + 128u;
-            // Re: sum over the whole K = 2*DP (4 steps of 16 = +2 in the low word)
-            mma_lo(dre, alo + 0u, blo + 0u, Idesc<kHalf>::pos, 0u, hi);
-            mma_lo(dre, alo + 2u, blo + 2u, Idesc<kHalf>::pos, 1u, hi);
-            mma_lo(dre, alo + 4u, blo + 4u, Idesc<kHalf>::pos, 1u, hi);
-            mma_lo(dre, alo + 6u, blo + 6u, Idesc<kHalf>::pos, 1u, hi);
-            // Im: A_I^T B_J (K slices 0,1 against 2,3) - B_I^T A_J (2,3 against 0,1)
-            mma_lo(dim, alo + 0u, blo + 4u, Idesc<kHalf>::pos, 0u, hi);
-            mma_lo(dim, alo + 2u, blo + 6u, Idesc<kHalf>::pos, 1u, hi);
-            mma_lo(dim, alo + 4u, blo + 0u, Idesc<kHalf>::neg_a, 1u, hi);
-            mma_lo(dim, alo + 6u, blo + 2u, Idesc<kHalf>::neg_a, 1u, hi);
+            if constexpr (F == kScreenTF32) {
+              // K steps of 8 tf32 = 32 bytes = +2 in the low word; the second
+              // atom (Im parts) is 16 KiB = +1024 further
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)   // Re: A_I^T A_J ...
+                mma_lo<F>(dre, alo + 2u * kk, blo + 2u * kk, Idesc<F>::pos, kk > 0 ? 1u : 0u, hi);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)   // ... + B_I^T B_J
+                mma_lo<F>(dre, alo + 1024u + 2u * kk, blo + 1024u + 2u * kk, Idesc<F>::pos, 1u, hi);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)   // Im: A_I^T B_J ...
+                mma_lo<F>(dim, alo + 2u * kk, blo + 1024u + 2u * kk, Idesc<F>::pos, kk > 0 ? 1u : 0u, hi);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)   // ... - B_I^T A_J
+                mma_lo<F>(dim, alo + 1024u + 2u * kk, blo + 2u * kk, Idesc<F>::neg_a, 1u, hi);
+            } else {
+              // Re: sum over the whole K = 2*DP (4 steps of 16 = +2 in the low word)
+              mma_lo<F>(dre, alo + 0u, blo + 0u, Idesc<F>::pos, 0u, hi);
+              mma_lo<F>(dre, alo + 2u, blo + 2u, Idesc<F>::pos, 1u, hi);
+              mma_lo<F>(dre, alo + 4u, blo + 4u, Idesc<F>::pos, 1u, hi);
+              mma_lo<F>(dre, alo + 6u, blo + 6u, Idesc<F>::pos, 1u, hi);
+              // Im: A_I^T B_J (K slices 0,1 against 2,3) - B_I^T A_J (2,3 against 0,1)
+              mma_lo<F>(dim, alo + 0u, blo + 4u, Idesc<F>::pos, 0u, hi);
+              mma_lo<F>(dim, alo + 2u, blo + 6u, Idesc<F>::pos, 1u, hi);
+              mma_lo<F>(dim, alo + 4u, blo + 0u, Idesc<F>::neg_a, 1u, hi);
+              mma_lo<F>(dim, alo + 6u, blo + 2u, Idesc<F>::neg_a, 1u, hi);
+            }
             mma_commit(&ctl.acc_full[buf]);
           }
           if (ok) mma_commit(&ctl.blk_empty[sI]);   // row I done: block I's slot is free
         }
         slot0 += (uint32_t)nb;
-        if (slot0 >= (uint32_t)kRing) { slot0 -= (uint32_t)kRing; par0 ^= 1u; }
+        if (slot0 >= (uint32_t)kSlots) { slot0 -= (uint32_t)kSlots; par0 ^= 1u; }
       }
       // all issued MMAs complete before tensor memory is released
       mma_commit(&ctl.drain);
@@ -648,46 +708,70 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
   }
 }
 
-size_t screen_smem_bytes(int nb) { return (size_t)nb * kBlockBytes + 1024; }
+// the operand area is the same for every format: all slots of the ring
+constexpr size_t kScreenSmem = (size_t)kOperandBytes + 1024;
 
 template <class K> cudaError_t allow_screen_smem(K kernel, int optin) {
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              std::min((int)screen_smem_bytes(kMaxBlocks),
-                                       optin - (int)fa.sharedSizeBytes));
+                              std::min((int)kScreenSmem, optin - (int)fa.sharedSizeBytes));
 }
 
 // refuse (without launching) a configuration the SM cannot hold
 template <class K> cudaError_t screen_fits(K kernel) {
   int fit = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, kThreads,
-                                                                screen_smem_bytes(kMaxBlocks));
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, kThreads, kScreenSmem);
   if (e != cudaSuccess) return e;
   return fit < 1 ? cudaErrorLaunchOutOfResources : cudaSuccess;
 }
 
+template <int F, class Src>
+cudaError_t launch_fmt(const Src& src, int grid, cudaStream_t s) {
+  cudaError_t e = screen_fits(k_screen<F, Src>);
+  if (e != cudaSuccess) return e;
+  // the operand area is always reserved for the whole ring, so every
+  // descriptor address lies inside the CTA's shared memory
+  k_screen<F, Src><<<grid, kThreads, kScreenSmem, s>>>(src);
+  return cudaGetLastError();
+}
+
+template <class Src>
+cudaError_t launch_any(int fmt, const Src& src, int grid, cudaStream_t s) {
+  switch (fmt) {
+    case kScreenBF16: return launch_fmt<kScreenBF16>(src, grid, s);
+    case kScreenFP16: return launch_fmt<kScreenFP16>(src, grid, s);
+    case kScreenTF32: return launch_fmt<kScreenTF32>(src, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
-bool screen_supported(int N, int d) {
+bool screen_supported(int N, int d, int fmt) {
   const int nb = (N + kBlockCols - 1) / kBlockCols;
-  return N >= 2 && d >= 1 && d <= kDP && nb <= kMaxBlocks;
+  const int slots = fmt == kScreenTF32 ? FmtTraits<kScreenTF32>::kSlots
+                                       : FmtTraits<kScreenBF16>::kSlots;
+  return N >= 2 && d >= 1 && d <= kDP && nb <= slots;
 }
 
 cudaError_t init_screen_attributes(int optin) {
   cudaError_t e;
-  if ((e = allow_screen_smem(k_screen<false, OneInstance>, optin)) != cudaSuccess) return e;
-  if ((e = allow_screen_smem(k_screen<true, OneInstance>, optin)) != cudaSuccess) return e;
-  if ((e = allow_screen_smem(k_screen<false, ManyInstances>, optin)) != cudaSuccess) return e;
-  return allow_screen_smem(k_screen<true, ManyInstances>, optin);
+  if ((e = allow_screen_smem(k_screen<kScreenBF16, OneInstance>, optin)) != cudaSuccess) return e;
+  if ((e = allow_screen_smem(k_screen<kScreenFP16, OneInstance>, optin)) != cudaSuccess) return e;
+  if ((e = allow_screen_smem(k_screen<kScreenTF32, OneInstance>, optin)) != cudaSuccess) return e;
+  if ((e = allow_screen_smem(k_screen<kScreenBF16, ManyInstances>, optin)) != cudaSuccess) return e;
+  if ((e = allow_screen_smem(k_screen<kScreenFP16, ManyInstances>, optin)) != cudaSuccess) return e;
+  return allow_screen_smem(k_screen<kScreenTF32, ManyInstances>, optin);
 }
 
-cudaError_t launch_screen(bool fp16, int N, int d, uint64_t seed, const float2* phi32, int K,
+cudaError_t launch_screen(int fmt, int N, int d, uint64_t seed, const float2* phi32, int K,
                           uint32_t c0, uint32_t t, double delta, const DevState* st,
                           unsigned int* mu2_out, uint32_t* err_flag, int num_sms,
                           cudaStream_t s) {
-  if (!screen_supported(N, d) || K < 1) return cudaErrorInvalidValue;
+  if (!screen_supported(N, d, fmt) || K < 1) return cudaErrorInvalidValue;
   OneInstance src;
   ScreenArgs& a = src.a;
   a.N = N; a.d = d;
@@ -696,18 +780,10 @@ cudaError_t launch_screen(bool fp16, int N, int d, uint64_t seed, const float2* 
   a.K = K; a.seed = seed; a.phi = phi32; a.c0 = c0; a.t = t; a.delta = (float)delta;
   a.keys = philox_round_keys(seed);
   a.st = st; a.out = mu2_out; a.err = err_flag;
-  const int grid = std::min(K, num_sms);
-  cudaError_t e = fp16 ? screen_fits(k_screen<true, OneInstance>)
-                       : screen_fits(k_screen<false, OneInstance>);
-  if (e != cudaSuccess) return e;
-  // the operand area is always reserved for the largest block count, so every
-  // descriptor address lies inside the CTA's shared memory
-  if (fp16) k_screen<true, OneInstance><<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(src);
-  else k_screen<false, OneInstance><<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(src);
-  return cudaGetLastError();
+  return launch_any(fmt, src, std::min(K, num_sms), s);
 }
 
-cudaError_t launch_screen_batched(bool fp16, const ScreenSlot* slots, const uint2* items,
+cudaError_t launch_screen_batched(int fmt, const ScreenSlot* slots, const uint2* items,
                                   int n_items, uint32_t* err_flag, int num_sms, cudaStream_t s) {
   if (n_items < 1) return cudaSuccess;
   ManyInstances src;
@@ -715,13 +791,7 @@ cudaError_t launch_screen_batched(bool fp16, const ScreenSlot* slots, const uint
   src.items = items;
   src.n_items = n_items;
   src.error = err_flag;
-  const int grid = std::min(n_items, num_sms);
-  cudaError_t e = fp16 ? screen_fits(k_screen<true, ManyInstances>)
-                       : screen_fits(k_screen<false, ManyInstances>);
-  if (e != cudaSuccess) return e;
-  if (fp16) k_screen<true, ManyInstances><<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(src);
-  else k_screen<false, ManyInstances><<<grid, kThreads, screen_smem_bytes(kMaxBlocks), s>>>(src);
-  return cudaGetLastError();
+  return launch_any(fmt, src, std::min(n_items, num_sms), s);
 }
 
 }  // namespace trstmi

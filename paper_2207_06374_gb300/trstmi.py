@@ -19,8 +19,9 @@ TRSTMI_OK, TRSTMI_PENDING = 0, 1
 TRSTMI_EINVAL, TRSTMI_ENOMEM, TRSTMI_ECUDA, TRSTMI_ETIMEOUT = -1, -2, -3, -4
 TRSTMI_ECANCELLED, TRSTMI_EBUSY, TRSTMI_EUNSUPPORTED, TRSTMI_ENOTFOUND = -5, -6, -7, -8
 TRSTMI_ESIZE = -9
-FP64, FP32, BF16_SCREEN, FP16_SCREEN = 0, 1, 2, 3
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16_SCREEN, "fp16": FP16_SCREEN}
+FP64, FP32, BF16_SCREEN, FP16_SCREEN, TF32_SCREEN = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16_SCREEN, "fp16": FP16_SCREEN,
+              "tf32": TF32_SCREEN}
 
 
 class TrstmiError(RuntimeError):

@@ -98,7 +98,7 @@ SCREEN_MIX = [(4, 2), (9, 3), (40, 8), (129, 13), (200, 16), (17, 16), (300, 32)
               (50, 40), (1600, 4)]
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("precision", ["bf16", "fp16", "tf32"])
 def test_batch_screen_modes_match_single_runs_bitwise(precision):
     """Precision form in the batch: the shared screen launch over all
     (instance, candidate) items, shared top-k re-score and certification.

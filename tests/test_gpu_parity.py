@@ -249,6 +249,44 @@ def test_screen_scores_match_oracle(d, N, K):
             assert np.max(np.abs(np.sqrt(gbf) - np.sqrt(ref))) < 4e-3
 
 
+@pytest.mark.parametrize("d,N,K", [(32, 768, 4), (32, 300, 16), (7, 129, 16), (2, 4, 64),
+                                   (1, 5, 8), (32, 2, 4)])
+def test_tf32_screen_scores_match_oracle(d, N, K):
+    """tf32 screen (fp32 values rounded to 10 mantissa bits, kind::tf32 MMAs)
+    within 1e-3 of the oracle's mu on the same seeded candidates."""
+    seed = 97
+    with T.Search(N, d, seed, K=K, precision="fp32") as s:
+        phi0 = s.get_phi()
+        for (t, c0, delta) in [(1, 0, 0.1), (3, 40, 0.4)]:
+            ref = O.score(phi0, seed, delta, t, c0, K, nthreads=4)
+            g = s.score(t, c0, K, delta, "tf32")
+            assert np.max(np.abs(np.sqrt(g) - np.sqrt(ref))) < 1e-3
+
+
+def test_tf32_screen_rejects_shapes_beyond_its_range():
+    with T.Search(769, 8, 1, K=4, precision="fp32") as s:
+        with pytest.raises(T.TrstmiError) as e:
+            s.score(1, 0, 4, 0.1, "tf32")
+        assert e.value.status == T.TRSTMI_EUNSUPPORTED
+
+
+def test_tf32_mode_decisions_replay_exactly():
+    """tf32 precision form: screened iterations, fp32 re-score, fp64
+    certification; every decision reproduced by the oracle in binary64."""
+    d, N, K, iters, seed = 12, 200, 96, 15, 13
+    with T.Search(N, d, seed, K=K, precision="tf32", topk=6, screen_min_delta=0.0) as s:
+        phi0 = s.get_phi()
+        s.step(iters)
+        tr = s.trace()
+        phi = s.get_phi()
+    assert np.all(tr["flags"] & 1 == 1)
+    rphi, rm2, _, rtr = O.replay(phi0, seed, O.make_opts(K=K, T=iters), 0.1, O.mu2(phi0), 0,
+                                 tr["cstar"])
+    assert np.array_equal(tr["accepted"], rtr["accepted"])
+    check_precision_form_rows(tr, rtr, d, O.mu2(phi0))
+    assert np.abs(phi - rphi).max() < 1e-12
+
+
 def test_bf16_mode_decisions_replay_exactly():
     """Screen + fp32 top-k + fp64 certification: the certified mu of every
     chosen candidate equals the oracle's binary64 mu of that candidate, and the

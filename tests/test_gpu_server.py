@@ -50,7 +50,7 @@ def test_results_equal_standalone_runs():
             assert res.mu <= target
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("precision", ["bf16", "fp16", "tf32"])
 def test_screen_mode_results_equal_standalone_runs(precision):
     """Precision form through the serving loop (screen, fp32 top-k re-score,
     fp64 certification as shared launches over the resident slots): each

@@ -39,7 +39,8 @@ def _run_sharded(N, d, seed, K, iters, world, **opt):
 
 
 @pytest.mark.parametrize("precision,N,d,K", [("fp64", 12, 3, 40), ("fp32", 70, 8, 50),
-                                             ("bf16", 300, 24, 64), ("fp16", 40, 6, 33)])
+                                             ("bf16", 300, 24, 64), ("fp16", 40, 6, 33),
+                                             ("tf32", 150, 10, 24)])
 def test_sharded_search_equals_unsharded(precision, N, d, K):
     seed, iters = 17, 10
     with T.Search(N, d, seed, K=K, precision=precision, trace_cap=64) as s:
