@@ -38,6 +38,9 @@ WORKLOADS = {
     "precision_d32_n1024": (32, 1024, 1024, "bf16",
                             "complex d=32 N=1024, 1024 candidates/iteration, bf16 screen + "
                             "fp32 top-8 re-score + fp64 certify"),
+    "precision_tf32_d32_n768": (32, 768, 1024, "tf32",
+                                "complex d=32 N=768, 1024 candidates/iteration, tf32 screen + "
+                                "fp32 top-8 re-score + fp64 certify"),
     "plain_d32_n1024_fp32": (32, 1024, 1024, "fp32",
                              "complex d=32 N=1024, 1024 candidates/iteration, plain fp32"),
     "plain_d8_n64": (8, 64, 4096, "fp32",
@@ -62,7 +65,7 @@ def flops_per_pair(d):
 
 def kernels_per_step(precision):
     # one k_set_stop per trstmi_step call plus the iteration's kernels
-    return 1 + {"fp64": 4, "fp32": 5, "bf16": 11}[precision]
+    return 1 + {"fp64": 4, "fp32": 5, "bf16": 11, "tf32": 11}[precision]
 
 
 def dist_env():
@@ -147,7 +150,11 @@ KERNEL_SOURCES = {
     "fp32": ["paper_2207_06374_gb300/csrc/simt_kernels.cu", "paper_2207_06374_gb300/csrc/philox.cuh",
              "paper_2207_06374_gb300/csrc/common.cuh"],
 }
-KERNEL_PROFILE = {"bf16": "k_screen_bf16_d32_n1024.txt", "fp32": "k_gram_tile_f32_d32_n1024.txt"}
+KERNEL_SOURCES["tf32"] = KERNEL_SOURCES["bf16"]
+KERNEL_SOURCES["batched"] = KERNEL_SOURCES["fp32"]
+KERNEL_PROFILE = {"bf16": "k_screen_bf16_d32_n1024.txt", "tf32": "k_screen_tf32_d32_n768.txt",
+                  "fp32": "k_gram_tile_f32_d32_n1024.txt",
+                  "batched": "k_batch_resident_f32_batched_512.txt"}
 
 
 def kernel_source_sha1(precision):
@@ -390,6 +397,11 @@ def main():
         peak = peaks.get("bf16_tflops", 1900.0)
         roof = {"bound": "tensor", "unit": "TFLOP/s"}
         peak_note = f"bf16_tflops burst ({peak_kind})"
+    elif prec == "tf32":
+        # tf32 dense runs at half the bf16 rate (nominal 1.1 of 2.25 PFLOP/s)
+        peak = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25
+        roof = {"bound": "tensor", "unit": "TFLOP/s"}
+        peak_note = f"bf16_tflops burst ({peak_kind}) x 1.1 / 2.25 (nominal tf32 / bf16 ratio)"
     else:
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = fp32_alu_peak_tflops(sm_mhz) if prec == "fp32" else fp32_alu_peak_tflops(sm_mhz) / 64
@@ -399,7 +411,9 @@ def main():
     achieved = flops_launch / (kernel_ms * 1e-3) / 1e12
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
                  "traffic": profiled_traffic(prec),
-                 "kernel": "k_screen (bf16)" if prec == "bf16" else ("k_gen_planes_f32 + k_gram_tile (one fp32 scoring pass)" if prec == "fp32" else "k_gram_tile"),
+                 "kernel": (f"k_screen ({prec})" if prec in ("bf16", "tf32") else
+                            "k_gen_planes_f32 + k_gram_tile (one fp32 scoring pass)" if prec == "fp32"
+                            else "k_gram_tile"),
                  "kernel_ms": kernel_ms, "flops_per_launch": flops_launch, "peak_source": peak_note})
 
     side = None
@@ -414,7 +428,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
             "higher_is_better": True, "scaling": "strong" if sharded else "weak",
             "vs_baseline": None,
-            "dtype": {"bf16": "bf16", "fp32": "f32", "fp64": "f64"}[prec],
+            "dtype": {"bf16": "bf16", "tf32": "tf32", "fp32": "f32", "fp64": "f64"}[prec],
             "data": "synthetic (seeded Philox complex-Gaussian frames)",
             "config": {"workload": wl, "description": desc, "d": d, "N": N, "K": K,
                        "precision": prec, "seed": SEED, "screen_min_delta": 0.0,
@@ -506,8 +520,11 @@ def run_batched(args, ws, rank, local, dist, torch, T):
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write outside the timed events)",
                        "parallelism": f"independent batch per GPU x{ws}"},
             "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_batch_score (all width groups of one iteration)",
+                         "frac": achieved / peak,
+                         "traffic": profiled_traffic("batched") if set(widths) == {0} else None,
+                         "kernel": ("k_batch_resident (whole candidates in shared memory)"
+                                    if set(widths) == {0} else
+                                    "k_batch_resident / k_batch_score (all groups of one iteration)"),
                          "kernel_ms": kernel_ms, "flops_per_launch": flops,
                          "peak_source": f"fp32 FMA peak derived: 152 SMs x 128 lanes x 2 flops x {sm_mhz} MHz"},
             "gpu_launches": (4 + ngroups) * args.steps,

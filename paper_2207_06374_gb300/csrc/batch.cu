@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -138,7 +139,7 @@ int time_width(const std::vector<SlotDesc>& h, SlotDesc* d_slots, const std::vec
       cudaMemcpyAsync(d_begin, begin.data(), sizeof(long long) * begin.size(), cudaMemcpyHostToDevice, s))
     rc = TRSTMI_ECUDA;
   float best = 1e30f;
-  for (int rep = 0; rep < 3 && rc == TRSTMI_OK; ++rep) {
+  for (int rep = 0; rep < 5 && rc == TRSTMI_OK; ++rep) {
     float t = 0.f;
     if (cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s) ||
         cudaEventRecord(e0, s) ||
@@ -202,9 +203,21 @@ int autotune(trstmi_batch* b) {
   BTRY(cudaGetLastError());
   BTRY(launch_batch_begin(b->d_slots, b->n, b->plan.d_counters, BatchPlan::kCounters, f64s, false,
                           b->stream));
+  // TRSTMI_TILE_WIDTH = 0 (whole candidates), 16, 32 or 64 fixes the choice
+  // wherever it is feasible instead of timing the bucket (for measurements
+  // that must reproduce a given configuration)
+  int forced = -1;
+  if (const char* env = std::getenv("TRSTMI_TILE_WIDTH")) {
+    const int w = std::atoi(env);
+    if (w == 0 || w == 16 || w == 32 || w == 64) forced = w / 16;
+  }
   for (auto& kv : buckets) {
     int R = cached_width(f64s, kv.first.first, b->N[kv.second[0]]);
-    if (R < 0) {
+    if (forced >= 0) {
+      bool ok = true;
+      for (int i : kv.second) ok = ok && width_feasible(f64s, b->d[i], b->N[i], forced);
+      R = ok ? forced : 1;
+    } else if (R < 0) {
       float best = 1e30f;
       for (int cand : {kResident, 1, 2, 4}) {
         bool ok = true;

@@ -152,3 +152,22 @@ def test_batch_bf16_decisions_replay_in_fp64():
                           <= 2.0 * (2 * ds[i] + 18) * 2.0 ** -24)
             assert np.array_equal(tr["accepted"], rtr["accepted"])
             assert np.abs(b.get_phi(i) - rphi).max() < 1e-12
+
+
+def test_batched_workload_full_size_sampled_against_oracle():
+    """The bench's batched workload at full size (512 instances, d ~ U{2..16},
+    N ~ U{d+1..d^2}, K = 512, fp32, autotuned widths): one iteration, then for
+    a sample of instances the oracle scores all 512 candidates in binary64 and
+    the batch's choice must be a valid argmin (its binary32 score within 1e-6
+    of its binary64 mu, and no candidate better by more than 2e-6 in mu)."""
+    Ns, ds, seeds = W.batched_instances(512, seed=7)
+    K = 512
+    with T.Batch(Ns, ds, seeds, K=K, precision="fp32", trace_cap=4) as b:
+        phi0 = {i: b.get_phi(i) for i in range(0, 512, 37)}
+        b.step(1)
+        for i, phi in phi0.items():
+            ref = np.sqrt(O.score(phi, seeds[i], 0.1, 1, 0, K, nthreads=8))
+            row = b.trace(i)[0]
+            c = int(row["cstar"])
+            assert abs(np.sqrt(row["mu2_best"]) - ref[c]) < 1e-6, (i, Ns[i], ds[i])
+            assert ref[c] <= ref.min() + 2e-6, (i, Ns[i], ds[i])
