@@ -1016,13 +1016,10 @@ __device__ T score_resident(int N, int d, const void* phi, uint64_t seed, uint32
       const T* ri = sRe + (size_t)i * Np;
       const T* ii = sIm + (size_t)i * Np;
       T ar[4], ai[4], br[4], bi[4];
-#pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        ar[x] = ri[4 * a + x];
-        ai[x] = ii[4 * a + x];
-        br[x] = ri[4 * b + x];
-        bi[x] = ii[4 * b + x];
-      }
+      load_run<T, 4>(ri + 4 * a, ar);
+      load_run<T, 4>(ii + 4 * a, ai);
+      load_run<T, 4>(ri + 4 * b, br);
+      load_run<T, 4>(ii + 4 * b, bi);
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
