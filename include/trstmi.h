@@ -428,6 +428,25 @@ int trstmi_mu2_frame_noalloc(int N, int d, const double *phi_dev, double *mu2_de
 int trstmi_profile_score(trstmi_handle h, int precision, int launches, double delta,
                          size_t flush_bytes, double *avg_ms);
 
+/*
+ * Exercises the bounded device-side waits; the paper has no counterpart.
+ * Every wait inside the tensor-core screen (a consumer waiting for a column
+ * block, the MMA issuer waiting for a free accumulator, the epilogue waiting
+ * for a finished tile) gives up after a time limit instead of spinning
+ * forever, flags TRSTMI_ETIMEOUT and lets the other roles of the CTA leave,
+ * so a stalled launch ends and the CUDA context stays usable.  This call
+ * launches the screen of the given precision (TRSTMI_BF16_SCREEN,
+ * TRSTMI_FP16_SCREEN or TRSTMI_TF32_SCREEN) over min(K, 8) candidates of the
+ * instance with its block producers withheld, so the first wait can never
+ * complete, and with the limit shortened to wait_limit_ms (0 < limit <=
+ * 2000; the screen's normal limit is 2000 ms).  Blocks until the launch
+ * ends.  Returns TRSTMI_ETIMEOUT when the wait ran out as intended,
+ * TRSTMI_OK if it did not, TRSTMI_EUNSUPPORTED outside the screen's range
+ * and TRSTMI_EINVAL on bad arguments.  Uses only the instance's scoring
+ * scratch; the search state is unchanged.
+ */
+int trstmi_screen_wait_test(trstmi_handle h, int precision, double wait_limit_ms);
+
 #ifdef __cplusplus
 }
 #endif

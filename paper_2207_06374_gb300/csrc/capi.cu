@@ -757,14 +757,20 @@ int trstmi_score(trstmi_handle h, uint32_t t, uint32_t c0, int count, double del
         e = launch_gram_f32(h->N, h->d, count, src, (unsigned int*)tmp, nullptr, h->num_sms, s);
       } else {
         if (!screen_supported(h->N, h->d, screen_fmt_of(precision))) { rc = TRSTMI_EUNSUPPORTED; break; }
-        e = launch_screen(screen_fmt_of(precision), h->N, h->d, h->seed, h->phi32, count,
-                          c0, t, delta, nullptr, (unsigned int*)tmp, &h->misc[1], h->num_sms, s);
+        e = cudaMemsetAsync(&h->misc[1], 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess)
+          e = launch_screen(screen_fmt_of(precision), h->N, h->d, h->seed, h->phi32, count,
+                            c0, t, delta, nullptr, (unsigned int*)tmp, &h->misc[1], h->num_sms, s);
       }
       if (e != cudaSuccess) { rc = record_cuda_error(e, "score kernel launch", __LINE__); break; }
       std::vector<unsigned int> b(count);
+      uint32_t err = 0;
       if (cudaMemcpyAsync(b.data(), tmp, (size_t)count * sizeof(unsigned int),
                           cudaMemcpyDeviceToHost, s) ||
+          (precision != TRSTMI_FP32 &&
+           cudaMemcpyAsync(&err, &h->misc[1], sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) ||
           cudaStreamSynchronize(s)) { rc = TRSTMI_ECUDA; break; }
+      if (err & kErrTimeout) { rc = TRSTMI_ETIMEOUT; break; }
       for (int q = 0; q < count; ++q) {
         float f;
         std::memcpy(&f, &b[q], sizeof(float));
@@ -896,6 +902,23 @@ int trstmi_profile_score(trstmi_handle h, int precision, int launches, double de
   if (flush) cudaFree(flush);
   if (rc == TRSTMI_OK) *avg_ms = total / launches;
   return rc;
+}
+
+int trstmi_screen_wait_test(trstmi_handle h, int precision, double wait_limit_ms) {
+  if (!h || !is_screen_precision(precision)) return TRSTMI_EINVAL;
+  if (!(wait_limit_ms > 0.0 && wait_limit_ms <= 2000.0)) return TRSTMI_EINVAL;
+  if (!screen_supported(h->N, h->d, screen_fmt_of(precision))) return TRSTMI_EUNSUPPORTED;
+  TRY_CUDA(cudaSetDevice(h->opt.device));
+  cudaStream_t s = h->stream;
+  const int count = std::min(h->opt.K, 8);
+  TRY_CUDA(cudaMemsetAsync(&h->misc[1], 0, sizeof(uint32_t), s));
+  TRY_CUDA(launch_screen_wait_test(screen_fmt_of(precision), h->N, h->d, h->phi32, count,
+                                   h->mu2_k32, &h->misc[1],
+                                   (unsigned long long)(wait_limit_ms * 1e6), h->num_sms, s));
+  uint32_t err = 0;
+  TRY_CUDA(cudaMemcpyAsync(&err, &h->misc[1], sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  TRY_CUDA(cudaStreamSynchronize(s));
+  return (err & kErrTimeout) ? TRSTMI_ETIMEOUT : TRSTMI_OK;
 }
 
 }  // extern "C"

@@ -129,6 +129,15 @@ cudaError_t launch_screen(int fmt, int N, int d, uint64_t seed, const float2* ph
                           unsigned int* mu2_out, uint32_t* err_flag, int num_sms,
                           cudaStream_t s);
 
+// The screen over K candidates with its block producers withheld: no column
+// block is ever filled, so the MMA issuer's first wait runs out after
+// wait_limit_ns (at most the default bound), sets err_flag's timeout bit and
+// every role of each CTA leaves.  Exercises the bounded waits.
+cudaError_t launch_screen_wait_test(int fmt, int N, int d, const float2* phi32, int K,
+                                    unsigned int* mu2_out, uint32_t* err_flag,
+                                    unsigned long long wait_limit_ns, int num_sms,
+                                    cudaStream_t s);
+
 // ------------------------------------------------------ batched searches
 // One instance of a batch, as the batched kernels see it (device table).
 struct SlotDesc {

@@ -207,6 +207,69 @@ __device__ __forceinline__ void load_run(const T* p, T (&v)[R]) {
   }
 }
 
+// R x R complex accumulators of a micro-tile and one step i of their chains:
+//   Re += a_ij a_ik + b_ij b_ik,  Im += a_ij b_ik - b_ij a_ik,
+// each as two fused multiply-adds in that order, so every pair's value is a
+// fixed sequence of roundings whatever the micro-tile shape.
+template <typename T, int R, bool Packed = (sizeof(T) == 4 && R % 2 == 0)>
+struct MicroTile {
+  T re[R][R], im[R][R];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int x = 0; x < R; ++x)
+#pragma unroll
+      for (int y = 0; y < R; ++y) { re[x][y] = T(0); im[x][y] = T(0); }
+  }
+  __device__ __forceinline__ void step(const T (&ar)[R], const T (&ai)[R], const T (&br)[R],
+                                       const T (&bi)[R]) {
+#pragma unroll
+    for (int x = 0; x < R; ++x)
+#pragma unroll
+      for (int y = 0; y < R; ++y) {
+        re[x][y] = fma(ar[x], br[y], fma(ai[x], bi[y], re[x][y]));
+        im[x][y] = fma(ar[x], bi[y], fma(-ai[x], br[y], im[x][y]));
+      }
+  }
+  __device__ __forceinline__ T get_re(int x, int y) const { return re[x][y]; }
+  __device__ __forceinline__ T get_im(int x, int y) const { return im[x][y]; }
+};
+
+// binary32 with an even R: neighbouring columns y, y+1 in one packed pair,
+// updated by paired fused multiply-adds (each lane rounds exactly as the
+// scalar fma, so the values are the same bits) in half the instructions
+template <int R>
+struct MicroTile<float, R, true> {
+  float2 re[R][R / 2], im[R][R / 2];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int x = 0; x < R; ++x)
+#pragma unroll
+      for (int h = 0; h < R / 2; ++h) { re[x][h] = make_float2(0.f, 0.f); im[x][h] = re[x][h]; }
+  }
+  __device__ __forceinline__ void step(const float (&ar)[R], const float (&ai)[R],
+                                       const float (&br)[R], const float (&bi)[R]) {
+#pragma unroll
+    for (int x = 0; x < R; ++x) {
+      const float2 a = make_float2(ar[x], ar[x]);
+      const float2 b = make_float2(ai[x], ai[x]);
+      const float2 nb = make_float2(-ai[x], -ai[x]);
+#pragma unroll
+      for (int h = 0; h < R / 2; ++h) {
+        const float2 r = make_float2(br[2 * h], br[2 * h + 1]);
+        const float2 q = make_float2(bi[2 * h], bi[2 * h + 1]);
+        re[x][h] = __ffma2_rn(a, r, __ffma2_rn(b, q, re[x][h]));
+        im[x][h] = __ffma2_rn(a, q, __ffma2_rn(nb, r, im[x][h]));
+      }
+    }
+  }
+  __device__ __forceinline__ float get_re(int x, int y) const {
+    return (y & 1) ? re[x][y >> 1].y : re[x][y >> 1].x;
+  }
+  __device__ __forceinline__ float get_im(int x, int y) const {
+    return (y & 1) ? im[x][y >> 1].y : im[x][y >> 1].x;
+  }
+};
+
 // One work item of a Gram pass: tile (I <= J) of one frame, either the
 // candidate normalise(Phi + delta Z_{t,c}) or a stored frame.
 struct TileItem {
@@ -280,11 +343,8 @@ __device__ T score_tile(const TileItem& it, T* sm, int* zero_col, T thr,
   __syncthreads();
   const T* bRe = diag ? sIre : sJre;
   const T* bIm = diag ? sIim : sJim;
-  T accR[R][R], accI[R][R];
-#pragma unroll
-  for (int x = 0; x < R; ++x)
-#pragma unroll
-    for (int y = 0; y < R; ++y) { accR[x][y] = T(0); accI[x][y] = T(0); }
+  MicroTile<T, R> acc;
+  acc.zero();
   // thread (ty, tx) owns rows R ty .. R ty + R-1 and columns R tx .. R tx + R-1
   // of the tile: R consecutive values per plane, one vector load each
 #pragma unroll 2
@@ -294,13 +354,7 @@ __device__ T score_tile(const TileItem& it, T* sm, int* zero_col, T thr,
     load_run<T, R>(sIim + i * BT + R * ty, ai);
     load_run<T, R>(bRe + i * BT + R * tx, br);
     load_run<T, R>(bIm + i * BT + R * tx, bi);
-#pragma unroll
-    for (int x = 0; x < R; ++x)
-#pragma unroll
-      for (int y = 0; y < R; ++y) {
-        accR[x][y] = fma(ar[x], br[y], fma(ai[x], bi[y], accR[x][y]));
-        accI[x][y] = fma(ar[x], bi[y], fma(-ai[x], br[y], accI[x][y]));
-      }
+    acc.step(ar, ai, br, bi);
   }
   T m = T(0);
 #pragma unroll
@@ -308,7 +362,7 @@ __device__ T score_tile(const TileItem& it, T* sm, int* zero_col, T thr,
 #pragma unroll
     for (int y = 0; y < R; ++y) {
       const int gj = I * BT + R * ty + x, gk = J * BT + R * tx + y;
-      const T v = pair_abs2(accR[x][y], accI[x][y]);
+      const T v = pair_abs2(acc.get_re(x, y), acc.get_im(x, y));
       if (gj < gk && gk < N) {
         m = fmax(m, v);
         if (filter && v >= thr) {
@@ -1007,11 +1061,8 @@ __device__ T score_resident(int N, int d, const void* phi, uint64_t seed, uint32
   for (int w = threadIdx.x; w < nmt; w += blockDim.x) {
     int a, b;
     tile_coords(w, a, b);   // a <= b: rows 4a.., columns 4b..
-    T accR[4][4], accI[4][4];
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y) { accR[x][y] = T(0); accI[x][y] = T(0); }
+    MicroTile<T, 4> acc;
+    acc.zero();
     for (int i = 0; i < d; ++i) {
       const T* ri = sRe + (size_t)i * Np;
       const T* ii = sIm + (size_t)i * Np;
@@ -1020,20 +1071,14 @@ __device__ T score_resident(int N, int d, const void* phi, uint64_t seed, uint32
       load_run<T, 4>(ii + 4 * a, ai);
       load_run<T, 4>(ri + 4 * b, br);
       load_run<T, 4>(ii + 4 * b, bi);
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) {
-          accR[x][y] = fma(ar[x], br[y], fma(ai[x], bi[y], accR[x][y]));
-          accI[x][y] = fma(ar[x], bi[y], fma(-ai[x], br[y], accI[x][y]));
-        }
+      acc.step(ar, ai, br, bi);
     }
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) {
         const int j = 4 * a + x, k = 4 * b + y;
-        if (j < k && k < N) m = fmax(m, pair_abs2(accR[x][y], accI[x][y]));
+        if (j < k && k < N) m = fmax(m, pair_abs2(acc.get_re(x, y), acc.get_im(x, y)));
       }
   }
   return m;

@@ -64,7 +64,7 @@ static_assert(gen_index(1) == 0 && gen_index(15) == 5 && gen_index(19) == 8 &&
                   gen_index(12) == kGenWarps - 1 && gen_index(16) == -1 && gen_index(0) == -1,
               "roles");
 constexpr uint32_t kTmemCols = 512;                    // 2 buffers x (128 Re + 128 Im)
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // default bound of every wait
 #ifndef TRSTMI_MMA_BACKOFF_NS
 #define TRSTMI_MMA_BACKOFF_NS 20
 #endif
@@ -80,6 +80,8 @@ struct ScreenArgs {
   const DevState* st;
   unsigned int* out;
   uint32_t* err;
+  unsigned long long wait_limit_ns;   // bound of every mbarrier wait
+  int withhold_blocks;                // test of the bounded waits: generators fill nothing
 };
 
 struct SmemCtl {
@@ -90,6 +92,7 @@ struct SmemCtl {
   unsigned long long drain;
   uint32_t tmem_base;
   volatile int abort_flag;
+  unsigned long long wait_limit_ns;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -118,7 +121,7 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, uint32_t pa
 }
 
 // Bounded wait: false (and the CTA-wide abort flag and the error bit set) if
-// the phase does not complete within kWaitLimitNs or another role aborted.
+// the phase does not complete within ctl->wait_limit_ns or another role aborted.
 // Between unsuccessful polls the thread sleeps backoff_ns, so a waiting warp
 // leaves the issue slots to the working ones.
 __device__ bool mbar_wait(unsigned long long* b, uint32_t parity, SmemCtl* ctl, uint32_t* err,
@@ -130,7 +133,7 @@ __device__ bool mbar_wait(unsigned long long* b, uint32_t parity, SmemCtl* ctl, 
     if (mbar_try_wait(b, parity)) return true;
     if ((it & 7u) == 0u) {
       if (ctl->abort_flag) return false;
-      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      if (globaltimer_ns() - t0 > ctl->wait_limit_ns) {
         ctl->abort_flag = 1;
         if (err) atomicOr(err, (uint32_t)kErrTimeout);
         return false;
@@ -271,6 +274,8 @@ struct OneInstance {
     });
   }
   __device__ uint32_t* err() const { return a.err; }
+  __device__ unsigned long long wait_limit() const { return a.wait_limit_ns; }
+  __device__ bool withhold() const { return a.withhold_blocks != 0; }
 };
 
 // Work source: (instance, candidate) items of many instances; every instance
@@ -309,6 +314,8 @@ struct ManyInstances {
     });
   }
   __device__ uint32_t* err() const { return error; }
+  __device__ unsigned long long wait_limit() const { return kWaitLimitNs; }
+  __device__ bool withhold() const { return false; }
 };
 
 // Bounded wait by every lane of a warp; the warp acts on the unanimous result.
@@ -424,6 +431,7 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
     }
     mbar_init(&ctl.drain, 1);
     ctl.abort_flag = 0;
+    ctl.wait_limit_ns = src.wait_limit();
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == kMmaWarp) {
@@ -455,7 +463,8 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
     // fill barrier (kOctets arrivals complete a fill).
     const int q = lane >> 3;
     uint32_t gb0 = 0;
-    for (int idx = blockIdx.x; idx < nitems; idx += gridDim.x) {
+    const int gen_items = src.withhold() ? 0 : nitems;
+    for (int idx = blockIdx.x; idx < gen_items; idx += gridDim.x) {
       ScreenItem it;
       if (!src.item(idx, t0, delta0, it)) continue;
       const int d = it.d, P = (d + 1) >> 1;
@@ -780,6 +789,28 @@ cudaError_t launch_screen(int fmt, int N, int d, uint64_t seed, const float2* ph
   a.K = K; a.seed = seed; a.phi = phi32; a.c0 = c0; a.t = t; a.delta = (float)delta;
   a.keys = philox_round_keys(seed);
   a.st = st; a.out = mu2_out; a.err = err_flag;
+  a.wait_limit_ns = kWaitLimitNs;
+  a.withhold_blocks = 0;
+  return launch_any(fmt, src, std::min(K, num_sms), s);
+}
+
+cudaError_t launch_screen_wait_test(int fmt, int N, int d, const float2* phi32, int K,
+                                    unsigned int* mu2_out, uint32_t* err_flag,
+                                    unsigned long long wait_limit_ns, int num_sms,
+                                    cudaStream_t s) {
+  if (!screen_supported(N, d, fmt) || K < 1 || wait_limit_ns == 0 ||
+      wait_limit_ns > kWaitLimitNs)
+    return cudaErrorInvalidValue;
+  OneInstance src;
+  ScreenArgs& a = src.a;
+  a.N = N; a.d = d;
+  a.nb = (N + kBlockCols - 1) / kBlockCols;
+  a.ntiles = a.nb * (a.nb + 1) / 2;
+  a.K = K; a.seed = 0; a.phi = phi32; a.c0 = 0; a.t = 1; a.delta = 0.f;
+  a.keys = philox_round_keys(0);
+  a.st = nullptr; a.out = mu2_out; a.err = err_flag;
+  a.wait_limit_ns = wait_limit_ns;
+  a.withhold_blocks = 1;
   return launch_any(fmt, src, std::min(K, num_sms), s);
 }
 

@@ -125,6 +125,7 @@ SIGNATURES = {
     "trstmi_mu2_frame": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp]),
     "trstmi_profile_score": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_size_t, _dp]),
+    "trstmi_screen_wait_test": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "trstmi_mu2_frame_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
     "trstmi_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -317,6 +318,12 @@ class Search:
         _check(lib().trstmi_profile_score(self._h, p, launches, delta, flush_bytes,
                                           ctypes.byref(out)), "trstmi_profile_score")
         return out.value
+
+    def screen_wait_test(self, precision="bf16", wait_limit_ms=20.0) -> int:
+        """Status of a screen launch whose block producers are withheld, so its
+        bounded wait runs out after wait_limit_ms (TRSTMI_ETIMEOUT expected)."""
+        p = PRECISIONS[precision] if isinstance(precision, str) else precision
+        return lib().trstmi_screen_wait_test(self._h, p, wait_limit_ms)
 
     @property
     def handle(self) -> int:
