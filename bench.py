@@ -412,7 +412,7 @@ def main():
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
                  "traffic": profiled_traffic(prec),
                  "kernel": (f"k_screen ({prec})" if prec in ("bf16", "tf32") else
-                            "k_gen_planes_f32 + k_gram_tile (one fp32 scoring pass)" if prec == "fp32"
+                            "k_gen_planes_f32 + k_gram_planes (one fp32 scoring pass)" if prec == "fp32"
                             else "k_gram_tile"),
                  "kernel_ms": kernel_ms, "flops_per_launch": flops_launch, "peak_source": peak_note})
 

@@ -282,15 +282,61 @@ struct TileItem {
   const void* planes = nullptr;   // candidate drawn already: [i][column] re, then im planes
 };
 
+// The reduction of tile (I, J) of width BT = 16 R once its column blocks are
+// in shared memory: sI holds block I as [i][column] planes (d x BT real
+// parts, then d x BT imaginary parts) and sJ block J in the same layout
+// (sJ == sI on a diagonal tile).  Thread (ty, tx) of the 16 x 16 CTA owns
+// rows R ty .. R ty + R-1 and columns R tx .. R tx + R-1 of the tile and
+// reads R consecutive values per plane in one vector load each.  Returns the
+// thread's max of |G_jk|^2 over its pairs j < k < N and appends the pairs at
+// or above thr when filter != nullptr.
+template <typename T, int R>
+__device__ __forceinline__ T tile_pairs_max(const T* sIre, const T* sIim, const T* sJ, int d,
+                                            int N, int I, int J, T thr,
+                                            const PairFilter* filter) {
+  constexpr int BT = 16 * R;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const T* bRe = sJ;
+  const T* bIm = sJ + (size_t)d * BT;
+  MicroTile<T, R> acc;
+  acc.zero();
+#pragma unroll 2
+  for (int i = 0; i < d; ++i) {
+    T ar[R], ai[R], br[R], bi[R];
+    load_run<T, R>(sIre + i * BT + R * ty, ar);
+    load_run<T, R>(sIim + i * BT + R * ty, ai);
+    load_run<T, R>(bRe + i * BT + R * tx, br);
+    load_run<T, R>(bIm + i * BT + R * tx, bi);
+    acc.step(ar, ai, br, bi);
+  }
+  T m = T(0);
+#pragma unroll
+  for (int x = 0; x < R; ++x)
+#pragma unroll
+    for (int y = 0; y < R; ++y) {
+      const int gj = I * BT + R * ty + x, gk = J * BT + R * tx + y;
+      const T v = pair_abs2(acc.get_re(x, y), acc.get_im(x, y));
+      if (gj < gk && gk < N) {
+        m = fmax(m, v);
+        if (filter && v >= thr) {
+          const uint32_t idx = atomicAdd(filter->npairs, 1u);
+          if (idx < filter->cap) filter->pairs[idx] = make_uint2((unsigned)gj, (unsigned)gk);
+          else atomicExch(filter->overflow, 1u);
+        }
+      }
+    }
+  return m;
+}
+
 // The CTA (256 threads, 16 x 16) scores tile (I, J) of width BT = 16 R.
 // Column blocks I and J are generated (or loaded) into shared memory as
 // [i][column] planes of real and imaginary parts; each thread accumulates an
 // R x R micro-tile of
 //   Re G_jk = sum_i a_ij a_ik + b_ij b_ik,  Im G_jk = sum_i a_ij b_ik - b_ij a_ik
-// as a sequential chain over i, so a pair's |G_jk|^2 does not depend on the
-// tile shape.  Returns this thread's max over its pairs j < k < N (and
-// appends the pairs at or above thr when filter != nullptr).  Begins and
-// ends with a CTA barrier; *zero_col is set if a column had zero norm.
+// as a sequential chain over i (tile_pairs_max), so a pair's |G_jk|^2 does
+// not depend on the tile shape.  Returns this thread's max over its pairs
+// j < k < N (and appends the pairs at or above thr when filter != nullptr).
+// Begins with a CTA barrier; *zero_col is set if a column had zero norm.
 template <typename T, int R>
 __device__ T score_tile(const TileItem& it, T* sm, int* zero_col, T thr,
                         const PairFilter* filter) {
@@ -301,7 +347,6 @@ __device__ T score_tile(const TileItem& it, T* sm, int* zero_col, T thr,
   T* sIim = sm + (size_t)d * BT;
   T* sJre = sm + (size_t)2 * d * BT;
   T* sJim = sm + (size_t)3 * d * BT;
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   const bool diag = (I == J);
   __syncthreads();
   const int ncols = diag ? BT : 2 * BT;
@@ -341,38 +386,7 @@ __device__ T score_tile(const TileItem& it, T* sm, int* zero_col, T thr,
     if (!ok) *zero_col = 1;
   }
   __syncthreads();
-  const T* bRe = diag ? sIre : sJre;
-  const T* bIm = diag ? sIim : sJim;
-  MicroTile<T, R> acc;
-  acc.zero();
-  // thread (ty, tx) owns rows R ty .. R ty + R-1 and columns R tx .. R tx + R-1
-  // of the tile: R consecutive values per plane, one vector load each
-#pragma unroll 2
-  for (int i = 0; i < d; ++i) {
-    T ar[R], ai[R], br[R], bi[R];
-    load_run<T, R>(sIre + i * BT + R * ty, ar);
-    load_run<T, R>(sIim + i * BT + R * ty, ai);
-    load_run<T, R>(bRe + i * BT + R * tx, br);
-    load_run<T, R>(bIm + i * BT + R * tx, bi);
-    acc.step(ar, ai, br, bi);
-  }
-  T m = T(0);
-#pragma unroll
-  for (int x = 0; x < R; ++x)
-#pragma unroll
-    for (int y = 0; y < R; ++y) {
-      const int gj = I * BT + R * ty + x, gk = J * BT + R * tx + y;
-      const T v = pair_abs2(acc.get_re(x, y), acc.get_im(x, y));
-      if (gj < gk && gk < N) {
-        m = fmax(m, v);
-        if (filter && v >= thr) {
-          const uint32_t idx = atomicAdd(filter->npairs, 1u);
-          if (idx < filter->cap) filter->pairs[idx] = make_uint2((unsigned)gj, (unsigned)gk);
-          else atomicExch(filter->overflow, 1u);
-        }
-      }
-    }
-  return m;
+  return tile_pairs_max<T, R>(sIre, sIim, diag ? sIre : sJre, d, N, I, J, thr, filter);
 }
 
 // Gram pass over nslots frames (candidates of one instance, or stored
@@ -436,6 +450,116 @@ __global__ void __launch_bounds__(256, TileCtas<T>::value) k_gram_tile(const Gra
   }
 }
 
+// ------------------------------------------- binary32 pass over drawn planes
+// The tile pass when the iteration's candidates are already drawn (planes,
+// [i][column] real then imaginary, 2 d N floats per candidate): the column
+// blocks of the CTA's next work item are copied into a second shared-memory
+// stage with asynchronous copies while the current item is reduced, so the
+// copy latency hides behind the arithmetic of the same CTA.  The reduction is
+// tile_pairs_max, the scores the same bits as k_gram_tile's.
+
+__device__ __forceinline__ uint32_t shared_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// 4 bytes (or zeros when !valid); src must be a valid address either way
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(shared_addr(dst)), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+// 16 bytes, both addresses 16-byte aligned (or zeros when !valid)
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(shared_addr(dst)),
+               "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int Pending> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(Pending) : "memory");
+}
+
+// Issues the copies of work item w's column blocks into stage dst (block I,
+// then block J unless the tile is diagonal; each d x BT real, d x BT
+// imaginary).  vec: N % 4 == 0 and a 16-byte aligned planes array, so every
+// run of 4 columns is one aligned 16-byte copy.
+template <int R>
+__device__ __forceinline__ void prefetch_planes(const GramArgs<float>& a, long long w, float* dst,
+                                                bool vec) {
+  constexpr int BT = 16 * R;
+  const int d = a.d, N = a.N;
+  const int slot = (int)(w / a.ntiles);
+  int I, J;
+  tile_coords((int)(w - (long long)slot * a.ntiles), I, J);
+  const float* pre = reinterpret_cast<const float*>(a.src.planes) + (size_t)slot * 2 * d * N;
+  const float* pim = pre + (size_t)d * N;
+  for (int blk = 0; blk < (I == J ? 1 : 2); ++blk) {
+    const int c0 = (blk == 0 ? I : J) * BT;
+    float* ore = dst + (size_t)blk * 2 * d * BT;
+    float* oim = ore + (size_t)d * BT;
+    if (vec) {
+      for (int q = threadIdx.x; q < d * (BT / 4); q += blockDim.x) {
+        const int i = q / (BT / 4), c4 = q % (BT / 4);
+        const int gj = c0 + 4 * c4;
+        const bool ok = gj < N;
+        const size_t g = ok ? (size_t)i * N + gj : 0;
+        cp_async16(ore + i * BT + 4 * c4, pre + g, ok);
+        cp_async16(oim + i * BT + 4 * c4, pim + g, ok);
+      }
+    } else {
+      for (int q = threadIdx.x; q < d * BT; q += blockDim.x) {
+        const int i = q / BT, loc = q % BT;
+        const int gj = c0 + loc;
+        const bool ok = gj < N;
+        const size_t g = ok ? (size_t)i * N + gj : 0;
+        cp_async4(ore + q, pre + g, ok);
+        cp_async4(oim + q, pim + g, ok);
+      }
+    }
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256, 3) k_gram_planes(const GramArgs<float> a, int vec) {
+  constexpr int BT = 16 * R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float red[8];
+  float* const stage0 = reinterpret_cast<float*>(smem_raw);
+  const size_t stage_floats = (size_t)4 * a.d * BT;
+  const GramSource& src = a.src;
+  if (src.gate && *src.gate == 0u) return;
+  if (src.st && !src.st->active) return;
+  float thr = -1.f;
+  if (a.has_filter) {
+    const float ref = sqrtf(__uint_as_float(*a.filter.mu2_ref));
+    const float lo = fmaxf(ref - a.filter.margin, 0.0f);
+    thr = lo * lo;
+  }
+  const long long nitems = (long long)a.nslots * a.ntiles;
+  long long w = blockIdx.x;
+  if (w < nitems) prefetch_planes<R>(a, w, stage0, vec != 0);
+  cp_async_commit();
+  for (int sg = 0; w < nitems; w += gridDim.x, sg ^= 1) {
+    const long long wn = w + gridDim.x;
+    if (wn < nitems) prefetch_planes<R>(a, wn, stage0 + (sg ^ 1) * stage_floats, vec != 0);
+    cp_async_commit();
+    cp_async_wait<1>();   // this thread's copies of item w have landed ...
+    __syncthreads();      // ... and every other thread's
+    const int slot = (int)(w / a.ntiles);
+    int I, J;
+    tile_coords((int)(w - (long long)slot * a.ntiles), I, J);
+    const float* sI = stage0 + sg * stage_floats;
+    const float* sJ = I == J ? sI : sI + (size_t)2 * a.d * BT;
+    float m = tile_pairs_max<float, R>(sI, sI + (size_t)a.d * BT, sJ, a.d, a.N, I, J, thr,
+                                       a.has_filter ? &a.filter : nullptr);
+    m = block_max<float>(m, red);
+    if (threadIdx.x == 0) atomic_max_nonneg(a.out + slot, m);
+    __syncthreads();      // stage sg is free for the copies issued next round
+  }
+  cp_async_wait<0>();
+}
+
 // Candidates drawn once for the tile pass (see launch_gen_planes_f32).
 __global__ void k_gen_planes_f32(int N, int d, int count, const float2* phi, uint64_t seed,
                                  uint32_t c0, DevState* st, uint32_t t, float delta,
@@ -465,6 +589,9 @@ cudaError_t launch_gen_planes_f32(int N, int d, int count, const float2* phi, ui
   return cudaGetLastError();
 }
 
+// shared memory of the double-buffered binary32 pass (two stages)
+constexpr size_t kPlanesSmemMax = 200 * 1024;
+
 template <typename T> static size_t gram_smem(int d, int R) {
   return (size_t)4 * d * 16 * R * sizeof(T);
 }
@@ -492,6 +619,24 @@ static cudaError_t launch_gram(int N, int d, int nslots, const GramSource& src,
   const size_t smem = gram_smem<T>(d, R);
   const long long items = (long long)nslots * a.ntiles;
   int per_sm = 1;
+  if constexpr (sizeof(T) == 4) {
+    // candidates already drawn: the double-buffered pass when two stages fit
+    if (src.planes && 2 * smem <= kPlanesSmemMax) {
+      const int vec = (N % 4 == 0 && reinterpret_cast<uintptr_t>(src.planes) % 16 == 0) ? 1 : 0;
+      cudaError_t oe = R == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_planes<4>, 256, 2 * smem)
+                     : R == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_planes<2>, 256, 2 * smem)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_planes<1>, 256, 2 * smem);
+      if (oe != cudaSuccess) return oe;
+      per_sm = std::max(per_sm, 1);
+      const int grid = (int)std::min<long long>(items, (long long)num_sms * per_sm);
+      switch (R) {
+        case 4: k_gram_planes<4><<<grid, 256, 2 * smem, s>>>(a, vec); break;
+        case 2: k_gram_planes<2><<<grid, 256, 2 * smem, s>>>(a, vec); break;
+        default: k_gram_planes<1><<<grid, 256, 2 * smem, s>>>(a, vec); break;
+      }
+      return cudaGetLastError();
+    }
+  }
   cudaError_t oe = R == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_tile<T, 4>, 256, smem)
                  : R == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_tile<T, 2>, 256, smem)
                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_tile<T, 1>, 256, smem);
@@ -1443,6 +1588,9 @@ cudaError_t init_kernel_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_gram_planes<4>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_gram_planes<2>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_gram_planes<1>, optin)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_gram_tile<float, 4>, optin)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_gram_tile<float, 2>, optin)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_gram_tile<float, 1>, optin)) != cudaSuccess) return e;
