@@ -91,8 +91,10 @@ def lib():
             L.oracle_replay.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                         ctypes.POINTER(OracleOpts), _dp, _dp, _dp,
                                         ctypes.c_uint32, ctypes.c_int, _u32p, ctypes.c_void_p]
+            L.oracle_lse.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, _dp, _dp,
+                                     _dp]
             for f in ("oracle_init", "oracle_candidate", "oracle_score", "oracle_search",
-                      "oracle_run", "oracle_replay"):
+                      "oracle_run", "oracle_replay", "oracle_lse"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -213,3 +215,16 @@ def replay(phi: np.ndarray, seed: int, opts: OracleOpts, delta: float, mu2_cur: 
                                ctypes.byref(m2), t0, len(cs),
                                cs.ctypes.data_as(_u32p), tr.ctypes.data), "replay")
     return _unflat(b, d, N), m2.value, dl.value, tr[: len(cs)]
+
+
+def lse(v: np.ndarray, delta: float, grad: bool = True):
+    """Smooth maximum F_{s,delta} of |G_jk|^2 (j < k) of the column-normalised
+    frame of V (d, N), its s = max |G_jk|^2, and the real gradient in V as a
+    complex (d, N) array (dF/dRe V + i dF/dIm V), or None."""
+    d, N = v.shape
+    b = _flat(v)
+    Fv, sv = ctypes.c_double(), ctypes.c_double()
+    g = np.zeros_like(b) if grad else None
+    _check(lib().oracle_lse(N, d, _ptr(b), delta, ctypes.byref(Fv), ctypes.byref(sv),
+                            _ptr(g) if grad else None), "lse")
+    return Fv.value, sv.value, (_unflat(g, d, N) if grad else None)

@@ -362,3 +362,108 @@ int oracle_replay(int N, int d, uint64_t seed, const oracle_opts *o,
     free(cand);
     return st;
 }
+
+/* ------------------------------------------- smooth maximum (log-sum-exp) */
+
+/*
+ * The paper's objective (Sec. "Optimization procedure"): the smooth maximum
+ *   F_{s,delta}(x) = s + delta * log sum_{i=1}^{n} exp((x_i - s) / delta),
+ *   s = max_i x_i,  delta > 0,
+ * taken over x = the values |G_jk|^2, j < k, of the frame obtained by
+ * dividing each column of the variable V (d x N, complex) by its norm, so
+ * n = N(N-1)/2 (Remark on n; Remark on the unconstrained variable).  The
+ * Proposition bounds it: s <= F <= s + delta log n.
+ *
+ * Gradient.  The shift by s cancels (F = delta log sum exp(x_i / delta)
+ * identically), so dF/dx_i = w_i = exp((x_i - s)/delta) / sum_l exp((x_l -
+ * s)/delta), the softmax weights; the subgradient of the max named in the
+ * Remark on the shift contributes (1 - sum_i w_i) = 0 at the argmax.  With
+ * phi_k = v_k / r_k (r_k = |v_k|) and G the Hermitian Gram matrix of Phi,
+ *   x_jk = G_jk conj(G_jk),  d x_jk / d conj(phi_k) = G_jk phi_j,
+ *   d x_jk / d conj(phi_j) = conj(G_jk) phi_k,
+ * so the real gradient in Phi, written as a complex array (dF/dRe + i
+ * dF/dIm = 2 dF/d conj), is
+ *   g_k = 2 sum_{j != k} w_jk G_jk phi_j          (w symmetric, G Hermitian)
+ * and through the normalisation (d phi = (dv - phi Re(phi^* dv)) / r)
+ *   grad_k = (g_k - phi_k Re(phi_k^* g_k)) / r_k.
+ * Frames use the layout of the rest of this file.  grad (2dN doubles) may be
+ * NULL.  Returns ORACLE_EINVAL for N < 2, d < 1, delta <= 0 or a zero column.
+ */
+int oracle_lse(int N, int d, const double *v, double delta, double *F, double *s_out,
+               double *grad)
+{
+    if (N < 2 || d < 1 || !v || !F || !(delta > 0.0)) return ORACLE_EINVAL;
+    size_t m = 2 * (size_t)d * (size_t)N;
+    size_t n = (size_t)N * (size_t)(N - 1) / 2;
+    double *phi = (double *)malloc(sizeof(double) * m);
+    double *r = (double *)malloc(sizeof(double) * (size_t)N);
+    double *x = (double *)malloc(sizeof(double) * n);
+    int st = ORACLE_OK;
+    if (!phi || !r || !x) { st = ORACLE_EINVAL; goto out; }
+    memcpy(phi, v, sizeof(double) * m);
+    for (int j = 0; j < N; ++j) {
+        double q = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double a = v[2 * (j * d + i)], b = v[2 * (j * d + i) + 1];
+            q += a * a + b * b;
+        }
+        r[j] = sqrt(q);
+    }
+    st = normalise_columns(N, d, phi);
+    if (st != ORACLE_OK) goto out;
+
+    /* x over the pairs j < k in row order, its max s and the shifted sum */
+    size_t p = 0;
+    double s = 0.0;
+    for (int j = 0; j < N; ++j)
+        for (int k = j + 1; k < N; ++k, ++p) {
+            x[p] = oracle_gram_abs2(d, phi, j, k);
+            if (p == 0 || x[p] > s) s = x[p];
+        }
+    double S = 0.0;
+    for (p = 0; p < n; ++p) S += exp((x[p] - s) / delta);
+    *F = s + delta * log(S);
+    if (s_out) *s_out = s;
+
+    if (grad) {
+        double *g = grad;
+        memset(g, 0, sizeof(double) * m);
+        p = 0;
+        for (int j = 0; j < N; ++j)
+            for (int k = j + 1; k < N; ++k, ++p) {
+                double w = exp((x[p] - s) / delta) / S;
+                double gr = 0.0, gi = 0.0;   /* G_jk = sum_i conj(phi_ij) phi_ik */
+                for (int i = 0; i < d; ++i) {
+                    double a = phi[2 * (j * d + i)], b = phi[2 * (j * d + i) + 1];
+                    double c = phi[2 * (k * d + i)], e = phi[2 * (k * d + i) + 1];
+                    gr += a * c + b * e;
+                    gi += a * e - b * c;
+                }
+                for (int i = 0; i < d; ++i) {
+                    double a = phi[2 * (j * d + i)], b = phi[2 * (j * d + i) + 1];
+                    double c = phi[2 * (k * d + i)], e = phi[2 * (k * d + i) + 1];
+                    /* g_k += 2 w G_jk phi_j;  g_j += 2 w conj(G_jk) phi_k */
+                    g[2 * (k * d + i)] += 2.0 * w * (gr * a - gi * b);
+                    g[2 * (k * d + i) + 1] += 2.0 * w * (gr * b + gi * a);
+                    g[2 * (j * d + i)] += 2.0 * w * (gr * c + gi * e);
+                    g[2 * (j * d + i) + 1] += 2.0 * w * (gr * e - gi * c);
+                }
+            }
+        for (int k = 0; k < N; ++k) {
+            double rad = 0.0;   /* Re(phi_k^* g_k) */
+            for (int i = 0; i < d; ++i)
+                rad += phi[2 * (k * d + i)] * g[2 * (k * d + i)] +
+                       phi[2 * (k * d + i) + 1] * g[2 * (k * d + i) + 1];
+            for (int i = 0; i < d; ++i) {
+                g[2 * (k * d + i)] = (g[2 * (k * d + i)] - phi[2 * (k * d + i)] * rad) / r[k];
+                g[2 * (k * d + i) + 1] =
+                    (g[2 * (k * d + i) + 1] - phi[2 * (k * d + i) + 1] * rad) / r[k];
+            }
+        }
+    }
+out:
+    free(phi);
+    free(r);
+    free(x);
+    return st;
+}
