@@ -413,6 +413,52 @@ int trstmi_mu2_frame(int N, int d, const double *phi, int precision, double *mu2
 int trstmi_mu2_frame_noalloc(int N, int d, const double *phi_dev, double *mu2_dev,
                              void *stream);
 
+/* ------------------------------------------- the paper's smooth maximum */
+
+/*
+ * The objective of the paper's optimisation procedure (Sec. "Optimization
+ * procedure"): the shifted log-sum-exp
+ *   F_{s,delta}(x) = s + delta * log sum_{j<k} exp((x_jk - s) / delta),
+ *   x_jk = |G_jk|^2,  s = max_{j<k} x_jk,
+ * of the Gram matrix G of the frame obtained by dividing each column of a
+ * variable V (d x N complex) by its norm, and the real gradient of F in V.
+ * By the paper's Proposition, s <= F <= s + delta log(N(N-1)/2).
+ *
+ * The gradient is returned as a complex array in the frame layout:
+ * grad_ij = dF/dRe V_ij + i dF/dIm V_ij.  (The shift by s cancels
+ * algebraically, so dF/dx_jk are the softmax weights of x / delta.)
+ *
+ * count frames of the same shape are evaluated together; frame q of v is
+ * the 2*d*N doubles at v + 2*d*N*q.  precision: TRSTMI_FP64 (binary64
+ * throughout) or TRSTMI_FP32 (the variable rounded to binary32, Gram,
+ * weights and block products in binary32; the sums over tiles, S, F and the
+ * gradient's final assembly in binary64).  Requires N >= 2, 1 <= d <= 256,
+ * count >= 1, 0 < delta < inf, count*N*d < 2^31; a zero column makes that
+ * frame's results NaN (TRSTMI_EINVAL from trstmi_lse_frames).  The results
+ * do not depend on the order in which the device runs its tiles.
+ */
+
+/* Host buffers (v: count*2*d*N doubles; F, s (nullable): count doubles;
+ * grad (nullable): count*2*d*N doubles).  Device 0, default stream;
+ * allocates and frees its device memory, blocks until done. */
+int trstmi_lse_frames(int N, int d, int count, const double *v, double delta, int precision,
+                      double *F, double *s, double *grad);
+
+/* Bytes of device scratch that trstmi_lse_frames_device needs. */
+int trstmi_lse_scratch_bytes(int N, int d, int count, int precision, size_t *bytes);
+
+/*
+ * Allocation-free form on device buffers of the current device: v_dev
+ * (count*2*d*N doubles), scratch_dev (256-byte aligned, at least
+ * trstmi_lse_scratch_bytes), out_dev (count x [F, s] doubles), grad_dev
+ * (count*2*d*N doubles, or NULL for the value alone).  Only enqueues work on
+ * `stream` (NULL = legacy default stream); the results are ready when the
+ * stream is.  Calls sharing one scratch array must not overlap.
+ */
+int trstmi_lse_frames_device(int N, int d, int count, const double *v_dev, double delta,
+                             int precision, void *scratch_dev, size_t scratch_bytes,
+                             double *out_dev, double *grad_dev, void *stream);
+
 /* ------------------------------------------------- measurement entry point */
 
 /*

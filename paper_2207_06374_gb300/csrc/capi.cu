@@ -904,6 +904,76 @@ int trstmi_profile_score(trstmi_handle h, int precision, int launches, double de
   return rc;
 }
 
+namespace {
+int lse_check(int N, int d, int count, double delta, int precision) {
+  if (N < 2 || d < 1 || d > kMaxD || count < 1) return TRSTMI_EINVAL;
+  if (!(delta > 0.0) || !(delta < INFINITY)) return TRSTMI_EINVAL;
+  if (precision != TRSTMI_FP64 && precision != TRSTMI_FP32) return TRSTMI_EINVAL;
+  if ((long long)count * N * d >= (1ll << 31)) return TRSTMI_ESIZE;
+  return TRSTMI_OK;
+}
+}  // namespace
+
+int trstmi_lse_scratch_bytes(int N, int d, int count, int precision, size_t* bytes) {
+  if (!bytes) return TRSTMI_EINVAL;
+  const int rc = lse_check(N, d, count, 1.0, precision);
+  if (rc) return rc;
+  *bytes = lse_scratch_bytes(N, d, count, precision == TRSTMI_FP64);
+  return TRSTMI_OK;
+}
+
+int trstmi_lse_frames_device(int N, int d, int count, const double* v_dev, double delta,
+                             int precision, void* scratch_dev, size_t scratch_bytes,
+                             double* out_dev, double* grad_dev, void* stream) {
+  int rc = lse_check(N, d, count, delta, precision);
+  if (rc) return rc;
+  if (!v_dev || !scratch_dev || !out_dev) return TRSTMI_EINVAL;
+  if (scratch_bytes < lse_scratch_bytes(N, d, count, precision == TRSTMI_FP64))
+    return TRSTMI_EINVAL;
+  if (reinterpret_cast<uintptr_t>(scratch_dev) % 256 != 0) return TRSTMI_EINVAL;
+  int dev = 0, num_sms = 0;
+  TRY_CUDA(cudaGetDevice(&dev));
+  if ((rc = ensure_device(dev, &num_sms)) != TRSTMI_OK) return rc;
+  TRY_CUDA(launch_lse(N, d, count, v_dev, delta, precision == TRSTMI_FP64, scratch_dev, out_dev,
+                      grad_dev, num_sms, static_cast<cudaStream_t>(stream)));
+  return TRSTMI_OK;
+}
+
+int trstmi_lse_frames(int N, int d, int count, const double* v, double delta, int precision,
+                      double* F, double* s, double* grad) {
+  int rc = lse_check(N, d, count, delta, precision);
+  if (rc) return rc;
+  if (!v || !F) return TRSTMI_EINVAL;
+  int num_sms = 0;
+  if ((rc = ensure_device(0, &num_sms)) != TRSTMI_OK) return rc;
+  const size_t nv = (size_t)count * N * d * sizeof(double2);
+  const size_t nscratch = lse_scratch_bytes(N, d, count, precision == TRSTMI_FP64);
+  const size_t o_out = align_up(nv, 256), o_grad = align_up(o_out + 2 * sizeof(double) * count, 256);
+  const size_t o_scr = align_up(o_grad + (grad ? nv : 0), 256);
+  void* buf = nullptr;
+  TRY_CUDA(cudaMalloc(&buf, o_scr + nscratch));
+  char* b = static_cast<char*>(buf);
+  std::vector<double> out(2 * (size_t)count);
+  do {
+    cudaError_t e = cudaMemcpy(b, v, nv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = launch_lse(N, d, count, reinterpret_cast<const double*>(b), delta,
+                     precision == TRSTMI_FP64, b + o_scr, reinterpret_cast<double*>(b + o_out),
+                     grad ? reinterpret_cast<double*>(b + o_grad) : nullptr, num_sms, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(out.data(), b + o_out, out.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && grad) e = cudaMemcpy(grad, b + o_grad, nv, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { rc = record_cuda_error(e, "smooth maximum", __LINE__); break; }
+    for (int q = 0; q < count; ++q) {
+      if (std::isnan(out[2 * q])) { rc = TRSTMI_EINVAL; break; }   // a zero column
+      F[q] = out[2 * q];
+      if (s) s[q] = out[2 * q + 1];
+    }
+  } while (0);
+  cudaFree(buf);
+  return rc;
+}
+
 int trstmi_screen_wait_test(trstmi_handle h, int precision, double wait_limit_ms) {
   if (!h || !is_screen_precision(precision)) return TRSTMI_EINVAL;
   if (!(wait_limit_ms > 0.0 && wait_limit_ms <= 2000.0)) return TRSTMI_EINVAL;

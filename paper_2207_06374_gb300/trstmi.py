@@ -125,6 +125,15 @@ SIGNATURES = {
     "trstmi_mu2_frame": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp]),
     "trstmi_profile_score": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_size_t, _dp]),
+    "trstmi_lse_frames": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
+                                         ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]),
+    "trstmi_lse_scratch_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "trstmi_lse_frames_device": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                                ctypes.c_void_p, ctypes.c_size_t,
+                                                ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p]),
     "trstmi_screen_wait_test": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "trstmi_mu2_frame_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
@@ -478,6 +487,50 @@ class Server:
         s = ServerStats()
         _check(lib().trstmi_server_stats(self._h, ctypes.byref(s)), "trstmi_server_stats")
         return s
+
+
+def lse(v: np.ndarray, delta: float, precision="fp64", grad: bool = True):
+    """The paper's smooth maximum F_{s,delta} of |G_jk|^2 (j < k) of the
+    column-normalised frame of V, s = max |G_jk|^2, and the real gradient in
+    V (dF/dRe V + i dF/dIm V).  v: (d, N) or a stack (count, d, N) of complex
+    frames; returns (F, s, grad) as scalars and a (d, N) array, or arrays."""
+    v = np.asarray(v, dtype=np.complex128)
+    single = v.ndim == 2
+    if single:
+        v = v[None]
+    count, d, N = v.shape
+    p = PRECISIONS[precision] if isinstance(precision, str) else precision
+    b = np.ascontiguousarray(np.transpose(v, (0, 2, 1))).view(np.float64).reshape(-1).copy()
+    F = np.zeros(count)
+    s = np.zeros(count)
+    g = np.zeros_like(b) if grad else None
+    _check(lib().trstmi_lse_frames(N, d, count, b.ctypes.data_as(_dp), delta, p,
+                                   F.ctypes.data_as(_dp), s.ctypes.data_as(_dp),
+                                   g.ctypes.data_as(_dp) if grad else None), "trstmi_lse_frames")
+    G = None
+    if grad:
+        G = g.view(np.complex128).reshape(count, N, d).transpose(0, 2, 1).copy()
+    if single:
+        return float(F[0]), float(s[0]), (G[0] if grad else None)
+    return F, s, G
+
+
+def lse_scratch_bytes(N: int, d: int, count: int, precision="fp32") -> int:
+    p = PRECISIONS[precision] if isinstance(precision, str) else precision
+    out = ctypes.c_size_t()
+    _check(lib().trstmi_lse_scratch_bytes(N, d, count, p, ctypes.byref(out)),
+           "trstmi_lse_scratch_bytes")
+    return out.value
+
+
+def lse_device(N: int, d: int, count: int, v_ptr: int, delta: float, precision, scratch_ptr: int,
+               scratch_bytes: int, out_ptr: int, grad_ptr: int = 0, stream: int = 0) -> None:
+    """Allocation-free smooth maximum on device buffers (raw pointers); only
+    enqueues on `stream`."""
+    p = PRECISIONS[precision] if isinstance(precision, str) else precision
+    _check(lib().trstmi_lse_frames_device(N, d, count, v_ptr, delta, p, scratch_ptr,
+                                          scratch_bytes, out_ptr, grad_ptr or None,
+                                          stream or None), "trstmi_lse_frames_device")
 
 
 def mu2_frame(phi: np.ndarray, precision="fp64") -> float:
