@@ -49,7 +49,12 @@ WORKLOADS = {
     "serving": (None, None, 8, "bf16", "Poisson request stream through the serving loop"),
     "plain_d2_n4_fp64": (2, 4, 256, "fp64",
                          "complex d=2 N=4, 256 candidates/iteration, fp64"),
+    # K = frames per call of the smooth-maximum objective
+    "objective_d32_n1024": (32, 1024, 64, "fp32",
+                            "the paper's smooth maximum F_{s,delta} (delta = 0.01) and its "
+                            "gradient for 64 frames, complex d=32 N=1024, fp32"),
 }
+LSE_DELTA = 0.01
 L2_FLUSH_BYTES = 512 << 20
 SEED = 1
 
@@ -150,11 +155,14 @@ KERNEL_SOURCES = {
     "fp32": ["paper_2207_06374_gb300/csrc/simt_kernels.cu", "paper_2207_06374_gb300/csrc/philox.cuh",
              "paper_2207_06374_gb300/csrc/common.cuh"],
 }
+KERNEL_SOURCES["lse"] = ["paper_2207_06374_gb300/csrc/lse.cu", "paper_2207_06374_gb300/csrc/tile.cuh",
+                         "paper_2207_06374_gb300/csrc/common.cuh"]
 KERNEL_SOURCES["tf32"] = KERNEL_SOURCES["bf16"]
 KERNEL_SOURCES["batched"] = KERNEL_SOURCES["fp32"]
 KERNEL_PROFILE = {"bf16": "k_screen_bf16_d32_n1024.txt", "tf32": "k_screen_tf32_d32_n768.txt",
                   "fp32": "k_gram_tile_f32_d32_n1024.txt",
-                  "batched": "k_batch_resident_f32_batched_512.txt"}
+                  "batched": "k_batch_resident_f32_batched_512.txt",
+                  "lse": "k_lse_tile_f32_d32_n1024.txt"}
 
 
 def kernel_source_sha1(precision):
@@ -213,11 +221,51 @@ def cpu_baseline(d, N, K, steps=1):
                       f"{steps} step(s), {dt:.2f} s"}
 
 
+def lse_frames(count, d, N, seed):
+    """Seeded synthetic variables for the objective: complex Gaussian entries
+    with column lengths spread over [0.5, 2] (the objective normalises them)."""
+    rng = np.random.default_rng(seed)
+    z = rng.standard_normal((count, d, N)) + 1j * rng.standard_normal((count, d, N))
+    return z * rng.uniform(0.5, 2.0, size=(count, 1, N))
+
+
+def lse_oracle_rate(d, N, frames):
+    """The oracle's objective + gradient on a bounded sample of frames (single
+    thread, about 10 s at most); returns (pairs/s, frames done, seconds)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    done = 0
+    for q in range(frames.shape[0]):
+        O.lse(frames[q], LSE_DELTA)
+        done += 1
+        if time.perf_counter() - t0 > 10.0:
+            break
+    dt = time.perf_counter() - t0
+    return done * N * (N - 1) / 2 / dt, done, dt
+
+
 def run_reference(args, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     d, N, K, prec, desc = WORKLOADS[wl]
+    if wl == "objective_d32_n1024":
+        fr = lse_frames(max(1, args.steps) * 8, d, N, SEED)
+        rate, done, dt = lse_oracle_rate(d, N, fr)
+        line = {"impl": "reference", "metric": "off-diagonal Gram pairs per second through the "
+                "smooth-maximum objective and its gradient", "value": rate, "unit": "pairs/s",
+                "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": dt / done * 1e3 * K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded complex Gaussian frames)",
+                "config": {"workload": wl, "d": d, "N": N, "frames": K, "delta": LSE_DELTA,
+                           "precision": "fp64 oracle", "sample_frames": done},
+                "cpu_baseline": {"value": rate, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"{done} frames, objective + gradient, {dt:.1f} s"},
+                "e2e": {"value": rate, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     steps, warm = args.steps, args.warmup
     import oracle as O
     cores = len(os.sched_getaffinity(0))
@@ -283,6 +331,11 @@ def main():
         return
     if wl == "serving":
         run_serving(args, ws, rank, local, dist, torch, T)
+        if dist:
+            dist.destroy_process_group()
+        return
+    if wl == "objective_d32_n1024":
+        run_objective(args, ws, rank, local, dist, torch, T)
         if dist:
             dist.destroy_process_group()
         return
@@ -553,6 +606,120 @@ def run_batched(args, ws, rank, local, dist, torch, T):
                                 "kind": "oracle",
                                 "sample": f"all 512 instances, all {K} candidates of iterations "
                                           f"1..{it} scored by the fp64 oracle, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_objective(args, ws, rank, local, dist, torch, T):
+    """The paper's objective: F_{s,delta} and its gradient for a stack of 64
+    frames (d = 32, N = 1024) per call; a step is one call.  Weak scaling:
+    every rank evaluates its own stack."""
+    d, N, K, prec, desc = WORKLOADS["objective_d32_n1024"]
+    pairs = K * N * (N - 1) // 2
+    flops = pairs * 32 * d     # max pass 8d, Gram 8d, the two block products 16d
+    frames = lse_frames(K, d, N, SEED + rank)
+    flat = np.ascontiguousarray(np.transpose(frames, (0, 2, 1))).view(np.float64).reshape(-1)
+    dev = torch.device("cuda", local)
+    v = torch.from_numpy(flat.copy()).to(dev)
+    nbytes = T.lse_scratch_bytes(N, d, K, prec)
+    scratch = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    sp = (scratch.data_ptr() + 255) // 256 * 256
+    out = torch.zeros(2 * K, dtype=torch.float64, device=dev)
+    grad = torch.zeros_like(v)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(dev)
+
+    def call():
+        T.lse_device(N, d, K, v.data_ptr(), LSE_DELTA, prec, sp, nbytes, out.data_ptr(),
+                     grad.data_ptr(), stream.cuda_stream)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        call()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        barrier()
+        for e0, e1 in ev:
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+        barrier()
+    clocks = clk.summary()
+    t_dev = sum(e0.elapsed_time(e1) for e0, e1 in ev) * 1e-3
+    if dist:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    kernel_ms = 1e3 * t_dev / args.steps
+    value = ws * args.steps * pairs / t_dev
+    F = out.view(K, 2)[:, 0].cpu().numpy()
+    s = out.view(K, 2)[:, 1].cpu().numpy()
+    n = N * (N - 1) // 2
+    assert np.all(s <= F) and np.all(F <= s + LSE_DELTA * np.log(n) + 1e-9)
+    # end to end through the public host API: the stack copied in, F, s and the
+    # gradient copied out (the library allocates and frees its device memory)
+    e2e_steps = max(3, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        T.lse(frames, LSE_DELTA, prec)
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    # the same stack in binary64, for comparison
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nb64 = T.lse_scratch_bytes(N, d, K, "fp64")
+    scr64 = torch.empty(nb64 + 256, dtype=torch.uint8, device=dev)
+    sp64 = (scr64.data_ptr() + 255) // 256 * 256
+    T.lse_device(N, d, K, v.data_ptr(), LSE_DELTA, "fp64", sp64, nb64, out.data_ptr(),
+                 grad.data_ptr(), stream.cuda_stream)
+    e0.record(stream)
+    T.lse_device(N, d, K, v.data_ptr(), LSE_DELTA, "fp64", sp64, nb64, out.data_ptr(),
+                 grad.data_ptr(), stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    peaks, peak_kind = measured_peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = fp32_alu_peak_tflops(sm_mhz)
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    line = {"metric": "off-diagonal Gram pairs per second through the smooth-maximum objective "
+                      "and its gradient (K frames x N(N-1)/2 per call)",
+            "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": kernel_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded complex Gaussian frames, column lengths in [0.5, 2])",
+            "config": {"workload": "objective_d32_n1024", "description": desc, "d": d, "N": N,
+                       "frames": K, "delta": LSE_DELTA, "precision": prec,
+                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write outside "
+                             f"the timed events)",
+                       "parallelism": f"independent stack per GPU x{ws}"},
+            "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
+                         "frac": achieved / peak, "traffic": profiled_traffic("lse"),
+                         "kernel": "one objective call: k_lse_prepare, k_gram_planes (s), "
+                                   "k_lse_tile, k_lse_total, k_lse_finish",
+                         "kernel_ms": kernel_ms, "flops_per_launch": flops,
+                         "peak_source": f"fp32 FMA peak derived: 152 SMs x 128 lanes x 2 flops "
+                                        f"x {sm_mhz} MHz"},
+            "gpu_launches": 5 * args.steps,
+            "e2e": {"value": ws * e2e_steps * pairs / t_e2e, "unit": "pairs/s",
+                    "h2d_bytes_per_step": int(flat.nbytes),
+                    "d2h_bytes_per_step": int(flat.nbytes + 16 * K),
+                    "call": "trstmi_lse_frames (host buffers in and out)"},
+            "fp64_same_stack": {"ms": ms64, "pairs_per_s": pairs / (ms64 * 1e-3),
+                                "tflops": flops / (ms64 * 1e-3) / 1e12},
+            "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, done, dt = lse_oracle_rate(d, N, frames)
+        line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{done} of the {K} frames, objective + gradient by the "
+                                          f"fp64 oracle (one thread), {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -431,8 +431,8 @@ int trstmi_mu2_frame_noalloc(int N, int d, const double *phi_dev, double *mu2_de
  * count frames of the same shape are evaluated together; frame q of v is
  * the 2*d*N doubles at v + 2*d*N*q.  precision: TRSTMI_FP64 (binary64
  * throughout) or TRSTMI_FP32 (the variable rounded to binary32, Gram,
- * weights and block products in binary32; the sums over tiles, S, F and the
- * gradient's final assembly in binary64).  Requires N >= 2, 1 <= d <= 256,
+ * weights, block products and each column's sum over its tiles in binary32;
+ * S, F and the projection through the normalisation in binary64).  Requires N >= 2, 1 <= d <= 256,
  * count >= 1, 0 < delta < inf, count*N*d < 2^31; a zero column makes that
  * frame's results NaN (TRSTMI_EINVAL from trstmi_lse_frames).  The results
  * do not depend on the order in which the device runs its tiles.

@@ -142,7 +142,8 @@ cudaError_t launch_screen_wait_test(int fmt, int N, int d, const float2* phi32, 
 // F_{s,delta}, s and the gradient in V of `count` frames (v: device, count x
 // N x d complex interleaved doubles); out: device, count x [F, s]; grad:
 // device, count x N x d complex, or null.  Arithmetic in binary64 (f64) or
-// binary32 (sums of the weights and of the partial products in binary64).
+// binary32 (the sums of the tiles' weights, S, F and the final projection in
+// binary64).
 size_t lse_scratch_bytes(int N, int d, int count, bool f64);
 cudaError_t launch_lse(int N, int d, int count, const double* v, double delta, bool f64,
                        void* scratch, double* out, double* grad, int num_sms, cudaStream_t s);

@@ -16,17 +16,21 @@
 //
 // Passes (all on the caller's stream, no host synchronisation):
 //   1. k_lse_prepare  r_j and the unit columns as [i][column] planes;
-//   2. k_lse_max      s = max_{j<k} |G_jk|^2 per frame (tile pass);
-//   3. k_lse_tile     per upper-triangle tile (I, J): G, the weights
+//   2. the search's Gram pass over the planes: s = max_{j<k} |G_jk|^2 per
+//                     frame (the same micro-tile arithmetic as below, so
+//                     every x_jk has the same bits in both passes);
+//   3. k_lse_tile     per upper-triangle tile (I, J), the next tile's column
+//                     blocks copied asynchronously meanwhile: G, the weights
 //                     e_jk = exp((x_jk - s)/delta), M = e (.) G, and the two
 //                     products Phi_I M (to block J) and Phi_J M^* (to block
 //                     I), written as per-tile partials with the tile's sum
 //                     of e (no atomics: the result does not depend on the
 //                     order the tiles ran in);
 //   4. k_lse_total    S = sum of the tiles' sums in a fixed order, F;
-//   5. k_lse_finish   per column: the partials of its tiles in a fixed
-//                     order, / S, times 2, projected through the
-//                     normalisation.
+//   5. k_lse_finish   per group of columns: the partials of each column's
+//                     tiles in a fixed order, / S, times 2, staged in shared
+//                     memory, projected through the normalisation and
+//                     written column by column.
 #include <algorithm>
 
 #include "kernels.h"
@@ -45,6 +49,7 @@ template <typename T> struct LseArgs {
   T* planes;                // count x [d x N re][d x N im] unit columns
   T* rnorm;                 // count x N column norms
   uint32_t* bad;            // count: a zero column was seen
+  int vec;                  // planes copied in 16-byte runs (N % (16 / sizeof(T)) == 0)
   typename Mu2Bits<T>::type* smax;   // count: s as bits
   T* part;                  // count x ntiles x [2: to I, to J][2: re, im][d][BT]
   double* part_sum;         // count x ntiles
@@ -88,49 +93,6 @@ __global__ void k_lse_prepare(const LseArgs<T> a) {
   }
 }
 
-// column blocks I and J of a frame's planes into shared memory (d x BT real,
-// d x BT imaginary each; block J only off the diagonal), zeros past N
-template <typename T, int BT>
-__device__ __forceinline__ void load_blocks(const LseArgs<T>& a, int slot, int I, int J, T* sI,
-                                            T* sJ) {
-  const int d = a.d, N = a.N;
-  const T* pre = a.planes + (size_t)slot * 2 * d * N;
-  const T* pim = pre + (size_t)d * N;
-  for (int blk = 0; blk < (I == J ? 1 : 2); ++blk) {
-    const int c0 = (blk == 0 ? I : J) * BT;
-    T* ore = blk == 0 ? sI : sJ;
-    T* oim = ore + (size_t)d * BT;
-    for (int q = threadIdx.x; q < d * BT; q += blockDim.x) {
-      const int i = q / BT, loc = q % BT, gj = c0 + loc;
-      ore[q] = gj < N ? pre[(size_t)i * N + gj] : T(0);
-      oim[q] = gj < N ? pim[(size_t)i * N + gj] : T(0);
-    }
-  }
-}
-
-// 2. s per frame
-template <typename T, int R>
-__global__ void __launch_bounds__(kLseThreads) k_lse_max(const LseArgs<T> a) {
-  constexpr int BT = 16 * R;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T red[kLseThreads / 32];
-  T* sI = reinterpret_cast<T*>(smem_raw);
-  T* sJ = sI + (size_t)2 * a.d * BT;
-  const long long nitems = (long long)a.count * a.ntiles;
-  for (long long w = blockIdx.x; w < nitems; w += gridDim.x) {
-    const int slot = (int)(w / a.ntiles);
-    int I, J;
-    tile_coords((int)(w - (long long)slot * a.ntiles), I, J);
-    __syncthreads();
-    load_blocks<T, BT>(a, slot, I, J, sI, sJ);
-    __syncthreads();
-    T m = tile_pairs_max<T, R>(sI, sI + (size_t)a.d * BT, I == J ? sI : sJ, a.d, a.N, I, J,
-                               T(-1), nullptr);
-    m = block_max<T>(m, red);
-    if (threadIdx.x == 0) atomic_max_nonneg(a.smax + slot, m);
-  }
-}
-
 __device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -146,33 +108,131 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return v;  // valid in thread 0
 }
 
-// 3. per tile: weights, M = e (.) G and the two block products
+// R consecutive values to shared or global memory (R * sizeof(T)-aligned)
+template <typename T, int R>
+__device__ __forceinline__ void store_run(T* p, const T (&v)[R]) {
+  if constexpr (sizeof(T) == 4 && R == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (sizeof(T) == 4 && R == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else if constexpr (sizeof(T) == 8 && R % 2 == 0) {
+#pragma unroll
+    for (int h = 0; h < R; h += 2) *reinterpret_cast<double2*>(p + h) = make_double2(v[h], v[h + 1]);
+  } else {
+#pragma unroll
+    for (int x = 0; x < R; ++x) p[x] = v[x];
+  }
+}
+
+// Four complex multiply-adds p[c] += (a + ib) (mr[c] + i mi[c]); binary32
+// pairs neighbouring columns in paired fused multiply-adds.
+template <typename T>
+__device__ __forceinline__ void cmac4(T (&pr)[4], T (&pi)[4], T a, T b, const T (&mr)[4],
+                                      const T (&mi)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 aa = make_float2(a, a), bb = make_float2(b, b), nb = make_float2(-b, -b);
+#pragma unroll
+    for (int h = 0; h < 4; h += 2) {
+      const float2 r = make_float2(mr[h], mr[h + 1]), q = make_float2(mi[h], mi[h + 1]);
+      float2 xr = make_float2(pr[h], pr[h + 1]), xi = make_float2(pi[h], pi[h + 1]);
+      xr = __ffma2_rn(aa, r, __ffma2_rn(nb, q, xr));
+      xi = __ffma2_rn(aa, q, __ffma2_rn(bb, r, xi));
+      pr[h] = xr.x; pr[h + 1] = xr.y;
+      pi[h] = xi.x; pi[h + 1] = xi.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      pr[c] = fma(a, mr[c], fma(-b, mi[c], pr[c]));
+      pi[c] = fma(a, mi[c], fma(b, mr[c], pi[c]));
+    }
+  }
+}
+
+// out[i][c] = sum_l src[i][l] X[l][c] over a tile's BT columns: src is a
+// column block in shared memory (d x BT real, then d x BT imaginary), X a
+// complex BT x BT matrix in shared memory (real and imaginary planes, row
+// pitch P), out d x BT real then imaginary (global).  Each thread owns four
+// adjacent columns c of two rows i (i0, i0 + RG): per step l one vector load
+// of X's row segment per plane and four scalar loads of src, 32 fused
+// multiply-adds.
+template <typename T, int BT, int P>
+__device__ __forceinline__ void block_product(const T* src, const T* xre, const T* xim, T* out,
+                                              int d) {
+  constexpr int CG = BT / 4;
+  constexpr int RG = kLseThreads / CG;
+  const int cg = threadIdx.x % CG, rg = threadIdx.x / CG;
+  const T* sre = src;
+  const T* sim = src + (size_t)d * BT;
+  for (int i0 = rg; i0 < d; i0 += 2 * RG) {
+    const int i1 = i0 + RG;
+    const bool two = i1 < d;
+    T pr0[4], pi0[4], pr1[4], pi1[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { pr0[c] = pi0[c] = pr1[c] = pi1[c] = T(0); }
+#pragma unroll 4
+    for (int l = 0; l < BT; ++l) {
+      T mr[4], mi[4];
+      load_run<T, 4>(xre + l * P + 4 * cg, mr);
+      load_run<T, 4>(xim + l * P + 4 * cg, mi);
+      const T a0 = sre[i0 * BT + l], b0 = sim[i0 * BT + l];
+      const T a1 = two ? sre[i1 * BT + l] : T(0), b1 = two ? sim[i1 * BT + l] : T(0);
+      cmac4<T>(pr0, pi0, a0, b0, mr, mi);
+      cmac4<T>(pr1, pi1, a1, b1, mr, mi);
+    }
+    store_run<T, 4>(out + i0 * BT + 4 * cg, pr0);
+    store_run<T, 4>(out + (size_t)d * BT + i0 * BT + 4 * cg, pi0);
+    if (two) {
+      store_run<T, 4>(out + i1 * BT + 4 * cg, pr1);
+      store_run<T, 4>(out + (size_t)d * BT + i1 * BT + 4 * cg, pi1);
+    }
+  }
+}
+
+// 3. per tile: weights, M = e (.) G and the two block products.  The
+// thread that forms G_jk for its R x R micro-tile keeps M_jk in registers:
+// it writes M for Phi_I M (to block J), then M^* transposed for Phi_J M^*
+// (to block I), so both products read row segments of one matrix.
+template <typename T, int R>
+__device__ __forceinline__ void lse_prefetch(const LseArgs<T>& a, long long w, T* dst) {
+  const int slot = (int)(w / a.ntiles);
+  int I, J;
+  tile_coords((int)(w - (long long)slot * a.ntiles), I, J);
+  prefetch_blocks<T, 16 * R>(a.planes + (size_t)slot * 2 * a.d * a.N, a.d, a.N, I, J, dst,
+                             a.vec != 0);
+}
+
 template <typename T, int R>
 __global__ void __launch_bounds__(kLseThreads) k_lse_tile(const LseArgs<T> a) {
   constexpr int BT = 16 * R;
-  constexpr int MP = BT + 1;                  // padded row pitch of M
-  constexpr int STEP = kLseThreads / BT;      // rows i handled side by side
+  constexpr int P = BT + 4;                   // row pitch of M (vector-aligned)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[kLseThreads / 32];
   const int d = a.d, N = a.N;
-  T* sI = reinterpret_cast<T*>(smem_raw);
-  T* sJ = sI + (size_t)2 * d * BT;
-  T* sMre = sJ + (size_t)2 * d * BT;
-  T* sMim = sMre + (size_t)BT * MP;
+  // two stages of column blocks (I then J, 4 d BT values each), then M
+  T* stage0 = reinterpret_cast<T*>(smem_raw);
+  const size_t stage = (size_t)4 * d * BT;
+  T* sMre = stage0 + 2 * stage;
+  T* sMim = sMre + (size_t)BT * P;
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   const long long nitems = (long long)a.count * a.ntiles;
-  for (long long w = blockIdx.x; w < nitems; w += gridDim.x) {
+  long long w = blockIdx.x;
+  if (w < nitems) lse_prefetch<T, R>(a, w, stage0);
+  cp_async_commit();
+  for (int sg = 0; w < nitems; w += gridDim.x, sg ^= 1) {
+    const long long wn = w + gridDim.x;
+    if (wn < nitems) lse_prefetch<T, R>(a, wn, stage0 + (sg ^ 1) * stage);
+    cp_async_commit();
+    cp_async_wait<1>();   // this thread's copies of item w have landed ...
+    __syncthreads();      // ... and every other thread's
     const int slot = (int)(w / a.ntiles);
     const int tau = (int)(w - (long long)slot * a.ntiles);
     int I, J;
     tile_coords(tau, I, J);
     const T s = nonneg_from_bits(a.smax[slot]);
     const T delta = (T)a.delta;
-    __syncthreads();
-    load_blocks<T, BT>(a, slot, I, J, sI, sJ);
-    __syncthreads();
-    const T* bI = sI;
-    const T* bJ = I == J ? sI : sJ;
+    const T* bI = stage0 + sg * stage;
+    const T* bJ = I == J ? bI : bI + (size_t)2 * d * BT;
     // G of the tile, as in the search's tile pass
     MicroTile<T, R> acc;
     acc.zero();
@@ -185,62 +245,49 @@ __global__ void __launch_bounds__(kLseThreads) k_lse_tile(const LseArgs<T> a) {
       load_run<T, R>(bJ + (size_t)d * BT + i * BT + R * tx, bi);
       acc.step(ar, ai, br, bi);
     }
-    double esum = 0.0;
+    // weights and M (zero outside j < k < N); the thread's few weights are
+    // summed in T, the CTA's sum and everything after it in binary64
+    T esum = T(0);
+    T mre[R][R], mim[R][R];
 #pragma unroll
     for (int x = 0; x < R; ++x)
 #pragma unroll
       for (int y = 0; y < R; ++y) {
-        const int jl = R * ty + x, kl = R * tx + y;
-        const int gj = I * BT + jl, gk = J * BT + kl;
-        T mre = T(0), mim = T(0);
+        const int gj = I * BT + R * ty + x, gk = J * BT + R * tx + y;
+        mre[x][y] = mim[x][y] = T(0);
         if (gj < gk && gk < N) {
           const T gre = acc.get_re(x, y), gim = acc.get_im(x, y);
           const T e = exp_of<T>((pair_abs2(gre, gim) - s) / delta);
-          esum += (double)e;
-          mre = e * gre;
-          mim = e * gim;
-        }
-        sMre[jl * MP + kl] = mre;
-        sMim[jl * MP + kl] = mim;
-      }
-    esum = block_sum(esum, red);
-    if (threadIdx.x == 0) a.part_sum[(size_t)slot * a.ntiles + tau] = esum;
-    __syncthreads();
-    // Phi_I M -> columns of block J:  P[i][kl] = sum_jl phi_I[i][jl] M[jl][kl]
-    // Phi_J M^* -> columns of block I: Q[i][jl] = sum_kl phi_J[i][kl] conj(M[jl][kl])
-    T* part = a.part + ((size_t)slot * a.ntiles + tau) * 4 * d * BT;
-    const int col = threadIdx.x % BT, i0 = threadIdx.x / BT;
-    for (int side = 0; side < 2; ++side) {
-      const T* src = side == 0 ? bI : bJ;       // side 0: to J; side 1: to I
-      T* dst = part + (size_t)(side == 0 ? 1 : 0) * 2 * d * BT;
-      for (int ib = i0; ib < d; ib += 8 * STEP) {
-        T pr[8], pi[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) { pr[u] = T(0); pi[u] = T(0); }
-        for (int l = 0; l < BT; ++l) {
-          const T mr = side == 0 ? sMre[l * MP + col] : sMre[col * MP + l];
-          const T mi = side == 0 ? sMim[l * MP + col] : -sMim[col * MP + l];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int i = ib + u * STEP;
-            if (i < d) {
-              const T re = src[i * BT + l], im = src[(size_t)d * BT + i * BT + l];
-              pr[u] = fma(re, mr, fma(-im, mi, pr[u]));
-              pi[u] = fma(re, mi, fma(im, mr, pi[u]));
-            }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int i = ib + u * STEP;
-          if (i < d) {
-            dst[i * BT + col] = pr[u];
-            dst[(size_t)d * BT + i * BT + col] = pi[u];
-          }
+          esum += e;
+          mre[x][y] = e * gre;
+          mim[x][y] = e * gim;
         }
       }
+#pragma unroll
+    for (int x = 0; x < R; ++x) {
+      store_run<T, R>(sMre + (R * ty + x) * P + R * tx, mre[x]);
+      store_run<T, R>(sMim + (R * ty + x) * P + R * tx, mim[x]);
     }
+    const double tsum = block_sum((double)esum, red);   // its barriers also publish M
+    if (threadIdx.x == 0) a.part_sum[(size_t)slot * a.ntiles + tau] = tsum;
+    T* part = a.part + ((size_t)slot * a.ntiles + tau) * 4 * d * BT;
+    // Phi_I M -> columns of block J:  P[i][kl] = sum_jl phi_I[i][jl] M[jl][kl]
+    block_product<T, BT, P>(bI, sMre, sMim, part + (size_t)2 * d * BT, d);
+    __syncthreads();
+    // Phi_J M^* -> columns of block I: Q[i][jl] = sum_kl phi_J[i][kl] conj(M[jl][kl])
+#pragma unroll
+    for (int y = 0; y < R; ++y) {
+      T cr[R], ci[R];
+#pragma unroll
+      for (int x = 0; x < R; ++x) { cr[x] = mre[x][y]; ci[x] = -mim[x][y]; }
+      store_run<T, R>(sMre + (R * tx + y) * P + R * ty, cr);
+      store_run<T, R>(sMim + (R * tx + y) * P + R * ty, ci);
+    }
+    __syncthreads();
+    block_product<T, BT, P>(bJ, sMre, sMim, part, d);
+    __syncthreads();      // stage sg and M are free for the next round
   }
+  cp_async_wait<0>();
 }
 
 // 4. one CTA per frame: S over the tiles in a fixed order, F = s + delta log S
@@ -267,56 +314,97 @@ __global__ void __launch_bounds__(kLseThreads) k_lse_total(const LseArgs<T> a) {
   }
 }
 
-// 5. one thread per (frame, column): the partials of the column's tiles in a
-// fixed order (tiles (I', b) for I' <= b to its block J side, then (b, J')
-// for J' >= b to its block I side), 2 / S, then the normalisation
+// 5. one CTA per (frame, group of CW columns).  Thread (row, col) sums, for
+// rows i = row, row + 256/CW, ..., the partials of column j = j0 + col over
+// its tiles in a fixed order (tiles (I', b) for I' <= b: the side "to J";
+// then (b, J') for J' >= b: the side "to I"; b = j / BT), reading runs of
+// consecutive columns, and stages 2 g / S and the unit column in shared
+// memory; then each warp takes whole columns: Re(phi^* g) by a warp sum and
+// the projected, rescaled column written in consecutive entries.
 template <typename T, int R>
-__global__ void k_lse_finish(const LseArgs<T> a) {
+__global__ void __launch_bounds__(kLseThreads) k_lse_finish(const LseArgs<T> a, int CW) {
   constexpr int BT = 16 * R;
-  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (g >= (long long)a.count * a.N) return;
-  const int slot = (int)(g / a.N), j = (int)(g - (long long)slot * a.N);
-  const int d = a.d, N = a.N, b = j / BT, loc = j % BT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int d = a.d, N = a.N;
+  double2* sG = reinterpret_cast<double2*>(smem_raw);                 // d x CW
+  typename Cplx<T>::type* sP = reinterpret_cast<typename Cplx<T>::type*>(sG + (size_t)d * CW);
+  const int groups = (N + CW - 1) / CW;
+  const int slot = blockIdx.x / groups, j0 = (blockIdx.x - slot * groups) * CW;
   const double* o = a.sums + 3 * (size_t)slot;
-  double2* gout = reinterpret_cast<double2*>(a.grad) + ((size_t)slot * N + j) * d;
+  double2* gout = reinterpret_cast<double2*>(a.grad) + (size_t)slot * N * d;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (a.bad[slot]) {
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
-    for (int i = 0; i < d; ++i) gout[i] = make_double2(nan, nan);
+    for (int c = warp; c < CW && j0 + c < N; c += kLseThreads / 32)
+      for (int i = lane; i < d; i += 32) gout[(size_t)(j0 + c) * d + i] = make_double2(nan, nan);
     return;
   }
   const double scale = 2.0 / o[2];
   const T* part = a.part + (size_t)slot * a.ntiles * 4 * d * BT;
   const T* pre = a.planes + (size_t)slot * 2 * d * N;
   const T* pim = pre + (size_t)d * N;
-  double rad = 0.0;
-  for (int i = 0; i < d; ++i) {
-    double gr = 0.0, gi = 0.0;
-    for (int I = 0; I <= b; ++I) {               // tiles (I, b): side "to J"
-      const T* p = part + ((size_t)(b * (b + 1) / 2 + I) * 4 + 2) * d * BT;
-      gr += (double)p[i * BT + loc];
-      gi += (double)p[(size_t)d * BT + i * BT + loc];
+  {
+    const int col = threadIdx.x % CW, row = threadIdx.x / CW, rows = kLseThreads / CW;
+    const int j = j0 + col;
+    const bool in = j < N;
+    const int b = j / BT, loc = j % BT;
+    for (int i = row; i < d; i += rows) {
+      // summed in T: binary64 arithmetic runs at a small fraction of the
+      // binary32 rate, and the partials are T already
+      T gr = T(0), gi = T(0);
+      if (in) {
+#pragma unroll 4
+        for (int I = 0; I <= b; ++I) {               // tiles (I, b): side "to J"
+          const T* p = part + ((size_t)(b * (b + 1) / 2 + I) * 4 + 2) * d * BT;
+          gr += p[i * BT + loc];
+          gi += p[(size_t)d * BT + i * BT + loc];
+        }
+#pragma unroll 4
+        for (int J = b; J < a.nb; ++J) {             // tiles (b, J): side "to I"
+          const T* p = part + ((size_t)(J * (J + 1) / 2 + b) * 4 + 0) * d * BT;
+          gr += p[i * BT + loc];
+          gi += p[(size_t)d * BT + i * BT + loc];
+        }
+      }
+      sG[i * CW + col] = make_double2((double)gr * scale, (double)gi * scale);
+      typename Cplx<T>::type ph;
+      ph.x = in ? pre[(size_t)i * N + j] : T(0);
+      ph.y = in ? pim[(size_t)i * N + j] : T(0);
+      sP[i * CW + col] = ph;
     }
-    for (int J = b; J < a.nb; ++J) {             // tiles (b, J): side "to I"
-      const T* p = part + ((size_t)(J * (J + 1) / 2 + b) * 4 + 0) * d * BT;
-      gr += (double)p[i * BT + loc];
-      gi += (double)p[(size_t)d * BT + i * BT + loc];
+  }
+  __syncthreads();
+  for (int c = warp; c < CW; c += kLseThreads / 32) {
+    const int j = j0 + c;
+    if (j >= N) break;
+    double rad = 0.0;
+    for (int i = lane; i < d; i += 32) {
+      const double2 g = sG[i * CW + c];
+      const auto ph = sP[i * CW + c];
+      rad += (double)ph.x * g.x + (double)ph.y * g.y;
     }
-    gr *= scale;
-    gi *= scale;
-    gout[i] = make_double2(gr, gi);
-    rad += (double)pre[(size_t)i * N + j] * gr + (double)pim[(size_t)i * N + j] * gi;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) rad += __shfl_xor_sync(0xffffffffu, rad, off);
+    const double inv_r = 1.0 / (double)a.rnorm[(size_t)slot * N + j];
+    for (int i = lane; i < d; i += 32) {
+      const double2 g = sG[i * CW + c];
+      const auto ph = sP[i * CW + c];
+      gout[(size_t)j * d + i] =
+          make_double2((g.x - (double)ph.x * rad) * inv_r, (g.y - (double)ph.y * rad) * inv_r);
+    }
   }
-  const double inv_r = 1.0 / (double)a.rnorm[(size_t)slot * N + j];
-  for (int i = 0; i < d; ++i) {
-    const double2 q = gout[i];
-    gout[i] = make_double2((q.x - (double)pre[(size_t)i * N + j] * rad) * inv_r,
-                           (q.y - (double)pim[(size_t)i * N + j] * rad) * inv_r);
-  }
+}
+
+// columns per CTA of the final pass: as many as fit 96 KiB of staging
+template <typename T> int finish_cols(int d) {
+  int cw = 32;
+  while (cw > 8 && (size_t)d * cw * (sizeof(double2) + 2 * sizeof(T)) > 96 * 1024) cw >>= 1;
+  return cw;
 }
 
 template <typename T> size_t lse_smem(int d, int R) {
   const size_t BT = 16 * (size_t)R;
-  return (4 * (size_t)d * BT + 2 * BT * (BT + 1)) * sizeof(T);
+  return (8 * (size_t)d * BT + 2 * BT * (BT + 4)) * sizeof(T);
 }
 
 template <typename T> int lse_pick_R(int N, int d) {
@@ -364,22 +452,29 @@ template <typename K> cudaError_t lse_grid(K kernel, size_t smem, long long item
 
 template <typename T, int R>
 cudaError_t lse_launch_R(const LseArgs<T>& a, int num_sms, cudaStream_t s) {
-  const size_t smem_max = (size_t)4 * a.d * 16 * R * sizeof(T);
   const size_t smem_tile = lse_smem<T>(a.d, R);
   const long long items = (long long)a.count * a.ntiles;
   int grid = 0;
-  cudaError_t e = lse_grid(k_lse_max<T, R>, smem_max, items, num_sms, &grid);
+  cudaError_t e;
+  // s: the search's tile pass over the planes
+  GramSource src{};
+  src.perturb = true;       // candidates given as planes: no generation
+  src.planes = a.planes;
+  if constexpr (sizeof(T) == 4)
+    e = launch_gram_f32(a.N, a.d, a.count, src, a.smax, nullptr, num_sms, s);
+  else
+    e = launch_gram_f64(a.N, a.d, a.count, src, a.smax, num_sms, s);
   if (e != cudaSuccess) return e;
-  k_lse_max<T, R><<<grid, kLseThreads, smem_max, s>>>(a);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = lse_grid(k_lse_tile<T, R>, smem_tile, items, num_sms, &grid)) != cudaSuccess) return e;
   k_lse_tile<T, R><<<grid, kLseThreads, smem_tile, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_lse_total<T><<<a.count, kLseThreads, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.grad) {
-    const long long threads = (long long)a.count * a.N;
-    k_lse_finish<T, R><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(a);
+    const int cw = finish_cols<T>(a.d);
+    const long long ctas = (long long)a.count * ((a.N + cw - 1) / cw);
+    const size_t smem = (size_t)a.d * cw * (sizeof(double2) + 2 * sizeof(T));
+    k_lse_finish<T, R><<<(unsigned)ctas, kLseThreads, smem, s>>>(a, cw);
     e = cudaGetLastError();
   }
   return e;
@@ -397,6 +492,7 @@ cudaError_t lse_run(int N, int d, int count, const double* v, double delta, void
   a.planes = reinterpret_cast<T*>(b + L.o_planes);
   a.rnorm = reinterpret_cast<T*>(b + L.o_rnorm);
   a.bad = reinterpret_cast<uint32_t*>(b + L.o_bad);
+  a.vec = (N % (16 / (int)sizeof(T)) == 0) ? 1 : 0;
   a.smax = reinterpret_cast<typename Mu2Bits<T>::type*>(b + L.o_smax);
   a.part = reinterpret_cast<T*>(b + L.o_part);
   a.part_sum = reinterpret_cast<double*>(b + L.o_psum);
@@ -440,18 +536,18 @@ cudaError_t launch_lse(int N, int d, int count, const double* v, double delta, b
 
 cudaError_t init_lse_attributes(int optin) {
   cudaError_t e;
-  if ((e = lse_allow(k_lse_max<float, 4>, optin)) != cudaSuccess) return e;
-  if ((e = lse_allow(k_lse_max<float, 2>, optin)) != cudaSuccess) return e;
-  if ((e = lse_allow(k_lse_max<float, 1>, optin)) != cudaSuccess) return e;
-  if ((e = lse_allow(k_lse_max<double, 4>, optin)) != cudaSuccess) return e;
-  if ((e = lse_allow(k_lse_max<double, 2>, optin)) != cudaSuccess) return e;
-  if ((e = lse_allow(k_lse_max<double, 1>, optin)) != cudaSuccess) return e;
   if ((e = lse_allow(k_lse_tile<float, 4>, optin)) != cudaSuccess) return e;
   if ((e = lse_allow(k_lse_tile<float, 2>, optin)) != cudaSuccess) return e;
   if ((e = lse_allow(k_lse_tile<float, 1>, optin)) != cudaSuccess) return e;
   if ((e = lse_allow(k_lse_tile<double, 4>, optin)) != cudaSuccess) return e;
   if ((e = lse_allow(k_lse_tile<double, 2>, optin)) != cudaSuccess) return e;
-  return lse_allow(k_lse_tile<double, 1>, optin);
+  if ((e = lse_allow(k_lse_tile<double, 1>, optin)) != cudaSuccess) return e;
+  if ((e = lse_allow(k_lse_finish<float, 4>, optin)) != cudaSuccess) return e;
+  if ((e = lse_allow(k_lse_finish<float, 2>, optin)) != cudaSuccess) return e;
+  if ((e = lse_allow(k_lse_finish<float, 1>, optin)) != cudaSuccess) return e;
+  if ((e = lse_allow(k_lse_finish<double, 4>, optin)) != cudaSuccess) return e;
+  if ((e = lse_allow(k_lse_finish<double, 2>, optin)) != cudaSuccess) return e;
+  return lse_allow(k_lse_finish<double, 1>, optin);
 }
 
 }  // namespace trstmi

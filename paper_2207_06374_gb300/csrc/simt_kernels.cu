@@ -296,28 +296,6 @@ __global__ void __launch_bounds__(256, TileCtas<T>::value) k_gram_tile(const Gra
 // copy latency hides behind the arithmetic of the same CTA.  The reduction is
 // tile_pairs_max, the scores the same bits as k_gram_tile's.
 
-__device__ __forceinline__ uint32_t shared_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-// 4 bytes (or zeros when !valid); src must be a valid address either way
-__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(shared_addr(dst)), "l"(src),
-               "r"(valid ? 4 : 0)
-               : "memory");
-}
-// 16 bytes, both addresses 16-byte aligned (or zeros when !valid)
-__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(shared_addr(dst)),
-               "l"(src), "r"(valid ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int Pending> __device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(Pending) : "memory");
-}
-
 // Issues the copies of work item w's column blocks into stage dst (block I,
 // then block J unless the tile is diagonal; each d x BT real, d x BT
 // imaginary).  vec: N % 4 == 0 and a 16-byte aligned planes array, so every
@@ -325,37 +303,11 @@ template <int Pending> __device__ __forceinline__ void cp_async_wait() {
 template <int R>
 __device__ __forceinline__ void prefetch_planes(const GramArgs<float>& a, long long w, float* dst,
                                                 bool vec) {
-  constexpr int BT = 16 * R;
-  const int d = a.d, N = a.N;
   const int slot = (int)(w / a.ntiles);
   int I, J;
   tile_coords((int)(w - (long long)slot * a.ntiles), I, J);
-  const float* pre = reinterpret_cast<const float*>(a.src.planes) + (size_t)slot * 2 * d * N;
-  const float* pim = pre + (size_t)d * N;
-  for (int blk = 0; blk < (I == J ? 1 : 2); ++blk) {
-    const int c0 = (blk == 0 ? I : J) * BT;
-    float* ore = dst + (size_t)blk * 2 * d * BT;
-    float* oim = ore + (size_t)d * BT;
-    if (vec) {
-      for (int q = threadIdx.x; q < d * (BT / 4); q += blockDim.x) {
-        const int i = q / (BT / 4), c4 = q % (BT / 4);
-        const int gj = c0 + 4 * c4;
-        const bool ok = gj < N;
-        const size_t g = ok ? (size_t)i * N + gj : 0;
-        cp_async16(ore + i * BT + 4 * c4, pre + g, ok);
-        cp_async16(oim + i * BT + 4 * c4, pim + g, ok);
-      }
-    } else {
-      for (int q = threadIdx.x; q < d * BT; q += blockDim.x) {
-        const int i = q / BT, loc = q % BT;
-        const int gj = c0 + loc;
-        const bool ok = gj < N;
-        const size_t g = ok ? (size_t)i * N + gj : 0;
-        cp_async4(ore + q, pre + g, ok);
-        cp_async4(oim + q, pim + g, ok);
-      }
-    }
-  }
+  const float* pre = reinterpret_cast<const float*>(a.src.planes) + (size_t)slot * 2 * a.d * a.N;
+  prefetch_blocks<float, 16 * R>(pre, a.d, a.N, I, J, dst, vec);
 }
 
 template <int R>

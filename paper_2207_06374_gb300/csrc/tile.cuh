@@ -170,4 +170,65 @@ __device__ __forceinline__ T tile_pairs_max(const T* sIre, const T* sIim, const 
   return m;
 }
 
+// ------------------------------------------- asynchronous tile copies
+__device__ __forceinline__ uint32_t shared_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// B = 4, 8 or 16 bytes from global to shared memory, zeros when !valid (src
+// must be a valid address either way); both addresses B-byte aligned
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
+  if constexpr (B == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(shared_addr(dst)),
+                 "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(shared_addr(dst)),
+                 "l"(src), "n"(B), "r"(valid ? B : 0)
+                 : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int Pending> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(Pending) : "memory");
+}
+
+// Issues the copies of column blocks I and J (J only off the diagonal) of a
+// frame held as planes (pre: d x N real parts, then d x N imaginary parts)
+// into dst: block I as d x BT real, d x BT imaginary, then block J; columns
+// past N are zeros.  vec: N a multiple of 16 / sizeof(T) and pre 16-byte
+// aligned, so every run of 16 bytes is one aligned copy.
+template <typename T, int BT>
+__device__ __forceinline__ void prefetch_blocks(const T* pre, int d, int N, int I, int J, T* dst,
+                                                bool vec) {
+  constexpr int V = 16 / (int)sizeof(T);
+  const T* pim = pre + (size_t)d * N;
+  for (int blk = 0; blk < (I == J ? 1 : 2); ++blk) {
+    const int c0 = (blk == 0 ? I : J) * BT;
+    T* ore = dst + (size_t)blk * 2 * d * BT;
+    T* oim = ore + (size_t)d * BT;
+    if (vec) {
+      for (int q = threadIdx.x; q < d * (BT / V); q += blockDim.x) {
+        const int i = q / (BT / V), cv = q % (BT / V);
+        const int gj = c0 + V * cv;
+        const bool ok = gj < N;
+        const size_t g = ok ? (size_t)i * N + gj : 0;
+        cp_async<16>(ore + i * BT + V * cv, pre + g, ok);
+        cp_async<16>(oim + i * BT + V * cv, pim + g, ok);
+      }
+    } else {
+      for (int q = threadIdx.x; q < d * BT; q += blockDim.x) {
+        const int i = q / BT, loc = q % BT;
+        const int gj = c0 + loc;
+        const bool ok = gj < N;
+        const size_t g = ok ? (size_t)i * N + gj : 0;
+        cp_async<(int)sizeof(T)>(ore + q, pre + g, ok);
+        cp_async<(int)sizeof(T)>(oim + q, pim + g, ok);
+      }
+    }
+  }
+}
+
 }  // namespace trstmi
