@@ -93,6 +93,14 @@ def lib():
                                         ctypes.c_uint32, ctypes.c_int, _u32p, ctypes.c_void_p]
             L.oracle_lse.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, _dp, _dp,
                                      _dp]
+            for f in ("oracle_orthoplex", "oracle_levenshtein"):
+                getattr(L, f).argtypes = [ctypes.c_int, ctypes.c_int]
+                getattr(L, f).restype = ctypes.c_double
+            L.oracle_gram_extremes.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+            L.oracle_gram_extremes.restype = None
+            L.oracle_distinct_distances.argtypes = [ctypes.c_int, ctypes.c_int, _dp,
+                                                    ctypes.c_double]
+            L.oracle_distinct_distances.restype = ctypes.c_int
             for f in ("oracle_init", "oracle_candidate", "oracle_score", "oracle_search",
                       "oracle_run", "oracle_replay", "oracle_lse"):
                 getattr(L, f).restype = ctypes.c_int
@@ -228,3 +236,29 @@ def lse(v: np.ndarray, delta: float, grad: bool = True):
     _check(lib().oracle_lse(N, d, _ptr(b), delta, ctypes.byref(Fv), ctypes.byref(sv),
                             _ptr(g) if grad else None), "lse")
     return Fv.value, sv.value, (_unflat(g, d, N) if grad else None)
+
+
+def orthoplex(N: int, d: int) -> float:
+    return float(lib().oracle_orthoplex(N, d))
+
+
+def levenshtein(N: int, d: int) -> float:
+    return float(lib().oracle_levenshtein(N, d))
+
+
+def gram_extremes(phi: np.ndarray):
+    """(max, min) of |G_jk|^2 over j < k."""
+    d, N = phi.shape
+    b = _flat(phi)
+    mx, mn = ctypes.c_double(), ctypes.c_double()
+    lib().oracle_gram_extremes(N, d, _ptr(b), ctypes.byref(mx), ctypes.byref(mn))
+    return mx.value, mn.value
+
+
+def distinct_distances(phi: np.ndarray, tol: float) -> int:
+    d, N = phi.shape
+    b = _flat(phi)
+    r = int(lib().oracle_distinct_distances(N, d, _ptr(b), tol))
+    if r < 0:
+        raise ValueError("oracle distinct_distances: bad arguments")
+    return r

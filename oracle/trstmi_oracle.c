@@ -467,3 +467,64 @@ out:
     free(x);
     return st;
 }
+
+/* ------------------------------------------------ bounds and diagnostics */
+
+/* Orthoplex bound (Sec. "Conjectures from Numerics", Proposition on the
+ * orthoplex and Levenshtein bounds): mu >= 1/sqrt(d) when N > d^2 (d > 1);
+ * 0 where it does not apply. */
+double oracle_orthoplex(int N, int d)
+{
+    if (d < 2 || (long long)N <= (long long)d * d) return 0.0;
+    return 1.0 / sqrt((double)d);
+}
+
+/* Levenshtein bound (same Proposition): mu >= sqrt((2N - d(d+1)) /
+ * ((N - d)(d+1))) when N > d^2 (d > 1); 0 where it does not apply. */
+double oracle_levenshtein(int N, int d)
+{
+    if (d < 2 || (long long)N <= (long long)d * d) return 0.0;
+    double n = (double)N, dd = (double)d;
+    return sqrt((2.0 * n - dd * (dd + 1.0)) / ((n - dd) * (dd + 1.0)));
+}
+
+/* max and min of |G_jk|^2 over j < k (N >= 2) by enumerating every pair. */
+void oracle_gram_extremes(int N, int d, const double *phi, double *mx, double *mn)
+{
+    double hi = 0.0, lo = 0.0;
+    int first = 1;
+    for (int j = 0; j < N; ++j)
+        for (int k = j + 1; k < N; ++k) {
+            double g = oracle_gram_abs2(d, phi, j, k);
+            if (first || g > hi) hi = g;
+            if (first || g < lo) lo = g;
+            first = 0;
+        }
+    *mx = hi;
+    *mn = lo;
+}
+
+/* Number of distinct distances among the |G_jk|, j < k, at resolution tol:
+ * each value v falls in bin floor(v / tol), and one distance is a maximal
+ * run of consecutive occupied bins.  (The single-distance observation of
+ * Sec. "Conjectures from Numerics" counts how many different |<phi_j,
+ * phi_k>| a configuration has.)  Returns -1 on bad arguments. */
+int oracle_distinct_distances(int N, int d, const double *phi, double tol)
+{
+    if (N < 2 || d < 1 || !phi || !(tol > 0.0) || tol > 1.0) return -1;
+    long nbins = (long)floor(1.0 / tol) + 2;
+    unsigned char *occ = (unsigned char *)calloc((size_t)nbins, 1);
+    if (!occ) return -1;
+    for (int j = 0; j < N; ++j)
+        for (int k = j + 1; k < N; ++k) {
+            double v = sqrt(oracle_gram_abs2(d, phi, j, k));
+            long b = (long)floor(v / tol);
+            if (b >= nbins) b = nbins - 1;
+            occ[b] = 1;
+        }
+    int runs = 0;
+    for (long b = 0; b < nbins; ++b)
+        if (occ[b] && (b == 0 || !occ[b - 1])) ++runs;
+    free(occ);
+    return runs;
+}
