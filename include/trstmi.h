@@ -272,6 +272,30 @@ int trstmi_batch_profile_score(trstmi_batch_handle b, int launches, size_t flush
 /* Frees everything.  Safe on NULL. */
 void trstmi_batch_destroy(trstmi_batch_handle b);
 
+/* --------------------------------------------------------- multi-start
+ * The paper repeats its procedure for L random initialisations and returns
+ * the minimum over the trials (Algorithm "TRSTMI optimization steps", last
+ * step; its experiments use L = 2 d^2).  Trial i is the search with seed
+ * seed0 + i, run for iters iterations with the given options exactly as
+ * trstmi_create + trstmi_step would run it alone; the trials are advanced
+ * as batched instances, at most batch_cap per batch (<= 0: all at once),
+ * which does not change any result.
+ */
+typedef struct trstmi_multistart_result {
+  double mu;            /* min over the trials of mu (deciding precision) */
+  int32_t best;         /* trial reaching it (lowest index on ties) */
+  int32_t trials;       /* L used */
+  uint64_t best_seed;   /* seed0 + best */
+} trstmi_multistart_result;
+
+/* L <= 0 selects 2*d*d trials.  mu_all (nullable, host): L doubles, every
+ * trial's mu.  best_phi (nullable, host): 2*d*N doubles, the winning trial's
+ * binary64 frame.  Returns the batch or search errors (TRSTMI_EINVAL for bad
+ * shapes or options). */
+int trstmi_multistart(int N, int d, uint64_t seed0, int L, int iters,
+                      const trstmi_options *opt, int batch_cap,
+                      trstmi_multistart_result *out, double *mu_all, double *best_phi);
+
 /* ------------------------------------------------------------- serving
  * A persistent request loop on one GPU.  A host scheduler thread keeps up to
  * max_slots searches resident (frame, radius, counters and random-stream
@@ -412,6 +436,41 @@ int trstmi_mu2_frame(int N, int d, const double *phi, int precision, double *mu2
  */
 int trstmi_mu2_frame_noalloc(int N, int d, const double *phi_dev, double *mu2_dev,
                              void *stream);
+
+/* ---------------------------------------------------------- certificates
+ * What a frame proves about itself (binary64, on the GPU): its coherence and
+ * smallest off-diagonal |G_jk|, the lower bounds of the paper that apply to
+ * its shape -- Welch (Sec. "Welch bound and equiangular lines"), orthoplex
+ * and Levenshtein (for N > d^2, Proposition in Sec. "Conjectures from
+ * Numerics") -- the distance of mu above the best of them, the smallest
+ * chordal distance sqrt(1 - mu^2) between its lines (Sec. "Introduction"),
+ * and how many distinct distances |G_jk| it has at resolution tol (the
+ * single-distance observation of the same section): every |G_jk| marks bin
+ * floor(|G_jk| / tol) and one distance is a maximal run of consecutive
+ * marked bins, so values closer than tol always count once and values
+ * farther apart than 2 tol always count twice.
+ */
+typedef struct trstmi_certificates {
+  double mu;            /* max_{j<k} |G_jk| */
+  double mu_min;        /* min_{j<k} |G_jk| */
+  double welch;         /* sqrt((N-d)/(d(N-1))) for N > d, else 0 */
+  double orthoplex;     /* 1/sqrt(d) for N > d^2 and d > 1, else 0 */
+  double levenshtein;   /* sqrt((2N-d(d+1))/((N-d)(d+1))) for N > d^2 and d > 1, else 0 */
+  double lower_bound;   /* the largest of the three */
+  double gap;           /* mu - lower_bound */
+  double min_chordal;   /* sqrt(1 - mu^2) */
+  int32_t distinct;     /* distinct distances at resolution tol */
+  int32_t reserved;
+} trstmi_certificates;
+
+/* Certificates of a host frame (2*d*N doubles, frame layout; columns are
+ * normalised first).  N >= 2, 1 <= d <= 256, 1e-7 <= tol <= 1; a zero column
+ * gives TRSTMI_EINVAL.  Device 0; allocates and frees device memory. */
+int trstmi_frame_certificates(int N, int d, const double *phi, double tol,
+                              trstmi_certificates *out);
+/* Certificates of an instance's current binary64 frame (its device and
+ * stream; blocks until done). */
+int trstmi_instance_certificates(trstmi_handle h, double tol, trstmi_certificates *out);
 
 /* ------------------------------------------- the paper's smooth maximum */
 

@@ -974,6 +974,65 @@ int trstmi_lse_frames(int N, int d, int count, const double* v, double delta, in
   return rc;
 }
 
+namespace {
+int certificates_of(int N, int d, const double* v_dev, double tol, int num_sms,
+                    cudaStream_t s, trstmi_certificates* out) {
+  void* scr = nullptr;
+  TRY_CUDA(cudaMalloc(&scr, diag_scratch_bytes(N, d, tol)));
+  unsigned char res[24];
+  cudaError_t e = launch_diagnostics(N, d, v_dev, tol, scr, num_sms, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(res, scr, sizeof(res), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(scr);
+  if (e != cudaSuccess) return record_cuda_error(e, "certificates", __LINE__);
+  uint32_t runs = 0, bad = 0;
+  double mx = 0, mn = 0;
+  std::memcpy(&mx, res, 8);
+  std::memcpy(&mn, res + 8, 8);
+  std::memcpy(&runs, res + 16, 4);
+  std::memcpy(&bad, res + 20, 4);
+  if (bad) return TRSTMI_EINVAL;
+  trstmi_certificates c{};
+  c.mu = std::sqrt(mx);
+  c.mu_min = std::sqrt(mn);
+  c.welch = N > d ? std::sqrt((double)(N - d) / ((double)d * (N - 1))) : 0.0;
+  const bool above = d > 1 && (long long)N > (long long)d * d;
+  c.orthoplex = above ? 1.0 / std::sqrt((double)d) : 0.0;
+  c.levenshtein = above ? std::sqrt((2.0 * N - (double)d * (d + 1)) /
+                                    (((double)N - d) * (d + 1.0))) : 0.0;
+  c.lower_bound = std::max(c.welch, std::max(c.orthoplex, c.levenshtein));
+  c.gap = c.mu - c.lower_bound;
+  c.min_chordal = std::sqrt(std::max(0.0, 1.0 - mx));
+  c.distinct = (int32_t)runs;
+  *out = c;
+  return TRSTMI_OK;
+}
+}  // namespace
+
+int trstmi_frame_certificates(int N, int d, const double* phi, double tol,
+                              trstmi_certificates* out) {
+  if (N < 2 || d < 1 || d > kMaxD || !phi || !out || !(tol >= 1e-7 && tol <= 1.0))
+    return TRSTMI_EINVAL;
+  int num_sms = 0;
+  int rc = ensure_device(0, &num_sms);
+  if (rc) return rc;
+  const size_t nv = (size_t)N * d * sizeof(double2);
+  void* v = nullptr;
+  TRY_CUDA(cudaMalloc(&v, nv));
+  cudaError_t e = cudaMemcpy(v, phi, nv, cudaMemcpyHostToDevice);
+  rc = e == cudaSuccess ? certificates_of(N, d, static_cast<const double*>(v), tol, num_sms, 0, out)
+                        : record_cuda_error(e, "certificates copy", __LINE__);
+  cudaFree(v);
+  return rc;
+}
+
+int trstmi_instance_certificates(trstmi_handle h, double tol, trstmi_certificates* out) {
+  if (!h || !out || !(tol >= 1e-7 && tol <= 1.0)) return TRSTMI_EINVAL;
+  TRY_CUDA(cudaSetDevice(h->opt.device));
+  return certificates_of(h->N, h->d, reinterpret_cast<const double*>(h->phi64), tol,
+                         h->num_sms, h->stream, out);
+}
+
 int trstmi_screen_wait_test(trstmi_handle h, int precision, double wait_limit_ms) {
   if (!h || !is_screen_precision(precision)) return TRSTMI_EINVAL;
   if (!(wait_limit_ms > 0.0 && wait_limit_ms <= 2000.0)) return TRSTMI_EINVAL;

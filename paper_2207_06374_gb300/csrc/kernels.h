@@ -138,6 +138,16 @@ cudaError_t launch_screen_wait_test(int fmt, int N, int d, const float2* phi32, 
                                     unsigned long long wait_limit_ns, int num_sms,
                                     cudaStream_t s);
 
+// ------------------------------------------ certificates (diag.cu)
+// max / min of |G_jk|^2 and the distinct distances at resolution tol of a
+// frame (v: device, N x d complex interleaved doubles, normalised inside).
+// Results at the start of scratch: [max bits u64][min bits u64][runs u32]
+// [zero column u32].
+size_t diag_scratch_bytes(int N, int d, double tol);
+cudaError_t launch_diagnostics(int N, int d, const double* v_dev, double tol, void* scratch,
+                               int num_sms, cudaStream_t s);
+cudaError_t init_diag_attributes(int optin);
+
 // ------------------------------------------ smooth maximum (lse.cu)
 // F_{s,delta}, s and the gradient in V of `count` frames (v: device, count x
 // N x d complex interleaved doubles); out: device, count x [F, s]; grad:

@@ -1396,6 +1396,7 @@ cudaError_t init_kernel_attributes() {
   if ((e = allow_max_dynamic_smem(k_batch_resident<float>, optin)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_batch_resident<double>, optin)) != cudaSuccess) return e;
   if ((e = init_lse_attributes(optin)) != cudaSuccess) return e;
+  if ((e = init_diag_attributes(optin)) != cudaSuccess) return e;
   return init_screen_attributes(optin);
 }
 

@@ -96,6 +96,22 @@ _lock = threading.Lock()
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 
+class Certificates(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("mu_min", ctypes.c_double),
+                ("welch", ctypes.c_double), ("orthoplex", ctypes.c_double),
+                ("levenshtein", ctypes.c_double), ("lower_bound", ctypes.c_double),
+                ("gap", ctypes.c_double), ("min_chordal", ctypes.c_double),
+                ("distinct", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class MultistartResult(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("best", ctypes.c_int32), ("trials", ctypes.c_int32),
+                ("best_seed", ctypes.c_uint64)]
+
+
 # name -> (restype, argtypes); mirrors include/trstmi.h
 SIGNATURES = {
     "trstmi_default_options": (None, [ctypes.POINTER(Options)]),
@@ -134,6 +150,14 @@ SIGNATURES = {
                                                 ctypes.c_void_p, ctypes.c_size_t,
                                                 ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p]),
+    "trstmi_frame_certificates": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp,
+                                                 ctypes.c_double, ctypes.POINTER(Certificates)]),
+    "trstmi_instance_certificates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double,
+                                           ctypes.POINTER(Certificates)]),
+    "trstmi_multistart": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                         ctypes.c_int, ctypes.c_int, ctypes.POINTER(Options),
+                                         ctypes.c_int, ctypes.POINTER(MultistartResult), _dp,
+                                         _dp]),
     "trstmi_screen_wait_test": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "trstmi_mu2_frame_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
@@ -320,6 +344,13 @@ class Search:
         return _unflat(b, self.d, self.N)
 
 
+    def certificates(self, tol: float = 1e-6) -> dict:
+        """Coherence, bounds and distinct distances of the current frame."""
+        c = Certificates()
+        _check(lib().trstmi_instance_certificates(self._h, tol, ctypes.byref(c)),
+               "trstmi_instance_certificates")
+        return c.as_dict()
+
     def profile_score(self, precision="fp32", launches=5, delta=0.1, flush_bytes=0) -> float:
         """Mean device ms of one launch of the scoring kernel (events around it alone)."""
         p = PRECISIONS[precision] if isinstance(precision, str) else precision
@@ -337,6 +368,34 @@ class Search:
     @property
     def handle(self) -> int:
         return self._h.value
+
+
+def certificates(phi: np.ndarray, tol: float = 1e-6) -> dict:
+    """Coherence, bounds, smallest chordal distance and distinct distances of a
+    frame (d, N) computed on the GPU in binary64."""
+    d, N = phi.shape
+    b = _flat(phi)
+    c = Certificates()
+    _check(lib().trstmi_frame_certificates(N, d, b.ctypes.data_as(_dp), tol, ctypes.byref(c)),
+           "trstmi_frame_certificates")
+    return c.as_dict()
+
+
+def multistart(N: int, d: int, seed0: int, L: int, iters: int, batch_cap: int = 0,
+               want_phi: bool = True, **options):
+    """L random initialisations (seeds seed0 ..), each searched for `iters`
+    iterations, and the minimum over the trials.  Returns (result, mu of every
+    trial, the winning frame or None)."""
+    o = make_options(**options)
+    trials = L if L > 0 else 2 * d * d
+    res = MultistartResult()
+    mus = np.zeros(trials)
+    phi = np.zeros(2 * d * N) if want_phi else None
+    _check(lib().trstmi_multistart(N, d, seed0, L, iters, ctypes.byref(o), batch_cap,
+                                   ctypes.byref(res), mus.ctypes.data_as(_dp),
+                                   phi.ctypes.data_as(_dp) if want_phi else None),
+           "trstmi_multistart")
+    return res, mus, (_unflat(phi, d, N) if want_phi else None)
 
 
 class Batch:
