@@ -58,6 +58,21 @@ assert TRACE_DTYPE.itemsize == ctypes.sizeof(TraceRow)
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
+HV_FN = ctypes.CFUNCTYPE(None, _dp, _dp, ctypes.c_void_p)
+
+
+class TrOpts(ctypes.Structure):
+    _fields_ = [("n_delta", ctypes.c_int), ("delta", ctypes.c_double * 16),
+                ("max_outer", ctypes.c_int), ("max_cg", ctypes.c_int),
+                ("radius0", ctypes.c_double), ("radius_max", ctypes.c_double),
+                ("eta", ctypes.c_double), ("gtol", ctypes.c_double),
+                ("fd_step", ctypes.c_double)]
+
+
+TR_DTYPE = np.dtype([("stage", "<i4"), ("iter", "<i4"), ("F", "<f8"), ("s", "<f8"),
+                     ("gnorm", "<f8"), ("radius", "<f8"), ("rho", "<f8"),
+                     ("step_norm", "<f8"), ("pred", "<f8"), ("cg_iters", "<i4"),
+                     ("cg_status", "<i4"), ("accepted", "<i4"), ("pad", "<i4")])
 
 
 def lib():
@@ -101,8 +116,18 @@ def lib():
             L.oracle_distinct_distances.argtypes = [ctypes.c_int, ctypes.c_int, _dp,
                                                     ctypes.c_double]
             L.oracle_distinct_distances.restype = ctypes.c_int
+            L.oracle_cg_steihaug.argtypes = [ctypes.c_int, _dp, HV_FN, ctypes.c_void_p,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                             _dp, _dp, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_int)]
+            L.oracle_lse_hv.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
+                                        ctypes.c_double, _dp, _dp]
+            L.oracle_tr_solve.argtypes = [ctypes.c_int, ctypes.c_int, _dp,
+                                          ctypes.POINTER(TrOpts), ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int)]
             for f in ("oracle_init", "oracle_candidate", "oracle_score", "oracle_search",
-                      "oracle_run", "oracle_replay", "oracle_lse"):
+                      "oracle_run", "oracle_replay", "oracle_lse", "oracle_cg_steihaug",
+                      "oracle_lse_hv", "oracle_tr_solve"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -262,3 +287,56 @@ def distinct_distances(phi: np.ndarray, tol: float) -> int:
     if r < 0:
         raise ValueError("oracle distinct_distances: bad arguments")
     return r
+
+
+def cg_steihaug(g, hv, radius: float, eps: float, maxit: int):
+    """CG-Steihaug on m(p) = g.p + p.Bp/2, |p| <= radius; hv(v) -> B v (numpy).
+    Returns (p, m(p), iterations, status)."""
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.float64))
+    n = g.size
+
+    def _cb(vp, op, _ctx):
+        v = np.ctypeslib.as_array(vp, shape=(n,))
+        o = np.ctypeslib.as_array(op, shape=(n,))
+        o[:] = hv(v.copy())
+
+    cb = HV_FN(_cb)
+    p = np.zeros(n)
+    m, it, st = ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().oracle_cg_steihaug(n, _ptr(g), cb, None, radius, eps, maxit, _ptr(p),
+                                    ctypes.byref(m), ctypes.byref(it), ctypes.byref(st)),
+           "cg_steihaug")
+    return p, m.value, it.value, st.value
+
+
+def lse_hv(v: np.ndarray, delta: float, h: float, u: np.ndarray) -> np.ndarray:
+    """Hessian of F_{s,delta} at V applied to U by a central difference of the
+    exact gradient (complex (d, N) arrays, real inner product)."""
+    d, N = v.shape
+    b, ub = _flat(v), _flat(u)
+    o = np.zeros_like(b)
+    _check(lib().oracle_lse_hv(N, d, _ptr(b), delta, h, _ptr(ub), _ptr(o)), "lse_hv")
+    return _unflat(o, d, N)
+
+
+def tr_opts(deltas=(0.1, 0.01, 0.001), max_outer=50, max_cg=50, radius0=0.1, radius_max=1.0,
+            eta=1e-4, gtol=1e-9, fd_step=1e-6) -> TrOpts:
+    o = TrOpts()
+    o.n_delta = len(deltas)
+    for i, x in enumerate(deltas):
+        o.delta[i] = x
+    o.max_outer, o.max_cg = max_outer, max_cg
+    o.radius0, o.radius_max, o.eta, o.gtol, o.fd_step = radius0, radius_max, eta, gtol, fd_step
+    return o
+
+
+def tr_solve(v: np.ndarray, opts: TrOpts, cap: int = 4096):
+    """The trust-region CG-Steihaug procedure over the smoothing stages.
+    Returns (the final frame, unit columns; the per-iteration trace)."""
+    d, N = v.shape
+    b = _flat(v)
+    tr = np.zeros(max(cap, 1), dtype=TR_DTYPE)
+    n = ctypes.c_int()
+    _check(lib().oracle_tr_solve(N, d, _ptr(b), ctypes.byref(opts), tr.ctypes.data, cap,
+                                 ctypes.byref(n)), "tr_solve")
+    return _unflat(b, d, N), tr[: min(n.value, cap)]

@@ -528,3 +528,217 @@ int oracle_distinct_distances(int N, int d, const double *phi, double tol)
     free(occ);
     return runs;
 }
+
+/* ------------------------------------- trust-region CG-Steihaug (Alg. 1) */
+
+static double vdot(int n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* tau >= 0 with |z + tau d| = radius (the root of the quadratic in tau). */
+static double to_boundary(int n, const double *z, const double *d, double radius, int pos)
+{
+    double dd = vdot(n, d, d), zd = vdot(n, z, d), zz = vdot(n, z, z);
+    double disc = zd * zd - dd * (zz - radius * radius);
+    if (disc < 0.0) disc = 0.0;
+    return pos ? (-zd + sqrt(disc)) / dd : (-zd - sqrt(disc)) / dd;
+}
+
+typedef void (*oracle_hv_fn)(const double *v, double *out, void *ctx);
+
+/*
+ * CG-Steihaug (Algorithm "Trust-Region CG-Steihaug", after Nocedal and
+ * Wright, Alg. 7.2): approximately minimise m(p) = g.p + p.Bp / 2 over
+ * |p| <= radius, B given by its products hv.  z_0 = 0, r_0 = g, d_0 = -g;
+ * stop when |r_0| < eps (p = 0); per step: on d.Bd <= 0 go to the boundary
+ * along d at the root with the smaller m; else alpha = r.r / d.Bd, and if
+ * |z + alpha d| >= radius go to the boundary along d (tau >= 0); else
+ * r <- r + alpha Bd, stop if |r| < eps, beta = r_new.r_new / r.r,
+ * d <- -r + beta d.  The model value m(p) is carried along (m(z + tau d) =
+ * m(z) + tau r.d + tau^2 d.Bd / 2, r = g + Bz).  status: 0 residual below
+ * eps, 1 boundary, 2 negative curvature, 3 iteration limit.
+ */
+int oracle_cg_steihaug(int n, const double *g, oracle_hv_fn hv, void *ctx, double radius,
+                       double eps, int maxit, double *p, double *m_out, int *iters,
+                       int *status)
+{
+    if (n < 1 || !g || !hv || !p || !(radius > 0.0) || maxit < 0) return ORACLE_EINVAL;
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *d = (double *)malloc(sizeof(double) * (size_t)n);
+    double *bd = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!r || !d || !bd) { free(r); free(d); free(bd); return ORACLE_EINVAL; }
+    for (int i = 0; i < n; ++i) { p[i] = 0.0; r[i] = g[i]; d[i] = -g[i]; }
+    double m = 0.0, rr = vdot(n, r, r);
+    int st = 3, it = 0;
+    if (sqrt(rr) < eps) {
+        st = 0;
+    } else {
+        for (it = 0; it < maxit; ++it) {
+            hv(d, bd, ctx);
+            double dbd = vdot(n, d, bd), rd = vdot(n, r, d);
+            if (dbd <= 0.0) {
+                double t1 = to_boundary(n, p, d, radius, 1), t2 = to_boundary(n, p, d, radius, 0);
+                double m1 = m + t1 * rd + 0.5 * t1 * t1 * dbd;
+                double m2 = m + t2 * rd + 0.5 * t2 * t2 * dbd;
+                double t = m1 <= m2 ? t1 : t2;
+                for (int i = 0; i < n; ++i) p[i] += t * d[i];
+                m = m1 <= m2 ? m1 : m2;
+                st = 2; ++it;
+                break;
+            }
+            double alpha = rr / dbd;
+            double zn2 = 0.0;
+            for (int i = 0; i < n; ++i) { double zi = p[i] + alpha * d[i]; zn2 += zi * zi; }
+            if (sqrt(zn2) >= radius) {
+                double t = to_boundary(n, p, d, radius, 1);
+                for (int i = 0; i < n; ++i) p[i] += t * d[i];
+                m += t * rd + 0.5 * t * t * dbd;
+                st = 1; ++it;
+                break;
+            }
+            for (int i = 0; i < n; ++i) { p[i] += alpha * d[i]; r[i] += alpha * bd[i]; }
+            m += alpha * rd + 0.5 * alpha * alpha * dbd;
+            double rr_new = vdot(n, r, r);
+            if (sqrt(rr_new) < eps) { st = 0; ++it; break; }
+            double beta = rr_new / rr;
+            for (int i = 0; i < n; ++i) d[i] = -r[i] + beta * d[i];
+            rr = rr_new;
+        }
+    }
+    if (m_out) *m_out = m;
+    if (iters) *iters = it;
+    if (status) *status = st;
+    free(r); free(d); free(bd);
+    return ORACLE_OK;
+}
+
+typedef struct oracle_hv_ctx {
+    int N, d;
+    const double *v;      /* the point */
+    double delta, h;
+    double *tmp, *gp, *gm;
+    int products;
+} oracle_hv_ctx;
+
+/* B u by a central difference of the exact gradient along u:
+ * |u| (grad F(V + h u/|u|) - grad F(V - h u/|u|)) / (2h). */
+static void lse_hv(const double *u, double *out, void *vctx)
+{
+    oracle_hv_ctx *c = (oracle_hv_ctx *)vctx;
+    int n = 2 * c->d * c->N;
+    double nu = sqrt(vdot(n, u, u));
+    if (!(nu > 0.0)) { for (int i = 0; i < n; ++i) out[i] = 0.0; return; }
+    double F, s, step = c->h / nu;
+    for (int i = 0; i < n; ++i) c->tmp[i] = c->v[i] + step * u[i];
+    oracle_lse(c->N, c->d, c->tmp, c->delta, &F, &s, c->gp);
+    for (int i = 0; i < n; ++i) c->tmp[i] = c->v[i] - step * u[i];
+    oracle_lse(c->N, c->d, c->tmp, c->delta, &F, &s, c->gm);
+    for (int i = 0; i < n; ++i) out[i] = (c->gp[i] - c->gm[i]) * (nu / (2.0 * c->h));
+    c->products++;
+}
+
+/* The product above, for tests. */
+int oracle_lse_hv(int N, int d, const double *v, double delta, double h, const double *u,
+                  double *out)
+{
+    if (N < 2 || d < 1 || !v || !u || !out || !(delta > 0.0) || !(h > 0.0))
+        return ORACLE_EINVAL;
+    size_t n = 2 * (size_t)d * (size_t)N;
+    oracle_hv_ctx c = {N, d, v, delta, h, NULL, NULL, NULL, 0};
+    c.tmp = (double *)malloc(sizeof(double) * n);
+    c.gp = (double *)malloc(sizeof(double) * n);
+    c.gm = (double *)malloc(sizeof(double) * n);
+    if (!c.tmp || !c.gp || !c.gm) { free(c.tmp); free(c.gp); free(c.gm); return ORACLE_EINVAL; }
+    lse_hv(u, out, &c);
+    free(c.tmp); free(c.gp); free(c.gm);
+    return ORACLE_OK;
+}
+
+typedef struct oracle_tr_opts {
+    int n_delta;
+    double delta[16];     /* the smoothing parameters, stage by stage */
+    int max_outer;        /* trust-region iterations per stage */
+    int max_cg;           /* CG iterations per step */
+    double radius0, radius_max, eta, gtol, fd_step;
+} oracle_tr_opts;
+
+typedef struct oracle_tr_row {
+    int32_t stage, iter;
+    double F, s, gnorm, radius, rho, step_norm, pred;
+    int32_t cg_iters, cg_status, accepted, pad;
+} oracle_tr_row;
+
+/*
+ * The paper's procedure on one frame (Sec. "Optimization procedure";
+ * Algorithm "TRSTMI optimization steps", step 2): for each smoothing
+ * parameter delta_k in turn, minimise F_{s,delta_k} over the variable V by
+ * trust-region iterations whose steps come from CG-Steihaug (above), starting
+ * from the previous stage's result.  Per iteration (the standard trust-region
+ * loop, Nocedal and Wright Alg. 4.1): g = grad F; stop the stage when
+ * |g| <= gtol; p from CG-Steihaug with eps = min(1/2, sqrt|g|) |g|;
+ * rho = (F(V) - F(V + p)) / (-m(p)); radius /4 if rho < 1/4, doubled (capped)
+ * if rho > 3/4 and |p| reached it; accept if rho > eta, then every column of
+ * V is divided by its norm (F does not change).  The radius starts at
+ * radius0 in every stage.  v (2dN doubles) is updated in place.
+ */
+int oracle_tr_solve(int N, int d, double *v, const oracle_tr_opts *o, oracle_tr_row *trace,
+                    int cap, int *n_rows)
+{
+    if (N < 2 || d < 1 || !v || !o || o->n_delta < 1 || o->n_delta > 16) return ORACLE_EINVAL;
+    int n = 2 * d * N;
+    size_t bytes = sizeof(double) * (size_t)n;
+    double *g = (double *)malloc(bytes), *p = (double *)malloc(bytes);
+    double *vn = (double *)malloc(bytes);
+    oracle_hv_ctx c = {N, d, v, 0.0, o->fd_step, NULL, NULL, NULL, 0};
+    c.tmp = (double *)malloc(bytes); c.gp = (double *)malloc(bytes);
+    c.gm = (double *)malloc(bytes);
+    int st = ORACLE_OK, rows = 0;
+    if (!g || !p || !vn || !c.tmp || !c.gp || !c.gm) { st = ORACLE_EINVAL; goto out; }
+    st = normalise_columns(N, d, v);
+    if (st != ORACLE_OK) goto out;
+    for (int k = 0; k < o->n_delta; ++k) {
+        double delta = o->delta[k], radius = o->radius0;
+        c.delta = delta;
+        for (int it = 0; it < o->max_outer; ++it) {
+            double F, s, Fn, sn;
+            st = oracle_lse(N, d, v, delta, &F, &s, g);
+            if (st != ORACLE_OK) goto out;
+            double gn = sqrt(vdot(n, g, g));
+            if (gn <= o->gtol) break;
+            double eps = (sqrt(gn) < 0.5 ? sqrt(gn) : 0.5) * gn, m;
+            int cgit, cgst;
+            oracle_cg_steihaug(n, g, lse_hv, &c, radius, eps, o->max_cg, p, &m, &cgit, &cgst);
+            double pn = sqrt(vdot(n, p, p));
+            for (int i = 0; i < n; ++i) vn[i] = v[i] + p[i];
+            st = oracle_lse(N, d, vn, delta, &Fn, &sn, NULL);
+            if (st != ORACLE_OK) goto out;
+            double pred = -m;
+            double rho = pred > 0.0 ? (F - Fn) / pred : -1.0;
+            double r_used = radius;
+            if (rho < 0.25) radius *= 0.25;
+            else if (rho > 0.75 && pn >= (1.0 - 1e-12) * radius)
+                radius = (2.0 * radius < o->radius_max) ? 2.0 * radius : o->radius_max;
+            int acc = rho > o->eta;
+            if (acc) {
+                memcpy(v, vn, bytes);
+                st = normalise_columns(N, d, v);
+                if (st != ORACLE_OK) goto out;
+            }
+            if (trace && rows < cap) {
+                oracle_tr_row *r = &trace[rows];
+                r->stage = k; r->iter = it; r->F = F; r->s = s; r->gnorm = gn;
+                r->radius = r_used; r->rho = rho; r->step_norm = pn; r->pred = pred;
+                r->cg_iters = cgit; r->cg_status = cgst; r->accepted = acc; r->pad = 0;
+            }
+            ++rows;
+            if (radius < 1e-14) break;
+        }
+    }
+out:
+    if (n_rows) *n_rows = rows;
+    free(g); free(p); free(vn); free(c.tmp); free(c.gp); free(c.gm);
+    return st;
+}
