@@ -518,6 +518,72 @@ int trstmi_lse_frames_device(int N, int d, int count, const double *v_dev, doubl
                              int precision, void *scratch_dev, size_t scratch_bytes,
                              double *out_dev, double *grad_dev, void *stream);
 
+/* ------------------------------------ trust-region CG-Steihaug procedure
+ * The paper's optimisation procedure on one frame (Sec. "Optimization
+ * procedure"; Algorithm "TRSTMI optimization steps", step 2): for each
+ * smoothing parameter delta_k in turn (a decreasing sequence), trust-region
+ * iterations on F_{s,delta_k} over the variable V, each step from CG-Steihaug
+ * (Algorithm "Trust-Region CG-Steihaug", after Nocedal and Wright Alg. 7.2),
+ * the result of one stage starting the next.  Per iteration (Nocedal and
+ * Wright Alg. 4.1): g = grad F; the stage ends when |g| <= gtol or after
+ * max_outer iterations or when the radius falls below 1e-14; the step p
+ * solves the model with CG tolerance eps = min(1/2, sqrt|g|) |g| and at most
+ * max_cg iterations; rho = (F(V) - F(V + p)) / (m(0) - m(p)); the radius is
+ * divided by 4 if rho < 1/4 and doubled (up to radius_max) if rho > 3/4 and
+ * the step reached it; the step is taken if rho > eta, after which each
+ * column of V is divided by its norm (F does not change).  The radius starts
+ * at radius0 in every stage.  Hessian products are central differences of
+ * the exact gradient along the direction (step fd_step), in binary64
+ * throughout, on the GPU (F and its gradient by the smooth-maximum kernels,
+ * every vector operation and inner product in device kernels; the host
+ * keeps the scalars).
+ */
+typedef struct trstmi_tr_options {
+  int32_t n_delta;      /* stages, 1..16 */
+  int32_t max_outer;    /* trust-region iterations per stage (default 100) */
+  double delta[16];     /* smoothing parameters (default 0.1, 0.03, 0.01, 0.003, 0.001,
+                           3e-4, 1e-4), each > 0 */
+  int32_t max_cg;       /* CG iterations per step (default 200), >= 1 */
+  int32_t reserved;
+  double radius0;       /* initial radius of every stage (default 0.1), > 0 */
+  double radius_max;    /* radius cap (default 1.0), >= radius0 */
+  double eta;           /* acceptance threshold on rho (default 1e-4), in [0, 1/4) */
+  double gtol;          /* stage ends when |grad F| <= gtol (default 1e-9), >= 0 */
+  double fd_step;       /* Hessian-product difference step (default 1e-6), > 0 */
+} trstmi_tr_options;
+
+/* One row per trust-region iteration. */
+typedef struct trstmi_tr_row {
+  int32_t stage, iter;
+  double F;             /* F_{s,delta} at the iterate */
+  double s;             /* max |G_jk|^2 at the iterate */
+  double gnorm;         /* |grad F| */
+  double radius;        /* radius the step was solved in */
+  double rho;           /* actual / predicted decrease (-1 if the prediction was not positive) */
+  double step_norm;     /* |p| */
+  double pred;          /* m(0) - m(p) */
+  int32_t cg_iters;     /* CG iterations of the step */
+  int32_t cg_status;    /* 0 residual below eps, 1 boundary, 2 negative curvature, 3 limit */
+  int32_t accepted;
+  int32_t reserved;
+} trstmi_tr_row;
+
+/* Fills *o with the defaults listed above. */
+void trstmi_tr_default_options(trstmi_tr_options *o);
+
+/* The procedure on a host frame phi (2*d*N doubles, frame layout), replaced
+ * by the result (unit columns).  trace (nullable): up to cap rows; *n_rows
+ * (nullable): rows produced.  N >= 2, 1 <= d <= 256; a zero column gives
+ * TRSTMI_EINVAL.  Device 0; allocates and frees its device memory. */
+int trstmi_tr_solve(int N, int d, double *phi, const trstmi_tr_options *o,
+                    trstmi_tr_row *trace, int cap, int *n_rows);
+
+/* The procedure applied to an instance's current frame (polishing a
+ * search's result): the frame is replaced by the procedure's result and
+ * recertified, as with trstmi_set_phi. */
+int trstmi_instance_tr_solve(trstmi_handle h, const trstmi_tr_options *o,
+                             trstmi_tr_row *trace, int cap, int *n_rows);
+
 /* ------------------------------------------------- measurement entry point */
 
 /*

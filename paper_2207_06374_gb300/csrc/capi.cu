@@ -1033,6 +1033,70 @@ int trstmi_instance_certificates(trstmi_handle h, double tol, trstmi_certificate
                          h->num_sms, h->stream, out);
 }
 
+void trstmi_tr_default_options(trstmi_tr_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  const double ds[] = {0.1, 0.03, 0.01, 0.003, 0.001, 3e-4, 1e-4};
+  o->n_delta = 7;
+  for (int k = 0; k < 7; ++k) o->delta[k] = ds[k];
+  o->max_outer = 100;
+  o->max_cg = 200;
+  o->radius0 = 0.1;
+  o->radius_max = 1.0;
+  o->eta = 1e-4;
+  o->gtol = 1e-9;
+  o->fd_step = 1e-6;
+}
+
+namespace {
+int tr_check(int N, int d, const trstmi_tr_options* o) {
+  if (N < 2 || d < 1 || d > kMaxD || !o) return TRSTMI_EINVAL;
+  if (o->n_delta < 1 || o->n_delta > 16 || o->max_outer < 0 || o->max_cg < 1) return TRSTMI_EINVAL;
+  for (int k = 0; k < o->n_delta; ++k)
+    if (!(o->delta[k] > 0.0) || !(o->delta[k] < INFINITY)) return TRSTMI_EINVAL;
+  if (!(o->radius0 > 0.0) || !(o->radius_max >= o->radius0) || !(o->eta >= 0.0 && o->eta < 0.25) ||
+      !(o->gtol >= 0.0) || !(o->fd_step > 0.0))
+    return TRSTMI_EINVAL;
+  if ((long long)N * d >= (1ll << 28)) return TRSTMI_ESIZE;
+  return TRSTMI_OK;
+}
+}  // namespace
+
+int trstmi_tr_solve(int N, int d, double* phi, const trstmi_tr_options* o, trstmi_tr_row* trace,
+                    int cap, int* n_rows) {
+  int rc = tr_check(N, d, o);
+  if (rc) return rc;
+  if (!phi || cap < 0) return TRSTMI_EINVAL;
+  int num_sms = 0;
+  if ((rc = ensure_device(0, &num_sms)) != TRSTMI_OK) return rc;
+  const size_t nv = (size_t)N * d * sizeof(double2);
+  const size_t o_scr = align_up(nv, 256);
+  void* buf = nullptr;
+  TRY_CUDA(cudaMalloc(&buf, o_scr + tr_device_bytes(N, d)));
+  char* b = static_cast<char*>(buf);
+  cudaError_t e = cudaMemcpy(b, phi, nv, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    rc = tr_solve_device(N, d, reinterpret_cast<double*>(b), *o, b + o_scr, num_sms, 0, trace,
+                         cap, n_rows, nullptr);
+    if (rc == TRSTMI_OK && cudaMemcpy(phi, b, nv, cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = TRSTMI_ECUDA;
+  } else {
+    rc = record_cuda_error(e, "trust-region frame copy", __LINE__);
+  }
+  cudaFree(buf);
+  return rc;
+}
+
+int trstmi_instance_tr_solve(trstmi_handle h, const trstmi_tr_options* o, trstmi_tr_row* trace,
+                             int cap, int* n_rows) {
+  if (!h) return TRSTMI_EINVAL;
+  std::vector<double> phi(2 * (size_t)h->N * h->d);
+  int rc = trstmi_get_phi(h, phi.data());
+  if (rc) return rc;
+  if ((rc = trstmi_tr_solve(h->N, h->d, phi.data(), o, trace, cap, n_rows)) != TRSTMI_OK) return rc;
+  return trstmi_set_phi(h, phi.data());
+}
+
 int trstmi_screen_wait_test(trstmi_handle h, int precision, double wait_limit_ms) {
   if (!h || !is_screen_precision(precision)) return TRSTMI_EINVAL;
   if (!(wait_limit_ms > 0.0 && wait_limit_ms <= 2000.0)) return TRSTMI_EINVAL;

@@ -138,6 +138,15 @@ cudaError_t launch_screen_wait_test(int fmt, int N, int d, const float2* phi32, 
                                     unsigned long long wait_limit_ns, int num_sms,
                                     cudaStream_t s);
 
+// ------------------------------------------ trust-region procedure (tr.cu)
+// Device bytes the procedure needs beside the variable; the variable v_dev
+// (N x d complex doubles) is replaced by the result.  Returns a TRSTMI_
+// status.
+size_t tr_device_bytes(int N, int d);
+int tr_solve_device(int N, int d, double* v_dev, const trstmi_tr_options& o, void* scratch,
+                    int num_sms, cudaStream_t s, trstmi_tr_row* trace, int cap, int* n_rows,
+                    int* hv_products);
+
 // ------------------------------------------ certificates (diag.cu)
 // max / min of |G_jk|^2 and the distinct distances at resolution tol of a
 // frame (v: device, N x d complex interleaved doubles, normalised inside).

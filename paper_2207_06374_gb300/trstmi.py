@@ -107,6 +107,32 @@ class Certificates(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class TrOptions(ctypes.Structure):
+    _fields_ = [("n_delta", ctypes.c_int32), ("max_outer", ctypes.c_int32),
+                ("delta", ctypes.c_double * 16), ("max_cg", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("radius0", ctypes.c_double),
+                ("radius_max", ctypes.c_double), ("eta", ctypes.c_double),
+                ("gtol", ctypes.c_double), ("fd_step", ctypes.c_double)]
+
+
+TR_ROW_DTYPE = np.dtype([("stage", "<i4"), ("iter", "<i4"), ("F", "<f8"), ("s", "<f8"),
+                         ("gnorm", "<f8"), ("radius", "<f8"), ("rho", "<f8"),
+                         ("step_norm", "<f8"), ("pred", "<f8"), ("cg_iters", "<i4"),
+                         ("cg_status", "<i4"), ("accepted", "<i4"), ("reserved", "<i4")])
+
+
+def tr_options(deltas=None, **kw) -> TrOptions:
+    o = TrOptions()
+    lib().trstmi_tr_default_options(ctypes.byref(o))
+    if deltas is not None:
+        o.n_delta = len(deltas)
+        for i, x in enumerate(deltas):
+            o.delta[i] = x
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
 class MultistartResult(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_double), ("best", ctypes.c_int32), ("trials", ctypes.c_int32),
                 ("best_seed", ctypes.c_uint64)]
@@ -154,6 +180,13 @@ SIGNATURES = {
                                                  ctypes.c_double, ctypes.POINTER(Certificates)]),
     "trstmi_instance_certificates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double,
                                            ctypes.POINTER(Certificates)]),
+    "trstmi_tr_default_options": (None, [ctypes.POINTER(TrOptions)]),
+    "trstmi_tr_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(TrOptions),
+                                       ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]),
+    "trstmi_instance_tr_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TrOptions),
+                                                ctypes.c_void_p, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_int)]),
     "trstmi_multistart": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                          ctypes.c_int, ctypes.c_int, ctypes.POINTER(Options),
                                          ctypes.c_int, ctypes.POINTER(MultistartResult), _dp,
@@ -344,6 +377,15 @@ class Search:
         return _unflat(b, self.d, self.N)
 
 
+    def tr_solve(self, cap: int = 1 << 16, **options):
+        """Polish the current frame with the trust-region procedure; returns the trace."""
+        o = tr_options(**options)
+        tr = np.zeros(max(cap, 1), dtype=TR_ROW_DTYPE)
+        n = ctypes.c_int()
+        _check(lib().trstmi_instance_tr_solve(self._h, ctypes.byref(o), tr.ctypes.data, cap,
+                                              ctypes.byref(n)), "trstmi_instance_tr_solve")
+        return tr[: min(n.value, cap)]
+
     def certificates(self, tol: float = 1e-6) -> dict:
         """Coherence, bounds and distinct distances of the current frame."""
         c = Certificates()
@@ -368,6 +410,20 @@ class Search:
     @property
     def handle(self) -> int:
         return self._h.value
+
+
+def tr_solve(phi: np.ndarray, cap: int = 1 << 16, **options):
+    """The paper's trust-region CG-Steihaug procedure over the smoothing
+    stages on a frame (d, N), on the GPU in binary64.  Returns (the result,
+    unit columns; the per-iteration trace)."""
+    d, N = phi.shape
+    o = tr_options(**options)
+    b = _flat(phi)
+    tr = np.zeros(max(cap, 1), dtype=TR_ROW_DTYPE)
+    n = ctypes.c_int()
+    _check(lib().trstmi_tr_solve(N, d, b.ctypes.data_as(_dp), ctypes.byref(o), tr.ctypes.data,
+                                 cap, ctypes.byref(n)), "trstmi_tr_solve")
+    return _unflat(b, d, N), tr[: min(n.value, cap)]
 
 
 def certificates(phi: np.ndarray, tol: float = 1e-6) -> dict:

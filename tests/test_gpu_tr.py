@@ -1,0 +1,101 @@
+"""The trust-region CG-Steihaug procedure on the GPU against the oracle.
+
+Both sides run the same sequence (smoothing stages, trust-region loop,
+CG-Steihaug steps, Hessian products by central differences of the exact
+gradient) in binary64; they differ only in the order of their sums, which the
+difference quotient amplifies by 1/h (h = 1e-6), so iterates agree to about
+1e-9.  Rows are compared while the gradient is still well above that noise
+(|grad F| > 1e-5): F and s to 1e-8 relative, |grad F| to 1e-4 relative, and
+the discrete decisions (CG iterations and exit, accept) exactly.  The end
+points are compared through their coherence.
+"""
+import numpy as np
+import pytest
+
+import frames as F
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+T = pytest.importorskip("paper_2207_06374_gb300.trstmi")
+
+SCHEDULE = (0.1, 0.03, 0.01, 0.003, 0.001, 3e-4, 1e-4)
+
+
+def _start(d, N, seed):
+    rng = np.random.default_rng(seed)
+    z = rng.standard_normal((d, N)) + 1j * rng.standard_normal((d, N))
+    return z / np.linalg.norm(z, axis=0, keepdims=True)
+
+
+@pytest.mark.parametrize("d,N,seed", [(2, 4, 1), (3, 7, 1), (3, 9, 2), (4, 8, 3), (2, 5, 4)])
+def test_trace_matches_oracle(d, N, seed):
+    v = _start(d, N, seed)
+    phi, tr = T.tr_solve(v, deltas=SCHEDULE, max_outer=100, max_cg=200)
+    ophi, otr = O.tr_solve(v, O.tr_opts(deltas=SCHEDULE, max_outer=100, max_cg=200))
+    k = 0
+    while (k < min(len(tr), len(otr)) and otr["gnorm"][k] > 1e-5
+           and tr["stage"][k] == otr["stage"][k]):
+        a, b = tr[k], otr[k]
+        assert a["F"] == pytest.approx(b["F"], rel=1e-8)
+        assert a["s"] == pytest.approx(b["s"], rel=1e-8)
+        assert a["gnorm"] == pytest.approx(b["gnorm"], rel=1e-4)
+        assert a["radius"] == pytest.approx(b["radius"], rel=1e-8)
+        assert (a["cg_iters"], a["cg_status"], a["accepted"]) == \
+            (b["cg_iters"], b["cg_status"], b["accepted"]), k
+        k += 1
+    assert k >= 5
+    assert np.sqrt(O.mu2(phi)) == pytest.approx(np.sqrt(O.mu2(ophi)), abs=1e-6)
+
+
+@pytest.mark.parametrize("d,N,seed", [(4, 16, 0), (5, 25, 1)])
+def test_reaches_the_sics(d, N, seed):
+    phi, tr = T.tr_solve(_start(d, N, seed), deltas=SCHEDULE)
+    assert np.sqrt(O.mu2(phi)) == pytest.approx(F.welch(N, d), abs=1e-6)
+    assert np.allclose(np.linalg.norm(phi, axis=0), 1.0, atol=1e-14)
+
+
+def test_config_shape_d8_n64_descends_and_obeys_the_rules():
+    v = _start(8, 64, 3)
+    mu0 = np.sqrt(O.mu2(v))
+    phi, tr = T.tr_solve(v, deltas=(0.03, 0.01, 0.003), max_outer=40, max_cg=60)
+    mu1 = np.sqrt(O.mu2(phi))
+    assert mu1 < mu0 - 0.2
+    for a, b in zip(tr[:-1], tr[1:]):
+        if a["stage"] != b["stage"]:
+            continue
+        if a["accepted"]:
+            assert b["F"] <= a["F"] + 1e-14
+        else:
+            assert b["F"] == a["F"]
+        assert a["step_norm"] <= a["radius"] * (1 + 1e-12)
+    # the first rows as the oracle takes them
+    otr = O.tr_solve(v, O.tr_opts(deltas=(0.03,), max_outer=3, max_cg=60))[1]
+    for k in range(len(otr)):
+        assert tr["F"][k] == pytest.approx(otr["F"][k], rel=1e-8)
+        assert tr["cg_iters"][k] == otr["cg_iters"][k]
+
+
+def test_polishing_a_search_result():
+    with T.Search(9, 3, 11, K=64, precision="fp64") as s:
+        s.step(20)
+        mu_before = s.coherence()[0]
+        tr = s.tr_solve(deltas=SCHEDULE)
+        mu_after, welch = s.coherence()
+        assert len(tr) > 0
+        assert mu_after < mu_before
+        assert mu_after == pytest.approx(0.5, abs=1e-6)       # the SIC of C^3
+        assert np.sqrt(O.mu2(s.get_phi())) == pytest.approx(mu_after, rel=1e-12)
+
+
+def test_rejects_bad_options():
+    v = _start(2, 4, 0)
+    for kw in [dict(deltas=()), dict(deltas=(0.1, 0.0)), dict(max_cg=0), dict(eta=0.3),
+               dict(radius0=0.0), dict(fd_step=0.0), dict(radius0=2.0, radius_max=1.0)]:
+        with pytest.raises(T.TrstmiError) as e:
+            T.tr_solve(v, **kw)
+        assert e.value.status == T.TRSTMI_EINVAL
+    z = v.copy()
+    z[:, 1] = 0
+    with pytest.raises(T.TrstmiError):
+        T.tr_solve(z)
