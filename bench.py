@@ -53,8 +53,14 @@ WORKLOADS = {
     "objective_d32_n1024": (32, 1024, 64, "fp32",
                             "the paper's smooth maximum F_{s,delta} (delta = 0.01) and its "
                             "gradient for 64 frames, complex d=32 N=1024, fp32"),
+    # K = trust-region iterations timed
+    "trust_region_d32_n1024": (32, 1024, 5, "fp64",
+                               "the paper's trust-region CG-Steihaug procedure on F_{s,delta} "
+                               "(delta = 0.01, at most 20 CG steps per iteration) for one frame, "
+                               "complex d=32 N=1024, binary64"),
 }
 LSE_DELTA = 0.01
+TR_MAX_CG = 20
 L2_FLUSH_BYTES = 512 << 20
 SEED = 1
 
@@ -153,14 +159,14 @@ KERNEL_SOURCES = {
     "bf16": ["paper_2207_06374_gb300/csrc/tc_screen.cu", "paper_2207_06374_gb300/csrc/philox.cuh",
              "paper_2207_06374_gb300/csrc/common.cuh"],
     "fp32": ["paper_2207_06374_gb300/csrc/simt_kernels.cu", "paper_2207_06374_gb300/csrc/philox.cuh",
-             "paper_2207_06374_gb300/csrc/common.cuh"],
+             "paper_2207_06374_gb300/csrc/common.cuh", "paper_2207_06374_gb300/csrc/tile.cuh"],
 }
 KERNEL_SOURCES["lse"] = ["paper_2207_06374_gb300/csrc/lse.cu", "paper_2207_06374_gb300/csrc/tile.cuh",
                          "paper_2207_06374_gb300/csrc/common.cuh"]
 KERNEL_SOURCES["tf32"] = KERNEL_SOURCES["bf16"]
 KERNEL_SOURCES["batched"] = KERNEL_SOURCES["fp32"]
 KERNEL_PROFILE = {"bf16": "k_screen_bf16_d32_n1024.txt", "tf32": "k_screen_tf32_d32_n768.txt",
-                  "fp32": "k_gram_tile_f32_d32_n1024.txt",
+                  "fp32": "k_gram_planes_f32_d32_n1024.txt",
                   "batched": "k_batch_resident_f32_batched_512.txt",
                   "lse": "k_lse_tile_f32_d32_n1024.txt"}
 
@@ -249,6 +255,29 @@ def run_reference(args, wl):
     if rank != 0:
         return
     d, N, K, prec, desc = WORKLOADS[wl]
+    if wl == "trust_region_d32_n1024":
+        import oracle as O
+        v = lse_frames(1, d, N, SEED)[0]
+        v = v / np.linalg.norm(v, axis=0, keepdims=True)
+        t0 = time.perf_counter()
+        _, tr = O.tr_solve(v, O.tr_opts(deltas=(LSE_DELTA,), max_outer=1, max_cg=3))
+        dt = time.perf_counter() - t0
+        rate = len(tr) / dt
+        line = {"impl": "reference", "metric": "trust-region iterations per second",
+                "value": rate, "unit": "iterations/s", "n_gpus": 1, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dt / max(len(tr), 1) * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic (seeded complex Gaussian frame)",
+                "config": {"workload": wl, "d": d, "N": N, "delta": LSE_DELTA,
+                           "precision": "fp64 oracle",
+                           "sample": f"{len(tr)} iteration(s) with at most 3 CG steps"},
+                "cpu_baseline": {"value": rate, "unit": "iterations/s", "cores": 1,
+                                 "kind": "oracle",
+                                 "sample": f"{len(tr)} iteration(s), at most 3 CG steps, {dt:.1f} s"},
+                "e2e": {"value": rate, "unit": "iterations/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     if wl == "objective_d32_n1024":
         fr = lse_frames(max(1, args.steps) * 8, d, N, SEED)
         rate, done, dt = lse_oracle_rate(d, N, fr)
@@ -331,6 +360,11 @@ def main():
         return
     if wl == "serving":
         run_serving(args, ws, rank, local, dist, torch, T)
+        if dist:
+            dist.destroy_process_group()
+        return
+    if wl == "trust_region_d32_n1024":
+        run_trust_region(args, ws, rank, local, dist, torch, T)
         if dist:
             dist.destroy_process_group()
         return
@@ -702,6 +736,7 @@ def run_objective(args, ws, rank, local, dist, torch, T):
                        "parallelism": f"independent stack per GPU x{ws}"},
             "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
                          "frac": achieved / peak, "traffic": profiled_traffic("lse"),
+                         "traffic_kernel": "k_lse_tile (the call's dominant kernel, 60% of it)",
                          "kernel": "one objective call: k_lse_prepare, k_gram_planes (s), "
                                    "k_lse_tile, k_lse_total, k_lse_finish",
                          "kernel_ms": kernel_ms, "flops_per_launch": flops,
@@ -720,6 +755,84 @@ def run_objective(args, ws, rank, local, dist, torch, T):
         line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{done} of the {K} frames, objective + gradient by the "
                                           f"fp64 oracle (one thread), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_trust_region(args, ws, rank, local, dist, torch, T):
+    """The paper's trust-region CG-Steihaug procedure on one d = 32, N = 1024
+    frame: `steps` trust-region iterations of one smoothing stage (delta =
+    0.01, at most 20 CG steps each) from a seeded random frame, timed on the
+    host clock around the library call (the procedure synchronises on every
+    reduced scalar).  Every objective evaluation is one smooth-maximum pass
+    (F, s and the gradient: 32 d flops per pair)."""
+    d, N, K, prec, desc = WORKLOADS["trust_region_d32_n1024"]
+    steps = max(args.steps, 1)
+    v = lse_frames(1, d, N, SEED + rank)[0]
+    v = v / np.linalg.norm(v, axis=0, keepdims=True)
+    pairs = N * (N - 1) // 2
+    # warm-up: the same call with one iteration
+    for _ in range(max(args.warmup, 1)):
+        T.tr_solve(v, deltas=(LSE_DELTA,), max_outer=1, max_cg=TR_MAX_CG)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        phi, tr = T.tr_solve(v, deltas=(LSE_DELTA,), max_outer=steps, max_cg=TR_MAX_CG)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    clocks = clk.summary()
+    if dist:
+        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt.item())
+    iters = len(tr)
+    hv = int(tr["cg_iters"].sum())
+    evals = 2 * iters + 2 * hv
+    flops = evals * pairs * 32 * d
+    peaks, peak_kind = measured_peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = fp32_alu_peak_tflops(sm_mhz) / 64
+    achieved = flops / dt / 1e12
+    line = {"metric": "trust-region iterations per second (one frame)",
+            "value": ws * iters / dt, "unit": "iterations/s", "n_gpus": ws, "steps": iters,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(iters, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded complex Gaussian frame)",
+            "config": {"workload": "trust_region_d32_n1024", "description": desc, "d": d,
+                       "N": N, "delta": LSE_DELTA, "max_cg": TR_MAX_CG,
+                       "hessian_products": hv, "objective_evaluations": evals,
+                       "F_first": float(tr["F"][0]) if iters else None,
+                       "F_last": float(tr["F"][-1]) if iters else None,
+                       "l2": "the frame and all vectors (about 12 MB) stay in L2; no flush",
+                       "parallelism": f"independent frame per GPU x{ws}"},
+            "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "all smooth-maximum passes of the procedure (binary64), "
+                                   "timed with the host-side scalar logic between them",
+                         "kernel_ms": 1e3 * dt / max(evals, 1),
+                         "flops_per_launch": pairs * 32 * d,
+                         "peak_source": f"fp64 peak derived: 152 SMs x 2 lanes x 2 flops x {sm_mhz} MHz"},
+            "gpu_launches": evals * 5 + (iters + hv) * 8,
+            "e2e": {"value": ws * iters / dt, "unit": "iterations/s",
+                    "h2d_bytes_per_step": int(16 * d * N / max(iters, 1)),
+                    "d2h_bytes_per_step": int(16 * d * N / max(iters, 1)),
+                    "call": "trstmi_tr_solve (host frame in and out; the timed region is "
+                            "this call)"},
+            "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as O
+        t0 = time.perf_counter()
+        _, otr = O.tr_solve(v, O.tr_opts(deltas=(LSE_DELTA,), max_outer=1, max_cg=3))
+        odt = time.perf_counter() - t0
+        ohv = int(otr["cg_iters"].sum())
+        oevals = 2 * len(otr) + 2 * ohv
+        # scaled to the GPU run's evaluations per iteration
+        per_eval = odt / max(oevals, 1)
+        line["cpu_baseline"] = {"value": 1.0 / (per_eval * evals / max(iters, 1)),
+                                "unit": "iterations/s", "cores": 1, "kind": "oracle",
+                                "sample": f"1 iteration with at most 3 CG steps ({oevals} "
+                                          f"objective evaluations, {odt:.1f} s), scaled to "
+                                          f"{evals / max(iters, 1):.1f} evaluations per iteration"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
