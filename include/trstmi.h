@@ -578,6 +578,20 @@ void trstmi_tr_default_options(trstmi_tr_options *o);
 int trstmi_tr_solve(int N, int d, double *phi, const trstmi_tr_options *o,
                     trstmi_tr_row *trace, int cap, int *n_rows);
 
+/* The paper's whole algorithm (Algorithm "TRSTMI optimization steps"): L
+ * random initialisations -- trial i starts from the frame trstmi_create
+ * draws for seed seed0 + i -- each run through the procedure above, and the
+ * minimum over the trials.  The trials advance together as one stack of
+ * frames on the GPU, at most batch_cap at a time (<= 0: all), and each
+ * follows exactly the trajectory trstmi_tr_solve gives it alone.  L <= 0
+ * selects 2 d^2 trials.  out: the minimum of mu over the trials (binary64),
+ * its trial (lowest index on ties) and seed.  mu_all (nullable): L doubles.
+ * best_phi (nullable): 2*d*N doubles, the winning frame.  trace (nullable):
+ * up to cap rows of the winning trial; *n_rows (nullable) its row count. */
+int trstmi_tr_multistart(int N, int d, uint64_t seed0, int L, const trstmi_tr_options *o,
+                         int batch_cap, trstmi_multistart_result *out, double *mu_all,
+                         double *best_phi, trstmi_tr_row *trace, int cap, int *n_rows);
+
 /* The procedure applied to an instance's current frame (polishing a
  * search's result): the frame is replaced by the procedure's result and
  * recertified, as with trstmi_set_phi. */

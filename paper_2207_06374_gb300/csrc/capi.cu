@@ -1072,18 +1072,88 @@ int trstmi_tr_solve(int N, int d, double* phi, const trstmi_tr_options* o, trstm
   const size_t nv = (size_t)N * d * sizeof(double2);
   const size_t o_scr = align_up(nv, 256);
   void* buf = nullptr;
-  TRY_CUDA(cudaMalloc(&buf, o_scr + tr_device_bytes(N, d)));
+  TRY_CUDA(cudaMalloc(&buf, o_scr + tr_device_bytes(N, d, 1)));
   char* b = static_cast<char*>(buf);
   cudaError_t e = cudaMemcpy(b, phi, nv, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    rc = tr_solve_device(N, d, reinterpret_cast<double*>(b), *o, b + o_scr, num_sms, 0, trace,
-                         cap, n_rows, nullptr);
+    TrFrameLog log{trace, cap, 0, 0.0, 0};
+    rc = tr_solve_device(N, d, 1, reinterpret_cast<double*>(b), *o, b + o_scr, num_sms, 0, &log);
+    if (n_rows) *n_rows = log.n;
     if (rc == TRSTMI_OK && cudaMemcpy(phi, b, nv, cudaMemcpyDeviceToHost) != cudaSuccess)
       rc = TRSTMI_ECUDA;
   } else {
     rc = record_cuda_error(e, "trust-region frame copy", __LINE__);
   }
   cudaFree(buf);
+  return rc;
+}
+
+int trstmi_tr_multistart(int N, int d, uint64_t seed0, int L, const trstmi_tr_options* o,
+                         int batch_cap, trstmi_multistart_result* out, double* mu_all,
+                         double* best_phi, trstmi_tr_row* trace, int cap, int* n_rows) {
+  int rc = tr_check(N, d, o);
+  if (rc) return rc;
+  if (!out || cap < 0) return TRSTMI_EINVAL;
+  if (L <= 0) L = 2 * d * d;
+  const int B = batch_cap > 0 ? std::min(batch_cap, L) : L;
+  int num_sms = 0;
+  if ((rc = ensure_device(0, &num_sms)) != TRSTMI_OK) return rc;
+  const size_t nv = (size_t)N * d * sizeof(double2);
+  const size_t o_f32 = align_up(nv * B, 256);
+  const size_t o_scr = o_f32 + align_up(nv / 2, 256);
+  void* buf = nullptr;
+  TRY_CUDA(cudaMalloc(&buf, o_scr + tr_device_bytes(N, d, B)));
+  char* b = static_cast<char*>(buf);
+  std::vector<double> mu(L);
+  std::vector<TrFrameLog> logs(B);
+  int best = 0;
+  for (int b0 = 0; b0 < L && rc == TRSTMI_OK; b0 += B) {
+    const int n = std::min(B, L - b0);
+    // every trial starts from the frame trstmi_create draws for its seed
+    for (int i = 0; i < n; ++i) {
+      cudaError_t e = launch_init_frame(N, d, seed0 + (uint64_t)(b0 + i),
+                                        reinterpret_cast<double2*>(b + nv * i),
+                                        reinterpret_cast<float2*>(b + o_f32), nullptr, 0);
+      if (e != cudaSuccess) { rc = record_cuda_error(e, "trial initialisation", __LINE__); break; }
+    }
+    if (rc) break;
+    for (int i = 0; i < n; ++i) logs[i] = TrFrameLog{nullptr, 0, 0, 0.0, 0};
+    rc = tr_solve_device(N, d, n, reinterpret_cast<double*>(b), *o, b + o_scr, num_sms, 0,
+                         logs.data());
+    if (rc) break;
+    for (int i = 0; i < n; ++i) {
+      mu[b0 + i] = std::sqrt(logs[i].mu2);
+      if (b0 + i == 0 || mu[b0 + i] < mu[best]) {
+        best = b0 + i;
+        if (best_phi && cudaMemcpy(best_phi, b + nv * i, nv, cudaMemcpyDeviceToHost) != cudaSuccess)
+          rc = TRSTMI_ECUDA;
+      }
+    }
+  }
+  cudaFree(buf);
+  if (rc) return rc;
+  out->mu = mu[best];
+  out->best = best;
+  out->trials = L;
+  out->best_seed = seed0 + (uint64_t)best;
+  if (mu_all) std::copy(mu.begin(), mu.end(), mu_all);
+  if (n_rows) *n_rows = 0;
+  if (trace || n_rows) {
+    // the winning trial alone again: the same trajectory, so the same rows
+    void* one = nullptr;
+    TRY_CUDA(cudaMalloc(&one, align_up(nv, 256) + align_up(nv / 2, 256) + tr_device_bytes(N, d, 1)));
+    char* c = static_cast<char*>(one);
+    cudaError_t e = launch_init_frame(N, d, out->best_seed, reinterpret_cast<double2*>(c),
+                                      reinterpret_cast<float2*>(c + align_up(nv, 256)), nullptr, 0);
+    TrFrameLog log{trace, cap, 0, 0.0, 0};
+    if (e == cudaSuccess)
+      rc = tr_solve_device(N, d, 1, reinterpret_cast<double*>(c), *o,
+                           c + align_up(nv, 256) + align_up(nv / 2, 256), num_sms, 0, &log);
+    else
+      rc = record_cuda_error(e, "trial initialisation", __LINE__);
+    if (n_rows) *n_rows = log.n;
+    cudaFree(one);
+  }
   return rc;
 }
 

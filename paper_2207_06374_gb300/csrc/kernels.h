@@ -139,13 +139,20 @@ cudaError_t launch_screen_wait_test(int fmt, int N, int d, const float2* phi32, 
                                     cudaStream_t s);
 
 // ------------------------------------------ trust-region procedure (tr.cu)
-// Device bytes the procedure needs beside the variable; the variable v_dev
-// (N x d complex doubles) is replaced by the result.  Returns a TRSTMI_
-// status.
-size_t tr_device_bytes(int N, int d);
-int tr_solve_device(int N, int d, double* v_dev, const trstmi_tr_options& o, void* scratch,
-                    int num_sms, cudaStream_t s, trstmi_tr_row* trace, int cap, int* n_rows,
-                    int* hv_products);
+// L frames advance together, each exactly as it would alone.  Device bytes
+// the procedure needs beside the frames; v_dev (L x N x d complex doubles)
+// is replaced by the results.  logs (nullable, L entries): each frame's trace
+// rows (up to cap; n counts them all), its final max |G_jk|^2 and Hessian
+// products.  Returns a TRSTMI_ status.
+struct TrFrameLog {
+  trstmi_tr_row* rows;
+  int cap, n;
+  double mu2;
+  int hv_products;
+};
+size_t tr_device_bytes(int N, int d, int L);
+int tr_solve_device(int N, int d, int L, double* v_dev, const trstmi_tr_options& o,
+                    void* scratch, int num_sms, cudaStream_t s, TrFrameLog* logs);
 
 // ------------------------------------------ certificates (diag.cu)
 // max / min of |G_jk|^2 and the distinct distances at resolution tol of a
@@ -166,6 +173,10 @@ cudaError_t init_diag_attributes(int optin);
 size_t lse_scratch_bytes(int N, int d, int count, bool f64);
 cudaError_t launch_lse(int N, int d, int count, const double* v, double delta, bool f64,
                        void* scratch, double* out, double* grad, int num_sms, cudaStream_t s);
+// The same with a smoothing parameter per frame (deltas: device, count doubles, > 0).
+cudaError_t launch_lse_deltas(int N, int d, int count, const double* v, const double* deltas,
+                              bool f64, void* scratch, double* out, double* grad, int num_sms,
+                              cudaStream_t s);
 cudaError_t init_lse_attributes(int optin);
 
 // ------------------------------------------------------ batched searches

@@ -45,6 +45,7 @@ constexpr int kLseThreads = 256;
 template <typename T> struct LseArgs {
   int N, d, nb, ntiles, count;
   double delta;
+  const double* deltas;     // count smoothing parameters (device), or null: delta for all
   const double* v;          // count x N x d complex (interleaved), caller's variables
   T* planes;                // count x [d x N re][d x N im] unit columns
   T* rnorm;                 // count x N column norms
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(kLseThreads) k_lse_tile(const LseArgs<T> a) {
     int I, J;
     tile_coords(tau, I, J);
     const T s = nonneg_from_bits(a.smax[slot]);
-    const T delta = (T)a.delta;
+    const T delta = (T)(a.deltas ? a.deltas[slot] : a.delta);
     const T* bI = stage0 + sg * stage;
     const T* bJ = I == J ? bI : bI + (size_t)2 * d * BT;
     // G of the tile, as in the search's tile pass
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(kLseThreads) k_lse_total(const LseArgs<T> a) {
     if (a.bad[slot]) {
       o[0] = o[1] = o[2] = __longlong_as_double(0x7ff8000000000000ll);
     } else {
-      o[0] = s + a.delta * log(v);
+      o[0] = s + (a.deltas ? a.deltas[slot] : a.delta) * log(v);
       o[1] = s;
       o[2] = v;
     }
@@ -481,13 +482,15 @@ cudaError_t lse_launch_R(const LseArgs<T>& a, int num_sms, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t lse_run(int N, int d, int count, const double* v, double delta, void* scratch,
+cudaError_t lse_run(int N, int d, int count, const double* v, double delta,
+                    const double* deltas, void* scratch,
                     double* out, double* grad, int num_sms, cudaStream_t s) {
   const LseLayout<T> L = lse_layout<T>(N, d, count);
   unsigned char* b = static_cast<unsigned char*>(scratch);
   LseArgs<T> a;
   a.N = N; a.d = d; a.nb = L.nb; a.ntiles = L.ntiles; a.count = count;
   a.delta = delta;
+  a.deltas = deltas;
   a.v = v;
   a.planes = reinterpret_cast<T*>(b + L.o_planes);
   a.rnorm = reinterpret_cast<T*>(b + L.o_rnorm);
@@ -530,8 +533,16 @@ size_t lse_scratch_bytes(int N, int d, int count, bool f64) {
 cudaError_t launch_lse(int N, int d, int count, const double* v, double delta, bool f64,
                        void* scratch, double* out, double* grad, int num_sms, cudaStream_t s) {
   if (N < 2 || d < 1 || d > kMaxD || count < 1 || !(delta > 0.0)) return cudaErrorInvalidValue;
-  return f64 ? lse_run<double>(N, d, count, v, delta, scratch, out, grad, num_sms, s)
-             : lse_run<float>(N, d, count, v, delta, scratch, out, grad, num_sms, s);
+  return f64 ? lse_run<double>(N, d, count, v, delta, nullptr, scratch, out, grad, num_sms, s)
+             : lse_run<float>(N, d, count, v, delta, nullptr, scratch, out, grad, num_sms, s);
+}
+
+cudaError_t launch_lse_deltas(int N, int d, int count, const double* v, const double* deltas,
+                              bool f64, void* scratch, double* out, double* grad, int num_sms,
+                              cudaStream_t s) {
+  if (N < 2 || d < 1 || d > kMaxD || count < 1 || !deltas) return cudaErrorInvalidValue;
+  return f64 ? lse_run<double>(N, d, count, v, 0.0, deltas, scratch, out, grad, num_sms, s)
+             : lse_run<float>(N, d, count, v, 0.0, deltas, scratch, out, grad, num_sms, s);
 }
 
 cudaError_t init_lse_attributes(int optin) {

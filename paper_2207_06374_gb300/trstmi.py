@@ -184,6 +184,11 @@ SIGNATURES = {
     "trstmi_tr_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(TrOptions),
                                        ctypes.c_void_p, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int)]),
+    "trstmi_tr_multistart": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                            ctypes.c_int, ctypes.POINTER(TrOptions),
+                                            ctypes.c_int, ctypes.POINTER(MultistartResult), _dp,
+                                            _dp, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int)]),
     "trstmi_instance_tr_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TrOptions),
                                                 ctypes.c_void_p, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_int)]),
@@ -424,6 +429,29 @@ def tr_solve(phi: np.ndarray, cap: int = 1 << 16, **options):
     _check(lib().trstmi_tr_solve(N, d, b.ctypes.data_as(_dp), ctypes.byref(o), tr.ctypes.data,
                                  cap, ctypes.byref(n)), "trstmi_tr_solve")
     return _unflat(b, d, N), tr[: min(n.value, cap)]
+
+
+def tr_multistart(N: int, d: int, seed0: int, L: int = 0, batch_cap: int = 0,
+                  want_phi: bool = True, trace_cap: int = 0, **options):
+    """The paper's whole algorithm: L random initialisations (seeds seed0 ..,
+    the frames trstmi_create draws; L <= 0: 2 d^2), each through the
+    trust-region procedure, advanced together on the GPU; the minimum over
+    the trials.  Returns (result, mu of every trial, the winning frame or
+    None, the winning trial's trace)."""
+    o = tr_options(**options)
+    trials = L if L > 0 else 2 * d * d
+    res = MultistartResult()
+    mus = np.zeros(trials)
+    phi = np.zeros(2 * d * N) if want_phi else None
+    tr = np.zeros(max(trace_cap, 1), dtype=TR_ROW_DTYPE)
+    n = ctypes.c_int()
+    _check(lib().trstmi_tr_multistart(N, d, seed0, L, ctypes.byref(o), batch_cap,
+                                      ctypes.byref(res), mus.ctypes.data_as(_dp),
+                                      phi.ctypes.data_as(_dp) if want_phi else None,
+                                      tr.ctypes.data if trace_cap > 0 else None, trace_cap,
+                                      ctypes.byref(n)), "trstmi_tr_multistart")
+    return (res, mus, (_unflat(phi, d, N) if want_phi else None),
+            tr[: min(n.value, trace_cap)] if trace_cap > 0 else None)
 
 
 def certificates(phi: np.ndarray, tol: float = 1e-6) -> dict:

@@ -99,3 +99,47 @@ def test_rejects_bad_options():
     z[:, 1] = 0
     with pytest.raises(T.TrstmiError):
         T.tr_solve(z)
+
+
+# ----------------------------------------- the whole algorithm: L trials together
+
+def _init(N, d, seed):
+    with T.Search(N, d, seed, K=1) as s:
+        return s.get_phi()
+
+
+def test_trials_advance_together_exactly_as_alone():
+    N, d, seed0, L = 9, 3, 20, 5
+    kw = dict(deltas=(0.1, 0.01, 0.001), max_outer=40, max_cg=50)
+    res, mus, phi, tr = T.tr_multistart(N, d, seed0, L, trace_cap=4096, **kw)
+    assert res.trials == L
+    for i in range(L):
+        solo_phi, solo_tr = T.tr_solve(_init(N, d, seed0 + i), **kw)
+        assert np.sqrt(O.mu2(solo_phi)) == pytest.approx(mus[i], rel=1e-13)
+        if i == res.best:
+            assert np.array_equal(solo_phi, phi)
+            assert np.array_equal(solo_tr, tr)
+    assert res.best == int(np.argmin(mus)) and res.mu == mus[res.best]
+
+
+def test_trials_match_the_oracle_and_batches_change_nothing():
+    N, d, seed0, L = 8, 4, 3, 6
+    kw = dict(deltas=SCHEDULE, max_outer=100, max_cg=200)
+    a = T.tr_multistart(N, d, seed0, L, **kw)
+    b = T.tr_multistart(N, d, seed0, L, batch_cap=4, **kw)
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    for i in range(L):
+        ophi, _ = O.tr_solve(O.init(N, d, seed0 + i), O.tr_opts(deltas=SCHEDULE, max_outer=100,
+                                                                 max_cg=200))
+        assert a[1][i] == pytest.approx(np.sqrt(O.mu2(ophi)), abs=1e-6)
+
+
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_the_papers_table_2_shapes_with_2d2_trials(d):
+    """Algorithm "TRSTMI optimization steps" with L = 2 d^2 at N = d^2: the
+    minimum over the trials is no worse than Table 2 (values rounded up)."""
+    table = {2: 0.5774, 3: 0.5001, 4: 0.4473}
+    res, mus, phi, _ = T.tr_multistart(d * d, d, 1, 0, deltas=SCHEDULE)
+    assert res.trials == 2 * d * d
+    assert res.mu <= table[d]
+    assert np.sqrt(O.mu2(phi)) == pytest.approx(res.mu, rel=1e-12)
