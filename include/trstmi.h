@@ -544,7 +544,12 @@ typedef struct trstmi_tr_options {
   double delta[16];     /* smoothing parameters (default 0.1, 0.03, 0.01, 0.003, 0.001,
                            3e-4, 1e-4), each > 0 */
   int32_t max_cg;       /* CG iterations per step (default 200), >= 1 */
-  int32_t reserved;
+  int32_t path;         /* 0 (default): frames that fit in one CTA's shared memory (up
+                           to about d = 9, N = 81) run resident, one CTA per frame,
+                           larger ones as a stack driven from the host; 1: always the
+                           stack; 2: always resident (TRSTMI_EUNSUPPORTED if a frame
+                           does not fit).  Both run the same algorithm; their sums
+                           are ordered differently. */
   double radius0;       /* initial radius of every stage (default 0.1), > 0 */
   double radius_max;    /* radius cap (default 1.0), >= radius0 */
   double eta;           /* acceptance threshold on rho (default 1e-4), in [0, 1/4) */

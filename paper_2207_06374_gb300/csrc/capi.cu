@@ -1052,6 +1052,7 @@ namespace {
 int tr_check(int N, int d, const trstmi_tr_options* o) {
   if (N < 2 || d < 1 || d > kMaxD || !o) return TRSTMI_EINVAL;
   if (o->n_delta < 1 || o->n_delta > 16 || o->max_outer < 0 || o->max_cg < 1) return TRSTMI_EINVAL;
+  if (o->path < 0 || o->path > 2) return TRSTMI_EINVAL;
   for (int k = 0; k < o->n_delta; ++k)
     if (!(o->delta[k] > 0.0) || !(o->delta[k] < INFINITY)) return TRSTMI_EINVAL;
   if (!(o->radius0 > 0.0) || !(o->radius_max >= o->radius0) || !(o->eta >= 0.0 && o->eta < 0.25) ||
@@ -1072,7 +1073,7 @@ int trstmi_tr_solve(int N, int d, double* phi, const trstmi_tr_options* o, trstm
   const size_t nv = (size_t)N * d * sizeof(double2);
   const size_t o_scr = align_up(nv, 256);
   void* buf = nullptr;
-  TRY_CUDA(cudaMalloc(&buf, o_scr + tr_device_bytes(N, d, 1)));
+  TRY_CUDA(cudaMalloc(&buf, o_scr + tr_device_bytes(N, d, 1, cap)));
   char* b = static_cast<char*>(buf);
   cudaError_t e = cudaMemcpy(b, phi, nv, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
@@ -1102,7 +1103,7 @@ int trstmi_tr_multistart(int N, int d, uint64_t seed0, int L, const trstmi_tr_op
   const size_t o_f32 = align_up(nv * B, 256);
   const size_t o_scr = o_f32 + align_up(nv / 2, 256);
   void* buf = nullptr;
-  TRY_CUDA(cudaMalloc(&buf, o_scr + tr_device_bytes(N, d, B)));
+  TRY_CUDA(cudaMalloc(&buf, o_scr + tr_device_bytes(N, d, B, 0)));
   char* b = static_cast<char*>(buf);
   std::vector<double> mu(L);
   std::vector<TrFrameLog> logs(B);
@@ -1141,7 +1142,7 @@ int trstmi_tr_multistart(int N, int d, uint64_t seed0, int L, const trstmi_tr_op
   if (trace || n_rows) {
     // the winning trial alone again: the same trajectory, so the same rows
     void* one = nullptr;
-    TRY_CUDA(cudaMalloc(&one, align_up(nv, 256) + align_up(nv / 2, 256) + tr_device_bytes(N, d, 1)));
+    TRY_CUDA(cudaMalloc(&one, align_up(nv, 256) + align_up(nv / 2, 256) + tr_device_bytes(N, d, 1, cap)));
     char* c = static_cast<char*>(one);
     cudaError_t e = launch_init_frame(N, d, out->best_seed, reinterpret_cast<double2*>(c),
                                       reinterpret_cast<float2*>(c + align_up(nv, 256)), nullptr, 0);

@@ -150,7 +150,7 @@ struct TrFrameLog {
   double mu2;
   int hv_products;
 };
-size_t tr_device_bytes(int N, int d, int L);
+size_t tr_device_bytes(int N, int d, int L, int trace_cap);
 int tr_solve_device(int N, int d, int L, double* v_dev, const trstmi_tr_options& o,
                     void* scratch, int num_sms, cudaStream_t s, TrFrameLog* logs);
 

@@ -75,6 +75,48 @@ __global__ void __launch_bounds__(kDotThreads) k_dots(long long n, const double*
   }
 }
 
+// frame f = blockIdx.x: the five products of a CG-Steihaug step, in the same
+// order of operations as k_dots: out[5f..5f+4] = d.Bd, d.r, p.p, p.d, d.d
+__global__ void __launch_bounds__(kDotThreads) k_dots5(long long n, const double* dv,
+                                                       const double* bd, const double* r,
+                                                       const double* p, double* out) {
+  __shared__ double red[5][kDotThreads];
+  const long long base = blockIdx.x * n;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = dv[base + i], pi = p[base + i];
+    a0 += x * bd[base + i];
+    a1 += x * r[base + i];
+    a2 += pi * pi;
+    a3 += pi * x;
+    a4 += x * x;
+  }
+  red[0][threadIdx.x] = a0; red[1][threadIdx.x] = a1; red[2][threadIdx.x] = a2;
+  red[3][threadIdx.x] = a3; red[4][threadIdx.x] = a4;
+  __syncthreads();
+  for (int s = kDotThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < 5; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) out[5 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// the coefficients of a Hessian product from nu^2 = u.u (dots[3f]): the step
+// h / nu along u, and nu / 2h for the difference (zeros when u = 0).  Layout of
+// c: [1 ...][step ...][-step ...][nu/2h ...][-nu/2h ...], L each.
+__global__ void k_hv_coef(int L, const double* dots, double h, double* c) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= L) return;
+  const double nu = sqrt(dots[3 * f]);
+  const double step = nu > 0.0 ? h / nu : 0.0, q = nu > 0.0 ? nu / (2.0 * h) : 0.0;
+  c[f] = 1.0;
+  c[L + f] = step;
+  c[2 * L + f] = -step;
+  c[3 * L + f] = q;
+  c[4 * L + f] = -q;
+}
+
 // where flag[f]: frame f's columns divided by their norms (a zero column sets bad[f])
 __global__ void k_unit_columns(int N, int d, int L, double2* v, const int* flag, uint32_t* bad) {
   const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -103,7 +145,7 @@ struct Stack {
   int num_sms;
   cudaStream_t s;
   double *x, *xn, *g, *p, *r, *dv, *bd, *tmp, *gp, *gm;
-  double *out, *dots, *coef, *deltas;
+  double *out, *dots, *coef, *deltas, *hvc;
   int* flag;
   uint32_t* bad;
   void* lse;
@@ -150,12 +192,20 @@ struct Stack {
     q.assign(h_dots, h_dots + 3 * L);
     return e;
   }
-  cudaError_t norms(const double* x1, std::vector<double>& nrm) {
-    std::vector<double> q;
-    cudaError_t e = dots3(x1, x1, nullptr, q);
-    nrm.resize(L);
-    for (int f = 0; f < L; ++f) nrm[f] = std::sqrt(q[3 * f]);
+  // the five products of a CG-Steihaug step, q[5f..5f+4] = d.Bd, d.r, p.p, p.d, d.d
+  cudaError_t dots5(std::vector<double>& q) {
+    k_dots5<<<L, kDotThreads, 0, s>>>(n, dv, bd, r, p, dots);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_dots, dots, 5 * L * sizeof(double),
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = sync();
+    q.assign(h_dots, h_dots + 5 * L);
     return e;
+  }
+  // the gradient at v with the smoothing parameters already on the device
+  // (enqueued only: nothing is read back)
+  cudaError_t gradient_async(const double* v, double* grad) {
+    return launch_lse_deltas(N, d, L, v, deltas, true, lse, out, grad, num_sms, s);
   }
   // F and s of every frame at v (smoothing parameter per frame), gradient into grad
   cudaError_t objective(const double* v, const std::vector<double>& delta, double* grad,
@@ -175,22 +225,23 @@ struct Stack {
     }
     return e;
   }
-  // o = B u, frame by frame: |u| (grad F(x + h u/|u|) - grad F(x - h u/|u|)) / (2h)
-  cudaError_t hv(const double* u, const std::vector<double>& delta, double h, double* o) {
-    std::vector<double> nu, step(L), c(L), F;
-    cudaError_t e = norms(u, nu);
+  // o = B u, frame by frame: |u| (grad F(x + h u/|u|) - grad F(x - h u/|u|)) / (2h),
+  // with the smoothing parameters of the current round already on the device;
+  // enqueued only (the coefficients are formed on the device)
+  cudaError_t hv(const double* u, double h, double* o) {
+    k_dots<<<L, kDotThreads, 0, s>>>(n, u, u, nullptr, dots);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    for (int f = 0; f < L; ++f) {
-      step[f] = nu[f] > 0.0 ? h / nu[f] : 0.0;
-      c[f] = nu[f] > 0.0 ? nu[f] / (2.0 * h) : 0.0;
-    }
-    std::vector<double> nstep(L), nc(L);
-    for (int f = 0; f < L; ++f) { nstep[f] = -step[f]; nc[f] = -c[f]; }
-    if ((e = axpby(1.0, x, step, u, tmp)) != cudaSuccess) return e;
-    if ((e = objective(tmp, delta, gp, F, nullptr)) != cudaSuccess) return e;
-    if ((e = axpby(1.0, x, nstep, u, tmp)) != cudaSuccess) return e;
-    if ((e = objective(tmp, delta, gm, F, nullptr)) != cudaSuccess) return e;
-    return axpby(c, gp, nc, gm, o);
+    k_hv_coef<<<(L + 127) / 128, 128, 0, s>>>(L, dots, h, hvc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_axpby<<<grid(), 256, 0, s>>>(n, total, hvc, x, hvc + L, u, tmp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = gradient_async(tmp, gp)) != cudaSuccess) return e;
+    k_axpby<<<grid(), 256, 0, s>>>(n, total, hvc, x, hvc + 2 * L, u, tmp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = gradient_async(tmp, gm)) != cudaSuccess) return e;
+    k_axpby<<<grid(), 256, 0, s>>>(n, total, hvc + 3 * L, gp, hvc + 4 * L, gm, o);
+    return cudaGetLastError();
   }
   // where want[f]: frame f's columns to unit norm; false if a column was zero
   cudaError_t unit(double* v, const std::vector<int>& want, bool* ok) {
@@ -218,6 +269,11 @@ struct Stack {
 };
 
 // tau >= 0 (pos) or <= 0 with |z + tau d| = radius, from z.z, z.d, d.d
+__device__ double to_boundary_dev(double zz, double zd, double dd, double radius, bool pos) {
+  double disc = zd * zd - dd * (zz - radius * radius);
+  if (disc < 0.0) disc = 0.0;
+  return pos ? (-zd + sqrt(disc)) / dd : (-zd - sqrt(disc)) / dd;
+}
 double to_boundary(double zz, double zd, double dd, double radius, bool pos) {
   double disc = zd * zd - dd * (zz - radius * radius);
   if (disc < 0.0) disc = 0.0;
@@ -226,7 +282,7 @@ double to_boundary(double zz, double zd, double dd, double radius, bool pos) {
 
 // CG-Steihaug for the frames with step[f] (the others keep p = 0): the
 // paper's Algorithm, frame by frame, on m(p) = g.p + p.Bp / 2, |p| <= radius.
-cudaError_t cg_steihaug(Stack& T, const std::vector<double>& delta, double h,
+cudaError_t cg_steihaug(Stack& T, double h,
                         const std::vector<double>& radius, const std::vector<double>& eps,
                         const std::vector<int>& step, int maxit, std::vector<double>& m,
                         std::vector<int>& iters, std::vector<int>& status,
@@ -250,18 +306,17 @@ cudaError_t cg_steihaug(Stack& T, const std::vector<double>& delta, double h,
     if (step[f] && !(std::sqrt(rr[f]) < eps[f])) { active[f] = 1; ++n_active; }
   }
   for (int it = 0; it < maxit && n_active > 0; ++it) {
-    if ((e = T.hv(T.dv, delta, h, T.bd)) != cudaSuccess) return e;
+    if ((e = T.hv(T.dv, h, T.bd)) != cudaSuccess) return e;
     for (int f = 0; f < L; ++f) products[f] += active[f];
-    std::vector<double> dq, zq;
-    if ((e = T.dots3(T.dv, T.bd, T.r, dq)) != cudaSuccess) return e;   // d.Bd, d.r
-    if ((e = T.dots3(T.p, T.p, T.dv, zq)) != cudaSuccess) return e;    // z.z, z.d, d.d
+    std::vector<double> dq;
+    if ((e = T.dots5(dq)) != cudaSuccess) return e;   // d.Bd, d.r, z.z, z.d, d.d
     std::vector<double> tp(L, 0.0), tr(L, 0.0);
     std::vector<int> cont(L, 0);
     int n_cont = 0;
     for (int f = 0; f < L; ++f) {
       if (!active[f]) continue;
-      const double dbd = dq[3 * f], rd = dq[3 * f + 1];
-      const double zz = zq[3 * f], zd = zq[3 * f + 1], dd = zq[3 * f + 2];
+      const double dbd = dq[5 * f], rd = dq[5 * f + 1];
+      const double zz = dq[5 * f + 2], zd = dq[5 * f + 3], dd = dq[5 * f + 4];
       if (dbd <= 0.0) {
         const double t1 = to_boundary(zz, zd, dd, radius[f], true);
         const double t2 = to_boundary(zz, zd, dd, radius[f], false);
@@ -312,15 +367,20 @@ cudaError_t cg_steihaug(Stack& T, const std::vector<double>& delta, double h,
 
 }  // namespace
 
-size_t tr_device_bytes(int N, int d, int L) {
+size_t tr_device_bytes(int N, int d, int L, int trace_cap) {
   const size_t vec = ((size_t)L * 2 * d * N * sizeof(double) + 255) & ~(size_t)255;
-  const size_t small = (((size_t)L * (2 + 3 + 2 * kCoefRing + 1) * sizeof(double) +
+  const size_t small = (((size_t)L * (2 + 5 + 2 * kCoefRing + 1 + 5) * sizeof(double) +
                          (size_t)L * (sizeof(int) + sizeof(uint32_t))) + 255) & ~(size_t)255;
-  return 10 * vec + small + lse_scratch_bytes(N, d, L, true);
+  const size_t stack = 10 * vec + small + lse_scratch_bytes(N, d, L, true);
+  // the resident path: per frame mu^2 and three ints, then the trace rows
+  const size_t resident = (((size_t)L * 20 + 255) & ~(size_t)255) +
+                          (size_t)L * std::max(trace_cap, 0) * sizeof(trstmi_tr_row);
+  return std::max(stack, resident);
 }
 
-int tr_solve_device(int N, int d, int L, double* v_dev, const trstmi_tr_options& o,
-                    void* scratch, int num_sms, cudaStream_t s, TrFrameLog* logs) {
+namespace {
+int tr_solve_stack(int N, int d, int L, double* v_dev, const trstmi_tr_options& o,
+                   void* scratch, int num_sms, cudaStream_t s, TrFrameLog* logs) {
   Stack T;
   T.N = N; T.d = d; T.L = L; T.n = 2LL * d * N; T.total = T.n * L;
   T.num_sms = num_sms; T.s = s;
@@ -331,22 +391,23 @@ int tr_solve_device(int N, int d, int L, double* v_dev, const trstmi_tr_options&
   double* small = reinterpret_cast<double*>(b + 9 * vec);
   T.out = small;
   T.dots = T.out + 2 * L;
-  T.coef = T.dots + 3 * L;
+  T.coef = T.dots + 5 * L;
   T.deltas = T.coef + 2 * (size_t)kCoefRing * L;
-  T.flag = reinterpret_cast<int*>(T.deltas + L);
+  T.hvc = T.deltas + L;
+  T.flag = reinterpret_cast<int*>(T.hvc + 5 * L);
   T.bad = reinterpret_cast<uint32_t*>(T.flag + L);
-  const size_t small_bytes = (((size_t)L * (2 + 3 + 2 * kCoefRing + 1) * sizeof(double) +
+  const size_t small_bytes = (((size_t)L * (2 + 5 + 2 * kCoefRing + 1 + 5) * sizeof(double) +
                                (size_t)L * (sizeof(int) + sizeof(uint32_t))) + 255) & ~(size_t)255;
   T.lse = b + 9 * vec + small_bytes;
   T.x = v_dev;
   void* pinned = nullptr;
-  const size_t pinned_bytes = (size_t)L * (2 * kCoefRing + 2 + 3 + 1) * sizeof(double) +
+  const size_t pinned_bytes = (size_t)L * (2 * kCoefRing + 2 + 5 + 1) * sizeof(double) +
                               (size_t)L * (sizeof(int) + sizeof(uint32_t));
   if (cudaMallocHost(&pinned, pinned_bytes) != cudaSuccess) return TRSTMI_ENOMEM;
   T.h_coef = static_cast<double*>(pinned);
   T.h_out = T.h_coef + 2 * (size_t)kCoefRing * L;
   T.h_dots = T.h_out + 2 * L;
-  T.h_deltas = T.h_dots + 3 * L;
+  T.h_deltas = T.h_dots + 5 * L;
   T.h_flag = reinterpret_cast<int*>(T.h_deltas + L);
   T.h_bad = reinterpret_cast<uint32_t*>(T.h_flag + L);
 
@@ -385,7 +446,8 @@ int tr_solve_device(int N, int d, int L, double* v_dev, const trstmi_tr_options&
     if (n_step == 0) continue;
     std::vector<double> m;
     std::vector<int> cgit, cgst;
-    if ((e = cg_steihaug(T, delta, o.fd_step, radius, eps, step, o.max_cg, m, cgit, cgst,
+    // the round's smoothing parameters stay on the device for the Hessian products
+    if ((e = cg_steihaug(T, o.fd_step, radius, eps, step, o.max_cg, m, cgit, cgst,
                          products)) != cudaSuccess)
       break;
     if ((e = T.dots3(T.p, T.p, nullptr, pq)) != cudaSuccess) break;
@@ -432,6 +494,359 @@ int tr_solve_device(int N, int d, int L, double* v_dev, const trstmi_tr_options&
   cudaFreeHost(pinned);
   if (rc != TRSTMI_OK) return rc;
   return e == cudaSuccess ? TRSTMI_OK : TRSTMI_ECUDA;
+}
+
+// ------------------------------------------------- frames resident in one CTA
+// For frames small enough to live in shared memory (the paper's Table 2 shapes
+// up to d = 9, N = 81), one CTA runs a frame's whole procedure: every vector in
+// shared memory, F and its gradient formed by the CTA (pairs j < k spread over
+// the threads, a fixed order in every sum), inner products by a fixed tree, the
+// algorithms' scalar logic computed by every thread from the same reduced
+// values.  No host round trip and no other frame to wait for: L trials are L
+// independent CTAs.  Every loop is bounded by the options (stages x max_outer x
+// max_cg).
+
+constexpr int kResThreads = 256;
+
+struct ResArgs {
+  int N, d, P;                     // P = N(N-1)/2 pairs
+  double* v;                       // L frames, N x d complex (in / out)
+  trstmi_tr_options o;
+  trstmi_tr_row* rows;             // L x cap, or null
+  int cap;
+  int* n_rows;                     // L
+  double* mu2;                     // L: max |G_jk|^2 at the end
+  int* hv;                         // L: Hessian products
+  int* bad;                        // L: a zero column was met
+};
+
+struct ResSmem {
+  double *x, *xn, *g, *p, *r, *dv, *bd, *gp, *gm, *phi, *rn, *Gre, *Gim, *W, *red;
+  unsigned short *pj, *pk;
+};
+
+size_t res_doubles(int N, int d) {
+  const size_t n = 2 * (size_t)d * N, P = (size_t)N * (N - 1) / 2;
+  return 10 * n + N + 3 * P + kResThreads;
+}
+size_t res_smem_bytes(int N, int d) {
+  const size_t P = (size_t)N * (N - 1) / 2;
+  return res_doubles(N, d) * sizeof(double) + ((2 * P * sizeof(unsigned short) + 15) & ~15ull);
+}
+
+// sum over the CTA of each thread's v, the same order every call; all threads
+// get the result
+__device__ double res_sum(double v, double* red) {
+  __syncthreads();
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int st = kResThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  const double out = red[0];
+  __syncthreads();
+  return out;
+}
+__device__ double res_max(double v, double* red) {
+  __syncthreads();
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int st = kResThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + st]);
+    __syncthreads();
+  }
+  const double out = red[0];
+  __syncthreads();
+  return out;
+}
+__device__ double res_dot(const double* a, const double* b, int n, double* red) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += kResThreads) t += a[i] * b[i];
+  return res_sum(t, red);
+}
+// o = a x + b y over n entries
+__device__ void res_axpby(double a, const double* x, double b, const double* y, double* o, int n) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += kResThreads) o[i] = a * x[i] + b * y[i];
+  __syncthreads();
+}
+
+// F_{s,delta} and s at v; the gradient into gout when it is not null.
+// Returns false (in every thread) if a column of v is zero.
+__device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double delta,
+                         double* gout, double* F, double* smax) {
+  const int N = a.N, d = a.d, P = a.P;
+  __syncthreads();
+  double zero = 0.0;
+  for (int k = threadIdx.x; k < N; k += kResThreads) {
+    double q = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double re = v[2 * (k * d + i)], im = v[2 * (k * d + i) + 1];
+      q += re * re + im * im;
+    }
+    if (!(q > 0.0)) zero = 1.0;
+    const double r = sqrt(q);
+    S.rn[k] = r;
+    for (int i = 0; i < d; ++i) {
+      S.phi[2 * (k * d + i)] = v[2 * (k * d + i)] / r;
+      S.phi[2 * (k * d + i) + 1] = v[2 * (k * d + i) + 1] / r;
+    }
+  }
+  if (res_max(zero, S.red) > 0.0) return false;
+  // G_jk = sum_i conj(phi_ij) phi_ik and x = |G_jk|^2 for every pair
+  double hi = 0.0;
+  for (int q = threadIdx.x; q < P; q += kResThreads) {
+    const int j = S.pj[q], k = S.pk[q];
+    double gr = 0.0, gi = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double ar = S.phi[2 * (j * d + i)], ai = S.phi[2 * (j * d + i) + 1];
+      const double br = S.phi[2 * (k * d + i)], bi = S.phi[2 * (k * d + i) + 1];
+      gr += ar * br + ai * bi;
+      gi += ar * bi - ai * br;
+    }
+    S.Gre[q] = gr;
+    S.Gim[q] = gi;
+    const double x = gr * gr + gi * gi;
+    S.W[q] = x;
+    hi = fmax(hi, x);
+  }
+  const double s = res_max(hi, S.red);
+  double e = 0.0;
+  for (int q = threadIdx.x; q < P; q += kResThreads) e += exp((S.W[q] - s) / delta);
+  const double Ssum = res_sum(e, S.red);
+  *F = s + delta * log(Ssum);
+  *smax = s;
+  if (!gout) return true;
+  for (int q = threadIdx.x; q < P; q += kResThreads) S.W[q] = exp((S.W[q] - s) / delta) / Ssum;
+  __syncthreads();
+  // g_k = 2 sum_{j != k} w_jk G_jk phi_j (G Hermitian), then the projection
+  const int half = d * N;
+  for (int t = threadIdx.x; t < half; t += kResThreads) {
+    const int k = t / d, i = t - k * d;
+    double gr = 0.0, gi = 0.0;
+    for (int j = 0; j < N; ++j) {
+      if (j == k) continue;
+      const int lo = j < k ? j : k, hi2 = j < k ? k : j;
+      const int q = lo * N - lo * (lo + 1) / 2 + (hi2 - lo - 1);
+      const double mr = S.W[q] * S.Gre[q];
+      const double mi = j < k ? S.W[q] * S.Gim[q] : -S.W[q] * S.Gim[q];
+      const double pr = S.phi[2 * (j * d + i)], pi = S.phi[2 * (j * d + i) + 1];
+      gr += mr * pr - mi * pi;
+      gi += mr * pi + mi * pr;
+    }
+    gout[2 * (k * d + i)] = 2.0 * gr;
+    gout[2 * (k * d + i) + 1] = 2.0 * gi;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < N; k += kResThreads) {
+    double rad = 0.0;
+    for (int i = 0; i < d; ++i)
+      rad += S.phi[2 * (k * d + i)] * gout[2 * (k * d + i)] +
+             S.phi[2 * (k * d + i) + 1] * gout[2 * (k * d + i) + 1];
+    const double inv = 1.0 / S.rn[k];
+    for (int i = 0; i < d; ++i) {
+      gout[2 * (k * d + i)] = (gout[2 * (k * d + i)] - S.phi[2 * (k * d + i)] * rad) * inv;
+      gout[2 * (k * d + i) + 1] =
+          (gout[2 * (k * d + i) + 1] - S.phi[2 * (k * d + i) + 1] * rad) * inv;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+__global__ void __launch_bounds__(kResThreads, 1) k_tr_resident(const ResArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  const int f = blockIdx.x;
+  const int N = a.N, d = a.d, P = a.P, n = 2 * d * N;
+  const trstmi_tr_options& o = a.o;
+  ResSmem S;
+  double* c = sm;
+  S.x = c; c += n; S.xn = c; c += n; S.g = c; c += n; S.p = c; c += n; S.r = c; c += n;
+  S.dv = c; c += n; S.bd = c; c += n; S.gp = c; c += n; S.gm = c; c += n; S.phi = c; c += n;
+  S.rn = c; c += N; S.Gre = c; c += P; S.Gim = c; c += P; S.W = c; c += P;
+  S.red = c; c += kResThreads;
+  S.pj = reinterpret_cast<unsigned short*>(c);
+  S.pk = S.pj + P;
+  for (int q = threadIdx.x; q < P; q += kResThreads) {
+    int j = 0, rem = q;
+    while (rem >= N - 1 - j) { rem -= N - 1 - j; ++j; }
+    S.pj[q] = (unsigned short)j;
+    S.pk[q] = (unsigned short)(j + 1 + rem);
+  }
+  double* vf = a.v + (size_t)f * n;
+  for (int i = threadIdx.x; i < n; i += kResThreads) S.x[i] = vf[i];
+  __syncthreads();
+  // columns to unit norm
+  bool ok = true;
+  {
+    double F0, s0;
+    ok = res_eval(a, S, S.x, 1.0, nullptr, &F0, &s0);
+    if (ok) {
+      for (int i = threadIdx.x; i < n; i += kResThreads) S.x[i] = S.phi[i];
+      __syncthreads();
+    }
+  }
+  int rows = 0, products = 0;
+  trstmi_tr_row* trace = a.rows ? a.rows + (size_t)f * a.cap : nullptr;
+  const double h = o.fd_step;
+  for (int k = 0; k < o.n_delta && ok; ++k) {
+    const double delta = o.delta[k];
+    double radius = o.radius0;
+    for (int it = 0; it < o.max_outer && ok; ++it) {
+      double F, smax, Fn, sn;
+      ok = res_eval(a, S, S.x, delta, S.g, &F, &smax);
+      if (!ok) break;
+      const double gn = sqrt(res_dot(S.g, S.g, n, S.red));
+      if (gn <= o.gtol) break;
+      const double eps = fmin(0.5, sqrt(gn)) * gn;
+      // CG-Steihaug (the paper's Algorithm, Nocedal and Wright Alg. 7.2)
+      res_axpby(0.0, S.g, 0.0, S.g, S.p, n);
+      res_axpby(1.0, S.g, 0.0, S.g, S.r, n);
+      res_axpby(-1.0, S.g, 0.0, S.g, S.dv, n);
+      double m = 0.0, rr = res_dot(S.r, S.r, n, S.red);
+      int st = 3, cgit = 0;
+      if (sqrt(rr) < eps) {
+        st = 0;
+      } else {
+        for (cgit = 0; cgit < o.max_cg; ++cgit) {
+          // B d by a central difference of the gradient
+          const double nu = sqrt(res_dot(S.dv, S.dv, n, S.red));
+          const double step = nu > 0.0 ? h / nu : 0.0, cq = nu > 0.0 ? nu / (2.0 * h) : 0.0;
+          double Ft, st2;
+          res_axpby(1.0, S.x, step, S.dv, S.xn, n);
+          ok = res_eval(a, S, S.xn, delta, S.gp, &Ft, &st2);
+          res_axpby(1.0, S.x, -step, S.dv, S.xn, n);
+          ok = ok && res_eval(a, S, S.xn, delta, S.gm, &Ft, &st2);
+          if (!ok) break;
+          res_axpby(cq, S.gp, -cq, S.gm, S.bd, n);
+          ++products;
+          const double dbd = res_dot(S.dv, S.bd, n, S.red), rd = res_dot(S.dv, S.r, n, S.red);
+          const double zz = res_dot(S.p, S.p, n, S.red), zd = res_dot(S.p, S.dv, n, S.red);
+          const double dd = res_dot(S.dv, S.dv, n, S.red);
+          if (dbd <= 0.0) {
+            const double t1 = to_boundary_dev(zz, zd, dd, radius, true);
+            const double t2 = to_boundary_dev(zz, zd, dd, radius, false);
+            const double m1 = m + t1 * rd + 0.5 * t1 * t1 * dbd;
+            const double m2 = m + t2 * rd + 0.5 * t2 * t2 * dbd;
+            res_axpby(1.0, S.p, m1 <= m2 ? t1 : t2, S.dv, S.p, n);
+            m = m1 <= m2 ? m1 : m2;
+            st = 2; ++cgit;
+            break;
+          }
+          const double alpha = rr / dbd;
+          const double zn2 = zz + 2.0 * alpha * zd + alpha * alpha * dd;
+          if (sqrt(fmax(zn2, 0.0)) >= radius) {
+            const double t = to_boundary_dev(zz, zd, dd, radius, true);
+            res_axpby(1.0, S.p, t, S.dv, S.p, n);
+            m += t * rd + 0.5 * t * t * dbd;
+            st = 1; ++cgit;
+            break;
+          }
+          res_axpby(1.0, S.p, alpha, S.dv, S.p, n);
+          res_axpby(1.0, S.r, alpha, S.bd, S.r, n);
+          m += alpha * rd + 0.5 * alpha * alpha * dbd;
+          const double rr_new = res_dot(S.r, S.r, n, S.red);
+          if (sqrt(rr_new) < eps) { st = 0; ++cgit; break; }
+          res_axpby(-1.0, S.r, rr_new / rr, S.dv, S.dv, n);
+          rr = rr_new;
+        }
+      }
+      if (!ok) break;
+      const double pn = sqrt(res_dot(S.p, S.p, n, S.red));
+      res_axpby(1.0, S.x, 1.0, S.p, S.xn, n);
+      ok = res_eval(a, S, S.xn, delta, nullptr, &Fn, &sn);
+      if (!ok) break;
+      const double pred = -m;
+      const double rho = pred > 0.0 ? (F - Fn) / pred : -1.0;
+      const double r_used = radius;
+      if (rho < 0.25) radius *= 0.25;
+      else if (rho > 0.75 && pn >= (1.0 - 1e-12) * radius) radius = fmin(2.0 * radius, o.radius_max);
+      const bool acc = rho > o.eta;
+      if (acc) {
+        // V <- V + p with unit columns: the phi of the last evaluation
+        for (int i = threadIdx.x; i < n; i += kResThreads) S.x[i] = S.phi[i];
+        __syncthreads();
+      }
+      if (trace && rows < a.cap && threadIdx.x == 0) {
+        trstmi_tr_row& w = trace[rows];
+        w.stage = k; w.iter = it; w.F = F; w.s = smax; w.gnorm = gn; w.radius = r_used;
+        w.rho = rho; w.step_norm = pn; w.pred = pred; w.cg_iters = cgit; w.cg_status = st;
+        w.accepted = acc ? 1 : 0; w.reserved = 0;
+      }
+      ++rows;
+      if (radius < 1e-14) break;
+    }
+  }
+  double Fe = 0.0, se = 0.0;
+  if (ok) ok = res_eval(a, S, S.x, o.delta[o.n_delta - 1], nullptr, &Fe, &se);
+  for (int i = threadIdx.x; i < n; i += kResThreads) vf[i] = S.x[i];
+  if (threadIdx.x == 0) {
+    a.n_rows[f] = rows;
+    a.mu2[f] = se;
+    a.hv[f] = products;
+    a.bad[f] = ok ? 0 : 1;
+  }
+}
+
+}  // namespace
+
+bool tr_resident_fits(int N, int d) {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return false;
+  return N <= 65535 && res_smem_bytes(N, d) + 1024 <= (size_t)optin;
+}
+
+int tr_solve_device(int N, int d, int L, double* v_dev, const trstmi_tr_options& o,
+                    void* scratch, int num_sms, cudaStream_t s, TrFrameLog* logs) {
+  const bool resident = o.path == 2 || (o.path == 0 && tr_resident_fits(N, d));
+  if (!resident) return tr_solve_stack(N, d, L, v_dev, o, scratch, num_sms, s, logs);
+  if (!tr_resident_fits(N, d)) return TRSTMI_EUNSUPPORTED;
+  int cap = 0;
+  for (int f = 0; f < L && logs; ++f) cap = std::max(cap, logs[f].rows ? logs[f].cap : 0);
+  // results in the scratch array: L ints x 3 and L doubles, then the rows
+  unsigned char* b = static_cast<unsigned char*>(scratch);
+  ResArgs a;
+  a.N = N; a.d = d; a.P = N * (N - 1) / 2; a.v = v_dev; a.o = o; a.cap = cap;
+  a.mu2 = reinterpret_cast<double*>(b);
+  a.n_rows = reinterpret_cast<int*>(a.mu2 + L);
+  a.hv = a.n_rows + L;
+  a.bad = a.hv + L;
+  a.rows = cap > 0 ? reinterpret_cast<trstmi_tr_row*>(b + (((size_t)L * 20 + 255) & ~(size_t)255))
+                   : nullptr;
+  const size_t smem = res_smem_bytes(N, d);
+  cudaError_t e = cudaFuncSetAttribute(k_tr_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e == cudaSuccess) {
+    k_tr_resident<<<L, kResThreads, smem, s>>>(a);
+    e = cudaGetLastError();
+  }
+  std::vector<double> mu2(L);
+  std::vector<int> ints(3 * (size_t)L);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(mu2.data(), a.mu2, L * sizeof(double),
+                                            cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ints.data(), a.n_rows, 3 * L * sizeof(int),
+                                            cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return TRSTMI_ECUDA;
+  for (int f = 0; f < L; ++f)
+    if (ints[2 * L + f]) return TRSTMI_EINVAL;
+  if (logs) {
+    for (int f = 0; f < L; ++f) {
+      logs[f].n = ints[f];
+      logs[f].mu2 = mu2[f];
+      logs[f].hv_products = ints[L + f];
+      if (logs[f].rows && cap > 0) {
+        const int k = std::min(ints[f], std::min(cap, logs[f].cap));
+        if (k > 0 && cudaMemcpy(logs[f].rows, a.rows + (size_t)f * cap, k * sizeof(trstmi_tr_row),
+                                cudaMemcpyDeviceToHost) != cudaSuccess)
+          return TRSTMI_ECUDA;
+      }
+    }
+  }
+  return TRSTMI_OK;
 }
 
 }  // namespace trstmi

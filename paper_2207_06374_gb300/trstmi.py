@@ -110,7 +110,7 @@ class Certificates(ctypes.Structure):
 class TrOptions(ctypes.Structure):
     _fields_ = [("n_delta", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("delta", ctypes.c_double * 16), ("max_cg", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("radius0", ctypes.c_double),
+                ("path", ctypes.c_int32), ("radius0", ctypes.c_double),
                 ("radius_max", ctypes.c_double), ("eta", ctypes.c_double),
                 ("gtol", ctypes.c_double), ("fd_step", ctypes.c_double)]
 

@@ -28,10 +28,11 @@ def _start(d, N, seed):
     return z / np.linalg.norm(z, axis=0, keepdims=True)
 
 
+@pytest.mark.parametrize("path", [1, 2])       # 1: stack driven from the host; 2: resident
 @pytest.mark.parametrize("d,N,seed", [(2, 4, 1), (3, 7, 1), (3, 9, 2), (4, 8, 3), (2, 5, 4)])
-def test_trace_matches_oracle(d, N, seed):
+def test_trace_matches_oracle(d, N, seed, path):
     v = _start(d, N, seed)
-    phi, tr = T.tr_solve(v, deltas=SCHEDULE, max_outer=100, max_cg=200)
+    phi, tr = T.tr_solve(v, deltas=SCHEDULE, max_outer=100, max_cg=200, path=path)
     ophi, otr = O.tr_solve(v, O.tr_opts(deltas=SCHEDULE, max_outer=100, max_cg=200))
     k = 0
     while (k < min(len(tr), len(otr)) and otr["gnorm"][k] > 1e-5
@@ -48,17 +49,19 @@ def test_trace_matches_oracle(d, N, seed):
     assert np.sqrt(O.mu2(phi)) == pytest.approx(np.sqrt(O.mu2(ophi)), abs=1e-6)
 
 
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("d,N,seed", [(4, 16, 0), (5, 25, 1)])
-def test_reaches_the_sics(d, N, seed):
-    phi, tr = T.tr_solve(_start(d, N, seed), deltas=SCHEDULE)
+def test_reaches_the_sics(d, N, seed, path):
+    phi, tr = T.tr_solve(_start(d, N, seed), deltas=SCHEDULE, path=path)
     assert np.sqrt(O.mu2(phi)) == pytest.approx(F.welch(N, d), abs=1e-6)
     assert np.allclose(np.linalg.norm(phi, axis=0), 1.0, atol=1e-14)
 
 
-def test_config_shape_d8_n64_descends_and_obeys_the_rules():
+@pytest.mark.parametrize("path", [1, 2])
+def test_config_shape_d8_n64_descends_and_obeys_the_rules(path):
     v = _start(8, 64, 3)
     mu0 = np.sqrt(O.mu2(v))
-    phi, tr = T.tr_solve(v, deltas=(0.03, 0.01, 0.003), max_outer=40, max_cg=60)
+    phi, tr = T.tr_solve(v, deltas=(0.03, 0.01, 0.003), max_outer=40, max_cg=60, path=path)
     mu1 = np.sqrt(O.mu2(phi))
     assert mu1 < mu0 - 0.2
     for a, b in zip(tr[:-1], tr[1:]):
@@ -91,7 +94,8 @@ def test_polishing_a_search_result():
 def test_rejects_bad_options():
     v = _start(2, 4, 0)
     for kw in [dict(deltas=()), dict(deltas=(0.1, 0.0)), dict(max_cg=0), dict(eta=0.3),
-               dict(radius0=0.0), dict(fd_step=0.0), dict(radius0=2.0, radius_max=1.0)]:
+               dict(radius0=0.0), dict(fd_step=0.0), dict(radius0=2.0, radius_max=1.0),
+               dict(path=3)]:
         with pytest.raises(T.TrstmiError) as e:
             T.tr_solve(v, **kw)
         assert e.value.status == T.TRSTMI_EINVAL
@@ -108,9 +112,10 @@ def _init(N, d, seed):
         return s.get_phi()
 
 
-def test_trials_advance_together_exactly_as_alone():
+@pytest.mark.parametrize("path", [1, 2])
+def test_trials_advance_together_exactly_as_alone(path):
     N, d, seed0, L = 9, 3, 20, 5
-    kw = dict(deltas=(0.1, 0.01, 0.001), max_outer=40, max_cg=50)
+    kw = dict(deltas=(0.1, 0.01, 0.001), max_outer=40, max_cg=50, path=path)
     res, mus, phi, tr = T.tr_multistart(N, d, seed0, L, trace_cap=4096, **kw)
     assert res.trials == L
     for i in range(L):
@@ -143,3 +148,9 @@ def test_the_papers_table_2_shapes_with_2d2_trials(d):
     assert res.trials == 2 * d * d
     assert res.mu <= table[d]
     assert np.sqrt(O.mu2(phi)) == pytest.approx(res.mu, rel=1e-12)
+
+
+def test_resident_path_refuses_frames_it_cannot_hold():
+    with pytest.raises(T.TrstmiError) as e:
+        T.tr_solve(_start(32, 300, 0), deltas=(0.1,), max_outer=1, path=2)
+    assert e.value.status == T.TRSTMI_EUNSUPPORTED
