@@ -122,6 +122,9 @@ def lib():
                                              ctypes.POINTER(ctypes.c_int)]
             L.oracle_lse_hv.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
                                         ctypes.c_double, _dp, _dp]
+            L.oracle_lse_hv_exact.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
+                                              _dp, _dp]
+            L.oracle_lse_hv_exact.restype = ctypes.c_int
             L.oracle_tr_solve.argtypes = [ctypes.c_int, ctypes.c_int, _dp,
                                           ctypes.POINTER(TrOpts), ctypes.c_void_p, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int)]
@@ -340,3 +343,13 @@ def tr_solve(v: np.ndarray, opts: TrOpts, cap: int = 4096):
     _check(lib().oracle_tr_solve(N, d, _ptr(b), ctypes.byref(opts), tr.ctypes.data, cap,
                                  ctypes.byref(n)), "tr_solve")
     return _unflat(b, d, N), tr[: min(n.value, cap)]
+
+
+def lse_hv_exact(v: np.ndarray, delta: float, u: np.ndarray) -> np.ndarray:
+    """The exact Hessian of F_{s,delta} at V applied to U (the chain rule
+    through the gradient), complex (d, N) arrays."""
+    d, N = v.shape
+    b, ub = _flat(v), _flat(u)
+    o = np.zeros_like(b)
+    _check(lib().oracle_lse_hv_exact(N, d, _ptr(b), delta, _ptr(ub), _ptr(o)), "lse_hv_exact")
+    return _unflat(o, d, N)

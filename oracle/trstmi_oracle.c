@@ -742,3 +742,117 @@ out:
     free(g); free(p); free(vn); free(c.tmp); free(c.gp); free(c.gm);
     return st;
 }
+
+/*
+ * The exact Hessian of F_{s,delta} at V applied to U, by differentiating the
+ * gradient above along U (the chain rule, written out):
+ *   d phi_k = (u_k - phi_k Re(phi_k^* u_k)) / r_k,   d r_k = Re(phi_k^* u_k),
+ *   dG_jk = d phi_j^* phi_k + phi_j^* d phi_k,        dx_jk = 2 Re(conj(G_jk) dG_jk),
+ *   dw_jk = w_jk (dx_jk - sum_l w_l dx_l) / delta     (the shift s cancels),
+ *   dM_jk = dw_jk G_jk + w_jk dG_jk                   (j < k; M Hermitian),
+ *   dg_k = 2 sum_{j != k} (dM_jk phi_j + M_jk d phi_j),
+ *   d rho_k = Re(d phi_k^* g_k + phi_k^* dg_k),
+ *   (H u)_k = (dg_k - d phi_k rho_k - phi_k d rho_k) / r_k - grad_k d r_k / r_k.
+ * The paper's B_k; the procedure above uses central differences of the
+ * gradient instead, and this function measures how far they are apart.
+ */
+int oracle_lse_hv_exact(int N, int d, const double *v, double delta, const double *u,
+                        double *out)
+{
+    if (N < 2 || d < 1 || !v || !u || !out || !(delta > 0.0)) return ORACLE_EINVAL;
+    size_t m = 2 * (size_t)d * (size_t)N, n = (size_t)N * (size_t)(N - 1) / 2;
+    double *phi = (double *)malloc(sizeof(double) * m), *dphi = (double *)malloc(sizeof(double) * m);
+    double *g = (double *)calloc(m, sizeof(double)), *dg = (double *)calloc(m, sizeof(double));
+    double *r = (double *)malloc(sizeof(double) * (size_t)N), *dr = (double *)malloc(sizeof(double) * (size_t)N);
+    double *G = (double *)malloc(sizeof(double) * 2 * n), *dG = (double *)malloc(sizeof(double) * 2 * n);
+    double *x = (double *)malloc(sizeof(double) * n), *dx = (double *)malloc(sizeof(double) * n);
+    int st = ORACLE_OK;
+    if (!phi || !dphi || !g || !dg || !r || !dr || !G || !dG || !x || !dx) { st = ORACLE_EINVAL; goto out; }
+    for (int k = 0; k < N; ++k) {
+        double q = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double a = v[2 * (k * d + i)], b = v[2 * (k * d + i) + 1];
+            q += a * a + b * b;
+        }
+        if (!(q > 0.0)) { st = ORACLE_EINVAL; goto out; }
+        r[k] = sqrt(q);
+        double pu = 0.0;   /* Re(phi_k^* u_k) */
+        for (int i = 0; i < d; ++i) {
+            phi[2 * (k * d + i)] = v[2 * (k * d + i)] / r[k];
+            phi[2 * (k * d + i) + 1] = v[2 * (k * d + i) + 1] / r[k];
+            pu += phi[2 * (k * d + i)] * u[2 * (k * d + i)] +
+                  phi[2 * (k * d + i) + 1] * u[2 * (k * d + i) + 1];
+        }
+        dr[k] = pu;
+        for (int i = 0; i < d; ++i) {
+            dphi[2 * (k * d + i)] = (u[2 * (k * d + i)] - phi[2 * (k * d + i)] * pu) / r[k];
+            dphi[2 * (k * d + i) + 1] =
+                (u[2 * (k * d + i) + 1] - phi[2 * (k * d + i) + 1] * pu) / r[k];
+        }
+    }
+    size_t p = 0;
+    double s = 0.0;
+    for (int j = 0; j < N; ++j)
+        for (int k = j + 1; k < N; ++k, ++p) {
+            double gr = 0.0, gi = 0.0, hr = 0.0, hi = 0.0;
+            for (int i = 0; i < d; ++i) {
+                double a = phi[2 * (j * d + i)], b = phi[2 * (j * d + i) + 1];
+                double c = phi[2 * (k * d + i)], e = phi[2 * (k * d + i) + 1];
+                double da = dphi[2 * (j * d + i)], db = dphi[2 * (j * d + i) + 1];
+                double dc = dphi[2 * (k * d + i)], de = dphi[2 * (k * d + i) + 1];
+                gr += a * c + b * e;             /* conj(a + ib)(c + ie) */
+                gi += a * e - b * c;
+                hr += da * c + db * e + a * dc + b * de;
+                hi += da * e - db * c + a * de - b * dc;
+            }
+            G[2 * p] = gr; G[2 * p + 1] = gi; dG[2 * p] = hr; dG[2 * p + 1] = hi;
+            x[p] = gr * gr + gi * gi;
+            dx[p] = 2.0 * (gr * hr + gi * hi);
+            if (p == 0 || x[p] > s) s = x[p];
+        }
+    double S = 0.0, T = 0.0;
+    for (p = 0; p < n; ++p) S += exp((x[p] - s) / delta);
+    for (p = 0; p < n; ++p) T += exp((x[p] - s) / delta) / S * dx[p];
+    p = 0;
+    for (int j = 0; j < N; ++j)
+        for (int k = j + 1; k < N; ++k, ++p) {
+            double w = exp((x[p] - s) / delta) / S, dw = w * (dx[p] - T) / delta;
+            double Mr = w * G[2 * p], Mi = w * G[2 * p + 1];
+            double dMr = dw * G[2 * p] + w * dG[2 * p], dMi = dw * G[2 * p + 1] + w * dG[2 * p + 1];
+            for (int i = 0; i < d; ++i) {
+                double a = phi[2 * (j * d + i)], b = phi[2 * (j * d + i) + 1];
+                double c = phi[2 * (k * d + i)], e = phi[2 * (k * d + i) + 1];
+                double da = dphi[2 * (j * d + i)], db = dphi[2 * (j * d + i) + 1];
+                double dc = dphi[2 * (k * d + i)], de = dphi[2 * (k * d + i) + 1];
+                /* column k: M phi_j, dM phi_j + M dphi_j */
+                g[2 * (k * d + i)] += 2.0 * (Mr * a - Mi * b);
+                g[2 * (k * d + i) + 1] += 2.0 * (Mr * b + Mi * a);
+                dg[2 * (k * d + i)] += 2.0 * (dMr * a - dMi * b + Mr * da - Mi * db);
+                dg[2 * (k * d + i) + 1] += 2.0 * (dMr * b + dMi * a + Mr * db + Mi * da);
+                /* column j: conj(M) phi_k, conj(dM) phi_k + conj(M) dphi_k */
+                g[2 * (j * d + i)] += 2.0 * (Mr * c + Mi * e);
+                g[2 * (j * d + i) + 1] += 2.0 * (Mr * e - Mi * c);
+                dg[2 * (j * d + i)] += 2.0 * (dMr * c + dMi * e + Mr * dc + Mi * de);
+                dg[2 * (j * d + i) + 1] += 2.0 * (dMr * e - dMi * c + Mr * de - Mi * dc);
+            }
+        }
+    for (int k = 0; k < N; ++k) {
+        double rho = 0.0, drho = 0.0;
+        for (int i = 0; i < d; ++i) {
+            size_t a = 2 * ((size_t)k * d + i);
+            rho += phi[a] * g[a] + phi[a + 1] * g[a + 1];
+            drho += dphi[a] * g[a] + dphi[a + 1] * g[a + 1] + phi[a] * dg[a] + phi[a + 1] * dg[a + 1];
+        }
+        for (int i = 0; i < d; ++i) {
+            size_t a = 2 * ((size_t)k * d + i);
+            for (int c = 0; c < 2; ++c) {
+                double grad = (g[a + c] - phi[a + c] * rho) / r[k];
+                out[a + c] = (dg[a + c] - dphi[a + c] * rho - phi[a + c] * drho) / r[k] -
+                             grad * dr[k] / r[k];
+            }
+        }
+    }
+out:
+    free(phi); free(dphi); free(g); free(dg); free(r); free(dr); free(G); free(dG); free(x); free(dx);
+    return st;
+}

@@ -159,3 +159,52 @@ def test_trace_obeys_the_trust_region_rules():
             assert b["radius"] == a["radius"]
         assert a["step_norm"] <= a["radius"] * (1 + 1e-12)
         assert a["pred"] > 0
+
+
+# ------------------------------------------------ the exact Hessian product
+
+def _ip(a, b):
+    return float(np.sum(a.real * b.real + a.imag * b.imag))
+
+
+@pytest.mark.parametrize("d,N,delta", [(2, 4, 0.05), (3, 8, 0.02), (4, 12, 0.1), (3, 9, 0.003)])
+def test_exact_hessian_against_second_differences_and_symmetry(d, N, delta):
+    rng = np.random.default_rng(7 * d + N)
+    v = _raw(d, N, rng) * rng.uniform(0.5, 2.0, size=(1, N))
+    u = rng.standard_normal((d, N)) + 1j * rng.standard_normal((d, N))
+    w = rng.standard_normal((d, N)) + 1j * rng.standard_normal((d, N))
+    Hu, Hw = O.lse_hv_exact(v, delta, u), O.lse_hv_exact(v, delta, w)
+    assert _ip(w, Hu) == pytest.approx(_ip(u, Hw), rel=1e-12, abs=1e-12)
+    e = 1e-4
+
+    def f(x):
+        return O.lse(x, delta, grad=False)[0]
+
+    sd = (f(v + e * u + e * w) - f(v + e * u - e * w) - f(v - e * u + e * w)
+          + f(v - e * u - e * w)) / (4 * e * e)
+    assert _ip(u, Hw) == pytest.approx(sd, rel=2e-4, abs=1e-6)
+
+
+def test_exact_hessian_along_scaling_and_phase():
+    """F is invariant under scaling and rotating the columns, so the gradient
+    is homogeneous of degree -1 and equivariant under phases:
+    H V = -grad F(V) and H (iV) = i grad F(V)."""
+    rng = np.random.default_rng(11)
+    v = _raw(4, 14, rng) * rng.uniform(0.5, 2.0, size=(1, 14))
+    _, _, g = O.lse(v, 0.03)
+    scale = np.max(np.abs(g))
+    assert np.max(np.abs(O.lse_hv_exact(v, 0.03, v) + g)) < 1e-12 * scale
+    assert np.max(np.abs(O.lse_hv_exact(v, 0.03, 1j * v) - 1j * g)) < 1e-12 * scale
+
+
+@pytest.mark.parametrize("delta", [0.1, 0.01, 0.001])
+def test_central_difference_products_are_within_1e_6_of_the_exact_ones(delta):
+    """The reading used by the procedure (central differences of the exact
+    gradient, h = 1e-6) against the paper's exact Hessian."""
+    rng = np.random.default_rng(5)
+    v = _raw(3, 10, rng)
+    for _ in range(3):
+        u = rng.standard_normal((3, 10)) + 1j * rng.standard_normal((3, 10))
+        he = O.lse_hv_exact(v, delta, u)
+        hf = O.lse_hv(v, delta, 1e-6, u)
+        assert np.max(np.abs(hf - he)) <= 1e-6 * np.max(np.abs(he))
