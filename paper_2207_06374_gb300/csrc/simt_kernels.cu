@@ -79,6 +79,57 @@ __device__ bool gen_column(const typename Cplx<T>::type* phi, int d, int j,
   return true;
 }
 
+// CTA-cooperative form of gen_column for all N columns of candidate (c, t)
+// into [i][column] planes of row pitch `stride`: the draws (Philox,
+// Box-Muller, phi + delta z) are spread over the (column, entry pair) items,
+// then one thread per column forms the squared norm in the same sequential
+// order over i and divides, so every value has the bits gen_column gives it.
+// Returns (in every thread) whether a column had zero norm.  Begins and ends
+// with a CTA barrier.
+template <typename T>
+__device__ bool gen_candidate_cta(const typename Cplx<T>::type* phi, int N, int d, uint64_t seed,
+                                  uint32_t c, uint32_t t, T delta, T* out_re, T* out_im,
+                                  int stride, int* zero_flag) {
+  const uint32_t k0 = seed_lo(seed), k1 = seed_hi(seed);
+  const int P = (d + 1) >> 1;
+  __syncthreads();
+  for (int q = threadIdx.x; q < N * P; q += blockDim.x) {
+    const int j = q / P, p = q - j * P;
+    const PhiloxOut u = philox4x32_10((uint32_t)j * (uint32_t)P + (uint32_t)p, c, t, 0u, k0, k1);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * p + h;
+      if (i < d) {
+        T zr, zi;
+        cn_draw<T>(u.x[2 * h], u.x[2 * h + 1], zr, zi);
+        const auto v = phi[(size_t)j * d + i];
+        out_re[i * stride + j] = add_rn(v.x, mul_rn(delta, zr));
+        out_im[i * stride + j] = add_rn(v.y, mul_rn(delta, zi));
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    T s = T(0);
+    for (int i = 0; i < d; ++i) {
+      const T xr = out_re[i * stride + j], xi = out_im[i * stride + j];
+      s = add_rn(s, add_rn(mul_rn(xr, xr), mul_rn(xi, xi)));
+    }
+    if (!(s > T(0))) {
+      for (int i = 0; i < d; ++i) { out_re[i * stride + j] = T(0); out_im[i * stride + j] = T(0); }
+      *zero_flag = 1;
+      continue;
+    }
+    const T nrm = sqrt_rn(s);
+    for (int i = 0; i < d; ++i) {
+      out_re[i * stride + j] = div_rn(out_re[i * stride + j], nrm);
+      out_im[i * stride + j] = div_rn(out_im[i * stride + j], nrm);
+    }
+  }
+  __syncthreads();
+  return *zero_flag != 0;
+}
+
 // Warp-cooperative form of gen_column for an interleaved column in global
 // memory: lane l draws the entry pairs p = l, l + 32, ...; the squared norm
 // is reduced across the warp.  All 32 lanes must call it.
@@ -969,9 +1020,10 @@ __global__ void __launch_bounds__(256, TileCtas<T>::value) k_batch_score(const S
 // all N columns of candidate c once into shared memory as [i][column] planes
 // (the tile path draws every column block once per tile of its row and
 // column), then reduces every pair j < k with 4 x 4 micro-tiles spread over
-// the threads.  Generation (gen_column), the sequential chain over i and the
-// explicit rounding of |G|^2 are those of score_tile, so the scores are the
-// same bits.  Np = N rounded up to a multiple of 4; padded columns are zero.
+// the threads.  Generation (gen_candidate_cta: gen_column's arithmetic with
+// the draws spread over the CTA), the sequential chain over i and the explicit
+// rounding of |G|^2 are those of score_tile, so the scores are the same bits.
+// Np = N rounded up to a multiple of 4; padded columns are zero.
 template <typename T>
 __device__ T score_resident(int N, int d, const void* phi, uint64_t seed, uint32_t c, uint32_t t,
                             double delta, T* sm, int* zero_col) {
@@ -980,16 +1032,13 @@ __device__ T score_resident(int N, int d, const void* phi, uint64_t seed, uint32
   T* sRe = sm;
   T* sIm = sm + (size_t)d * Np;
   __syncthreads();
-  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
-    if (j < N) {
-      if (!gen_column<T>(reinterpret_cast<const C*>(phi), d, j, seed, c, t, 0u, (T)delta, sRe + j,
-                         sIm + j, Np))
-        *zero_col = 1;
-    } else {
-      for (int i = 0; i < d; ++i) { sRe[i * Np + j] = T(0); sIm[i * Np + j] = T(0); }
-    }
+  for (int q = threadIdx.x; q < (Np - N) * d; q += blockDim.x) {   // padded columns
+    const int j = N + q / d, i = q % d;
+    sRe[i * Np + j] = T(0);
+    sIm[i * Np + j] = T(0);
   }
-  __syncthreads();
+  gen_candidate_cta<T>(reinterpret_cast<const C*>(phi), N, d, seed, c, t, (T)delta, sRe, sIm, Np,
+                       zero_col);
   const int nq = Np >> 2;
   const int nmt = nq * (nq + 1) / 2;
   T m = T(0);
