@@ -396,6 +396,85 @@ __global__ void __launch_bounds__(kLseThreads) k_lse_finish(const LseArgs<T> a, 
   }
 }
 
+// 5'. The same pass with one CTA per (frame, column block b): thread (row, c4)
+// sums four adjacent columns 4 c4 .. 4 c4 + 3 of row i over the block's tiles
+// in the same fixed order with vector loads, stages them with the block's
+// unit columns, and every warp then finishes whole columns as in k_lse_finish.
+// Used while d x BT staged values fit 96 KiB.
+template <typename T, int R>
+__global__ void __launch_bounds__(kLseThreads) k_lse_finish_block(const LseArgs<T> a) {
+  constexpr int BT = 16 * R, C4 = BT / 4, ROWS = kLseThreads / C4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int d = a.d, N = a.N;
+  double2* sG = reinterpret_cast<double2*>(smem_raw);                 // d x BT
+  typename Cplx<T>::type* sP = reinterpret_cast<typename Cplx<T>::type*>(sG + (size_t)d * BT);
+  const int slot = blockIdx.x / a.nb, b = blockIdx.x - slot * a.nb, j0 = b * BT;
+  const double* o = a.sums + 3 * (size_t)slot;
+  double2* gout = reinterpret_cast<double2*>(a.grad) + (size_t)slot * N * d;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (a.bad[slot]) {
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int c = warp; c < BT && j0 + c < N; c += kLseThreads / 32)
+      for (int i = lane; i < d; i += 32) gout[(size_t)(j0 + c) * d + i] = make_double2(nan, nan);
+    return;
+  }
+  const double scale = 2.0 / o[2];
+  const T* part = a.part + (size_t)slot * a.ntiles * 4 * d * BT;
+  const T* pre = a.planes + (size_t)slot * 2 * d * N;
+  const T* pim = pre + (size_t)d * N;
+  const int c4 = threadIdx.x % C4, row = threadIdx.x / C4;
+  for (int i = row; i < d; i += ROWS) {
+    T gr[4] = {T(0), T(0), T(0), T(0)}, gi[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 2
+    for (int I = 0; I <= b; ++I) {               // tiles (I, b): side "to J"
+      const T* p = part + ((size_t)(b * (b + 1) / 2 + I) * 4 + 2) * d * BT + i * BT + 4 * c4;
+      T vr[4], vi[4];
+      load_run<T, 4>(p, vr);
+      load_run<T, 4>(p + (size_t)d * BT, vi);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { gr[e] += vr[e]; gi[e] += vi[e]; }
+    }
+#pragma unroll 2
+    for (int J = b; J < a.nb; ++J) {             // tiles (b, J): side "to I"
+      const T* p = part + ((size_t)(J * (J + 1) / 2 + b) * 4 + 0) * d * BT + i * BT + 4 * c4;
+      T vr[4], vi[4];
+      load_run<T, 4>(p, vr);
+      load_run<T, 4>(p + (size_t)d * BT, vi);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { gr[e] += vr[e]; gi[e] += vi[e]; }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int loc = 4 * c4 + e, j = j0 + loc;
+      sG[i * BT + loc] = make_double2((double)gr[e] * scale, (double)gi[e] * scale);
+      typename Cplx<T>::type ph;
+      ph.x = j < N ? pre[(size_t)i * N + j] : T(0);
+      ph.y = j < N ? pim[(size_t)i * N + j] : T(0);
+      sP[i * BT + loc] = ph;
+    }
+  }
+  __syncthreads();
+  for (int c = warp; c < BT; c += kLseThreads / 32) {
+    const int j = j0 + c;
+    if (j >= N) break;
+    double rad = 0.0;
+    for (int i = lane; i < d; i += 32) {
+      const double2 g = sG[i * BT + c];
+      const auto ph = sP[i * BT + c];
+      rad += (double)ph.x * g.x + (double)ph.y * g.y;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) rad += __shfl_xor_sync(0xffffffffu, rad, off);
+    const double inv_r = 1.0 / (double)a.rnorm[(size_t)slot * N + j];
+    for (int i = lane; i < d; i += 32) {
+      const double2 g = sG[i * BT + c];
+      const auto ph = sP[i * BT + c];
+      gout[(size_t)j * d + i] =
+          make_double2((g.x - (double)ph.x * rad) * inv_r, (g.y - (double)ph.y * rad) * inv_r);
+    }
+  }
+}
+
 // columns per CTA of the final pass: as many as fit 96 KiB of staging
 template <typename T> int finish_cols(int d) {
   int cw = 32;
@@ -472,10 +551,17 @@ cudaError_t lse_launch_R(const LseArgs<T>& a, int num_sms, cudaStream_t s) {
   k_lse_total<T><<<a.count, kLseThreads, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.grad) {
-    const int cw = finish_cols<T>(a.d);
-    const long long ctas = (long long)a.count * ((a.N + cw - 1) / cw);
-    const size_t smem = (size_t)a.d * cw * (sizeof(double2) + 2 * sizeof(T));
-    k_lse_finish<T, R><<<(unsigned)ctas, kLseThreads, smem, s>>>(a, cw);
+    constexpr int BT = 16 * R;
+    const size_t block_smem = (size_t)a.d * BT * (sizeof(double2) + 2 * sizeof(T));
+    if (block_smem <= 96 * 1024) {
+      k_lse_finish_block<T, R><<<(unsigned)((long long)a.count * a.nb), kLseThreads, block_smem,
+                                 s>>>(a);
+    } else {
+      const int cw = finish_cols<T>(a.d);
+      const long long ctas = (long long)a.count * ((a.N + cw - 1) / cw);
+      const size_t smem = (size_t)a.d * cw * (sizeof(double2) + 2 * sizeof(T));
+      k_lse_finish<T, R><<<(unsigned)ctas, kLseThreads, smem, s>>>(a, cw);
+    }
     e = cudaGetLastError();
   }
   return e;
@@ -558,6 +644,12 @@ cudaError_t init_lse_attributes(int optin) {
   if ((e = lse_allow(k_lse_finish<float, 1>, optin)) != cudaSuccess) return e;
   if ((e = lse_allow(k_lse_finish<double, 4>, optin)) != cudaSuccess) return e;
   if ((e = lse_allow(k_lse_finish<double, 2>, optin)) != cudaSuccess) return e;
+  if ((e = lse_allow(k_lse_finish_block<float, 4>, optin)) != cudaSuccess) return e;
+  if ((e = lse_allow(k_lse_finish_block<float, 2>, optin)) != cudaSuccess) return e;
+  if ((e = lse_allow(k_lse_finish_block<float, 1>, optin)) != cudaSuccess) return e;
+  if ((e = lse_allow(k_lse_finish_block<double, 4>, optin)) != cudaSuccess) return e;
+  if ((e = lse_allow(k_lse_finish_block<double, 2>, optin)) != cudaSuccess) return e;
+  if ((e = lse_allow(k_lse_finish_block<double, 1>, optin)) != cudaSuccess) return e;
   return lse_allow(k_lse_finish<double, 1>, optin);
 }
 
