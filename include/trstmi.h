@@ -598,8 +598,8 @@ int trstmi_tr_multistart(int N, int d, uint64_t seed0, int L, const trstmi_tr_op
                          double *best_phi, trstmi_tr_row *trace, int cap, int *n_rows);
 
 /* The procedure applied to an instance's current frame (polishing a
- * search's result): the frame is replaced by the procedure's result and
- * recertified, as with trstmi_set_phi. */
+ * search's result), on the instance's device: the frame is replaced by the
+ * procedure's result and recertified, as with trstmi_set_phi. */
 int trstmi_instance_tr_solve(trstmi_handle h, const trstmi_tr_options *o,
                              trstmi_tr_row *trace, int cap, int *n_rows);
 

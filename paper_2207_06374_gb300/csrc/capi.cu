@@ -1063,13 +1063,14 @@ int tr_check(int N, int d, const trstmi_tr_options* o) {
 }
 }  // namespace
 
-int trstmi_tr_solve(int N, int d, double* phi, const trstmi_tr_options* o, trstmi_tr_row* trace,
-                    int cap, int* n_rows) {
+namespace {
+int tr_solve_on(int device, int N, int d, double* phi, const trstmi_tr_options* o,
+                trstmi_tr_row* trace, int cap, int* n_rows) {
   int rc = tr_check(N, d, o);
   if (rc) return rc;
   if (!phi || cap < 0) return TRSTMI_EINVAL;
   int num_sms = 0;
-  if ((rc = ensure_device(0, &num_sms)) != TRSTMI_OK) return rc;
+  if ((rc = ensure_device(device, &num_sms)) != TRSTMI_OK) return rc;
   const size_t nv = (size_t)N * d * sizeof(double2);
   const size_t o_scr = align_up(nv, 256);
   void* buf = nullptr;
@@ -1087,6 +1088,12 @@ int trstmi_tr_solve(int N, int d, double* phi, const trstmi_tr_options* o, trstm
   }
   cudaFree(buf);
   return rc;
+}
+}  // namespace
+
+int trstmi_tr_solve(int N, int d, double* phi, const trstmi_tr_options* o, trstmi_tr_row* trace,
+                    int cap, int* n_rows) {
+  return tr_solve_on(0, N, d, phi, o, trace, cap, n_rows);
 }
 
 int trstmi_tr_multistart(int N, int d, uint64_t seed0, int L, const trstmi_tr_options* o,
@@ -1164,7 +1171,9 @@ int trstmi_instance_tr_solve(trstmi_handle h, const trstmi_tr_options* o, trstmi
   std::vector<double> phi(2 * (size_t)h->N * h->d);
   int rc = trstmi_get_phi(h, phi.data());
   if (rc) return rc;
-  if ((rc = trstmi_tr_solve(h->N, h->d, phi.data(), o, trace, cap, n_rows)) != TRSTMI_OK) return rc;
+  if ((rc = tr_solve_on(h->opt.device, h->N, h->d, phi.data(), o, trace, cap, n_rows)) !=
+      TRSTMI_OK)
+    return rc;
   return trstmi_set_phi(h, phi.data());
 }
 
