@@ -338,6 +338,10 @@ typedef struct trstmi_request {
   int32_t want_phi;        /* keep the final frame for trstmi_poll */
   double target_mu;        /* stop at mu <= target_mu if > 0 ... */
   double target_rel_welch; /* ... else at mu <= target_rel_welch * Welch bound if > 0 */
+  double deadline_ms;      /* 0 = none; > 0: a request not finished within deadline_ms of
+                              its submission ends with TRSTMI_ETIMEOUT -- dropped from the
+                              queue if it has not started, else retired at the next round
+                              boundary with the iterations and mu it reached */
 } trstmi_request;
 
 typedef struct trstmi_result {
@@ -357,7 +361,7 @@ typedef struct trstmi_server_stats_t {
   size_t hbm_in_use;       /* bytes of the budget held by resident searches */
   int32_t active_slots, queued;
   int32_t worker_status;   /* TRSTMI_OK, or the error that stopped the loop */
-  int32_t reserved;
+  int32_t timed_out;       /* requests that ended with TRSTMI_ETIMEOUT */
 } trstmi_server_stats_t;
 
 void trstmi_default_server_opts(trstmi_server_opts *opts);

@@ -206,6 +206,7 @@ struct trstmi_server {
   std::thread worker;
   // statistics
   uint64_t submitted = 0, admitted = 0, completed = 0, cancelled = 0, rounds = 0;
+  int32_t timed_out = 0;
   uint64_t pairs_scored = 0;
   double gpu_busy_s = 0.0;
 };
@@ -362,6 +363,11 @@ int admit(trstmi_server* sv, uint64_t ticket, Req& r, Slot* out) {
   return TRSTMI_OK;
 }
 
+// a request past its deadline (deadline_ms after submission)
+bool expired(const Req& r, int64_t now) {
+  return r.req.deadline_ms > 0.0 && (double)(now - r.t_submit) > r.req.deadline_ms * 1e6;
+}
+
 void retire(trstmi_server* sv, size_t k, const DevState& st, int status) {
   Slot& sl = sv->slots[k];
   Req& r = sv->reqs[sl.ticket];
@@ -386,7 +392,9 @@ void retire(trstmi_server* sv, size_t k, const DevState& st, int status) {
   sv->free_states.push_back(sl.state_idx);
   sv->slots.erase(sv->slots.begin() + k);
   sv->active_count = (int)sv->slots.size();
-  if (status == TRSTMI_ECANCELLED) ++sv->cancelled; else ++sv->completed;
+  if (status == TRSTMI_ECANCELLED) ++sv->cancelled;
+  else if (status == TRSTMI_ETIMEOUT) ++sv->timed_out;
+  else ++sv->completed;
 }
 
 void worker_main(trstmi_server* sv) {
@@ -401,13 +409,14 @@ void worker_main(trstmi_server* sv) {
       if (sv->slots.empty() && pending.empty() && sv->queue.empty())
         sv->cv_work.wait_for(lk, std::chrono::milliseconds(50));
       while (!sv->queue.empty()) { pending.push_back(sv->queue.front()); sv->queue.pop_front(); }
-      // drop cancelled requests that never started
+      // drop cancelled and expired requests that never started
+      const int64_t now = now_ns();
       for (auto it = pending.begin(); it != pending.end();) {
         Req& r = sv->reqs[*it];
-        if (r.cancel) {
-          r.status = TRSTMI_ECANCELLED;
-          r.t_done = now_ns();
-          ++sv->cancelled;
+        if (r.cancel || expired(r, now)) {
+          r.status = r.cancel ? TRSTMI_ECANCELLED : TRSTMI_ETIMEOUT;
+          r.t_done = now;
+          if (r.cancel) ++sv->cancelled; else ++sv->timed_out;
           it = pending.erase(it);
           sv->cv_done.notify_all();
         } else {
@@ -491,6 +500,7 @@ void worker_main(trstmi_server* sv) {
       for (int k = 0; k < n; ++k)
         sv->pairs_scored += (uint64_t)(st[k].t - st[k].t_call) * (uint64_t)sv->slots[k].desc.K *
                             ((uint64_t)sv->slots[k].desc.N * (sv->slots[k].desc.N - 1) / 2);
+      const int64_t now = now_ns();
       for (int k = n - 1; k >= 0; --k) {
         const Req& r = sv->reqs[sv->slots[k].ticket];
         const uint32_t err = st[k].error;
@@ -502,6 +512,9 @@ void worker_main(trstmi_server* sv) {
           changed = true;
         } else if (st[k].done || st[k].t >= sv->slots[k].budget) {
           retire(sv, k, st[k], TRSTMI_OK);
+          changed = true;
+        } else if (expired(r, now)) {
+          retire(sv, k, st[k], TRSTMI_ETIMEOUT);
           changed = true;
         }
       }
@@ -632,7 +645,8 @@ int trstmi_server_create(const trstmi_server_opts* opts, trstmi_server** out) {
 int trstmi_submit(trstmi_server* sv, const trstmi_request* req, uint64_t* ticket) {
   if (!sv || !req || !ticket) return TRSTMI_EINVAL;
   if (req->N < 2 || req->d < 1 || req->d > kMaxD || req->budget_iters < 0 ||
-      (long long)req->N * ((req->d + 1) / 2) >= (1ll << 32))
+      (long long)req->N * ((req->d + 1) / 2) >= (1ll << 32) || !(req->deadline_ms >= 0.0) ||
+      !(req->deadline_ms < INFINITY))
     return TRSTMI_EINVAL;
   std::lock_guard<std::mutex> g(sv->mu);
   if (sv->worker_error) return sv->worker_error;
@@ -701,6 +715,7 @@ int trstmi_server_stats(trstmi_server* sv, trstmi_server_stats_t* out) {
   out->active_slots = (int32_t)sv->active_count.load();
   out->queued = (int32_t)sv->queue.size();
   out->worker_status = sv->worker_error;
+  out->timed_out = sv->timed_out;
   return TRSTMI_OK;
 }
 

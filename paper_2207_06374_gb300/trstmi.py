@@ -72,7 +72,8 @@ class ServerOpts(ctypes.Structure):
 class Request(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("d", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("budget_iters", ctypes.c_int32), ("want_phi", ctypes.c_int32),
-                ("target_mu", ctypes.c_double), ("target_rel_welch", ctypes.c_double)]
+                ("target_mu", ctypes.c_double), ("target_rel_welch", ctypes.c_double),
+                ("deadline_ms", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -89,7 +90,7 @@ class ServerStats(ctypes.Structure):
                 ("rounds", ctypes.c_uint64), ("pairs_scored", ctypes.c_uint64),
                 ("gpu_busy_s", ctypes.c_double), ("hbm_in_use", ctypes.c_size_t),
                 ("active_slots", ctypes.c_int32), ("queued", ctypes.c_int32),
-                ("worker_status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("worker_status", ctypes.c_int32), ("timed_out", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -592,8 +593,9 @@ class Server:
         self.close()
 
     def submit(self, N, d, seed, budget_iters, target_mu=0.0, target_rel_welch=0.0,
-               want_phi=False) -> int:
-        r = Request(N, d, seed, budget_iters, int(bool(want_phi)), target_mu, target_rel_welch)
+               want_phi=False, deadline_ms=0.0) -> int:
+        r = Request(N, d, seed, budget_iters, int(bool(want_phi)), target_mu, target_rel_welch,
+                    deadline_ms)
         t = ctypes.c_uint64()
         _check(lib().trstmi_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "trstmi_submit")
         self._shapes[t.value] = (d, N)

@@ -139,6 +139,30 @@ def test_cancel_and_unknown_ticket():
         assert st == T.TRSTMI_ENOTFOUND
 
 
+def test_deadlines_end_running_and_queued_requests():
+    """A request past its deadline ends with TRSTMI_ETIMEOUT: while running at
+    the next round boundary (with the iterations and mu it reached), while
+    queued without starting; a request without a deadline is unaffected."""
+    with T.Server(hbm_budget=64 << 20, max_slots=1, iters_per_round=5, K=8,
+                  precision="fp32") as srv:
+        long = srv.submit(512, 16, 1, 1_000_000, deadline_ms=300.0)
+        queued = srv.submit(16, 4, 2, 10, deadline_ms=100.0)
+        after = srv.submit(12, 3, 3, 20)
+        st, res, _ = srv.wait(long)
+        assert st == T.TRSTMI_ETIMEOUT
+        assert 0 < res.iters < 1_000_000 and res.mu >= res.welch
+        assert (res.t_done_ns - res.t_submit_ns) >= 300e6
+        st, res, _ = srv.wait(queued)
+        assert st == T.TRSTMI_ETIMEOUT and res.iters == 0
+        st, res, _ = srv.wait(after)
+        assert st == T.TRSTMI_OK and res.iters == 20
+        s = srv.stats()
+        assert s.timed_out == 2 and s.completed >= 1
+        with pytest.raises(T.TrstmiError) as e:
+            srv.submit(8, 2, 0, 10, deadline_ms=-1.0)
+        assert e.value.status == T.TRSTMI_EINVAL
+
+
 def test_bad_requests_rejected_on_host():
     with T.Server(hbm_budget=16 << 20, max_slots=2, K=8, precision="fp32") as srv:
         for bad in ((1, 3), (8, 0), (8, 300)):
