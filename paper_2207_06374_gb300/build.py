@@ -74,7 +74,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for l in logs:
             sys.stderr.write(l)
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), "-shared", "-gencode", GENCODE, "-o", tmp, *objs, "-lcudart", "-lcuda"]
+    cmd = [nvcc(), "-shared", "-gencode", GENCODE, "-o", tmp, *objs, "-lcudart", "-lcuda", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

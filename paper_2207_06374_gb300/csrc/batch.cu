@@ -28,6 +28,7 @@
 
 #include "../../include/trstmi.h"
 #include "kernels.h"
+#include "trace.h"
 
 using namespace trstmi;
 
@@ -293,6 +294,7 @@ void trstmi_batch_destroy(trstmi_batch_handle b) {
 
 int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds,
                         const trstmi_options* opt, trstmi_batch_handle* out) {
+  trstmi::TraceRange trace_range("trstmi_batch_create");
   if (!out) return TRSTMI_EINVAL;
   *out = nullptr;
   if (n < 1 || !N || !d || !seeds) return TRSTMI_EINVAL;
@@ -450,6 +452,7 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
 }
 
 int trstmi_batch_step(trstmi_batch_handle b, int iters, trstmi_step_info* info) {
+  trstmi::TraceRange trace_range("trstmi_batch_step");
   if (!b || iters < 0) return TRSTMI_EINVAL;
   BTRY(cudaSetDevice(b->opt.device));
   cudaStream_t s = b->stream;

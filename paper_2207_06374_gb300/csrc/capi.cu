@@ -19,6 +19,7 @@
 
 #include "../../include/trstmi.h"
 #include "kernels.h"
+#include "trace.h"
 
 using namespace trstmi;
 
@@ -396,6 +397,7 @@ void trstmi_destroy(trstmi_handle h) {
 }
 
 int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi_handle* out) {
+  trstmi::TraceRange trace_range("trstmi_create");
   if (!out) return TRSTMI_EINVAL;
   *out = nullptr;
   trstmi_options o;
@@ -503,6 +505,7 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
 }
 
 int trstmi_step(trstmi_handle h, int iters, trstmi_step_info* info) {
+  trstmi::TraceRange trace_range("trstmi_step");
   if (!h || iters < 0) return TRSTMI_EINVAL;
   TRY_CUDA(cudaSetDevice(h->opt.device));
   cudaStream_t s = h->stream;
@@ -547,6 +550,7 @@ int trstmi_shard_score_bytes(trstmi_handle h, size_t* bytes) {
 }
 
 int trstmi_shard_score(trstmi_handle h, int c_lo, int c_hi, void* scores) {
+  trstmi::TraceRange trace_range("trstmi_shard_score");
   if (!h || !scores || c_lo < 0 || c_hi < c_lo || c_hi > h->opt.K) return TRSTMI_EINVAL;
   TRY_CUDA(cudaSetDevice(h->opt.device));
   cudaStream_t s = h->stream;
@@ -564,6 +568,7 @@ int trstmi_shard_score(trstmi_handle h, int c_lo, int c_hi, void* scores) {
 }
 
 int trstmi_shard_finish(trstmi_handle h, const void* scores, trstmi_step_info* info) {
+  trstmi::TraceRange trace_range("trstmi_shard_finish");
   if (!h || !scores) return TRSTMI_EINVAL;
   TRY_CUDA(cudaSetDevice(h->opt.device));
   cudaStream_t s = h->stream;
@@ -925,6 +930,7 @@ int trstmi_lse_scratch_bytes(int N, int d, int count, int precision, size_t* byt
 int trstmi_lse_frames_device(int N, int d, int count, const double* v_dev, double delta,
                              int precision, void* scratch_dev, size_t scratch_bytes,
                              double* out_dev, double* grad_dev, void* stream) {
+  trstmi::TraceRange trace_range("trstmi_lse_frames_device");
   int rc = lse_check(N, d, count, delta, precision);
   if (rc) return rc;
   if (!v_dev || !scratch_dev || !out_dev) return TRSTMI_EINVAL;
@@ -941,6 +947,7 @@ int trstmi_lse_frames_device(int N, int d, int count, const double* v_dev, doubl
 
 int trstmi_lse_frames(int N, int d, int count, const double* v, double delta, int precision,
                       double* F, double* s, double* grad) {
+  trstmi::TraceRange trace_range("trstmi_lse_frames");
   int rc = lse_check(N, d, count, delta, precision);
   if (rc) return rc;
   if (!v || !F) return TRSTMI_EINVAL;
@@ -1011,6 +1018,7 @@ int certificates_of(int N, int d, const double* v_dev, double tol, int num_sms,
 
 int trstmi_frame_certificates(int N, int d, const double* phi, double tol,
                               trstmi_certificates* out) {
+  trstmi::TraceRange trace_range("trstmi_frame_certificates");
   if (N < 2 || d < 1 || d > kMaxD || !phi || !out || !(tol >= 1e-7 && tol <= 1.0))
     return TRSTMI_EINVAL;
   int num_sms = 0;
@@ -1027,6 +1035,7 @@ int trstmi_frame_certificates(int N, int d, const double* phi, double tol,
 }
 
 int trstmi_instance_certificates(trstmi_handle h, double tol, trstmi_certificates* out) {
+  trstmi::TraceRange trace_range("trstmi_instance_certificates");
   if (!h || !out || !(tol >= 1e-7 && tol <= 1.0)) return TRSTMI_EINVAL;
   TRY_CUDA(cudaSetDevice(h->opt.device));
   return certificates_of(h->N, h->d, reinterpret_cast<const double*>(h->phi64), tol,
@@ -1093,12 +1102,14 @@ int tr_solve_on(int device, int N, int d, double* phi, const trstmi_tr_options* 
 
 int trstmi_tr_solve(int N, int d, double* phi, const trstmi_tr_options* o, trstmi_tr_row* trace,
                     int cap, int* n_rows) {
+  trstmi::TraceRange trace_range("trstmi_tr_solve");
   return tr_solve_on(0, N, d, phi, o, trace, cap, n_rows);
 }
 
 int trstmi_tr_multistart(int N, int d, uint64_t seed0, int L, const trstmi_tr_options* o,
                          int batch_cap, trstmi_multistart_result* out, double* mu_all,
                          double* best_phi, trstmi_tr_row* trace, int cap, int* n_rows) {
+  trstmi::TraceRange trace_range("trstmi_tr_multistart");
   int rc = tr_check(N, d, o);
   if (rc) return rc;
   if (!out || cap < 0) return TRSTMI_EINVAL;

@@ -8,11 +8,13 @@
 #include <vector>
 
 #include "../../include/trstmi.h"
+#include "trace.h"
 
 extern "C" int trstmi_multistart(int N, int d, uint64_t seed0, int L, int iters,
                                  const trstmi_options* opt, int batch_cap,
                                  trstmi_multistart_result* out, double* mu_all,
                                  double* best_phi) {
+  trstmi::TraceRange trace_range("trstmi_multistart");
   if (!out || N < 2 || d < 1 || iters < 0) return TRSTMI_EINVAL;
   if (L <= 0) L = 2 * d * d;
   const int cap = batch_cap > 0 ? std::min(batch_cap, L) : L;

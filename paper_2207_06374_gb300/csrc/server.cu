@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "../../include/trstmi.h"
+#include "trace.h"
 #include "kernels.h"
 
 using namespace trstmi;
@@ -470,6 +471,7 @@ void worker_main(trstmi_server* sv) {
       changed = false;
     }
     // one round: I iterations of every active slot, shared launches
+    trstmi::TraceRange trace_range("server round");
     const int n = (int)sv->slots.size();
     const int64_t t0 = now_ns();
     cudaStream_t s = sv->stream;
