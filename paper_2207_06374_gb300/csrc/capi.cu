@@ -93,6 +93,8 @@ struct trstmi_instance {
   uint32_t* misc = nullptr;                // [0] npairs, [1] overflow (standalone certify)
   uint2* pairs = nullptr;                  // kPairCap
   TraceRowDev* trace = nullptr;            // trace_cap
+  float* planes_top = nullptr;             // screen modes: the top-k survivors drawn once
+                                           // for their binary32 re-score (2dN floats each)
   float* planes = nullptr;                 // TRSTMI_FP32: the K candidates of an iteration,
                                            // drawn once as [i][column] planes (2dN floats each)
   std::map<int, cudaGraphExec_t> graphs;
@@ -275,6 +277,11 @@ int enqueue_iteration_finish(trstmi_instance* h, cudaStream_t s) {
     src.cand_list = h->topk;
     src.st = st;
     src.gate = &st->use_screen;
+    // the survivors drawn once (the tile pass's gen_column arithmetic), then
+    // the double-buffered tile pass over them
+    TRY_CUDA(launch_gen_planes_f32(N, d, k, h->phi32, h->seed, 0u, st, 0u, 0.0, h->planes_top, s,
+                                   h->topk, &st->use_screen));
+    src.planes = h->planes_top;
     TRY_CUDA(launch_gram_f32(N, d, k, src, h->mu2_top, nullptr, h->num_sms, s));
     TRY_CUDA(launch_materialize64(N, d, h->seed, st, h->topk, h->mu2_top, k, h->phi64,
                                   h->cand64, h->cand32, s));
@@ -447,6 +454,8 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   const size_t planes_bytes = (size_t)K * 2 * nd * sizeof(float);
   const size_t o_planes = (o.precision == TRSTMI_FP32 && planes_bytes <= ((size_t)1 << 30))
                               ? take(planes_bytes) : (size_t)-1;
+  const size_t o_ptop = is_screen(o.precision) ? take((size_t)k * 2 * nd * sizeof(float))
+                                               : (size_t)-1;
   h->block_bytes = off;
   if (cudaMalloc(&h->block, off) != cudaSuccess) {
     cudaGetLastError();
@@ -470,6 +479,7 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   h->pairs = (uint2*)(b + o_pairs);
   h->trace = (TraceRowDev*)(b + o_trace);
   if (o_planes != (size_t)-1) h->planes = (float*)(b + o_planes);
+  if (o_ptop != (size_t)-1) h->planes_top = (float*)(b + o_ptop);
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
     trstmi_destroy(h);
     return TRSTMI_ECUDA;

@@ -47,7 +47,9 @@ struct GramSource {
 // One thread per column, the arithmetic of the tile pass.
 cudaError_t launch_gen_planes_f32(int N, int d, int count, const float2* phi, uint64_t seed,
                                   uint32_t c0, DevState* st, uint32_t t, double delta,
-                                  float* planes, cudaStream_t s);
+                                  float* planes, cudaStream_t s,
+                                  const uint32_t* cand_list = nullptr,
+                                  const uint32_t* gate = nullptr);
 
 // Optional pair filter of the binary32 certification pass.
 struct PairFilter {

@@ -401,32 +401,117 @@ __global__ void __launch_bounds__(256, 3) k_gram_planes(const GramArgs<float> a,
   cp_async_wait<0>();
 }
 
-// Candidates drawn once for the tile pass (see launch_gen_planes_f32).
-__global__ void k_gen_planes_f32(int N, int d, int count, const float2* phi, uint64_t seed,
-                                 uint32_t c0, DevState* st, uint32_t t, float delta,
-                                 float* planes) {
-  if (st) {
-    if (!st->active) return;
-    t = st->t + 1u;
-    delta = (float)st->delta_used;
+// Candidates drawn once for the tile pass.  Many columns (the K candidates of
+// an iteration): k_gen_planes_f32, one thread per column running gen_column.
+// Few columns (the top-k survivors), where that leaves most SMs idle: two
+// steps with gen_column's arithmetic -- k_draw_planes_f32 spreads the draws
+// (Philox, Box-Muller, phi + delta z) over (candidate, column, entry pair)
+// items, k_norm_planes_f32 forms each column's squared norm in the same
+// sequential order over i and divides.  Both give every value the bits
+// gen_column gives it.
+struct PlanesDraw {
+  int N, d, P, count;
+  const float2* phi;
+  uint64_t seed;
+  uint32_t c0, t;
+  float delta;
+  float* planes;
+  const uint32_t* cand_list;
+  const uint32_t* gate;
+  DevState* st;
+};
+
+__device__ __forceinline__ bool planes_draw_setup(PlanesDraw& a) {
+  if (a.gate && *a.gate == 0u) return false;
+  if (a.st) {
+    if (!a.st->active) return false;
+    a.t = a.st->t + 1u;
+    a.delta = (float)a.st->delta_used;
   }
+  return true;
+}
+
+__global__ void k_gen_planes_f32(PlanesDraw a) {
+  if (!planes_draw_setup(a)) return;
   const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (g >= (long long)count * N) return;
-  const int slot = (int)(g / N), j = (int)(g - (long long)slot * N);
-  float* pre = planes + (size_t)slot * 2 * d * N;
+  if (g >= (long long)a.count * a.N) return;
+  const int slot = (int)(g / a.N), j = (int)(g - (long long)slot * a.N);
+  float* pre = a.planes + (size_t)slot * 2 * a.d * a.N;
+  float* pim = pre + (size_t)a.d * a.N;
+  const uint32_t c = a.cand_list ? a.cand_list[slot] : a.c0 + (uint32_t)slot;
+  if (!gen_column<float>(a.phi, a.d, j, a.seed, c, a.t, 0u, a.delta, pre + j, pim + j, a.N) && a.st)
+    atomicOr(&a.st->error, (uint32_t)kErrZeroColumn);
+}
+
+__global__ void k_draw_planes_f32(PlanesDraw a) {
+  if (!planes_draw_setup(a)) return;
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long per = (long long)a.N * a.P;
+  if (g >= (long long)a.count * per) return;
+  const int slot = (int)(g / per);
+  const int rem = (int)(g - (long long)slot * per);
+  const int j = rem / a.P, p = rem - j * a.P;
+  const uint32_t c = a.cand_list ? a.cand_list[slot] : a.c0 + (uint32_t)slot;
+  const int d = a.d, N = a.N;
+  float* pre = a.planes + (size_t)slot * 2 * d * N;
   float* pim = pre + (size_t)d * N;
-  if (!gen_column<float>(phi, d, j, seed, c0 + (uint32_t)slot, t, 0u, delta, pre + j, pim + j,
-                         N) && st)
-    atomicOr(&st->error, (uint32_t)kErrZeroColumn);
+  const PhiloxOut u = philox4x32_10((uint32_t)j * (uint32_t)a.P + (uint32_t)p, c, a.t, 0u,
+                                    seed_lo(a.seed), seed_hi(a.seed));
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = 2 * p + h;
+    if (i < d) {
+      float zr, zi;
+      cn_draw<float>(u.x[2 * h], u.x[2 * h + 1], zr, zi);
+      const float2 v = a.phi[(size_t)j * d + i];
+      pre[(size_t)i * N + j] = add_rn(v.x, mul_rn(a.delta, zr));
+      pim[(size_t)i * N + j] = add_rn(v.y, mul_rn(a.delta, zi));
+    }
+  }
+}
+
+__global__ void k_norm_planes_f32(PlanesDraw a) {
+  if (!planes_draw_setup(a)) return;
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= (long long)a.count * a.N) return;
+  const int slot = (int)(g / a.N), j = (int)(g - (long long)slot * a.N);
+  const int d = a.d, N = a.N;
+  float* pre = a.planes + (size_t)slot * 2 * d * N;
+  float* pim = pre + (size_t)d * N;
+  float s = 0.f;
+  for (int i = 0; i < d; ++i) {
+    const float xr = pre[(size_t)i * N + j], xi = pim[(size_t)i * N + j];
+    s = add_rn(s, add_rn(mul_rn(xr, xr), mul_rn(xi, xi)));
+  }
+  if (!(s > 0.f)) {
+    for (int i = 0; i < d; ++i) { pre[(size_t)i * N + j] = 0.f; pim[(size_t)i * N + j] = 0.f; }
+    if (a.st) atomicOr(&a.st->error, (uint32_t)kErrZeroColumn);
+    return;
+  }
+  const float nrm = sqrt_rn(s);
+  for (int i = 0; i < d; ++i) {
+    pre[(size_t)i * N + j] = div_rn(pre[(size_t)i * N + j], nrm);
+    pim[(size_t)i * N + j] = div_rn(pim[(size_t)i * N + j], nrm);
+  }
 }
 
 cudaError_t launch_gen_planes_f32(int N, int d, int count, const float2* phi, uint64_t seed,
                                   uint32_t c0, DevState* st, uint32_t t, double delta,
-                                  float* planes, cudaStream_t s) {
+                                  float* planes, cudaStream_t s, const uint32_t* cand_list,
+                                  const uint32_t* gate) {
   if (count < 1) return cudaSuccess;
-  const long long threads = (long long)count * N;
-  k_gen_planes_f32<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-      N, d, count, phi, seed, c0, st, t, (float)delta, planes);
+  PlanesDraw a{N, d, (d + 1) / 2, count, phi, seed, c0, t, (float)delta, planes, cand_list, gate,
+               st};
+  const long long cols = (long long)count * N;
+  if (cols >= 65536) {
+    k_gen_planes_f32<<<(unsigned)((cols + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  const long long items = cols * a.P;
+  k_draw_planes_f32<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_norm_planes_f32<<<(unsigned)((cols + 255) / 256), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -666,15 +751,18 @@ cudaError_t launch_commit_f64(int N, int d, uint64_t seed, DevState* st, double2
 // survivors' binary32 scores are known already and are copied into mu2_top
 // (the re-score pass, gated on use_screen, then does not run): the values are
 // bit-identical to a re-score, which runs the same pair arithmetic.
+// The k smallest keys (mu^2 bits << 32 | candidate), in increasing order: each
+// warp extracts its own k smallest keys by k rounds of warp minima above the
+// previous one (no CTA barrier), then warp 0 does the same over the warps'
+// lists.  Keys are unique, so the result is the k smallest of all K.
+constexpr int kTopkMax = 64;
 __global__ void k_topk(DevState* st, const unsigned int* mu2, int K, int k, uint32_t* topk,
                        unsigned int* mu2_top) {
   if (!st->active) return;
-  __shared__ unsigned long long sk[32];
-  __shared__ unsigned long long last;
-  if (threadIdx.x == 0) last = 0ull;
-  __syncthreads();
+  __shared__ unsigned long long cand[32 * kTopkMax];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long floor_key = 0ull;
   for (int r = 0; r < k; ++r) {
-    const unsigned long long floor_key = last;
     unsigned long long best = ~0ull;
     for (int c = threadIdx.x; c < K; c += blockDim.x) {
       const unsigned long long key = ((unsigned long long)mu2[c] << 32) | (unsigned)c;
@@ -685,15 +773,29 @@ __global__ void k_topk(DevState* st, const unsigned int* mu2, int K, int k, uint
       const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
       best = ov < best ? ov : best;
     }
-    if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = best;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = sk[w] < best ? sk[w] : best;
+    if (lane == 0) cand[warp * k + r] = best;
+    floor_key = best;
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  const int n = nw * k;
+  floor_key = 0ull;
+  for (int r = 0; r < k; ++r) {
+    unsigned long long best = ~0ull;
+    for (int q = lane; q < n; q += 32) {
+      const unsigned long long key = cand[q];
+      if ((r == 0 || key > floor_key) && key < best) best = key;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+      best = ov < best ? ov : best;
+    }
+    if (lane == 0) {
       topk[r] = (uint32_t)(best & 0xffffffffull);
       if (!st->use_screen) mu2_top[r] = (unsigned int)(best >> 32);
-      last = best;
     }
-    __syncthreads();
+    floor_key = best;
   }
 }
 
