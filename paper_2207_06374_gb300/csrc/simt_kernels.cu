@@ -94,7 +94,9 @@ __device__ bool gen_candidate_cta(const typename Cplx<T>::type* phi, int N, int 
   const int P = (d + 1) >> 1;
   __syncthreads();
   for (int q = threadIdx.x; q < N * P; q += blockDim.x) {
-    const int j = q / P, p = q - j * P;
+    // consecutive threads take consecutive columns of one entry pair, so their
+    // shared-memory stores fall in consecutive words
+    const int p = q / N, j = q - p * N;
     const PhiloxOut u = philox4x32_10((uint32_t)j * (uint32_t)P + (uint32_t)p, c, t, 0u, k0, k1);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
