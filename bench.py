@@ -83,7 +83,11 @@ def flops_per_pair(d):
 
 def kernels_per_step(precision):
     # one k_set_stop per trstmi_step call plus the iteration's kernels
-    return 1 + {"fp64": 4, "fp32": 5, "bf16": 11, "tf32": 11}[precision]
+    # screen modes: iter_begin, screen, the gated fp32 ranking pass, top-k, the
+    # survivors' draw (2) and re-score, the fp64 draw of the winner, the certify
+    # passes (binary32 max, filter, binary64 pairs, gated binary64 pass),
+    # decide, commit
+    return 1 + {"fp64": 4, "fp32": 5, "bf16": 14, "tf32": 14}[precision]
 
 
 def dist_env():
