@@ -58,6 +58,10 @@ WORKLOADS = {
                                "the paper's trust-region CG-Steihaug procedure on F_{s,delta} "
                                "(delta = 0.01, at most 20 CG steps per iteration) for one frame, "
                                "complex d=32 N=1024, binary64"),
+    # every row of Table 2 (d = 2..9, N = d^2, 2 d^2 trials each)
+    "table2_all": (None, None, None, "fp64",
+                   "the paper's whole algorithm on every row of Table 2: d = 2..9, N = d^2, "
+                   "2d^2 trials, seven smoothing stages, binary64"),
     # K = trials (2 d^2); the paper's Table 2 row for this shape: 189 s, mu 0.3705
     "table2_d8_n64": (8, 64, 128, "fp64",
                       "the paper's whole algorithm: 2d^2 = 128 random initialisations, each "
@@ -66,6 +70,9 @@ WORKLOADS = {
 }
 TABLE2_PAPER_S = 189.0       # Table 2, TRSTMI column, d = 8, N = 64 (i7-8750H CPU)
 TABLE2_PAPER_MU = 0.3705
+# Table 2, TRSTMI column: d -> (seconds, mu rounded up at the fourth decimal), N = d^2
+TABLE2_PAPER = {2: (2.36, 0.5774), 3: (13.1, 0.5001), 4: (21.3, 0.4473), 5: (39.3, 0.4083),
+                6: (79.7, 0.3780), 7: (146.0, 0.3536), 8: (189.0, 0.3705), 9: (388.0, 0.3575)}
 LSE_DELTA = 0.01
 TR_MAX_CG = 20
 L2_FLUSH_BYTES = 512 << 20
@@ -398,6 +405,11 @@ def main():
         return
     if wl == "serving":
         run_serving(args, ws, rank, local, dist, torch, T)
+        if dist:
+            dist.destroy_process_group()
+        return
+    if wl == "table2_all":
+        run_table2_all(args, ws, rank, local, dist, torch, T)
         if dist:
             dist.destroy_process_group()
         return
@@ -876,6 +888,52 @@ def run_trust_region(args, ws, rank, local, dist, torch, T):
                                 "sample": f"1 iteration with at most 3 CG steps ({oevals} "
                                           f"objective evaluations, {odt:.1f} s), scaled to "
                                           f"{evals / max(iters, 1):.1f} evaluations per iteration"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_table2_all(args, ws, rank, local, dist, torch, T):
+    """Every row of the paper's Table 2: the whole algorithm (2 d^2 trials of the
+    trust-region procedure over seven smoothing stages, minimum over the
+    trials) for d = 2..9 at N = d^2, one run per row, host clock around each
+    library call.  value = the sum of the rows' seconds (lower is better)."""
+    deltas = (0.1, 0.03, 0.01, 0.003, 0.001, 3e-4, 1e-4)
+    T.tr_multistart(4, 2, SEED, 2, deltas=(0.1,), max_outer=2, want_phi=False)   # warm-up
+    torch.cuda.synchronize()
+    rows = {}
+    total = 0.0
+    with Clocks(local) as clk:
+        for d in range(2, 10):
+            N = d * d
+            t0 = time.perf_counter()
+            res, mus, _, _ = T.tr_multistart(N, d, SEED + 1000 * rank, 0, deltas=deltas,
+                                             want_phi=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            total += dt
+            ps, pmu = TABLE2_PAPER[d]
+            rows[f"d{d}_n{N}"] = {"seconds": dt, "mu": res.mu, "trials": res.trials,
+                                  "paper_seconds": ps, "paper_mu": pmu,
+                                  "welch": float(np.sqrt((N - d) / (d * (N - 1))))}
+    clocks = clk.summary()
+    paper_total = sum(v[0] for v in TABLE2_PAPER.values())
+    line = {"metric": "seconds for the whole algorithm on every row of Table 2",
+            "value": total, "unit": "s", "n_gpus": ws, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * total, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": total / paper_total, "dtype": "f64",
+            "data": "synthetic (seeded Philox initial frames, as trstmi_create draws them)",
+            "config": {"workload": "table2_all", "rows": rows,
+                       "paper_seconds_total": paper_total,
+                       "paper_hardware": "Intel i7-8750H CPU (Table 2)",
+                       "parallelism": f"independent trials per GPU x{ws}"},
+            "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": None, "peak": None,
+                         "frac": None, "traffic": None,
+                         "kernel": "k_tr_resident (one CTA per trial)",
+                         "note": "see table2_d8_n64"},
+            "gpu_launches": 16,
+            "e2e": {"value": total, "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0, "call": "trstmi_tr_multistart per row"},
+            "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
