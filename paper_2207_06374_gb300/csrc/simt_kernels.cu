@@ -570,7 +570,7 @@ static cudaError_t launch_gram(int N, int d, int nslots, const GramSource& src,
                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_tile<T, 1>, 256, smem);
   if (oe != cudaSuccess) return oe;
   per_sm = std::max(per_sm, 1);
-  const int grid = (int)std::min<long long>(items, (long long)num_sms * per_sm * 4);
+  const int grid = (int)std::min<long long>(items, (long long)num_sms * per_sm);
   switch (R) {
     case 4: k_gram_tile<T, 4><<<grid, 256, smem, s>>>(a); break;
     case 2: k_gram_tile<T, 2><<<grid, 256, smem, s>>>(a); break;
