@@ -208,3 +208,16 @@ def test_central_difference_products_are_within_1e_6_of_the_exact_ones(delta):
         he = O.lse_hv_exact(v, delta, u)
         hf = O.lse_hv(v, delta, 1e-6, u)
         assert np.max(np.abs(hf - he)) <= 1e-6 * np.max(np.abs(he))
+
+
+@pytest.mark.parametrize("d,seed", [(6, 1), (7, 2)])
+def test_reaches_the_sics_of_c6_and_c7(d, seed):
+    """Table 2's rows d = 6, 7 (N = d^2): from the seeded initial frame the
+    procedure ends at the Welch bound 1/sqrt(d+1), a SIC, below the paper's
+    printed values 0.3780 and 0.3536 (rounded up)."""
+    N = d * d
+    vf, _ = O.tr_solve(O.init(N, d, seed), O.tr_opts(deltas=SCHEDULE, max_outer=100,
+                                                      max_cg=200))
+    mu = np.sqrt(O.mu2(vf))
+    assert mu == pytest.approx(1 / np.sqrt(d + 1), abs=1e-8)
+    assert mu <= {6: 0.3780, 7: 0.3536}[d]
