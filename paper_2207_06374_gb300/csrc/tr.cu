@@ -574,6 +574,13 @@ __device__ void res_axpby(double a, const double* x, double b, const double* y, 
 
 // F_{s,delta} and s at v; the gradient into gout when it is not null.
 // Returns false (in every thread) if a column of v is zero.
+//
+// Binary64 runs at about two fused multiply-adds per clock per SM on this
+// part, so the pass is written for the fewest binary64 operations: one
+// reciprocal per column and one of delta and of the sum (no division per
+// entry or pair), one exponential per pair (kept in W), and the weighted
+// Gram M = w (.) G formed once per pair, so that the gradient's inner loop is
+// four fused multiply-adds per (k, i, j).
 __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double delta,
                          double* gout, double* F, double* smax) {
   const int N = a.N, d = a.d, P = a.P;
@@ -586,11 +593,11 @@ __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double d
       q += re * re + im * im;
     }
     if (!(q > 0.0)) zero = 1.0;
-    const double r = sqrt(q);
-    S.rn[k] = r;
+    const double r = sqrt(q), inv = 1.0 / r;
+    S.rn[k] = inv;
     for (int i = 0; i < d; ++i) {
-      S.phi[2 * (k * d + i)] = v[2 * (k * d + i)] / r;
-      S.phi[2 * (k * d + i) + 1] = v[2 * (k * d + i) + 1] / r;
+      S.phi[2 * (k * d + i)] = v[2 * (k * d + i)] * inv;
+      S.phi[2 * (k * d + i) + 1] = v[2 * (k * d + i) + 1] * inv;
     }
   }
   if (res_max(zero, S.red) > 0.0) return false;
@@ -612,28 +619,45 @@ __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double d
     hi = fmax(hi, x);
   }
   const double s = res_max(hi, S.red);
+  const double inv_delta = 1.0 / delta;
   double e = 0.0;
-  for (int q = threadIdx.x; q < P; q += kResThreads) e += exp((S.W[q] - s) / delta);
+  for (int q = threadIdx.x; q < P; q += kResThreads) {
+    const double t = exp((S.W[q] - s) * inv_delta);
+    S.W[q] = t;
+    e += t;
+  }
   const double Ssum = res_sum(e, S.red);
   *F = s + delta * log(Ssum);
   *smax = s;
   if (!gout) return true;
-  for (int q = threadIdx.x; q < P; q += kResThreads) S.W[q] = exp((S.W[q] - s) / delta) / Ssum;
+  // M = w (.) G with the softmax weights w = exp((x - s)/delta) / Ssum
+  const double inv_sum = 1.0 / Ssum;
+  for (int q = threadIdx.x; q < P; q += kResThreads) {
+    const double w = S.W[q] * inv_sum;
+    S.Gre[q] *= w;
+    S.Gim[q] *= w;
+  }
   __syncthreads();
-  // g_k = 2 sum_{j != k} w_jk G_jk phi_j (G Hermitian), then the projection
+  // g_k = 2 sum_{j != k} M_jk phi_j (M Hermitian: M_jk = conj(M_kj) for j > k),
+  // j ascending, then the projection
   const int half = d * N;
   for (int t = threadIdx.x; t < half; t += kResThreads) {
     const int k = t / d, i = t - k * d;
     double gr = 0.0, gi = 0.0;
-    for (int j = 0; j < N; ++j) {
-      if (j == k) continue;
-      const int lo = j < k ? j : k, hi2 = j < k ? k : j;
-      const int q = lo * N - lo * (lo + 1) / 2 + (hi2 - lo - 1);
-      const double mr = S.W[q] * S.Gre[q];
-      const double mi = j < k ? S.W[q] * S.Gim[q] : -S.W[q] * S.Gim[q];
+    for (int j = 0; j < k; ++j) {
+      const int q = j * N - j * (j + 1) / 2 + (k - j - 1);
+      const double mr = S.Gre[q], mi = S.Gim[q];
       const double pr = S.phi[2 * (j * d + i)], pi = S.phi[2 * (j * d + i) + 1];
       gr += mr * pr - mi * pi;
       gi += mr * pi + mi * pr;
+    }
+    const int base = k * N - k * (k + 1) / 2 - k - 1;
+    for (int j = k + 1; j < N; ++j) {
+      const int q = base + j;
+      const double mr = S.Gre[q], mi = S.Gim[q];
+      const double pr = S.phi[2 * (j * d + i)], pi = S.phi[2 * (j * d + i) + 1];
+      gr += mr * pr + mi * pi;
+      gi += mr * pi - mi * pr;
     }
     gout[2 * (k * d + i)] = 2.0 * gr;
     gout[2 * (k * d + i) + 1] = 2.0 * gi;
@@ -644,7 +668,7 @@ __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double d
     for (int i = 0; i < d; ++i)
       rad += S.phi[2 * (k * d + i)] * gout[2 * (k * d + i)] +
              S.phi[2 * (k * d + i) + 1] * gout[2 * (k * d + i) + 1];
-    const double inv = 1.0 / S.rn[k];
+    const double inv = S.rn[k];
     for (int i = 0; i < d; ++i) {
       gout[2 * (k * d + i)] = (gout[2 * (k * d + i)] - S.phi[2 * (k * d + i)] * rad) * inv;
       gout[2 * (k * d + i) + 1] =
