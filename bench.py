@@ -184,6 +184,7 @@ KERNEL_SOURCES = {
 KERNEL_SOURCES["lse"] = ["paper_2207_06374_gb300/csrc/lse.cu", "paper_2207_06374_gb300/csrc/tile.cuh",
                          "paper_2207_06374_gb300/csrc/common.cuh"]
 KERNEL_SOURCES["tf32"] = KERNEL_SOURCES["bf16"]
+KERNEL_SOURCES["tr"] = ["paper_2207_06374_gb300/csrc/tr.cu"]
 KERNEL_SOURCES["batched"] = KERNEL_SOURCES["fp32"]
 KERNEL_PROFILE = {"bf16": "k_screen_bf16_d32_n1024.txt", "tf32": "k_screen_tf32_d32_n768.txt",
                   "fp32": "k_gram_planes_f32_d32_n1024.txt",
@@ -224,6 +225,17 @@ def profiled_traffic(precision):
 def fp32_alu_peak_tflops(sm_mhz):
     # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def resident_tr_flops(d, N, work):
+    """Algorithmic binary64 flops of the resident trust-region runs whose
+    per-trial (iterations, Hessian products) are the rows of `work`: an
+    objective-and-gradient pass is 24 d P (the Gram 8 d P, the gradient
+    16 d P, P = N(N-1)/2 pairs), an objective-only pass 8 d P; an iteration
+    takes one of each, a Hessian product two gradients.  Exponentials and the
+    O(dN) vector work are not counted."""
+    P = N * (N - 1) // 2
+    return float(d * P * (32 * int(work[:, 0].sum()) + 48 * int(work[:, 1].sum())))
 
 
 def cpu_baseline(d, N, K, steps=1):
@@ -903,21 +915,30 @@ def run_table2_all(args, ws, rank, local, dist, torch, T):
     T.tr_multistart(4, 2, SEED, 2, deltas=(0.1,), max_outer=2, want_phi=False)   # warm-up
     torch.cuda.synchronize()
     rows = {}
-    total = 0.0
+    total, flops = 0.0, 0.0
     with Clocks(local) as clk:
         for d in range(2, 10):
             N = d * d
+            work = np.zeros((2 * d * d, 2), dtype=np.int32)
             t0 = time.perf_counter()
             res, mus, _, _ = T.tr_multistart(N, d, SEED + 1000 * rank, 0, deltas=deltas,
-                                             want_phi=False)
+                                             want_phi=False, work=work)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             total += dt
+            fl = resident_tr_flops(d, N, work)
+            flops += fl
             ps, pmu = TABLE2_PAPER[d]
             rows[f"d{d}_n{N}"] = {"seconds": dt, "mu": res.mu, "trials": res.trials,
                                   "paper_seconds": ps, "paper_mu": pmu,
-                                  "welch": float(np.sqrt((N - d) / (d * (N - 1))))}
+                                  "welch": float(np.sqrt((N - d) / (d * (N - 1)))),
+                                  "iterations": int(work[:, 0].sum()),
+                                  "hessian_products": int(work[:, 1].sum()),
+                                  "fp64_tflops": fl / dt / 1e12}
     clocks = clk.summary()
+    peaks, _ = measured_peaks()
+    peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0)) / 64
+    achieved = flops / total / 1e12
     paper_total = sum(v[0] for v in TABLE2_PAPER.values())
     line = {"metric": "seconds for the whole algorithm on every row of Table 2",
             "value": total, "unit": "s", "n_gpus": ws, "steps": 1, "warmup": 1,
@@ -928,10 +949,14 @@ def run_table2_all(args, ws, rank, local, dist, torch, T):
                        "paper_seconds_total": paper_total,
                        "paper_hardware": "Intel i7-8750H CPU (Table 2)",
                        "parallelism": f"independent trials per GPU x{ws}"},
-            "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": None, "peak": None,
-                         "frac": None, "traffic": None,
-                         "kernel": "k_tr_resident (one CTA per trial)",
-                         "note": "see table2_d8_n64"},
+            "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_tr_resident (one CTA per trial): algorithmic binary64 "
+                                   "flops of every trial's passes over the rows' summed "
+                                   "wall time (rows with fewer trials than SMs, and the "
+                                   "slowest trial of each row, leave SMs idle)",
+                         "peak_source": "fp64 peak derived: 152 SMs x 2 lanes x 2 flops x "
+                                        f"{peaks.get('sm_max_mhz', 2070.0)} MHz"},
             "gpu_launches": 16,
             "e2e": {"value": total, "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0, "call": "trstmi_tr_multistart per row"},
@@ -952,15 +977,22 @@ def run_table2(args, ws, rank, local, dist, torch, T):
     T.tr_multistart(N, d, SEED, 4, deltas=(0.1,), max_outer=2, want_phi=False)   # warm-up
     torch.cuda.synchronize()
     times, res, mus = [], None, None
+    work = np.zeros((K, 2), dtype=np.int32)
     with Clocks(local) as clk:
         for _ in range(steps):
             t0 = time.perf_counter()
             res, mus, phi, tr = T.tr_multistart(N, d, SEED + 1000 * rank, K, deltas=deltas,
-                                                trace_cap=1 << 14)
+                                                trace_cap=1 << 14, work=work)
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
     clocks = clk.summary()
     t = sum(times) / len(times)
+    peaks, _ = measured_peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = fp32_alu_peak_tflops(sm_mhz) / 64
+    # the trials' passes, plus the winning trial's second run for its trace
+    flops = resident_tr_flops(d, N, work) + resident_tr_flops(d, N, work[res.best:res.best + 1])
+    achieved = flops / t / 1e12
     if dist:
         tt = torch.tensor([t], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -977,17 +1009,22 @@ def run_table2(args, ws, rank, local, dist, torch, T):
                        "paper_seconds": TABLE2_PAPER_S,
                        "paper_hardware": "Intel i7-8750H CPU (Table 2)",
                        "winning_trial_iterations": int(len(tr)),
+                       "iterations": int(work[:, 0].sum()),
+                       "hessian_products": int(work[:, 1].sum()),
                        "l2": "all frames and vectors stay in L2; no flush",
                        "parallelism": f"independent trials per GPU x{ws}"},
-            "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": None, "peak": None,
-                         "frac": None, "traffic": None,
+            "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
+                         "frac": achieved / peak, "traffic": None,
                          "kernel": "k_tr_resident: one CTA per trial runs the whole procedure "
                                    "in shared memory; each trial is bound by its SM's binary64 "
-                                   "rate, the run by the slowest trial",
-                         "note": "the number of objective evaluations differs per trial and is "
-                                 "not returned by the call, so no achieved rate is claimed; the "
-                                 "ALU roofline is reported on objective_d32_n1024 and "
-                                 "trust_region_d32_n1024"},
+                                   "rate, the run by the slowest trial (128 trials on 152 SMs: "
+                                   "at most 0.84 of the GPU)",
+                         "flops_per_run": flops,
+                         "flops_note": "algorithmic: 24 d P per objective-and-gradient pass, "
+                                       "8 d P per objective-only pass (P = N(N-1)/2), from each "
+                                       "trial's iteration and Hessian-product counts",
+                         "peak_source": f"fp64 peak derived: 152 SMs x 2 lanes x 2 flops x "
+                                        f"{sm_mhz} MHz"},
             "gpu_launches": 2 * steps,
             "e2e": {"value": t, "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(16 * d * N + 8 * K),

@@ -596,10 +596,15 @@ int trstmi_tr_solve(int N, int d, double *phi, const trstmi_tr_options *o,
  * selects 2 d^2 trials.  out: the minimum of mu over the trials (binary64),
  * its trial (lowest index on ties) and seed.  mu_all (nullable): L doubles.
  * best_phi (nullable): 2*d*N doubles, the winning frame.  trace (nullable):
- * up to cap rows of the winning trial; *n_rows (nullable) its row count. */
+ * up to cap rows of the winning trial; *n_rows (nullable) its row count.
+ * work (nullable, host): 2*L ints, for trial i its trust-region iterations
+ * (work[2i], the rows it would trace) and Hessian-vector products
+ * (work[2i+1]); each iteration evaluates F and its gradient once and F once
+ * more at the trial point, each product two gradients. */
 int trstmi_tr_multistart(int N, int d, uint64_t seed0, int L, const trstmi_tr_options *o,
                          int batch_cap, trstmi_multistart_result *out, double *mu_all,
-                         double *best_phi, trstmi_tr_row *trace, int cap, int *n_rows);
+                         double *best_phi, trstmi_tr_row *trace, int cap, int *n_rows,
+                         int *work);
 
 /* The procedure applied to an instance's current frame (polishing a
  * search's result), on the instance's device: the frame is replaced by the

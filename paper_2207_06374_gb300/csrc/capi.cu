@@ -1118,7 +1118,8 @@ int trstmi_tr_solve(int N, int d, double* phi, const trstmi_tr_options* o, trstm
 
 int trstmi_tr_multistart(int N, int d, uint64_t seed0, int L, const trstmi_tr_options* o,
                          int batch_cap, trstmi_multistart_result* out, double* mu_all,
-                         double* best_phi, trstmi_tr_row* trace, int cap, int* n_rows) {
+                         double* best_phi, trstmi_tr_row* trace, int cap, int* n_rows,
+                         int* work) {
   trstmi::TraceRange trace_range("trstmi_tr_multistart");
   int rc = tr_check(N, d, o);
   if (rc) return rc;
@@ -1151,6 +1152,10 @@ int trstmi_tr_multistart(int N, int d, uint64_t seed0, int L, const trstmi_tr_op
                          logs.data());
     if (rc) break;
     for (int i = 0; i < n; ++i) {
+      if (work) {
+        work[2 * (size_t)(b0 + i)] = logs[i].n;
+        work[2 * (size_t)(b0 + i) + 1] = logs[i].hv_products;
+      }
       mu[b0 + i] = std::sqrt(logs[i].mu2);
       if (b0 + i == 0 || mu[b0 + i] < mu[best]) {
         best = b0 + i;

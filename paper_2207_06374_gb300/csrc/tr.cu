@@ -580,7 +580,9 @@ __device__ void res_axpby(double a, const double* x, double b, const double* y, 
 // reciprocal per column and one of delta and of the sum (no division per
 // entry or pair), one exponential per pair (kept in W), and the weighted
 // Gram M = w (.) G formed once per pair, so that the gradient's inner loop is
-// four fused multiply-adds per (k, i, j).
+// four fused multiply-adds per (k, i, j).  The complex products are written
+// as explicit fma chains: "acc += a*b + c*d" would compile to a multiply, a
+// fused multiply-add and an add, three binary64 instructions for two.
 __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double delta,
                          double* gout, double* F, double* smax) {
   const int N = a.N, d = a.d, P = a.P;
@@ -590,7 +592,8 @@ __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double d
     double q = 0.0;
     for (int i = 0; i < d; ++i) {
       const double re = v[2 * (k * d + i)], im = v[2 * (k * d + i) + 1];
-      q += re * re + im * im;
+      q = fma(re, re, q);
+      q = fma(im, im, q);
     }
     if (!(q > 0.0)) zero = 1.0;
     const double r = sqrt(q), inv = 1.0 / r;
@@ -609,8 +612,10 @@ __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double d
     for (int i = 0; i < d; ++i) {
       const double ar = S.phi[2 * (j * d + i)], ai = S.phi[2 * (j * d + i) + 1];
       const double br = S.phi[2 * (k * d + i)], bi = S.phi[2 * (k * d + i) + 1];
-      gr += ar * br + ai * bi;
-      gi += ar * bi - ai * br;
+      gr = fma(ar, br, gr);
+      gr = fma(ai, bi, gr);
+      gi = fma(ar, bi, gi);
+      gi = fma(-ai, br, gi);
     }
     S.Gre[q] = gr;
     S.Gim[q] = gi;
@@ -648,16 +653,20 @@ __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double d
       const int q = j * N - j * (j + 1) / 2 + (k - j - 1);
       const double mr = S.Gre[q], mi = S.Gim[q];
       const double pr = S.phi[2 * (j * d + i)], pi = S.phi[2 * (j * d + i) + 1];
-      gr += mr * pr - mi * pi;
-      gi += mr * pi + mi * pr;
+      gr = fma(mr, pr, gr);
+      gr = fma(-mi, pi, gr);
+      gi = fma(mr, pi, gi);
+      gi = fma(mi, pr, gi);
     }
     const int base = k * N - k * (k + 1) / 2 - k - 1;
     for (int j = k + 1; j < N; ++j) {
       const int q = base + j;
       const double mr = S.Gre[q], mi = S.Gim[q];
       const double pr = S.phi[2 * (j * d + i)], pi = S.phi[2 * (j * d + i) + 1];
-      gr += mr * pr + mi * pi;
-      gi += mr * pi - mi * pr;
+      gr = fma(mr, pr, gr);
+      gr = fma(mi, pi, gr);
+      gi = fma(mr, pi, gi);
+      gi = fma(-mi, pr, gi);
     }
     gout[2 * (k * d + i)] = 2.0 * gr;
     gout[2 * (k * d + i) + 1] = 2.0 * gi;
@@ -665,9 +674,10 @@ __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double d
   __syncthreads();
   for (int k = threadIdx.x; k < N; k += kResThreads) {
     double rad = 0.0;
-    for (int i = 0; i < d; ++i)
-      rad += S.phi[2 * (k * d + i)] * gout[2 * (k * d + i)] +
-             S.phi[2 * (k * d + i) + 1] * gout[2 * (k * d + i) + 1];
+    for (int i = 0; i < d; ++i) {
+      rad = fma(S.phi[2 * (k * d + i)], gout[2 * (k * d + i)], rad);
+      rad = fma(S.phi[2 * (k * d + i) + 1], gout[2 * (k * d + i) + 1], rad);
+    }
     const double inv = S.rn[k];
     for (int i = 0; i < d; ++i) {
       gout[2 * (k * d + i)] = (gout[2 * (k * d + i)] - S.phi[2 * (k * d + i)] * rad) * inv;

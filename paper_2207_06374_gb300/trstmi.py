@@ -189,7 +189,7 @@ SIGNATURES = {
                                             ctypes.c_int, ctypes.POINTER(TrOptions),
                                             ctypes.c_int, ctypes.POINTER(MultistartResult), _dp,
                                             _dp, ctypes.c_void_p, ctypes.c_int,
-                                            ctypes.POINTER(ctypes.c_int)]),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "trstmi_instance_tr_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TrOptions),
                                                 ctypes.c_void_p, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_int)]),
@@ -433,14 +433,19 @@ def tr_solve(phi: np.ndarray, cap: int = 1 << 16, **options):
 
 
 def tr_multistart(N: int, d: int, seed0: int, L: int = 0, batch_cap: int = 0,
-                  want_phi: bool = True, trace_cap: int = 0, **options):
+                  want_phi: bool = True, trace_cap: int = 0, work=None, **options):
     """The paper's whole algorithm: L random initialisations (seeds seed0 ..,
     the frames trstmi_create draws; L <= 0: 2 d^2), each through the
     trust-region procedure, advanced together on the GPU; the minimum over
     the trials.  Returns (result, mu of every trial, the winning frame or
-    None, the winning trial's trace)."""
+    None, the winning trial's trace).  `work`, an int32 array of shape
+    (trials, 2), receives each trial's trust-region iterations and
+    Hessian-vector products."""
     o = tr_options(**options)
     trials = L if L > 0 else 2 * d * d
+    if work is not None and (work.dtype != np.int32 or work.shape != (trials, 2)
+                             or not work.flags.c_contiguous):
+        raise ValueError(f"work must be a C-contiguous int32 array of shape ({trials}, 2)")
     res = MultistartResult()
     mus = np.zeros(trials)
     phi = np.zeros(2 * d * N) if want_phi else None
@@ -450,7 +455,9 @@ def tr_multistart(N: int, d: int, seed0: int, L: int = 0, batch_cap: int = 0,
                                       ctypes.byref(res), mus.ctypes.data_as(_dp),
                                       phi.ctypes.data_as(_dp) if want_phi else None,
                                       tr.ctypes.data if trace_cap > 0 else None, trace_cap,
-                                      ctypes.byref(n)), "trstmi_tr_multistart")
+                                      ctypes.byref(n),
+                                      work.ctypes.data if work is not None else None),
+           "trstmi_tr_multistart")
     return (res, mus, (_unflat(phi, d, N) if want_phi else None),
             tr[: min(n.value, trace_cap)] if trace_cap > 0 else None)
 

@@ -116,11 +116,15 @@ def _init(N, d, seed):
 def test_trials_advance_together_exactly_as_alone(path):
     N, d, seed0, L = 9, 3, 20, 5
     kw = dict(deltas=(0.1, 0.01, 0.001), max_outer=40, max_cg=50, path=path)
-    res, mus, phi, tr = T.tr_multistart(N, d, seed0, L, trace_cap=4096, **kw)
+    work = np.zeros((L, 2), dtype=np.int32)
+    res, mus, phi, tr = T.tr_multistart(N, d, seed0, L, trace_cap=4096, work=work, **kw)
     assert res.trials == L
+    # every CG iteration takes one Hessian product; the winner's rows are its iterations
+    assert tuple(work[res.best]) == (len(tr), int(tr["cg_iters"].sum()))
     for i in range(L):
         solo_phi, solo_tr = T.tr_solve(_init(N, d, seed0 + i), **kw)
         assert np.sqrt(O.mu2(solo_phi)) == pytest.approx(mus[i], rel=1e-13)
+        assert work[i, 0] == len(solo_tr) and work[i, 1] == solo_tr["cg_iters"].sum()
         if i == res.best:
             assert np.array_equal(solo_phi, phi)
             assert np.array_equal(solo_tr, tr)
