@@ -41,12 +41,15 @@ WORKLOADS = {
     "precision_tf32_d32_n768": (32, 768, 1024, "tf32",
                                 "complex d=32 N=768, 1024 candidates/iteration, tf32 screen + "
                                 "fp32 top-8 re-score + fp64 certify"),
+    "precision_d64_n768": (64, 768, 1024, "bf16",
+                           "complex d=64 N=768, 1024 candidates/iteration, wide bf16 screen "
+                           "(two operand atoms per column) + fp32 top-8 re-score + fp64 certify"),
     "plain_d32_n1024_fp32": (32, 1024, 1024, "fp32",
                              "complex d=32 N=1024, 1024 candidates/iteration, plain fp32"),
     "plain_d8_n64": (8, 64, 4096, "fp32",
                      "complex d=8 N=64, 4096 candidates/iteration, plain fp32"),
     "batched_512": (None, None, 512, "fp32", "512 uneven instances in shared launches"),
-    "serving": (None, None, 8, "bf16", "Poisson request stream through the serving loop"),
+    "serving": (None, None, 64, "bf16", "Poisson request stream through the serving loop"),
     "plain_d2_n4_fp64": (2, 4, 256, "fp64",
                          "complex d=2 N=4, 256 candidates/iteration, fp64"),
     # K = frames per call of the smooth-maximum objective
@@ -184,9 +187,11 @@ KERNEL_SOURCES = {
 KERNEL_SOURCES["lse"] = ["paper_2207_06374_gb300/csrc/lse.cu", "paper_2207_06374_gb300/csrc/tile.cuh",
                          "paper_2207_06374_gb300/csrc/common.cuh"]
 KERNEL_SOURCES["tf32"] = KERNEL_SOURCES["bf16"]
+KERNEL_SOURCES["bf16w"] = KERNEL_SOURCES["bf16"]
 KERNEL_SOURCES["tr"] = ["paper_2207_06374_gb300/csrc/tr.cu"]
 KERNEL_SOURCES["batched"] = KERNEL_SOURCES["fp32"]
 KERNEL_PROFILE = {"bf16": "k_screen_bf16_d32_n1024.txt", "tf32": "k_screen_tf32_d32_n768.txt",
+                  "bf16w": "k_screen_bf16w_d64_n768.txt",
                   "fp32": "k_gram_planes_f32_d32_n1024.txt",
                   "batched": "k_batch_resident_f32_batched_512.txt",
                   "lse": "k_lse_tile_f32_d32_n1024.txt"}
@@ -391,7 +396,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-side", action="store_true", help="skip the fp32 side-by-side run")
     ap.add_argument("--requests", type=int, default=100, help="serving: requests in the stream")
-    ap.add_argument("--budget", type=int, default=200, help="serving: iterations per request")
+    ap.add_argument("--budget", type=int, default=50, help="serving: iterations per request")
+    ap.add_argument("--serve-k", type=int, default=64,
+                    help="serving: candidates per iteration of every request")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--shard", action="store_true",
                     help="N>1: one search with its candidates split over the ranks (strong "
@@ -566,8 +573,9 @@ def main():
                      f"{'128' if prec == 'fp32' else '2'} lanes x 2 flops x {sm_mhz} MHz")
     achieved = flops_launch / (kernel_ms * 1e-3) / 1e12
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
-                 "traffic": profiled_traffic(prec),
-                 "kernel": (f"k_screen ({prec})" if prec in ("bf16", "tf32") else
+                 "traffic": profiled_traffic("bf16w" if prec == "bf16" and d > 32 else prec),
+                 "kernel": (f"k_screen ({prec}{', wide' if d > 32 else ''})"
+                            if prec in ("bf16", "tf32") else
                             "k_gen_planes_f32 + k_gram_planes (one fp32 scoring pass)" if prec == "fp32"
                             else "k_gram_tile"),
                  "kernel_ms": kernel_ms, "flops_per_launch": flops_launch, "peak_source": peak_note})
@@ -1050,7 +1058,7 @@ def run_table2(args, ws, rank, local, dist, torch, T):
 
 def run_serving(args, ws, rank, local, dist, torch, T):
     """Seeded Poisson stream of search requests (d ~ U{4..64}, N log-uniform on
-    [d+1, 4096], target 1.05 x Welch, K = 8) replayed into the serving loop in
+    [d+1, 4096], target 1.05 x Welch, K = 64) replayed into the serving loop in
     the precision form (bf16 screen, fp32 re-score of the top 2, fp64
     certification; shapes outside the screen's range rank in fp32); every
     request runs to its target or its iteration budget.  Reported: p50 / p99
@@ -1060,7 +1068,7 @@ def run_serving(args, ws, rank, local, dist, torch, T):
     arrival times)."""
     import threading
     from paper_2207_06374_gb300 import workloads as W
-    K, prec, topk = 8, WORKLOADS["serving"][3], 2
+    K, prec, topk = args.serve_k, WORKLOADS["serving"][3], 2
     reqs = W.serving_requests(args.requests, seed=11 + rank, rate_hz=args.rate)
     budget = args.budget
 
@@ -1096,7 +1104,8 @@ def run_serving(args, ws, rank, local, dist, torch, T):
     lat = np.array([(res.t_done_ns - res.t_submit_ns) * 1e-9 for _, res, _ in results])
     ok = sum(1 for st, _, _ in results if st == T.TRSTMI_OK)
     pairs = sum(res.pairs_scored for _, res, _ in results)
-    n_screened = sum(1 for r in reqs if r["d"] <= 32 and r["N"] <= 1536)
+    n_screened = sum(1 for r in reqs
+                     if (r["d"] <= 32 and r["N"] <= 1536) or (r["d"] <= 64 and r["N"] <= 768))
     reached = sum(res.reached_target for _, res, _ in results)
     # plain fp32 single-instance path, one request at a time (same requests)
     run_s = []

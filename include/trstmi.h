@@ -83,9 +83,10 @@ typedef struct trstmi_options {
      screen while its radius is >= screen_min_delta, and with the binary32
      Gram of every candidate below it, where candidate coherences differ by
      less than the screen's resolution (default 0.01; 0 = always screen).
-     Shapes the screen kernel does not take (d > 32, or N > 1536; N > 768
-     with tf32 operands) always rank with the binary32 Gram; the re-score and
-     certification are unchanged. */
+     The screen takes d <= 32 with N <= 1536 (bf16, fp16) or N <= 768
+     (tf32), and 32 < d <= 64 with N <= 768 (bf16, fp16: two 128-byte
+     operand atoms per column).  Other shapes always rank with the binary32
+     Gram; the re-score and certification are unchanged. */
   double screen_min_delta;
   void *stream;         /* cudaStream_t to issue on, or NULL */
   int32_t device;       /* CUDA device ordinal (default 0) */

@@ -386,7 +386,7 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
     sd.N = N[i]; sd.d = d[i]; sd.K = o.K; sd.R = 1; sd.ntiles = ntiles_for(N[i], 1);
     if (screen) {
       char* q = base + o_scr[i];
-      sd.screen = screen_supported(N[i], d[i], screen_fmt_of(o.precision)) ? 1 : 0;
+      sd.screen = screen_supported(N[i], d[i], screen_fmt_of(o.precision, d[i])) ? 1 : 0;
       sd.topk = (uint32_t*)q; q += up(tk * sizeof(uint32_t));
       sd.mu2_top = (unsigned int*)q; q += up(tk * sizeof(uint32_t));
       sd.cand64 = (double2*)q; q += up(nd * sizeof(double2));
@@ -562,8 +562,7 @@ int trstmi_batch_profile_score(trstmi_batch_handle b, int launches, size_t flush
         (flush && cudaMemsetAsync(flush, l & 0xff, flush_bytes, s)) ||
         cudaEventRecord(b->ev0, s) != cudaSuccess) { rc = TRSTMI_ECUDA; break; }
     cudaError_t e = b->screen
-        ? launch_screen_batched(screen_fmt_of(b->opt.precision), b->plan.d_screen_slots,
-                                b->plan.d_items, b->plan.n_items, b->d_err, b->num_sms, s)
+        ? b->plan.launch_screen(b->d_err, s)
         : b->plan.launch_pass(kPassFull, b->d_slots, s);
     float ms = 0.f;
     if (e != cudaSuccess || cudaEventRecord(b->ev1, s) != cudaSuccess ||

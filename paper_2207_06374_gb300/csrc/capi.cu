@@ -235,8 +235,8 @@ int enqueue_iteration_score(trstmi_instance* h, cudaStream_t s, int c_lo, int c_
       // rank the candidates: tensor-core screen while delta >= screen_min_delta,
       // else the fp32 Gram of every candidate (each kernel returns at once when
       // the other one is selected for this iteration)
-      if (screen_supported(N, d, screen_fmt_of(prec)))
-        TRY_CUDA(launch_screen(screen_fmt_of(prec), N, d, h->seed, h->phi32, count,
+      if (screen_supported(N, d, screen_fmt_of(prec, d)))
+        TRY_CUDA(launch_screen(screen_fmt_of(prec, d), N, d, h->seed, h->phi32, count,
                                (uint32_t)c_lo, 0u, 0.0, st, h->mu2_k32 + c_lo, &st->error,
                                h->num_sms, s));
       GramSource full{};
@@ -494,7 +494,7 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   s0.delta_min = o.delta_min;
   s0.delta_max = o.delta_max;
   // a shape outside the screen kernel's range ranks with the binary32 Gram
-  s0.screen_min_delta = (is_screen(o.precision) && !screen_supported(N, d, screen_fmt_of(o.precision)))
+  s0.screen_min_delta = (is_screen(o.precision) && !screen_supported(N, d, screen_fmt_of(o.precision, d)))
                             ? std::numeric_limits<double>::infinity()
                             : o.screen_min_delta;
   s0.trace_cap = (uint32_t)o.trace_cap;
@@ -771,10 +771,10 @@ int trstmi_score(trstmi_handle h, uint32_t t, uint32_t c0, int count, double del
         src.phi = h->phi32;
         e = launch_gram_f32(h->N, h->d, count, src, (unsigned int*)tmp, nullptr, h->num_sms, s);
       } else {
-        if (!screen_supported(h->N, h->d, screen_fmt_of(precision))) { rc = TRSTMI_EUNSUPPORTED; break; }
+        if (!screen_supported(h->N, h->d, screen_fmt_of(precision, h->d))) { rc = TRSTMI_EUNSUPPORTED; break; }
         e = cudaMemsetAsync(&h->misc[1], 0, sizeof(uint32_t), s);
         if (e == cudaSuccess)
-          e = launch_screen(screen_fmt_of(precision), h->N, h->d, h->seed, h->phi32, count,
+          e = launch_screen(screen_fmt_of(precision, h->d), h->N, h->d, h->seed, h->phi32, count,
                             c0, t, delta, nullptr, (unsigned int*)tmp, &h->misc[1], h->num_sms, s);
       }
       if (e != cudaSuccess) { rc = record_cuda_error(e, "score kernel launch", __LINE__); break; }
@@ -860,7 +860,7 @@ int trstmi_profile_score(trstmi_handle h, int precision, int launches, double de
                          size_t flush_bytes, double* avg_ms) {
   if (!h || launches < 1 || !avg_ms || !(delta >= 0)) return TRSTMI_EINVAL;
   if (precision < TRSTMI_FP64 || precision > TRSTMI_TF32_SCREEN) return TRSTMI_EINVAL;
-  if (is_screen(precision) && !screen_supported(h->N, h->d, screen_fmt_of(precision)))
+  if (is_screen(precision) && !screen_supported(h->N, h->d, screen_fmt_of(precision, h->d)))
     return TRSTMI_EUNSUPPORTED;
   TRY_CUDA(cudaSetDevice(h->opt.device));
   cudaStream_t s = h->stream;
@@ -898,7 +898,7 @@ int trstmi_profile_score(trstmi_handle h, int precision, int launches, double de
       if (e == cudaSuccess)
         e = launch_gram_f32(h->N, h->d, K, src, h->mu2_k32, nullptr, h->num_sms, s);
     } else {
-      e = launch_screen(screen_fmt_of(precision), h->N, h->d, h->seed, h->phi32, K, 0u,
+      e = launch_screen(screen_fmt_of(precision, h->d), h->N, h->d, h->seed, h->phi32, K, 0u,
                         (uint32_t)(l + 1), delta, nullptr, h->mu2_k32, &h->misc[1], h->num_sms, s);
     }
     cudaEventRecord(ev[2 * l + 1], s);
@@ -1206,12 +1206,12 @@ int trstmi_instance_tr_solve(trstmi_handle h, const trstmi_tr_options* o, trstmi
 int trstmi_screen_wait_test(trstmi_handle h, int precision, double wait_limit_ms) {
   if (!h || !is_screen_precision(precision)) return TRSTMI_EINVAL;
   if (!(wait_limit_ms > 0.0 && wait_limit_ms <= 2000.0)) return TRSTMI_EINVAL;
-  if (!screen_supported(h->N, h->d, screen_fmt_of(precision))) return TRSTMI_EUNSUPPORTED;
+  if (!screen_supported(h->N, h->d, screen_fmt_of(precision, h->d))) return TRSTMI_EUNSUPPORTED;
   TRY_CUDA(cudaSetDevice(h->opt.device));
   cudaStream_t s = h->stream;
   const int count = std::min(h->opt.K, 8);
   TRY_CUDA(cudaMemsetAsync(&h->misc[1], 0, sizeof(uint32_t), s));
-  TRY_CUDA(launch_screen_wait_test(screen_fmt_of(precision), h->N, h->d, h->phi32, count,
+  TRY_CUDA(launch_screen_wait_test(screen_fmt_of(precision, h->d), h->N, h->d, h->phi32, count,
                                    h->mu2_k32, &h->misc[1],
                                    (unsigned long long)(wait_limit_ms * 1e6), h->num_sms, s));
   uint32_t err = 0;

@@ -8,14 +8,20 @@
 
 namespace trstmi {
 
-// Operand format of the tensor-core screen.
-enum ScreenFmt : int { kScreenBF16 = 0, kScreenFP16 = 1, kScreenTF32 = 2 };
+// Operand format of the tensor-core screen: bf16 / fp16 / tf32 for d <= 32,
+// and the wide bf16 / fp16 layouts (two 128-byte atoms per column) for
+// 32 < d <= 64.
+enum ScreenFmt : int {
+  kScreenBF16 = 0, kScreenFP16 = 1, kScreenTF32 = 2, kScreenBF16W = 3, kScreenFP16W = 4
+};
 inline bool is_screen_precision(int p) {
   return p == TRSTMI_BF16_SCREEN || p == TRSTMI_FP16_SCREEN || p == TRSTMI_TF32_SCREEN;
 }
-inline int screen_fmt_of(int precision) {
-  return precision == TRSTMI_FP16_SCREEN ? kScreenFP16
-         : precision == TRSTMI_TF32_SCREEN ? kScreenTF32 : kScreenBF16;
+inline int screen_fmt_of(int precision, int d) {
+  if (precision == TRSTMI_TF32_SCREEN) return kScreenTF32;
+  const bool wide = d > 32;
+  return precision == TRSTMI_FP16_SCREEN ? (wide ? kScreenFP16W : kScreenFP16)
+                                         : (wide ? kScreenBF16W : kScreenBF16);
 }
 
 // Which frame a Gram pass reads.
@@ -284,7 +290,8 @@ struct BatchPlan {
   std::vector<Group> groups[kPasses];
   ScreenSlot* d_screen_slots = nullptr;
   uint2* d_items = nullptr;
-  int n_items = 0;
+  int n_items = 0;        // screen items; the last n_wide of them take the wide format
+  int n_wide = 0;
   unsigned long long* d_counters = nullptr;
 
   int init(int capacity_slots, long long capacity_items, int num_sms);
@@ -292,6 +299,8 @@ struct BatchPlan {
   // h: host copy of the device slot table (R of every slot chosen)
   int rebuild(const std::vector<SlotDesc>& h, int precision, cudaStream_t s);
   int enqueue_iteration(SlotDesc* d_slots, int n, uint32_t* err, cudaStream_t s) const;
+  // the screen of every item: one launch per operand format present
+  cudaError_t launch_screen(uint32_t* err, cudaStream_t s) const;
   cudaError_t launch_pass(int pass, SlotDesc* d_slots, cudaStream_t s) const;
   int kernels_per_iteration() const;
 };

@@ -122,6 +122,7 @@ int BatchPlan::rebuild(const std::vector<SlotDesc>& h, int precision_, cudaStrea
   }
   // screen work items (instance, candidate), heaviest instances first
   n_items = 0;
+  n_wide = 0;
   if (screen) {
     std::vector<ScreenSlot> ss(n);
     std::vector<int> order;
@@ -134,13 +135,21 @@ int BatchPlan::rebuild(const std::vector<SlotDesc>& h, int precision_, cudaStrea
       ss[i].d = h[i].d;
       if (h[i].screen) order.push_back(i);
     }
+    // the instances of the d <= 32 format first, then those of the wide
+    // format (32 < d <= 64), each part heaviest first
+    const auto wide = [&](int i) { return screen_fmt_of(precision, h[i].d) != screen_fmt_of(precision, 1); };
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      if (wide(x) != wide(y)) return wide(y);
       const long long nx = (h[x].N + 127) / 128, ny = (h[y].N + 127) / 128;
       return nx * (nx + 1) > ny * (ny + 1);
     });
     std::vector<uint2> items;
+    n_wide = 0;
     for (int i : order)
-      for (int c = 0; c < h[i].K; ++c) items.push_back(make_uint2((unsigned)i, (unsigned)c));
+      for (int c = 0; c < h[i].K; ++c) {
+        items.push_back(make_uint2((unsigned)i, (unsigned)c));
+        if (wide(i)) ++n_wide;
+      }
     if ((long long)items.size() > cap_items) return TRSTMI_EINVAL;
     n_items = (int)items.size();
     if (cudaMemcpyAsync(d_screen_slots, ss.data(), sizeof(ScreenSlot) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -178,8 +187,7 @@ int BatchPlan::enqueue_iteration(SlotDesc* d_slots, int n, uint32_t* err, cudaSt
   }
   // rank (screen, or fp32 below the screen radius), keep the top-k, re-score
   // them in fp32, regenerate the winner in fp64 and certify it, decide, commit
-  if (launch_screen_batched(screen_fmt_of(precision), d_screen_slots, d_items, n_items, err,
-                            num_sms, s) != cudaSuccess ||
+  if (launch_screen(err, s) != cudaSuccess ||
       launch_pass(kPassFull, d_slots, s) != cudaSuccess ||
       launch_batch_topk(d_slots, n, s) != cudaSuccess ||
       launch_pass(kPassRescore, d_slots, s) != cudaSuccess ||
@@ -194,10 +202,22 @@ int BatchPlan::enqueue_iteration(SlotDesc* d_slots, int n, uint32_t* err, cudaSt
   return TRSTMI_OK;
 }
 
+cudaError_t BatchPlan::launch_screen(uint32_t* err, cudaStream_t s) const {
+  const int n_narrow = n_items - n_wide;
+  cudaError_t e = cudaSuccess;
+  if (n_narrow > 0)
+    e = launch_screen_batched(screen_fmt_of(precision, 1), d_screen_slots, d_items, n_narrow,
+                              err, num_sms, s);
+  if (e == cudaSuccess && n_wide > 0)
+    e = launch_screen_batched(screen_fmt_of(precision, 64), d_screen_slots, d_items + n_narrow,
+                              n_wide, err, num_sms, s);
+  return e;
+}
+
 int BatchPlan::kernels_per_iteration() const {
   int k = 1;   // begin
   for (int p = 0; p < kPasses; ++p) k += (int)groups[p].size();
-  if (is_screen_prec(precision)) k += (n_items ? 1 : 0) + 6;
+  if (is_screen_prec(precision)) k += (n_items > n_wide ? 1 : 0) + (n_wide ? 1 : 0) + 6;
   else k += 2;
   return k;
 }

@@ -309,7 +309,7 @@ int admit(trstmi_server* sv, uint64_t ticket, Req& r, Slot* out) {
   std::memset(&sd, 0, sizeof(sd));
   if (sv->screen) {
     char* q = (char*)tr + up256((size_t)std::max(o.trace_cap, 1) * sizeof(TraceRowDev));
-    sd.screen = screen_supported(N, d, screen_fmt_of(o.precision)) ? 1 : 0;
+    sd.screen = screen_supported(N, d, screen_fmt_of(o.precision, d)) ? 1 : 0;
     sd.topk = (uint32_t*)q; q += up256((size_t)o.topk * sizeof(uint32_t));
     sd.mu2_top = (unsigned int*)q; q += up256((size_t)o.topk * sizeof(uint32_t));
     sd.cand64 = (double2*)q; q += up256(nd * sizeof(double2));

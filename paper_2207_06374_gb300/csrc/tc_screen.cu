@@ -28,18 +28,25 @@
 namespace trstmi {
 namespace {
 
-constexpr int kDP = 32;                 // padded d: K = 2*kDP = 64 bf16 = 128 bytes / column
 constexpr int kBlockCols = 128;         // columns per block = MMA M = N
-// Operand formats (ScreenFmt): a column block is 128 columns x 2 DP values.
-// bf16 / fp16: one 128-byte swizzle atom per column (Re 0..31 then Im 0..31),
-// 16 KiB per block, twelve slots (N <= 1536).  tf32: two atoms per column,
-// Re in the first 16 KiB of the block and Im in the second, 32 KiB per block,
-// six slots (N <= 768).  Either way the slots fill the same 192 KiB.
+// Operand formats (ScreenFmt): a column block is 128 columns x 2 DP values,
+// DP the padded d.
+// bf16 / fp16 (d <= 32, DP = 32): one 128-byte swizzle atom per column (Re
+// 0..31 then Im 0..31), 16 KiB per block, twelve slots (N <= 1536).
+// tf32 (d <= 32, DP = 32) and wide bf16 / fp16 (d <= 64, DP = 64): two atoms
+// per column, Re in the first 16 KiB of the block and Im in the second (32
+// tf32 or 64 bf16 values = 128 bytes each), 32 KiB per block, six slots
+// (N <= 768).  Either way the slots fill the same 192 KiB.
 template <int F> struct FmtTraits {
-  static constexpr int kBlockBytes = F == kScreenTF32 ? 32768 : 16384;
-  static constexpr int kSlots = F == kScreenTF32 ? 6 : 12;
+  static constexpr bool kWide16 = F == kScreenBF16W || F == kScreenFP16W;
+  static constexpr bool kTwoAtoms = F == kScreenTF32 || kWide16;
+  static constexpr int kDP = kWide16 ? 64 : 32;
+  static constexpr int kEntries = kDP / 4;        // entries of a column per generator lane
+  static constexpr int kBlockBytes = kTwoAtoms ? 32768 : 16384;
+  static constexpr int kSlots = kTwoAtoms ? 6 : 12;
   // instruction-descriptor operand format: fp16 0, bf16 1 (kind::f16), tf32 2 (kind::tf32)
-  static constexpr uint32_t kAB = F == kScreenFP16 ? 0u : F == kScreenBF16 ? 1u : 2u;
+  static constexpr uint32_t kAB = (F == kScreenFP16 || F == kScreenFP16W) ? 0u
+                                  : (F == kScreenBF16 || F == kScreenBF16W) ? 1u : 2u;
 };
 constexpr int kOperandBytes = 12 * 16384;
 constexpr int kRing = 12;               // barrier slots: the largest ring
@@ -210,7 +217,7 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
 }
 
 template <int F> __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-  if constexpr (F == kScreenFP16) {
+  if constexpr (FmtTraits<F>::kAB == 0u) {
     __half2 v = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
   } else {
@@ -456,11 +463,13 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
     // the current one is still being swept.  The work is cut into 8-column
     // units (octets), numbered consecutively over all blocks of this CTA;
     // generator gi takes the units u = gi (mod kGenWarps).  In a unit, lane l
-    // takes column 8o + (l & 7) and the quarter q = l >> 3 of its entries
-    // (8q .. 8q+7, four draws); the eight lanes of one quarter write eight
-    // different 16-byte chunks of a swizzled row group, so the stores are
-    // free of bank conflicts.  Each unit's warp arrives once on the slot's
-    // fill barrier (kOctets arrivals complete a fill).
+    // takes column 8o + (l & 7) and the quarter q = l >> 3 of its DP padded
+    // entries: E = DP/4 of them (Eq .. Eq+E-1, E/2 draws); the eight lanes of
+    // one quarter write eight different 16-byte chunks of a swizzled row
+    // group, so the stores are free of bank conflicts.  Each unit's warp
+    // arrives once on the slot's fill barrier (kOctets arrivals complete a
+    // fill).
+    constexpr int kDP = FmtTraits<F>::kDP, kE = FmtTraits<F>::kEntries;
     const int q = lane >> 3;
     uint32_t gb0 = 0;
     const int gen_items = src.withhold() ? 0 : nitems;
@@ -482,26 +491,32 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
         unsigned char* blk = xs + slot * (uint32_t)kBlockBytes;
         const int r = 8 * o + (lane & 7);        // row of the block (column of Phi)
         const int j = b * kBlockCols + r;
-        float2 x[8];
+        float2 x[kE];
         float2 ss = make_float2(0.f, 0.f);
         if (j < it.N && d == kDP) {
-          // full width: entries 8q .. 8q+7 are 64 contiguous bytes of phi
-          const float4* col4 = reinterpret_cast<const float4*>(it.phi + (size_t)j * kDP + 8 * q);
-          float4 v[4];
+          // full width: entries Eq .. Eq+E-1 are 8E contiguous bytes of phi,
+          // read as float4 (two entries) in groups of eight entries
 #pragma unroll
-          for (int pp = 0; pp < 4; ++pp) v[pp] = __ldg(col4 + pp);
+          for (int h = 0; h < kE / 8; ++h) {
+            const float4* col4 =
+                reinterpret_cast<const float4*>(it.phi + (size_t)j * kDP + kE * q + 8 * h);
+            float4 v[4];
 #pragma unroll
-          for (int pp = 0; pp < 4; ++pp) {
-            const PhiloxOut w =
-                src.philox((uint32_t)j * (uint32_t)(kDP / 2) + (uint32_t)(4 * q + pp), pc, it);
-            perturb2_fast(w.x, it.delta, make_float2(v[pp].x, v[pp].y),
-                          make_float2(v[pp].z, v[pp].w), x[2 * pp], x[2 * pp + 1]);
+            for (int pp = 0; pp < 4; ++pp) v[pp] = __ldg(col4 + pp);
+#pragma unroll
+            for (int pp = 0; pp < 4; ++pp) {
+              const PhiloxOut w = src.philox(
+                  (uint32_t)j * (uint32_t)(kDP / 2) + (uint32_t)(kE / 2 * q + 4 * h + pp), pc, it);
+              perturb2_fast(w.x, it.delta, make_float2(v[pp].x, v[pp].y),
+                            make_float2(v[pp].z, v[pp].w), x[8 * h + 2 * pp],
+                            x[8 * h + 2 * pp + 1]);
+            }
           }
         } else if (j < it.N) {
           const float2* col = it.phi + (size_t)j * d;
 #pragma unroll
-          for (int pp = 0; pp < 4; ++pp) {
-            const int p = 4 * q + pp;
+          for (int pp = 0; pp < kE / 2; ++pp) {
+            const int p = kE / 2 * q + pp;
             x[2 * pp] = x[2 * pp + 1] = make_float2(0.f, 0.f);
             if (p < P) {
               const PhiloxOut w = src.philox((uint32_t)j * (uint32_t)P + (uint32_t)p, pc, it);
@@ -516,18 +531,34 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
           }
         } else {
 #pragma unroll
-          for (int e = 0; e < 8; ++e) x[e] = make_float2(0.f, 0.f);
+          for (int e = 0; e < kE; ++e) x[e] = make_float2(0.f, 0.f);
         }
 #pragma unroll
-        for (int e = 0; e < 8; ++e) ss = __ffma2_rn(x[e], x[e], ss);
+        for (int e = 0; e < kE; ++e) ss = __ffma2_rn(x[e], x[e], ss);
         float sn = ss.x + ss.y;
         sn += __shfl_xor_sync(0xffffffffu, sn, 8);
         sn += __shfl_xor_sync(0xffffffffu, sn, 16);
         const float inv = sn > 0.f ? rsqrtf(sn) : 0.f;
         const float2 inv2 = make_float2(inv, inv);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) x[e] = __fmul2_rn(x[e], inv2);
-        if constexpr (F == kScreenTF32) {
+        for (int e = 0; e < kE; ++e) x[e] = __fmul2_rn(x[e], inv2);
+        if constexpr (FmtTraits<F>::kWide16) {
+          // real parts of entries 16q .. 16q+15 -> chunks 2q, 2q+1 of the
+          // first atom; imaginary parts -> the same chunks of the second
+          uint4 re0, re1, im0, im1;
+          re0.x = pack2<F>(x[0].x, x[1].x);   re1.x = pack2<F>(x[8].x, x[9].x);
+          re0.y = pack2<F>(x[2].x, x[3].x);   re1.y = pack2<F>(x[10].x, x[11].x);
+          re0.z = pack2<F>(x[4].x, x[5].x);   re1.z = pack2<F>(x[12].x, x[13].x);
+          re0.w = pack2<F>(x[6].x, x[7].x);   re1.w = pack2<F>(x[14].x, x[15].x);
+          im0.x = pack2<F>(x[0].y, x[1].y);   im1.x = pack2<F>(x[8].y, x[9].y);
+          im0.y = pack2<F>(x[2].y, x[3].y);   im1.y = pack2<F>(x[10].y, x[11].y);
+          im0.z = pack2<F>(x[4].y, x[5].y);   im1.z = pack2<F>(x[12].y, x[13].y);
+          im0.w = pack2<F>(x[6].y, x[7].y);   im1.w = pack2<F>(x[14].y, x[15].y);
+          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q)) = re0;
+          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q + 1)) = re1;
+          *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q)) = im0;
+          *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q + 1)) = im1;
+        } else if constexpr (F == kScreenTF32) {
           // real parts of entries 8q .. 8q+7 -> chunks 2q, 2q+1 of the first
           // atom; imaginary parts -> the same chunks of the second
           const uint4 r0 = make_uint4(to_tf32(x[0].x), to_tf32(x[1].x), to_tf32(x[2].x), to_tf32(x[3].x));
@@ -666,9 +697,9 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
             tc_fence_after();
             const uint32_t blo = xs_lo + sJ * (uint32_t)(kBlockBytes >> 4);
             const uint32_t dre = tmem + buf * 256u, dim = dre + 128u;
-            if constexpr (F == kScreenTF32) {
-              // K steps of 8 tf32 = 32 bytes = +2 in the low word; the second
-              // atom (Im parts) is 16 KiB = +1024 further
+            if constexpr (FmtTraits<F>::kTwoAtoms) {
+              // K steps of 8 tf32 or 16 bf16 / fp16 = 32 bytes = +2 in the low
+              // word; the second atom (Im parts) is 16 KiB = +1024 further
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk)   // Re: A_I^T A_J ...
                 mma_lo<F>(dre, alo + 2u * kk, blo + 2u * kk, Idesc<F>::pos, kk > 0 ? 1u : 0u, hi);
@@ -753,6 +784,8 @@ cudaError_t launch_any(int fmt, const Src& src, int grid, cudaStream_t s) {
     case kScreenBF16: return launch_fmt<kScreenBF16>(src, grid, s);
     case kScreenFP16: return launch_fmt<kScreenFP16>(src, grid, s);
     case kScreenTF32: return launch_fmt<kScreenTF32>(src, grid, s);
+    case kScreenBF16W: return launch_fmt<kScreenBF16W>(src, grid, s);
+    case kScreenFP16W: return launch_fmt<kScreenFP16W>(src, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -760,10 +793,11 @@ cudaError_t launch_any(int fmt, const Src& src, int grid, cudaStream_t s) {
 }  // namespace
 
 bool screen_supported(int N, int d, int fmt) {
+  if (fmt < kScreenBF16 || fmt > kScreenFP16W) return false;
   const int nb = (N + kBlockCols - 1) / kBlockCols;
-  const int slots = fmt == kScreenTF32 ? FmtTraits<kScreenTF32>::kSlots
-                                       : FmtTraits<kScreenBF16>::kSlots;
-  return N >= 2 && d >= 1 && d <= kDP && nb <= slots;
+  const bool wide16 = fmt == kScreenBF16W || fmt == kScreenFP16W;
+  const int slots = (fmt == kScreenTF32 || wide16) ? 6 : 12;
+  return N >= 2 && d >= 1 && d <= (wide16 ? 64 : 32) && nb <= slots;
 }
 
 cudaError_t init_screen_attributes(int optin) {
@@ -771,6 +805,10 @@ cudaError_t init_screen_attributes(int optin) {
   if ((e = allow_screen_smem(k_screen<kScreenBF16, OneInstance>, optin)) != cudaSuccess) return e;
   if ((e = allow_screen_smem(k_screen<kScreenFP16, OneInstance>, optin)) != cudaSuccess) return e;
   if ((e = allow_screen_smem(k_screen<kScreenTF32, OneInstance>, optin)) != cudaSuccess) return e;
+  if ((e = allow_screen_smem(k_screen<kScreenBF16W, OneInstance>, optin)) != cudaSuccess) return e;
+  if ((e = allow_screen_smem(k_screen<kScreenFP16W, OneInstance>, optin)) != cudaSuccess) return e;
+  if ((e = allow_screen_smem(k_screen<kScreenBF16W, ManyInstances>, optin)) != cudaSuccess) return e;
+  if ((e = allow_screen_smem(k_screen<kScreenFP16W, ManyInstances>, optin)) != cudaSuccess) return e;
   if ((e = allow_screen_smem(k_screen<kScreenBF16, ManyInstances>, optin)) != cudaSuccess) return e;
   if ((e = allow_screen_smem(k_screen<kScreenFP16, ManyInstances>, optin)) != cudaSuccess) return e;
   return allow_screen_smem(k_screen<kScreenTF32, ManyInstances>, optin);

@@ -93,9 +93,16 @@ def test_batch_rejects_bad_arguments():
 
 
 # shapes of the screen modes: inside the tensor-core screen's range (d <= 32,
-# N <= 1536) and outside it (d = 40; N = 1600), which rank in binary32
+# N <= 1536; 32 < d <= 64, N <= 768 with bf16 / fp16 operands) and outside it
+# (N = 1600; d = 40 at N = 800; d > 32 with tf32), which rank in binary32
 SCREEN_MIX = [(4, 2), (9, 3), (40, 8), (129, 13), (200, 16), (17, 16), (300, 32), (1024, 32),
-              (50, 40), (1600, 4)]
+              (50, 40), (1600, 4), (700, 64), (120, 33), (800, 40)]
+
+
+def screened_shape(precision, N, d):
+    if d <= 32:
+        return N <= (768 if precision == "tf32" else 1536)
+    return precision != "tf32" and d <= 64 and N <= 768
 
 
 @pytest.mark.parametrize("precision", ["bf16", "fp16", "tf32"])
@@ -126,7 +133,7 @@ def test_batch_screen_modes_match_single_runs_bitwise(precision):
                 assert np.array_equal(tr[f], tr_single[f]), (f, i, N, d)
             assert np.array_equal(b.get_phi(i), phi_single), (i, N, d)
             assert mus[i] == mu_single
-            if d > 32 or N > 1536:
+            if not screened_shape(precision, N, d):
                 assert np.all(tr["flags"] & 1 == 0)
             screened += int(np.sum(tr["flags"] & 1))
         assert screened > 0

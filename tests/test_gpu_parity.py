@@ -346,6 +346,50 @@ def test_fp16_screen_scores_match_oracle(d, N, K):
         assert np.max(np.abs(np.sqrt(g16) - np.sqrt(ref))) < 1e-3
 
 
+# ----------------------------- wide bf16 / fp16 screen: 32 < d <= 64, N <= 768
+
+@pytest.mark.parametrize("precision,tol", [("bf16", 4e-3), ("fp16", 1e-3)])
+@pytest.mark.parametrize("d,N,K", [(64, 768, 4), (40, 300, 16), (33, 129, 16), (64, 2, 4),
+                                   (48, 700, 6), (64, 130, 8), (63, 5, 32)])
+def test_wide_screen_scores_match_oracle(d, N, K, precision, tol):
+    """Two 128-byte operand atoms per column (Re 0..63, Im 0..63) and sixteen
+    kind::f16 MMAs per tile: the same input-rounding bound as for d <= 32 (the
+    error of |G_jk| is bounded by the rounding of unit vectors, whatever d)."""
+    seed = 96
+    with T.Search(N, d, seed, K=K, precision="fp32") as s:
+        phi0 = s.get_phi()
+        for (t, c0, delta) in [(1, 0, 0.1), (5, 31, 0.6)]:
+            ref = O.score(phi0, seed, delta, t, c0, K, nthreads=4)
+            g = s.score(t, c0, K, delta, precision)
+            assert np.max(np.abs(np.sqrt(g) - np.sqrt(ref))) < tol
+
+
+@pytest.mark.parametrize("d,N", [(65, 40), (40, 769), (33, 1024)])
+def test_wide_screen_rejects_shapes_beyond_its_range(d, N):
+    with T.Search(N, d, 1, K=4, precision="fp32") as s:
+        for precision in ("bf16", "fp16", "tf32"):
+            with pytest.raises(T.TrstmiError) as e:
+                s.score(1, 0, 4, 0.1, precision)
+            assert e.value.status == T.TRSTMI_EUNSUPPORTED
+
+
+def test_wide_bf16_mode_decisions_replay_exactly():
+    """Precision form at d = 48 (wide screen every iteration, fp32 top-k,
+    fp64 certification): every decision reproduced by the oracle in binary64."""
+    d, N, K, iters, seed = 48, 300, 96, 12, 17
+    with T.Search(N, d, seed, K=K, precision="bf16", topk=6, screen_min_delta=0.0) as s:
+        phi0 = s.get_phi()
+        s.step(iters)
+        tr = s.trace()
+        phi = s.get_phi()
+    assert np.all(tr["flags"] & 1 == 1)
+    rphi, rm2, _, rtr = O.replay(phi0, seed, O.make_opts(K=K, T=iters), 0.1, O.mu2(phi0), 0,
+                                 tr["cstar"])
+    assert np.array_equal(tr["accepted"], rtr["accepted"])
+    check_precision_form_rows(tr, rtr, d, O.mu2(phi0))
+    assert np.abs(phi - rphi).max() < 1e-12
+
+
 def test_screen_gate_by_radius():
     """screen_min_delta = 0: every iteration screened; huge: none screened
     (fp32 Gram of all candidates); decisions replay in binary64 either way."""

@@ -57,7 +57,8 @@ def test_screen_mode_results_equal_standalone_runs(precision):
     result equals the standalone run of the same request bit for bit."""
     K = 32
     reqs = [(4, 2, 21, 120, 0.5775), (40, 6, 22, 30, 0.0), (300, 24, 23, 10, 0.0),
-            (50, 40, 24, 12, 0.0), (1024, 32, 25, 4, 0.0), (12, 4, 26, 40, 0.0)]
+            (50, 40, 24, 12, 0.0), (1024, 32, 25, 4, 0.0), (12, 4, 26, 40, 0.0),
+            (600, 56, 27, 6, 0.0)]
     with T.Server(hbm_budget=256 << 20, max_slots=4, iters_per_round=5, K=K, topk=4,
                   precision=precision) as srv:
         tickets = [srv.submit(N, d, seed, budget, target_mu=target, want_phi=True)

@@ -20,9 +20,9 @@ pytestmark = pytest.mark.gpu
 T = pytest.importorskip("paper_2207_06374_gb300.trstmi")
 
 
-@pytest.mark.parametrize("precision", ["bf16", "tf32"])
-def test_stalled_screen_times_out_and_context_survives(precision):
-    N, d, seed, K = 200, 16, 11, 32
+@pytest.mark.parametrize("precision,d", [("bf16", 16), ("tf32", 16), ("bf16", 48)])
+def test_stalled_screen_times_out_and_context_survives(precision, d):
+    N, seed, K = 200, 11, 32
     with T.Search(N, d, seed, K=K, precision=precision) as s:
         phi0 = s.get_phi()
         t0 = time.perf_counter()
@@ -46,5 +46,5 @@ def test_wait_test_rejects_bad_arguments():
         assert s.screen_wait_test("fp32", 20.0) == T.TRSTMI_EINVAL
         assert s.screen_wait_test("bf16", 0.0) == T.TRSTMI_EINVAL
         assert s.screen_wait_test("bf16", 5000.0) == T.TRSTMI_EINVAL
-    with T.Search(40, 40, 3, K=8) as s:   # d > 32: outside the screen's range
+    with T.Search(40, 65, 3, K=8) as s:   # d > 64: outside the screen's range
         assert s.screen_wait_test("bf16", 20.0) == T.TRSTMI_EUNSUPPORTED
