@@ -319,7 +319,10 @@ typedef struct trstmi_server_opts {
   trstmi_options search;   /* options of every search (K, precision, radius rule,
                               trace_cap, device, stream); target_mu comes from
                               the request */
-  size_t hbm_budget;       /* bytes of device memory for resident searches (default 4 GiB) */
+  size_t hbm_budget;       /* bytes of device memory for resident searches (default 4 GiB);
+                              outside binary64, min(1/8, 256 MiB) of it is the scratch in
+                              which the candidates of large searches (N >= 384) are
+                              drawn once per pass */
   int32_t max_slots;       /* resident searches at most (default 256) */
   int32_t iters_per_round; /* iterations per shared round (default 20) */
   int32_t queue_cap;       /* queued requests at most; beyond: TRSTMI_EBUSY (default 65536) */

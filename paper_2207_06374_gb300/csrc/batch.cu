@@ -35,6 +35,7 @@ using namespace trstmi;
 namespace {
 
 constexpr int kBatchGraphChunk = 16;
+constexpr size_t kBatchPlanesMax = 512ull << 20;
 // Pair list of the certification: the standalone instance's 65536 pairs, or
 // every pair when there are fewer, so that the list overflows exactly when a
 // standalone run's does.
@@ -357,8 +358,18 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
             up((size_t)slot_pair_cap(N[i]) * sizeof(uint2));
     }
   }
+  // scratch for drawing the candidates of the large binary32 instances once
+  // per pass (the largest such instance's candidates, at most 512 MiB)
+  size_t planes_bytes = 0;
+  if (o.precision != TRSTMI_FP64)
+    for (int i = 0; i < n; ++i) {
+      const size_t need = std::max<size_t>((size_t)o.K, tk) * 2 * (size_t)d[i] *
+                          (size_t)N[i] * sizeof(float);
+      if (N[i] >= BatchPlan::kPlanesMinN && need <= kBatchPlanesMax)
+        planes_bytes = std::max(planes_bytes, need);
+    }
   if (cudaMalloc(&b->block, off) != cudaSuccess ||
-      b->plan.init(n, screen ? (long long)n * o.K : 0, b->num_sms) != TRSTMI_OK) {
+      b->plan.init(n, screen ? (long long)n * o.K : 0, b->num_sms, planes_bytes) != TRSTMI_OK) {
     cudaGetLastError();
     trstmi_batch_destroy(b);
     return TRSTMI_ENOMEM;
@@ -564,6 +575,7 @@ int trstmi_batch_profile_score(trstmi_batch_handle b, int launches, size_t flush
     cudaError_t e = b->screen
         ? b->plan.launch_screen(b->d_err, s)
         : b->plan.launch_pass(kPassFull, b->d_slots, s);
+    if (e == cudaSuccess && !b->screen) e = b->plan.launch_large(kPassFull, s);
     float ms = 0.f;
     if (e != cudaSuccess || cudaEventRecord(b->ev1, s) != cudaSuccess ||
         cudaEventSynchronize(b->ev1) != cudaSuccess ||

@@ -493,8 +493,10 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   s0.gamma_dec = o.gamma_dec;
   s0.delta_min = o.delta_min;
   s0.delta_max = o.delta_max;
-  // a shape outside the screen kernel's range ranks with the binary32 Gram
-  s0.screen_min_delta = (is_screen(o.precision) && !screen_supported(N, d, screen_fmt_of(o.precision, d)))
+  // a shape outside the screen kernel's range ranks with the binary32 Gram,
+  // and the plain modes never use the screen (trace flag bit 0 stays clear)
+  s0.screen_min_delta = (!is_screen(o.precision) ||
+                         !screen_supported(N, d, screen_fmt_of(o.precision, d)))
                             ? std::numeric_limits<double>::infinity()
                             : o.screen_min_delta;
   s0.trace_cap = (uint32_t)o.trace_cap;

@@ -293,14 +293,25 @@ struct BatchPlan {
   int n_items = 0;        // screen items; the last n_wide of them take the wide format
   int n_wide = 0;
   unsigned long long* d_counters = nullptr;
+  // Large binary32 instances (N >= kPlanesMinN, scored in tiles): their
+  // candidate passes draw each candidate once into the planes scratch and run
+  // the double-buffered tile pass over them (the single-instance kernels, the
+  // same bits as the shared pass), one instance after the other.
+  static constexpr int kPlanesMinN = 384;
+  void* planes = nullptr;
+  size_t planes_bytes = 0;
+  std::vector<SlotDesc> large;
 
-  int init(int capacity_slots, long long capacity_items, int num_sms);
+  // planes_bytes: the scratch for large instances (0: none)
+  int init(int capacity_slots, long long capacity_items, int num_sms, size_t planes_bytes = 0);
   void destroy();
   // h: host copy of the device slot table (R of every slot chosen)
   int rebuild(const std::vector<SlotDesc>& h, int precision, cudaStream_t s);
   int enqueue_iteration(SlotDesc* d_slots, int n, uint32_t* err, cudaStream_t s) const;
   // the screen of every item: one launch per operand format present
   cudaError_t launch_screen(uint32_t* err, cudaStream_t s) const;
+  // a candidate pass (kPassFull or kPassRescore) of the large instances
+  cudaError_t launch_large(int pass, cudaStream_t s) const;
   cudaError_t launch_pass(int pass, SlotDesc* d_slots, cudaStream_t s) const;
   int kernels_per_iteration() const;
 };

@@ -25,7 +25,8 @@ int frame64_width(int d, int N, int R) {
 }
 }  // namespace
 
-int BatchPlan::init(int capacity_slots, long long capacity_items, int num_sms_) {
+int BatchPlan::init(int capacity_slots, long long capacity_items, int num_sms_,
+                    size_t planes_bytes_) {
   cap_slots = capacity_slots;
   cap_items = capacity_items;
   num_sms = num_sms_;
@@ -47,12 +48,29 @@ int BatchPlan::init(int capacity_slots, long long capacity_items, int num_sms_) 
   d_screen_slots = (ScreenSlot*)p; p += up(sizeof(ScreenSlot) * (size_t)cap_slots);
   d_items = (uint2*)p; p += up(sizeof(uint2) * (size_t)std::max<long long>(cap_items, 1));
   d_counters = (unsigned long long*)p;
+  planes_bytes = planes_bytes_ / 256 * 256;
+  if (planes_bytes > 0 && cudaMalloc(&planes, planes_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    planes = nullptr;
+    planes_bytes = 0;
+    return TRSTMI_ENOMEM;
+  }
   return TRSTMI_OK;
 }
 
 void BatchPlan::destroy() {
   if (mem) cudaFree(mem);
+  if (planes) cudaFree(planes);
   mem = nullptr;
+  planes = nullptr;
+  planes_bytes = 0;
+}
+
+// Whether instance sd's candidate passes run as a large instance.
+bool planes_instance(const SlotDesc& sd, bool f64, bool screen, size_t planes_bytes) {
+  if (f64 || sd.R == kResident || sd.N < BatchPlan::kPlanesMinN) return false;
+  const size_t cands = (size_t)std::max(sd.K, screen ? sd.topk_n : 0);
+  return cands * 2 * (size_t)sd.d * (size_t)sd.N * sizeof(float) <= planes_bytes;
 }
 
 int BatchPlan::rebuild(const std::vector<SlotDesc>& h, int precision_, cudaStream_t s) {
@@ -63,6 +81,13 @@ int BatchPlan::rebuild(const std::vector<SlotDesc>& h, int precision_, cudaStrea
   const bool screen = is_screen_prec(precision);
   maxN = 0; maxd = 0;
   for (const auto& sd : h) { maxN = std::max(maxN, sd.N); maxd = std::max(maxd, sd.d); }
+  std::vector<char> is_large(n, 0);
+  large.clear();
+  for (int i = 0; i < n; ++i)
+    if (planes && planes_instance(h[i], f64, screen, planes_bytes)) {
+      is_large[i] = 1;
+      large.push_back(h[i]);
+    }
   ncounters = 0;
   for (int pass = 0; pass < kPasses; ++pass) {
     groups[pass].clear();
@@ -79,7 +104,7 @@ int BatchPlan::rebuild(const std::vector<SlotDesc>& h, int precision_, cudaStrea
         const int r_tile = h[i].R == kResident ? 1 : h[i].R;
         const int r_i = pass == kPassFrame64 ? frame64_width(h[i].d, h[i].N, r_tile)
                         : cand_pass ? h[i].R : r_tile;
-        if (r_i == R) ids.push_back(i);
+        if (r_i == R && !(cand_pass && is_large[i])) ids.push_back(i);
       }
       if (ids.empty()) continue;
       auto keff = [&](int i) {
@@ -180,6 +205,7 @@ int BatchPlan::enqueue_iteration(SlotDesc* d_slots, int n, uint32_t* err, cudaSt
     return TRSTMI_ECUDA;
   if (!screen) {
     if (launch_pass(kPassFull, d_slots, s) != cudaSuccess ||
+        launch_large(kPassFull, s) != cudaSuccess ||
         launch_batch_decide(d_slots, n, f64, s) != cudaSuccess ||
         launch_batch_commit(d_slots, n, maxN, f64, s) != cudaSuccess)
       return TRSTMI_ECUDA;
@@ -189,8 +215,10 @@ int BatchPlan::enqueue_iteration(SlotDesc* d_slots, int n, uint32_t* err, cudaSt
   // them in fp32, regenerate the winner in fp64 and certify it, decide, commit
   if (launch_screen(err, s) != cudaSuccess ||
       launch_pass(kPassFull, d_slots, s) != cudaSuccess ||
+      launch_large(kPassFull, s) != cudaSuccess ||
       launch_batch_topk(d_slots, n, s) != cudaSuccess ||
       launch_pass(kPassRescore, d_slots, s) != cudaSuccess ||
+      launch_large(kPassRescore, s) != cudaSuccess ||
       launch_batch_materialize64(d_slots, n, maxN, s) != cudaSuccess ||
       launch_pass(kPassFrameMax, d_slots, s) != cudaSuccess ||
       launch_pass(kPassFilter, d_slots, s) != cudaSuccess ||
@@ -200,6 +228,35 @@ int BatchPlan::enqueue_iteration(SlotDesc* d_slots, int n, uint32_t* err, cudaSt
       launch_batch_commit_copy(d_slots, n, maxN, maxd, s) != cudaSuccess)
     return TRSTMI_ECUDA;
   return TRSTMI_OK;
+}
+
+cudaError_t BatchPlan::launch_large(int pass, cudaStream_t s) const {
+  for (const SlotDesc& sd : large) {
+    const bool full = pass == kPassFull;
+    // kPassFull: every candidate, while the instance ranks with the binary32
+    // Gram (use_full: always in the binary32 mode); kPassRescore: the top-k
+    // survivors, after the screen ranked them (use_screen)
+    const uint32_t* gate = full ? &sd.st->use_full : &sd.st->use_screen;
+    const int count = full ? sd.K : sd.topk_n;
+    const uint32_t* cands = full ? nullptr : sd.topk;
+    const float2* phi = reinterpret_cast<const float2*>(sd.phi);
+    cudaError_t e = launch_gen_planes_f32(sd.N, sd.d, count, phi, sd.seed, 0u, sd.st, 0u, 0.0,
+                                          reinterpret_cast<float*>(planes), s, cands, gate);
+    if (e != cudaSuccess) return e;
+    GramSource src{};
+    src.perturb = true;
+    src.phi = phi;
+    src.seed = sd.seed;
+    src.cand_list = cands;
+    src.st = sd.st;
+    src.gate = gate;
+    src.planes = planes;
+    e = launch_gram_f32(sd.N, sd.d, count, src,
+                        full ? reinterpret_cast<unsigned int*>(sd.mu2) : sd.mu2_top, nullptr,
+                        num_sms, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t BatchPlan::launch_screen(uint32_t* err, cudaStream_t s) const {
@@ -219,6 +276,7 @@ int BatchPlan::kernels_per_iteration() const {
   for (int p = 0; p < kPasses; ++p) k += (int)groups[p].size();
   if (is_screen_prec(precision)) k += (n_items > n_wide ? 1 : 0) + (n_wide ? 1 : 0) + 6;
   else k += 2;
+  k += (int)large.size() * (is_screen_prec(precision) ? 4 : 2);
   return k;
 }
 

@@ -218,6 +218,12 @@ int choose_width(trstmi_server* sv, Slot& sl) {
   const int N = sl.desc.N, d = sl.desc.d;
   int R = cached_width(sv->f64, d, N);   // the binary32 pass in the screen modes
   if (R >= 0) return R;
+  // large binary32 searches draw their candidates once into the plan's
+  // scratch and take the widest tiles; nothing to measure
+  if (!sv->f64 && N >= BatchPlan::kPlanesMinN && width_feasible(false, d, N, 4)) {
+    store_width(false, d, N, 4);
+    return 4;
+  }
   // measure this bucket on this slot alone (its state is active for timing)
   int best_R = 1;
   float best = 1e30f;
@@ -620,12 +626,18 @@ int trstmi_server_create(const trstmi_server_opts* opts, trstmi_server** out) {
   const size_t b_st = up256(ms * sizeof(DevState)), b_sl = up256(ms * sizeof(SlotDesc)),
                b_bu = up256(ms * sizeof(uint32_t)), b_er = up256(sizeof(uint32_t)),
                b_ti = up256(sizeof(int)), b_tb = up256(2 * sizeof(long long));
+  // of the budget, min(1/8, 256 MiB) is the scratch in which the candidates
+  // of large binary32 searches are drawn once per pass; the rest holds the
+  // resident searches
+  const size_t planes_bytes =
+      sv->f64 ? 0 : std::min<size_t>(256ull << 20, o.hbm_budget / 8) / 256 * 256;
+  const size_t arena_bytes = o.hbm_budget - planes_bytes;
   char* ctl = nullptr;
   if (cudaMalloc(&ctl, b_st + b_sl + b_bu + b_er + b_ti + b_tb) != cudaSuccess ||
       cudaMemset(ctl, 0, b_st + b_sl + b_bu + b_er + b_ti + b_tb) != cudaSuccess ||
-      cudaMalloc(&sv->arena_mem, o.hbm_budget) != cudaSuccess ||
-      sv->plan.init(o.max_slots, sv->screen ? (long long)o.max_slots * so.K : 0, sv->num_sms) !=
-          TRSTMI_OK) {
+      cudaMalloc(&sv->arena_mem, arena_bytes) != cudaSuccess ||
+      sv->plan.init(o.max_slots, sv->screen ? (long long)o.max_slots * so.K : 0, sv->num_sms,
+                    planes_bytes) != TRSTMI_OK) {
     cudaGetLastError();
     sv->d_states = (DevState*)ctl;   // freed by destroy
     trstmi_server_destroy(sv);
@@ -637,7 +649,7 @@ int trstmi_server_create(const trstmi_server_opts* opts, trstmi_server** out) {
   sv->d_err = (uint32_t*)(ctl + b_st + b_sl + b_bu);
   sv->d_tune_ids = (int*)(ctl + b_st + b_sl + b_bu + b_er);
   sv->d_tune_begin = (long long*)(ctl + b_st + b_sl + b_bu + b_er + b_ti);
-  sv->arena.reset((char*)sv->arena_mem, o.hbm_budget);
+  sv->arena.reset((char*)sv->arena_mem, arena_bytes);
   for (int i = o.max_slots - 1; i >= 0; --i) sv->free_states.push_back(i);
   sv->worker = std::thread(worker_main, sv);
   *out = sv;

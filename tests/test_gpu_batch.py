@@ -46,6 +46,34 @@ def test_batch_instances_match_single_runs_bitwise(precision):
             assert mus[i] == mu_single
 
 
+# large instances (N >= 384, scored in tiles): their candidate passes draw each
+# candidate once into a scratch and run the double-buffered tile pass, one
+# instance at a time, between the shared launches of the others
+LARGE_MIX = [(400, 12), (1024, 24), (30, 5), (700, 48), (2000, 8), (129, 13)]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_large_instances_match_single_runs_bitwise(precision):
+    Ns = [n for n, _ in LARGE_MIX]
+    ds = [d for _, d in LARGE_MIX]
+    seeds = [500 + i for i in range(len(LARGE_MIX))]
+    K, iters = 64, 10
+    with T.Batch(Ns, ds, seeds, K=K, precision=precision, topk=4, trace_cap=32) as b:
+        b.step(iters)
+        mus, its = b.mu()
+        assert np.all(its == iters)
+        for i, (N, d) in enumerate(LARGE_MIX):
+            with T.Search(N, d, seeds[i], K=K, precision=precision, topk=4, trace_cap=32) as s:
+                s.step(iters)
+                tr_single = s.trace()
+                assert np.array_equal(b.get_phi(i), s.get_phi()), (i, N, d)
+                mu_single = s.step(0).mu
+            tr = b.trace(i)
+            for f in ("cstar", "accepted", "flags", "mu2_best", "mu2_screen"):
+                assert np.array_equal(tr[f], tr_single[f]), (f, i, N, d)
+            assert mus[i] == mu_single
+
+
 def test_batch_fp64_matches_oracle():
     Ns, ds = [4, 7, 12, 30], [2, 3, 5, 4]
     seeds = [5, 6, 7, 8]

@@ -77,6 +77,23 @@ def test_screen_mode_results_equal_standalone_runs(precision):
         assert np.array_equal(phi, phi_alone), (N, d)
 
 
+def test_fp32_results_with_large_requests_equal_standalone_runs():
+    """Binary32 serving with requests large enough (N >= 384) for the loop's
+    draw-once scratch: every result equals the standalone run."""
+    K = 32
+    reqs = [(1024, 16, 31, 12), (40, 6, 32, 30), (600, 40, 33, 10), (3000, 4, 34, 6)]
+    with T.Server(hbm_budget=512 << 20, max_slots=4, iters_per_round=4, K=K,
+                  precision="fp32") as srv:
+        tickets = [srv.submit(N, d, seed, budget, want_phi=True) for N, d, seed, budget in reqs]
+        results = [srv.wait(t, with_phi=True) for t in tickets]
+    for (N, d, seed, budget), (st, res, phi) in zip(reqs, results):
+        assert st == T.TRSTMI_OK and res.iters == budget
+        with T.Search(N, d, seed, K=K, precision="fp32", trace_cap=0) as s:
+            s.step(budget)
+            assert res.mu == s.step(0).mu, (N, d)
+            assert np.array_equal(phi, s.get_phi()), (N, d)
+
+
 def test_admission_respects_memory_budget():
     # each (N=1024, d=32) slot needs ~0.8 MiB; a 2 MiB budget holds two at a time
     with T.Server(hbm_budget=2 << 20, max_slots=8, iters_per_round=2, K=8,
