@@ -6,8 +6,9 @@ CG-Steihaug (Algorithm "Trust-Region CG-Steihaug", after Nocedal and Wright
 Alg. 7.2), from L random starts (Algorithm "TRSTMI optimization steps").
 
 * CG-Steihaug on explicit quadratic models: the interior solution -B^-1 g
-  (library solve), the boundary, negative curvature, no worse than the
-  Cauchy point (Nocedal and Wright (4.12)), termination within n steps;
+  (library solve), the boundary, negative curvature (and there the better of
+  the two boundary points), no worse than the Cauchy point (Nocedal and
+  Wright (4.12)), termination within n steps;
 * the Hessian-vector product against second differences of F itself and
   its symmetry;
 * the whole procedure from random starts reaches the known optima: the
@@ -73,6 +74,42 @@ def test_cg_follows_negative_curvature_to_the_boundary():
     assert st == 2
     assert np.linalg.norm(p) == pytest.approx(0.5, rel=1e-12)
     assert m < 0 and m == pytest.approx(_m(g, B, p), rel=1e-10)
+
+
+def test_cg_negative_curvature_takes_the_better_boundary_point():
+    """On negative curvature after the first step, CG-Steihaug moves from its
+    iterate z_j along d_j to the boundary; of the two points where that line
+    meets the sphere it takes the one with the smaller model value.  Checked
+    from the oracle's outputs alone: z_j is the result of the same call
+    stopped after j iterations, the line is the one through z_j and the
+    returned p, its other intersection is z_j + (c/a)(p - z_j) (the product of
+    the roots of |z_j + s (p - z_j)|^2 = radius^2 is c/a and s = 1 is one of
+    them), and the root taken was the negative one exactly when the model
+    gradient at z_j, r_j = g + B z_j, has r_j.(p - z_j) > 0 (CG keeps
+    r_j.d_j = -|r_j|^2).  Both roots must occur among the cases."""
+    found = negative = 0
+    for seed in range(400):
+        rng = np.random.default_rng(seed)
+        n = int(rng.integers(2, 6))
+        q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        lam = rng.uniform(-1.0, 3.0, size=n)
+        lam[0] = -abs(lam[0]) - 0.1
+        B = q @ np.diag(lam) @ q.T
+        g = rng.standard_normal(n)
+        radius = float(rng.uniform(0.2, 3.0))
+        p, m, it, st = O.cg_steihaug(g, lambda v: B @ v, radius, 1e-13, 50)
+        if st != 2 or it < 2:
+            continue
+        found += 1
+        z, _, itz, stz = O.cg_steihaug(g, lambda v: B @ v, radius, 1e-13, it - 1)
+        assert (itz, stz) == (it - 1, 3)
+        u = p - z
+        other = z + ((z @ z - radius ** 2) / (u @ u)) * u
+        assert np.linalg.norm(other) == pytest.approx(radius, rel=1e-10)
+        assert m == pytest.approx(_m(g, B, p), rel=1e-10, abs=1e-13)
+        assert _m(g, B, p) <= _m(g, B, other) + 1e-12
+        negative += int((g + B @ z) @ u > 0)
+    assert found >= 40 and 3 <= negative < found
 
 
 def test_cg_returns_zero_for_a_small_gradient():
