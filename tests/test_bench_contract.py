@@ -1,5 +1,5 @@
 """The benchmark's JSON line (CPU only): the reference arm times the oracle and
-prints one line with the keys the driver reads."""
+prints one line with every key of the benchmark contract."""
 import json
 import os
 import subprocess

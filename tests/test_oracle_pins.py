@@ -118,7 +118,7 @@ def test_etf_meets_welch_bound(name, make):
     assert abs(O.welch(N, d) - W) < 1e-15
 
 
-def test_welch_values_printed_in_survey_of_configs():
+def test_welch_values_at_the_workload_shapes():
     # closed-form values at the workload shapes (Sec. "Welch bound ...")
     assert abs(O.welch(4, 2) - 1 / np.sqrt(3)) < 1e-15
     assert abs(O.welch(7, 3) - np.sqrt(2 / 9)) < 1e-15
