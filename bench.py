@@ -1162,7 +1162,7 @@ def run_serving(args, ws, rank, local, dist, torch, T):
             "completed_ok": ok, "reached_target": reached,
             "offered_load_ratio": float(sum(run_s) / max(arrivals_span, 1e-9)),
             "server": {"rounds": stats.rounds, "gpu_busy_s": stats.gpu_busy_s, "wall_s": wall},
-            "gpu_launches": None, "clocks": clocks,
+            "gpu_launches": int(stats.kernel_launches), "clocks": clocks,
             "e2e": {"value": pairs / wall, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0,
                     "call": "trstmi_submit + trstmi_wait (the served run above is end to end)"}}

@@ -366,6 +366,8 @@ typedef struct trstmi_server_stats_t {
   int32_t active_slots, queued;
   int32_t worker_status;   /* TRSTMI_OK, or the error that stopped the loop */
   int32_t timed_out;       /* requests that ended with TRSTMI_ETIMEOUT */
+  uint64_t kernel_launches; /* kernels the loop launched (rounds, admissions, width
+                               measurements) */
 } trstmi_server_stats_t;
 
 void trstmi_default_server_opts(trstmi_server_opts *opts);

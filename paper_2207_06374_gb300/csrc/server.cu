@@ -210,6 +210,7 @@ struct trstmi_server {
   int32_t timed_out = 0;
   uint64_t pairs_scored = 0;
   double gpu_busy_s = 0.0;
+  std::atomic<uint64_t> launches{0};   // kernels the loop launched
 };
 
 namespace {
@@ -230,6 +231,7 @@ int choose_width(trstmi_server* sv, Slot& sl) {
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return 1;
   k_srv_activate<<<1, 1, 0, sv->stream>>>(sl.desc.st, 1u);
+  sv->launches += 2;   // this one and the deactivation below
   for (int cand : {kResident, 1, 2, 4}) {
     if (!width_feasible(sv->f64, d, N, cand)) continue;
     SlotDesc tmp = sl.desc;
@@ -260,6 +262,7 @@ int choose_width(trstmi_server* sv, Slot& sl) {
         launch_batch_score(sv->f64, cand, sv->d_slots, sv->d_tune_ids, sv->d_tune_begin, 1, nitems,
                            sv->plan.d_counters, smem, grid, sv->stream, kPassFull);
       cudaEventRecord(e1, sv->stream);
+      sv->launches += 1;
       cudaEventSynchronize(e1);
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
@@ -360,6 +363,7 @@ int admit(trstmi_server* sv, uint64_t ticket, Req& r, Slot* out) {
   if (sv->f64 || sv->screen) k_srv_set_mu2cur<unsigned long long><<<1, 1, 0, s>>>(sd.st, init_out);
   else k_srv_set_mu2cur<unsigned int><<<1, 1, 0, s>>>(sd.st, init_out);
   if (cudaGetLastError() != cudaSuccess) return TRSTMI_ECUDA;
+  sv->launches += 3;   // initial frame, initial score, its copy into the state
   // tile width: the cached choice for this (d, N) bucket, measured if new
   sd.R = 1;
   sd.ntiles = tiles_at_width(N, 1);
@@ -485,6 +489,7 @@ void worker_main(trstmi_server* sv) {
     bool ok = cudaGetLastError() == cudaSuccess;
     for (int it = 0; ok && it < I; ++it)
       ok = sv->plan.enqueue_iteration(sv->d_slots, n, sv->d_err, s) == TRSTMI_OK;
+    sv->launches += 1 + (uint64_t)I * (uint64_t)sv->plan.kernels_per_iteration();
     // one copy of the whole state array, then each slot's entry
     all_st.resize(sv->opt.max_slots);
     ok = ok && cudaMemcpyAsync(all_st.data(), sv->d_states, sizeof(DevState) * all_st.size(),
@@ -730,6 +735,7 @@ int trstmi_server_stats(trstmi_server* sv, trstmi_server_stats_t* out) {
   out->queued = (int32_t)sv->queue.size();
   out->worker_status = sv->worker_error;
   out->timed_out = sv->timed_out;
+  out->kernel_launches = sv->launches.load();
   return TRSTMI_OK;
 }
 

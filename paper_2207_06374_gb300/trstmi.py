@@ -90,7 +90,8 @@ class ServerStats(ctypes.Structure):
                 ("rounds", ctypes.c_uint64), ("pairs_scored", ctypes.c_uint64),
                 ("gpu_busy_s", ctypes.c_double), ("hbm_in_use", ctypes.c_size_t),
                 ("active_slots", ctypes.c_int32), ("queued", ctypes.c_int32),
-                ("worker_status", ctypes.c_int32), ("timed_out", ctypes.c_int32)]
+                ("worker_status", ctypes.c_int32), ("timed_out", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_uint64)]
 
 
 _lock = threading.Lock()

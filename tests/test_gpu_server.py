@@ -86,6 +86,9 @@ def test_fp32_results_with_large_requests_equal_standalone_runs():
                   precision="fp32") as srv:
         tickets = [srv.submit(N, d, seed, budget, want_phi=True) for N, d, seed, budget in reqs]
         results = [srv.wait(t, with_phi=True) for t in tickets]
+        stats = srv.stats()
+    # three kernels per admission, at least three per iteration of the longest request
+    assert stats.kernel_launches >= 3 * len(reqs) + 3 * max(r[3] for r in reqs)
     for (N, d, seed, budget), (st, res, phi) in zip(reqs, results):
         assert st == T.TRSTMI_OK and res.iters == budget
         with T.Search(N, d, seed, K=K, precision="fp32", trace_cap=0) as s:
