@@ -82,6 +82,25 @@ L2_FLUSH_BYTES = 512 << 20
 SEED = 1
 
 
+# the metric of each workload, shared by both arms (--impl reference prints the
+# same metric, unit and direction as the library's arm)
+PAIRS_METRIC = "off-diagonal Gram pairs scored per second (K*N(N-1)/2 per iteration)"
+METRICS = {
+    "batched_512": "off-diagonal Gram pairs scored per second (sum over instances of "
+                   "K*N(N-1)/2 per iteration)",
+    "serving": "serving: p50/p99 solve latency and off-diagonal Gram pairs scored per second",
+    "objective_d32_n1024": "off-diagonal Gram pairs per second through the smooth-maximum "
+                           "objective and its gradient (K frames x N(N-1)/2 per call)",
+    "trust_region_d32_n1024": "trust-region iterations per second (one frame)",
+    "table2_all": "seconds for the whole algorithm on every row of Table 2",
+    "table2_d8_n64": "seconds for the whole algorithm (2d^2 trials, seven smoothing stages)",
+}
+
+
+def metric_of(wl):
+    return METRICS.get(wl, PAIRS_METRIC)
+
+
 def pairs_per_step(d, N, K):
     return K * N * (N - 1) // 2
 
@@ -305,7 +324,7 @@ def run_reference(args, wl):
                 break
         dt = time.perf_counter() - t0
         total = dt / done * K
-        line = {"impl": "reference", "metric": "seconds for the whole algorithm (2d^2 trials)",
+        line = {"impl": "reference", "metric": metric_of(wl),
                 "value": total, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
                 "ms_per_step": total * 1e3, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": total / TABLE2_PAPER_S, "dtype": "f64",
@@ -327,7 +346,7 @@ def run_reference(args, wl):
         _, tr = O.tr_solve(v, O.tr_opts(deltas=(LSE_DELTA,), max_outer=1, max_cg=3))
         dt = time.perf_counter() - t0
         rate = len(tr) / dt
-        line = {"impl": "reference", "metric": "trust-region iterations per second",
+        line = {"impl": "reference", "metric": metric_of(wl),
                 "value": rate, "unit": "iterations/s", "n_gpus": 1, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": dt / max(len(tr), 1) * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -345,8 +364,7 @@ def run_reference(args, wl):
     if wl == "objective_d32_n1024":
         fr = lse_frames(max(1, args.steps) * 8, d, N, SEED)
         rate, done, dt = lse_oracle_rate(d, N, fr)
-        line = {"impl": "reference", "metric": "off-diagonal Gram pairs per second through the "
-                "smooth-maximum objective and its gradient", "value": rate, "unit": "pairs/s",
+        line = {"impl": "reference", "metric": metric_of(wl), "value": rate, "unit": "pairs/s",
                 "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": dt / done * 1e3 * K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -358,6 +376,12 @@ def run_reference(args, wl):
                 "e2e": {"value": rate, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
+        return
+    if wl in ("batched_512", "serving"):
+        run_reference_many(args, wl)
+        return
+    if wl == "table2_all":
+        run_reference_table2_all(args, wl)
         return
     steps, warm = args.steps, args.warmup
     import oracle as O
@@ -372,7 +396,7 @@ def run_reference(args, wl):
         O.score(phi, SEED, 0.1, 1 + s, 0, count, nthreads=cores)
     dt = time.perf_counter() - t0
     value = steps * count * per_cand / dt
-    line = {"impl": "reference", "metric": "off-diagonal Gram pairs scored per second",
+    line = {"impl": "reference", "metric": metric_of(wl),
             "value": value, "unit": "pairs/s", "n_gpus": 1, "steps": steps, "warmup": warm,
             "ms_per_step": dt / steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox frames)",
@@ -382,6 +406,82 @@ def run_reference(args, wl):
                              "kind": "oracle",
                              "sample": f"{count} of {K} candidates per step, d={d}, N={N}"},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_many(args, wl):
+    """The oracle on the instances of the batched form or the requests of the
+    serving stream, one after the other, each scoring its K candidates of one
+    iteration on the host cores, until about 20 s of work; pairs per second."""
+    import oracle as O
+    from paper_2207_06374_gb300 import workloads as W
+    cores = len(os.sched_getaffinity(0))
+    if wl == "batched_512":
+        Ns, ds, seeds = W.batched_instances(512, seed=7)
+        K = WORKLOADS[wl][2]
+    else:
+        reqs = W.serving_requests(args.requests, seed=11, rate_hz=args.rate)
+        Ns, ds, seeds = [r["N"] for r in reqs], [r["d"] for r in reqs], [r["seed"] for r in reqs]
+        K = args.serve_k
+    t0 = time.perf_counter()
+    pairs = done = 0
+    for N, d, seed in zip(Ns, ds, seeds):
+        O.score(O.init(N, d, seed), seed, 0.1, 1, 0, K, nthreads=cores)
+        pairs += pairs_per_step(d, N, K)
+        done += 1
+        if time.perf_counter() - t0 > 20.0:
+            break
+    dt = time.perf_counter() - t0
+    value = pairs / dt
+    what = "instances" if wl == "batched_512" else "requests"
+    sample = f"{done} of {len(Ns)} {what}, one iteration of K={K} candidates each, {dt:.1f} s"
+    line = {"impl": "reference", "metric": metric_of(wl), "value": value, "unit": "pairs/s",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Philox frames, the workload's recipe)",
+            "config": {"workload": wl, "K": K, "precision": "fp64 oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_table2_all(args, wl):
+    """The oracle's whole algorithm on every row of Table 2 (2d^2 trials of the
+    trust-region procedure, seven smoothing stages), each row timed on a sample
+    of its trials (at most 10 s per row, one core) and scaled to all of them;
+    value = the sum of the rows' seconds."""
+    import oracle as O
+    deltas = (0.1, 0.03, 0.01, 0.003, 0.001, 3e-4, 1e-4)
+    rows, total = {}, 0.0
+    for d in range(2, 10):
+        N, L = d * d, 2 * d * d
+        t0 = time.perf_counter()
+        done, best = 0, 1.0
+        for i in range(L):
+            phi, _ = O.tr_solve(O.init(N, d, SEED + i),
+                                O.tr_opts(deltas=deltas, max_outer=100, max_cg=200))
+            best = min(best, float(np.sqrt(O.mu2(phi))))
+            done += 1
+            if time.perf_counter() - t0 > 10.0:
+                break
+        dt = time.perf_counter() - t0
+        secs = dt / done * L
+        total += secs
+        rows[f"d{d}_n{N}"] = {"seconds": secs, "trials": L, "trials_run": done,
+                              "best_mu_of_trials_run": best}
+    sample = "every row: the trials run within 10 s on one core, scaled to 2d^2 trials"
+    line = {"impl": "reference", "metric": metric_of(wl), "value": total, "unit": "s",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": total * 1e3,
+            "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": total / sum(v[0] for v in TABLE2_PAPER.values()), "dtype": "f64",
+            "data": "synthetic (seeded Philox initial frames)",
+            "config": {"workload": wl, "precision": "fp64 oracle", "rows": rows},
+            "cpu_baseline": {"value": total, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": total, "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -587,7 +687,7 @@ def main():
                 "unit": "pairs/s", "ms_per_step": 1e3 * sum(times2) / len(times2)}
         s2.close()
 
-    line = {"metric": "off-diagonal Gram pairs scored per second (K*N(N-1)/2 per iteration)",
+    line = {"metric": metric_of(wl),
             "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
             "higher_is_better": True, "scaling": "strong" if sharded else "weak",
@@ -669,7 +769,7 @@ def run_batched(args, ws, rank, local, dist, torch, T):
     achieved = flops / (kernel_ms * 1e-3) / 1e12
     mus, its = b.mu()
     ngroups = len(set(widths))
-    line = {"metric": "off-diagonal Gram pairs scored per second (sum over instances of K*N(N-1)/2 per iteration)",
+    line = {"metric": metric_of("batched_512"),
             "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -800,8 +900,7 @@ def run_objective(args, ws, rank, local, dist, torch, T):
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = fp32_alu_peak_tflops(sm_mhz)
     achieved = flops / (kernel_ms * 1e-3) / 1e12
-    line = {"metric": "off-diagonal Gram pairs per second through the smooth-maximum objective "
-                      "and its gradient (K frames x N(N-1)/2 per call)",
+    line = {"metric": metric_of("objective_d32_n1024"),
             "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": kernel_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -870,7 +969,7 @@ def run_trust_region(args, ws, rank, local, dist, torch, T):
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = fp32_alu_peak_tflops(sm_mhz) / 64
     achieved = flops / dt / 1e12
-    line = {"metric": "trust-region iterations per second (one frame)",
+    line = {"metric": metric_of("trust_region_d32_n1024"),
             "value": ws * iters / dt, "unit": "iterations/s", "n_gpus": ws, "steps": iters,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(iters, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -948,7 +1047,7 @@ def run_table2_all(args, ws, rank, local, dist, torch, T):
     peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0)) / 64
     achieved = flops / total / 1e12
     paper_total = sum(v[0] for v in TABLE2_PAPER.values())
-    line = {"metric": "seconds for the whole algorithm on every row of Table 2",
+    line = {"metric": metric_of("table2_all"),
             "value": total, "unit": "s", "n_gpus": ws, "steps": 1, "warmup": 1,
             "ms_per_step": 1e3 * total, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": total / paper_total, "dtype": "f64",
@@ -1006,7 +1105,7 @@ def run_table2(args, ws, rank, local, dist, torch, T):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt.item())
     pairs = N * (N - 1) // 2
-    line = {"metric": "seconds for the whole algorithm (2d^2 trials, seven smoothing stages)",
+    line = {"metric": metric_of("table2_d8_n64"),
             "value": t, "unit": "s", "n_gpus": ws, "steps": steps, "warmup": 1,
             "ms_per_step": 1e3 * t, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": t / TABLE2_PAPER_S, "dtype": "f64",
@@ -1132,7 +1231,7 @@ def run_serving(args, ws, rank, local, dist, torch, T):
         seq_lat.append(free_at - r["t_arrive"])
     seq_lat = np.array(seq_lat)
     arrivals_span = reqs[-1]["t_arrive"] if reqs else 0.0
-    line = {"metric": "serving: p50/p99 solve latency and off-diagonal Gram pairs scored per second",
+    line = {"metric": metric_of("serving"),
             "value": pairs / wall, "unit": "pairs/s", "n_gpus": ws, "steps": len(reqs),
             "warmup": 0, "ms_per_step": 1e3 * wall / max(len(reqs), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec == "bf16" else "f32",

@@ -22,10 +22,14 @@ def _run(*args):
     return json.loads(lines[0])
 
 
-@pytest.mark.parametrize("workload", ["plain_d2_n4_fp64", "plain_d8_n64"])
+@pytest.mark.parametrize("workload", ["plain_d2_n4_fp64", "plain_d8_n64", "batched_512"])
 def test_reference_arm_prints_one_complete_line(workload):
+    sys.path.insert(0, ROOT)
+    import bench
     line = _run("--workload", workload, "--steps", "2", "--warmup", "1")
     assert KEYS <= set(line)
+    # the same metric as the library's arm of this workload
+    assert line["metric"] == bench.metric_of(workload)
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["config"]["workload"] == workload
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
