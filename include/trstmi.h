@@ -239,9 +239,14 @@ const char *trstmi_last_error(void);
  * columns) are chosen per (d, ceil log2 N) by an autotuner that times the
  * scoring pass on the instances themselves at creation; choices are cached
  * for the process.  Every precision mode is accepted; in the screen modes the
- * tensor-core screen of every instance it takes runs as one shared launch
- * over all (instance, candidate) pairs, then re-score, certification, accept
- * rule and commit run as shared launches too.
+ * tensor-core screen of every instance it takes runs as one shared launch per
+ * operand format (d <= 32, and 32 < d <= 64) over all (instance, candidate)
+ * pairs, then re-score, certification, accept rule and commit run as shared
+ * launches too.  Outside binary64, the candidate passes of large instances
+ * (N >= 384, scored in tiles) draw each candidate once into a scratch and run
+ * the double-buffered tile pass, one such instance after the other; the
+ * scratch holds the largest such instance's candidates (at most 512 MiB) and
+ * is allocated at creation.
  */
 typedef struct trstmi_batch *trstmi_batch_handle;
 
