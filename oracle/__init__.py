@@ -66,7 +66,8 @@ class TrOpts(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("max_cg", ctypes.c_int),
                 ("radius0", ctypes.c_double), ("radius_max", ctypes.c_double),
                 ("eta", ctypes.c_double), ("gtol", ctypes.c_double),
-                ("fd_step", ctypes.c_double)]
+                ("fd_step", ctypes.c_double), ("hessian", ctypes.c_int),
+                ("pad", ctypes.c_int)]
 
 
 TR_DTYPE = np.dtype([("stage", "<i4"), ("iter", "<i4"), ("F", "<f8"), ("s", "<f8"),
@@ -323,8 +324,11 @@ def lse_hv(v: np.ndarray, delta: float, h: float, u: np.ndarray) -> np.ndarray:
 
 
 def tr_opts(deltas=(0.1, 0.01, 0.001), max_outer=50, max_cg=50, radius0=0.1, radius_max=1.0,
-            eta=1e-4, gtol=1e-9, fd_step=1e-6) -> TrOpts:
+            eta=1e-4, gtol=1e-9, fd_step=1e-6, hessian="exact") -> TrOpts:
+    """hessian: "exact" (B_k, the Hessian of F: the paper's model) or
+    "difference" (central differences of the gradient with step fd_step)."""
     o = TrOpts()
+    o.hessian = {"exact": 0, "difference": 1}[hessian]
     o.n_delta = len(deltas)
     for i, x in enumerate(deltas):
         o.delta[i] = x

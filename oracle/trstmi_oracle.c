@@ -663,6 +663,10 @@ typedef struct oracle_tr_opts {
     int max_outer;        /* trust-region iterations per stage */
     int max_cg;           /* CG iterations per step */
     double radius0, radius_max, eta, gtol, fd_step;
+    int hessian;          /* 0: B_k = the exact Hessian of F (the paper's model);
+                             1: central differences of the gradient with step
+                             fd_step (for diagnosis only) */
+    int pad;
 } oracle_tr_opts;
 
 typedef struct oracle_tr_row {
@@ -671,14 +675,33 @@ typedef struct oracle_tr_row {
     int32_t cg_iters, cg_status, accepted, pad;
 } oracle_tr_row;
 
+int oracle_lse_hv_exact(int N, int d, const double *v, double delta, const double *u,
+                        double *out);
+
+/* B u with B the exact Hessian of F_{s,delta} at the context's point
+ * (oracle_lse_hv_exact, below). */
+static void lse_hv_exact_cb(const double *u, double *out, void *vctx)
+{
+    oracle_hv_ctx *c = (oracle_hv_ctx *)vctx;
+    if (oracle_lse_hv_exact(c->N, c->d, c->v, c->delta, u, out) != ORACLE_OK) {
+        int n = 2 * c->d * c->N;
+        for (int i = 0; i < n; ++i) out[i] = NAN;
+    }
+    c->products++;
+}
+
 /*
  * The paper's procedure on one frame (Sec. "Optimization procedure";
  * Algorithm "TRSTMI optimization steps", step 2): for each smoothing
  * parameter delta_k in turn, minimise F_{s,delta_k} over the variable V by
  * trust-region iterations whose steps come from CG-Steihaug (above), starting
- * from the previous stage's result.  Per iteration (the standard trust-region
- * loop, Nocedal and Wright Alg. 4.1): g = grad F; stop the stage when
- * |g| <= gtol; p from CG-Steihaug with eps = min(1/2, sqrt|g|) |g|;
+ * from the previous stage's result.  The model of each step is the paper's
+ * m(p) = F + g.p + p.B p / 2 with B the Hessian of F at V (Algorithm
+ * "Trust-Region CG-Steihaug", B_k = grad^2 f_k); its products come from
+ * oracle_lse_hv_exact, or, with o->hessian = 1, from central differences of
+ * the gradient (a diagnosis option).  Per iteration (the standard
+ * trust-region loop, Nocedal and Wright Alg. 4.1): g = grad F; stop the
+ * stage when |g| <= gtol; p from CG-Steihaug with eps = min(1/2, sqrt|g|) |g|;
  * rho = (F(V) - F(V + p)) / (-m(p)); radius /4 if rho < 1/4, doubled (capped)
  * if rho > 3/4 and |p| reached it; accept if rho > eta, then every column of
  * V is divided by its norm (F does not change).  The radius starts at
@@ -688,6 +711,7 @@ int oracle_tr_solve(int N, int d, double *v, const oracle_tr_opts *o, oracle_tr_
                     int cap, int *n_rows)
 {
     if (N < 2 || d < 1 || !v || !o || o->n_delta < 1 || o->n_delta > 16) return ORACLE_EINVAL;
+    if (o->hessian != 0 && o->hessian != 1) return ORACLE_EINVAL;
     int n = 2 * d * N;
     size_t bytes = sizeof(double) * (size_t)n;
     double *g = (double *)malloc(bytes), *p = (double *)malloc(bytes);
@@ -710,7 +734,8 @@ int oracle_tr_solve(int N, int d, double *v, const oracle_tr_opts *o, oracle_tr_
             if (gn <= o->gtol) break;
             double eps = (sqrt(gn) < 0.5 ? sqrt(gn) : 0.5) * gn, m;
             int cgit, cgst;
-            oracle_cg_steihaug(n, g, lse_hv, &c, radius, eps, o->max_cg, p, &m, &cgit, &cgst);
+            oracle_cg_steihaug(n, g, o->hessian == 1 ? lse_hv : lse_hv_exact_cb, &c, radius, eps,
+                               o->max_cg, p, &m, &cgit, &cgst);
             double pn = sqrt(vdot(n, p, p));
             for (int i = 0; i < n; ++i) vn[i] = v[i] + p[i];
             st = oracle_lse(N, d, vn, delta, &Fn, &sn, NULL);
@@ -753,8 +778,8 @@ out:
  *   dg_k = 2 sum_{j != k} (dM_jk phi_j + M_jk d phi_j),
  *   d rho_k = Re(d phi_k^* g_k + phi_k^* dg_k),
  *   (H u)_k = (dg_k - d phi_k rho_k - phi_k d rho_k) / r_k - grad_k d r_k / r_k.
- * The paper's B_k; the procedure above uses central differences of the
- * gradient instead, and this function measures how far they are apart.
+ * The paper's B_k, used by oracle_tr_solve (its central-difference option,
+ * lse_hv, is measured against this function by the tests).
  */
 int oracle_lse_hv_exact(int N, int d, const double *v, double delta, const double *u,
                         double *out)

@@ -10,7 +10,9 @@ Alg. 7.2), from L random starts (Algorithm "TRSTMI optimization steps").
   the two boundary points), no worse than the Cauchy point (Nocedal and
   Wright (4.12)), termination within n steps;
 * the Hessian-vector product against second differences of F itself and
-  its symmetry;
+  its symmetry; the procedure's model uses the exact Hessian B_k of F (the
+  paper's model), and its central-difference option agrees with it on the
+  first rows;
 * the whole procedure from random starts reaches the known optima: the
   equiangular tight frames (2,4), (3,7), (3,9), (4,8) at the Welch bound,
   the SICs (4,16), (5,25) likewise and no worse than the paper's Table 2
@@ -258,3 +260,18 @@ def test_reaches_the_sics_of_c6_and_c7(d, seed):
     mu = np.sqrt(O.mu2(vf))
     assert mu == pytest.approx(1 / np.sqrt(d + 1), abs=1e-8)
     assert mu <= {6: 0.3780, 7: 0.3536}[d]
+
+
+def test_central_difference_option_follows_the_exact_model_at_first():
+    """The procedure with B_k the exact Hessian (default) and with its
+    central-difference option take the same first steps: the products differ
+    by ~1e-9 relative, far below what changes a CG exit or an acceptance."""
+    v = _raw(3, 9, np.random.default_rng(11))
+    kw = dict(deltas=(0.03,), max_outer=6, max_cg=60)
+    _, te = O.tr_solve(v, O.tr_opts(**kw))
+    _, tf = O.tr_solve(v, O.tr_opts(hessian="difference", **kw))
+    assert len(te) == len(tf) == 6
+    for a, b in zip(te, tf):
+        assert a["F"] == pytest.approx(b["F"], rel=1e-7)
+        assert (a["cg_iters"], a["cg_status"], a["accepted"]) == \
+            (b["cg_iters"], b["cg_status"], b["accepted"])
