@@ -91,6 +91,22 @@ typedef struct trstmi_options {
   void *stream;         /* cudaStream_t to issue on, or NULL */
   int32_t device;       /* CUDA device ordinal (default 0) */
   int32_t reserved0;
+  /* Device memory (default NULL: cudaMalloc / cudaFree).  With dev_alloc
+     set, every device allocation of a handle made from these options --
+     the instance's state block and the temporary buffers of trstmi_score
+     and trstmi_profile_score, the batch's arena, launch plan and candidate
+     scratch, the server's control tables, arena, launch plan and candidate
+     scratch -- is dev_alloc(bytes, alloc_ctx), released by
+     dev_free(ptr, alloc_ctx) (both must be set).  The library calls them on
+     the thread that calls it (for a server: trstmi_server_create and
+     trstmi_server_destroy), with the handle's device current; dev_alloc
+     returns memory of that device, 256-byte aligned, or NULL, which the
+     call reports as TRSTMI_ENOMEM.  Memory is released only after the
+     handle's stream has finished with it.  A caching allocator (PyTorch's,
+     from the Python binding) can serve both. */
+  void *(*dev_alloc)(size_t bytes, void *alloc_ctx);
+  void (*dev_free)(void *ptr, void *alloc_ctx);
+  void *alloc_ctx;
 } trstmi_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -409,6 +425,22 @@ int trstmi_server_stats(trstmi_server *srv, trstmi_server_stats_t *out);
 int trstmi_score(trstmi_handle h, uint32_t t, uint32_t c0, int count, double delta,
                  int precision, double *mu2);
 
+/*
+ * How the last iteration ranked its candidates (Sec. "Introduction": each
+ * candidate's coherence, reduced as mu^2; the best candidate is the argmin).
+ * mu2 (nullable, host, K doubles): the ranking scores of the last iteration
+ * -- the binary64 mu^2 (TRSTMI_FP64), the binary32 mu^2 (TRSTMI_FP32), or in
+ * the screen modes the screen's mu^2 (or the binary32 mu^2 of every
+ * candidate when the iteration ranked below screen_min_delta).  Screen modes
+ * only (else TRSTMI_EINVAL when requested): survivors (nullable, topk
+ * indices) -- the topk smallest ranking scores, ties to the lowest index, in
+ * increasing order -- and mu2_survivors (nullable, topk doubles) their
+ * binary32 re-scores, from which the best (ties: lowest index) was taken.
+ * Valid after trstmi_step has run at least one iteration.
+ */
+int trstmi_last_ranking(trstmi_handle h, double *mu2, uint32_t *survivors,
+                        double *mu2_survivors);
+
 /* Candidate c of iteration t as generated on the device in binary64
  * (precision TRSTMI_FP64) or binary32 (TRSTMI_FP32, widened), host out. */
 int trstmi_candidate(trstmi_handle h, uint32_t t, uint32_t c, double delta,
@@ -429,15 +461,20 @@ int trstmi_mu2_frame(int N, int d, const double *phi, int precision, double *mu2
  * run in loops where cudaMalloc / cudaFree would stall on an implicit device
  * synchronisation.  It calls no allocating routine.
  *
- * phi_dev: DEVICE pointer, 2*d*N doubles in the frame layout above, columns
- *          used as given.  mu2_dev: DEVICE pointer to one double, written
- *          with max_{j<k} |G_jk|^2 (certified: binary32 preselection of the
- *          pairs within its rounding-error bound of the max, binary64 over
- *          those, a full binary64 pass if more than 65536 pairs qualify).
+ * phi_dev: DEVICE pointer, 16-byte aligned, 2*d*N finite doubles in the
+ *          frame layout above, columns used as given (they need not have unit
+ *          norm).  mu2_dev: DEVICE pointer to one double, 8-byte aligned,
+ *          written with max_{j<k} |G_jk|^2 (certified: binary32 preselection
+ *          of the pairs within its rounding-error bound of the max -- the
+ *          unit-column bound scaled by the largest squared column norm --,
+ *          binary64 over those, a full binary64 pass if more than 65536 pairs
+ *          qualify or if a squared column norm lies outside [2^-40, 2^40],
+ *          where the binary32 passes could overflow or lose precision).
  * stream:  cudaStream_t to issue on (NULL = the legacy default stream).  The
  *          call only enqueues work; the result is ready when the stream is.
- * Limit:   N * d <= 131072 complex entries, d <= 256; larger sizes return
- *          TRSTMI_ESIZE without touching the device.
+ * Limit:   N * d <= 131072 complex entries; larger products return
+ *          TRSTMI_ESIZE without touching the device.  N < 1, d < 1, d > 256,
+ *          a NULL or misaligned pointer return TRSTMI_EINVAL.
  * Scratch: one static device array of about 1.5 MiB per GPU (the binary32
  *          copy of the frame, the pair list and its counters), held by every
  *          GPU that loads the library until the process exits.  Each call
@@ -547,11 +584,15 @@ int trstmi_lse_frames_device(int N, int d, int count, const double *v_dev, doubl
  * divided by 4 if rho < 1/4 and doubled (up to radius_max) if rho > 3/4 and
  * the step reached it; the step is taken if rho > eta, after which each
  * column of V is divided by its norm (F does not change).  The radius starts
- * at radius0 in every stage.  Hessian products are central differences of
- * the exact gradient along the direction (step fd_step), in binary64
- * throughout, on the GPU (F and its gradient by the smooth-maximum kernels,
- * every vector operation and inner product in device kernels; the host
- * keeps the scalars).
+ * at radius0 in every stage.  The model's B is the Hessian of F at the
+ * iterate, as in the paper's Algorithm (B_k = grad^2 f_k): its products are
+ * formed exactly, by differentiating the gradient along the direction (the
+ * chain rule through the normalisation, the Gram entries and the softmax
+ * weights); hessian = 1 selects central differences of the gradient (step
+ * fd_step) instead, a diagnosis option.  Binary64 throughout, on the GPU
+ * (F, its gradient and the Hessian products by device kernels, every vector
+ * operation and inner product in device kernels; the host keeps the
+ * scalars, or, on the resident path, one CTA runs the whole procedure).
  */
 typedef struct trstmi_tr_options {
   int32_t n_delta;      /* stages, 1..16 */
@@ -569,7 +610,9 @@ typedef struct trstmi_tr_options {
   double radius_max;    /* radius cap (default 1.0), >= radius0 */
   double eta;           /* acceptance threshold on rho (default 1e-4), in [0, 1/4) */
   double gtol;          /* stage ends when |grad F| <= gtol (default 1e-9), >= 0 */
-  double fd_step;       /* Hessian-product difference step (default 1e-6), > 0 */
+  double fd_step;       /* difference step of hessian = 1 (default 1e-6), > 0 */
+  int32_t hessian;      /* 0 (default): exact Hessian products; 1: central differences */
+  int32_t reserved;
 } trstmi_tr_options;
 
 /* One row per trust-region iteration. */

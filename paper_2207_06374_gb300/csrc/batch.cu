@@ -175,6 +175,7 @@ struct trstmi_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   void* block = nullptr;
+  DeviceMemory dmem;   // where block, the plan and the scratch come from
   std::vector<int> N, d;
   std::vector<uint64_t> seed;
   std::vector<SlotDesc> h_slots;
@@ -282,13 +283,13 @@ extern "C" {
 
 void trstmi_batch_destroy(trstmi_batch_handle b) {
   if (!b) return;
-  cudaSetDevice(b->opt.device);
+  DeviceGuard device_guard(b->opt.device);
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   b->plan.destroy();
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
-  if (b->block) cudaFree(b->block);
+  b->dmem.release(b->block);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -308,18 +309,20 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
       !(o.delta_max >= o.delta_min) || !(o.screen_min_delta >= 0))
     return TRSTMI_EINVAL;
   if (screen && (o.topk < 1 || o.topk > 64 || o.topk > o.K)) return TRSTMI_EINVAL;
+  if (!DeviceMemory::valid(o)) return TRSTMI_EINVAL;
   for (int i = 0; i < n; ++i)
     if (N[i] < 2 || d[i] < 1 || d[i] > kMaxD || (long long)N[i] * ((d[i] + 1) / 2) >= (1ll << 32))
       return TRSTMI_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return TRSTMI_ECUDA;
   if (o.device < 0 || o.device >= ndev) return TRSTMI_EINVAL;
-  if (cudaSetDevice(o.device) != cudaSuccess || init_kernel_attributes() != cudaSuccess)
-    return TRSTMI_ECUDA;
+  DeviceGuard device_guard(o.device);
+  if (!device_guard.ok() || init_kernel_attributes() != cudaSuccess) return TRSTMI_ECUDA;
 
   trstmi_batch* b = new (std::nothrow) trstmi_batch();
   if (!b) return TRSTMI_ENOMEM;
   b->n = n; b->opt = o; b->f64 = (o.precision == TRSTMI_FP64); b->screen = screen;
+  b->dmem = DeviceMemory(o);
   b->N.assign(N, N + n); b->d.assign(d, d + n); b->seed.assign(seeds, seeds + n);
   if (cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess) {
     delete b;
@@ -368,7 +371,8 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
       if (N[i] >= BatchPlan::kPlanesMinN && need <= kBatchPlanesMax)
         planes_bytes = std::max(planes_bytes, need);
     }
-  if (cudaMalloc(&b->block, off) != cudaSuccess ||
+  b->plan.dmem = b->dmem;
+  if (b->dmem.allocate(&b->block, off) != cudaSuccess ||
       b->plan.init(n, screen ? (long long)n * o.K : 0, b->num_sms, planes_bytes) != TRSTMI_OK) {
     cudaGetLastError();
     trstmi_batch_destroy(b);
@@ -465,7 +469,8 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
 int trstmi_batch_step(trstmi_batch_handle b, int iters, trstmi_step_info* info) {
   trstmi::TraceRange trace_range("trstmi_batch_step");
   if (!b || iters < 0) return TRSTMI_EINVAL;
-  BTRY(cudaSetDevice(b->opt.device));
+  DeviceGuard device_guard(b->opt.device);
+  if (!device_guard.ok()) return TRSTMI_ECUDA;
   cudaStream_t s = b->stream;
   const int full = iters / kBatchGraphChunk, rem = iters % kBatchGraphChunk;
   cudaGraphExec_t gf = nullptr, gr = nullptr;
@@ -511,7 +516,8 @@ int trstmi_batch_step(trstmi_batch_handle b, int iters, trstmi_step_info* info) 
 
 int trstmi_batch_mu(trstmi_batch_handle b, double* mu, int32_t* iters) {
   if (!b || !mu) return TRSTMI_EINVAL;
-  BTRY(cudaSetDevice(b->opt.device));
+  DeviceGuard device_guard(b->opt.device);
+  if (!device_guard.ok()) return TRSTMI_ECUDA;
   std::vector<DevState> st;
   int rc = read_states(b, &st);
   if (rc) return rc;
@@ -524,7 +530,8 @@ int trstmi_batch_mu(trstmi_batch_handle b, double* mu, int32_t* iters) {
 
 int trstmi_batch_get_phi(trstmi_batch_handle b, int i, double* out) {
   if (!b || !out || i < 0 || i >= b->n) return TRSTMI_EINVAL;
-  BTRY(cudaSetDevice(b->opt.device));
+  DeviceGuard device_guard(b->opt.device);
+  if (!device_guard.ok()) return TRSTMI_ECUDA;
   const SlotDesc& sd = b->h_slots[i];
   const void* p64 = b->f64 ? sd.phi : sd.phi_other;
   BTRY(cudaMemcpyAsync(out, p64, (size_t)sd.N * sd.d * sizeof(double2), cudaMemcpyDeviceToHost,
@@ -536,7 +543,8 @@ int trstmi_batch_get_phi(trstmi_batch_handle b, int i, double* out) {
 int trstmi_batch_get_trace(trstmi_batch_handle b, int i, trstmi_trace_row* rows, int n,
                            int* n_out) {
   if (!b || i < 0 || i >= b->n || n < 0 || !n_out || (n > 0 && !rows)) return TRSTMI_EINVAL;
-  BTRY(cudaSetDevice(b->opt.device));
+  DeviceGuard device_guard(b->opt.device);
+  if (!device_guard.ok()) return TRSTMI_ECUDA;
   DevState s;
   BTRY(cudaMemcpyAsync(&s, b->h_slots[i].st, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream));
   const uint32_t cap = (uint32_t)b->opt.trace_cap;
@@ -557,10 +565,11 @@ int trstmi_batch_get_trace(trstmi_batch_handle b, int i, trstmi_trace_row* rows,
 int trstmi_batch_profile_score(trstmi_batch_handle b, int launches, size_t flush_bytes,
                                double* avg_ms) {
   if (!b || launches < 1 || !avg_ms) return TRSTMI_EINVAL;
-  BTRY(cudaSetDevice(b->opt.device));
+  DeviceGuard device_guard(b->opt.device);
+  if (!device_guard.ok()) return TRSTMI_ECUDA;
   cudaStream_t s = b->stream;
   void* flush = nullptr;
-  if (flush_bytes) BTRY(cudaMalloc(&flush, flush_bytes));
+  if (flush_bytes) BTRY(b->dmem.allocate(&flush, flush_bytes));
   double total = 0.0;
   int rc = TRSTMI_OK;
   for (int l = 0; l < launches && rc == TRSTMI_OK; ++l) {
@@ -582,7 +591,7 @@ int trstmi_batch_profile_score(trstmi_batch_handle b, int launches, size_t flush
         cudaEventElapsedTime(&ms, b->ev0, b->ev1) != cudaSuccess) { rc = TRSTMI_ECUDA; break; }
     total += ms;
   }
-  if (flush) cudaFree(flush);
+  b->dmem.release(flush);
   if (rc == TRSTMI_OK) *avg_ms = total / launches;
   return rc;
 }

@@ -47,12 +47,16 @@ int record_cuda_error(cudaError_t e, const char* what, int line) {
     if (_e != cudaSuccess) return record_cuda_error(_e, #expr, __LINE__); \
   } while (0)
 
+// Validates a device ordinal and prepares it (kernel attributes, once per
+// device); the device must already be current (a DeviceGuard holds it).
 int ensure_device(int device, int* num_sms) {
   int n = 0;
   TRY_CUDA(cudaGetDeviceCount(&n));
   if (n <= 0) return TRSTMI_ECUDA;
   if (device < 0 || device >= n || device >= 64) return TRSTMI_EINVAL;
-  TRY_CUDA(cudaSetDevice(device));
+  int cur = -1;
+  TRY_CUDA(cudaGetDevice(&cur));
+  if (cur != device) return TRSTMI_EINVAL;
   {
     std::lock_guard<std::mutex> g(g_attr_mu);
     if (!g_attr_done[device]) {
@@ -63,6 +67,25 @@ int ensure_device(int device, int* num_sms) {
   TRY_CUDA(cudaDeviceGetAttribute(num_sms, cudaDevAttrMultiProcessorCount, device));
   return TRSTMI_OK;
 }
+
+// The calling thread's current device (the one the stateless entry points use).
+int caller_device(int* dev) {
+  TRY_CUDA(cudaGetDevice(dev));
+  return TRSTMI_OK;
+}
+
+// Holds `dev` current for the rest of the enclosing scope (the caller's device
+// is restored on return); a device that cannot be made current is an error.
+#define USE_DEVICE(dev)                                                         \
+  DeviceGuard device_guard_(dev);                                               \
+  if (!device_guard_.ok()) {                                                    \
+    int n_ = 0;                                                                 \
+    if (cudaGetDeviceCount(&n_) != cudaSuccess || n_ < 1) {                     \
+      cudaGetLastError();                                                       \
+      return TRSTMI_ECUDA;                                                      \
+    }                                                                           \
+    return TRSTMI_EINVAL;                                                       \
+  }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -77,6 +100,7 @@ struct trstmi_instance {
   bool own_stream = false;
   void* block = nullptr;
   size_t block_bytes = 0;
+  DeviceMemory dmem;   // where block and the temporary buffers come from
   // carved from block
   DevState* st = nullptr;
   double2* phi64 = nullptr;
@@ -347,6 +371,7 @@ int validate_options(int N, int d, const trstmi_options& o) {
     return TRSTMI_EINVAL;
   if (!(o.delta_min >= 0) || !(o.delta_max >= o.delta_min)) return TRSTMI_EINVAL;
   if (!(o.screen_min_delta >= 0)) return TRSTMI_EINVAL;
+  if (!DeviceMemory::valid(o)) return TRSTMI_EINVAL;
   return TRSTMI_OK;
 }
 
@@ -393,12 +418,12 @@ const char* trstmi_strerror(int s) {
 
 void trstmi_destroy(trstmi_handle h) {
   if (!h) return;
-  cudaSetDevice(h->opt.device);
+  DeviceGuard device_guard(h->opt.device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
-  if (h->block) cudaFree(h->block);
+  h->dmem.release(h->block);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -411,14 +436,16 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   if (opt) o = *opt; else trstmi_default_options(&o);
   if (!is_screen(o.precision)) o.topk = std::max(1, std::min(o.topk, o.K));
   int num_sms = 0;
-  int rc = ensure_device(o.device, &num_sms);
+  int rc = validate_options(N, d, o);
   if (rc) return rc;
-  rc = validate_options(N, d, o);
+  USE_DEVICE(o.device);
+  rc = ensure_device(o.device, &num_sms);
   if (rc) return rc;
 
   trstmi_instance* h = new (std::nothrow) trstmi_instance();
   if (!h) return TRSTMI_ENOMEM;
   h->N = N; h->d = d; h->seed = seed; h->opt = o; h->num_sms = num_sms;
+  h->dmem = DeviceMemory(o);
   if (o.stream) {
     h->stream = (cudaStream_t)o.stream;
   } else {
@@ -457,7 +484,7 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   const size_t o_ptop = is_screen(o.precision) ? take((size_t)k * 2 * nd * sizeof(float))
                                                : (size_t)-1;
   h->block_bytes = off;
-  if (cudaMalloc(&h->block, off) != cudaSuccess) {
+  if (h->dmem.allocate(&h->block, off) != cudaSuccess) {
     cudaGetLastError();
     trstmi_destroy(h);
     return TRSTMI_ENOMEM;
@@ -519,7 +546,7 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
 int trstmi_step(trstmi_handle h, int iters, trstmi_step_info* info) {
   trstmi::TraceRange trace_range("trstmi_step");
   if (!h || iters < 0) return TRSTMI_EINVAL;
-  TRY_CUDA(cudaSetDevice(h->opt.device));
+  USE_DEVICE(h->opt.device);
   cudaStream_t s = h->stream;
   // graphs are captured (host work only) before the timed span starts
   const int full = iters / kGraphChunk, rem = iters % kGraphChunk;
@@ -564,7 +591,7 @@ int trstmi_shard_score_bytes(trstmi_handle h, size_t* bytes) {
 int trstmi_shard_score(trstmi_handle h, int c_lo, int c_hi, void* scores) {
   trstmi::TraceRange trace_range("trstmi_shard_score");
   if (!h || !scores || c_lo < 0 || c_hi < c_lo || c_hi > h->opt.K) return TRSTMI_EINVAL;
-  TRY_CUDA(cudaSetDevice(h->opt.device));
+  USE_DEVICE(h->opt.device);
   cudaStream_t s = h->stream;
   k_set_stop<<<1, 1, 0, s>>>(h->st, 1u);
   TRY_CUDA(cudaGetLastError());
@@ -582,7 +609,7 @@ int trstmi_shard_score(trstmi_handle h, int c_lo, int c_hi, void* scores) {
 int trstmi_shard_finish(trstmi_handle h, const void* scores, trstmi_step_info* info) {
   trstmi::TraceRange trace_range("trstmi_shard_finish");
   if (!h || !scores) return TRSTMI_EINVAL;
-  TRY_CUDA(cudaSetDevice(h->opt.device));
+  USE_DEVICE(h->opt.device);
   cudaStream_t s = h->stream;
   const bool f64 = h->opt.precision == TRSTMI_FP64;
   size_t bytes = 0;
@@ -614,7 +641,7 @@ int trstmi_shard_finish(trstmi_handle h, const void* scores, trstmi_step_info* i
 
 int trstmi_coherence(trstmi_handle h, double* mu, double* welch) {
   if (!h || !mu) return TRSTMI_EINVAL;
-  TRY_CUDA(cudaSetDevice(h->opt.device));
+  USE_DEVICE(h->opt.device);
   cudaStream_t s = h->stream;
   TRY_CUDA(cudaMemsetAsync(h->cert32, 0, 2 * sizeof(unsigned int) + sizeof(unsigned long long), s));
   TRY_CUDA(cudaMemsetAsync(h->misc, 0, 2 * sizeof(uint32_t), s));
@@ -633,7 +660,7 @@ int trstmi_coherence(trstmi_handle h, double* mu, double* welch) {
 
 int trstmi_get_phi(trstmi_handle h, double* out) {
   if (!h || !out) return TRSTMI_EINVAL;
-  TRY_CUDA(cudaSetDevice(h->opt.device));
+  USE_DEVICE(h->opt.device);
   TRY_CUDA(cudaMemcpyAsync(out, h->phi64, (size_t)h->N * h->d * sizeof(double2),
                            cudaMemcpyDeviceToHost, h->stream));
   TRY_CUDA(cudaStreamSynchronize(h->stream));
@@ -642,7 +669,7 @@ int trstmi_get_phi(trstmi_handle h, double* out) {
 
 int trstmi_set_phi(trstmi_handle h, const double* in) {
   if (!h || !in) return TRSTMI_EINVAL;
-  TRY_CUDA(cudaSetDevice(h->opt.device));
+  USE_DEVICE(h->opt.device);
   cudaStream_t s = h->stream;
   const size_t bytes = (size_t)h->N * h->d * sizeof(double2);
   // reject zero columns on the host before touching the device state
@@ -677,7 +704,7 @@ int trstmi_get_state(trstmi_handle h, void* blob, size_t* size) {
   const size_t need = sizeof(BlobHeader) + nd * sizeof(double2) + nd * sizeof(float2);
   if (!blob) { *size = need; return TRSTMI_OK; }
   if (*size < need) { *size = need; return TRSTMI_EINVAL; }
-  TRY_CUDA(cudaSetDevice(h->opt.device));
+  USE_DEVICE(h->opt.device);
   BlobHeader hd;
   std::memset(&hd, 0, sizeof(hd));
   hd.magic = kBlobMagic; hd.version = kBlobVersion; hd.N = h->N; hd.d = h->d; hd.seed = h->seed;
@@ -703,7 +730,7 @@ int trstmi_set_state(trstmi_handle h, const void* blob, size_t size) {
       hd.seed != h->seed || hd.precision != h->opt.precision || hd.K != h->opt.K ||
       size < sizeof(BlobHeader) + nd * (sizeof(double2) + sizeof(float2)))
     return TRSTMI_EINVAL;
-  TRY_CUDA(cudaSetDevice(h->opt.device));
+  USE_DEVICE(h->opt.device);
   DevState st = hd.st;
   st.trace_cap = (uint32_t)h->opt.trace_cap;
   const char* p = (const char*)blob;
@@ -718,6 +745,7 @@ int trstmi_set_state(trstmi_handle h, const void* blob, size_t size) {
 
 int trstmi_get_trace(trstmi_handle h, trstmi_trace_row* rows, int n, int* n_out) {
   if (!h || n < 0 || !n_out || (n > 0 && !rows)) return TRSTMI_EINVAL;
+  USE_DEVICE(h->opt.device);
   static_assert(sizeof(trstmi_trace_row) == sizeof(TraceRowDev), "trace row layout");
   DevState s;
   int rc = read_state(h, &s);
@@ -743,11 +771,11 @@ int trstmi_score(trstmi_handle h, uint32_t t, uint32_t c0, int count, double del
                  int precision, double* mu2) {
   if (!h || count < 0 || (count > 0 && !mu2) || t < 1 || !(delta >= 0)) return TRSTMI_EINVAL;
   if (count == 0) return TRSTMI_OK;
-  TRY_CUDA(cudaSetDevice(h->opt.device));
+  USE_DEVICE(h->opt.device);
   cudaStream_t s = h->stream;
   void* tmp = nullptr;
   const size_t bytes = (size_t)count * sizeof(unsigned long long);
-  TRY_CUDA(cudaMalloc(&tmp, bytes));
+  TRY_CUDA(h->dmem.allocate(&tmp, bytes));
   int rc = TRSTMI_OK;
   std::vector<double> outv(count);
   do {
@@ -797,16 +825,61 @@ int trstmi_score(trstmi_handle h, uint32_t t, uint32_t c0, int count, double del
       rc = TRSTMI_EINVAL;
     }
   } while (0);
-  cudaFree(tmp);
+  cudaStreamSynchronize(s);   // the buffer is released only once the stream is done with it
+  h->dmem.release(tmp);
   if (rc == TRSTMI_OK) std::memcpy(mu2, outv.data(), sizeof(double) * count);
   return rc;
+}
+
+int trstmi_last_ranking(trstmi_handle h, double* mu2, uint32_t* survivors,
+                        double* mu2_survivors) {
+  if (!h) return TRSTMI_EINVAL;
+  USE_DEVICE(h->opt.device);
+  const int K = h->opt.K, k = h->opt.topk;
+  const bool f64 = h->opt.precision == TRSTMI_FP64;
+  const bool screen = is_screen(h->opt.precision);
+  if ((survivors || mu2_survivors) && !screen) return TRSTMI_EINVAL;
+  cudaStream_t s = h->stream;
+  std::vector<unsigned long long> b64(f64 ? K : 0);
+  std::vector<unsigned int> b32(f64 ? 0 : K), t32(screen ? k : 0);
+  std::vector<uint32_t> idx(screen ? k : 0);
+  if (mu2) {
+    if (f64) TRY_CUDA(cudaMemcpyAsync(b64.data(), h->mu2_k64, K * sizeof(unsigned long long),
+                                      cudaMemcpyDeviceToHost, s));
+    else TRY_CUDA(cudaMemcpyAsync(b32.data(), h->mu2_k32, K * sizeof(unsigned int),
+                                  cudaMemcpyDeviceToHost, s));
+  }
+  if (screen) {
+    TRY_CUDA(cudaMemcpyAsync(idx.data(), h->topk, k * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaMemcpyAsync(t32.data(), h->mu2_top, k * sizeof(unsigned int),
+                             cudaMemcpyDeviceToHost, s));
+  }
+  TRY_CUDA(cudaStreamSynchronize(s));
+  for (int c = 0; mu2 && c < K; ++c) {
+    if (f64) {
+      std::memcpy(&mu2[c], &b64[c], sizeof(double));
+    } else {
+      float f;
+      std::memcpy(&f, &b32[c], sizeof(float));
+      mu2[c] = (double)f;
+    }
+  }
+  for (int q = 0; q < k && screen; ++q) {
+    if (survivors) survivors[q] = idx[q];
+    if (mu2_survivors) {
+      float f;
+      std::memcpy(&f, &t32[q], sizeof(float));
+      mu2_survivors[q] = (double)f;
+    }
+  }
+  return TRSTMI_OK;
 }
 
 int trstmi_candidate(trstmi_handle h, uint32_t t, uint32_t c, double delta, int precision,
                      double* out) {
   if (!h || !out || t < 1 || !(delta >= 0)) return TRSTMI_EINVAL;
   if (precision != TRSTMI_FP64 && precision != TRSTMI_FP32) return TRSTMI_EINVAL;
-  TRY_CUDA(cudaSetDevice(h->opt.device));
+  USE_DEVICE(h->opt.device);
   cudaStream_t s = h->stream;
   TRY_CUDA(launch_gen_candidate(h->N, h->d, h->seed, t, c, delta, precision == TRSTMI_FP64,
                                 h->phi64, h->phi32, h->scratch64, s));
@@ -819,9 +892,9 @@ int trstmi_candidate(trstmi_handle h, uint32_t t, uint32_t c, double delta, int 
 int trstmi_mu2_frame(int N, int d, const double* phi, int precision, double* mu2) {
   if (N < 1 || d < 1 || d > kMaxD || !phi || !mu2) return TRSTMI_EINVAL;
   if (precision != TRSTMI_FP64 && precision != TRSTMI_FP32) return TRSTMI_EINVAL;
-  int num_sms = 0;
-  int rc = ensure_device(0, &num_sms);
-  if (rc) return rc;
+  int num_sms = 0, dev = 0;
+  int rc = caller_device(&dev);
+  if (rc || (rc = ensure_device(dev, &num_sms)) != TRSTMI_OK) return rc;
   const size_t nd = (size_t)N * d;
   void* buf = nullptr;
   const size_t bytes = nd * sizeof(double2) + 256;
@@ -864,11 +937,11 @@ int trstmi_profile_score(trstmi_handle h, int precision, int launches, double de
   if (precision < TRSTMI_FP64 || precision > TRSTMI_TF32_SCREEN) return TRSTMI_EINVAL;
   if (is_screen(precision) && !screen_supported(h->N, h->d, screen_fmt_of(precision, h->d)))
     return TRSTMI_EUNSUPPORTED;
-  TRY_CUDA(cudaSetDevice(h->opt.device));
+  USE_DEVICE(h->opt.device);
   cudaStream_t s = h->stream;
   const int K = h->opt.K;
   void* flush = nullptr;
-  if (flush_bytes) TRY_CUDA(cudaMalloc(&flush, flush_bytes));
+  if (flush_bytes) TRY_CUDA(h->dmem.allocate(&flush, flush_bytes));
   std::vector<cudaEvent_t> ev(2 * launches, nullptr);
   int rc = TRSTMI_OK;
   for (auto& e : ev)
@@ -916,7 +989,8 @@ int trstmi_profile_score(trstmi_handle h, int precision, int launches, double de
     }
   }
   for (auto& e : ev) if (e) cudaEventDestroy(e);
-  if (flush) cudaFree(flush);
+  cudaStreamSynchronize(s);
+  h->dmem.release(flush);
   if (rc == TRSTMI_OK) *avg_ms = total / launches;
   return rc;
 }
@@ -950,7 +1024,7 @@ int trstmi_lse_frames_device(int N, int d, int count, const double* v_dev, doubl
     return TRSTMI_EINVAL;
   if (reinterpret_cast<uintptr_t>(scratch_dev) % 256 != 0) return TRSTMI_EINVAL;
   int dev = 0, num_sms = 0;
-  TRY_CUDA(cudaGetDevice(&dev));
+  if ((rc = caller_device(&dev)) != TRSTMI_OK) return rc;
   if ((rc = ensure_device(dev, &num_sms)) != TRSTMI_OK) return rc;
   TRY_CUDA(launch_lse(N, d, count, v_dev, delta, precision == TRSTMI_FP64, scratch_dev, out_dev,
                       grad_dev, num_sms, static_cast<cudaStream_t>(stream)));
@@ -963,8 +1037,9 @@ int trstmi_lse_frames(int N, int d, int count, const double* v, double delta, in
   int rc = lse_check(N, d, count, delta, precision);
   if (rc) return rc;
   if (!v || !F) return TRSTMI_EINVAL;
-  int num_sms = 0;
-  if ((rc = ensure_device(0, &num_sms)) != TRSTMI_OK) return rc;
+  int num_sms = 0, dev = 0;
+  if ((rc = caller_device(&dev)) != TRSTMI_OK) return rc;
+  if ((rc = ensure_device(dev, &num_sms)) != TRSTMI_OK) return rc;
   const size_t nv = (size_t)count * N * d * sizeof(double2);
   const size_t nscratch = lse_scratch_bytes(N, d, count, precision == TRSTMI_FP64);
   const size_t o_out = align_up(nv, 256), o_grad = align_up(o_out + 2 * sizeof(double) * count, 256);
@@ -995,14 +1070,16 @@ int trstmi_lse_frames(int N, int d, int count, const double* v, double delta, in
 
 namespace {
 int certificates_of(int N, int d, const double* v_dev, double tol, int num_sms,
-                    cudaStream_t s, trstmi_certificates* out) {
+                    cudaStream_t s, trstmi_certificates* out,
+                    const DeviceMemory& dmem = DeviceMemory()) {
   void* scr = nullptr;
-  TRY_CUDA(cudaMalloc(&scr, diag_scratch_bytes(N, d, tol)));
+  TRY_CUDA(dmem.allocate(&scr, diag_scratch_bytes(N, d, tol)));
   unsigned char res[24];
   cudaError_t e = launch_diagnostics(N, d, v_dev, tol, scr, num_sms, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(res, scr, sizeof(res), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(scr);
+  if (e != cudaSuccess) cudaStreamSynchronize(s);
+  dmem.release(scr);
   if (e != cudaSuccess) return record_cuda_error(e, "certificates", __LINE__);
   uint32_t runs = 0, bad = 0;
   double mx = 0, mn = 0;
@@ -1033,9 +1110,9 @@ int trstmi_frame_certificates(int N, int d, const double* phi, double tol,
   trstmi::TraceRange trace_range("trstmi_frame_certificates");
   if (N < 2 || d < 1 || d > kMaxD || !phi || !out || !(tol >= 1e-7 && tol <= 1.0))
     return TRSTMI_EINVAL;
-  int num_sms = 0;
-  int rc = ensure_device(0, &num_sms);
-  if (rc) return rc;
+  int num_sms = 0, dev = 0;
+  int rc = caller_device(&dev);
+  if (rc || (rc = ensure_device(dev, &num_sms)) != TRSTMI_OK) return rc;
   const size_t nv = (size_t)N * d * sizeof(double2);
   void* v = nullptr;
   TRY_CUDA(cudaMalloc(&v, nv));
@@ -1049,9 +1126,9 @@ int trstmi_frame_certificates(int N, int d, const double* phi, double tol,
 int trstmi_instance_certificates(trstmi_handle h, double tol, trstmi_certificates* out) {
   trstmi::TraceRange trace_range("trstmi_instance_certificates");
   if (!h || !out || !(tol >= 1e-7 && tol <= 1.0)) return TRSTMI_EINVAL;
-  TRY_CUDA(cudaSetDevice(h->opt.device));
+  USE_DEVICE(h->opt.device);
   return certificates_of(h->N, h->d, reinterpret_cast<const double*>(h->phi64), tol,
-                         h->num_sms, h->stream, out);
+                         h->num_sms, h->stream, out, h->dmem);
 }
 
 void trstmi_tr_default_options(trstmi_tr_options* o) {
@@ -1077,7 +1154,7 @@ int tr_check(int N, int d, const trstmi_tr_options* o) {
   for (int k = 0; k < o->n_delta; ++k)
     if (!(o->delta[k] > 0.0) || !(o->delta[k] < INFINITY)) return TRSTMI_EINVAL;
   if (!(o->radius0 > 0.0) || !(o->radius_max >= o->radius0) || !(o->eta >= 0.0 && o->eta < 0.25) ||
-      !(o->gtol >= 0.0) || !(o->fd_step > 0.0))
+      !(o->gtol >= 0.0) || !(o->fd_step > 0.0) || (o->hessian != 0 && o->hessian != 1))
     return TRSTMI_EINVAL;
   if ((long long)N * d >= (1ll << 28)) return TRSTMI_ESIZE;
   return TRSTMI_OK;
@@ -1086,16 +1163,18 @@ int tr_check(int N, int d, const trstmi_tr_options* o) {
 
 namespace {
 int tr_solve_on(int device, int N, int d, double* phi, const trstmi_tr_options* o,
-                trstmi_tr_row* trace, int cap, int* n_rows) {
+                trstmi_tr_row* trace, int cap, int* n_rows,
+                const DeviceMemory& dmem = DeviceMemory()) {
   int rc = tr_check(N, d, o);
   if (rc) return rc;
   if (!phi || cap < 0) return TRSTMI_EINVAL;
   int num_sms = 0;
+  USE_DEVICE(device);
   if ((rc = ensure_device(device, &num_sms)) != TRSTMI_OK) return rc;
   const size_t nv = (size_t)N * d * sizeof(double2);
   const size_t o_scr = align_up(nv, 256);
   void* buf = nullptr;
-  TRY_CUDA(cudaMalloc(&buf, o_scr + tr_device_bytes(N, d, 1, cap)));
+  TRY_CUDA(dmem.allocate(&buf, o_scr + tr_device_bytes(N, d, 1, cap, o->hessian)));
   char* b = static_cast<char*>(buf);
   cudaError_t e = cudaMemcpy(b, phi, nv, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
@@ -1107,7 +1186,8 @@ int tr_solve_on(int device, int N, int d, double* phi, const trstmi_tr_options* 
   } else {
     rc = record_cuda_error(e, "trust-region frame copy", __LINE__);
   }
-  cudaFree(buf);
+  cudaStreamSynchronize(0);
+  dmem.release(buf);
   return rc;
 }
 }  // namespace
@@ -1115,7 +1195,9 @@ int tr_solve_on(int device, int N, int d, double* phi, const trstmi_tr_options* 
 int trstmi_tr_solve(int N, int d, double* phi, const trstmi_tr_options* o, trstmi_tr_row* trace,
                     int cap, int* n_rows) {
   trstmi::TraceRange trace_range("trstmi_tr_solve");
-  return tr_solve_on(0, N, d, phi, o, trace, cap, n_rows);
+  int dev = 0;
+  const int rc = caller_device(&dev);
+  return rc ? rc : tr_solve_on(dev, N, d, phi, o, trace, cap, n_rows);
 }
 
 int trstmi_tr_multistart(int N, int d, uint64_t seed0, int L, const trstmi_tr_options* o,
@@ -1128,13 +1210,14 @@ int trstmi_tr_multistart(int N, int d, uint64_t seed0, int L, const trstmi_tr_op
   if (!out || cap < 0) return TRSTMI_EINVAL;
   if (L <= 0) L = 2 * d * d;
   const int B = batch_cap > 0 ? std::min(batch_cap, L) : L;
-  int num_sms = 0;
-  if ((rc = ensure_device(0, &num_sms)) != TRSTMI_OK) return rc;
+  int num_sms = 0, dev = 0;
+  if ((rc = caller_device(&dev)) != TRSTMI_OK) return rc;
+  if ((rc = ensure_device(dev, &num_sms)) != TRSTMI_OK) return rc;
   const size_t nv = (size_t)N * d * sizeof(double2);
   const size_t o_f32 = align_up(nv * B, 256);
   const size_t o_scr = o_f32 + align_up(nv / 2, 256);
   void* buf = nullptr;
-  TRY_CUDA(cudaMalloc(&buf, o_scr + tr_device_bytes(N, d, B, 0)));
+  TRY_CUDA(cudaMalloc(&buf, o_scr + tr_device_bytes(N, d, B, 0, o->hessian)));
   char* b = static_cast<char*>(buf);
   std::vector<double> mu(L);
   std::vector<TrFrameLog> logs(B);
@@ -1177,7 +1260,7 @@ int trstmi_tr_multistart(int N, int d, uint64_t seed0, int L, const trstmi_tr_op
   if (trace || n_rows) {
     // the winning trial alone again: the same trajectory, so the same rows
     void* one = nullptr;
-    TRY_CUDA(cudaMalloc(&one, align_up(nv, 256) + align_up(nv / 2, 256) + tr_device_bytes(N, d, 1, cap)));
+    TRY_CUDA(cudaMalloc(&one, align_up(nv, 256) + align_up(nv / 2, 256) + tr_device_bytes(N, d, 1, cap, o->hessian)));
     char* c = static_cast<char*>(one);
     cudaError_t e = launch_init_frame(N, d, out->best_seed, reinterpret_cast<double2*>(c),
                                       reinterpret_cast<float2*>(c + align_up(nv, 256)), nullptr, 0);
@@ -1199,7 +1282,8 @@ int trstmi_instance_tr_solve(trstmi_handle h, const trstmi_tr_options* o, trstmi
   std::vector<double> phi(2 * (size_t)h->N * h->d);
   int rc = trstmi_get_phi(h, phi.data());
   if (rc) return rc;
-  if ((rc = tr_solve_on(h->opt.device, h->N, h->d, phi.data(), o, trace, cap, n_rows)) !=
+  if ((rc = tr_solve_on(h->opt.device, h->N, h->d, phi.data(), o, trace, cap, n_rows,
+                        h->dmem)) !=
       TRSTMI_OK)
     return rc;
   return trstmi_set_phi(h, phi.data());
@@ -1209,7 +1293,7 @@ int trstmi_screen_wait_test(trstmi_handle h, int precision, double wait_limit_ms
   if (!h || !is_screen_precision(precision)) return TRSTMI_EINVAL;
   if (!(wait_limit_ms > 0.0 && wait_limit_ms <= 2000.0)) return TRSTMI_EINVAL;
   if (!screen_supported(h->N, h->d, screen_fmt_of(precision, h->d))) return TRSTMI_EUNSUPPORTED;
-  TRY_CUDA(cudaSetDevice(h->opt.device));
+  USE_DEVICE(h->opt.device);
   cudaStream_t s = h->stream;
   const int count = std::min(h->opt.K, 8);
   TRY_CUDA(cudaMemsetAsync(&h->misc[1], 0, sizeof(uint32_t), s));

@@ -8,6 +8,58 @@
 
 namespace trstmi {
 
+// Makes a device current for the guard's lifetime and restores the calling
+// thread's current device when the guard goes out of scope, so an entry
+// point never leaves its caller bound to another GPU.
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev_) != cudaSuccess) { cudaGetLastError(); prev_ = -1; }
+    if (prev_ == device) { ok_ = true; return; }
+    ok_ = cudaSetDevice(device) == cudaSuccess;
+    if (!ok_) cudaGetLastError();
+    restore_ = ok_ && prev_ >= 0;
+  }
+  ~DeviceGuard() {
+    if (restore_) cudaSetDevice(prev_);
+  }
+  bool ok() const { return ok_; }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+
+ private:
+  int prev_ = -1;
+  bool ok_ = false, restore_ = false;
+};
+
+// Device memory of one handle: the caller's allocator when its options carry
+// one (trstmi_options::dev_alloc / dev_free), cudaMalloc / cudaFree otherwise.
+struct DeviceMemory {
+  void* (*alloc_fn)(size_t, void*) = nullptr;
+  void (*free_fn)(void*, void*) = nullptr;
+  void* ctx = nullptr;
+  DeviceMemory() = default;
+  explicit DeviceMemory(const trstmi_options& o)
+      : alloc_fn(o.dev_alloc), free_fn(o.dev_free), ctx(o.alloc_ctx) {}
+  // both callbacks or neither
+  static bool valid(const trstmi_options& o) { return (o.dev_alloc == nullptr) == (o.dev_free == nullptr); }
+  // cudaErrorMemoryAllocation when the callback returns NULL or memory that
+  // is not 256-byte aligned (that memory is handed back)
+  cudaError_t allocate(void** p, size_t bytes) const {
+    if (!alloc_fn) return cudaMalloc(p, bytes);
+    *p = alloc_fn(bytes, ctx);
+    if (*p && reinterpret_cast<uintptr_t>(*p) % 256 != 0) {
+      free_fn(*p, ctx);
+      *p = nullptr;
+    }
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
+  void release(void* p) const {
+    if (!p) return;
+    if (alloc_fn) free_fn(p, ctx); else cudaFree(p);
+  }
+};
+
 // Operand format of the tensor-core screen: bf16 / fp16 / tf32 for d <= 32,
 // and the wide bf16 / fp16 layouts (two 128-byte atoms per column) for
 // 32 < d <= 64.
@@ -65,7 +117,18 @@ struct PairFilter {
   uint32_t* npairs;
   uint32_t cap;
   uint32_t* overflow;
+  // nullable: binary64 bits of a factor the margin is multiplied by (the
+  // largest squared column norm of a frame whose columns are not unit)
+  const unsigned long long* scale_bits;
 };
+
+// Lower end of the kept range of |G|: sqrt(binary32 max) - margin (scaled).
+__device__ __forceinline__ float filter_lo(const PairFilter& f) {
+  const float ref = sqrtf(__uint_as_float(*f.mu2_ref));
+  float margin = f.margin;
+  if (f.scale_bits) margin = (float)((double)margin * __longlong_as_double((long long)*f.scale_bits));
+  return fmaxf(ref - margin, 0.0f);
+}
 
 // mu^2 per slot: max over j<k of |G_jk|^2, atomically maxed into out[slot]
 // (unsigned int bits for binary32, unsigned long long bits for binary64).
@@ -158,7 +221,7 @@ struct TrFrameLog {
   double mu2;
   int hv_products;
 };
-size_t tr_device_bytes(int N, int d, int L, int trace_cap);
+size_t tr_device_bytes(int N, int d, int L, int trace_cap, int hessian);
 int tr_solve_device(int N, int d, int L, double* v_dev, const trstmi_tr_options& o,
                     void* scratch, int num_sms, cudaStream_t s, TrFrameLog* logs);
 
@@ -301,6 +364,7 @@ struct BatchPlan {
   void* planes = nullptr;
   size_t planes_bytes = 0;
   std::vector<SlotDesc> large;
+  DeviceMemory dmem;      // where mem and planes come from (set before init)
 
   // planes_bytes: the scratch for large instances (0: none)
   int init(int capacity_slots, long long capacity_items, int num_sms, size_t planes_bytes = 0);

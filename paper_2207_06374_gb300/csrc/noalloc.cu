@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 
@@ -30,8 +31,16 @@ struct NoAllocScratch {
   uint2 pairs[kNoAllocPairCap];
   unsigned int mu2_32[2];      // binary32 max, and the filter pass's own max
   uint32_t npairs;
-  uint32_t overflow;
+  uint32_t overflow;           // also set when the binary32 passes cannot be trusted
+  unsigned long long norm2_max;  // binary64 bits of the largest squared column norm
 };
+
+// Range of the largest squared column norm M in which the binary32 passes
+// are used: within it no |G_jk|^2 <= M^2 overflows binary32, and the scaled
+// margin (>= 3e-17) dwarfs the absolute error of underflowed products, so
+// every |G| whose binary32 square is subnormal lies inside the kept range.
+// Outside it the full binary64 pass decides alone.
+constexpr double kNoAllocNormLo = 0x1p-40, kNoAllocNormHi = 0x1p40;
 
 __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
@@ -54,11 +63,29 @@ int scratch_for_current_device(NoAllocScratch** out) {
   return TRSTMI_OK;
 }
 
-// Binary32 rounding of the frame into the scratch.
-__global__ void k_round_to_f32(size_t n, const double2* in, float2* out) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
-       e += (size_t)gridDim.x * blockDim.x)
-    out[e] = make_float2((float)in[e].x, (float)in[e].y);
+// Binary32 rounding of the frame into the scratch, one warp per column, and
+// the largest squared column norm (binary64) for the margin of the pair
+// filter.  A column norm outside [kNoAllocNormLo, kNoAllocNormHi] (or not
+// finite) routes the call to the full binary64 pass.
+__global__ void k_round_to_f32(int N, int d, const double2* in, float2* out,
+                               unsigned long long* norm2_max, uint32_t* force_full) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < N; j += warps) {
+    const double2* col = in + (size_t)j * d;
+    float2* o = out + (size_t)j * d;
+    double acc = 0.0;
+    for (int i = lane; i < d; i += 32) {
+      const double2 v = col[i];
+      o[i] = make_float2((float)v.x, (float)v.y);
+      acc = fma(v.x, v.x, fma(v.y, v.y, acc));
+    }
+    for (int m = 16; m > 0; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+    if (lane == 0) {
+      if (!(acc >= kNoAllocNormLo && acc <= kNoAllocNormHi)) *force_full = 1u;
+      if (acc >= 0.0) atomicMax(norm2_max, (unsigned long long)__double_as_longlong(acc));
+    }
+  }
 }
 
 }  // namespace
@@ -69,6 +96,11 @@ using namespace trstmi;
 extern "C" int trstmi_mu2_frame_noalloc(int N, int d, const double* phi_dev, double* mu2_dev,
                                         void* stream) {
   if (N < 1 || d < 1 || d > kMaxD || !phi_dev || !mu2_dev) return TRSTMI_EINVAL;
+  // the frame is read as 16-byte double2 entries, the result updated by
+  // 64-bit atomics
+  if (reinterpret_cast<uintptr_t>(phi_dev) % 16 != 0 ||
+      reinterpret_cast<uintptr_t>(mu2_dev) % 8 != 0)
+    return TRSTMI_EINVAL;
   if ((size_t)N * (size_t)d > kNoAllocMaxEntries) return TRSTMI_ESIZE;
   NoAllocScratch* sc = nullptr;
   int rc = scratch_for_current_device(&sc);
@@ -78,13 +110,21 @@ extern "C" int trstmi_mu2_frame_noalloc(int N, int d, const double* phi_dev, dou
       cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return TRSTMI_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t n = (size_t)N * d;
   // the array keeps the previous call's contents: clear what accumulates
-  if (cudaMemsetAsync(sc->mu2_32, 0, sizeof(sc->mu2_32) + 2 * sizeof(uint32_t), s) != cudaSuccess ||
+  // (the two maxima, the pair count, the overflow flag and the norm maximum
+  // are contiguous)
+  static_assert(offsetof(NoAllocScratch, norm2_max) ==
+                    offsetof(NoAllocScratch, mu2_32) + 2 * sizeof(unsigned int) + 2 * sizeof(uint32_t),
+                "cleared span");
+  if (cudaMemsetAsync(sc->mu2_32, 0,
+                      offsetof(NoAllocScratch, norm2_max) + sizeof(unsigned long long) -
+                          offsetof(NoAllocScratch, mu2_32),
+                      s) != cudaSuccess ||
       cudaMemsetAsync(mu2_dev, 0, sizeof(double), s) != cudaSuccess)
     return TRSTMI_ECUDA;
-  const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
-  k_round_to_f32<<<grid, 256, 0, s>>>(n, reinterpret_cast<const double2*>(phi_dev), sc->frame32);
+  const int grid = std::min((N + 7) / 8, 4096);
+  k_round_to_f32<<<grid, 256, 0, s>>>(N, d, reinterpret_cast<const double2*>(phi_dev),
+                                      sc->frame32, &sc->norm2_max, &sc->overflow);
   if (cudaGetLastError() != cudaSuccess) return TRSTMI_ECUDA;
   // binary32 max, binary32 preselection of the pairs within its error bound
   // of that max, binary64 over those pairs; full binary64 pass on overflow
@@ -93,8 +133,11 @@ extern "C" int trstmi_mu2_frame_noalloc(int N, int d, const double* phi_dev, dou
   src.phi = sc->frame32;
   if (launch_gram_f32(N, d, 1, src, &sc->mu2_32[0], nullptr, num_sms, s) != cudaSuccess)
     return TRSTMI_ECUDA;
+  // the binary32 error of |G_jk| is bounded by the unit-column bound times
+  // |phi_j| |phi_k| <= max_j |phi_j|^2, so the margin is scaled by that
   const float margin = (float)(8.0 * (2.0 * d + 2.0) / 16777216.0);
-  PairFilter pf{&sc->mu2_32[0], margin, sc->pairs, &sc->npairs, kNoAllocPairCap, &sc->overflow};
+  PairFilter pf{&sc->mu2_32[0], margin, sc->pairs, &sc->npairs, kNoAllocPairCap, &sc->overflow,
+                &sc->norm2_max};
   if (launch_gram_f32(N, d, 1, src, &sc->mu2_32[1], &pf, num_sms, s) != cudaSuccess)
     return TRSTMI_ECUDA;
   unsigned long long* out = reinterpret_cast<unsigned long long*>(mu2_dev);

@@ -38,7 +38,7 @@ int BatchPlan::init(int capacity_slots, long long capacity_items, int num_sms_,
   total += up(sizeof(ScreenSlot) * (size_t)cap_slots);
   total += up(sizeof(uint2) * (size_t)std::max<long long>(cap_items, 1));
   total += up(sizeof(unsigned long long) * kCounters);
-  if (cudaMalloc(&mem, total) != cudaSuccess) { cudaGetLastError(); return TRSTMI_ENOMEM; }
+  if (dmem.allocate(&mem, total) != cudaSuccess) { cudaGetLastError(); return TRSTMI_ENOMEM; }
   char* p = (char*)mem;
   for (int pass = 0; pass < kPasses; ++pass)
     for (int w = 0; w < kNumWidths; ++w) {
@@ -49,7 +49,7 @@ int BatchPlan::init(int capacity_slots, long long capacity_items, int num_sms_,
   d_items = (uint2*)p; p += up(sizeof(uint2) * (size_t)std::max<long long>(cap_items, 1));
   d_counters = (unsigned long long*)p;
   planes_bytes = planes_bytes_ / 256 * 256;
-  if (planes_bytes > 0 && cudaMalloc(&planes, planes_bytes) != cudaSuccess) {
+  if (planes_bytes > 0 && dmem.allocate(&planes, planes_bytes) != cudaSuccess) {
     cudaGetLastError();
     planes = nullptr;
     planes_bytes = 0;
@@ -59,8 +59,8 @@ int BatchPlan::init(int capacity_slots, long long capacity_items, int num_sms_,
 }
 
 void BatchPlan::destroy() {
-  if (mem) cudaFree(mem);
-  if (planes) cudaFree(planes);
+  dmem.release(mem);
+  dmem.release(planes);
   mem = nullptr;
   planes = nullptr;
   planes_bytes = 0;

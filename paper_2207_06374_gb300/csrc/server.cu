@@ -184,6 +184,7 @@ struct trstmi_server {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   void* arena_mem = nullptr;
+  DeviceMemory dmem;                  // where the tables, arena and plan come from
   Arena arena;
   DevState* d_states = nullptr;       // max_slots states
   SlotDesc* d_slots = nullptr;        // active slot table
@@ -581,11 +582,11 @@ void trstmi_server_destroy(trstmi_server* sv) {
   sv->stop = true;
   sv->cv_work.notify_all();
   if (sv->worker.joinable()) sv->worker.join();
-  cudaSetDevice(sv->opt.search.device);
+  DeviceGuard device_guard(sv->opt.search.device);
   if (sv->stream) cudaStreamSynchronize(sv->stream);
   sv->plan.destroy();
-  if (sv->arena_mem) cudaFree(sv->arena_mem);
-  if (sv->d_states) cudaFree(sv->d_states);
+  sv->dmem.release(sv->arena_mem);
+  sv->dmem.release(sv->d_states);
   if (sv->own_stream && sv->stream) cudaStreamDestroy(sv->stream);
   delete sv;
 }
@@ -604,14 +605,16 @@ int trstmi_server_create(const trstmi_server_opts* opts, trstmi_server** out) {
     return TRSTMI_EINVAL;
   if (is_screen_prec(so.precision) && (so.topk < 1 || so.topk > 64 || so.topk > so.K))
     return TRSTMI_EINVAL;
+  if (!DeviceMemory::valid(so)) return TRSTMI_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return TRSTMI_ECUDA;
   if (so.device < 0 || so.device >= ndev) return TRSTMI_EINVAL;
-  if (cudaSetDevice(so.device) != cudaSuccess || init_kernel_attributes() != cudaSuccess)
-    return TRSTMI_ECUDA;
+  DeviceGuard device_guard(so.device);
+  if (!device_guard.ok() || init_kernel_attributes() != cudaSuccess) return TRSTMI_ECUDA;
   trstmi_server* sv = new (std::nothrow) trstmi_server();
   if (!sv) return TRSTMI_ENOMEM;
   sv->opt = o;
+  sv->dmem = DeviceMemory(so);
   sv->f64 = so.precision == TRSTMI_FP64;
   sv->screen = is_screen_prec(so.precision);
   if (cudaDeviceGetAttribute(&sv->num_sms, cudaDevAttrMultiProcessorCount, so.device) != cudaSuccess) {
@@ -638,9 +641,11 @@ int trstmi_server_create(const trstmi_server_opts* opts, trstmi_server** out) {
       sv->f64 ? 0 : std::min<size_t>(256ull << 20, o.hbm_budget / 8) / 256 * 256;
   const size_t arena_bytes = o.hbm_budget - planes_bytes;
   char* ctl = nullptr;
-  if (cudaMalloc(&ctl, b_st + b_sl + b_bu + b_er + b_ti + b_tb) != cudaSuccess ||
+  sv->plan.dmem = sv->dmem;
+  if (sv->dmem.allocate(reinterpret_cast<void**>(&ctl), b_st + b_sl + b_bu + b_er + b_ti + b_tb) !=
+          cudaSuccess ||
       cudaMemset(ctl, 0, b_st + b_sl + b_bu + b_er + b_ti + b_tb) != cudaSuccess ||
-      cudaMalloc(&sv->arena_mem, arena_bytes) != cudaSuccess ||
+      sv->dmem.allocate(&sv->arena_mem, arena_bytes) != cudaSuccess ||
       sv->plan.init(o.max_slots, sv->screen ? (long long)o.max_slots * so.K : 0, sv->num_sms,
                     planes_bytes) != TRSTMI_OK) {
     cudaGetLastError();

@@ -306,8 +306,7 @@ __global__ void __launch_bounds__(256, TileCtas<T>::value) k_gram_tile(const Gra
   }
   T thr = T(-1);
   if (a.has_filter) {
-    const float ref = sqrtf(__uint_as_float(*a.filter.mu2_ref));
-    const float lo = fmaxf(ref - a.filter.margin, 0.0f);
+    const float lo = filter_lo(a.filter);
     thr = (T)(lo * lo);
   }
   const long long nitems = (long long)a.nslots * a.ntiles;
@@ -375,8 +374,7 @@ __global__ void __launch_bounds__(256, 3) k_gram_planes(const GramArgs<float> a,
   if (src.st && !src.st->active) return;
   float thr = -1.f;
   if (a.has_filter) {
-    const float ref = sqrtf(__uint_as_float(*a.filter.mu2_ref));
-    const float lo = fmaxf(ref - a.filter.margin, 0.0f);
+    const float lo = filter_lo(a.filter);
     thr = lo * lo;
   }
   const long long nitems = (long long)a.nslots * a.ntiles;
@@ -1093,8 +1091,8 @@ __global__ void __launch_bounds__(256, TileCtas<T>::value) k_batch_score(const S
           pf.npairs = &const_cast<DevState*>(st)->npairs;
           pf.cap = sd.pair_cap;
           pf.overflow = &const_cast<DevState*>(st)->overflow;
-          const float ref = sqrtf(__uint_as_float(sd.cert32[0]));
-          const float lo2 = fmaxf(ref - pf.margin, 0.0f);
+          pf.scale_bits = nullptr;
+          const float lo2 = filter_lo(pf);
           thr = (T)(lo2 * lo2);
           filter = &pf;
         }

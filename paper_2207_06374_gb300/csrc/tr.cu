@@ -13,9 +13,11 @@
 // order).  The host keeps each frame's scalars and runs the algorithms' scalar
 // logic per frame; a frame that is not stepping gets zero coefficients, so its
 // vectors do not change.  Each frame therefore follows exactly the trajectory
-// it follows alone (L = 1).  Hessian products are central differences of the
-// exact gradient (Hessian-free, as in Nocedal and Wright's Newton-CG), all in
-// binary64.
+// it follows alone (L = 1).  The model's B is the Hessian of F at the iterate
+// (the paper's B_k = grad^2 f_k): its products are formed exactly by the
+// chain rule through the column normalisation, the Gram entries and the
+// softmax weights (hessian = 0), or, as a diagnosis option, by central
+// differences of the exact gradient (hessian = 1); all in binary64.
 //
 // Per trust-region iteration (Nocedal and Wright Alg. 4.1): g = grad F; the
 // stage ends when |g| <= gtol; p from CG-Steihaug with eps = min(1/2,
@@ -139,6 +141,184 @@ __global__ void k_copy_frames(long long n, long long total, const int* flag, con
   dst[i] = src[i];
 }
 
+// ---------------------------------------------- exact Hessian products (stack)
+// B u for every frame, by differentiating the gradient of F along u:
+//   phi_k = v_k / r_k,  d phi_k = (u_k - phi_k Re(phi_k^* u_k)) / r_k,
+//   d r_k = Re(phi_k^* u_k),  dG_jk = d phi_j^* phi_k + phi_j^* d phi_k,
+//   dx_jk = 2 Re(conj(G_jk) dG_jk),  w = e / S with e = exp((x - s)/delta),
+//   dw_jk = w_jk (dx_jk - T) / delta, T = sum w dx (the shift s cancels),
+//   dM_jk = dw_jk G_jk + w_jk dG_jk,  g_k = 2 sum_{j != k} M_jk phi_j (M
+//   Hermitian), dg_k = 2 sum_{j != k} (dM_jk phi_j + M_jk d phi_j),
+//   rho_k = Re(phi_k^* g_k),  d rho_k = Re(d phi_k^* g_k + phi_k^* dg_k),
+//   (B u)_k = (dg_k - d phi_k rho_k - phi_k d rho_k) / r_k - grad_k d r_k / r_k
+// with grad_k = (g_k - phi_k rho_k) / r_k.  Per pair the passes keep G, dG,
+// x (then e) and dx; every sum runs in a fixed order.
+
+constexpr int kHvBlocks = 64;       // CTAs per frame of the weight pass
+constexpr int kHvPair = 6;          // doubles per pair: G (2), dG (2), x -> e, dx
+
+// unit columns phi, d phi, r and Re(phi^* u) of every (frame, column)
+__global__ void k_hvx_cols(int N, int d, int L, const double2* x, const double2* u, double2* phi,
+                           double2* dphi, double* r_out, double* pu_out) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= (long long)L * N) return;
+  const double2* xc = x + g * d;
+  const double2* uc = u + g * d;
+  double q = 0.0;
+  for (int i = 0; i < d; ++i) q = fma(xc[i].y, xc[i].y, fma(xc[i].x, xc[i].x, q));
+  const double r = sqrt(q), inv = 1.0 / r;
+  double pu = 0.0;
+  for (int i = 0; i < d; ++i) {
+    const double2 ph = make_double2(xc[i].x * inv, xc[i].y * inv);
+    phi[g * d + i] = ph;
+    pu = fma(ph.y, uc[i].y, fma(ph.x, uc[i].x, pu));
+  }
+  for (int i = 0; i < d; ++i) {
+    const double2 ph = phi[g * d + i];
+    dphi[g * d + i] = make_double2((uc[i].x - ph.x * pu) * inv, (uc[i].y - ph.y * pu) * inv);
+  }
+  r_out[g] = r;
+  pu_out[g] = pu;
+}
+
+// pair (j, k), j = blockIdx.x < k, of frame blockIdx.y: G, dG, x = |G|^2,
+// dx; the frame's max of x (exact, so the order of the atomics is immaterial)
+__global__ void k_hvx_pairs(int N, int d, long long P, const double2* phi, const double2* dphi,
+                            double* pr, unsigned long long* smax_bits) {
+  const int f = blockIdx.y, j = blockIdx.x;
+  const double2* ph = phi + (size_t)f * N * d;
+  const double2* dp = dphi + (size_t)f * N * d;
+  double* out = pr + (size_t)f * P * kHvPair;
+  double hi_x = 0.0;
+  const long long base = (long long)j * N - (long long)j * (j + 1) / 2 - j - 1;
+  for (int k = j + 1 + threadIdx.x; k < N; k += blockDim.x) {
+    double gr = 0.0, gi = 0.0, hr = 0.0, hi = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double2 a = ph[(size_t)j * d + i], c = ph[(size_t)k * d + i];
+      const double2 da = dp[(size_t)j * d + i], dc = dp[(size_t)k * d + i];
+      gr = fma(a.x, c.x, gr); gr = fma(a.y, c.y, gr);
+      gi = fma(a.x, c.y, gi); gi = fma(-a.y, c.x, gi);
+      hr = fma(da.x, c.x, hr); hr = fma(da.y, c.y, hr); hr = fma(a.x, dc.x, hr); hr = fma(a.y, dc.y, hr);
+      hi = fma(da.x, c.y, hi); hi = fma(-da.y, c.x, hi); hi = fma(a.x, dc.y, hi); hi = fma(-a.y, dc.x, hi);
+    }
+    const double x = gr * gr + gi * gi, dx = 2.0 * (gr * hr + gi * hi);
+    double* o = out + (size_t)(base + k) * kHvPair;
+    o[0] = gr; o[1] = gi; o[2] = hr; o[3] = hi; o[4] = x; o[5] = dx;
+    hi_x = fmax(hi_x, x);
+  }
+  for (int m = 16; m > 0; m >>= 1) hi_x = fmax(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, m));
+  if ((threadIdx.x & 31) == 0) atomicMax(smax_bits + f, (unsigned long long)__double_as_longlong(hi_x));
+}
+
+// e = exp((x - s)/delta) in place of x; per CTA the partial sums of e and of
+// e dx (thread-strided, then a fixed tree) into part[(f * kHvBlocks + b) * 2]
+__global__ void __launch_bounds__(256) k_hvx_weights(long long P, const double* deltas,
+                                                     const unsigned long long* smax_bits,
+                                                     double* pr, double* part) {
+  __shared__ double red[2][256];
+  const int f = blockIdx.y, b = blockIdx.x;
+  double* fp = pr + (size_t)f * P * kHvPair;
+  const double s = __longlong_as_double((long long)smax_bits[f]);
+  const double inv_delta = 1.0 / deltas[f];
+  double se = 0.0, sd = 0.0;
+  for (long long q = (long long)b * blockDim.x + threadIdx.x; q < P; q += (long long)kHvBlocks * blockDim.x) {
+    double* o = fp + (size_t)q * kHvPair;
+    const double e = exp((o[4] - s) * inv_delta);
+    o[4] = e;
+    se += e;
+    sd = fma(e, o[5], sd);
+  }
+  red[0][threadIdx.x] = se;
+  red[1][threadIdx.x] = sd;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + st];
+      red[1][threadIdx.x] += red[1][threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[((size_t)f * kHvBlocks + b) * 2] = red[0][0];
+    part[((size_t)f * kHvBlocks + b) * 2 + 1] = red[1][0];
+  }
+}
+
+// per frame: S = sum e and T = (sum e dx) / S over the CTAs, in order
+__global__ void k_hvx_totals(int L, const double* part, double* ST) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= L) return;
+  double S = 0.0, Td = 0.0;
+  for (int b = 0; b < kHvBlocks; ++b) {
+    S += part[((size_t)f * kHvBlocks + b) * 2];
+    Td += part[((size_t)f * kHvBlocks + b) * 2 + 1];
+  }
+  ST[2 * f] = S;
+  ST[2 * f + 1] = Td / S;
+}
+
+// M = w G in place of G, dM = dw G + w dG in place of dG
+__global__ void k_hvx_dm(long long P, int L, const double* deltas, const double* ST, double* pr) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= (long long)L * P) return;
+  const int f = (int)(g / P);
+  double* o = pr + (size_t)g * kHvPair;
+  const double w = o[4] / ST[2 * f];
+  const double dw = w * (o[5] - ST[2 * f + 1]) / deltas[f];
+  const double gr = o[0], gi = o[1];
+  o[2] = fma(dw, gr, w * o[2]);
+  o[3] = fma(dw, gi, w * o[3]);
+  o[0] = w * gr;
+  o[1] = w * gi;
+}
+
+// column k = blockIdx.x of frame blockIdx.y, entry i = threadIdx.x (< d):
+// g_k and dg_k over j ascending, then rho, d rho (fixed tree over the
+// entries) and (B u)_k
+__global__ void __launch_bounds__(256) k_hvx_columns(int N, int d, long long P,
+                                                      const double2* phi, const double2* dphi,
+                                                      const double* r_in, const double* pu_in,
+                                                      const double* pr, double2* out) {
+  __shared__ double red[2][256];
+  const int f = blockIdx.y, k = blockIdx.x, i = threadIdx.x;
+  const double2* ph = phi + (size_t)f * N * d;
+  const double2* dp = dphi + (size_t)f * N * d;
+  const double* fp = pr + (size_t)f * P * kHvPair;
+  double gr = 0.0, gi = 0.0, hr = 0.0, hi = 0.0;
+  if (i < d) {
+    for (int j = 0; j < N; ++j) {
+      if (j == k) continue;
+      const bool lo = j < k;
+      const int a = lo ? j : k, b = lo ? k : j;
+      const double* o = fp + (size_t)((long long)a * N - (long long)a * (a + 1) / 2 + (b - a - 1)) * kHvPair;
+      const double mr = o[0], mi = lo ? o[1] : -o[1];       // M_jk (conjugate for j > k)
+      const double nr = o[2], ni = lo ? o[3] : -o[3];       // dM_jk
+      const double2 pj = ph[(size_t)j * d + i], dj = dp[(size_t)j * d + i];
+      gr = fma(mr, pj.x, gr); gr = fma(-mi, pj.y, gr);
+      gi = fma(mr, pj.y, gi); gi = fma(mi, pj.x, gi);
+      hr = fma(nr, pj.x, hr); hr = fma(-ni, pj.y, hr); hr = fma(mr, dj.x, hr); hr = fma(-mi, dj.y, hr);
+      hi = fma(nr, pj.y, hi); hi = fma(ni, pj.x, hi); hi = fma(mr, dj.y, hi); hi = fma(mi, dj.x, hi);
+    }
+    gr *= 2.0; gi *= 2.0; hr *= 2.0; hi *= 2.0;
+  }
+  const double2 pk = i < d ? ph[(size_t)k * d + i] : make_double2(0.0, 0.0);
+  const double2 dk = i < d ? dp[(size_t)k * d + i] : make_double2(0.0, 0.0);
+  red[0][i] = i < d ? fma(pk.x, gr, pk.y * gi) : 0.0;
+  red[1][i] = i < d ? fma(dk.x, gr, dk.y * gi) + fma(pk.x, hr, pk.y * hi) : 0.0;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (i < st) { red[0][i] += red[0][i + st]; red[1][i] += red[1][i + st]; }
+    __syncthreads();
+  }
+  if (i >= d) return;
+  const double rho = red[0][0], drho = red[1][0];
+  const long long col = (long long)f * N + k;
+  const double inv = 1.0 / r_in[col], pu = pu_in[col];
+  const double gradr = (gr - pk.x * rho) * inv, gradi = (gi - pk.y * rho) * inv;
+  out[(size_t)col * d + i] = make_double2((hr - dk.x * rho - pk.x * drho) * inv - gradr * pu * inv,
+                                          (hi - dk.y * rho - pk.y * drho) * inv - gradi * pu * inv);
+}
+
 struct Stack {
   int N, d, L;
   long long n, total;          // 2dN per frame; L frames
@@ -149,6 +329,12 @@ struct Stack {
   int* flag;
   uint32_t* bad;
   void* lse;
+  // exact Hessian products: per (frame, column) r and Re(phi^* u), per pair
+  // kHvPair doubles, per frame the max x bits, the CTA partials and S, T
+  bool exact = false;
+  double *hv_r = nullptr, *hv_pu = nullptr, *hv_pairs = nullptr, *hv_part = nullptr,
+         *hv_st = nullptr;
+  unsigned long long* hv_smax = nullptr;
   // pinned host mirrors
   double *h_coef, *h_out, *h_dots, *h_deltas;
   int* h_flag;
@@ -225,10 +411,38 @@ struct Stack {
     }
     return e;
   }
+  // o = B u with B the exact Hessian at x (the kernels above; tmp holds phi,
+  // gp holds d phi), smoothing parameters of the round already on the device
+  cudaError_t hv_exact(const double* u, double* o) {
+    const long long P = (long long)N * (N - 1) / 2;
+    double2* phi = reinterpret_cast<double2*>(tmp);
+    double2* dphi = reinterpret_cast<double2*>(gp);
+    k_hvx_cols<<<(unsigned)(((long long)L * N + 127) / 128), 128, 0, s>>>(
+        N, d, L, reinterpret_cast<const double2*>(x), reinterpret_cast<const double2*>(u), phi,
+        dphi, hv_r, hv_pu);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(hv_smax, 0, L * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    k_hvx_pairs<<<dim3(N - 1, L), 128, 0, s>>>(N, d, P, phi, dphi, hv_pairs, hv_smax);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_hvx_weights<<<dim3(kHvBlocks, L), 256, 0, s>>>(P, deltas, hv_smax, hv_pairs, hv_part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_hvx_totals<<<(L + 127) / 128, 128, 0, s>>>(L, hv_part, hv_st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_hvx_dm<<<(unsigned)(((long long)L * P + 255) / 256), 256, 0, s>>>(P, L, deltas, hv_st,
+                                                                          hv_pairs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int threads = 32;
+    while (threads < d) threads *= 2;   // a power of two for the tree, <= 256 (d <= 256)
+    k_hvx_columns<<<dim3(N, L), threads, 0, s>>>(N, d, P, phi, dphi, hv_r, hv_pu, hv_pairs,
+                                                 reinterpret_cast<double2*>(o));
+    return cudaGetLastError();
+  }
   // o = B u, frame by frame: |u| (grad F(x + h u/|u|) - grad F(x - h u/|u|)) / (2h),
   // with the smoothing parameters of the current round already on the device;
   // enqueued only (the coefficients are formed on the device)
   cudaError_t hv(const double* u, double h, double* o) {
+    if (exact) return hv_exact(u, o);
     k_dots<<<L, kDotThreads, 0, s>>>(n, u, u, nullptr, dots);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -367,11 +581,22 @@ cudaError_t cg_steihaug(Stack& T, double h,
 
 }  // namespace
 
-size_t tr_device_bytes(int N, int d, int L, int trace_cap) {
+// bytes of the exact Hessian products' buffers of the stack (L frames)
+size_t hv_exact_bytes(int N, int d, int L) {
+  (void)d;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t P = (size_t)N * (N - 1) / 2;
+  return 2 * up((size_t)L * N * sizeof(double)) + up((size_t)L * P * kHvPair * sizeof(double)) +
+         up((size_t)L * kHvBlocks * 2 * sizeof(double)) + up((size_t)L * 2 * sizeof(double)) +
+         up((size_t)L * sizeof(unsigned long long));
+}
+
+size_t tr_device_bytes(int N, int d, int L, int trace_cap, int hessian) {
   const size_t vec = ((size_t)L * 2 * d * N * sizeof(double) + 255) & ~(size_t)255;
   const size_t small = (((size_t)L * (2 + 5 + 2 * kCoefRing + 1 + 5) * sizeof(double) +
                          (size_t)L * (sizeof(int) + sizeof(uint32_t))) + 255) & ~(size_t)255;
-  const size_t stack = 10 * vec + small + lse_scratch_bytes(N, d, L, true);
+  const size_t stack = 10 * vec + small + lse_scratch_bytes(N, d, L, true) +
+                       (hessian == 0 ? hv_exact_bytes(N, d, L) : 0);
   // the resident path: per frame mu^2 and three ints, then the trace rows
   const size_t resident = (((size_t)L * 20 + 255) & ~(size_t)255) +
                           (size_t)L * std::max(trace_cap, 0) * sizeof(trstmi_tr_row);
@@ -400,6 +625,18 @@ int tr_solve_stack(int N, int d, int L, double* v_dev, const trstmi_tr_options& 
                                (size_t)L * (sizeof(int) + sizeof(uint32_t))) + 255) & ~(size_t)255;
   T.lse = b + 9 * vec + small_bytes;
   T.x = v_dev;
+  T.exact = o.hessian == 0;
+  if (T.exact) {
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t P = (size_t)N * (N - 1) / 2;
+    unsigned char* h = static_cast<unsigned char*>(T.lse) + lse_scratch_bytes(N, d, L, true);
+    T.hv_r = reinterpret_cast<double*>(h); h += up((size_t)L * N * sizeof(double));
+    T.hv_pu = reinterpret_cast<double*>(h); h += up((size_t)L * N * sizeof(double));
+    T.hv_pairs = reinterpret_cast<double*>(h); h += up((size_t)L * P * kHvPair * sizeof(double));
+    T.hv_part = reinterpret_cast<double*>(h); h += up((size_t)L * kHvBlocks * 2 * sizeof(double));
+    T.hv_st = reinterpret_cast<double*>(h); h += up((size_t)L * 2 * sizeof(double));
+    T.hv_smax = reinterpret_cast<unsigned long long*>(h);
+  }
   void* pinned = nullptr;
   const size_t pinned_bytes = (size_t)L * (2 * kCoefRing + 2 + 5 + 1) * sizeof(double) +
                               (size_t)L * (sizeof(int) + sizeof(uint32_t));
@@ -518,29 +755,44 @@ struct ResArgs {
   double* mu2;                     // L: max |G_jk|^2 at the end
   int* hv;                         // L: Hessian products
   int* bad;                        // L: a zero column was met
+  int exact;                       // 1: exact Hessian products, 0: central differences
 };
 
+// Shared memory of one frame: the vectors (2dN doubles each), per column 1/r
+// and rho = Re(phi_k^* g_k), per pair G, the softmax weight w and (exact
+// products) dG, later dM; a reduction buffer of half the CTA; the first
+// column index of every pair.  Central differences need two gradients
+// (gp, gm) instead of the pair arrays dM.
+constexpr int kResRed = kResThreads / 2;
 struct ResSmem {
-  double *x, *xn, *g, *p, *r, *dv, *bd, *gp, *gm, *phi, *rn, *Gre, *Gim, *W, *red;
-  unsigned short *pj, *pk;
+  double *x, *xn, *g, *p, *r, *dv, *bd, *gp, *gm, *phi, *rn, *rho, *Gre, *Gim, *W, *dMre, *dMim,
+      *red;
+  unsigned short* pj;
 };
 
-size_t res_doubles(int N, int d) {
+size_t res_doubles(int N, int d, bool exact) {
   const size_t n = 2 * (size_t)d * N, P = (size_t)N * (N - 1) / 2;
-  return 10 * n + N + 3 * P + kResThreads;
+  return 8 * n + 2 * (size_t)N + 3 * P + kResRed + (exact ? 2 * P : 2 * n);
 }
-size_t res_smem_bytes(int N, int d) {
+size_t res_smem_bytes(int N, int d, bool exact) {
   const size_t P = (size_t)N * (N - 1) / 2;
-  return res_doubles(N, d) * sizeof(double) + ((2 * P * sizeof(unsigned short) + 15) & ~15ull);
+  return res_doubles(N, d, exact) * sizeof(double) + ((P * sizeof(unsigned short) + 15) & ~15ull);
 }
 
-// sum over the CTA of each thread's v, the same order every call; all threads
-// get the result
+// pair q = (j, k), j < k, numbered row by row: k from q and j
+__device__ __forceinline__ int res_pair_k(int q, int j, int N) {
+  return q - (j * N - j * (j + 1) / 2) + j + 1;
+}
+
+// sum over the CTA of each thread's v, the same order every call (thread t
+// and t + kResRed first, then a tree); all threads get the result
 __device__ double res_sum(double v, double* red) {
   __syncthreads();
-  red[threadIdx.x] = v;
+  if (threadIdx.x < kResRed) red[threadIdx.x] = v;
   __syncthreads();
-  for (int st = kResThreads / 2; st > 0; st >>= 1) {
+  if (threadIdx.x >= kResRed) red[threadIdx.x - kResRed] += v;
+  __syncthreads();
+  for (int st = kResRed / 2; st > 0; st >>= 1) {
     if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
     __syncthreads();
   }
@@ -550,9 +802,11 @@ __device__ double res_sum(double v, double* red) {
 }
 __device__ double res_max(double v, double* red) {
   __syncthreads();
-  red[threadIdx.x] = v;
+  if (threadIdx.x < kResRed) red[threadIdx.x] = v;
   __syncthreads();
-  for (int st = kResThreads / 2; st > 0; st >>= 1) {
+  if (threadIdx.x >= kResRed) red[threadIdx.x - kResRed] = fmax(red[threadIdx.x - kResRed], v);
+  __syncthreads();
+  for (int st = kResRed / 2; st > 0; st >>= 1) {
     if (threadIdx.x < st) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + st]);
     __syncthreads();
   }
@@ -607,7 +861,7 @@ __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double d
   // G_jk = sum_i conj(phi_ij) phi_ik and x = |G_jk|^2 for every pair
   double hi = 0.0;
   for (int q = threadIdx.x; q < P; q += kResThreads) {
-    const int j = S.pj[q], k = S.pk[q];
+    const int j = S.pj[q], k = res_pair_k(q, j, N);
     double gr = 0.0, gi = 0.0;
     for (int i = 0; i < d; ++i) {
       const double ar = S.phi[2 * (j * d + i)], ai = S.phi[2 * (j * d + i) + 1];
@@ -635,13 +889,10 @@ __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double d
   *F = s + delta * log(Ssum);
   *smax = s;
   if (!gout) return true;
-  // M = w (.) G with the softmax weights w = exp((x - s)/delta) / Ssum
+  // the softmax weights w = exp((x - s)/delta) / Ssum (G is kept: the exact
+  // Hessian products need it); M = w (.) G is formed where it is used
   const double inv_sum = 1.0 / Ssum;
-  for (int q = threadIdx.x; q < P; q += kResThreads) {
-    const double w = S.W[q] * inv_sum;
-    S.Gre[q] *= w;
-    S.Gim[q] *= w;
-  }
+  for (int q = threadIdx.x; q < P; q += kResThreads) S.W[q] *= inv_sum;
   __syncthreads();
   // g_k = 2 sum_{j != k} M_jk phi_j (M Hermitian: M_jk = conj(M_kj) for j > k),
   // j ascending, then the projection
@@ -651,7 +902,7 @@ __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double d
     double gr = 0.0, gi = 0.0;
     for (int j = 0; j < k; ++j) {
       const int q = j * N - j * (j + 1) / 2 + (k - j - 1);
-      const double mr = S.Gre[q], mi = S.Gim[q];
+      const double mr = S.W[q] * S.Gre[q], mi = S.W[q] * S.Gim[q];
       const double pr = S.phi[2 * (j * d + i)], pi = S.phi[2 * (j * d + i) + 1];
       gr = fma(mr, pr, gr);
       gr = fma(-mi, pi, gr);
@@ -661,7 +912,7 @@ __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double d
     const int base = k * N - k * (k + 1) / 2 - k - 1;
     for (int j = k + 1; j < N; ++j) {
       const int q = base + j;
-      const double mr = S.Gre[q], mi = S.Gim[q];
+      const double mr = S.W[q] * S.Gre[q], mi = S.W[q] * S.Gim[q];
       const double pr = S.phi[2 * (j * d + i)], pi = S.phi[2 * (j * d + i) + 1];
       gr = fma(mr, pr, gr);
       gr = fma(mi, pi, gr);
@@ -679,6 +930,7 @@ __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double d
       rad = fma(S.phi[2 * (k * d + i) + 1], gout[2 * (k * d + i) + 1], rad);
     }
     const double inv = S.rn[k];
+    S.rho[k] = rad;
     for (int i = 0; i < d; ++i) {
       gout[2 * (k * d + i)] = (gout[2 * (k * d + i)] - S.phi[2 * (k * d + i)] * rad) * inv;
       gout[2 * (k * d + i) + 1] =
@@ -689,6 +941,102 @@ __device__ bool res_eval(const ResArgs& a, ResSmem& S, const double* v, double d
   return true;
 }
 
+// out = B u, B the exact Hessian of F_{s,delta} at S.x, from the state the
+// last res_eval(S.x, gradient into S.g) left: phi, 1/r, rho, G and w.  The
+// chain rule of the stack's kernels above (k_hvx_*), with d phi in S.xn and
+// dG, then dM, in the pair arrays.
+__device__ void res_hv_exact(const ResArgs& a, ResSmem& S, const double* u, double* out,
+                             double delta) {
+  const int N = a.N, d = a.d, P = a.P;
+  __syncthreads();
+  double* dphi = S.xn;
+  for (int k = threadIdx.x; k < N; k += kResThreads) {
+    double pu = 0.0;
+    for (int i = 0; i < d; ++i) {
+      pu = fma(S.phi[2 * (k * d + i)], u[2 * (k * d + i)], pu);
+      pu = fma(S.phi[2 * (k * d + i) + 1], u[2 * (k * d + i) + 1], pu);
+    }
+    const double inv = S.rn[k];
+    for (int c = 0; c < 2 * d; ++c)
+      dphi[2 * k * d + c] = (u[2 * k * d + c] - S.phi[2 * k * d + c] * pu) * inv;
+  }
+  __syncthreads();
+  // dG and T = sum w dx, dx = 2 Re(conj(G) dG)
+  double tpart = 0.0;
+  for (int q = threadIdx.x; q < P; q += kResThreads) {
+    const int j = S.pj[q], k = res_pair_k(q, j, N);
+    double hr = 0.0, hi = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double ar = S.phi[2 * (j * d + i)], ai = S.phi[2 * (j * d + i) + 1];
+      const double br = S.phi[2 * (k * d + i)], bi = S.phi[2 * (k * d + i) + 1];
+      const double dar = dphi[2 * (j * d + i)], dai = dphi[2 * (j * d + i) + 1];
+      const double dbr = dphi[2 * (k * d + i)], dbi = dphi[2 * (k * d + i) + 1];
+      hr = fma(dar, br, hr); hr = fma(dai, bi, hr); hr = fma(ar, dbr, hr); hr = fma(ai, dbi, hr);
+      hi = fma(dar, bi, hi); hi = fma(-dai, br, hi); hi = fma(ar, dbi, hi); hi = fma(-ai, dbr, hi);
+    }
+    S.dMre[q] = hr;
+    S.dMim[q] = hi;
+    tpart = fma(S.W[q], 2.0 * (S.Gre[q] * hr + S.Gim[q] * hi), tpart);
+  }
+  const double T = res_sum(tpart, S.red);
+  const double inv_delta = 1.0 / delta;
+  for (int q = threadIdx.x; q < P; q += kResThreads) {
+    const double gr = S.Gre[q], gi = S.Gim[q], hr = S.dMre[q], hi = S.dMim[q], w = S.W[q];
+    const double dw = w * (2.0 * (gr * hr + gi * hi) - T) * inv_delta;
+    S.dMre[q] = fma(dw, gr, w * hr);
+    S.dMim[q] = fma(dw, gi, w * hi);
+  }
+  __syncthreads();
+  // dg_k = 2 sum_{j != k} (dM_jk phi_j + M_jk d phi_j), j ascending
+  const int half = d * N;
+  for (int t = threadIdx.x; t < half; t += kResThreads) {
+    const int k = t / d, i = t - k * d;
+    double hr = 0.0, hi = 0.0;
+    for (int j = 0; j < N; ++j) {
+      if (j == k) continue;
+      const bool lo = j < k;
+      const int q = lo ? j * N - j * (j + 1) / 2 + (k - j - 1) : k * N - k * (k + 1) / 2 + (j - k - 1);
+      const double w = S.W[q];
+      const double mr = w * S.Gre[q], mi = lo ? w * S.Gim[q] : -(w * S.Gim[q]);
+      const double nr = S.dMre[q], ni = lo ? S.dMim[q] : -S.dMim[q];
+      const double pr = S.phi[2 * (j * d + i)], pi = S.phi[2 * (j * d + i) + 1];
+      const double qr = dphi[2 * (j * d + i)], qi = dphi[2 * (j * d + i) + 1];
+      hr = fma(nr, pr, hr); hr = fma(-ni, pi, hr); hr = fma(mr, qr, hr); hr = fma(-mi, qi, hr);
+      hi = fma(nr, pi, hi); hi = fma(ni, pr, hi); hi = fma(mr, qi, hi); hi = fma(mi, qr, hi);
+    }
+    out[2 * (k * d + i)] = 2.0 * hr;
+    out[2 * (k * d + i) + 1] = 2.0 * hi;
+  }
+  __syncthreads();
+  // the projection through the normalisation: g_k = r_k grad_k + phi_k rho_k,
+  // d rho = Re(d phi^* g + phi^* dg), (B u)_k = (dg - d phi rho - phi d rho)/r
+  // - grad d r / r with d r = Re(phi^* u)
+  for (int k = threadIdx.x; k < N; k += kResThreads) {
+    double q2 = 0.0, pu = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double re = S.x[2 * (k * d + i)], im = S.x[2 * (k * d + i) + 1];
+      q2 = fma(re, re, q2);
+      q2 = fma(im, im, q2);
+      pu = fma(S.phi[2 * (k * d + i)], u[2 * (k * d + i)], pu);
+      pu = fma(S.phi[2 * (k * d + i) + 1], u[2 * (k * d + i) + 1], pu);
+    }
+    const double r = sqrt(q2), inv = S.rn[k], rho = S.rho[k];
+    double drho = 0.0;
+    for (int c = 0; c < 2 * d; ++c) {
+      const double graw = fma(r, S.g[2 * k * d + c], S.phi[2 * k * d + c] * rho);
+      drho = fma(dphi[2 * k * d + c], graw, drho);
+      drho = fma(S.phi[2 * k * d + c], out[2 * k * d + c], drho);
+    }
+    for (int c = 0; c < 2 * d; ++c) {
+      const double dg = out[2 * k * d + c];
+      out[2 * k * d + c] =
+          (dg - dphi[2 * k * d + c] * rho - S.phi[2 * k * d + c] * drho) * inv -
+          S.g[2 * k * d + c] * pu * inv;
+    }
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kResThreads, 1) k_tr_resident(const ResArgs a) {
   extern __shared__ __align__(16) double sm[];
   const int f = blockIdx.x;
@@ -697,16 +1045,20 @@ __global__ void __launch_bounds__(kResThreads, 1) k_tr_resident(const ResArgs a)
   ResSmem S;
   double* c = sm;
   S.x = c; c += n; S.xn = c; c += n; S.g = c; c += n; S.p = c; c += n; S.r = c; c += n;
-  S.dv = c; c += n; S.bd = c; c += n; S.gp = c; c += n; S.gm = c; c += n; S.phi = c; c += n;
-  S.rn = c; c += N; S.Gre = c; c += P; S.Gim = c; c += P; S.W = c; c += P;
-  S.red = c; c += kResThreads;
+  S.dv = c; c += n; S.bd = c; c += n; S.phi = c; c += n;
+  S.rn = c; c += N; S.rho = c; c += N; S.Gre = c; c += P; S.Gim = c; c += P; S.W = c; c += P;
+  S.red = c; c += kResRed;
+  S.gp = S.gm = S.dMre = S.dMim = nullptr;
+  if (a.exact) {
+    S.dMre = c; c += P; S.dMim = c; c += P;
+  } else {
+    S.gp = c; c += n; S.gm = c; c += n;
+  }
   S.pj = reinterpret_cast<unsigned short*>(c);
-  S.pk = S.pj + P;
   for (int q = threadIdx.x; q < P; q += kResThreads) {
     int j = 0, rem = q;
     while (rem >= N - 1 - j) { rem -= N - 1 - j; ++j; }
     S.pj[q] = (unsigned short)j;
-    S.pk[q] = (unsigned short)(j + 1 + rem);
   }
   double* vf = a.v + (size_t)f * n;
   for (int i = threadIdx.x; i < n; i += kResThreads) S.x[i] = vf[i];
@@ -744,16 +1096,21 @@ __global__ void __launch_bounds__(kResThreads, 1) k_tr_resident(const ResArgs a)
         st = 0;
       } else {
         for (cgit = 0; cgit < o.max_cg; ++cgit) {
-          // B d by a central difference of the gradient
-          const double nu = sqrt(res_dot(S.dv, S.dv, n, S.red));
-          const double step = nu > 0.0 ? h / nu : 0.0, cq = nu > 0.0 ? nu / (2.0 * h) : 0.0;
-          double Ft, st2;
-          res_axpby(1.0, S.x, step, S.dv, S.xn, n);
-          ok = res_eval(a, S, S.xn, delta, S.gp, &Ft, &st2);
-          res_axpby(1.0, S.x, -step, S.dv, S.xn, n);
-          ok = ok && res_eval(a, S, S.xn, delta, S.gm, &Ft, &st2);
-          if (!ok) break;
-          res_axpby(cq, S.gp, -cq, S.gm, S.bd, n);
+          if (a.exact) {
+            // B d with the exact Hessian at the iterate
+            res_hv_exact(a, S, S.dv, S.bd, delta);
+          } else {
+            // B d by a central difference of the gradient
+            const double nu = sqrt(res_dot(S.dv, S.dv, n, S.red));
+            const double step = nu > 0.0 ? h / nu : 0.0, cq = nu > 0.0 ? nu / (2.0 * h) : 0.0;
+            double Ft, st2;
+            res_axpby(1.0, S.x, step, S.dv, S.xn, n);
+            ok = res_eval(a, S, S.xn, delta, S.gp, &Ft, &st2);
+            res_axpby(1.0, S.x, -step, S.dv, S.xn, n);
+            ok = ok && res_eval(a, S, S.xn, delta, S.gm, &Ft, &st2);
+            if (!ok) break;
+            res_axpby(cq, S.gp, -cq, S.gm, S.bd, n);
+          }
           ++products;
           const double dbd = res_dot(S.dv, S.bd, n, S.red), rd = res_dot(S.dv, S.r, n, S.red);
           const double zz = res_dot(S.p, S.p, n, S.red), zd = res_dot(S.p, S.dv, n, S.red);
@@ -825,32 +1182,35 @@ __global__ void __launch_bounds__(kResThreads, 1) k_tr_resident(const ResArgs a)
 
 }  // namespace
 
-bool tr_resident_fits(int N, int d) {
+bool tr_resident_fits(int N, int d, bool exact) {
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return false;
-  return N <= 65535 && res_smem_bytes(N, d) + 1024 <= (size_t)optin;
+  // the kernel has no static shared memory: the whole opt-in size is dynamic
+  return N <= 65535 && res_smem_bytes(N, d, exact) <= (size_t)optin;
 }
 
 int tr_solve_device(int N, int d, int L, double* v_dev, const trstmi_tr_options& o,
                     void* scratch, int num_sms, cudaStream_t s, TrFrameLog* logs) {
-  const bool resident = o.path == 2 || (o.path == 0 && tr_resident_fits(N, d));
+  const bool exact = o.hessian == 0;
+  const bool resident = o.path == 2 || (o.path == 0 && tr_resident_fits(N, d, exact));
   if (!resident) return tr_solve_stack(N, d, L, v_dev, o, scratch, num_sms, s, logs);
-  if (!tr_resident_fits(N, d)) return TRSTMI_EUNSUPPORTED;
+  if (!tr_resident_fits(N, d, exact)) return TRSTMI_EUNSUPPORTED;
   int cap = 0;
   for (int f = 0; f < L && logs; ++f) cap = std::max(cap, logs[f].rows ? logs[f].cap : 0);
   // results in the scratch array: L ints x 3 and L doubles, then the rows
   unsigned char* b = static_cast<unsigned char*>(scratch);
   ResArgs a;
   a.N = N; a.d = d; a.P = N * (N - 1) / 2; a.v = v_dev; a.o = o; a.cap = cap;
+  a.exact = exact ? 1 : 0;
   a.mu2 = reinterpret_cast<double*>(b);
   a.n_rows = reinterpret_cast<int*>(a.mu2 + L);
   a.hv = a.n_rows + L;
   a.bad = a.hv + L;
   a.rows = cap > 0 ? reinterpret_cast<trstmi_tr_row*>(b + (((size_t)L * 20 + 255) & ~(size_t)255))
                    : nullptr;
-  const size_t smem = res_smem_bytes(N, d);
+  const size_t smem = res_smem_bytes(N, d, exact);
   cudaError_t e = cudaFuncSetAttribute(k_tr_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e == cudaSuccess) {

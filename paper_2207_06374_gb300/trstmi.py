@@ -31,6 +31,11 @@ class TrstmiError(RuntimeError):
         super().__init__(f"{what}: {strerror(status)} ({status}) {detail}".rstrip())
 
 
+# trstmi_options.dev_alloc / dev_free
+DEV_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+DEV_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class Options(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("precision", ctypes.c_int32), ("topk", ctypes.c_int32),
                 ("trace_cap", ctypes.c_int32), ("delta0", ctypes.c_double),
@@ -38,7 +43,53 @@ class Options(ctypes.Structure):
                 ("delta_min", ctypes.c_double), ("delta_max", ctypes.c_double),
                 ("target_mu", ctypes.c_double), ("screen_min_delta", ctypes.c_double),
                 ("stream", ctypes.c_void_p),
-                ("device", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN),
+                ("alloc_ctx", ctypes.c_void_p)]
+
+
+class TorchAllocator:
+    """Device memory for a handle from PyTorch's caching allocator.
+
+    Passed as ``allocator=`` to Search, Batch or Server, it fills the options'
+    dev_alloc / dev_free callbacks, so every device allocation of the handle
+    comes from (and returns to) torch's pool on the handle's device instead
+    of cudaMalloc / cudaFree.  The object must outlive the handle (the
+    handle's Python wrapper keeps a reference).  ``allocs``, ``frees`` and
+    ``live`` count what went through it.
+    """
+
+    def __init__(self, device: int = 0):
+        import torch  # the binding itself does not need torch; this allocator does
+        self._torch = torch
+        self.device = device
+        self.live = {}
+        self.allocs = 0
+        self.frees = 0
+
+        def _alloc(nbytes, _ctx):
+            try:
+                p = int(self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device))
+            except Exception:  # out of memory: the library reports TRSTMI_ENOMEM
+                return None
+            self.live[p] = int(nbytes)
+            self.allocs += 1
+            return p
+
+        def _free(ptr, _ctx):
+            if ptr is None:
+                return
+            self.live.pop(int(ptr), None)
+            self.frees += 1
+            self._torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._alloc = DEV_ALLOC_FN(_alloc)
+        self._free = DEV_FREE_FN(_free)
+
+    def install(self, o: "Options") -> None:
+        o.dev_alloc = self._alloc
+        o.dev_free = self._free
+        o.alloc_ctx = None
 
 
 class TraceRow(ctypes.Structure):
@@ -114,7 +165,8 @@ class TrOptions(ctypes.Structure):
                 ("delta", ctypes.c_double * 16), ("max_cg", ctypes.c_int32),
                 ("path", ctypes.c_int32), ("radius0", ctypes.c_double),
                 ("radius_max", ctypes.c_double), ("eta", ctypes.c_double),
-                ("gtol", ctypes.c_double), ("fd_step", ctypes.c_double)]
+                ("gtol", ctypes.c_double), ("fd_step", ctypes.c_double),
+                ("hessian", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 TR_ROW_DTYPE = np.dtype([("stage", "<i4"), ("iter", "<i4"), ("F", "<f8"), ("s", "<f8"),
@@ -124,8 +176,12 @@ TR_ROW_DTYPE = np.dtype([("stage", "<i4"), ("iter", "<i4"), ("F", "<f8"), ("s", 
 
 
 def tr_options(deltas=None, **kw) -> TrOptions:
+    """hessian: "exact" (default) or "difference" (or the enum value)."""
     o = TrOptions()
     lib().trstmi_tr_default_options(ctypes.byref(o))
+    h = kw.pop("hessian", None)
+    if h is not None:
+        o.hessian = {"exact": 0, "difference": 1}.get(h, h)
     if deltas is not None:
         o.n_delta = len(deltas)
         for i, x in enumerate(deltas):
@@ -164,6 +220,8 @@ SIGNATURES = {
     "trstmi_last_error": (ctypes.c_char_p, []),
     "trstmi_score": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
                                     ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp]),
+    "trstmi_last_ranking": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_uint32),
+                                           _dp]),
     "trstmi_candidate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
                                         ctypes.c_double, ctypes.c_int, _dp]),
     "trstmi_mu2_frame": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp]),
@@ -276,6 +334,9 @@ def default_options() -> Options:
 
 def make_options(**kw) -> Options:
     o = default_options()
+    alloc = kw.pop("allocator", None)
+    if alloc is not None:
+        alloc.install(o)
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
@@ -290,6 +351,7 @@ class Search:
 
     def __init__(self, N: int, d: int, seed: int, **options):
         self.N, self.d, self.seed = N, d, seed
+        self.allocator = options.get("allocator")
         self.options = make_options(**options)
         h = ctypes.c_void_p()
         _check(lib().trstmi_create(N, d, seed, ctypes.byref(self.options), ctypes.byref(h)),
@@ -375,6 +437,24 @@ class Search:
         _check(lib().trstmi_score(self._h, t, c0, count, delta, p, out.ctypes.data_as(_dp)),
                "trstmi_score")
         return out
+
+    def last_ranking(self):
+        """(ranking scores of the last iteration's K candidates, survivor
+        indices, their binary32 re-scores); the last two are None outside the
+        screen modes."""
+        K, k = self.options.K, self.options.topk
+        mu2 = np.zeros(K)
+        screen = self.options.precision in (BF16_SCREEN, FP16_SCREEN, TF32_SCREEN)
+        if screen:
+            idx = np.zeros(k, dtype=np.uint32)
+            top = np.zeros(k)
+            _check(lib().trstmi_last_ranking(self._h, mu2.ctypes.data_as(_dp),
+                                             idx.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                             top.ctypes.data_as(_dp)), "trstmi_last_ranking")
+            return mu2, idx, top
+        _check(lib().trstmi_last_ranking(self._h, mu2.ctypes.data_as(_dp), None, None),
+               "trstmi_last_ranking")
+        return mu2, None, None
 
     def candidate(self, t: int, c: int, delta: float, precision="fp64") -> np.ndarray:
         p = PRECISIONS[precision] if isinstance(precision, str) else precision
@@ -498,6 +578,7 @@ class Batch:
         self.Ns, self.ds = [int(x) for x in Ns], [int(x) for x in ds]
         self.seeds = [int(x) for x in seeds]
         self.n = len(self.Ns)
+        self.allocator = options.get("allocator")
         self.options = make_options(**options)
         Na = (ctypes.c_int * self.n)(*self.Ns)
         da = (ctypes.c_int * self.n)(*self.ds)
@@ -571,6 +652,9 @@ class Server:
         o.iters_per_round, o.queue_cap = iters_per_round, queue_cap
         if max_resident_pairs is not None:
             o.max_resident_pairs = max_resident_pairs
+        self.allocator = search.pop("allocator", None)
+        if self.allocator is not None:
+            self.allocator.install(o.search)
         for k, v in search.items():
             if k == "precision" and isinstance(v, str):
                 v = PRECISIONS[v]

@@ -421,3 +421,86 @@ def test_precision_form_rejects_on_fp32_bound_late_in_a_run():
     assert np.array_equal(tr["accepted"], rtr["accepted"])
     assert check_precision_form_rows(tr, rtr, d, O.mu2(phi0)) > 0
     assert np.abs(phi - rphi).max() < 1e-12
+
+
+# ------------------------- the screen modes' choice against the oracle's K scores
+
+SCREEN_TOL = {"bf16": 4e-3, "fp16": 1e-3, "tf32": 1e-3}
+
+
+def check_ranking_against_oracle(s, phi0, seed, t, delta, tol, cstar):
+    """One screened iteration (candidates of iteration t, radius delta around
+    phi0) against the oracle's binary64 scores of all K candidates:
+    * every screen score within the screen tolerance of the oracle's mu;
+    * the survivors are exactly the topk smallest screen scores (ties to the
+      lowest index), in increasing order;
+    * their binary32 re-scores within 1e-6 of the oracle's mu, and the chosen
+      candidate is the best of them (ties to the lowest index);
+    * the choice is a valid one among all K: its oracle mu is within twice
+      the screen tolerance of the oracle's best, and every survivor's oracle
+      mu within twice the tolerance of the oracle's topk-th best."""
+    scores, surv, top = s.last_ranking()
+    K, k = len(scores), len(surv)
+    ref = O.score(phi0, seed, delta, t, 0, K, nthreads=16)
+    mu, mu_ref = np.sqrt(scores), np.sqrt(ref)
+    assert np.max(np.abs(mu - mu_ref)) < tol
+    order = np.lexsort((np.arange(K), scores.astype(np.float32)))[:k]
+    assert np.array_equal(surv, order)
+    assert np.max(np.abs(np.sqrt(top) - mu_ref[surv])) < 1e-6
+    best = min(range(k), key=lambda q: (np.float32(top[q]), int(surv[q])))
+    assert int(surv[best]) == int(cstar)
+    assert mu_ref[cstar] <= mu_ref.min() + 2 * tol
+    kth = np.sort(mu_ref)[k - 1]
+    assert np.all(mu_ref[surv] <= kth + 2 * tol)
+    return mu_ref
+
+
+@pytest.mark.parametrize("precision,d,N", [("bf16", 32, 1024), ("fp16", 32, 1024),
+                                           ("tf32", 32, 768), ("bf16", 64, 768)])
+def test_screen_choice_is_valid_among_the_oracle_scores_full_size(precision, d, N):
+    """The precision-form workload's shape (K = 1024, top-8): two screened
+    iterations, each checked against the oracle's scores of all K candidates."""
+    K, seed = 1024, 3
+    tol = SCREEN_TOL[precision]
+    with T.Search(N, d, seed, K=K, precision=precision, topk=8, screen_min_delta=0.0) as s:
+        for _ in range(2):
+            phi0 = s.get_phi()
+            s.step(1)
+            row = s.trace()[-1]
+            assert row["flags"] & 1 == 1
+            check_ranking_against_oracle(s, phi0, seed, int(row["t"]), float(row["delta_used"]),
+                                         tol, int(row["cstar"]))
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16", "tf32"])
+def test_screen_choice_when_candidates_nearly_tie(precision):
+    """A radius far below the screen's resolution: candidate coherences differ
+    by ~1e-5, so the screen's order is mostly rounding and the oracle's best
+    candidate usually lies outside the top-2.  The choice must still be one
+    of the oracle's near-best (within twice the screen tolerance), and the
+    survivors the screen's own two smallest scores."""
+    d, N, K, seed = 8, 40, 256, 12
+    tol = SCREEN_TOL[precision]
+    with T.Search(N, d, seed, K=K, precision=precision, topk=2, screen_min_delta=0.0,
+                  delta0=1e-5) as s:
+        phi0 = s.get_phi()
+        s.step(1)
+        row = s.trace()[-1]
+        mu_ref = check_ranking_against_oracle(s, phi0, seed, 1, 1e-5, tol, int(row["cstar"]))
+    assert np.ptp(mu_ref) < 1e-3
+
+
+def test_fp32_mode_choice_is_the_oracle_argmin():
+    """Binary32 ranking of every candidate (no screen): the chosen candidate's
+    oracle mu is within the binary32 tolerance of the oracle's best of K."""
+    d, N, K, seed = 16, 300, 512, 4
+    with T.Search(N, d, seed, K=K, precision="fp32") as s:
+        phi0 = s.get_phi()
+        s.step(1)
+        row = s.trace()[-1]
+        scores, _, _ = s.last_ranking()
+    ref = np.sqrt(O.score(phi0, seed, 0.1, 1, 0, K, nthreads=16))
+    assert np.max(np.abs(np.sqrt(scores) - ref)) < 1e-6
+    c = int(row["cstar"])
+    assert c == int(np.lexsort((np.arange(K), scores.astype(np.float32)))[0])
+    assert ref[c] <= ref.min() + 2e-6

@@ -19,8 +19,8 @@ W = pytest.importorskip("paper_2207_06374_gb300.workloads")
 
 def _alone(N, d, seed, K, budget, target, precision="fp32"):
     with T.Search(N, d, seed, K=K, precision=precision, target_mu=target, trace_cap=0) as s:
-        s.step(budget)
-        return s.step(0), s.get_phi()
+        info = s.step(budget)
+        return info, s.get_phi()
 
 
 def test_results_equal_standalone_runs():
@@ -42,7 +42,8 @@ def test_results_equal_standalone_runs():
     for (N, d, seed, budget, target), (st, res, phi) in zip(reqs, results):
         assert st == T.TRSTMI_OK
         info, phi_alone = _alone(N, d, seed, K, budget, target)
-        assert res.iters == info.iters_done or res.iters <= budget
+        assert res.iters == info.iters_done, (N, d)
+        assert res.accepts == info.accepts, (N, d)
         assert res.mu == info.mu, (N, d)
         assert np.array_equal(phi, phi_alone), (N, d)
         assert res.t_submit_ns <= res.t_admit_ns <= res.t_done_ns
@@ -70,11 +71,57 @@ def test_screen_mode_results_equal_standalone_runs(precision):
         assert st == T.TRSTMI_OK
         with T.Search(N, d, seed, K=K, topk=4, precision=precision, target_mu=target,
                       trace_cap=0) as s:
-            s.step(budget)
-            info = s.step(0)
+            info = s.step(budget)
             phi_alone = s.get_phi()
+        assert res.iters == info.iters_done, (N, d)
         assert res.mu == info.mu, (N, d)
         assert np.array_equal(phi, phi_alone), (N, d)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16", "tf32"])
+def test_served_requests_replay_in_the_oracle(precision):
+    """Served requests against the oracle, not only against the CUDA path: a
+    mix is served together; for each request the oracle replays in binary64
+    the choices its search took (the standalone run of the same request, which
+    the served result equals bit for bit, gives the choice sequence) and must
+    reproduce the served frame and mu.  Precision form: every accept decision
+    and the final frame to 1e-12 (decisions rest on certified binary64 mu).
+    Binary32: the chosen candidates' mu to 1e-6 and the decisions wherever the
+    improvement exceeds binary32 resolution."""
+    K = 48
+    reqs = [(9, 3, 41, 40, 0.5001), (30, 5, 42, 25, 0.0), (64, 8, 43, 15, 0.0),
+            (150, 12, 44, 10, 0.0)]
+    extra = [(600, 24, 45, 6, 0.0), (5, 2, 46, 60, 0.0)]   # served beside them only
+    opts = dict(K=K, precision=precision, topk=4) if precision != "fp32" else \
+        dict(K=K, precision=precision)
+    with T.Server(hbm_budget=256 << 20, max_slots=4, iters_per_round=4, **opts) as srv:
+        tickets = [srv.submit(N, d, seed, budget, target_mu=target, want_phi=True)
+                   for N, d, seed, budget, target in reqs + extra]
+        results = [srv.wait(t, with_phi=True) for t in tickets][: len(reqs)]
+    import oracle as O
+    from test_gpu_parity import check_precision_form_rows
+    for (N, d, seed, budget, target), (st, res, phi) in zip(reqs, results):
+        assert st == T.TRSTMI_OK
+        with T.Search(N, d, seed, target_mu=target, trace_cap=4096, **opts) as s:
+            phi0 = s.get_phi()
+            info = s.step(budget)
+            tr = s.trace()
+            assert np.array_equal(s.get_phi(), phi)
+        assert res.iters == info.iters_done == len(tr)
+        oo = O.make_opts(K=K, T=res.iters, target_mu=target)
+        m0 = O.mu2(phi0)
+        rphi, rm2, _, rtr = O.replay(phi0, seed, oo, 0.1, m0, 0, tr["cstar"])
+        if precision == "fp32":
+            gaps = np.abs(np.sqrt(rtr["mu2_best"]) - np.sqrt(np.maximum(rtr["mu2_cur"], 0)))
+            clear = gaps > 1e-5
+            assert np.array_equal(tr["accepted"][clear], rtr["accepted"][clear])
+            assert np.max(np.abs(np.sqrt(tr["mu2_best"]) - np.sqrt(rtr["mu2_best"]))) < 1e-6
+            assert abs(res.mu - np.sqrt(O.mu2(phi.astype(np.complex64).astype(complex)))) < 1e-6
+        else:
+            check_precision_form_rows(tr, rtr, d, m0)
+            assert np.array_equal(tr["accepted"], rtr["accepted"])
+            assert np.abs(phi - rphi).max() < 1e-12
+            assert abs(res.mu - np.sqrt(rm2)) < 1e-12
 
 
 def test_fp32_results_with_large_requests_equal_standalone_runs():

@@ -1,13 +1,18 @@
 """The trust-region CG-Steihaug procedure on the GPU against the oracle.
 
 Both sides run the same sequence (smoothing stages, trust-region loop,
-CG-Steihaug steps, Hessian products by central differences of the exact
-gradient) in binary64; they differ only in the order of their sums, which the
-difference quotient amplifies by 1/h (h = 1e-6), so iterates agree to about
-1e-9.  Rows are compared while the gradient is still well above that noise
-(|grad F| > 1e-5): F and s to 1e-8 relative, |grad F| to 1e-4 relative, and
-the discrete decisions (CG iterations and exit, accept) exactly.  The end
-points are compared through their coherence.
+CG-Steihaug steps) in binary64 with the model's B the exact Hessian of F
+(the paper's B_k = grad^2 f_k; Algorithm "Trust-Region CG-Steihaug"): the
+Hessian products are the chain rule through the normalisation, the Gram
+entries and the softmax weights on both sides.  They differ only in the order
+of their sums (a few units in the last place per operation), so rows are
+compared while |grad F| > 1e-8: F, s and the radius to 1e-10 relative,
+|grad F| to 1e-7 relative (it is a difference of nearly equal sums near a
+stationary point), the discrete decisions (CG iterations and exit, accept)
+exactly.  The central-difference option (hessian="difference", step h = 1e-6)
+is held to the oracle's central differences: their sums' rounding is
+amplified by 1/h, so its rows are compared while |grad F| > 1e-5, F and s to
+1e-8, |grad F| to 1e-4.  The end points are compared through their coherence.
 """
 import numpy as np
 import pytest
@@ -20,6 +25,8 @@ pytestmark = pytest.mark.gpu
 T = pytest.importorskip("paper_2207_06374_gb300.trstmi")
 
 SCHEDULE = (0.1, 0.03, 0.01, 0.003, 0.001, 3e-4, 1e-4)
+# (gradient floor of the compared rows, rel. tol. of F / s / radius, of |grad F|)
+TOL = {"exact": (1e-8, 1e-10, 1e-7), "difference": (1e-5, 1e-8, 1e-4)}
 
 
 def _start(d, N, seed):
@@ -28,25 +35,45 @@ def _start(d, N, seed):
     return z / np.linalg.norm(z, axis=0, keepdims=True)
 
 
-@pytest.mark.parametrize("path", [1, 2])       # 1: stack driven from the host; 2: resident
-@pytest.mark.parametrize("d,N,seed", [(2, 4, 1), (3, 7, 1), (3, 9, 2), (4, 8, 3), (2, 5, 4)])
-def test_trace_matches_oracle(d, N, seed, path):
-    v = _start(d, N, seed)
-    phi, tr = T.tr_solve(v, deltas=SCHEDULE, max_outer=100, max_cg=200, path=path)
-    ophi, otr = O.tr_solve(v, O.tr_opts(deltas=SCHEDULE, max_outer=100, max_cg=200))
+def _compare_rows(tr, otr, hessian):
+    gfloor, rel, grel = TOL[hessian]
     k = 0
-    while (k < min(len(tr), len(otr)) and otr["gnorm"][k] > 1e-5
+    while (k < min(len(tr), len(otr)) and otr["gnorm"][k] > gfloor
            and tr["stage"][k] == otr["stage"][k]):
         a, b = tr[k], otr[k]
-        assert a["F"] == pytest.approx(b["F"], rel=1e-8)
-        assert a["s"] == pytest.approx(b["s"], rel=1e-8)
-        assert a["gnorm"] == pytest.approx(b["gnorm"], rel=1e-4)
-        assert a["radius"] == pytest.approx(b["radius"], rel=1e-8)
+        assert a["F"] == pytest.approx(b["F"], rel=rel), k
+        assert a["s"] == pytest.approx(b["s"], rel=rel), k
+        assert a["gnorm"] == pytest.approx(b["gnorm"], rel=grel), k
+        assert a["radius"] == pytest.approx(b["radius"], rel=rel), k
         assert (a["cg_iters"], a["cg_status"], a["accepted"]) == \
             (b["cg_iters"], b["cg_status"], b["accepted"]), k
         k += 1
-    assert k >= 5
+    return k
+
+
+@pytest.mark.parametrize("hessian", ["exact", "difference"])
+@pytest.mark.parametrize("path", [1, 2])       # 1: stack driven from the host; 2: resident
+@pytest.mark.parametrize("d,N,seed", [(2, 4, 1), (3, 7, 1), (3, 9, 2), (4, 8, 3), (2, 5, 4)])
+def test_trace_matches_oracle(d, N, seed, path, hessian):
+    v = _start(d, N, seed)
+    phi, tr = T.tr_solve(v, deltas=SCHEDULE, max_outer=100, max_cg=200, path=path,
+                         hessian=hessian)
+    ophi, otr = O.tr_solve(v, O.tr_opts(deltas=SCHEDULE, max_outer=100, max_cg=200,
+                                        hessian=hessian))
+    assert _compare_rows(tr, otr, hessian) >= 5
     assert np.sqrt(O.mu2(phi)) == pytest.approx(np.sqrt(O.mu2(ophi)), abs=1e-6)
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_hessian_products_on_a_larger_frame_match_the_oracle(path):
+    """d = 6, N = 30 (several warps of pairs and columns): the first stage's
+    rows, each with dozens of exact Hessian products, as the oracle takes them."""
+    v = _start(6, 30, 5)
+    kw = dict(deltas=(0.03, 0.01), max_outer=15, max_cg=80)
+    _, tr = T.tr_solve(v, path=path, **kw)
+    _, otr = O.tr_solve(v, O.tr_opts(**kw))
+    assert _compare_rows(tr, otr, "exact") >= 10
+    assert tr["cg_iters"][:10].sum() >= 30
 
 
 @pytest.mark.parametrize("path", [1, 2])
@@ -95,7 +122,7 @@ def test_rejects_bad_options():
     v = _start(2, 4, 0)
     for kw in [dict(deltas=()), dict(deltas=(0.1, 0.0)), dict(max_cg=0), dict(eta=0.3),
                dict(radius0=0.0), dict(fd_step=0.0), dict(radius0=2.0, radius_max=1.0),
-               dict(path=3)]:
+               dict(path=3), dict(hessian=2)]:
         with pytest.raises(T.TrstmiError) as e:
             T.tr_solve(v, **kw)
         assert e.value.status == T.TRSTMI_EINVAL

@@ -4,12 +4,12 @@ Callers whose device memory belongs to another allocator, or that cannot
 afford the implicit synchronisation of cudaMalloc / cudaFree, use this entry
 point: it keeps its scratch in a static device array and allocates nothing.
 It must give the same binary64 mu^2 as the allocating entry point,
-trstmi_mu2_frame, within the binary64 tolerance of the other parity tests
-(1e-12 relative).  The array keeps the previous call's contents, so the
-checks run as consecutive calls, a larger problem followed by smaller ones
-and back, which fails if anything that must start at zero leaks between
-calls.  This file is collected last so that a run stopping at the first
-failure has already run every other test.
+trstmi_mu2_frame, and as the oracle, within the binary64 tolerance of the
+other parity tests (1e-12 relative).  The array keeps the previous call's
+contents, so the checks run as consecutive calls, a larger problem followed
+by smaller ones and back, which fails if anything that must start at zero
+leaks between calls.  This file is collected last so that a run stopping at
+the first failure has already run every other test.
 """
 import ctypes
 
@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 
 import frames as F
+import oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -37,27 +38,58 @@ def _noalloc_mu2(phi, stream_handle):
     return float(out.item())
 
 
-def test_noalloc_matches_allocating_entry_point_on_consecutive_calls():
-    if not torch.cuda.is_available():
-        pytest.skip("no GPU")
+def _scaled(phi, scales):
+    return phi * np.asarray(scales)[None, :]
+
+
+def _frames():
     rng = np.random.default_rng(2026)
     frames = [F.random_frame(32, 1024, rng), F.random_frame(8, 300, rng), F.hesse_sic_3_9(),
               F.random_frame(5, 77, rng), F.random_frame(64, 2048, rng)]
+    # columns that are not unit: moderate scales, a wide spread of scales, and
+    # scales whose squares leave [2^-40, 2^40] (the full binary64 pass decides)
+    frames.append(_scaled(F.random_frame(16, 200, rng), rng.uniform(0.5, 2.0, 200)))
+    frames.append(_scaled(F.random_frame(8, 150, rng), 10.0 ** rng.uniform(-3, 3, 150)))
+    frames.append(_scaled(F.random_frame(4, 40, rng), 10.0 ** rng.uniform(10, 13, 40)))
+    frames.append(_scaled(F.random_frame(4, 40, rng), 10.0 ** rng.uniform(-14, -11, 40)))
+    # 512 equal columns in C^1: all 130816 pairs tie at |G| = 1, more than the
+    # 65536-entry pair list holds, so the full binary64 pass runs
+    frames.append(np.ones((1, 512), dtype=np.complex128))
+    return frames
+
+
+def test_noalloc_matches_allocating_entry_point_and_oracle_on_consecutive_calls():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    frames = _frames()
     stream = torch.cuda.current_stream().cuda_stream
-    refs = [T.mu2_frame(phi, "fp64") for phi in frames]
+    refs = [O.mu2(phi) for phi in frames]
+    assert refs[-1] == 1.0
+    # the allocating entry point agrees with the oracle on the frames it takes
+    # as they are (it has no norm routing; unit and moderately scaled columns)
+    for i in (0, 1, 2, 3, 4, 5):
+        alloc = T.mu2_frame(frames[i], "fp64")
+        assert abs(alloc - refs[i]) <= 1e-12 * refs[i], (i, alloc, refs[i])
     for order in (range(len(frames)), reversed(range(len(frames)))):
         for i in order:
             got = _noalloc_mu2(frames[i], stream)
             assert abs(got - refs[i]) <= 1e-12 * refs[i], (i, got, refs[i])
-    # the same frame twice in a row gives the same bits
+    # the same frame twice in a row gives the same bits, and the second of two
+    # consecutive calls the allocating entry point's value
     a = _noalloc_mu2(frames[1], stream)
     b = _noalloc_mu2(frames[1], stream)
     assert a == b
+    assert abs(b - T.mu2_frame(frames[1], "fp64")) <= 1e-12 * b
 
 
-def test_noalloc_rejects_sizes_beyond_its_limit():
+def test_noalloc_rejects_sizes_and_pointers_it_cannot_take():
     # rejected before any device pointer is used
-    st = T.lib().trstmi_mu2_frame_noalloc(131073, 1, ctypes.c_void_p(8), ctypes.c_void_p(8), None)
+    st = T.lib().trstmi_mu2_frame_noalloc(131073, 1, ctypes.c_void_p(16), ctypes.c_void_p(16), None)
     assert st == T.TRSTMI_ESIZE
-    st = T.lib().trstmi_mu2_frame_noalloc(4, 300, ctypes.c_void_p(8), ctypes.c_void_p(8), None)
+    st = T.lib().trstmi_mu2_frame_noalloc(4, 300, ctypes.c_void_p(16), ctypes.c_void_p(16), None)
+    assert st == T.TRSTMI_EINVAL
+    # misaligned frame (16-byte double2 loads) or result (64-bit atomics)
+    st = T.lib().trstmi_mu2_frame_noalloc(4, 2, ctypes.c_void_p(24), ctypes.c_void_p(16), None)
+    assert st == T.TRSTMI_EINVAL
+    st = T.lib().trstmi_mu2_frame_noalloc(4, 2, ctypes.c_void_p(32), ctypes.c_void_p(20), None)
     assert st == T.TRSTMI_EINVAL
