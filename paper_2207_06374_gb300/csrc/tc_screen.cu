@@ -619,13 +619,18 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
                                                           buf * 256u + (uint32_t)colh));
         if (I != J) {
           uint32_t ra[32], ia[32];
-#pragma unroll 1
-          for (int ch = 0; ch < 2; ++ch) {
-            tmem_ld32(base + 32u * ch, ra);
-            tmem_ld32(base + 128u + 32u * ch, ia);
-            tmem_wait_ld<32>(ra, ia);
-            absmax<32>(ra, ia, m);
-          }
+          tmem_ld32(base, ra);
+          tmem_ld32(base + 128u, ia);
+          tmem_wait_ld<32>(ra, ia);
+          absmax<32>(ra, ia, m);
+          tmem_ld32(base + 32u, ra);
+          tmem_ld32(base + 160u, ia);
+          tmem_wait_ld<32>(ra, ia);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&ctl.acc_empty[buf]);
+          absmax<32>(ra, ia, m);
+          continue;
         } else {
           // diagonal tile: only column k > row j counts.  This warp's rows
           // are 32qw .. 32qw+31; a 16-column chunk n0 .. n0+15 lies entirely
