@@ -149,18 +149,26 @@ float certify_margin(int d) {
 // binary64 mu^2 of a normalised binary64 frame (with its binary32 rounding)
 // into out64: binary32 max, binary32 preselection of the pairs within the
 // error bound, binary64 over those pairs, full binary64 pass on overflow.
+// hinted: cert32[0] already holds a hint within certify_margin_mu2(d) of the
+// frame's binary32 max (the chosen survivor's binary32 score), so the max pass
+// is skipped; the pair pass checks the hint against the filter pass's own max
+// and falls back to the full binary64 pass if it was too high.
 int enqueue_certify(trstmi_instance* h, const double2* f64, const float2* f32,
                     unsigned long long* out64, const uint32_t* active, uint32_t* npairs,
-                    uint32_t* overflow, cudaStream_t s) {
+                    uint32_t* overflow, cudaStream_t s, bool hinted = false) {
   GramSource src{};
   src.perturb = false;
   src.phi = f32;
   src.normalize = false;
   src.gate = active;
-  TRY_CUDA(launch_gram_f32(h->N, h->d, 1, src, h->cert32, nullptr, h->num_sms, s));
-  PairFilter pf{h->cert32, certify_margin(h->d), h->pairs, npairs, kPairCap, overflow};
+  const float slack = hinted ? (float)certify_margin_mu2(h->d) : 0.f;
+  if (!hinted) TRY_CUDA(launch_gram_f32(h->N, h->d, 1, src, h->cert32, nullptr, h->num_sms, s));
+  PairFilter pf{h->cert32, certify_margin(h->d), h->pairs, npairs, kPairCap, overflow, nullptr,
+                slack};
   TRY_CUDA(launch_gram_f32(h->N, h->d, 1, src, h->cert32 + 1, &pf, h->num_sms, s));
-  TRY_CUDA(launch_pairs64(active, npairs, h->pairs, kPairCap, h->d, f64, out64, s));
+  TRY_CUDA(launch_pairs64(active, npairs, h->pairs, kPairCap, h->d, f64, out64, s,
+                          hinted ? h->cert32 : nullptr, hinted ? h->cert32 + 1 : nullptr, slack,
+                          hinted ? overflow : nullptr));
   GramSource full{};
   full.perturb = false;
   full.phi = f64;
@@ -308,11 +316,12 @@ int enqueue_iteration_finish(trstmi_instance* h, cudaStream_t s) {
     src.planes = h->planes_top;
     TRY_CUDA(launch_gram_f32(N, d, k, src, h->mu2_top, nullptr, h->num_sms, s));
     TRY_CUDA(launch_materialize64(N, d, h->seed, st, h->topk, h->mu2_top, k, h->phi64,
-                                  h->cand64, h->cand32, s));
+                                  h->cand64, h->cand32, s, h->cert32));
     // cert32[0..1] and cert64 were zeroed by iter_begin (contiguous block);
-    // the passes run only for a survivor the rule could accept (st->certify)
+    // the passes run only for a survivor the rule could accept (st->certify),
+    // from the survivor's binary32 score as the filter hint
     int rc = enqueue_certify(h, h->cand64, h->cand32, h->cert64, &st->certify, &st->npairs,
-                             &st->overflow, s);
+                             &st->overflow, s, true);
     if (rc) return rc;
     TRY_CUDA(launch_decide_certified(st, h->cert64, h->trace, s));
     TRY_CUDA(launch_commit_copy(N, d, st, h->cand64, h->cand32, h->phi64, h->phi32, s));

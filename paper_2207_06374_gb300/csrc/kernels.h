@@ -120,11 +120,15 @@ struct PairFilter {
   // nullable: binary64 bits of a factor the margin is multiplied by (the
   // largest squared column norm of a frame whose columns are not unit)
   const unsigned long long* scale_bits;
+  // mu2_ref is a hint within this much (on mu^2) of the frame's binary32 max
+  // rather than that max itself (0: it is the max)
+  float ref_slack_mu2;
 };
 
-// Lower end of the kept range of |G|: sqrt(binary32 max) - margin (scaled).
+// Lower end of the kept range of |G|: sqrt(binary32 max, less the hint's
+// slack) - margin (scaled).
 __device__ __forceinline__ float filter_lo(const PairFilter& f) {
-  const float ref = sqrtf(__uint_as_float(*f.mu2_ref));
+  const float ref = sqrtf(fmaxf(__uint_as_float(*f.mu2_ref) - f.ref_slack_mu2, 0.0f));
   float margin = f.margin;
   if (f.scale_bits) margin = (float)((double)margin * __longlong_as_double((long long)*f.scale_bits));
   return fmaxf(ref - margin, 0.0f);
@@ -158,13 +162,21 @@ cudaError_t launch_commit_f64(int N, int d, uint64_t seed, DevState* st, double2
 // screen mode
 cudaError_t launch_topk(DevState* st, const unsigned int* mu2_screen, int K, int k,
                         uint32_t* topk, unsigned int* mu2_top, cudaStream_t s);
+// hint_out (nullable): receives the chosen survivor's binary32 score bits
+// when it is certified (the certification's filter hint).
 cudaError_t launch_materialize64(int N, int d, uint64_t seed, DevState* st,
                                  const uint32_t* topk, const unsigned int* mu2_top, int k,
                                  const double2* phi64, double2* cand64, float2* cand32,
-                                 cudaStream_t s);
+                                 cudaStream_t s, unsigned int* hint_out = nullptr);
+// hint_bits / own_bits (nullable): the filter pass ran from a hint (its
+// slack hint_slack_mu2) instead of the frame's binary32 max; if the hint less
+// its slack exceeds the pass's own max (own_bits), the kept set may miss the
+// maximum pair and *overflow is set, so the full binary64 pass runs.
 cudaError_t launch_pairs64(const uint32_t* active, const uint32_t* npairs, const uint2* pairs,
                            uint32_t cap, int d, const double2* frame64, unsigned long long* out,
-                           cudaStream_t s);
+                           cudaStream_t s, const unsigned int* hint_bits = nullptr,
+                           const unsigned int* own_bits = nullptr, float hint_slack_mu2 = 0.f,
+                           uint32_t* overflow = nullptr);
 cudaError_t launch_decide_certified(DevState* st, const unsigned long long* mu2_64,
                                     TraceRowDev* trace, cudaStream_t s);
 cudaError_t launch_commit_copy(int N, int d, DevState* st, const double2* cand64,

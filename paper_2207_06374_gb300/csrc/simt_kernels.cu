@@ -143,37 +143,29 @@ __device__ bool gen_column_warp(const typename Cplx<T>::type* phi, int d, int j,
   const int P = (d + 1) >> 1;
   const typename Cplx<T>::type* col = phi ? phi + (size_t)j * d : nullptr;
   typename Cplx<T>::type* o = out + (size_t)j * d;
+  // one entry per lane (the two lanes of an entry pair both run its Philox
+  // call), so every lane carries a Box-Muller transform
   T s = T(0);
-  for (int p = lane; p < P; p += 32) {
+  for (int i = lane; i < d; i += 32) {
+    const int p = i >> 1, h = i & 1;
     const PhiloxOut u = philox4x32_10((uint32_t)j * (uint32_t)P + (uint32_t)p, c, t, tag, k0, k1);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int i = 2 * p + h;
-      if (i < d) {
-        T zr, zi;
-        cn_draw<T>(u.x[2 * h], u.x[2 * h + 1], zr, zi);
-        T xr = zr, xi = zi;
-        if (col) {
-          const auto v = col[i];
-          xr = add_rn(v.x, mul_rn(delta, zr));
-          xi = add_rn(v.y, mul_rn(delta, zi));
-        }
-        o[i].x = xr;
-        o[i].y = xi;
-        s = add_rn(s, add_rn(mul_rn(xr, xr), mul_rn(xi, xi)));
-      }
+    T zr, zi;
+    cn_draw<T>(u.x[2 * h], u.x[2 * h + 1], zr, zi);
+    T xr = zr, xi = zi;
+    if (col) {
+      const auto v = col[i];
+      xr = add_rn(v.x, mul_rn(delta, zr));
+      xi = add_rn(v.y, mul_rn(delta, zi));
     }
+    o[i].x = xr;
+    o[i].y = xi;
+    s = add_rn(s, add_rn(mul_rn(xr, xr), mul_rn(xi, xi)));
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if (!(s > T(0))) return false;
   const T nrm = sqrt_rn(s);
-  for (int p = lane; p < P; p += 32)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int i = 2 * p + h;
-      if (i < d) { o[i].x = div_rn(o[i].x, nrm); o[i].y = div_rn(o[i].y, nrm); }
-    }
+  for (int i = lane; i < d; i += 32) { o[i].x = div_rn(o[i].x, nrm); o[i].y = div_rn(o[i].y, nrm); }
   return true;
 }
 
@@ -403,12 +395,9 @@ __global__ void __launch_bounds__(256, 3) k_gram_planes(const GramArgs<float> a,
 
 // Candidates drawn once for the tile pass.  Many columns (the K candidates of
 // an iteration): k_gen_planes_f32, one thread per column running gen_column.
-// Few columns (the top-k survivors), where that leaves most SMs idle: two
-// steps with gen_column's arithmetic -- k_draw_planes_f32 spreads the draws
-// (Philox, Box-Muller, phi + delta z) over (candidate, column, entry pair)
-// items, k_norm_planes_f32 forms each column's squared norm in the same
-// sequential order over i and divides.  Both give every value the bits
-// gen_column gives it.
+// Few columns (the top-k survivors), where that leaves most SMs idle:
+// k_draw_planes_tiled_f32 (below) spreads the draws over (column, entry pair)
+// items and gives every value the bits gen_column gives it.
 struct PlanesDraw {
   int N, d, P, count;
   const float2* phi;
@@ -443,55 +432,63 @@ __global__ void k_gen_planes_f32(PlanesDraw a) {
     atomicOr(&a.st->error, (uint32_t)kErrZeroColumn);
 }
 
-__global__ void k_draw_planes_f32(PlanesDraw a) {
+// Few columns, one pass: a CTA takes 32 consecutive columns of one slot.  Its
+// threads draw the (column, entry pair) items (Philox, Box-Muller, phi +
+// delta z) into shared memory as [part][i][column]; thread t < 32 then forms
+// column t's squared norm in gen_column's order (i ascending) and all threads
+// write the divided entries to the planes, 32 consecutive columns per row, so
+// the stores are coalesced.  Every value has the bits gen_column gives it.
+constexpr int kDrawCols = 32;
+__global__ void __launch_bounds__(256) k_draw_planes_tiled_f32(PlanesDraw a) {
+  extern __shared__ __align__(16) float xs[];   // [2][d][kDrawCols]
+  __shared__ float nrm[kDrawCols];
+  __shared__ int bad[kDrawCols];
   if (!planes_draw_setup(a)) return;
-  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long per = (long long)a.N * a.P;
-  if (g >= (long long)a.count * per) return;
-  const int slot = (int)(g / per);
-  const int rem = (int)(g - (long long)slot * per);
-  const int j = rem / a.P, p = rem - j * a.P;
+  const int d = a.d, N = a.N, P = a.P;
+  const int tiles = (N + kDrawCols - 1) / kDrawCols;
+  const int slot = blockIdx.x / tiles, c0 = (blockIdx.x - slot * tiles) * kDrawCols;
   const uint32_t c = a.cand_list ? a.cand_list[slot] : a.c0 + (uint32_t)slot;
-  const int d = a.d, N = a.N;
-  float* pre = a.planes + (size_t)slot * 2 * d * N;
-  float* pim = pre + (size_t)d * N;
-  const PhiloxOut u = philox4x32_10((uint32_t)j * (uint32_t)a.P + (uint32_t)p, c, a.t, 0u,
-                                    seed_lo(a.seed), seed_hi(a.seed));
+  float* xre = xs;
+  float* xim = xs + (size_t)d * kDrawCols;
+  for (int q = threadIdx.x; q < kDrawCols * P; q += blockDim.x) {
+    const int cl = q % kDrawCols, p = q / kDrawCols, j = c0 + cl;
+    if (j >= N) continue;
+    const PhiloxOut u = philox4x32_10((uint32_t)j * (uint32_t)P + (uint32_t)p, c, a.t, 0u,
+                                      seed_lo(a.seed), seed_hi(a.seed));
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int i = 2 * p + h;
-    if (i < d) {
-      float zr, zi;
-      cn_draw<float>(u.x[2 * h], u.x[2 * h + 1], zr, zi);
-      const float2 v = a.phi[(size_t)j * d + i];
-      pre[(size_t)i * N + j] = add_rn(v.x, mul_rn(a.delta, zr));
-      pim[(size_t)i * N + j] = add_rn(v.y, mul_rn(a.delta, zi));
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * p + h;
+      if (i < d) {
+        float zr, zi;
+        cn_draw<float>(u.x[2 * h], u.x[2 * h + 1], zr, zi);
+        const float2 v = a.phi[(size_t)j * d + i];
+        xre[i * kDrawCols + cl] = add_rn(v.x, mul_rn(a.delta, zr));
+        xim[i * kDrawCols + cl] = add_rn(v.y, mul_rn(a.delta, zi));
+      }
     }
   }
-}
-
-__global__ void k_norm_planes_f32(PlanesDraw a) {
-  if (!planes_draw_setup(a)) return;
-  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (g >= (long long)a.count * a.N) return;
-  const int slot = (int)(g / a.N), j = (int)(g - (long long)slot * a.N);
-  const int d = a.d, N = a.N;
+  __syncthreads();
+  if (threadIdx.x < kDrawCols) {
+    const int cl = threadIdx.x;
+    float sq = 0.f;
+    if (c0 + cl < N)
+      for (int i = 0; i < d; ++i) {
+        const float xr = xre[i * kDrawCols + cl], xi = xim[i * kDrawCols + cl];
+        sq = add_rn(sq, add_rn(mul_rn(xr, xr), mul_rn(xi, xi)));
+      }
+    bad[cl] = (c0 + cl < N) && !(sq > 0.f);
+    nrm[cl] = sq > 0.f ? sqrt_rn(sq) : 0.f;
+    if (bad[cl] && a.st) atomicOr(&a.st->error, (uint32_t)kErrZeroColumn);
+  }
+  __syncthreads();
   float* pre = a.planes + (size_t)slot * 2 * d * N;
   float* pim = pre + (size_t)d * N;
-  float s = 0.f;
-  for (int i = 0; i < d; ++i) {
-    const float xr = pre[(size_t)i * N + j], xi = pim[(size_t)i * N + j];
-    s = add_rn(s, add_rn(mul_rn(xr, xr), mul_rn(xi, xi)));
-  }
-  if (!(s > 0.f)) {
-    for (int i = 0; i < d; ++i) { pre[(size_t)i * N + j] = 0.f; pim[(size_t)i * N + j] = 0.f; }
-    if (a.st) atomicOr(&a.st->error, (uint32_t)kErrZeroColumn);
-    return;
-  }
-  const float nrm = sqrt_rn(s);
-  for (int i = 0; i < d; ++i) {
-    pre[(size_t)i * N + j] = div_rn(pre[(size_t)i * N + j], nrm);
-    pim[(size_t)i * N + j] = div_rn(pim[(size_t)i * N + j], nrm);
+  for (int q = threadIdx.x; q < d * kDrawCols; q += blockDim.x) {
+    const int cl = q % kDrawCols, i = q / kDrawCols, j = c0 + cl;
+    if (j >= N) continue;
+    const bool z = bad[cl] != 0;
+    pre[(size_t)i * N + j] = z ? 0.f : div_rn(xre[q], nrm[cl]);
+    pim[(size_t)i * N + j] = z ? 0.f : div_rn(xim[q], nrm[cl]);
   }
 }
 
@@ -507,11 +504,9 @@ cudaError_t launch_gen_planes_f32(int N, int d, int count, const float2* phi, ui
     k_gen_planes_f32<<<(unsigned)((cols + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
   }
-  const long long items = cols * a.P;
-  k_draw_planes_f32<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_norm_planes_f32<<<(unsigned)((cols + 255) / 256), 256, 0, s>>>(a);
+  const long long tiles = (long long)count * ((N + kDrawCols - 1) / kDrawCols);
+  const size_t smem = (size_t)2 * d * kDrawCols * sizeof(float);
+  k_draw_planes_tiled_f32<<<(unsigned)tiles, 256, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -799,9 +794,58 @@ __global__ void k_topk(DevState* st, const unsigned int* mu2, int K, int k, uint
   }
 }
 
+// The same k smallest keys for K <= 1024 without rounds over the block:
+// every thread holds one key ((score bits << 32) | c, all distinct); each warp
+// sorts its 32 keys with a register bitonic network (shuffles) and keeps its k
+// smallest, sorted, in shared memory; warp 0 then merges the 32 sorted lists,
+// one list per lane, by k rounds of a warp minimum over the lists' heads.
+constexpr int kSortMax = 1024;
+__device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int m) {
+  const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
+  const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
+  return ((unsigned long long)hi << 32) | lo;
+}
+__global__ void __launch_bounds__(1024) k_topk_sort(DevState* st, const unsigned int* mu2, int K,
+                                                    int k, uint32_t* topk, unsigned int* mu2_top) {
+  if (!st->active) return;
+  __shared__ unsigned long long lists[32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, c = threadIdx.x;
+  unsigned long long key = c < K ? (((unsigned long long)mu2[c] << 32) | (unsigned)c) : ~0ull;
+  // ascending bitonic sort of the warp's 32 keys, lane order
+#pragma unroll
+  for (int w = 2; w <= 32; w <<= 1) {
+#pragma unroll
+    for (int j = w >> 1; j > 0; j >>= 1) {
+      const unsigned long long o = shfl_xor_u64(key, j);
+      const bool lower = (lane & j) == 0, up = (lane & w) == 0;
+      key = (lower == up) ? (o < key ? o : key) : (o > key ? o : key);
+    }
+  }
+  if (lane < k) lists[warp][lane] = key;     // k <= 32
+  __syncthreads();
+  if (warp != 0) return;
+  const int nw = (min(K, 1024) + 31) >> 5;
+  int head = 0;
+  for (int r = 0; r < k; ++r) {
+    const unsigned long long mine = (lane < nw && head < k) ? lists[lane][head] : ~0ull;
+    unsigned long long best = mine;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ov = shfl_xor_u64(best, o);
+      best = ov < best ? ov : best;
+    }
+    if (mine == best) ++head;            // keys are distinct: exactly one lane pops
+    if (lane == 0) {
+      topk[r] = (uint32_t)(best & 0xffffffffull);
+      if (!st->use_screen) mu2_top[r] = (unsigned int)(best >> 32);
+    }
+  }
+}
+
 cudaError_t launch_topk(DevState* st, const unsigned int* mu2_screen, int K, int k,
                         uint32_t* topk, unsigned int* mu2_top, cudaStream_t s) {
-  k_topk<<<1, 1024, 0, s>>>(st, mu2_screen, K, k, topk, mu2_top);
+  if (K <= kSortMax && k <= 32) k_topk_sort<<<1, 1024, 0, s>>>(st, mu2_screen, K, k, topk, mu2_top);
+  else k_topk<<<1, 1024, 0, s>>>(st, mu2_screen, K, k, topk, mu2_top);
   return cudaGetLastError();
 }
 
@@ -809,7 +853,8 @@ cudaError_t launch_topk(DevState* st, const unsigned int* mu2_screen, int K, int
 // binary64 from the binary64 frame, plus its binary32 rounding.
 __global__ void k_materialize64(int N, int d, uint64_t seed, DevState* st,
                                 const uint32_t* topk, const unsigned int* mu2_top, int k,
-                                const double2* phi64, double2* cand64, float2* cand32) {
+                                const double2* phi64, double2* cand64, float2* cand32,
+                                unsigned int* hint_out) {
   if (!st->active) return;
   unsigned int bv = mu2_top[0];
   uint32_t bc = topk[0];
@@ -827,6 +872,7 @@ __global__ void k_materialize64(int N, int d, uint64_t seed, DevState* st,
     st->cstar = bc;
     st->mu2_screen = m32;
     st->certify = cert ? 1u : 0u;
+    if (hint_out && cert) *hint_out = bv;
   }
   if (!cert || j >= N) return;
   const bool ok = gen_column_warp<double>(phi64, d, j, seed, bc, st->t + 1u, 0u, st->delta_used,
@@ -842,17 +888,23 @@ __global__ void k_materialize64(int N, int d, uint64_t seed, DevState* st,
 cudaError_t launch_materialize64(int N, int d, uint64_t seed, DevState* st,
                                  const uint32_t* topk, const unsigned int* mu2_top, int k,
                                  const double2* phi64, double2* cand64, float2* cand32,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, unsigned int* hint_out) {
   const size_t threads = (size_t)N * 32;
   k_materialize64<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(N, d, seed, st, topk, mu2_top,
-                                                                   k, phi64, cand64, cand32);
+                                                                   k, phi64, cand64, cand32,
+                                                                   hint_out);
   return cudaGetLastError();
 }
 
 // binary64 |G_jk|^2 of the preselected pairs.
 __global__ void k_pairs64(const uint32_t* active, const uint32_t* npairs, const uint2* pairs,
-                          uint32_t cap, int d, const double2* f, unsigned long long* out) {
+                          uint32_t cap, int d, const double2* f, unsigned long long* out,
+                          const unsigned int* hint_bits, const unsigned int* own_bits,
+                          float hint_slack_mu2, uint32_t* overflow) {
   if (active && !*active) return;
+  if (hint_bits && blockIdx.x == 0 && threadIdx.x == 0 &&
+      fmaxf(__uint_as_float(*hint_bits) - hint_slack_mu2, 0.0f) > __uint_as_float(*own_bits))
+    atomicExch(overflow, 1u);
   const uint32_t n = min(*npairs, cap);
   double m = 0.0;
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
@@ -874,8 +926,11 @@ __global__ void k_pairs64(const uint32_t* active, const uint32_t* npairs, const 
 
 cudaError_t launch_pairs64(const uint32_t* active, const uint32_t* npairs, const uint2* pairs,
                            uint32_t cap, int d, const double2* frame64, unsigned long long* out,
-                           cudaStream_t s) {
-  k_pairs64<<<64, 256, 0, s>>>(active, npairs, pairs, cap, d, frame64, out);
+                           cudaStream_t s, const unsigned int* hint_bits,
+                           const unsigned int* own_bits, float hint_slack_mu2,
+                           uint32_t* overflow) {
+  k_pairs64<<<64, 256, 0, s>>>(active, npairs, pairs, cap, d, frame64, out, hint_bits, own_bits,
+                               hint_slack_mu2, overflow);
   return cudaGetLastError();
 }
 
@@ -1092,6 +1147,7 @@ __global__ void __launch_bounds__(256, TileCtas<T>::value) k_batch_score(const S
           pf.cap = sd.pair_cap;
           pf.overflow = &const_cast<DevState*>(st)->overflow;
           pf.scale_bits = nullptr;
+          pf.ref_slack_mu2 = 0.f;
           const float lo2 = filter_lo(pf);
           thr = (T)(lo2 * lo2);
           filter = &pf;
@@ -1546,6 +1602,7 @@ cudaError_t init_kernel_attributes() {
   if ((e = allow_max_dynamic_smem(k_batch_score<double, 1>, optin)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_batch_resident<float>, optin)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_batch_resident<double>, optin)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_draw_planes_tiled_f32, optin)) != cudaSuccess) return e;
   if ((e = init_lse_attributes(optin)) != cudaSuccess) return e;
   if ((e = init_diag_attributes(optin)) != cudaSuccess) return e;
   return init_screen_attributes(optin);
