@@ -246,6 +246,17 @@ def profiled_traffic(precision):
         return None
 
 
+_ALU_PEAKS = {}
+
+
+def alu_peaks(T):
+    """FFMA / DFMA / tf32 / bf16 MMA rates measured on this GPU by the
+    library's own loops (trstmi_measure_peaks), once per process."""
+    if not _ALU_PEAKS:
+        _ALU_PEAKS.update(T.measure_peaks())
+    return dict(_ALU_PEAKS)
+
+
 def fp32_alu_peak_tflops(sm_mhz):
     # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -277,10 +288,18 @@ def cpu_baseline(d, N, K, steps=1):
         O.score(phi, SEED, 0.1, 1 + s, 0, count, nthreads=cores)
     dt = time.perf_counter() - t0
     value = steps * count * per_cand / dt
+    # the binary32 plain-loop variant on a sample of the same candidates
+    count32 = int(max(cores, min(K, count)))
+    t1 = time.perf_counter()
+    O.score_f32(phi, SEED, 0.1, 1, 0, count32, nthreads=cores)
+    dt32 = time.perf_counter() - t1
     return {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
             "sample": f"{count} of the {K} candidates of iteration t=1..{steps} (d={d}, N={N}) "
                       f"scored by the fp64 oracle (generation + all-pairs |G|^2 max), "
-                      f"{steps} step(s), {dt:.2f} s"}
+                      f"{steps} step(s), {dt:.2f} s",
+            "fp32_variant": {"value": count32 * per_cand / dt32, "unit": "pairs/s",
+                             "cores": cores, "kind": "oracle fp32 plain loops",
+                             "sample": f"{count32} candidates of iteration 1, {dt32:.2f} s"}}
 
 
 def lse_frames(count, d, N, seed):
@@ -514,7 +533,7 @@ def main():
     ap.add_argument("--no-side", action="store_true", help="skip the fp32 side-by-side run")
     ap.add_argument("--requests", type=int, default=100, help="serving: requests in the stream")
     ap.add_argument("--budget", type=int, default=50, help="serving: iterations per request")
-    ap.add_argument("--serve-k", type=int, default=64,
+    ap.add_argument("--serve-k", type=int, default=256,
                     help="serving: candidates per iteration of every request")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--shard", action="store_true",
@@ -628,9 +647,22 @@ def main():
     seed = SEED if sharded else SEED + rank
     with Clocks(local) as clk:
         s, times, wall = timed_run(prec, args.steps, args.warmup, seed)
-        # live per-kernel timing of the dominant (scoring) kernel on the same stream
-        kernel_ms = s.profile_score(prec, launches=5, delta=0.1, flush_bytes=L2_FLUSH_BYTES)
+        # live per-kernel timing of the dominant (scoring) kernel on the same
+        # stream: 50 launches, L2 flushed before each
+        kernel_ms = s.profile_score(prec, launches=50, delta=0.1, flush_bytes=L2_FLUSH_BYTES)
     clocks = clk.summary()
+    # the same kernel back to back for >= 2 s (power-capped steady state), with
+    # its own clock samples, against the sustained peak
+    sustained = None
+    if prec in ("bf16", "tf32") and not sharded:
+        with Clocks(local) as clk2:
+            t_s0 = time.perf_counter()
+            runs = []
+            while time.perf_counter() - t_s0 < 2.0:
+                runs.append(s.profile_score(prec, launches=200, delta=0.1, flush_bytes=0))
+            t_sus = time.perf_counter() - t_s0
+        sustained = {"seconds": t_sus, "launches": 200 * len(runs),
+                     "kernel_ms": sum(runs) / len(runs), "clocks": clk2.summary()}
     t_dev = sum(times)
     if dist:
         tt = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
@@ -673,22 +705,31 @@ def main():
 
     peaks, peak_kind = measured_peaks()
     flops_launch = pps * flops_per_pair(d)
+    own = alu_peaks(T)
     if prec == "bf16":
         peak = peaks.get("bf16_tflops", 1900.0)
         roof = {"bound": "tensor", "unit": "TFLOP/s"}
         peak_note = f"bf16_tflops burst ({peak_kind})"
     elif prec == "tf32":
-        # tf32 dense runs at half the bf16 rate (nominal 1.1 of 2.25 PFLOP/s)
-        peak = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25
+        peak = own["tf32_tflops"]
         roof = {"bound": "tensor", "unit": "TFLOP/s"}
-        peak_note = f"bf16_tflops burst ({peak_kind}) x 1.1 / 2.25 (nominal tf32 / bf16 ratio)"
+        peak_note = ("tf32 tcgen05 MMA loop measured in this run (trstmi_measure_peaks: "
+                     "M=128 N=256 from shared memory on every SM)")
     else:
-        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-        peak = fp32_alu_peak_tflops(sm_mhz) if prec == "fp32" else fp32_alu_peak_tflops(sm_mhz) / 64
+        peak = own["fp32_tflops"] if prec == "fp32" else own["fp64_tflops"]
         roof = {"bound": "alu", "unit": "TFLOP/s"}
-        peak_note = (f"{prec} FMA peak derived: 152 SMs x "
-                     f"{'128' if prec == 'fp32' else '2'} lanes x 2 flops x {sm_mhz} MHz")
+        peak_note = (f"{'FFMA' if prec == 'fp32' else 'DFMA'} loop measured in this run "
+                     "(trstmi_measure_peaks: 32 warps per SM, 8 independent chains)")
     achieved = flops_launch / (kernel_ms * 1e-3) / 1e12
+    if sustained:
+        sus_peak = (peaks.get("bf16_tflops_sustained", 1700.0) if prec == "bf16"
+                    else own["tf32_tflops"] * peaks.get("bf16_tflops_sustained", 1700.0)
+                    / peaks.get("bf16_tflops", 1900.0))
+        sustained["achieved"] = flops_launch / (sustained["kernel_ms"] * 1e-3) / 1e12
+        sustained["peak"] = sus_peak
+        sustained["frac"] = sustained["achieved"] / sus_peak
+        sustained["peak_source"] = ("bf16_tflops_sustained (" + peak_kind + ")" if prec == "bf16"
+                                    else "measured tf32 loop x bf16 sustained/burst ratio")
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
                  "traffic": profiled_traffic("bf16w" if prec == "bf16" and d > 32 else prec),
                  "kernel": (f"k_screen ({prec}{', wide' if d > 32 else ''})"
@@ -719,7 +760,10 @@ def main():
                                        "(MAX all-reduce of the K-entry score vector)")
                                       if sharded else f"independent instance per GPU x{ws}"},
             "roofline": roof, "gpu_launches": kernels_per_step(prec) * args.steps,
-            "e2e": e2e, "clocks": clocks, "mu_after": s.coherence()[0]}
+            "e2e": e2e, "clocks": clocks, "mu_after": s.coherence()[0],
+            "measured_alu_peaks_tflops": own}
+    if sustained:
+        line["sustained"] = sustained
     if side:
         line["side_by_side_fp32"] = side
     s.close()
@@ -782,7 +826,7 @@ def run_batched(args, ws, rank, local, dist, torch, T):
     widths = b.tile_widths()
     peaks, peak_kind = measured_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = fp32_alu_peak_tflops(sm_mhz)
+    peak = alu_peaks(T)["fp32_tflops"]
     achieved = flops / (kernel_ms * 1e-3) / 1e12
     mus, its = b.mu()
     ngroups = len(set(widths))
@@ -807,7 +851,7 @@ def run_batched(args, ws, rank, local, dist, torch, T):
                                     if set(widths) == {0} else
                                     "k_batch_resident / k_batch_score (all groups of one iteration)"),
                          "kernel_ms": kernel_ms, "flops_per_launch": flops,
-                         "peak_source": f"fp32 FMA peak derived: 152 SMs x 128 lanes x 2 flops x {sm_mhz} MHz"},
+                         "peak_source": "FFMA loop measured in this run (trstmi_measure_peaks)"},
             "gpu_launches": (4 + ngroups) * args.steps,
             "e2e": {"value": ws * e2e_steps * pairs / t_e2e, "unit": "pairs/s",
                     # trstmi_batch_step and trstmi_batch_mu each read the 512 device
@@ -915,7 +959,7 @@ def run_objective(args, ws, rank, local, dist, torch, T):
     ms64 = e0.elapsed_time(e1)
     peaks, peak_kind = measured_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = fp32_alu_peak_tflops(sm_mhz)
+    peak = alu_peaks(T)["fp32_tflops"]
     achieved = flops / (kernel_ms * 1e-3) / 1e12
     line = {"metric": metric_of("objective_d32_n1024"),
             "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
@@ -933,8 +977,7 @@ def run_objective(args, ws, rank, local, dist, torch, T):
                          "kernel": "one objective call: k_lse_prepare, k_gram_planes (s), "
                                    "k_lse_tile, k_lse_total, k_lse_finish",
                          "kernel_ms": kernel_ms, "flops_per_launch": flops,
-                         "peak_source": f"fp32 FMA peak derived: 152 SMs x 128 lanes x 2 flops "
-                                        f"x {sm_mhz} MHz"},
+                         "peak_source": "FFMA loop measured in this run (trstmi_measure_peaks)"},
             "gpu_launches": 5 * args.steps,
             "e2e": {"value": ws * e2e_steps * pairs / t_e2e, "unit": "pairs/s",
                     "h2d_bytes_per_step": int(flat.nbytes),
@@ -984,7 +1027,7 @@ def run_trust_region(args, ws, rank, local, dist, torch, T):
     flops = evals * pairs * 32 * d
     peaks, peak_kind = measured_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = fp32_alu_peak_tflops(sm_mhz) / 64
+    peak = alu_peaks(T)["fp64_tflops"]
     achieved = flops / dt / 1e12
     line = {"metric": metric_of("trust_region_d32_n1024"),
             "value": ws * iters / dt, "unit": "iterations/s", "n_gpus": ws, "steps": iters,
@@ -1004,7 +1047,7 @@ def run_trust_region(args, ws, rank, local, dist, torch, T):
                                    "timed with the host-side scalar logic between them",
                          "kernel_ms": 1e3 * dt / max(evals, 1),
                          "flops_per_launch": pairs * 32 * d,
-                         "peak_source": f"fp64 peak derived: 152 SMs x 2 lanes x 2 flops x {sm_mhz} MHz"},
+                         "peak_source": "DFMA loop measured in this run (trstmi_measure_peaks)"},
             "gpu_launches": evals * 5 + (iters + hv) * 8,
             "e2e": {"value": ws * iters / dt, "unit": "iterations/s",
                     "h2d_bytes_per_step": int(16 * d * N / max(iters, 1)),
@@ -1061,7 +1104,7 @@ def run_table2_all(args, ws, rank, local, dist, torch, T):
                                   "fp64_tflops": fl / dt / 1e12}
     clocks = clk.summary()
     peaks, _ = measured_peaks()
-    peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0)) / 64
+    peak = alu_peaks(T)["fp64_tflops"]
     achieved = flops / total / 1e12
     paper_total = sum(v[0] for v in TABLE2_PAPER.values())
     line = {"metric": metric_of("table2_all"),
@@ -1079,8 +1122,7 @@ def run_table2_all(args, ws, rank, local, dist, torch, T):
                                    "flops of every trial's passes over the rows' summed "
                                    "wall time (rows with fewer trials than SMs, and the "
                                    "slowest trial of each row, leave SMs idle)",
-                         "peak_source": "fp64 peak derived: 152 SMs x 2 lanes x 2 flops x "
-                                        f"{peaks.get('sm_max_mhz', 2070.0)} MHz"},
+                         "peak_source": "DFMA loop measured in this run (trstmi_measure_peaks)"},
             "gpu_launches": 16,
             "e2e": {"value": total, "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0, "call": "trstmi_tr_multistart per row"},
@@ -1113,7 +1155,7 @@ def run_table2(args, ws, rank, local, dist, torch, T):
     t = sum(times) / len(times)
     peaks, _ = measured_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = fp32_alu_peak_tflops(sm_mhz) / 64
+    peak = alu_peaks(T)["fp64_tflops"]
     # the trials' passes, plus the winning trial's second run for its trace
     flops = resident_tr_flops(d, N, work) + resident_tr_flops(d, N, work[res.best:res.best + 1])
     achieved = flops / t / 1e12
@@ -1147,8 +1189,7 @@ def run_table2(args, ws, rank, local, dist, torch, T):
                          "flops_note": "algorithmic: 24 d P per objective-and-gradient pass, "
                                        "8 d P per objective-only pass (P = N(N-1)/2), from each "
                                        "trial's iteration and Hessian-product counts",
-                         "peak_source": f"fp64 peak derived: 152 SMs x 2 lanes x 2 flops x "
-                                        f"{sm_mhz} MHz"},
+                         "peak_source": "DFMA loop measured in this run (trstmi_measure_peaks)"},
             "gpu_launches": 2 * steps,
             "e2e": {"value": t, "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(16 * d * N + 8 * K),
@@ -1166,22 +1207,32 @@ def run_table2(args, ws, rank, local, dist, torch, T):
 
 
 def run_serving(args, ws, rank, local, dist, torch, T):
-    """Seeded Poisson stream of search requests (d ~ U{4..64}, N log-uniform on
-    [d+1, 4096], target 1.05 x Welch, K = 64) replayed into the serving loop in
-    the precision form (bf16 screen, fp32 re-score of the top 2, fp64
-    certification; shapes outside the screen's range rank in fp32); every
-    request runs to its target or its iteration budget.  Reported: p50 / p99
-    latency (submit -> done) and pairs scored per second of wall time; next to
-    it, the same requests served one at a time by the plain fp32
-    single-instance path (measured standalone run times, FIFO on the same
+    """Seeded stream of search requests (d ~ U{4..64}, N log-uniform on
+    [d+1, 4096], target 1.05 x Welch, K = --serve-k) served by the serving
+    loop in the precision form (bf16 screen, fp32 re-score of the top 2, fp64
+    certification); every request runs to its target or its iteration budget.
+
+    Three runs of the same requests: (1) all submitted at once, which gives the
+    drain rate (requests per second the GPU sustains); (2) Poisson arrivals at
+    0.7 x that rate, the headline: p50 / p99 latency (submit -> done) at a load
+    the GPU sustains, and pairs scored per second; (3) the recipe's 200/s,
+    with its offered-load ratio (above 1: the percentiles are queue drain).
+    Beside (2) and (3): the same arrivals through the loop with plain fp32
+    ranking and acceptance, and the requests run one at a time by the plain
+    fp32 single-instance path (measured run times, FIFO on the same
     arrival times)."""
     import threading
     from paper_2207_06374_gb300 import workloads as W
     K, prec, topk = args.serve_k, WORKLOADS["serving"][3], 2
-    reqs = W.serving_requests(args.requests, seed=11 + rank, rate_hz=args.rate)
+    base = W.serving_requests(args.requests, seed=11 + rank, rate_hz=args.rate)
     budget = args.budget
 
-    def serve(precision):
+    def at_rate(rate):
+        # the same requests, arrival gaps rescaled to the given mean rate
+        scale = args.rate / rate if rate > 0 else 0.0
+        return [dict(r, t_arrive=r["t_arrive"] * scale) for r in base]
+
+    def serve(precision, reqs):
         srv = T.Server(hbm_budget=8 << 30, max_slots=256, iters_per_round=10, K=K,
                        precision=precision, topk=topk, device=local, trace_cap=0)
         tickets = [None] * len(reqs)
@@ -1201,75 +1252,98 @@ def run_serving(args, ws, rank, local, dist, torch, T):
         wall = time.perf_counter() - t0
         stats = srv.stats()
         srv.close()
-        return results, wall, stats
+        lat = np.array([(res.t_done_ns - res.t_submit_ns) * 1e-9 for _, res, _ in results])
+        return results, wall, stats, lat
+
+    def pct(lat):
+        return {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                "max": float(lat.max())}
 
     # tile widths are measured once per (d, N) bucket and process; an untimed
-    # pass admits every request shape once (zero iterations) so that neither
-    # timed run pays for the measurements
-    srv = T.Server(hbm_budget=8 << 30, max_slots=256, iters_per_round=10, K=K,
-                   precision=prec, topk=topk, device=local, trace_cap=0)
-    warm = [srv.submit(r["N"], r["d"], r["seed"], 0) for r in reqs]
-    for t in warm:
-        srv.wait(t)
-    srv.close()
+    # pass admits every request shape once (zero iterations) so that no timed
+    # run pays for the measurements
+    for precision in (prec, "fp32"):
+        srv = T.Server(hbm_budget=8 << 30, max_slots=256, iters_per_round=10, K=K,
+                       precision=precision, topk=topk, device=local, trace_cap=0)
+        for t in [srv.submit(r["N"], r["d"], r["seed"], 0) for r in base]:
+            srv.wait(t)
+        srv.close()
+    # (1) drain rate
+    _, wall_drain, _, _ = serve(prec, at_rate(0))
+    drain_rate = len(base) / wall_drain
+    rate_sus = 0.7 * drain_rate
+    # (2) headline: 0.7 x the drain rate
+    reqs = at_rate(rate_sus)
     with Clocks(local) as clk:
-        results, wall, stats = serve(prec)
+        results, wall, stats, lat = serve(prec, reqs)
     clocks = clk.summary()
-    # the same stream through the serving loop with plain fp32 ranking and
-    # acceptance: the continuous-batching effect without the precision form
-    res32, wall32, stats32 = serve("fp32")
-    lat32 = np.array([(res.t_done_ns - res.t_submit_ns) * 1e-9 for _, res, _ in res32])
-    lat = np.array([(res.t_done_ns - res.t_submit_ns) * 1e-9 for _, res, _ in results])
+    _, wall32, stats32, lat32 = serve("fp32", reqs)
+    # (3) the recipe's rate
+    reqs_r = at_rate(args.rate)
+    res_r, wall_r, _, lat_r = serve(prec, reqs_r)
+    _, wall32_r, _, lat32_r = serve("fp32", reqs_r)
+
     ok = sum(1 for st, _, _ in results if st == T.TRSTMI_OK)
     pairs = sum(res.pairs_scored for _, res, _ in results)
-    n_screened = sum(1 for r in reqs
-                     if (r["d"] <= 32 and r["N"] <= 1536) or (r["d"] <= 64 and r["N"] <= 768))
+    pairs_r = sum(res.pairs_scored for _, res, _ in res_r)
+    n_screened = sum(1 for r in base if r["d"] <= 64)
     reached = sum(res.reached_target for _, res, _ in results)
     # plain fp32 single-instance path, one request at a time (same requests)
     run_s = []
-    for r in reqs:
+    for r in base:
         with T.Search(r["N"], r["d"], r["seed"], K=K, precision="fp32", device=local, trace_cap=0,
                       target_mu=1.05 * float(np.sqrt((r["N"] - r["d"]) / (r["d"] * (r["N"] - 1))))
                       if r["N"] > r["d"] else 0.0) as s:
             a = time.perf_counter()
             s.step(budget)
             run_s.append(time.perf_counter() - a)
-    free_at, seq_lat = 0.0, []
-    for r, rs in zip(reqs, run_s):
-        start = max(free_at, r["t_arrive"])
-        free_at = start + rs
-        seq_lat.append(free_at - r["t_arrive"])
-    seq_lat = np.array(seq_lat)
-    arrivals_span = reqs[-1]["t_arrive"] if reqs else 0.0
+
+    def sequential(rq):
+        free_at, out = 0.0, []
+        for r, rs in zip(rq, run_s):
+            start = max(free_at, r["t_arrive"])
+            free_at = start + rs
+            out.append(free_at - r["t_arrive"])
+        return np.array(out)
+
+    def span(rq):
+        return max(rq[-1]["t_arrive"], 1e-9) if rq else 1e-9
+
     line = {"metric": metric_of("serving"),
             "value": pairs / wall, "unit": "pairs/s", "n_gpus": ws, "steps": len(reqs),
             "warmup": 0, "ms_per_step": 1e3 * wall / max(len(reqs), 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec == "bf16" else "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if prec == "bf16" else "f32",
             "data": "synthetic (seeded Poisson request stream, seeded Philox frames)",
             "config": {"workload": "serving",
-                       "description": f"{len(reqs)} requests, Poisson {args.rate}/s, d ~ U{{4..64}}, "
-                                      f"N log-uniform [d+1, 4096], target 1.05 x Welch, budget "
-                                      f"{budget} iterations, K={K}, "
+                       "description": f"{len(reqs)} requests, Poisson at 0.7 x the measured drain "
+                                      f"rate ({rate_sus:.1f}/s), d ~ U{{4..64}}, N log-uniform "
+                                      f"[d+1, 4096], target 1.05 x Welch, budget {budget} "
+                                      f"iterations, K={K}, "
                                       + ("bf16 screen + fp32 top-2 re-score + fp64 certify"
                                          if prec == "bf16" else "fp32 ranking and acceptance"),
-                       "deviation": "the recipe's 10k requests x 2000 iterations exceed the GPU's "
-                                    "capacity many times over; request count and budget are scaled "
-                                    "down (CLI) and the run drains the whole stream",
-                       "requests": len(reqs), "rate_hz": args.rate, "budget_iters": budget, "K": K,
+                       "deviation": "the recipe's 10k requests x 2000 iterations at 200/s exceed "
+                                    "the GPU's capacity many times over; request count and budget "
+                                    "are scaled down (CLI) and the headline load is 0.7 x the "
+                                    "measured drain rate; the recipe's rate is reported beside it",
+                       "requests": len(reqs), "rate_hz": rate_sus, "budget_iters": budget, "K": K,
+                       "K_note": "K per iteration is not given by the recipe; K_serve = --serve-k",
                        "precision": prec, "topk": topk,
                        "max_slots": 256, "iters_per_round": 10},
-            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                          "max": float(lat.max())},
-            "requests_in_screen_range": n_screened,
-            "served_fp32": {"p50": float(np.percentile(lat32, 50)),
-                            "p99": float(np.percentile(lat32, 99)),
-                            "wall_s": wall32, "gpu_busy_s": stats32.gpu_busy_s,
-                            "pairs_per_s": sum(r.pairs_scored for _, r, _ in res32) / wall32},
-            "sequential_single_instance_fp32": {
-                "p50": float(np.percentile(seq_lat, 50)), "p99": float(np.percentile(seq_lat, 99)),
-                "sum_run_s": float(sum(run_s))},
+            "latency_s": pct(lat),
+            "drain": {"requests_per_s": drain_rate, "wall_s": wall_drain},
+            "offered_load_ratio": rate_sus / drain_rate,
+            "requests_screened_shapes": n_screened,
+            "served_fp32": dict(pct(lat32), wall_s=wall32, gpu_busy_s=stats32.gpu_busy_s),
+            "sequential_single_instance_fp32": dict(pct(sequential(reqs)),
+                                                    sum_run_s=float(sum(run_s))),
+            "recipe_rate": {"rate_hz": args.rate, "offered_load_ratio": args.rate / drain_rate,
+                            "latency_s": pct(lat_r), "pairs_per_s": pairs_r / wall_r,
+                            "wall_s": wall_r,
+                            "served_fp32": dict(pct(lat32_r), wall_s=wall32_r),
+                            "sequential_single_instance_fp32": pct(sequential(reqs_r)),
+                            "sequential_offered_load_ratio": float(sum(run_s)) / span(reqs_r)},
             "completed_ok": ok, "reached_target": reached,
-            "offered_load_ratio": float(sum(run_s) / max(arrivals_span, 1e-9)),
             "server": {"rounds": stats.rounds, "gpu_busy_s": stats.gpu_busy_s, "wall_s": wall},
             "gpu_launches": int(stats.kernel_launches), "clocks": clocks,
             "e2e": {"value": pairs / wall, "unit": "pairs/s", "h2d_bytes_per_step": 0,

@@ -58,8 +58,9 @@ typedef enum trstmi_precision {
      renormalised and certified in binary64; acceptance on the binary64 mu */
   TRSTMI_BF16_SCREEN = 2,
   /* as TRSTMI_BF16_SCREEN with fp16 screen operands: same tensor rate and
-     storage, 2^-11 instead of 2^-9 input rounding (screen error on mu <= 1e-3
-     instead of <= 4e-3 for unit vectors) */
+     storage, unit roundoff 2^-11 instead of 2^-8 (screen error on mu at most
+     2u + u^2 for unit columns: 9.8e-4 instead of 7.8e-3; measured on random
+     frames with d >= 2: below 1e-3 and 4e-3) */
   TRSTMI_FP16_SCREEN = 3,
   /* as TRSTMI_BF16_SCREEN with tf32 screen operands (fp32 values rounded to
      10 mantissa bits; kind::tf32 MMAs at half the bf16 tensor rate, twice the
@@ -83,10 +84,12 @@ typedef struct trstmi_options {
      screen while its radius is >= screen_min_delta, and with the binary32
      Gram of every candidate below it, where candidate coherences differ by
      less than the screen's resolution (default 0.01; 0 = always screen).
-     The screen takes d <= 32 with N <= 1536 (bf16, fp16) or N <= 768
-     (tf32), and 32 < d <= 64 with N <= 768 (bf16, fp16: two 128-byte
-     operand atoms per column).  Other shapes always rank with the binary32
-     Gram; the re-score and certification are unchanged. */
+     The screen takes d <= 32 (bf16, fp16, tf32) and 32 < d <= 64 (bf16,
+     fp16: two 128-byte operand atoms per column), 2 <= N <= 65536: up to
+     1536 columns (768 with two atoms) a candidate's blocks stay resident,
+     beyond that it is swept in bands of 1280 (512) columns whose right-hand
+     blocks stream through the shared memory.  Other shapes always rank with
+     the binary32 Gram; the re-score and certification are unchanged. */
   double screen_min_delta;
   void *stream;         /* cudaStream_t to issue on, or NULL */
   int32_t device;       /* CUDA device ordinal (default 0) */
@@ -488,6 +491,26 @@ int trstmi_mu2_frame(int N, int d, const double *phi, int precision, double *mu2
  */
 int trstmi_mu2_frame_noalloc(int N, int d, const double *phi_dev, double *mu2_dev,
                              void *stream);
+
+/* ---------------------------------------------------------- measurement
+ * The arithmetic rates that bound the library's kernels on this GPU, measured
+ * by short loops that keep one unit busy on every SM (the paper has no
+ * counterpart; these are the denominators of the roofline fractions the
+ * benchmark reports): binary32 and binary64 fused multiply-adds (32 warps
+ * per SM, eight independent chains per thread) and the tensor cores' bf16
+ * and tf32 MMAs (tcgen05, M = 128, N = 256, operands in shared memory).
+ * Runs on the caller's current device and the given stream (NULL = legacy
+ * default stream), a few tens of milliseconds; TRSTMI_ETIMEOUT if an MMA
+ * completion wait ran out (2 s).
+ */
+typedef struct trstmi_peaks {
+  double fp32_tflops;   /* 2 flops per FFMA */
+  double fp64_tflops;   /* 2 flops per DFMA */
+  double tf32_tflops;   /* 2 M N K per MMA */
+  double bf16_tflops;
+} trstmi_peaks;
+
+int trstmi_measure_peaks(trstmi_peaks *out, void *stream);
 
 /* ---------------------------------------------------------- certificates
  * What a frame proves about itself (binary64, on the GPU): its coherence and

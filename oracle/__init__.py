@@ -97,6 +97,7 @@ def lib():
             L.oracle_score.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _dp,
                                        ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32,
                                        ctypes.c_int, _dp, ctypes.c_int]
+            L.oracle_score_f32.argtypes = L.oracle_score.argtypes
             L.oracle_search.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                         ctypes.POINTER(OracleOpts), _dp, _dp, _dp,
                                         ctypes.c_uint32, ctypes.POINTER(ctypes.c_int),
@@ -129,7 +130,8 @@ def lib():
             L.oracle_tr_solve.argtypes = [ctypes.c_int, ctypes.c_int, _dp,
                                           ctypes.POINTER(TrOpts), ctypes.c_void_p, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int)]
-            for f in ("oracle_init", "oracle_candidate", "oracle_score", "oracle_search",
+            for f in ("oracle_init", "oracle_candidate", "oracle_score", "oracle_score_f32",
+                      "oracle_search",
                       "oracle_run", "oracle_replay", "oracle_lse", "oracle_cg_steihaug",
                       "oracle_lse_hv", "oracle_tr_solve"):
                 getattr(L, f).restype = ctypes.c_int
@@ -206,6 +208,18 @@ def score(phi: np.ndarray, seed: int, delta: float, t: int, c0: int, K: int,
     out = np.zeros(K)
     _check(lib().oracle_score(N, d, seed, _ptr(b), delta, t, c0, K, _ptr(out), nthreads),
            "score")
+    return out
+
+
+def score_f32(phi: np.ndarray, seed: int, delta: float, t: int, c0: int, K: int,
+              nthreads: int = 1) -> np.ndarray:
+    """mu^2 of K candidates by the binary32 plain-loop variant (a timing
+    baseline; equal to score() within binary32 rounding)."""
+    d, N = phi.shape
+    b = _flat(phi)
+    out = np.zeros(K)
+    _check(lib().oracle_score_f32(N, d, seed, _ptr(b), delta, t, c0, K, _ptr(out), nthreads),
+           "score_f32")
     return out
 
 

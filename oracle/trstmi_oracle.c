@@ -233,6 +233,111 @@ int oracle_score(int N, int d, uint64_t seed, const double *phi, double delta,
     return st;
 }
 
+/* ---------------------------------- binary32 plain-loop variant (timing)
+ * The same scoring in single precision with plain float loops: the frame
+ * rounded to float, each candidate entry phi + delta * Z with Z drawn by the
+ * same Philox words (U = (u + 1/2) 2^-32 rounded to float, Box-Muller with
+ * logf / sqrtf / cosf / sinf), columns normalised in float, mu^2 = max over
+ * j < k of |G_jk|^2 accumulated in float.  It serves as the CPU baseline of
+ * the binary32 path; its values agree with the binary64 oracle to binary32
+ * rounding (the tests pin that), not bit for bit with any GPU kernel. */
+
+static void gauss_entry_f32(uint64_t seed, int d, int i, int j, uint32_t c, uint32_t t,
+                            float *re, float *im)
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)j * (uint32_t)((d + 1) / 2) + (uint32_t)(i / 2), c, t, 0u};
+    uint32_t u[4];
+    oracle_philox4x32_10(ctr, key, u);
+    float ua = (float)u32_to_open01((i % 2 == 0) ? u[0] : u[2]);
+    float ub = (float)u32_to_open01((i % 2 == 0) ? u[1] : u[3]);
+    float r = sqrtf(-logf(ua));
+    float theta = 6.2831853071795864769f * ub;
+    *re = r * cosf(theta);
+    *im = r * sinf(theta);
+}
+
+typedef struct {
+    int N, d;
+    uint64_t seed;
+    const float *phi;
+    float delta;
+    uint32_t t, c0;
+    int begin, end;
+    double *mu2;
+    int status;
+} score32_job;
+
+static void *score32_worker(void *arg)
+{
+    score32_job *jb = (score32_job *)arg;
+    const int N = jb->N, d = jb->d;
+    float *x = (float *)malloc(sizeof(float) * 2 * (size_t)d * (size_t)N);
+    jb->status = ORACLE_OK;
+    if (!x) { jb->status = ORACLE_EINVAL; return NULL; }
+    for (int k = jb->begin; k < jb->end; ++k) {
+        const uint32_t c = jb->c0 + (uint32_t)k;
+        for (int j = 0; j < N; ++j) {
+            float s = 0.0f;
+            for (int i = 0; i < d; ++i) {
+                float zr, zi;
+                gauss_entry_f32(jb->seed, d, i, j, c, jb->t, &zr, &zi);
+                float a = jb->phi[2 * (j * d + i)] + jb->delta * zr;
+                float b = jb->phi[2 * (j * d + i) + 1] + jb->delta * zi;
+                x[2 * (j * d + i)] = a;
+                x[2 * (j * d + i) + 1] = b;
+                s += a * a + b * b;
+            }
+            if (!(s > 0.0f)) { jb->status = ORACLE_EINVAL; break; }
+            float nrm = sqrtf(s);
+            for (int i = 0; i < 2 * d; ++i) x[2 * j * d + i] /= nrm;
+        }
+        if (jb->status != ORACLE_OK) break;
+        float m = 0.0f;
+        for (int j = 0; j < N; ++j)
+            for (int l = j + 1; l < N; ++l) {
+                float gr = 0.0f, gi = 0.0f;
+                for (int i = 0; i < d; ++i) {
+                    float a = x[2 * (j * d + i)], b = x[2 * (j * d + i) + 1];
+                    float e = x[2 * (l * d + i)], f = x[2 * (l * d + i) + 1];
+                    gr += a * e + b * f;
+                    gi += a * f - b * e;
+                }
+                float g = gr * gr + gi * gi;
+                if (g > m) m = g;
+            }
+        jb->mu2[k] = (double)m;
+    }
+    free(x);
+    return NULL;
+}
+
+/* mu^2 of candidates c0 .. c0+K-1 of iteration t in binary32, split over
+ * nthreads (the frame phi is binary64 and rounded to float first). */
+int oracle_score_f32(int N, int d, uint64_t seed, const double *phi, double delta,
+                     uint32_t t, uint32_t c0, int K, double *mu2, int nthreads)
+{
+    if (N < 1 || d < 1 || K < 0 || !phi || (K > 0 && !mu2)) return ORACLE_EINVAL;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > K) nthreads = K > 0 ? K : 1;
+    float *f = (float *)malloc(sizeof(float) * 2 * (size_t)d * (size_t)N);
+    score32_job *jobs = (score32_job *)calloc((size_t)nthreads, sizeof(score32_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!f || !jobs || !th) { free(f); free(jobs); free(th); return ORACLE_EINVAL; }
+    for (size_t e = 0; e < 2 * (size_t)d * (size_t)N; ++e) f[e] = (float)phi[e];
+    for (int w = 0; w < nthreads; ++w)
+        jobs[w] = (score32_job){N, d, seed, f, (float)delta, t, c0,
+                                (int)((long long)K * w / nthreads),
+                                (int)((long long)K * (w + 1) / nthreads), mu2, 0};
+    for (int w = 1; w < nthreads; ++w) pthread_create(&th[w], NULL, score32_worker, &jobs[w]);
+    score32_worker(&jobs[0]);
+    for (int w = 1; w < nthreads; ++w) pthread_join(th[w], NULL);
+    int st = ORACLE_OK;
+    for (int w = 0; w < nthreads; ++w) if (jobs[w].status != ORACLE_OK) st = jobs[w].status;
+    free(f); free(jobs); free(th);
+    return st;
+}
+
 /* -------------------------------------------------------- the search */
 
 typedef struct {

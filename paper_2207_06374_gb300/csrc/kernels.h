@@ -190,7 +190,7 @@ cudaError_t launch_gen_candidate(int N, int d, uint64_t seed, uint32_t t, uint32
                                  const float2* phi32, double2* out, cudaStream_t s);
 
 // tensor-core screen (tc_screen.cu)
-// d <= 32 and N <= 1536 (bf16, fp16) or N <= 768 (tf32)
+// d <= 32 (bf16, fp16, tf32) or d <= 64 (wide bf16, fp16), 2 <= N <= 65536
 bool screen_supported(int N, int d, int fmt);
 // One instance as the batched screen sees it (device table).
 struct ScreenSlot {
@@ -293,7 +293,8 @@ struct SlotDesc {
 enum BatchPassMode : int {
   kPassFull = 0,      // every candidate, binary32/64 (ranking when not screened)
   kPassRescore = 1,   // the top-k survivors, binary32, into mu2_top
-  kPassFrameMax = 2,  // the winner's binary32 rounding: max |G|^2 into cert32[0]
+  kPassFrameMax = 2,  // the winner's binary32 rounding: max |G|^2 into cert32[0] (the
+                      // iteration uses the winner's score as that value's hint instead)
   kPassFilter = 3,    // same frame: pairs within the bound of cert32[0] into pairs
   kPassFrame64 = 4,   // the binary64 winner, all pairs, only after a pair-list overflow
 };

@@ -212,7 +212,8 @@ int BatchPlan::enqueue_iteration(SlotDesc* d_slots, int n, uint32_t* err, cudaSt
     return TRSTMI_OK;
   }
   // rank (screen, or fp32 below the screen radius), keep the top-k, re-score
-  // them in fp32, regenerate the winner in fp64 and certify it, decide, commit
+  // them in fp32, regenerate the winner in fp64 and certify it (one binary32
+  // filter pass from the winner's score, binary64 pairs), decide, commit
   if (launch_screen(err, s) != cudaSuccess ||
       launch_pass(kPassFull, d_slots, s) != cudaSuccess ||
       launch_large(kPassFull, s) != cudaSuccess ||
@@ -220,7 +221,6 @@ int BatchPlan::enqueue_iteration(SlotDesc* d_slots, int n, uint32_t* err, cudaSt
       launch_pass(kPassRescore, d_slots, s) != cudaSuccess ||
       launch_large(kPassRescore, s) != cudaSuccess ||
       launch_batch_materialize64(d_slots, n, maxN, s) != cudaSuccess ||
-      launch_pass(kPassFrameMax, d_slots, s) != cudaSuccess ||
       launch_pass(kPassFilter, d_slots, s) != cudaSuccess ||
       launch_batch_pairs64(d_slots, n, s) != cudaSuccess ||
       launch_pass(kPassFrame64, d_slots, s) != cudaSuccess ||
@@ -273,7 +273,8 @@ cudaError_t BatchPlan::launch_screen(uint32_t* err, cudaStream_t s) const {
 
 int BatchPlan::kernels_per_iteration() const {
   int k = 1;   // begin
-  for (int p = 0; p < kPasses; ++p) k += (int)groups[p].size();
+  for (int p = 0; p < kPasses; ++p)
+    if (p != kPassFrameMax) k += (int)groups[p].size();   // the max pass is not launched
   if (is_screen_prec(precision)) k += (n_items > n_wide ? 1 : 0) + (n_wide ? 1 : 0) + 6;
   else k += 2;
   k += (int)large.size() * (is_screen_prec(precision) ? 4 : 2);

@@ -1147,7 +1147,10 @@ __global__ void __launch_bounds__(256, TileCtas<T>::value) k_batch_score(const S
           pf.cap = sd.pair_cap;
           pf.overflow = &const_cast<DevState*>(st)->overflow;
           pf.scale_bits = nullptr;
-          pf.ref_slack_mu2 = 0.f;
+          // cert32[0] is the chosen survivor's binary32 score, within the
+          // fp32 / fp64 bound of this frame's binary32 max (checked by the
+          // pair pass, which falls back to the full binary64 pass)
+          pf.ref_slack_mu2 = (float)certify_margin_mu2(sd.d);
           const float lo2 = filter_lo(pf);
           thr = (T)(lo2 * lo2);
           filter = &pf;
@@ -1384,6 +1387,7 @@ __global__ void k_batch_materialize64(SlotDesc* slots, int n) {
     st->cstar = bc;
     st->mu2_screen = m32;
     st->certify = cert ? 1u : 0u;
+    if (cert) sd.cert32[0] = bv;   // the filter pass's hint (no separate max pass)
   }
   if (!cert || j >= sd.N) return;
   const double2* phi64 = reinterpret_cast<const double2*>(sd.phi_other);
@@ -1409,6 +1413,12 @@ __global__ void k_batch_pairs64(SlotDesc* slots, int n) {
   const SlotDesc& sd = slots[blockIdx.x];
   const DevState* st = sd.st;
   if (!st->active || !st->certify) return;
+  // the filter pass ran from the survivor's score as a hint: if the hint less
+  // its slack exceeds the pass's own max, pairs may have been missed
+  if (threadIdx.x == 0 &&
+      fmaxf(__uint_as_float(sd.cert32[0]) - (float)certify_margin_mu2(sd.d), 0.0f) >
+          __uint_as_float(sd.cert32[1]))
+    atomicExch(&const_cast<DevState*>(st)->overflow, 1u);
   const uint32_t np = min(st->npairs, sd.pair_cap);
   const int d = sd.d;
   double m = 0.0;

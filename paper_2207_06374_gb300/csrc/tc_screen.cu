@@ -238,6 +238,72 @@ __device__ __forceinline__ uint32_t swz_offset(int r, int c) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
 }
 
+// Where the column blocks of one item live.  The upper-triangle tiles are
+// swept band by band: a band is Rb <= R consecutive blocks r0 .. r0+Rb-1,
+// resident while its own triangle is swept row by row, and, when blocks lie
+// to its right (r0+Rb .. nb-1), while those stream through two further slots,
+// each used for one column of Rb tiles.  An item whose blocks all fit
+// (nb <= kSlots) is one band without a stream and releases its blocks row by
+// row, so the next item's first blocks fill the slots freed early.  Band
+// blocks go round a ring of B slots, stream blocks round the last two; bit s
+// of `par` is the parity of slot s's next fill, bit s of `used` records that
+// it was filled before.  Generators and the MMA issuer walk the same block
+// sequence (per band: its blocks, then its stream blocks) and so derive the
+// same slots and parities; a slot is always released before its next fill is
+// needed, because blocks are released in the order they are first used.
+template <int F> struct SlotPlan {
+  static constexpr int kS = FmtTraits<F>::kSlots;
+  static constexpr int kStream = 2;
+  // the state is packed so that it costs the generators' hot loop few
+  // registers: pu = par | used << 16; ring = bp | sp << 8 | B << 16 | R << 24;
+  // band = b0 | Rb << 8; bsnap = par | used << 16 as the band began
+  uint32_t pu = 0, ring = 0, band = 0, bsnap = 0;
+  int nb = 0, r0 = 0;
+  __device__ __forceinline__ int R() const { return (int)(ring >> 24); }
+  __device__ __forceinline__ int B() const { return (int)((ring >> 16) & 0xffu); }
+  __device__ __forceinline__ int Rb() const { return (int)(band >> 8); }
+  __device__ __forceinline__ void begin_item(int nb_) {
+    nb = nb_;
+    const bool fits = nb <= kS;
+    const uint32_t R_ = (uint32_t)(fits ? nb : kS - kStream), B_ = (uint32_t)(fits ? kS : kS - kStream);
+    uint32_t bp = ring & 0xffu;
+    if (bp >= B_) bp = 0;
+    ring = bp | (ring & 0xff00u) | (B_ << 16) | (min(R_, 255u) << 24);
+  }
+  __device__ __forceinline__ void begin_band(int r0_) {
+    r0 = r0_;
+    const int Rb_ = min(R(), nb - r0);
+    const uint32_t bp = ring & 0xffu;
+    band = bp | ((uint32_t)Rb_ << 8);
+    bsnap = pu;
+    for (int q = 0; q < Rb_; ++q) {
+      const uint32_t m = 1u << slot_band(q);
+      pu = (pu ^ m) | (m << 16);
+    }
+    ring = (ring & ~0xffu) | (uint32_t)((bp + Rb_) % B());
+  }
+  __device__ __forceinline__ bool streams() const { return r0 + Rb() < nb; }
+  __device__ __forceinline__ int slot_band(int q) const {
+    const int s = (int)(band & 0xffu) + q;
+    return s >= B() ? s - B() : s;
+  }
+  __device__ __forceinline__ uint32_t parity_band(int q) const { return (bsnap >> slot_band(q)) & 1u; }
+  __device__ __forceinline__ bool used_band(int q) const {
+    return ((bsnap >> (16 + slot_band(q))) & 1u) != 0;
+  }
+  // the next stream block's slot, the parity of this fill and whether the
+  // slot was filled before
+  __device__ __forceinline__ int next_stream(uint32_t& p, bool& u) {
+    const uint32_t sp = (ring >> 8) & 1u;
+    const int s = kS - kStream + (int)sp;
+    ring ^= 1u << 8;
+    p = (pu >> s) & 1u;
+    u = ((pu >> (16 + s)) & 1u) != 0;
+    pu = (pu ^ (1u << s)) | (1u << (16 + s));
+    return s;
+  }
+};
+
 // One candidate to screen.
 struct ScreenItem {
   int N, d, nb, ntiles;
@@ -411,7 +477,6 @@ __device__ __forceinline__ void absmax(const uint32_t (&re)[W], const uint32_t (
 // thread may use at most 16384 / (5 * 32) -> 96 registers
 template <int F, class Src>
 __global__ void __maxnreg__(96) k_screen(const Src src) {
-  constexpr int kSlots = FmtTraits<F>::kSlots;
   constexpr int kBlockBytes = FmtTraits<F>::kBlockBytes;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ SmemCtl ctl;
@@ -471,26 +536,19 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
     // fill).
     constexpr int kDP = FmtTraits<F>::kDP, kE = FmtTraits<F>::kEntries;
     const int q = lane >> 3;
-    uint32_t gb0 = 0;
+    SlotPlan<F> plan;
+    uint32_t ucount = 0;      // octet units so far (16 per block instance)
     const int gen_items = src.withhold() ? 0 : nitems;
     for (int idx = blockIdx.x; idx < gen_items; idx += gridDim.x) {
       ScreenItem it;
       if (!src.item(idx, t0, delta0, it)) continue;
       const int d = it.d, P = (d + 1) >> 1;
       const PhiloxCand pc = src.cand(it);
-      const uint32_t u0 = gb0 * (uint32_t)kOctets;
-      const uint32_t u1 = u0 + (uint32_t)(it.nb * kOctets);
-      uint32_t u = u0 + ((uint32_t)gi + (uint32_t)kGenWarps - u0 % (uint32_t)kGenWarps) %
-                            (uint32_t)kGenWarps;
-      for (; u < u1; u += (uint32_t)kGenWarps) {
-        const uint32_t gb = u / (uint32_t)kOctets;
-        const int b = (int)(gb - gb0), o = (int)(u % (uint32_t)kOctets);
-        const uint32_t slot = gb % (uint32_t)kSlots, fill = gb / (uint32_t)kSlots;
-        if (fill > 0 && !warp_wait(&ctl.blk_empty[slot], (fill - 1u) & 1u, &ctl, err, 64))
-          goto gen_done;
+      // octet o of column block jb into slot `slot`
+      auto fill_octet = [&](int o, int jb, int slot) {
         unsigned char* blk = xs + slot * (uint32_t)kBlockBytes;
         const int r = 8 * o + (lane & 7);        // row of the block (column of Phi)
-        const int j = b * kBlockCols + r;
+        const int j = jb * kBlockCols + r;
         float2 x[kE];
         float2 ss = make_float2(0.f, 0.f);
         if (j < it.N && d == kDP) {
@@ -561,14 +619,14 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
         } else if constexpr (F == kScreenTF32) {
           // real parts of entries 8q .. 8q+7 -> chunks 2q, 2q+1 of the first
           // atom; imaginary parts -> the same chunks of the second
-          const uint4 r0 = make_uint4(to_tf32(x[0].x), to_tf32(x[1].x), to_tf32(x[2].x), to_tf32(x[3].x));
-          const uint4 r1 = make_uint4(to_tf32(x[4].x), to_tf32(x[5].x), to_tf32(x[6].x), to_tf32(x[7].x));
-          const uint4 i0 = make_uint4(to_tf32(x[0].y), to_tf32(x[1].y), to_tf32(x[2].y), to_tf32(x[3].y));
-          const uint4 i1 = make_uint4(to_tf32(x[4].y), to_tf32(x[5].y), to_tf32(x[6].y), to_tf32(x[7].y));
-          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q)) = r0;
-          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q + 1)) = r1;
-          *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q)) = i0;
-          *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q + 1)) = i1;
+          const uint4 cr0 = make_uint4(to_tf32(x[0].x), to_tf32(x[1].x), to_tf32(x[2].x), to_tf32(x[3].x));
+          const uint4 cr1 = make_uint4(to_tf32(x[4].x), to_tf32(x[5].x), to_tf32(x[6].x), to_tf32(x[7].x));
+          const uint4 ci0 = make_uint4(to_tf32(x[0].y), to_tf32(x[1].y), to_tf32(x[2].y), to_tf32(x[3].y));
+          const uint4 ci1 = make_uint4(to_tf32(x[4].y), to_tf32(x[5].y), to_tf32(x[6].y), to_tf32(x[7].y));
+          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q)) = cr0;
+          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q + 1)) = cr1;
+          *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q)) = ci0;
+          *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q + 1)) = ci1;
         } else {
           uint4 re, im;
           re.x = pack2<F>(x[0].x, x[1].x);
@@ -586,8 +644,51 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&ctl.blk_full[slot]);
+      };
+      plan.begin_item(it.nb);
+      if (it.nb <= SlotPlan<F>::kS) {
+        // the item fits: its units in order, slot of block b = b0 + b (ring)
+        plan.begin_band(0);
+        const uint32_t u0 = ucount, u1 = ucount + (uint32_t)(it.nb * kOctets);
+        for (uint32_t u = u0 + ((uint32_t)gi + (uint32_t)kGenWarps - u0 % (uint32_t)kGenWarps) %
+                                   (uint32_t)kGenWarps;
+             u < u1; u += (uint32_t)kGenWarps) {
+          const int b = (int)((u - u0) / (uint32_t)kOctets), o = (int)((u - u0) % (uint32_t)kOctets);
+          const int slot = plan.slot_band(b);
+          if (plan.used_band(b) &&
+              !warp_wait(&ctl.blk_empty[slot], plan.parity_band(b) ^ 1u, &ctl, err, 64))
+            goto gen_done;
+          fill_octet(o, b, slot);
+        }
+        ucount = u1;
+        continue;
       }
-      gb0 += (uint32_t)it.nb;
+      plan.begin_item(it.nb);
+      for (int r0 = 0; r0 < it.nb; r0 += plan.R()) {
+        plan.begin_band(r0);
+        for (int qb = 0; qb < it.nb - r0; ++qb, ucount += (uint32_t)kOctets) {
+          int slot;
+          uint32_t parity;
+          bool used;
+          if (qb < plan.Rb()) {
+            slot = plan.slot_band(qb);
+            parity = plan.parity_band(qb);
+            used = plan.used_band(qb);
+          } else {
+            slot = plan.next_stream(parity, used);
+          }
+          const int jb = r0 + qb;     // column block of Phi
+          bool waited = false;
+          for (int o = (gi + kGenWarps - (int)(ucount % (uint32_t)kGenWarps)) % kGenWarps;
+               o < kOctets; o += kGenWarps) {
+            if (used && !waited) {
+              if (!warp_wait(&ctl.blk_empty[slot], parity ^ 1u, &ctl, err, 64)) goto gen_done;
+              waited = true;
+            }
+            fill_octet(o, jb, slot);
+          }
+        }
+      }
     }
   gen_done:;
   } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
@@ -595,29 +696,32 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
     // All eight warps read every tile: warp w takes TMEM lanes 32(w%4) .. +31
     // (its rows of the tile) and the accumulator columns 64h .. 64h+63,
     // h = (w - 4) / 4, in two rounds of 32 Re and 32 Im columns (few, large
-    // loads).  With two accumulator buffers the reading of tile t has to end
-    // within the MMAs of tile t+1, so the tile is split as finely as the
-    // warps allow rather than handed to alternating groups.
+    // loads), and releases the buffer as soon as the second round's loads
+    // have landed.  Tiles come in the MMA issuer's order (SlotPlan: each
+    // band's triangle row by row, then its stream columns); only a band's
+    // own triangle has diagonal tiles.
     const int qw = warp & 3;
     const int colh = 64 * ((warp - kEpiWarp0) >> 2);
     uint32_t gt = 0;
+    SlotPlan<F> plan;
     for (int idx = blockIdx.x; idx < nitems; idx += gridDim.x) {
       ScreenItem it;
       if (!src.item(idx, t0, delta0, it)) continue;
       const int nb = it.nb;
+      plan.begin_item(nb);
       float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      bool ok = true;
-      int I = 0, J = 0;
-      for (int tau = 0; tau < it.ntiles; ++tau, ++gt, J = (J + 1 < nb) ? J + 1 : ++I) {
+      // one tile from accumulator buffer gt & 1; false if the wait gave up
+      auto tile = [&](bool diag) -> bool {
         const uint32_t buf = gt & 1u, use = gt >> 1;
-        if (!warp_wait(&ctl.acc_full[buf], use & 1u, &ctl, err, 32)) { ok = false; break; }
+        ++gt;
+        if (!warp_wait(&ctl.acc_full[buf], use & 1u, &ctl, err, 32)) return false;
         tc_fence_after();
         // the base is re-materialised per tile so the chunk addresses are
         // formed next to their loads instead of being held across the loop
         uint32_t base;
         asm volatile("mov.b32 %0, %1;" : "=r"(base) : "r"(tmem + ((uint32_t)(32 * qw) << 16) +
                                                           buf * 256u + (uint32_t)colh));
-        if (I != J) {
+        if (!diag) {
           uint32_t ra[32], ia[32];
           tmem_ld32(base, ra);
           tmem_ld32(base + 128u, ia);
@@ -630,36 +734,49 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
           __syncwarp();
           if (lane == 0) mbar_arrive(&ctl.acc_empty[buf]);
           absmax<32>(ra, ia, m);
-          continue;
-        } else {
-          // diagonal tile: only column k > row j counts.  This warp's rows
-          // are 32qw .. 32qw+31; a 16-column chunk n0 .. n0+15 lies entirely
-          // at or below the diagonal (skip), entirely above it (no mask), or
-          // straddles it (mask column n0 + e against row 32qw + lane).
-          uint32_t ra[16], ia[16];
+          return true;
+        }
+        // diagonal tile: only column k > row j counts.  This warp's rows
+        // are 32qw .. 32qw+31; a 16-column chunk n0 .. n0+15 lies entirely
+        // at or below the diagonal (skip), entirely above it (no mask), or
+        // straddles it (mask column n0 + e against row 32qw + lane).
+        uint32_t ra[16], ia[16];
 #pragma unroll 1
-          for (int ch = 0; ch < 4; ++ch) {
-            const int n0 = colh + 16 * ch;
-            if (n0 + 16 <= 32 * qw) continue;
-            tmem_ld16(base + 16u * ch, ra);
-            tmem_ld16(base + 128u + 16u * ch, ia);
-            tmem_wait_ld<16>(ra, ia);
-            if (n0 >= 32 * qw + 32) {
-              absmax<16>(ra, ia, m);
-            } else {
-              const int lim = 32 * qw + lane - n0;   // mask e <= lim
+        for (int ch = 0; ch < 4; ++ch) {
+          const int n0 = colh + 16 * ch;
+          if (n0 + 16 <= 32 * qw) continue;
+          tmem_ld16(base + 16u * ch, ra);
+          tmem_ld16(base + 128u + 16u * ch, ia);
+          tmem_wait_ld<16>(ra, ia);
+          if (n0 >= 32 * qw + 32) {
+            absmax<16>(ra, ia, m);
+          } else {
+            const int lim = 32 * qw + lane - n0;   // mask e <= lim
 #pragma unroll
-              for (int e = 0; e < 16; ++e) {
-                const float x = __uint_as_float(ra[e]), y = __uint_as_float(ia[e]);
-                const float v = fmaf(x, x, y * y);
-                m[e & 7] = (e > lim) ? fmaxf(m[e & 7], v) : m[e & 7];
-              }
+            for (int e = 0; e < 16; ++e) {
+              const float x = __uint_as_float(ra[e]), y = __uint_as_float(ia[e]);
+              const float v = fmaf(x, x, y * y);
+              m[e & 7] = (e > lim) ? fmaxf(m[e & 7], v) : m[e & 7];
             }
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&ctl.acc_empty[buf]);
+        return true;
+      };
+      bool ok = true;
+      if (nb <= SlotPlan<F>::kS) {
+        int I = 0, J = 0;
+        for (int tau = 0; tau < it.ntiles && ok; ++tau, J = (J + 1 < nb) ? J + 1 : ++I)
+          ok = tile(I == J);
+      }
+      for (int r0 = 0; nb > SlotPlan<F>::kS && r0 < nb && ok; r0 += plan.R()) {
+        const int Rb = min(plan.R(), nb - r0);
+        for (int I = 0; I < Rb && ok; ++I)
+          for (int J = I; J < Rb && ok; ++J) ok = tile(I == J);
+        for (int J = Rb; J < nb - r0 && ok; ++J)
+          for (int I = 0; I < Rb && ok; ++I) ok = tile(false);
       }
       if (!ok) break;
       float mx = fmaxf(fmax3(m[0], m[1], m[2]), fmax3(m[3], m[4], m[5]));
@@ -672,69 +789,121 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
     // ------------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t gt = 0;
-      uint32_t slot0 = 0, par0 = 0;    // ring slot and fill parity of the item's block 0
+      SlotPlan<F> plan;
       const uint32_t hi = kDescHi;
       const uint32_t xs_lo = desc_lo(xs_addr);
       bool ok = true;
-      // Row-major sweep: block I is last read in row I (as A for J >= I, as B
-      // in rows I' <= I), so its slot is released right after its row.  Row 0
-      // reads every block; it waits for each one as it first needs it.
+      // One tile: A from slot sA, B from slot sB into accumulator buffer gt & 1.
+      // the MMAs of one tile: A at low word alo, B at blo, into dre (Re) / dim (Im)
+      auto issue_mmas = [&](uint32_t alo, uint32_t blo, uint32_t dre, uint32_t dim) {
+        if constexpr (FmtTraits<F>::kTwoAtoms) {
+          // K steps of 8 tf32 or 16 bf16 / fp16 = 32 bytes = +2 in the low
+          // word; the second atom (Im parts) is 16 KiB = +1024 further
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)   // Re: A_I^T A_J ...
+            mma_lo<F>(dre, alo + 2u * kk, blo + 2u * kk, Idesc<F>::pos, kk > 0 ? 1u : 0u, hi);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)   // ... + B_I^T B_J
+            mma_lo<F>(dre, alo + 1024u + 2u * kk, blo + 1024u + 2u * kk, Idesc<F>::pos, 1u, hi);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)   // Im: A_I^T B_J ...
+            mma_lo<F>(dim, alo + 2u * kk, blo + 1024u + 2u * kk, Idesc<F>::pos, kk > 0 ? 1u : 0u, hi);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)   // ... - B_I^T A_J
+            mma_lo<F>(dim, alo + 1024u + 2u * kk, blo + 2u * kk, Idesc<F>::neg_a, 1u, hi);
+        } else {
+          // Re: sum over the whole K = 2*DP (4 steps of 16 = +2 in the low word)
+          mma_lo<F>(dre, alo + 0u, blo + 0u, Idesc<F>::pos, 0u, hi);
+          mma_lo<F>(dre, alo + 2u, blo + 2u, Idesc<F>::pos, 1u, hi);
+          mma_lo<F>(dre, alo + 4u, blo + 4u, Idesc<F>::pos, 1u, hi);
+          mma_lo<F>(dre, alo + 6u, blo + 6u, Idesc<F>::pos, 1u, hi);
+          // Im: A_I^T B_J (K slices 0,1 against 2,3) - B_I^T A_J (2,3 against 0,1)
+          mma_lo<F>(dim, alo + 0u, blo + 4u, Idesc<F>::pos, 0u, hi);
+          mma_lo<F>(dim, alo + 2u, blo + 6u, Idesc<F>::pos, 1u, hi);
+          mma_lo<F>(dim, alo + 4u, blo + 0u, Idesc<F>::neg_a, 1u, hi);
+          mma_lo<F>(dim, alo + 6u, blo + 2u, Idesc<F>::neg_a, 1u, hi);
+        }
+      };
+      auto tile = [&](int sA, int sB) -> bool {
+        const uint32_t buf = gt & 1u, use = gt >> 1;
+        ++gt;
+        if (use > 0 &&
+            !mbar_wait(&ctl.acc_empty[buf], (use - 1u) & 1u, &ctl, err, kMmaBackoffNs))
+          return false;
+        tc_fence_after();
+        const uint32_t alo = xs_lo + (uint32_t)sA * (uint32_t)(kBlockBytes >> 4);
+        const uint32_t blo = xs_lo + (uint32_t)sB * (uint32_t)(kBlockBytes >> 4);
+        const uint32_t dre = tmem + buf * 256u, dim = dre + 128u;
+        issue_mmas(alo, blo, dre, dim);
+        mma_commit(&ctl.acc_full[buf]);
+        return true;
+      };
+      // Per band: its triangle row by row -- block I is last read in row I
+      // (as A for J >= I, as B in rows I' <= I); the first row waits for each
+      // block as it first needs it -- then, if blocks lie to its right, one
+      // column of Rb tiles per stream block, after which the band's blocks
+      // are released together.
       for (int idx = blockIdx.x; idx < nitems && ok; idx += gridDim.x) {
         ScreenItem it;
         if (!src.item(idx, t0, delta0, it)) continue;
         const int nb = it.nb;
-        for (int I = 0; I < nb && ok; ++I) {
-          uint32_t sI = slot0 + (uint32_t)I;
-          if (sI >= (uint32_t)kSlots) sI -= (uint32_t)kSlots;
-          const uint32_t alo = xs_lo + sI * (uint32_t)(kBlockBytes >> 4);
-          for (int J = I; J < nb; ++J, ++gt) {
-            uint32_t sJ = slot0 + (uint32_t)J, parJ = par0;
-            if (sJ >= (uint32_t)kSlots) { sJ -= (uint32_t)kSlots; parJ ^= 1u; }
-            if (I == 0) {
-              ok = mbar_wait(&ctl.blk_full[sJ], parJ, &ctl, err, kMmaBackoffNs);
-              if (!ok) break;
+        plan.begin_item(nb);
+        if (nb <= SlotPlan<F>::kS) {
+          // the item fits: row-major, slots of the ring advanced incrementally
+          plan.begin_band(0);
+          const int B = plan.B();
+          uint32_t sI = (uint32_t)plan.slot_band(0);
+          for (int I = 0; I < nb && ok; ++I, sI = (sI + 1 == (uint32_t)B) ? 0 : sI + 1) {
+            const uint32_t alo = xs_lo + sI * (uint32_t)(kBlockBytes >> 4);
+            uint32_t sJ = sI;
+            for (int J = I; J < nb; ++J, ++gt, sJ = (sJ + 1 == (uint32_t)B) ? 0 : sJ + 1) {
+              if (I == 0) {
+                ok = mbar_wait(&ctl.blk_full[sJ], (plan.bsnap >> sJ) & 1u, &ctl, err,
+                               kMmaBackoffNs);
+                if (!ok) break;
+              }
+              const uint32_t buf = gt & 1u, use = gt >> 1;
+              if (use > 0) {
+                ok = mbar_wait(&ctl.acc_empty[buf], (use - 1u) & 1u, &ctl, err, kMmaBackoffNs);
+                if (!ok) break;
+              }
+              tc_fence_after();
+              const uint32_t blo = xs_lo + sJ * (uint32_t)(kBlockBytes >> 4);
+              const uint32_t dre = tmem + buf * 256u, dim = dre + 128u;
+              issue_mmas(alo, blo, dre, dim);
+              mma_commit(&ctl.acc_full[buf]);
             }
-            const uint32_t buf = gt & 1u, use = gt >> 1;
-            if (use > 0) {
-              ok = mbar_wait(&ctl.acc_empty[buf], (use - 1u) & 1u, &ctl, err, kMmaBackoffNs);
-              if (!ok) break;
-            }
-            tc_fence_after();
-            const uint32_t blo = xs_lo + sJ * (uint32_t)(kBlockBytes >> 4);
-            const uint32_t dre = tmem + buf * 256u, dim = dre + 128u;
-            if constexpr (FmtTraits<F>::kTwoAtoms) {
-              // K steps of 8 tf32 or 16 bf16 / fp16 = 32 bytes = +2 in the low
-              // word; the second atom (Im parts) is 16 KiB = +1024 further
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk)   // Re: A_I^T A_J ...
-                mma_lo<F>(dre, alo + 2u * kk, blo + 2u * kk, Idesc<F>::pos, kk > 0 ? 1u : 0u, hi);
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk)   // ... + B_I^T B_J
-                mma_lo<F>(dre, alo + 1024u + 2u * kk, blo + 1024u + 2u * kk, Idesc<F>::pos, 1u, hi);
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk)   // Im: A_I^T B_J ...
-                mma_lo<F>(dim, alo + 2u * kk, blo + 1024u + 2u * kk, Idesc<F>::pos, kk > 0 ? 1u : 0u, hi);
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk)   // ... - B_I^T A_J
-                mma_lo<F>(dim, alo + 1024u + 2u * kk, blo + 2u * kk, Idesc<F>::neg_a, 1u, hi);
-            } else {
-              // Re: sum over the whole K = 2*DP (4 steps of 16 = +2 in the low word)
-              mma_lo<F>(dre, alo + 0u, blo + 0u, Idesc<F>::pos, 0u, hi);
-              mma_lo<F>(dre, alo + 2u, blo + 2u, Idesc<F>::pos, 1u, hi);
-              mma_lo<F>(dre, alo + 4u, blo + 4u, Idesc<F>::pos, 1u, hi);
-              mma_lo<F>(dre, alo + 6u, blo + 6u, Idesc<F>::pos, 1u, hi);
-              // Im: A_I^T B_J (K slices 0,1 against 2,3) - B_I^T A_J (2,3 against 0,1)
-              mma_lo<F>(dim, alo + 0u, blo + 4u, Idesc<F>::pos, 0u, hi);
-              mma_lo<F>(dim, alo + 2u, blo + 6u, Idesc<F>::pos, 1u, hi);
-              mma_lo<F>(dim, alo + 4u, blo + 0u, Idesc<F>::neg_a, 1u, hi);
-              mma_lo<F>(dim, alo + 6u, blo + 2u, Idesc<F>::neg_a, 1u, hi);
-            }
-            mma_commit(&ctl.acc_full[buf]);
+            if (ok) mma_commit(&ctl.blk_empty[sI]);   // row I done: block I's slot is free
           }
-          if (ok) mma_commit(&ctl.blk_empty[sI]);   // row I done: block I's slot is free
+          continue;
         }
-        slot0 += (uint32_t)nb;
-        if (slot0 >= (uint32_t)kSlots) { slot0 -= (uint32_t)kSlots; par0 ^= 1u; }
+        for (int r0 = 0; r0 < nb && ok; r0 += plan.R()) {
+          plan.begin_band(r0);
+          const int Rb = plan.Rb();
+          const bool stream = plan.streams();
+          for (int I = 0; I < Rb && ok; ++I) {
+            for (int J = I; J < Rb && ok; ++J) {
+              if (I == 0) {
+                ok = mbar_wait(&ctl.blk_full[plan.slot_band(J)], plan.parity_band(J), &ctl, err,
+                               kMmaBackoffNs);
+                if (!ok) break;
+              }
+              ok = tile(plan.slot_band(I), plan.slot_band(J));
+            }
+            if (ok && !stream) mma_commit(&ctl.blk_empty[plan.slot_band(I)]);   // row I done
+          }
+          if (!stream || !ok) continue;
+          for (int qb = Rb; qb < nb - r0 && ok; ++qb) {
+            uint32_t parity;
+            bool used;
+            const int sJ = plan.next_stream(parity, used);
+            ok = mbar_wait(&ctl.blk_full[sJ], parity, &ctl, err, kMmaBackoffNs);
+            for (int I = 0; I < Rb && ok; ++I) ok = tile(plan.slot_band(I), sJ);
+            if (ok) mma_commit(&ctl.blk_empty[sJ]);
+          }
+          if (ok)
+            for (int I = 0; I < Rb; ++I) mma_commit(&ctl.blk_empty[plan.slot_band(I)]);
+        }
       }
       // all issued MMAs complete before tensor memory is released
       mma_commit(&ctl.drain);
@@ -797,12 +966,13 @@ cudaError_t launch_any(int fmt, const Src& src, int grid, cudaStream_t s) {
 
 }  // namespace
 
+// Any N up to kScreenMaxN: beyond the ring (12 blocks of 128 columns, 6 for
+// two-atom formats) the candidate is swept in bands (SlotPlan).
+constexpr int kScreenMaxN = 65536;
 bool screen_supported(int N, int d, int fmt) {
   if (fmt < kScreenBF16 || fmt > kScreenFP16W) return false;
-  const int nb = (N + kBlockCols - 1) / kBlockCols;
   const bool wide16 = fmt == kScreenBF16W || fmt == kScreenFP16W;
-  const int slots = (fmt == kScreenTF32 || wide16) ? 6 : 12;
-  return N >= 2 && d >= 1 && d <= (wide16 ? 64 : 32) && nb <= slots;
+  return N >= 2 && N <= kScreenMaxN && d >= 1 && d <= (wide16 ? 64 : 32);
 }
 
 cudaError_t init_screen_attributes(int optin) {

@@ -160,6 +160,11 @@ class Certificates(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class Peaks(ctypes.Structure):
+    _fields_ = [("fp32_tflops", ctypes.c_double), ("fp64_tflops", ctypes.c_double),
+                ("tf32_tflops", ctypes.c_double), ("bf16_tflops", ctypes.c_double)]
+
+
 class TrOptions(ctypes.Structure):
     _fields_ = [("n_delta", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("delta", ctypes.c_double * 16), ("max_cg", ctypes.c_int32),
@@ -256,6 +261,7 @@ SIGNATURES = {
                                          ctypes.c_int, ctypes.c_int, ctypes.POINTER(Options),
                                          ctypes.c_int, ctypes.POINTER(MultistartResult), _dp,
                                          _dp]),
+    "trstmi_measure_peaks": (ctypes.c_int, [ctypes.POINTER(Peaks), ctypes.c_void_p]),
     "trstmi_screen_wait_test": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "trstmi_mu2_frame_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
@@ -768,6 +774,15 @@ def lse_device(N: int, d: int, count: int, v_ptr: int, delta: float, precision, 
     _check(lib().trstmi_lse_frames_device(N, d, count, v_ptr, delta, p, scratch_ptr,
                                           scratch_bytes, out_ptr, grad_ptr or None,
                                           stream or None), "trstmi_lse_frames_device")
+
+
+def measure_peaks(stream: int = 0) -> dict:
+    """TFLOP/s of FFMA, DFMA and the bf16 / tf32 tensor cores on the current
+    device (trstmi_measure_peaks)."""
+    p = Peaks()
+    _check(lib().trstmi_measure_peaks(ctypes.byref(p), ctypes.c_void_p(stream)),
+           "trstmi_measure_peaks")
+    return {k: getattr(p, k) for k, _ in p._fields_}
 
 
 def mu2_frame(phi: np.ndarray, precision="fp64") -> float:

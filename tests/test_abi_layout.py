@@ -26,6 +26,7 @@ MIRRORS = {
     "trstmi_certificates": T.Certificates,
     "trstmi_tr_options": T.TrOptions,
     "trstmi_tr_row": T.TR_ROW_DTYPE,
+    "trstmi_peaks": T.Peaks,
 }
 
 

@@ -120,17 +120,16 @@ def test_batch_rejects_bad_arguments():
     assert e.value.status == T.TRSTMI_EINVAL
 
 
-# shapes of the screen modes: inside the tensor-core screen's range (d <= 32,
-# N <= 1536; 32 < d <= 64, N <= 768 with bf16 / fp16 operands) and outside it
-# (N = 1600; d = 40 at N = 800; d > 32 with tf32), which rank in binary32
+# shapes of the screen modes: inside the tensor-core screen's range (d <= 32;
+# 32 < d <= 64 with bf16 / fp16 operands; N beyond 1536 (768 with two operand
+# atoms) swept in bands) and outside it (d > 32 with tf32), which rank in
+# binary32
 SCREEN_MIX = [(4, 2), (9, 3), (40, 8), (129, 13), (200, 16), (17, 16), (300, 32), (1024, 32),
               (50, 40), (1600, 4), (700, 64), (120, 33), (800, 40)]
 
 
 def screened_shape(precision, N, d):
-    if d <= 32:
-        return N <= (768 if precision == "tf32" else 1536)
-    return precision != "tf32" and d <= 64 and N <= 768
+    return d <= (32 if precision == "tf32" else 64) and 2 <= N <= 65536
 
 
 @pytest.mark.parametrize("precision", ["bf16", "fp16", "tf32"])

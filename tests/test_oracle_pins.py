@@ -304,3 +304,30 @@ def test_search_reaches_tetrahedral_code(seed):
     mu = np.sqrt(m2)
     assert abs(mu - 1 / np.sqrt(3)) < 1e-5
     assert mu <= _table2()[(2, 4)]
+
+
+# ------------------------------ the binary32 plain-loop variant (CPU baseline)
+
+@pytest.mark.parametrize("d,N,K", [(2, 4, 16), (8, 64, 12), (32, 200, 3), (5, 33, 9), (1, 6, 4)])
+def test_f32_variant_matches_the_binary64_oracle_to_f32_rounding(d, N, K):
+    """Same candidates, single-precision arithmetic: mu agrees with the
+    binary64 oracle to binary32 rounding (entries within ~8 ulp, a Gram entry
+    within ~(2d + 2) ulp more, so |dmu| <= ~(2d + 20) 2^-24 < 1e-5 here)."""
+    phi = O.init(N, d, 3)
+    for t, c0, delta in ((1, 0, 0.1), (7, 40, 0.6)):
+        ref = O.score(phi, 3, delta, t, c0, K)
+        f32 = O.score_f32(phi, 3, delta, t, c0, K, nthreads=2)
+        assert np.max(np.abs(np.sqrt(f32) - np.sqrt(ref))) < (2 * d + 20) * 2.0 ** -24 * 4
+        # the binary32 values are not the binary64 ones (the variant is not a copy)
+        assert d == 1 or np.any(f32 != ref)
+
+
+def test_f32_variant_on_closed_forms_and_zero_radius():
+    """Radius 0 leaves the frame unchanged: the variant's mu is the frame's
+    own, e.g. the tetrahedral code's 1/sqrt(3) and 1 in C^1."""
+    import frames as F
+    phi = F.tetrahedral_2_4()
+    m = O.score_f32(phi, 1, 0.0, 1, 0, 3)
+    assert np.allclose(np.sqrt(m), 1 / np.sqrt(3), atol=1e-6)
+    m1 = O.score_f32(np.ones((1, 5), dtype=complex), 1, 0.3, 2, 0, 4)
+    assert np.allclose(m1, 1.0, atol=1e-6)
