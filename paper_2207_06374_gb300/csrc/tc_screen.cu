@@ -51,14 +51,20 @@ template <int F> struct FmtTraits {
 constexpr int kOperandBytes = 12 * 16384;
 constexpr int kRing = 12;               // barrier slots: the largest ring
 // Warp roles.  A warp runs on SM sub-partition (warp % 4), and reads only
-// the tensor-memory lanes 32 (warp % 4) .. +31.  Sub-partition 0 holds the MMA
-// issuer (warp 0), two epilogue warps (4 and 8) and a single generator (12),
-// so the long integer-multiply streams of the random draws rarely delay an
-// MMA issue; the other nine generators (warps 1-3, 13-15, 17-19) share
-// sub-partitions 1-3 with the other epilogue warps; warp 16 idles.
+// the tensor-memory lanes 32 (warp % 4) .. +31.  Sub-partition 0 holds the two
+// MMA issuers (warps 0 and 16), two epilogue warps (4 and 8) and a single
+// generator (12), so the long integer-multiply streams of the random draws
+// rarely delay an MMA issue; the other nine generators (warps 1-3, 13-15,
+// 17-19) share sub-partitions 1-3 with the other epilogue warps.
+// Each issuer owns one accumulator buffer and issues every other tile: an
+// MMA instruction holds its issuing thread for about as long as the tensor
+// core takes to run it at N = 128, and a tile's hand-off (commit, epilogue,
+// release) takes longer than a tile's MMAs, so with one issuer the tensor
+// core idles while that thread waits for a buffer; with two, one issuer's
+// tile runs while the other waits.
 constexpr int kWarps = 20;
 constexpr int kThreads = 32 * kWarps;                  // 640
-constexpr int kMmaWarp = 0;
+constexpr int kMmaWarp = 0, kMmaWarp2 = 16;
 constexpr int kEpiWarp0 = 4, kEpiWarps = 8;            // warps 4..11: two warpgroups
 constexpr int kGenWarps = 10;
 constexpr int kOctets = 16;                            // 8-column units of a block
@@ -495,13 +501,13 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
   if (threadIdx.x == 0) {
     for (int b = 0; b < kRing; ++b) {
       mbar_init(&ctl.blk_full[b], kOctets);
-      mbar_init(&ctl.blk_empty[b], 1);
+      mbar_init(&ctl.blk_empty[b], 2);   // both MMA issuers commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ctl.acc_full[b], 1);
       mbar_init(&ctl.acc_empty[b], kEpiWarps);
     }
-    mbar_init(&ctl.drain, 1);
+    mbar_init(&ctl.drain, 2);
     ctl.abort_flag = 0;
     ctl.wait_limit_ns = src.wait_limit();
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -785,9 +791,13 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       if (lane == 0) atomicMax(it.out, __float_as_uint(mx));
     }
-  } else if (warp == kMmaWarp) {
-    // ------------------------------------------------------ MMA issuer
+  } else if (warp == kMmaWarp || warp == kMmaWarp2) {
+    // ------------------------------------------------------ MMA issuers
+    // Both walk the whole tile sequence, wait for every block, and commit
+    // every slot release (blk_empty counts two commits); issuer iw issues the
+    // tiles of accumulator buffer iw, i.e. the tiles gt with gt % 2 == iw.
     if (lane == 0) {
+      const uint32_t iw = warp == kMmaWarp ? 0u : 1u;
       uint32_t gt = 0;
       SlotPlan<F> plan;
       const uint32_t hi = kDescHi;
@@ -827,6 +837,7 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
       auto tile = [&](int sA, int sB) -> bool {
         const uint32_t buf = gt & 1u, use = gt >> 1;
         ++gt;
+        if (buf != iw) return true;
         if (use > 0 &&
             !mbar_wait(&ctl.acc_empty[buf], (use - 1u) & 1u, &ctl, err, kMmaBackoffNs))
           return false;
@@ -863,6 +874,7 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
                 if (!ok) break;
               }
               const uint32_t buf = gt & 1u, use = gt >> 1;
+              if (buf != iw) continue;
               if (use > 0) {
                 ok = mbar_wait(&ctl.acc_empty[buf], (use - 1u) & 1u, &ctl, err, kMmaBackoffNs);
                 if (!ok) break;
