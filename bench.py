@@ -111,12 +111,13 @@ def flops_per_pair(d):
 
 
 def kernels_per_step(precision):
-    # one k_set_stop per trstmi_step call plus the iteration's kernels
-    # screen modes: iter_begin, screen, the gated fp32 ranking pass, top-k, the
-    # survivors' draw (2) and re-score, the fp64 draw of the winner, the certify
-    # passes (binary32 max, filter, binary64 pairs, gated binary64 pass),
-    # decide, commit
-    return 1 + {"fp64": 4, "fp32": 5, "bf16": 14, "tf32": 14}[precision]
+    # one k_set_stop per trstmi_step call plus the iteration's kernels; screen
+    # modes with every iteration screened (screen_min_delta = 0): iter_begin,
+    # screen, top-k, the survivors' binary32 draw, the survivor pair pass, the
+    # listed pairs in binary32, the gated re-score over all pairs, the binary64
+    # draw of the winner, its listed pairs in binary64, the gated binary64 pass
+    # over all pairs, and the rule with the commit
+    return 1 + {"fp64": 4, "fp32": 5, "bf16": 11, "tf32": 11}[precision]
 
 
 def dist_env():
@@ -690,18 +691,25 @@ def main():
         if sharded:
             with torch.cuda.stream(stream):
                 ctx["sharded"].step(1)
+            mu = ctypes.c_double()
+            T._check(L.trstmi_coherence(s._h, ctypes.byref(mu), None), "coherence")
         else:
-            s.step(1)
+            # the step reports the certified mu of the frame it leaves (its
+            # device-state read), so no separate coherence pass
+            info = s.step(1)
+            assert info.mu > 0.0
         T._check(L.trstmi_get_phi(s._h, ctypes.cast(out_host.data_ptr(), dp)), "get_phi")
-        mu = ctypes.c_double()
-        T._check(L.trstmi_coherence(s._h, ctypes.byref(mu), None), "coherence")
     barrier()
     t_e2e = time.perf_counter() - t0
+    # device-to-host per step: the frame (16 d N bytes) and the state the step
+    # reads back (11 binary64 and 16 32-bit fields = 152 bytes, mu among them),
+    # or in the sharded form mu from trstmi_coherence (8 bytes)
     e2e = {"value": units * e2e_steps * pps / t_e2e, "unit": "pairs/s",
-           "h2d_bytes_per_step": 16 * d * N, "d2h_bytes_per_step": 16 * d * N + 8,
+           "h2d_bytes_per_step": 16 * d * N,
+           "d2h_bytes_per_step": 16 * d * N + (8 if sharded else 152),
            "call": ("trstmi_set_phi + trstmi_shard_score / all-reduce / trstmi_shard_finish + "
                     "trstmi_get_phi + trstmi_coherence") if sharded else
-                   "trstmi_set_phi + trstmi_step(1) + trstmi_get_phi + trstmi_coherence"}
+                   "trstmi_set_phi + trstmi_step(1) (returns mu) + trstmi_get_phi"}
 
     peaks, peak_kind = measured_peaks()
     flops_launch = pps * flops_per_pair(d)

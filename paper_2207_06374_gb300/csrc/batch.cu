@@ -64,7 +64,7 @@ __global__ void k_batch_set_mu2cur(SlotDesc* slots, int n) {
 }
 
 // Screen modes: the initial frame is certified in binary64 like every later
-// one, here simply by its binary64 mu^2 over all pairs (cert64 of the slot).
+// one, by the certification passes (cert64 of the slot).
 __global__ void k_batch_set_mu2cur_cert(SlotDesc* slots, int n) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
@@ -437,9 +437,9 @@ int trstmi_batch_create(int n, const int* N, const int* d, const uint64_t* seeds
     GramSource src{};
     src.perturb = false;
     cudaError_t e;
-    if (screen) {          // binary64 over all pairs of the initial frame
-      src.phi = p64;
-      e = launch_gram_f64(N[i], d[i], 1, src, sd.cert64, b->num_sms, s);
+    if (screen) {          // certified in binary64 as the standalone instance does
+      e = launch_frame_certify(N[i], d[i], p64, p32, sd.cert32, sd.cert64, sd.pairs, sd.pair_cap,
+                               &sd.st->npairs, &sd.st->overflow, nullptr, b->num_sms, s);
     } else {
       src.phi = sd.phi;
       e = b->f64 ? launch_gram_f64(N[i], d[i], 1, src, (unsigned long long*)sd.mu2, b->num_sms, s)

@@ -28,6 +28,12 @@ namespace {
 constexpr uint32_t kBlobMagic = 0x54525354u;  // "TRST"
 constexpr uint32_t kBlobVersion = 1u;
 constexpr uint32_t kPairCap = 1u << 16;
+// entries of a survivor's pair list (survivor pair pass); a survivor with more
+// pairs near its maximum is re-scored over all pairs
+constexpr uint32_t kListCap = 4096;
+// words zeroed with the top-k scores each iteration: the scores, the list
+// counts, the overflow flag and the winner selection (slot, filter needed)
+inline size_t top_words(int k) { return 2 * (size_t)k + 3; }
 constexpr int kGraphChunk = 32;
 
 std::mutex g_attr_mu;
@@ -110,11 +116,16 @@ struct trstmi_instance {
   double2* scratch64 = nullptr;
   unsigned int* mu2_k32 = nullptr;         // K
   unsigned long long* mu2_k64 = nullptr;   // K
-  unsigned int* mu2_top = nullptr;         // topk
+  unsigned int* mu2_top = nullptr;         // topk, followed by (zeroed with it) the
+  uint32_t* scount = nullptr;              // survivor pair lists' counts (topk),
+  uint32_t* sover = nullptr;               // a list overflowed (1),
+  uint32_t* ssel = nullptr;                // the winner's slot, filter needed (2)
+  uint2* slists = nullptr;                 // screen modes: topk x kListCap survivor pairs
   uint32_t* topk = nullptr;                // topk
   unsigned int* cert32 = nullptr;          // 1
   unsigned long long* cert64 = nullptr;    // 1
-  uint32_t* misc = nullptr;                // [0] npairs, [1] overflow (standalone certify)
+  uint32_t* misc = nullptr;                // [0] npairs, [1] overflow (standalone certify),
+                                           // [2] the decide-and-commit launch's CTA counter
   uint2* pairs = nullptr;                  // kPairCap
   TraceRowDev* trace = nullptr;            // trace_cap
   float* planes_top = nullptr;             // screen modes: the top-k survivors drawn once
@@ -123,6 +134,9 @@ struct trstmi_instance {
                                            // drawn once as [i][column] planes (2dN floats each)
   std::map<int, cudaGraphExec_t> graphs;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // the device state's screen threshold (infinite when the screen is not
+  // used); 0 means every iteration ranks with the screen
+  double screen_min_delta = std::numeric_limits<double>::infinity();
 };
 
 namespace {
@@ -138,43 +152,14 @@ int cuda_status(cudaError_t e) {
   return e == cudaSuccess ? TRSTMI_OK : record_cuda_error(e, "kernel launch", __LINE__);
 }
 
-float certify_margin(int d) {
-  // |G| in binary32 of a frame rounded from binary64 differs from the
-  // binary64 |G| by at most ~(2 + 2*(2d) ) u, u = 2^-24 (rounding of the
-  // entries plus a 2d-term dot product per part); twice a generous 4x of
-  // that bound separates "can be the max" from "cannot".
-  return (float)(8.0 * (2.0 * d + 2.0) * std::ldexp(1.0, -24));
-}
-
 // binary64 mu^2 of a normalised binary64 frame (with its binary32 rounding)
 // into out64: binary32 max, binary32 preselection of the pairs within the
 // error bound, binary64 over those pairs, full binary64 pass on overflow.
-// hinted: cert32[0] already holds a hint within certify_margin_mu2(d) of the
-// frame's binary32 max (the chosen survivor's binary32 score), so the max pass
-// is skipped; the pair pass checks the hint against the filter pass's own max
-// and falls back to the full binary64 pass if it was too high.
 int enqueue_certify(trstmi_instance* h, const double2* f64, const float2* f32,
                     unsigned long long* out64, const uint32_t* active, uint32_t* npairs,
-                    uint32_t* overflow, cudaStream_t s, bool hinted = false) {
-  GramSource src{};
-  src.perturb = false;
-  src.phi = f32;
-  src.normalize = false;
-  src.gate = active;
-  const float slack = hinted ? (float)certify_margin_mu2(h->d) : 0.f;
-  if (!hinted) TRY_CUDA(launch_gram_f32(h->N, h->d, 1, src, h->cert32, nullptr, h->num_sms, s));
-  PairFilter pf{h->cert32, certify_margin(h->d), h->pairs, npairs, kPairCap, overflow, nullptr,
-                slack};
-  TRY_CUDA(launch_gram_f32(h->N, h->d, 1, src, h->cert32 + 1, &pf, h->num_sms, s));
-  TRY_CUDA(launch_pairs64(active, npairs, h->pairs, kPairCap, h->d, f64, out64, s,
-                          hinted ? h->cert32 : nullptr, hinted ? h->cert32 + 1 : nullptr, slack,
-                          hinted ? overflow : nullptr));
-  GramSource full{};
-  full.perturb = false;
-  full.phi = f64;
-  full.normalize = false;
-  full.gate = overflow;  // reset every iteration, so 0 when the iteration is inactive
-  TRY_CUDA(launch_gram_f64(h->N, h->d, 1, full, out64, h->num_sms, s));
+                    uint32_t* overflow, cudaStream_t s) {
+  TRY_CUDA(launch_frame_certify(h->N, h->d, f64, f32, h->cert32, out64, h->pairs, kPairCap,
+                                npairs, overflow, active, h->num_sms, s));
   return TRSTMI_OK;
 }
 
@@ -261,7 +246,7 @@ int enqueue_iteration_score(trstmi_instance* h, cudaStream_t s, int c_lo, int c_
   } else {
     const int k = h->opt.topk;
     TRY_CUDA(launch_iter_begin(st, h->mu2_k32, sizeof(unsigned int) * K, h->mu2_top,
-                               sizeof(unsigned int) * k, h->cert32,
+                               top_words(k) * sizeof(uint32_t), h->cert32,
                                2 * sizeof(unsigned int) + sizeof(unsigned long long), s));
     if (count > 0) {
       // rank the candidates: tensor-core screen while delta >= screen_min_delta,
@@ -271,14 +256,17 @@ int enqueue_iteration_score(trstmi_instance* h, cudaStream_t s, int c_lo, int c_
         TRY_CUDA(launch_screen(screen_fmt_of(prec, d), N, d, h->seed, h->phi32, count,
                                (uint32_t)c_lo, 0u, 0.0, st, h->mu2_k32 + c_lo, &st->error,
                                h->num_sms, s));
-      GramSource full{};
-      full.perturb = true;
-      full.phi = h->phi32;
-      full.seed = h->seed;
-      full.c0 = (uint32_t)c_lo;
-      full.st = st;
-      full.gate = &st->use_full;
-      TRY_CUDA(launch_gram_f32(N, d, count, full, h->mu2_k32 + c_lo, nullptr, h->num_sms, s));
+      // (not enqueued at all when every iteration screens)
+      if (!(h->screen_min_delta <= 0.0)) {
+        GramSource full{};
+        full.perturb = true;
+        full.phi = h->phi32;
+        full.seed = h->seed;
+        full.c0 = (uint32_t)c_lo;
+        full.st = st;
+        full.gate = &st->use_full;
+        TRY_CUDA(launch_gram_f32(N, d, count, full, h->mu2_k32 + c_lo, nullptr, h->num_sms, s));
+      }
     }
   }
   return TRSTMI_OK;
@@ -299,32 +287,69 @@ int enqueue_iteration_finish(trstmi_instance* h, cudaStream_t s) {
     TRY_CUDA(launch_commit_f32(N, d, h->seed, st, h->phi32, h->phi64, s));
   } else {
     const int k = h->opt.topk;
+    const int fmt = screen_fmt_of(prec, d);
+    const bool screens = screen_supported(N, d, fmt);
+    // an iteration that ranked with the binary32 Gram of every candidate
+    // certifies through the binary32 filter pass; none does when every
+    // iteration screens
+    const bool filter = !(h->screen_min_delta <= 0.0);
     TRY_CUDA(launch_topk(st, h->mu2_k32, K, k, h->topk, h->mu2_top, s));
-    // re-score the survivors in binary32 when the screen ranked them (ranked by
-    // the binary32 Gram of every candidate, k_topk copied their scores)
+    // the survivors drawn once in binary32 (the tile pass's gen_column
+    // arithmetic), then their re-score: over the pairs the survivor pair pass
+    // lists (every pair that can be a survivor's binary32 or binary64
+    // maximum), and over all pairs only for a survivor whose list overflowed
+    // (each pass returns at once unless the screen ranked the candidates;
+    // otherwise k_topk copied the binary32 scores)
+    TRY_CUDA(launch_gen_planes_f32(N, d, k, h->phi32, h->seed, 0u, st, 0u, 0.0, h->planes_top, s,
+                                   h->topk, &st->use_screen));
     GramSource src{};
     src.perturb = true;
     src.phi = h->phi32;
     src.seed = h->seed;
     src.cand_list = h->topk;
     src.st = st;
-    src.gate = &st->use_screen;
-    // the survivors drawn once (the tile pass's gen_column arithmetic), then
-    // the double-buffered tile pass over them
-    TRY_CUDA(launch_gen_planes_f32(N, d, k, h->phi32, h->seed, 0u, st, 0u, 0.0, h->planes_top, s,
-                                   h->topk, &st->use_screen));
     src.planes = h->planes_top;
+    if (screens) {
+      TRY_CUDA(launch_screen_pairs(fmt, N, d, h->seed, h->phi32, st, h->topk, h->mu2_k32, k,
+                                   screen_pair_err(fmt), h->slists, h->scount, kListCap, h->sover,
+                                   &st->error, h->num_sms, s));
+      TRY_CUDA(launch_pairs32(st, h->slists, h->scount, kListCap, k, N, d, h->planes_top,
+                              h->mu2_top, s));
+      src.gate = h->sover;
+    } else {
+      src.gate = &st->use_screen;
+    }
     TRY_CUDA(launch_gram_f32(N, d, k, src, h->mu2_top, nullptr, h->num_sms, s));
     TRY_CUDA(launch_materialize64(N, d, h->seed, st, h->topk, h->mu2_top, k, h->phi64,
-                                  h->cand64, h->cand32, s, h->cert32));
-    // cert32[0..1] and cert64 were zeroed by iter_begin (contiguous block);
-    // the passes run only for a survivor the rule could accept (st->certify),
-    // from the survivor's binary32 score as the filter hint
-    int rc = enqueue_certify(h, h->cand64, h->cand32, h->cert64, &st->certify, &st->npairs,
-                             &st->overflow, s, true);
-    if (rc) return rc;
-    TRY_CUDA(launch_decide_certified(st, h->cert64, h->trace, s));
-    TRY_CUDA(launch_commit_copy(N, d, st, h->cand64, h->cand32, h->phi64, h->phi32, s));
+                                  h->cand64, h->cand32, s, h->cert32, h->scount,
+                                  screens ? kListCap : 0u, h->ssel, filter));
+    // certification of a survivor the rule could accept (st->certify):
+    // binary64 over the winner's listed pairs, or over the pairs the binary32
+    // filter pass keeps from the survivor's binary32 score as the hint
+    // (cert32[0..1] and cert64 were zeroed by iter_begin), or over all pairs
+    // when neither covers the maximum (st->overflow)
+    if (filter) {
+      GramSource fs{};
+      fs.perturb = false;
+      fs.phi = h->cand32;
+      fs.normalize = false;
+      fs.gate = &h->ssel[1];
+      PairFilter pf{h->cert32, certify_margin(d), h->pairs, &st->npairs, kPairCap, &st->overflow,
+                    nullptr, (float)certify_margin_mu2(d)};
+      TRY_CUDA(launch_gram_f32(N, d, 1, fs, h->cert32 + 1, &pf, h->num_sms, s));
+    }
+    TRY_CUDA(launch_pairs64(&st->certify, &st->npairs, h->pairs, kPairCap, d, h->cand64,
+                            h->cert64, s, h->cert32, h->cert32 + 1,
+                            (float)certify_margin_mu2(d), &st->overflow, h->ssel, h->slists,
+                            h->scount, screens ? kListCap : 0u));
+    GramSource full{};
+    full.perturb = false;
+    full.phi = h->cand64;
+    full.normalize = false;
+    full.gate = &st->overflow;  // reset every iteration, so 0 when the iteration is inactive
+    TRY_CUDA(launch_gram_f64(N, d, 1, full, h->cert64, h->num_sms, s));
+    TRY_CUDA(launch_decide_commit(N, d, st, h->cert64, h->trace, h->cand64, h->cand32,
+                                  h->phi64, h->phi32, &h->misc[2], s));
   }
   return TRSTMI_OK;
 }
@@ -477,11 +502,11 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   const size_t o_s64 = take(nd * sizeof(double2));
   const size_t o_k32 = take((size_t)K * sizeof(unsigned int));
   const size_t o_k64 = take((size_t)K * sizeof(unsigned long long));
-  const size_t o_top = take((size_t)k * sizeof(unsigned int));
+  const size_t o_top = take(top_words(k) * sizeof(uint32_t));
   const size_t o_topk = take((size_t)k * sizeof(uint32_t));
   // cert32[2] followed by cert64 in one 16-byte span (zeroed together)
   const size_t o_cert = take(2 * sizeof(unsigned int) + sizeof(unsigned long long));
-  const size_t o_misc = take(2 * sizeof(uint32_t));
+  const size_t o_misc = take(4 * sizeof(uint32_t));
   const size_t o_pairs = take((size_t)kPairCap * sizeof(uint2));
   const size_t o_trace = take((size_t)std::max(o.trace_cap, 1) * sizeof(TraceRowDev));
   // TRSTMI_FP32: room for the iteration's K candidates (up to 1 GiB), so each
@@ -492,6 +517,8 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
                               ? take(planes_bytes) : (size_t)-1;
   const size_t o_ptop = is_screen(o.precision) ? take((size_t)k * 2 * nd * sizeof(float))
                                                : (size_t)-1;
+  const size_t o_lists = is_screen(o.precision) ? take((size_t)k * kListCap * sizeof(uint2))
+                                                : (size_t)-1;
   h->block_bytes = off;
   if (h->dmem.allocate(&h->block, off) != cudaSuccess) {
     cudaGetLastError();
@@ -508,6 +535,9 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   h->mu2_k32 = (unsigned int*)(b + o_k32);
   h->mu2_k64 = (unsigned long long*)(b + o_k64);
   h->mu2_top = (unsigned int*)(b + o_top);
+  h->scount = (uint32_t*)(b + o_top) + k;
+  h->sover = h->scount + k;
+  h->ssel = h->sover + 1;
   h->topk = (uint32_t*)(b + o_topk);
   h->cert32 = (unsigned int*)(b + o_cert);
   h->cert64 = (unsigned long long*)(b + o_cert + 2 * sizeof(unsigned int));
@@ -516,6 +546,7 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   h->trace = (TraceRowDev*)(b + o_trace);
   if (o_planes != (size_t)-1) h->planes = (float*)(b + o_planes);
   if (o_ptop != (size_t)-1) h->planes_top = (float*)(b + o_ptop);
+  if (o_lists != (size_t)-1) h->slists = (uint2*)(b + o_lists);
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
     trstmi_destroy(h);
     return TRSTMI_ECUDA;
@@ -536,6 +567,7 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
                             ? std::numeric_limits<double>::infinity()
                             : o.screen_min_delta;
   s0.trace_cap = (uint32_t)o.trace_cap;
+  h->screen_min_delta = s0.screen_min_delta;
   cudaStream_t s = h->stream;
   if (cudaMemsetAsync(h->block, 0, off, s) != cudaSuccess ||
       cudaMemcpyAsync(h->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -742,6 +774,7 @@ int trstmi_set_state(trstmi_handle h, const void* blob, size_t size) {
   USE_DEVICE(h->opt.device);
   DevState st = hd.st;
   st.trace_cap = (uint32_t)h->opt.trace_cap;
+  st.screen_min_delta = h->screen_min_delta;   // this handle's options rule
   const char* p = (const char*)blob;
   TRY_CUDA(cudaMemcpyAsync(h->st, &st, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
   TRY_CUDA(cudaMemcpyAsync(h->phi64, p + sizeof(BlobHeader), nd * sizeof(double2),

@@ -164,10 +164,17 @@ cudaError_t launch_topk(DevState* st, const unsigned int* mu2_screen, int K, int
                         uint32_t* topk, unsigned int* mu2_top, cudaStream_t s);
 // hint_out (nullable): receives the chosen survivor's binary32 score bits
 // when it is certified (the certification's filter hint).
+// sel (nullable): sel[0] receives the winner's survivor slot and sel[1] 1 when
+// its certification needs the binary32 filter pass (its pair list from the
+// survivor pair pass, list_count / list_cap, is missing or overflowed); with
+// filter_available false such a winner sets st->overflow instead (the full
+// binary64 pass).
 cudaError_t launch_materialize64(int N, int d, uint64_t seed, DevState* st,
                                  const uint32_t* topk, const unsigned int* mu2_top, int k,
                                  const double2* phi64, double2* cand64, float2* cand32,
-                                 cudaStream_t s, unsigned int* hint_out = nullptr);
+                                 cudaStream_t s, unsigned int* hint_out = nullptr,
+                                 const uint32_t* list_count = nullptr, uint32_t list_cap = 0,
+                                 uint32_t* sel = nullptr, bool filter_available = true);
 // hint_bits / own_bits (nullable): the filter pass ran from a hint (its
 // slack hint_slack_mu2) instead of the frame's binary32 max; if the hint less
 // its slack exceeds the pass's own max (own_bits), the kept set may miss the
@@ -176,12 +183,37 @@ cudaError_t launch_pairs64(const uint32_t* active, const uint32_t* npairs, const
                            uint32_t cap, int d, const double2* frame64, unsigned long long* out,
                            cudaStream_t s, const unsigned int* hint_bits = nullptr,
                            const unsigned int* own_bits = nullptr, float hint_slack_mu2 = 0.f,
-                           uint32_t* overflow = nullptr);
-cudaError_t launch_decide_certified(DevState* st, const unsigned long long* mu2_64,
-                                    TraceRowDev* trace, cudaStream_t s);
-cudaError_t launch_commit_copy(int N, int d, DevState* st, const double2* cand64,
-                               const float2* cand32, double2* phi64, float2* phi32,
-                               cudaStream_t s);
+                           uint32_t* overflow = nullptr, const uint32_t* sel = nullptr,
+                           const uint2* lists = nullptr, const uint32_t* list_count = nullptr,
+                           uint32_t list_cap = 0);
+// Binary64 mu^2 of a normalised frame into *cert64 by the certification
+// passes (binary32 max into cert32[0], filter pass into cert32[1] / pairs /
+// *npairs, binary64 over the kept pairs, all pairs when *overflow is set);
+// cert32[0..1], *cert64, *npairs and *overflow zero before.  active: gate.
+cudaError_t launch_frame_certify(int N, int d, const double2* p64, const float2* p32,
+                                 unsigned int* cert32, unsigned long long* cert64, uint2* pairs,
+                                 uint32_t cap, uint32_t* npairs, uint32_t* overflow,
+                                 const uint32_t* active, int num_sms, cudaStream_t s);
+// |G| margin between a frame's binary32 and binary64 Gram entries
+float certify_margin(int d);
+// sel (nullable, from launch_materialize64): when sel[1] is 0 the pairs are the
+// winner's list, lists + sel[0] * list_cap (list_count[sel[0]] of them),
+// instead of pairs / npairs, and the hint check is skipped.
+// binary32 |G|^2 of each survivor's listed pairs (lists, k x cap; count[s]
+// above cap: left to the full pass) from its drawn planes, maxed into mu2[s]
+// with the bits the binary32 tile pass gives those pairs.  Returns at once
+// unless the iteration in st is active and screened.
+cudaError_t launch_pairs32(const DevState* st, const uint2* lists, const uint32_t* count,
+                           uint32_t cap, int k, int N, int d, const float* planes,
+                           unsigned int* mu2, cudaStream_t s);
+// The accept/radius rule on the certified binary64 mu^2 (or, uncertified, on
+// the survivor's binary32 score) with its trace row, and the copy of the
+// accepted candidate into the frame, in one launch; *done is a
+// zero-initialised counter the launch leaves at zero
+cudaError_t launch_decide_commit(int N, int d, DevState* st, const unsigned long long* mu2_64,
+                                 TraceRowDev* trace, const double2* cand64, const float2* cand32,
+                                 double2* phi64, float2* phi32, unsigned int* done,
+                                 cudaStream_t s);
 // frame utilities
 cudaError_t launch_normalize64(int N, int d, const double2* in, double2* out64, float2* out32,
                                DevState* st, cudaStream_t s);
@@ -216,6 +248,18 @@ cudaError_t launch_screen(int fmt, int N, int d, uint64_t seed, const float2* ph
 // block is ever filled, so the MMA issuer's first wait runs out after
 // wait_limit_ns (at most the default bound), sets err_flag's timeout bit and
 // every role of each CTA leaves.  Exercises the bounded waits.
+// Survivor pair pass (tc_screen.cu): for each of the k survivors (candidate
+// topk[s] of the iteration in st, screen score mu2[topk[s]]), the pairs whose
+// screened |G| is at least sqrt(score) - 2 err go to pairs[s * cap ..] with
+// count[s] (zeroed before); count[s] > cap marks an overflowed list and sets
+// *overflow_any.  Returns at once unless the iteration is active and screened.
+cudaError_t launch_screen_pairs(int fmt, int N, int d, uint64_t seed, const float2* phi32,
+                                const DevState* st, const uint32_t* topk,
+                                const unsigned int* mu2, int k, float err, uint2* pairs,
+                                uint32_t* count, uint32_t cap, uint32_t* overflow_any,
+                                uint32_t* err_flag, int num_sms, cudaStream_t s);
+// the err of launch_screen_pairs for screen format fmt
+float screen_pair_err(int fmt);
 cudaError_t launch_screen_wait_test(int fmt, int N, int d, const float2* phi32, int K,
                                     unsigned int* mu2_out, uint32_t* err_flag,
                                     unsigned long long wait_limit_ns, int num_sms,

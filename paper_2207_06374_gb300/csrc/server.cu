@@ -328,7 +328,7 @@ int admit(trstmi_server* sv, uint64_t ticket, Req& r, Slot* out) {
     sd.cert64 = (unsigned long long*)q; q += up256(sizeof(unsigned long long));
     sd.pairs = (uint2*)q;
     sd.topk_n = o.topk;
-    sd.pair_cap = slot_pair_cap(sd.N);
+    sd.pair_cap = slot_pair_cap(N);
   }
   sd.st = sv->d_states + sl.state_idx;
   sd.phi = sv->f64 ? (void*)p64 : (void*)p32;
@@ -352,19 +352,25 @@ int admit(trstmi_server* sv, uint64_t ticket, Req& r, Slot* out) {
       cudaMemcpyAsync(sd.st, &s0, sizeof(s0), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       launch_init_frame(N, d, sd.seed, p64, p32, sd.st, s) != cudaSuccess)
     return TRSTMI_ECUDA;
-  // initial score in the deciding precision (binary64 in the screen modes)
+  // initial score in the deciding precision (binary64 in the screen modes,
+  // certified by the same passes as the standalone instance's)
   GramSource src{};
   src.perturb = false;
-  src.phi = sv->screen ? (const void*)p64 : sd.phi;
+  src.phi = sd.phi;
   void* init_out = sv->screen ? (void*)sd.cert64 : mu2;
-  cudaError_t e = (sv->f64 || sv->screen)
-      ? launch_gram_f64(N, d, 1, src, (unsigned long long*)init_out, sv->num_sms, s)
-      : launch_gram_f32(N, d, 1, src, (unsigned int*)init_out, nullptr, sv->num_sms, s);
+  cudaError_t e =
+      sv->screen ? launch_frame_certify(N, d, p64, p32, sd.cert32, sd.cert64, sd.pairs,
+                                        sd.pair_cap, &sd.st->npairs, &sd.st->overflow, nullptr,
+                                        sv->num_sms, s)
+      : sv->f64  ? launch_gram_f64(N, d, 1, src, (unsigned long long*)init_out, sv->num_sms, s)
+                 : launch_gram_f32(N, d, 1, src, (unsigned int*)init_out, nullptr, sv->num_sms, s);
   if (e != cudaSuccess) return TRSTMI_ECUDA;
   if (sv->f64 || sv->screen) k_srv_set_mu2cur<unsigned long long><<<1, 1, 0, s>>>(sd.st, init_out);
   else k_srv_set_mu2cur<unsigned int><<<1, 1, 0, s>>>(sd.st, init_out);
   if (cudaGetLastError() != cudaSuccess) return TRSTMI_ECUDA;
-  sv->launches += 3;   // initial frame, initial score, its copy into the state
+  // initial frame, initial score (four certification passes in the screen
+  // modes), its copy into the state
+  sv->launches += sv->screen ? 6 : 3;
   // tile width: the cached choice for this (d, N) bucket, measured if new
   sd.R = 1;
   sd.ntiles = tiles_at_width(N, 1);

@@ -854,13 +854,15 @@ cudaError_t launch_topk(DevState* st, const unsigned int* mu2_screen, int K, int
 __global__ void k_materialize64(int N, int d, uint64_t seed, DevState* st,
                                 const uint32_t* topk, const unsigned int* mu2_top, int k,
                                 const double2* phi64, double2* cand64, float2* cand32,
-                                unsigned int* hint_out) {
+                                unsigned int* hint_out, const uint32_t* list_count,
+                                uint32_t list_cap, uint32_t* sel, int filter_available) {
   if (!st->active) return;
   unsigned int bv = mu2_top[0];
   uint32_t bc = topk[0];
+  int bs = 0;
   for (int s = 1; s < k; ++s) {
     const unsigned int v = mu2_top[s];
-    if (v < bv || (v == bv && topk[s] < bc)) { bv = v; bc = topk[s]; }
+    if (v < bv || (v == bv && topk[s] < bc)) { bv = v; bc = topk[s]; bs = s; }
   }
   // certify only a survivor the exact rule could accept
   const double m32 = (double)__uint_as_float(bv);
@@ -873,6 +875,16 @@ __global__ void k_materialize64(int N, int d, uint64_t seed, DevState* st,
     st->mu2_screen = m32;
     st->certify = cert ? 1u : 0u;
     if (hint_out && cert) *hint_out = bv;
+    if (sel) {
+      // the winner's pair list from the survivor pair pass, when complete,
+      // holds every pair the certification needs; otherwise the binary32
+      // filter pass runs, or without one the full binary64 pass
+      sel[0] = (uint32_t)bs;
+      const bool listed = st->use_screen && list_count[bs] <= list_cap;
+      const bool need = cert && !listed;
+      sel[1] = (need && filter_available) ? 1u : 0u;
+      if (need && !filter_available) st->overflow = 1u;
+    }
   }
   if (!cert || j >= N) return;
   const bool ok = gen_column_warp<double>(phi64, d, j, seed, bc, st->t + 1u, 0u, st->delta_used,
@@ -888,84 +900,202 @@ __global__ void k_materialize64(int N, int d, uint64_t seed, DevState* st,
 cudaError_t launch_materialize64(int N, int d, uint64_t seed, DevState* st,
                                  const uint32_t* topk, const unsigned int* mu2_top, int k,
                                  const double2* phi64, double2* cand64, float2* cand32,
-                                 cudaStream_t s, unsigned int* hint_out) {
+                                 cudaStream_t s, unsigned int* hint_out,
+                                 const uint32_t* list_count, uint32_t list_cap, uint32_t* sel,
+                                 bool filter_available) {
   const size_t threads = (size_t)N * 32;
-  k_materialize64<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(N, d, seed, st, topk, mu2_top,
-                                                                   k, phi64, cand64, cand32,
-                                                                   hint_out);
+  k_materialize64<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+      N, d, seed, st, topk, mu2_top, k, phi64, cand64, cand32, hint_out, list_count, list_cap,
+      sel, filter_available ? 1 : 0);
   return cudaGetLastError();
 }
 
-// binary64 |G_jk|^2 of the preselected pairs.
+// binary32 |G_jk|^2 of each survivor's listed pairs from its drawn planes
+// ([i][column], real then imaginary, 2 d N floats per survivor), maxed into
+// mu2[s]: the chain over i and the rounding of MicroTile::step and pair_abs2,
+// so every pair has the bits the binary32 tile pass gives it.  A survivor
+// whose list overflowed (count above cap) is left to the full pass.
+__global__ void k_pairs32(const DevState* st, const uint2* lists, const uint32_t* count,
+                          uint32_t cap, int k, int N, int d, const float* planes,
+                          unsigned int* mu2) {
+  if (!st->active || !st->use_screen) return;
+  // survivor blockIdx.y; one warp per listed pair: lane l loads entries l,
+  // l + 32, .. of both columns (all loads of a pair in flight together), and
+  // every lane runs the chain over i on the values broadcast from their lanes
+  const int sv = blockIdx.y;
+  const uint32_t n = count[sv];
+  if (n > cap) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  const float* re = planes + (size_t)sv * 2 * d * N;
+  const float* im = re + (size_t)d * N;
+  for (uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n; q += warps) {
+    const uint2 jk = lists[(size_t)sv * cap + q];
+    float gr = 0.f, gi = 0.f;
+    for (int i0 = 0; i0 < d; i0 += 32) {
+      const int i = i0 + lane;
+      const size_t o = (size_t)i * N;
+      const float ar = i < d ? re[o + jk.x] : 0.f, ai = i < d ? im[o + jk.x] : 0.f;
+      const float br = i < d ? re[o + jk.y] : 0.f, bi = i < d ? im[o + jk.y] : 0.f;
+      const int m = min(32, d - i0);
+      for (int t = 0; t < m; ++t) {
+        const float a = __shfl_sync(0xffffffffu, ar, t), b = __shfl_sync(0xffffffffu, ai, t);
+        const float c = __shfl_sync(0xffffffffu, br, t), e = __shfl_sync(0xffffffffu, bi, t);
+        gr = fmaf(a, c, fmaf(b, e, gr));
+        gi = fmaf(a, e, fmaf(-b, c, gi));
+      }
+    }
+    if (lane == 0) atomic_max_nonneg(mu2 + sv, pair_abs2(gr, gi));
+  }
+}
+
+cudaError_t launch_pairs32(const DevState* st, const uint2* lists, const uint32_t* count,
+                           uint32_t cap, int k, int N, int d, const float* planes,
+                           unsigned int* mu2, cudaStream_t s) {
+  const unsigned bx = std::min(16u, (cap + 7) / 8);
+  k_pairs32<<<dim3(bx, (unsigned)k), 256, 0, s>>>(st, lists, count, cap, k, N, d, planes, mu2);
+  return cudaGetLastError();
+}
+
+// |G| in binary32 of a frame rounded from binary64 differs from the binary64
+// |G| by at most ~(2 + 2 (2d)) u, u = 2^-24 (rounding of the entries plus a
+// 2d-term dot product per part); twice a generous 4x of that bound separates
+// "can be the maximum" from "cannot".
+float certify_margin(int d) { return (float)(8.0 * (2.0 * d + 2.0) * std::ldexp(1.0, -24)); }
+
+// Binary64 mu^2 of a normalised frame (p64, and p32 its binary32 rounding)
+// into *cert64: the binary32 maximum (cert32[0]), the pairs within the
+// binary32 / binary64 margin of it (filter pass into cert32[1] and pairs),
+// those pairs in binary64, and all pairs in binary64 when the list
+// overflowed.  cert32[0..1], *cert64, *npairs and *overflow start at zero.
+// Every certified mu^2 of the precision form comes from these passes (or the
+// iteration's own pair lists), so a frame has one certified value whatever
+// entry point scores it.
+cudaError_t launch_frame_certify(int N, int d, const double2* p64, const float2* p32,
+                                 unsigned int* cert32, unsigned long long* cert64, uint2* pairs,
+                                 uint32_t cap, uint32_t* npairs, uint32_t* overflow,
+                                 const uint32_t* active, int num_sms, cudaStream_t s) {
+  GramSource src{};
+  src.perturb = false;
+  src.phi = p32;
+  src.normalize = false;
+  src.gate = active;
+  cudaError_t e = launch_gram_f32(N, d, 1, src, cert32, nullptr, num_sms, s);
+  if (e != cudaSuccess) return e;
+  PairFilter pf{cert32, certify_margin(d), pairs, npairs, cap, overflow, nullptr, 0.f};
+  if ((e = launch_gram_f32(N, d, 1, src, cert32 + 1, &pf, num_sms, s)) != cudaSuccess) return e;
+  if ((e = launch_pairs64(active, npairs, pairs, cap, d, p64, cert64, s)) != cudaSuccess) return e;
+  GramSource full{};
+  full.perturb = false;
+  full.phi = p64;
+  full.normalize = false;
+  full.gate = overflow;
+  return launch_gram_f64(N, d, 1, full, cert64, num_sms, s);
+}
+
+// binary64 |G_jk|^2 of columns x and y (d entries each) by one warp: lane l
+// accumulates entries l, l + 32, .. (each part two fused multiply-adds, as in
+// the tile passes), and the lanes' partial sums meet in a butterfly of
+// additions, which leaves the same bits in every lane (a + b = b + a).  Every
+// binary64 pair kernel of the precision form uses it, so a pair has one value
+// whatever kernel evaluates it; the dependent chain is 2 d / 32 fused
+// multiply-adds and five additions instead of 2 d (binary64 latency is long
+// on this GPU).
+__device__ __forceinline__ double pair_abs2_warp64(const double2* x, const double2* y, int d,
+                                                   int lane) {
+  double re = 0.0, im = 0.0;
+  for (int i = lane; i < d; i += 32) {
+    const double2 u = x[i], v = y[i];
+    re = fma(u.x, v.x, fma(u.y, v.y, re));
+    im = fma(u.x, v.y, fma(-u.y, v.x, im));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  return pair_abs2(re, im);
+}
+
+// binary64 |G_jk|^2 of the preselected pairs, one warp per pair.
 __global__ void k_pairs64(const uint32_t* active, const uint32_t* npairs, const uint2* pairs,
                           uint32_t cap, int d, const double2* f, unsigned long long* out,
                           const unsigned int* hint_bits, const unsigned int* own_bits,
-                          float hint_slack_mu2, uint32_t* overflow) {
+                          float hint_slack_mu2, uint32_t* overflow, const uint32_t* sel,
+                          const uint2* lists, const uint32_t* list_count, uint32_t list_cap) {
   if (active && !*active) return;
-  if (hint_bits && blockIdx.x == 0 && threadIdx.x == 0 &&
-      fmaxf(__uint_as_float(*hint_bits) - hint_slack_mu2, 0.0f) > __uint_as_float(*own_bits))
-    atomicExch(overflow, 1u);
-  const uint32_t n = min(*npairs, cap);
-  double m = 0.0;
-  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const uint2 jk = pairs[p];
-    const double2* x = f + (size_t)jk.x * d;
-    const double2* y = f + (size_t)jk.y * d;
-    double re = 0.0, im = 0.0;
-    for (int i = 0; i < d; ++i) {
-      const double2 u = x[i], v = y[i];
-      re = fma(u.x, v.x, fma(u.y, v.y, re));
-      im = fma(u.x, v.y, fma(-u.y, v.x, im));
-    }
-    m = fmax(m, pair_abs2(re, im));
+  uint32_t n;
+  if (sel && sel[1] == 0u) {
+    // the winner's list from the survivor pair pass (complete: see k_materialize64)
+    const uint32_t w = sel[0];
+    pairs = lists + (size_t)w * list_cap;
+    n = min(list_count[w], list_cap);
+  } else {
+    if (hint_bits && blockIdx.x == 0 && threadIdx.x == 0 &&
+        fmaxf(__uint_as_float(*hint_bits) - hint_slack_mu2, 0.0f) > __uint_as_float(*own_bits))
+      atomicExch(overflow, 1u);
+    n = min(*npairs, cap);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_nonneg(out, m);
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  double m = 0.0;
+  for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += warps) {
+    const uint2 jk = pairs[p];
+    m = fmax(m, pair_abs2_warp64(f + (size_t)jk.x * d, f + (size_t)jk.y * d, d, lane));
+  }
+  if (lane == 0 && m > 0.0) atomic_max_nonneg(out, m);
 }
 
 cudaError_t launch_pairs64(const uint32_t* active, const uint32_t* npairs, const uint2* pairs,
                            uint32_t cap, int d, const double2* frame64, unsigned long long* out,
                            cudaStream_t s, const unsigned int* hint_bits,
                            const unsigned int* own_bits, float hint_slack_mu2,
-                           uint32_t* overflow) {
-  k_pairs64<<<64, 256, 0, s>>>(active, npairs, pairs, cap, d, frame64, out, hint_bits, own_bits,
-                               hint_slack_mu2, overflow);
+                           uint32_t* overflow, const uint32_t* sel, const uint2* lists,
+                           const uint32_t* list_count, uint32_t list_cap) {
+  k_pairs64<<<256, 256, 0, s>>>(active, npairs, pairs, cap, d, frame64, out, hint_bits, own_bits,
+                               hint_slack_mu2, overflow, sel, lists, list_count, list_cap);
   return cudaGetLastError();
 }
 
-__global__ void k_decide_certified(DevState* st, const unsigned long long* mu2_64,
-                                   TraceRowDev* trace) {
+// The rule and the commit of the certified (or bound-rejected) survivor in one
+// launch: every CTA forms the same decision from the state as the iteration
+// left it and copies its share of the candidate when it is accepted; the last
+// CTA to finish (counter *done, reset by that CTA) then applies the rule and
+// writes the trace row, so no CTA reads the state after it changed.
+__global__ void k_decide_commit(size_t n, DevState* st, const unsigned long long* mu2_64,
+                                TraceRowDev* trace, const double2* cand64, const float2* cand32,
+                                double2* phi64, float2* phi32, unsigned int* done) {
   if (!st->active) return;
-  // uncertified: the survivor's binary32 score is above the current mu^2 by
-  // more than the error bound, and the rule rejects it on that value
   const bool cert = st->certify != 0u;
-  apply_rule_and_trace(st, st->cstar, cert ? nonneg_from_bits(*mu2_64) : st->mu2_screen,
-                       st->mu2_screen, trace, (cert ? 0u : 2u) | (st->overflow ? 4u : 0u));
-}
-
-cudaError_t launch_decide_certified(DevState* st, const unsigned long long* mu2_64,
-                                    TraceRowDev* trace, cudaStream_t s) {
-  k_decide_certified<<<1, 1, 0, s>>>(st, mu2_64, trace);
-  return cudaGetLastError();
-}
-
-__global__ void k_commit_copy(size_t n, DevState* st, const double2* cand64,
-                              const float2* cand32, double2* phi64, float2* phi32) {
-  if (!st->active || !st->accepted) return;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
-       e += (size_t)gridDim.x * blockDim.x) {
-    phi64[e] = cand64[e];
-    phi32[e] = cand32[e];
+  const double best = cert ? nonneg_from_bits(*mu2_64) : st->mu2_screen;
+  if (best < st->mu2_cur) {   // the rule's acceptance test
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * blockDim.x) {
+      phi64[e] = cand64[e];
+      phi32[e] = cand32[e];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(done, 1u) == gridDim.x - 1u) {
+      *done = 0u;
+      __threadfence();
+      // uncertified: the survivor's binary32 score is above the current mu^2
+      // by more than the error bound, and the rule rejects it on that value
+      apply_rule_and_trace(st, st->cstar, best, st->mu2_screen, trace,
+                           (cert ? 0u : 2u) | (st->overflow ? 4u : 0u));
+    }
   }
 }
 
-cudaError_t launch_commit_copy(int N, int d, DevState* st, const double2* cand64,
-                               const float2* cand32, double2* phi64, float2* phi32,
-                               cudaStream_t s) {
+cudaError_t launch_decide_commit(int N, int d, DevState* st, const unsigned long long* mu2_64,
+                                 TraceRowDev* trace, const double2* cand64, const float2* cand32,
+                                 double2* phi64, float2* phi32, unsigned int* done,
+                                 cudaStream_t s) {
   const size_t n = (size_t)N * d;
   const int grid = (int)std::min<size_t>((n + 255) / 256, 1024);
-  k_commit_copy<<<grid, 256, 0, s>>>(n, st, cand64, cand32, phi64, phi32);
+  k_decide_commit<<<grid, 256, 0, s>>>(n, st, mu2_64, trace, cand64, cand32, phi64, phi32, done);
   return cudaGetLastError();
 }
 
@@ -1420,22 +1550,13 @@ __global__ void k_batch_pairs64(SlotDesc* slots, int n) {
           __uint_as_float(sd.cert32[1]))
     atomicExch(&const_cast<DevState*>(st)->overflow, 1u);
   const uint32_t np = min(st->npairs, sd.pair_cap);
-  const int d = sd.d;
+  const int d = sd.d, lane = threadIdx.x & 31;
   double m = 0.0;
-  for (uint32_t p = threadIdx.x; p < np; p += blockDim.x) {
+  for (uint32_t p = threadIdx.x >> 5; p < np; p += blockDim.x >> 5) {
     const uint2 jk = sd.pairs[p];
-    const double2* x = sd.cand64 + (size_t)jk.x * d;
-    const double2* y = sd.cand64 + (size_t)jk.y * d;
-    double re = 0.0, im = 0.0;
-    for (int i = 0; i < d; ++i) {
-      const double2 u = x[i], v = y[i];
-      re = fma(u.x, v.x, fma(u.y, v.y, re));
-      im = fma(u.x, v.y, fma(-u.y, v.x, im));
-    }
-    m = fmax(m, pair_abs2(re, im));
+    m = fmax(m, pair_abs2_warp64(sd.cand64 + (size_t)jk.x * d, sd.cand64 + (size_t)jk.y * d, d,
+                                 lane));
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_nonneg(sd.cert64, m);
 }
 

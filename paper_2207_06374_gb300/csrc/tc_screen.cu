@@ -24,6 +24,7 @@
 
 #include "kernels.h"
 #include "philox.cuh"
+#include "tile.cuh"
 
 namespace trstmi {
 namespace {
@@ -479,6 +480,151 @@ __device__ __forceinline__ void absmax(const uint32_t (&re)[W], const uint32_t (
   }
 }
 
+// The MMAs of one tile: A (block I) at descriptor low word alo, B (block J)
+// at blo, into the Re accumulator at tensor-memory column dre and the Im one
+// at dim (the high descriptor word is hi).
+template <int F>
+__device__ __forceinline__ void issue_tile_mmas(uint32_t alo, uint32_t blo, uint32_t dre,
+                                                uint32_t dim, uint32_t hi) {
+  if constexpr (FmtTraits<F>::kTwoAtoms) {
+    // K steps of 8 tf32 or 16 bf16 / fp16 = 32 bytes = +2 in the low
+    // word; the second atom (Im parts) is 16 KiB = +1024 further
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)   // Re: A_I^T A_J ...
+      mma_lo<F>(dre, alo + 2u * kk, blo + 2u * kk, Idesc<F>::pos, kk > 0 ? 1u : 0u, hi);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)   // ... + B_I^T B_J
+      mma_lo<F>(dre, alo + 1024u + 2u * kk, blo + 1024u + 2u * kk, Idesc<F>::pos, 1u, hi);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)   // Im: A_I^T B_J ...
+      mma_lo<F>(dim, alo + 2u * kk, blo + 1024u + 2u * kk, Idesc<F>::pos, kk > 0 ? 1u : 0u, hi);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)   // ... - B_I^T A_J
+      mma_lo<F>(dim, alo + 1024u + 2u * kk, blo + 2u * kk, Idesc<F>::neg_a, 1u, hi);
+  } else {
+    // Re: sum over the whole K = 2*DP (4 steps of 16 = +2 in the low word)
+    mma_lo<F>(dre, alo + 0u, blo + 0u, Idesc<F>::pos, 0u, hi);
+    mma_lo<F>(dre, alo + 2u, blo + 2u, Idesc<F>::pos, 1u, hi);
+    mma_lo<F>(dre, alo + 4u, blo + 4u, Idesc<F>::pos, 1u, hi);
+    mma_lo<F>(dre, alo + 6u, blo + 6u, Idesc<F>::pos, 1u, hi);
+    // Im: A_I^T B_J (K slices 0,1 against 2,3) - B_I^T A_J (2,3 against 0,1)
+    mma_lo<F>(dim, alo + 0u, blo + 4u, Idesc<F>::pos, 0u, hi);
+    mma_lo<F>(dim, alo + 2u, blo + 6u, Idesc<F>::pos, 1u, hi);
+    mma_lo<F>(dim, alo + 4u, blo + 0u, Idesc<F>::neg_a, 1u, hi);
+    mma_lo<F>(dim, alo + 6u, blo + 2u, Idesc<F>::neg_a, 1u, hi);
+  }
+}
+
+// Octet o (columns 8o .. 8o+7) of column block jb of candidate `it` into the
+// block at blk, in the operand layout of format F: lane l takes column
+// 8o + (l & 7) and the quarter l >> 3 of its DP padded entries (E = DP/4 of
+// them, E/2 draws), draws and perturbs them, normalises the column (the
+// quarter sums joined by two shuffles) and stores its chunks; the eight lanes
+// of one quarter write eight different 16-byte chunks of a swizzled row
+// group, so the stores are free of bank conflicts.
+template <int F, class Src>
+__device__ __forceinline__ void gen_octet(const Src& src, const ScreenItem& it,
+                                          const PhiloxCand& pc, int o, int jb,
+                                          unsigned char* blk, int lane) {
+  constexpr int kDP = FmtTraits<F>::kDP, kE = FmtTraits<F>::kEntries;
+  const int q = lane >> 3;
+  const int d = it.d, P = (d + 1) >> 1;
+  const int r = 8 * o + (lane & 7);        // row of the block (column of Phi)
+  const int j = jb * kBlockCols + r;
+  float2 x[kE];
+  float2 ss = make_float2(0.f, 0.f);
+  if (j < it.N && d == kDP) {
+    // full width: entries Eq .. Eq+E-1 are 8E contiguous bytes of phi,
+    // read as float4 (two entries) in groups of eight entries
+#pragma unroll
+    for (int h = 0; h < kE / 8; ++h) {
+      const float4* col4 =
+          reinterpret_cast<const float4*>(it.phi + (size_t)j * kDP + kE * q + 8 * h);
+      float4 v[4];
+#pragma unroll
+      for (int pp = 0; pp < 4; ++pp) v[pp] = __ldg(col4 + pp);
+#pragma unroll
+      for (int pp = 0; pp < 4; ++pp) {
+        const PhiloxOut w = src.philox(
+            (uint32_t)j * (uint32_t)(kDP / 2) + (uint32_t)(kE / 2 * q + 4 * h + pp), pc, it);
+        perturb2_fast(w.x, it.delta, make_float2(v[pp].x, v[pp].y),
+                      make_float2(v[pp].z, v[pp].w), x[8 * h + 2 * pp],
+                      x[8 * h + 2 * pp + 1]);
+      }
+    }
+  } else if (j < it.N) {
+    const float2* col = it.phi + (size_t)j * d;
+#pragma unroll
+    for (int pp = 0; pp < kE / 2; ++pp) {
+      const int p = kE / 2 * q + pp;
+      x[2 * pp] = x[2 * pp + 1] = make_float2(0.f, 0.f);
+      if (p < P) {
+        const PhiloxOut w = src.philox((uint32_t)j * (uint32_t)P + (uint32_t)p, pc, it);
+        const int i = 2 * p;
+        const float2 v0 = col[i];
+        const float2 v1 = (i + 1 < d) ? col[i + 1] : make_float2(0.f, 0.f);
+        float2 y0, y1;
+        perturb2_fast(w.x, it.delta, v0, v1, y0, y1);
+        x[2 * pp] = y0;
+        if (i + 1 < d) x[2 * pp + 1] = y1;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < kE; ++e) x[e] = make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int e = 0; e < kE; ++e) ss = __ffma2_rn(x[e], x[e], ss);
+  float sn = ss.x + ss.y;
+  sn += __shfl_xor_sync(0xffffffffu, sn, 8);
+  sn += __shfl_xor_sync(0xffffffffu, sn, 16);
+  const float inv = sn > 0.f ? rsqrtf(sn) : 0.f;
+  const float2 inv2 = make_float2(inv, inv);
+#pragma unroll
+  for (int e = 0; e < kE; ++e) x[e] = __fmul2_rn(x[e], inv2);
+  if constexpr (FmtTraits<F>::kWide16) {
+    // real parts of entries 16q .. 16q+15 -> chunks 2q, 2q+1 of the
+    // first atom; imaginary parts -> the same chunks of the second
+    uint4 re0, re1, im0, im1;
+    re0.x = pack2<F>(x[0].x, x[1].x);   re1.x = pack2<F>(x[8].x, x[9].x);
+    re0.y = pack2<F>(x[2].x, x[3].x);   re1.y = pack2<F>(x[10].x, x[11].x);
+    re0.z = pack2<F>(x[4].x, x[5].x);   re1.z = pack2<F>(x[12].x, x[13].x);
+    re0.w = pack2<F>(x[6].x, x[7].x);   re1.w = pack2<F>(x[14].x, x[15].x);
+    im0.x = pack2<F>(x[0].y, x[1].y);   im1.x = pack2<F>(x[8].y, x[9].y);
+    im0.y = pack2<F>(x[2].y, x[3].y);   im1.y = pack2<F>(x[10].y, x[11].y);
+    im0.z = pack2<F>(x[4].y, x[5].y);   im1.z = pack2<F>(x[12].y, x[13].y);
+    im0.w = pack2<F>(x[6].y, x[7].y);   im1.w = pack2<F>(x[14].y, x[15].y);
+    *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q)) = re0;
+    *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q + 1)) = re1;
+    *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q)) = im0;
+    *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q + 1)) = im1;
+  } else if constexpr (F == kScreenTF32) {
+    // real parts of entries 8q .. 8q+7 -> chunks 2q, 2q+1 of the first
+    // atom; imaginary parts -> the same chunks of the second
+    const uint4 cr0 = make_uint4(to_tf32(x[0].x), to_tf32(x[1].x), to_tf32(x[2].x), to_tf32(x[3].x));
+    const uint4 cr1 = make_uint4(to_tf32(x[4].x), to_tf32(x[5].x), to_tf32(x[6].x), to_tf32(x[7].x));
+    const uint4 ci0 = make_uint4(to_tf32(x[0].y), to_tf32(x[1].y), to_tf32(x[2].y), to_tf32(x[3].y));
+    const uint4 ci1 = make_uint4(to_tf32(x[4].y), to_tf32(x[5].y), to_tf32(x[6].y), to_tf32(x[7].y));
+    *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q)) = cr0;
+    *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q + 1)) = cr1;
+    *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q)) = ci0;
+    *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q + 1)) = ci1;
+  } else {
+    uint4 re, im;
+    re.x = pack2<F>(x[0].x, x[1].x);
+    re.y = pack2<F>(x[2].x, x[3].x);
+    re.z = pack2<F>(x[4].x, x[5].x);
+    re.w = pack2<F>(x[6].x, x[7].x);
+    im.x = pack2<F>(x[0].y, x[1].y);
+    im.y = pack2<F>(x[2].y, x[3].y);
+    im.z = pack2<F>(x[4].y, x[5].y);
+    im.w = pack2<F>(x[6].y, x[7].y);
+    // real parts of entries 8q .. 8q+7 -> chunk q; imaginary -> chunk 4 + q
+    *reinterpret_cast<uint4*>(blk + swz_offset(r, q)) = re;
+    *reinterpret_cast<uint4*>(blk + swz_offset(r, 4 + q)) = im;
+  }
+}
+
 // 20 warps: one SM sub-partition (16K registers) holds 5 of them, so a
 // thread may use at most 16384 / (5 * 32) -> 96 registers
 template <int F, class Src>
@@ -539,114 +685,17 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
     // one quarter write eight different 16-byte chunks of a swizzled row
     // group, so the stores are free of bank conflicts.  Each unit's warp
     // arrives once on the slot's fill barrier (kOctets arrivals complete a
-    // fill).
-    constexpr int kDP = FmtTraits<F>::kDP, kE = FmtTraits<F>::kEntries;
-    const int q = lane >> 3;
+    // fill).  The lanes' layout within a unit is gen_octet's.
     SlotPlan<F> plan;
     uint32_t ucount = 0;      // octet units so far (16 per block instance)
     const int gen_items = src.withhold() ? 0 : nitems;
     for (int idx = blockIdx.x; idx < gen_items; idx += gridDim.x) {
       ScreenItem it;
       if (!src.item(idx, t0, delta0, it)) continue;
-      const int d = it.d, P = (d + 1) >> 1;
       const PhiloxCand pc = src.cand(it);
       // octet o of column block jb into slot `slot`
       auto fill_octet = [&](int o, int jb, int slot) {
-        unsigned char* blk = xs + slot * (uint32_t)kBlockBytes;
-        const int r = 8 * o + (lane & 7);        // row of the block (column of Phi)
-        const int j = jb * kBlockCols + r;
-        float2 x[kE];
-        float2 ss = make_float2(0.f, 0.f);
-        if (j < it.N && d == kDP) {
-          // full width: entries Eq .. Eq+E-1 are 8E contiguous bytes of phi,
-          // read as float4 (two entries) in groups of eight entries
-#pragma unroll
-          for (int h = 0; h < kE / 8; ++h) {
-            const float4* col4 =
-                reinterpret_cast<const float4*>(it.phi + (size_t)j * kDP + kE * q + 8 * h);
-            float4 v[4];
-#pragma unroll
-            for (int pp = 0; pp < 4; ++pp) v[pp] = __ldg(col4 + pp);
-#pragma unroll
-            for (int pp = 0; pp < 4; ++pp) {
-              const PhiloxOut w = src.philox(
-                  (uint32_t)j * (uint32_t)(kDP / 2) + (uint32_t)(kE / 2 * q + 4 * h + pp), pc, it);
-              perturb2_fast(w.x, it.delta, make_float2(v[pp].x, v[pp].y),
-                            make_float2(v[pp].z, v[pp].w), x[8 * h + 2 * pp],
-                            x[8 * h + 2 * pp + 1]);
-            }
-          }
-        } else if (j < it.N) {
-          const float2* col = it.phi + (size_t)j * d;
-#pragma unroll
-          for (int pp = 0; pp < kE / 2; ++pp) {
-            const int p = kE / 2 * q + pp;
-            x[2 * pp] = x[2 * pp + 1] = make_float2(0.f, 0.f);
-            if (p < P) {
-              const PhiloxOut w = src.philox((uint32_t)j * (uint32_t)P + (uint32_t)p, pc, it);
-              const int i = 2 * p;
-              const float2 v0 = col[i];
-              const float2 v1 = (i + 1 < d) ? col[i + 1] : make_float2(0.f, 0.f);
-              float2 y0, y1;
-              perturb2_fast(w.x, it.delta, v0, v1, y0, y1);
-              x[2 * pp] = y0;
-              if (i + 1 < d) x[2 * pp + 1] = y1;
-            }
-          }
-        } else {
-#pragma unroll
-          for (int e = 0; e < kE; ++e) x[e] = make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int e = 0; e < kE; ++e) ss = __ffma2_rn(x[e], x[e], ss);
-        float sn = ss.x + ss.y;
-        sn += __shfl_xor_sync(0xffffffffu, sn, 8);
-        sn += __shfl_xor_sync(0xffffffffu, sn, 16);
-        const float inv = sn > 0.f ? rsqrtf(sn) : 0.f;
-        const float2 inv2 = make_float2(inv, inv);
-#pragma unroll
-        for (int e = 0; e < kE; ++e) x[e] = __fmul2_rn(x[e], inv2);
-        if constexpr (FmtTraits<F>::kWide16) {
-          // real parts of entries 16q .. 16q+15 -> chunks 2q, 2q+1 of the
-          // first atom; imaginary parts -> the same chunks of the second
-          uint4 re0, re1, im0, im1;
-          re0.x = pack2<F>(x[0].x, x[1].x);   re1.x = pack2<F>(x[8].x, x[9].x);
-          re0.y = pack2<F>(x[2].x, x[3].x);   re1.y = pack2<F>(x[10].x, x[11].x);
-          re0.z = pack2<F>(x[4].x, x[5].x);   re1.z = pack2<F>(x[12].x, x[13].x);
-          re0.w = pack2<F>(x[6].x, x[7].x);   re1.w = pack2<F>(x[14].x, x[15].x);
-          im0.x = pack2<F>(x[0].y, x[1].y);   im1.x = pack2<F>(x[8].y, x[9].y);
-          im0.y = pack2<F>(x[2].y, x[3].y);   im1.y = pack2<F>(x[10].y, x[11].y);
-          im0.z = pack2<F>(x[4].y, x[5].y);   im1.z = pack2<F>(x[12].y, x[13].y);
-          im0.w = pack2<F>(x[6].y, x[7].y);   im1.w = pack2<F>(x[14].y, x[15].y);
-          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q)) = re0;
-          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q + 1)) = re1;
-          *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q)) = im0;
-          *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q + 1)) = im1;
-        } else if constexpr (F == kScreenTF32) {
-          // real parts of entries 8q .. 8q+7 -> chunks 2q, 2q+1 of the first
-          // atom; imaginary parts -> the same chunks of the second
-          const uint4 cr0 = make_uint4(to_tf32(x[0].x), to_tf32(x[1].x), to_tf32(x[2].x), to_tf32(x[3].x));
-          const uint4 cr1 = make_uint4(to_tf32(x[4].x), to_tf32(x[5].x), to_tf32(x[6].x), to_tf32(x[7].x));
-          const uint4 ci0 = make_uint4(to_tf32(x[0].y), to_tf32(x[1].y), to_tf32(x[2].y), to_tf32(x[3].y));
-          const uint4 ci1 = make_uint4(to_tf32(x[4].y), to_tf32(x[5].y), to_tf32(x[6].y), to_tf32(x[7].y));
-          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q)) = cr0;
-          *reinterpret_cast<uint4*>(blk + swz_offset(r, 2 * q + 1)) = cr1;
-          *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q)) = ci0;
-          *reinterpret_cast<uint4*>(blk + 16384 + swz_offset(r, 2 * q + 1)) = ci1;
-        } else {
-          uint4 re, im;
-          re.x = pack2<F>(x[0].x, x[1].x);
-          re.y = pack2<F>(x[2].x, x[3].x);
-          re.z = pack2<F>(x[4].x, x[5].x);
-          re.w = pack2<F>(x[6].x, x[7].x);
-          im.x = pack2<F>(x[0].y, x[1].y);
-          im.y = pack2<F>(x[2].y, x[3].y);
-          im.z = pack2<F>(x[4].y, x[5].y);
-          im.w = pack2<F>(x[6].y, x[7].y);
-          // real parts of entries 8q .. 8q+7 -> chunk q; imaginary -> chunk 4 + q
-          *reinterpret_cast<uint4*>(blk + swz_offset(r, q)) = re;
-          *reinterpret_cast<uint4*>(blk + swz_offset(r, 4 + q)) = im;
-        }
+        gen_octet<F>(src, it, pc, o, jb, xs + slot * (uint32_t)kBlockBytes, lane);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&ctl.blk_full[slot]);
@@ -803,36 +852,8 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
       const uint32_t hi = kDescHi;
       const uint32_t xs_lo = desc_lo(xs_addr);
       bool ok = true;
-      // One tile: A from slot sA, B from slot sB into accumulator buffer gt & 1.
-      // the MMAs of one tile: A at low word alo, B at blo, into dre (Re) / dim (Im)
       auto issue_mmas = [&](uint32_t alo, uint32_t blo, uint32_t dre, uint32_t dim) {
-        if constexpr (FmtTraits<F>::kTwoAtoms) {
-          // K steps of 8 tf32 or 16 bf16 / fp16 = 32 bytes = +2 in the low
-          // word; the second atom (Im parts) is 16 KiB = +1024 further
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk)   // Re: A_I^T A_J ...
-            mma_lo<F>(dre, alo + 2u * kk, blo + 2u * kk, Idesc<F>::pos, kk > 0 ? 1u : 0u, hi);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk)   // ... + B_I^T B_J
-            mma_lo<F>(dre, alo + 1024u + 2u * kk, blo + 1024u + 2u * kk, Idesc<F>::pos, 1u, hi);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk)   // Im: A_I^T B_J ...
-            mma_lo<F>(dim, alo + 2u * kk, blo + 1024u + 2u * kk, Idesc<F>::pos, kk > 0 ? 1u : 0u, hi);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk)   // ... - B_I^T A_J
-            mma_lo<F>(dim, alo + 1024u + 2u * kk, blo + 2u * kk, Idesc<F>::neg_a, 1u, hi);
-        } else {
-          // Re: sum over the whole K = 2*DP (4 steps of 16 = +2 in the low word)
-          mma_lo<F>(dre, alo + 0u, blo + 0u, Idesc<F>::pos, 0u, hi);
-          mma_lo<F>(dre, alo + 2u, blo + 2u, Idesc<F>::pos, 1u, hi);
-          mma_lo<F>(dre, alo + 4u, blo + 4u, Idesc<F>::pos, 1u, hi);
-          mma_lo<F>(dre, alo + 6u, blo + 6u, Idesc<F>::pos, 1u, hi);
-          // Im: A_I^T B_J (K slices 0,1 against 2,3) - B_I^T A_J (2,3 against 0,1)
-          mma_lo<F>(dim, alo + 0u, blo + 4u, Idesc<F>::pos, 0u, hi);
-          mma_lo<F>(dim, alo + 2u, blo + 6u, Idesc<F>::pos, 1u, hi);
-          mma_lo<F>(dim, alo + 4u, blo + 0u, Idesc<F>::neg_a, 1u, hi);
-          mma_lo<F>(dim, alo + 6u, blo + 2u, Idesc<F>::neg_a, 1u, hi);
-        }
+        issue_tile_mmas<F>(alo, blo, dre, dim, hi);
       };
       auto tile = [&](int sA, int sB) -> bool {
         const uint32_t buf = gt & 1u, use = gt >> 1;
@@ -934,6 +955,164 @@ __global__ void __maxnreg__(96) k_screen(const Src src) {
   }
 }
 
+// ------------------------------------------------------ survivor pair pass
+// The precision form's preselection for the top-k re-score and for the
+// certification: for each survivor s (candidate topk[s]) every tile of its
+// upper-triangle Gram is formed again with the screen's operands and MMAs,
+// one (survivor, tile) item per CTA at a time, and every pair whose screened
+// |G_jk| is at least  mu_s - 2 err  is appended to the survivor's list, mu_s
+// the survivor's screen score and err a bound on | |G|_screen - |G| | for any
+// pair (|G| its binary32 or binary64 value).  The binary32 maximum pair of
+// survivor s, and its binary64 one, lie within err of mu_s in the screen, so
+// both are on the list; a list that would pass `cap` entries (or a bound that
+// admits every pair) is marked by a count above cap, and *overflow_any is set.
+struct PairPassArgs {
+  ScreenArgs a;                 // frame, seed and round keys, sizes; a.st gates and
+                                // gives the iteration's counter and radius
+  const uint32_t* topk;         // survivor s -> candidate index
+  const unsigned int* mu2;      // the K screen scores (float bits)
+  int k;
+  float err;
+  uint2* pairs;                 // k x cap entries (j, k), j < k
+  uint32_t* count;              // k counters (zero before the launch)
+  uint32_t cap;
+  uint32_t* overflow_any;
+};
+
+// 16 warps: all draw (one or two octets each per block pair), warp 0's lane 0
+// issues the MMAs, and warp w reads tensor-memory lanes 32 (w % 4) .. +31 and
+// accumulator columns 32 (w / 4) .. +31 of the tile.
+constexpr int kPairWarps = 16;
+template <int F>
+__global__ void __launch_bounds__(32 * kPairWarps) k_screen_pairs(const PairPassArgs p) {
+  constexpr int kBlockBytes = FmtTraits<F>::kBlockBytes;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ SmemCtl ctl;
+  const uint32_t raw = smem_u32(smem_raw);
+  unsigned char* xs = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  const uint32_t xs_addr = smem_u32(xs);
+  OneInstance src;
+  src.a = p.a;
+  uint32_t t0;
+  float delta0;
+  if (!src.launch(t0, delta0)) return;   // iteration inactive or not screened
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* err = p.a.err;
+  if (threadIdx.x == 0) {
+    mbar_init(&ctl.acc_full[0], 1);
+    ctl.abort_flag = 0;
+    ctl.wait_limit_ns = kWaitLimitNs;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+            smem_u32(&ctl.tmem_base)),
+        "r"(256u)
+        : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl.tmem_base;
+  const int ntiles = p.a.ntiles;
+  const int nitems = p.k * ntiles;
+  uint32_t phase = 0;
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int sv = w / ntiles, tau = w - sv * ntiles;
+    int I, J;
+    tile_coords(tau, I, J);
+    const uint32_t cand = p.topk[sv];
+    const float lo = sqrtf(__uint_as_float(p.mu2[cand])) - 2.0f * p.err;
+    if (!(lo > 0.0f)) {
+      // the bound admits every pair: no list (the full passes decide)
+      if (threadIdx.x == 0) {
+        atomicMax(&p.count[sv], p.cap + 1u);
+        atomicOr(p.overflow_any, 1u);
+      }
+      continue;
+    }
+    const float thr = __fmul_rd(lo, lo);
+    ScreenItem it;
+    it.N = p.a.N; it.d = p.a.d; it.nb = p.a.nb; it.ntiles = ntiles;
+    it.phi = p.a.phi; it.seed = p.a.seed;
+    it.cand = cand; it.t = t0; it.delta = delta0; it.out = nullptr;
+    const PhiloxCand pc = src.cand(it);
+    const int nblk = I == J ? 1 : 2;
+    for (int u = warp; u < nblk * kOctets; u += kPairWarps)
+      gen_octet<F>(src, it, pc, u % kOctets, u < kOctets ? I : J,
+                   xs + (u < kOctets ? 0u : (uint32_t)kBlockBytes), lane);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      const uint32_t alo = desc_lo(xs_addr);
+      const uint32_t blo = desc_lo(xs_addr + (nblk == 2 ? (uint32_t)kBlockBytes : 0u));
+      issue_tile_mmas<F>(alo, blo, tmem, tmem + 128u, kDescHi);
+      mma_commit(&ctl.acc_full[0]);
+    }
+    {
+      const int qw = warp & 3, c0 = 32 * (warp >> 2);
+      if (warp_wait(&ctl.acc_full[0], phase, &ctl, err, 32)) {
+        tc_fence_after();
+        const int row = 32 * qw + lane;
+        const int j = I * kBlockCols + row;
+        const uint32_t base = tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)c0;
+#pragma unroll 1
+        for (int ch = 0; ch < 2; ++ch) {
+          uint32_t ra[16], ia[16];
+          tmem_ld16(base + 16u * ch, ra);
+          tmem_ld16(base + 128u + 16u * ch, ia);
+          tmem_wait_ld<16>(ra, ia);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const float x = __uint_as_float(ra[e]), y = __uint_as_float(ia[e]);
+            const float v = fmaf(y, y, x * x);
+            const int col = c0 + 16 * ch + e;
+            const int kk = J * kBlockCols + col;
+            if (v >= thr && j < it.N && kk < it.N && (I != J || col > row)) {
+              const uint32_t pos = atomicAdd(&p.count[sv], 1u);
+              if (pos < p.cap)
+                p.pairs[(size_t)sv * p.cap + pos] = make_uint2((uint32_t)j, (uint32_t)kk);
+              else
+                atomicOr(p.overflow_any, 1u);
+            }
+          }
+        }
+      }
+    }
+    phase ^= 1u;
+    // the tile's tensor memory and shared-memory blocks are free again
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (ctl.abort_flag) break;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u)
+                 : "memory");
+}
+
+// two blocks of the largest format and the 1 KiB alignment, at least 80 KiB so
+// that at most two CTAs share an SM (2 x 256 tensor-memory columns)
+constexpr size_t kPairPassSmem = 80 * 1024;
+static_assert(kPairPassSmem >= 2 * 32768 + 1024, "pair pass blocks");
+
+template <int F>
+cudaError_t launch_pairs_fmt(const PairPassArgs& p, int grid, cudaStream_t s) {
+  int fit = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &fit, k_screen_pairs<F>, 32 * kPairWarps, kPairPassSmem);
+  if (e != cudaSuccess) return e;
+  if (fit < 1) return cudaErrorLaunchOutOfResources;
+  k_screen_pairs<F><<<grid, 32 * kPairWarps, kPairPassSmem, s>>>(p);
+  return cudaGetLastError();
+}
+
 // the operand area is the same for every format: all slots of the ring
 constexpr size_t kScreenSmem = (size_t)kOperandBytes + 1024;
 
@@ -981,6 +1160,17 @@ cudaError_t launch_any(int fmt, const Src& src, int grid, cudaStream_t s) {
 // Any N up to kScreenMaxN: beyond the ring (12 blocks of 128 columns, 6 for
 // two-atom formats) the candidate is swept in bands (SlotPlan).
 constexpr int kScreenMaxN = 65536;
+// Bound on | |G|_screen - |G| | for one pair of unit columns, |G| its binary32
+// or binary64 value: the operands' rounding (unit roundoff u: 2^-8 bf16,
+// 2^-11 fp16 and tf32) moves a Gram entry by at most (2u + u^2) |phi_j| |phi_k|;
+// 2^-12 covers, many times over, the rest (the screen's fast-math draw against
+// the binary32 one, binary32 normalisation and fp32 accumulation, each a few
+// 2^-24 per entry).
+float screen_pair_err(int fmt) {
+  const double u = (fmt == kScreenBF16 || fmt == kScreenBF16W) ? 0.00390625 : 0.00048828125;
+  return (float)(2.0 * u + u * u + 0.000244140625);
+}
+
 bool screen_supported(int N, int d, int fmt) {
   if (fmt < kScreenBF16 || fmt > kScreenFP16W) return false;
   const bool wide16 = fmt == kScreenBF16W || fmt == kScreenFP16W;
@@ -998,7 +1188,19 @@ cudaError_t init_screen_attributes(int optin) {
   if ((e = allow_screen_smem(k_screen<kScreenFP16W, ManyInstances>, optin)) != cudaSuccess) return e;
   if ((e = allow_screen_smem(k_screen<kScreenBF16, ManyInstances>, optin)) != cudaSuccess) return e;
   if ((e = allow_screen_smem(k_screen<kScreenFP16, ManyInstances>, optin)) != cudaSuccess) return e;
-  return allow_screen_smem(k_screen<kScreenTF32, ManyInstances>, optin);
+  if ((e = allow_screen_smem(k_screen<kScreenTF32, ManyInstances>, optin)) != cudaSuccess) return e;
+  const int pp = (int)kPairPassSmem;
+  if ((e = cudaFuncSetAttribute(k_screen_pairs<kScreenBF16>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, pp)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_screen_pairs<kScreenFP16>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, pp)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_screen_pairs<kScreenTF32>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, pp)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_screen_pairs<kScreenBF16W>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, pp)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_screen_pairs<kScreenFP16W>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, pp);
 }
 
 cudaError_t launch_screen(int fmt, int N, int d, uint64_t seed, const float2* phi32, int K,
@@ -1017,6 +1219,35 @@ cudaError_t launch_screen(int fmt, int N, int d, uint64_t seed, const float2* ph
   a.wait_limit_ns = kWaitLimitNs;
   a.withhold_blocks = 0;
   return launch_any(fmt, src, std::min(K, num_sms), s);
+}
+
+cudaError_t launch_screen_pairs(int fmt, int N, int d, uint64_t seed, const float2* phi32,
+                                const DevState* st, const uint32_t* topk,
+                                const unsigned int* mu2, int k, float err, uint2* pairs,
+                                uint32_t* count, uint32_t cap, uint32_t* overflow_any,
+                                uint32_t* err_flag, int num_sms, cudaStream_t s) {
+  if (!screen_supported(N, d, fmt) || k < 1 || cap < 1) return cudaErrorInvalidValue;
+  PairPassArgs p;
+  ScreenArgs& a = p.a;
+  a.N = N; a.d = d;
+  a.nb = (N + kBlockCols - 1) / kBlockCols;
+  a.ntiles = a.nb * (a.nb + 1) / 2;
+  a.K = k; a.seed = seed; a.phi = phi32; a.c0 = 0; a.t = 0; a.delta = 0.f;
+  a.keys = philox_round_keys(seed);
+  a.st = st; a.out = nullptr; a.err = err_flag;
+  a.wait_limit_ns = kWaitLimitNs;
+  a.withhold_blocks = 0;
+  p.topk = topk; p.mu2 = mu2; p.k = k; p.err = err;
+  p.pairs = pairs; p.count = count; p.cap = cap; p.overflow_any = overflow_any;
+  const int grid = (int)std::min<long long>((long long)k * a.ntiles, 2LL * num_sms);
+  switch (fmt) {
+    case kScreenBF16: return launch_pairs_fmt<kScreenBF16>(p, grid, s);
+    case kScreenFP16: return launch_pairs_fmt<kScreenFP16>(p, grid, s);
+    case kScreenTF32: return launch_pairs_fmt<kScreenTF32>(p, grid, s);
+    case kScreenBF16W: return launch_pairs_fmt<kScreenBF16W>(p, grid, s);
+    case kScreenFP16W: return launch_pairs_fmt<kScreenFP16W>(p, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_screen_wait_test(int fmt, int N, int d, const float2* phi32, int K,

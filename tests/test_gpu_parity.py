@@ -444,6 +444,41 @@ def test_wide_bf16_mode_decisions_replay_exactly():
     assert np.abs(phi - rphi).max() < 1e-12
 
 
+def test_overflowing_survivor_pair_lists_fall_back_to_the_full_passes():
+    """Two directions, each repeated N/2 times, perturbed at radius 1e-3: every
+    pair within a group stays within the screen's bound of the maximum, far
+    more than a survivor's pair list holds, so every list overflows.  The
+    survivors are then re-scored over all pairs and the winner certified by
+    the full binary64 pass (every iteration screens, so there is no filter
+    pass); the ranking and every decision still match the oracle."""
+    d, N, K, iters, seed, delta0 = 8, 600, 64, 3, 21, 1e-3
+    rng = np.random.default_rng(4)
+    dirs = rng.standard_normal((d, 2)) + 1j * rng.standard_normal((d, 2))
+    dirs /= np.linalg.norm(dirs, axis=0)
+    phi0 = np.repeat(dirs, N // 2, axis=1)
+    with T.Search(N, d, seed, K=K, precision="bf16", topk=8, screen_min_delta=0.0,
+                  delta0=delta0) as s:
+        s.set_phi(phi0)
+        phi_start = s.get_phi()
+        s.step(1)
+        row = s.trace()[-1]
+        # every pair near |G| = 1, so the screen's maximum collects the largest
+        # rounding of many pairs: the bf16 bound 2u + u^2 (u = 2^-8) itself,
+        # not the tolerance measured on random frames
+        check_ranking_against_oracle(s, phi_start, seed, int(row["t"]), delta0,
+                                     2.0 ** -7 + 2.0 ** -16, int(row["cstar"]))
+        s.step(iters - 1)
+        tr = s.trace()
+        phi = s.get_phi()
+    assert np.all(tr["flags"] & 1 == 1)
+    opts = O.make_opts(K=K, T=iters, delta0=delta0)
+    rphi, rm2, _, rtr = O.replay(phi_start, seed, opts, delta0, O.mu2(phi_start), 0,
+                                 tr["cstar"])
+    assert np.array_equal(tr["accepted"], rtr["accepted"])
+    check_precision_form_rows(tr, rtr, d, O.mu2(phi_start))
+    assert np.abs(phi - rphi).max() < 1e-12
+
+
 def test_screen_gate_by_radius():
     """screen_min_delta = 0: every iteration screened; huge: none screened
     (fp32 Gram of all candidates); decisions replay in binary64 either way."""
