@@ -34,6 +34,9 @@ constexpr uint32_t kListCap = 4096;
 // words zeroed with the top-k scores each iteration: the scores, the list
 // counts, the overflow flag and the winner selection (slot, filter needed)
 inline size_t top_words(int k) { return 2 * (size_t)k + 3; }
+// largest room for the survivors' screen blocks (drawn once per iteration;
+// beyond it every tile of the survivor pair pass draws its own two blocks)
+constexpr size_t kBlocksMax = (size_t)16 << 20;
 constexpr int kGraphChunk = 32;
 
 std::mutex g_attr_mu;
@@ -121,6 +124,8 @@ struct trstmi_instance {
   uint32_t* sover = nullptr;               // a list overflowed (1),
   uint32_t* ssel = nullptr;                // the winner's slot, filter needed (2)
   uint2* slists = nullptr;                 // screen modes: topk x kListCap survivor pairs
+  unsigned char* sblocks = nullptr;        // screen modes: the survivors' column blocks in
+                                           // the screen layout (when within kBlocksMax)
   uint32_t* topk = nullptr;                // topk
   unsigned int* cert32 = nullptr;          // 1
   unsigned long long* cert64 = nullptr;    // 1
@@ -312,7 +317,7 @@ int enqueue_iteration_finish(trstmi_instance* h, cudaStream_t s) {
     if (screens) {
       TRY_CUDA(launch_screen_pairs(fmt, N, d, h->seed, h->phi32, st, h->topk, h->mu2_k32, k,
                                    screen_pair_err(fmt), h->slists, h->scount, kListCap, h->sover,
-                                   &st->error, h->num_sms, s));
+                                   &st->error, h->num_sms, s, h->sblocks));
       TRY_CUDA(launch_pairs32(st, h->slists, h->scount, kListCap, k, N, d, h->planes_top,
                               h->mu2_top, s));
       src.gate = h->sover;
@@ -519,6 +524,12 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
                                                : (size_t)-1;
   const size_t o_lists = is_screen(o.precision) ? take((size_t)k * kListCap * sizeof(uint2))
                                                 : (size_t)-1;
+  const int sfmt = screen_fmt_of(o.precision, d);
+  const size_t blocks_bytes = is_screen(o.precision) && screen_supported(N, d, sfmt)
+                                  ? (size_t)k * ((N + 127) / 128) * screen_block_bytes(sfmt)
+                                  : 0;
+  const size_t o_blocks = (blocks_bytes > 0 && blocks_bytes <= kBlocksMax) ? take(blocks_bytes)
+                                                                          : (size_t)-1;
   h->block_bytes = off;
   if (h->dmem.allocate(&h->block, off) != cudaSuccess) {
     cudaGetLastError();
@@ -547,6 +558,7 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   if (o_planes != (size_t)-1) h->planes = (float*)(b + o_planes);
   if (o_ptop != (size_t)-1) h->planes_top = (float*)(b + o_ptop);
   if (o_lists != (size_t)-1) h->slists = (uint2*)(b + o_lists);
+  if (o_blocks != (size_t)-1) h->sblocks = (unsigned char*)(b + o_blocks);
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
     trstmi_destroy(h);
     return TRSTMI_ECUDA;

@@ -257,9 +257,15 @@ cudaError_t launch_screen_pairs(int fmt, int N, int d, uint64_t seed, const floa
                                 const DevState* st, const uint32_t* topk,
                                 const unsigned int* mu2, int k, float err, uint2* pairs,
                                 uint32_t* count, uint32_t cap, uint32_t* overflow_any,
-                                uint32_t* err_flag, int num_sms, cudaStream_t s);
+                                uint32_t* err_flag, int num_sms, cudaStream_t s,
+                                unsigned char* blocks = nullptr);
+// blocks (nullable): room for the k survivors' column blocks (k x nb x
+// screen_block_bytes(fmt)), drawn once by a first launch and copied by the
+// pair pass instead of each item drawing its two blocks.
 // the err of launch_screen_pairs for screen format fmt
 float screen_pair_err(int fmt);
+// bytes of one 128-column block in screen format fmt
+size_t screen_block_bytes(int fmt);
 cudaError_t launch_screen_wait_test(int fmt, int N, int d, const float2* phi32, int K,
                                     unsigned int* mu2_out, uint32_t* err_flag,
                                     unsigned long long wait_limit_ns, int num_sms,

@@ -121,6 +121,24 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
+// The next phase of b completes when `bytes` more have landed (and one arrival).
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// global to shared memory, completing on b's transaction count.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         unsigned long long* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(b))
+      : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, uint32_t parity) {
   uint32_t ok;
   // the thread may sleep in hardware up to the hint (ns) while the phase is
@@ -977,7 +995,39 @@ struct PairPassArgs {
   uint32_t* count;              // k counters (zero before the launch)
   uint32_t cap;
   uint32_t* overflow_any;
+  // nullable: the survivors' column blocks drawn once by k_survivor_blocks
+  // (survivor s, block b at (s nb + b) block sizes); else every item draws
+  // its two blocks
+  const unsigned char* blocks;
 };
+
+// The survivors' column blocks in the screen's operand layout, drawn once
+// into global memory: one warp per (survivor, block, octet) unit, the
+// screen's draw (gen_octet), so the pair pass only copies its two blocks.
+template <int F>
+__global__ void __launch_bounds__(256) k_survivor_blocks(const PairPassArgs p,
+                                                         unsigned char* blocks) {
+  constexpr int kBlockBytes = FmtTraits<F>::kBlockBytes;
+  OneInstance src;
+  src.a = p.a;
+  uint32_t t0;
+  float delta0;
+  if (!src.launch(t0, delta0)) return;
+  const int lane = threadIdx.x & 31;
+  const int nb = p.a.nb, per = nb * kOctets;
+  const int units = p.k * per;
+  const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int u = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); u < units; u += warps) {
+    const int sv = u / per, rem = u - sv * per;
+    const int b = rem / kOctets, o = rem - b * kOctets;
+    ScreenItem it;
+    it.N = p.a.N; it.d = p.a.d; it.nb = nb; it.ntiles = p.a.ntiles;
+    it.phi = p.a.phi; it.seed = p.a.seed;
+    it.cand = p.topk[sv]; it.t = t0; it.delta = delta0; it.out = nullptr;
+    const PhiloxCand pc = src.cand(it);
+    gen_octet<F>(src, it, pc, o, b, blocks + ((size_t)sv * nb + b) * kBlockBytes, lane);
+  }
+}
 
 // 16 warps: all draw (one or two octets each per block pair), warp 0's lane 0
 // issues the MMAs, and warp w reads tensor-memory lanes 32 (w % 4) .. +31 and
@@ -1000,6 +1050,7 @@ __global__ void __launch_bounds__(32 * kPairWarps) k_screen_pairs(const PairPass
   uint32_t* err = p.a.err;
   if (threadIdx.x == 0) {
     mbar_init(&ctl.acc_full[0], 1);
+    mbar_init(&ctl.blk_full[0], 1);   // the two blocks' copies of an item
     ctl.abort_flag = 0;
     ctl.wait_limit_ns = kWaitLimitNs;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1038,13 +1089,28 @@ __global__ void __launch_bounds__(32 * kPairWarps) k_screen_pairs(const PairPass
     it.N = p.a.N; it.d = p.a.d; it.nb = p.a.nb; it.ntiles = ntiles;
     it.phi = p.a.phi; it.seed = p.a.seed;
     it.cand = cand; it.t = t0; it.delta = delta0; it.out = nullptr;
-    const PhiloxCand pc = src.cand(it);
     const int nblk = I == J ? 1 : 2;
-    for (int u = warp; u < nblk * kOctets; u += kPairWarps)
-      gen_octet<F>(src, it, pc, u % kOctets, u < kOctets ? I : J,
-                   xs + (u < kOctets ? 0u : (uint32_t)kBlockBytes), lane);
-    fence_proxy_async_smem();
-    __syncthreads();
+    if (p.blocks) {
+      // copy the item's blocks, drawn before
+      if (threadIdx.x == 0) {
+        const unsigned char* base = p.blocks + (size_t)sv * it.nb * kBlockBytes;
+        mbar_expect_tx(&ctl.blk_full[0], (uint32_t)(nblk * kBlockBytes));
+        bulk_g2s(xs, base + (size_t)I * kBlockBytes, (uint32_t)kBlockBytes, &ctl.blk_full[0]);
+        if (nblk == 2)
+          bulk_g2s(xs + kBlockBytes, base + (size_t)J * kBlockBytes, (uint32_t)kBlockBytes,
+                   &ctl.blk_full[0]);
+      }
+      const bool got = warp_wait(&ctl.blk_full[0], phase, &ctl, err, 32);
+      __syncthreads();
+      if (!got || ctl.abort_flag) break;
+    } else {
+      const PhiloxCand pc = src.cand(it);
+      for (int u = warp; u < nblk * kOctets; u += kPairWarps)
+        gen_octet<F>(src, it, pc, u % kOctets, u < kOctets ? I : J,
+                     xs + (u < kOctets ? 0u : (uint32_t)kBlockBytes), lane);
+      fence_proxy_async_smem();
+      __syncthreads();
+    }
     if (threadIdx.x == 0) {
       tc_fence_after();
       const uint32_t alo = desc_lo(xs_addr);
@@ -1166,6 +1232,10 @@ constexpr int kScreenMaxN = 65536;
 // 2^-12 covers, many times over, the rest (the screen's fast-math draw against
 // the binary32 one, binary32 normalisation and fp32 accumulation, each a few
 // 2^-24 per entry).
+size_t screen_block_bytes(int fmt) {
+  return (fmt == kScreenTF32 || fmt == kScreenBF16W || fmt == kScreenFP16W) ? 32768 : 16384;
+}
+
 float screen_pair_err(int fmt) {
   const double u = (fmt == kScreenBF16 || fmt == kScreenBF16W) ? 0.00390625 : 0.00048828125;
   return (float)(2.0 * u + u * u + 0.000244140625);
@@ -1225,7 +1295,8 @@ cudaError_t launch_screen_pairs(int fmt, int N, int d, uint64_t seed, const floa
                                 const DevState* st, const uint32_t* topk,
                                 const unsigned int* mu2, int k, float err, uint2* pairs,
                                 uint32_t* count, uint32_t cap, uint32_t* overflow_any,
-                                uint32_t* err_flag, int num_sms, cudaStream_t s) {
+                                uint32_t* err_flag, int num_sms, cudaStream_t s,
+                                unsigned char* blocks) {
   if (!screen_supported(N, d, fmt) || k < 1 || cap < 1) return cudaErrorInvalidValue;
   PairPassArgs p;
   ScreenArgs& a = p.a;
@@ -1239,6 +1310,20 @@ cudaError_t launch_screen_pairs(int fmt, int N, int d, uint64_t seed, const floa
   a.withhold_blocks = 0;
   p.topk = topk; p.mu2 = mu2; p.k = k; p.err = err;
   p.pairs = pairs; p.count = count; p.cap = cap; p.overflow_any = overflow_any;
+  p.blocks = blocks;
+  if (blocks) {
+    const int warps = k * a.nb * kOctets;
+    const int bgrid = std::max(1, std::min((warps + 7) / 8, 8 * num_sms));
+    switch (fmt) {
+      case kScreenBF16: k_survivor_blocks<kScreenBF16><<<bgrid, 256, 0, s>>>(p, blocks); break;
+      case kScreenFP16: k_survivor_blocks<kScreenFP16><<<bgrid, 256, 0, s>>>(p, blocks); break;
+      case kScreenTF32: k_survivor_blocks<kScreenTF32><<<bgrid, 256, 0, s>>>(p, blocks); break;
+      case kScreenBF16W: k_survivor_blocks<kScreenBF16W><<<bgrid, 256, 0, s>>>(p, blocks); break;
+      default: k_survivor_blocks<kScreenFP16W><<<bgrid, 256, 0, s>>>(p, blocks); break;
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const int grid = (int)std::min<long long>((long long)k * a.ntiles, 2LL * num_sms);
   switch (fmt) {
     case kScreenBF16: return launch_pairs_fmt<kScreenBF16>(p, grid, s);
