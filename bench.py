@@ -111,13 +111,14 @@ def flops_per_pair(d):
 
 
 def kernels_per_step(precision):
-    # one k_set_stop per trstmi_step call plus the iteration's kernels; screen
+    # the iteration's kernels (a one-iteration trstmi_step call sets its stop in
+    # the iteration's first kernel); screen
     # modes with every iteration screened (screen_min_delta = 0): iter_begin,
     # screen, top-k, the survivors' binary32 draw, their screen blocks, the
     # survivor pair pass, the listed pairs in binary32, the gated re-score over
     # all pairs, the binary64 draw of the winner, its listed pairs in binary64,
     # the gated binary64 pass over all pairs, and the rule with the commit
-    return 1 + {"fp64": 4, "fp32": 5, "bf16": 12, "tf32": 12}[precision]
+    return {"fp64": 4, "fp32": 5, "bf16": 12, "tf32": 12}[precision]
 
 
 def dist_env():

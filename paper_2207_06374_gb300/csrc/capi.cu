@@ -214,14 +214,15 @@ int enqueue_rescore_current(trstmi_instance* h) {
 // scores of candidates c_lo .. c_hi-1 into the K-entry score vector
 // (mu2_k64 in binary64, mu2_k32 otherwise).  A whole iteration scores
 // 0 .. K-1; a candidate-sharded one scores its rank's range.
-int enqueue_iteration_score(trstmi_instance* h, cudaStream_t s, int c_lo, int c_hi) {
+int enqueue_iteration_score(trstmi_instance* h, cudaStream_t s, int c_lo, int c_hi,
+                            uint32_t call_iters = 0) {
   const int N = h->N, d = h->d, K = h->opt.K;
   const int count = c_hi - c_lo;
   DevState* st = h->st;
   const int prec = h->opt.precision;
   if (prec == TRSTMI_FP64) {
     TRY_CUDA(launch_iter_begin(st, h->mu2_k64, sizeof(unsigned long long) * K, nullptr, 0,
-                               nullptr, 0, s));
+                               nullptr, 0, s, call_iters));
     if (count > 0) {
       GramSource src{};
       src.perturb = true;
@@ -233,7 +234,7 @@ int enqueue_iteration_score(trstmi_instance* h, cudaStream_t s, int c_lo, int c_
     }
   } else if (prec == TRSTMI_FP32) {
     TRY_CUDA(launch_iter_begin(st, h->mu2_k32, sizeof(unsigned int) * K, nullptr, 0, nullptr,
-                               0, s));
+                               0, s, call_iters));
     if (count > 0) {
       GramSource src{};
       src.perturb = true;
@@ -252,7 +253,8 @@ int enqueue_iteration_score(trstmi_instance* h, cudaStream_t s, int c_lo, int c_
     const int k = h->opt.topk;
     TRY_CUDA(launch_iter_begin(st, h->mu2_k32, sizeof(unsigned int) * K, h->mu2_top,
                                top_words(k) * sizeof(uint32_t), h->cert32,
-                               2 * sizeof(unsigned int) + sizeof(unsigned long long), s));
+                               2 * sizeof(unsigned int) + sizeof(unsigned long long), s,
+                               call_iters));
     if (count > 0) {
       // rank the candidates: tensor-core screen while delta >= screen_min_delta,
       // else the fp32 Gram of every candidate (each kernel returns at once when
@@ -360,18 +362,22 @@ int enqueue_iteration_finish(trstmi_instance* h, cudaStream_t s) {
 }
 
 // One iteration of the search, enqueued on s (captured into the graph).
-int enqueue_iteration(trstmi_instance* h, cudaStream_t s) {
-  const int rc = enqueue_iteration_score(h, s, 0, h->opt.K);
+int enqueue_iteration(trstmi_instance* h, cudaStream_t s, uint32_t call_iters = 0) {
+  const int rc = enqueue_iteration_score(h, s, 0, h->opt.K, call_iters);
   return rc ? rc : enqueue_iteration_finish(h, s);
 }
 
-int get_graph(trstmi_instance* h, int iters, cudaGraphExec_t* out) {
-  auto it = h->graphs.find(iters);
+// The graph of `iters` iterations; with_stop: it is a whole trstmi_step call,
+// and its first kernel also sets the call's stop and start counters.
+int get_graph(trstmi_instance* h, int iters, cudaGraphExec_t* out, bool with_stop = false) {
+  const int key = 2 * iters + (with_stop ? 1 : 0);
+  auto it = h->graphs.find(key);
   if (it != h->graphs.end()) { *out = it->second; return TRSTMI_OK; }
   cudaGraph_t g = nullptr;
   TRY_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   int rc = TRSTMI_OK;
-  for (int i = 0; i < iters && rc == TRSTMI_OK; ++i) rc = enqueue_iteration(h, h->stream);
+  for (int i = 0; i < iters && rc == TRSTMI_OK; ++i)
+    rc = enqueue_iteration(h, h->stream, (with_stop && i == 0) ? (uint32_t)iters : 0u);
   cudaError_t e = cudaStreamEndCapture(h->stream, &g);
   if (rc != TRSTMI_OK || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -382,7 +388,7 @@ int get_graph(trstmi_instance* h, int iters, cudaGraphExec_t* out) {
   e = cudaGraphInstantiate(&ex, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return TRSTMI_ECUDA;
-  h->graphs[iters] = ex;
+  h->graphs[key] = ex;
   *out = ex;
   return TRSTMI_OK;
 }
@@ -603,15 +609,20 @@ int trstmi_step(trstmi_handle h, int iters, trstmi_step_info* info) {
   cudaStream_t s = h->stream;
   // graphs are captured (host work only) before the timed span starts
   const int full = iters / kGraphChunk, rem = iters % kGraphChunk;
+  // a call of fewer than kGraphChunk iterations is one graph whose first
+  // kernel sets the call's stop; longer calls set it in a kernel of their own
+  const bool whole = full == 0 && rem > 0;
   cudaGraphExec_t g_full = nullptr, g_rem = nullptr;
   int rc = TRSTMI_OK;
   if (full > 0 && (rc = get_graph(h, kGraphChunk, &g_full)) != TRSTMI_OK) return rc;
-  if (rem > 0 && (rc = get_graph(h, rem, &g_rem)) != TRSTMI_OK) return rc;
+  if (rem > 0 && (rc = get_graph(h, rem, &g_rem, whole)) != TRSTMI_OK) return rc;
   // no host synchronisation until the end: the start counters are snapshot
   // on the device by the first kernel
   TRY_CUDA(cudaEventRecord(h->ev0, s));
-  k_set_stop<<<1, 1, 0, s>>>(h->st, (uint32_t)iters);
-  TRY_CUDA(cudaGetLastError());
+  if (!whole) {
+    k_set_stop<<<1, 1, 0, s>>>(h->st, (uint32_t)iters);
+    TRY_CUDA(cudaGetLastError());
+  }
   for (int r = 0; r < full; ++r) TRY_CUDA(cudaGraphLaunch(g_full, s));
   if (g_rem) TRY_CUDA(cudaGraphLaunch(g_rem, s));
   TRY_CUDA(cudaEventRecord(h->ev1, s));

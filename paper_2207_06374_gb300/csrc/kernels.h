@@ -147,8 +147,12 @@ constexpr int kMaxD = 256;
 
 cudaError_t launch_init_frame(int N, int d, uint64_t seed, double2* phi64, float2* phi32,
                               DevState* st, cudaStream_t s);
+// call_iters (nonzero): this is the first iteration of a trstmi_step call of
+// that many iterations, and the kernel also sets the call's stop and start
+// counters (k_set_stop's work)
 cudaError_t launch_iter_begin(DevState* st, void* zero0, size_t bytes0, void* zero1,
-                              size_t bytes1, void* zero2, size_t bytes2, cudaStream_t s);
+                              size_t bytes1, void* zero2, size_t bytes2, cudaStream_t s,
+                              uint32_t call_iters = 0);
 // plain modes: argmin over K candidates, accept/radius rule, trace row
 cudaError_t launch_select_decide_f32(DevState* st, const unsigned int* mu2, int K,
                                      TraceRowDev* trace, cudaStream_t s);

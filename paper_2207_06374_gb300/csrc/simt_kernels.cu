@@ -605,9 +605,16 @@ cudaError_t launch_init_frame(int N, int d, uint64_t seed, double2* phi64, float
 // ---------------------------------------------------- iteration start
 
 __global__ void k_iter_begin(DevState* st, void* z0, size_t b0, void* z1, size_t b1, void* z2,
-                             size_t b2) {
+                             size_t b2, uint32_t call_iters) {
   __shared__ uint32_t act;
   if (threadIdx.x == 0) {
+    if (call_iters) {
+      // the first iteration of a call: its stop and its start counters
+      const unsigned long long stop = (unsigned long long)st->t + call_iters;
+      st->t_stop = stop > 0xffffffffull ? 0xffffffffu : (uint32_t)stop;
+      st->t_call = st->t;
+      st->accepts_call = st->accepts;
+    }
     act = (!st->done && st->t < st->t_stop) ? 1u : 0u;
     st->active = act;
     st->npairs = 0u;
@@ -636,8 +643,9 @@ __global__ void k_iter_begin(DevState* st, void* z0, size_t b0, void* z1, size_t
 }
 
 cudaError_t launch_iter_begin(DevState* st, void* zero0, size_t bytes0, void* zero1,
-                              size_t bytes1, void* zero2, size_t bytes2, cudaStream_t s) {
-  k_iter_begin<<<1, 1024, 0, s>>>(st, zero0, bytes0, zero1, bytes1, zero2, bytes2);
+                              size_t bytes1, void* zero2, size_t bytes2, cudaStream_t s,
+                              uint32_t call_iters) {
+  k_iter_begin<<<1, 1024, 0, s>>>(st, zero0, bytes0, zero1, bytes1, zero2, bytes2, call_iters);
   return cudaGetLastError();
 }
 
