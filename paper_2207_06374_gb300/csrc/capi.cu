@@ -199,8 +199,9 @@ int enqueue_rescore_current(trstmi_instance* h) {
     TRY_CUDA(launch_gram_f64(h->N, h->d, 1, src, h->cert64, h->num_sms, s));
     k_set_mu2cur<<<1, 1, 0, s>>>(h->st, nullptr, h->cert64);
   } else {
-    TRY_CUDA(cudaMemsetAsync(h->cert32, 0, 2 * sizeof(unsigned int), s));
-    TRY_CUDA(cudaMemsetAsync(h->cert64, 0, sizeof(unsigned long long), s));
+    // cert32[0..1] and cert64 are one 16-byte span
+    TRY_CUDA(cudaMemsetAsync(h->cert32, 0, 2 * sizeof(unsigned int) + sizeof(unsigned long long),
+                             s));
     TRY_CUDA(cudaMemsetAsync(h->misc, 0, 2 * sizeof(uint32_t), s));
     int rc = enqueue_certify(h, h->phi64, h->phi32, h->cert64, nullptr, h->misc, h->misc + 1, s);
     if (rc) return rc;
@@ -736,10 +737,22 @@ int trstmi_set_phi(trstmi_handle h, const double* in) {
   USE_DEVICE(h->opt.device);
   cudaStream_t s = h->stream;
   const size_t bytes = (size_t)h->N * h->d * sizeof(double2);
-  // reject zero columns on the host before touching the device state
+  // reject zero or non-finite columns on the host before touching the device
+  // state; four partial sums per column keep the check off one long chain of
+  // dependent additions (a sum of squares is zero exactly when every entry is)
+  const int m = 2 * h->d;
   for (int j = 0; j < h->N; ++j) {
-    double acc = 0.0;
-    for (int i = 0; i < 2 * h->d; ++i) acc += in[(size_t)j * 2 * h->d + i] * in[(size_t)j * 2 * h->d + i];
+    const double* c = in + (size_t)j * m;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int i = 0;
+    for (; i + 4 <= m; i += 4) {
+      a0 += c[i] * c[i];
+      a1 += c[i + 1] * c[i + 1];
+      a2 += c[i + 2] * c[i + 2];
+      a3 += c[i + 3] * c[i + 3];
+    }
+    for (; i < m; ++i) a0 += c[i] * c[i];
+    const double acc = (a0 + a1) + (a2 + a3);
     if (!(acc > 0.0) || !std::isfinite(acc)) return TRSTMI_EINVAL;
   }
   TRY_CUDA(cudaMemcpyAsync(h->scratch64, in, bytes, cudaMemcpyHostToDevice, s));

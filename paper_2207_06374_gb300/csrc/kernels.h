@@ -123,6 +123,11 @@ struct PairFilter {
   // mu2_ref is a hint within this much (on mu^2) of the frame's binary32 max
   // rather than that max itself (0: it is the max)
   float ref_slack_mu2;
+  // nonzero: no reference is read; each tile keeps its pairs within the
+  // margin of the tile's own maximum (at most the frame's, so the kept set
+  // holds every pair within the margin of the frame's maximum), and the max
+  // and the pair list come from one pass
+  int local;
 };
 
 // Lower end of the kept range of |G|: sqrt(binary32 max, less the hint's

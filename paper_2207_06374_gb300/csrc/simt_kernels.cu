@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(256, TileCtas<T>::value) k_gram_tile(const Gra
     delta = (T)src.st->delta_used;
   }
   T thr = T(-1);
-  if (a.has_filter) {
+  if (a.has_filter && !a.filter.local) {
     const float lo = filter_lo(a.filter);
     thr = (T)(lo * lo);
   }
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(256, 3) k_gram_planes(const GramArgs<float> a,
   if (src.gate && *src.gate == 0u) return;
   if (src.st && !src.st->active) return;
   float thr = -1.f;
-  if (a.has_filter) {
+  if (a.has_filter && !a.filter.local) {
     const float lo = filter_lo(a.filter);
     thr = lo * lo;
   }
@@ -988,10 +988,11 @@ cudaError_t launch_frame_certify(int N, int d, const double2* p64, const float2*
   src.phi = p32;
   src.normalize = false;
   src.gate = active;
-  cudaError_t e = launch_gram_f32(N, d, 1, src, cert32, nullptr, num_sms, s);
+  // one binary32 pass: the max into cert32[0] and, tile by tile, the pairs
+  // within the margin of the tile's maximum
+  PairFilter pf{nullptr, certify_margin(d), pairs, npairs, cap, overflow, nullptr, 0.f, 1};
+  cudaError_t e = launch_gram_f32(N, d, 1, src, cert32, &pf, num_sms, s);
   if (e != cudaSuccess) return e;
-  PairFilter pf{cert32, certify_margin(d), pairs, npairs, cap, overflow, nullptr, 0.f};
-  if ((e = launch_gram_f32(N, d, 1, src, cert32 + 1, &pf, num_sms, s)) != cudaSuccess) return e;
   if ((e = launch_pairs64(active, npairs, pairs, cap, d, p64, cert64, s)) != cudaSuccess) return e;
   GramSource full{};
   full.perturb = false;
@@ -1267,7 +1268,7 @@ __global__ void __launch_bounds__(256, TileCtas<T>::value) k_batch_score(const S
       it.t = st->t + 1u;
       it.delta = st->delta_used;
       T thr = T(-1);
-      PairFilter pf;
+      PairFilter pf{};   // every field zero until set below (local = 0)
       const PairFilter* filter = nullptr;
       if (mode == kPassFull || mode == kPassRescore) {
         it.perturb = true;

@@ -152,6 +152,23 @@ __device__ __forceinline__ T tile_pairs_max(const T* sIre, const T* sIim, const 
     acc.step(ar, ai, br, bi);
   }
   T m = T(0);
+  if (filter && filter->local) {
+    // the threshold from this tile's own maximum (see PairFilter::local)
+    __shared__ T red[8];
+    __shared__ T tile_max;
+#pragma unroll
+    for (int x = 0; x < R; ++x)
+#pragma unroll
+      for (int y = 0; y < R; ++y) {
+        const int gj = I * BT + R * ty + x, gk = J * BT + R * tx + y;
+        if (gj < gk && gk < N) m = fmax(m, pair_abs2(acc.get_re(x, y), acc.get_im(x, y)));
+      }
+    const T bm = block_max<T>(m, red);
+    if (threadIdx.x == 0) tile_max = bm;
+    __syncthreads();
+    const float lo = fmaxf(sqrtf((float)tile_max) - filter->margin, 0.0f);
+    thr = (T)(lo * lo);
+  }
 #pragma unroll
   for (int x = 0; x < R; ++x)
 #pragma unroll
