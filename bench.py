@@ -298,7 +298,8 @@ def cpu_baseline(d, N, K, steps=1):
     return {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
             "sample": f"{count} of the {K} candidates of iteration t=1..{steps} (d={d}, N={N}) "
                       f"scored by the fp64 oracle (generation + all-pairs |G|^2 max), "
-                      f"{steps} step(s), {dt:.2f} s",
+                      f"{steps} step(s), {dt:.2f} s on {cores} threads "
+                      f"(~{dt * cores:.0f} core-seconds)",
             "fp32_variant": {"value": count32 * per_cand / dt32, "unit": "pairs/s",
                              "cores": cores, "kind": "oracle fp32 plain loops",
                              "sample": f"{count32} candidates of iteration 1, {dt32:.2f} s"}}

@@ -427,6 +427,21 @@ def test_banded_screen_choice_is_valid_among_the_oracle_scores(precision, d, N):
                                      SCREEN_TOL[precision], int(row["cstar"]))
 
 
+def test_survivor_pair_pass_drawing_its_own_blocks_matches_the_oracle():
+    """40 survivors of N = 4096 (32 column blocks each) need more room than the
+    survivors' screen blocks may take, so every tile of the survivor pair pass
+    draws its own two blocks instead of copying them; the ranking, the listed
+    pairs' binary32 re-scores and the choice still match the oracle."""
+    d, N, K, seed = 16, 4096, 48, 8
+    with T.Search(N, d, seed, K=K, precision="bf16", topk=40, screen_min_delta=0.0) as s:
+        phi0 = s.get_phi()
+        s.step(1)
+        row = s.trace()[-1]
+        assert row["flags"] & 1 == 1
+        check_ranking_against_oracle(s, phi0, seed, int(row["t"]), float(row["delta_used"]),
+                                     SCREEN_TOL["bf16"], int(row["cstar"]))
+
+
 def test_wide_bf16_mode_decisions_replay_exactly():
     """Precision form at d = 48 (wide screen every iteration, fp32 top-k,
     fp64 certification): every decision reproduced by the oracle in binary64."""
