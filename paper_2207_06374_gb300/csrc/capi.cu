@@ -302,14 +302,13 @@ int enqueue_iteration_finish(trstmi_instance* h, cudaStream_t s) {
     // iteration screens
     const bool filter = !(h->screen_min_delta <= 0.0);
     TRY_CUDA(launch_topk(st, h->mu2_k32, K, k, h->topk, h->mu2_top, s));
-    // the survivors drawn once in binary32 (the tile pass's gen_column
-    // arithmetic), then their re-score: over the pairs the survivor pair pass
-    // lists (every pair that can be a survivor's binary32 or binary64
-    // maximum), and over all pairs only for a survivor whose list overflowed
-    // (each pass returns at once unless the screen ranked the candidates;
-    // otherwise k_topk copied the binary32 scores)
-    TRY_CUDA(launch_gen_planes_f32(N, d, k, h->phi32, h->seed, 0u, st, 0u, 0.0, h->planes_top, s,
-                                   h->topk, &st->use_screen));
+    // the survivors' re-score in binary32 when the screen ranked them (else
+    // k_topk copied the binary32 scores of the full ranking pass): over the
+    // pairs the survivor pair pass lists (every pair that can be a survivor's
+    // binary32 or binary64 maximum), each pair's two columns drawn with the
+    // bits of the survivors' draw; only when a list overflowed, the survivors
+    // drawn whole (the tile pass's gen_column arithmetic) and re-scored over
+    // all pairs
     GramSource src{};
     src.perturb = true;
     src.phi = h->phi32;
@@ -317,16 +316,18 @@ int enqueue_iteration_finish(trstmi_instance* h, cudaStream_t s) {
     src.cand_list = h->topk;
     src.st = st;
     src.planes = h->planes_top;
+    const uint32_t* full_gate = &st->use_screen;
     if (screens) {
       TRY_CUDA(launch_screen_pairs(fmt, N, d, h->seed, h->phi32, st, h->topk, h->mu2_k32, k,
                                    screen_pair_err(fmt), h->slists, h->scount, kListCap, h->sover,
                                    &st->error, h->num_sms, s, h->sblocks));
-      TRY_CUDA(launch_pairs32(st, h->slists, h->scount, kListCap, k, N, d, h->planes_top,
-                              h->mu2_top, s));
-      src.gate = h->sover;
-    } else {
-      src.gate = &st->use_screen;
+      TRY_CUDA(launch_pairs32(st, h->slists, h->scount, kListCap, k, N, d, h->phi32, h->seed,
+                              h->topk, h->mu2_top, s));
+      full_gate = h->sover;
     }
+    src.gate = full_gate;
+    TRY_CUDA(launch_gen_planes_f32(N, d, k, h->phi32, h->seed, 0u, st, 0u, 0.0, h->planes_top, s,
+                                   h->topk, full_gate));
     TRY_CUDA(launch_gram_f32(N, d, k, src, h->mu2_top, nullptr, h->num_sms, s));
     TRY_CUDA(launch_materialize64(N, d, h->seed, st, h->topk, h->mu2_top, k, h->phi64,
                                   h->cand64, h->cand32, s, h->cert32, h->scount,

@@ -209,12 +209,13 @@ float certify_margin(int d);
 // winner's list, lists + sel[0] * list_cap (list_count[sel[0]] of them),
 // instead of pairs / npairs, and the hint check is skipped.
 // binary32 |G|^2 of each survivor's listed pairs (lists, k x cap; count[s]
-// above cap: left to the full pass) from its drawn planes, maxed into mu2[s]
-// with the bits the binary32 tile pass gives those pairs.  Returns at once
-// unless the iteration in st is active and screened.
-cudaError_t launch_pairs32(const DevState* st, const uint2* lists, const uint32_t* count,
-                           uint32_t cap, int k, int N, int d, const float* planes,
-                           unsigned int* mu2, cudaStream_t s);
+// above cap: left to the full pass), the pair's two columns of candidate
+// topk[s] drawn by one warp with the bits of the survivors' binary32 draw,
+// maxed into mu2[s] with the bits the binary32 tile pass gives those pairs.
+// Returns at once unless the iteration in st is active and screened; d <= 64.
+cudaError_t launch_pairs32(DevState* st, const uint2* lists, const uint32_t* count,
+                           uint32_t cap, int k, int N, int d, const float2* phi, uint64_t seed,
+                           const uint32_t* topk, unsigned int* mu2, cudaStream_t s);
 // The accept/radius rule on the certified binary64 mu^2 (or, uncertified, on
 // the survivor's binary32 score) with its trace row, and the copy of the
 // accepted candidate into the frame, in one launch; *done is a

@@ -923,45 +923,88 @@ cudaError_t launch_materialize64(int N, int d, uint64_t seed, DevState* st,
 // mu2[s]: the chain over i and the rounding of MicroTile::step and pair_abs2,
 // so every pair has the bits the binary32 tile pass gives it.  A survivor
 // whose list overflowed (count above cap) is left to the full pass.
-__global__ void k_pairs32(const DevState* st, const uint2* lists, const uint32_t* count,
-                          uint32_t cap, int k, int N, int d, const float* planes,
-                          unsigned int* mu2) {
+// Column j of candidate c (iteration t, radius delta) around the binary32 frame
+// by one warp, with gen_column's bits: lane p < P draws entries 2p and 2p + 1
+// (x0 and x1), every lane adds the squared entries in gen_column's order (i
+// ascending, broadcast from their lanes), and each lane divides its entries
+// by the norm.  P <= 32 (d <= 64).  Returns false for a zero column (entries
+// zero, as gen_column leaves them).
+__device__ __forceinline__ bool gen_column_warp_f32(const float2* phi, int d, int j, uint64_t seed,
+                                                    uint32_t c, uint32_t t, float delta,
+                                                    int lane, float2& x0, float2& x1) {
+  const int P = (d + 1) >> 1;
+  x0 = x1 = make_float2(0.f, 0.f);
+  if (lane < P) {
+    const PhiloxOut u = philox4x32_10((uint32_t)j * (uint32_t)P + (uint32_t)lane, c, t, 0u,
+                                      seed_lo(seed), seed_hi(seed));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * lane + h;
+      if (i < d) {
+        float zr, zi;
+        cn_draw<float>(u.x[2 * h], u.x[2 * h + 1], zr, zi);
+        const float2 v = phi[(size_t)j * d + i];
+        const float2 x = make_float2(add_rn(v.x, mul_rn(delta, zr)), add_rn(v.y, mul_rn(delta, zi)));
+        if (h == 0) x0 = x; else x1 = x;
+      }
+    }
+  }
+  const float q0 = add_rn(mul_rn(x0.x, x0.x), mul_rn(x0.y, x0.y));
+  const float q1 = add_rn(mul_rn(x1.x, x1.x), mul_rn(x1.y, x1.y));
+  float sq = 0.f;
+  for (int i = 0; i < d; ++i) sq = add_rn(sq, __shfl_sync(0xffffffffu, (i & 1) ? q1 : q0, i >> 1));
+  if (!(sq > 0.f)) {
+    x0 = x1 = make_float2(0.f, 0.f);
+    return false;
+  }
+  const float nrm = sqrt_rn(sq);
+  x0 = make_float2(div_rn(x0.x, nrm), div_rn(x0.y, nrm));
+  x1 = make_float2(div_rn(x1.x, nrm), div_rn(x1.y, nrm));
+  return true;
+}
+
+__global__ void k_pairs32(DevState* st, const uint2* lists, const uint32_t* count,
+                          uint32_t cap, int N, int d, const float2* phi, uint64_t seed,
+                          const uint32_t* topk, unsigned int* mu2) {
   if (!st->active || !st->use_screen) return;
-  // survivor blockIdx.y; one warp per listed pair: lane l loads entries l,
-  // l + 32, .. of both columns (all loads of a pair in flight together), and
-  // every lane runs the chain over i on the values broadcast from their lanes
+  // survivor blockIdx.y; one warp per listed pair draws the pair's two columns
+  // (gen_column_warp_f32: the bits of the survivors' binary32 draw) and runs
+  // the tile pass's chain over i on the entries broadcast from their lanes
   const int sv = blockIdx.y;
   const uint32_t n = count[sv];
   if (n > cap) return;
   const int lane = threadIdx.x & 31;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  const float* re = planes + (size_t)sv * 2 * d * N;
-  const float* im = re + (size_t)d * N;
+  const uint32_t c = topk[sv], t = st->t + 1u;
+  const float delta = (float)st->delta_used;
   for (uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n; q += warps) {
     const uint2 jk = lists[(size_t)sv * cap + q];
+    float2 a0, a1, b0, b1;
+    const bool okj = gen_column_warp_f32(phi, d, (int)jk.x, seed, c, t, delta, lane, a0, a1);
+    const bool okk = gen_column_warp_f32(phi, d, (int)jk.y, seed, c, t, delta, lane, b0, b1);
+    if ((!okj || !okk) && lane == 0) atomicOr(&st->error, (uint32_t)kErrZeroColumn);
     float gr = 0.f, gi = 0.f;
-    for (int i0 = 0; i0 < d; i0 += 32) {
-      const int i = i0 + lane;
-      const size_t o = (size_t)i * N;
-      const float ar = i < d ? re[o + jk.x] : 0.f, ai = i < d ? im[o + jk.x] : 0.f;
-      const float br = i < d ? re[o + jk.y] : 0.f, bi = i < d ? im[o + jk.y] : 0.f;
-      const int m = min(32, d - i0);
-      for (int t = 0; t < m; ++t) {
-        const float a = __shfl_sync(0xffffffffu, ar, t), b = __shfl_sync(0xffffffffu, ai, t);
-        const float c = __shfl_sync(0xffffffffu, br, t), e = __shfl_sync(0xffffffffu, bi, t);
-        gr = fmaf(a, c, fmaf(b, e, gr));
-        gi = fmaf(a, e, fmaf(-b, c, gi));
-      }
+    for (int i = 0; i < d; ++i) {
+      const int src = i >> 1;
+      const bool odd = (i & 1) != 0;
+      const float ar = __shfl_sync(0xffffffffu, odd ? a1.x : a0.x, src);
+      const float ai = __shfl_sync(0xffffffffu, odd ? a1.y : a0.y, src);
+      const float br = __shfl_sync(0xffffffffu, odd ? b1.x : b0.x, src);
+      const float bi = __shfl_sync(0xffffffffu, odd ? b1.y : b0.y, src);
+      gr = fmaf(ar, br, fmaf(ai, bi, gr));
+      gi = fmaf(ar, bi, fmaf(-ai, br, gi));
     }
     if (lane == 0) atomic_max_nonneg(mu2 + sv, pair_abs2(gr, gi));
   }
 }
 
-cudaError_t launch_pairs32(const DevState* st, const uint2* lists, const uint32_t* count,
-                           uint32_t cap, int k, int N, int d, const float* planes,
-                           unsigned int* mu2, cudaStream_t s) {
+cudaError_t launch_pairs32(DevState* st, const uint2* lists, const uint32_t* count,
+                           uint32_t cap, int k, int N, int d, const float2* phi, uint64_t seed,
+                           const uint32_t* topk, unsigned int* mu2, cudaStream_t s) {
+  if (d > 64) return cudaErrorInvalidValue;
   const unsigned bx = std::min(16u, (cap + 7) / 8);
-  k_pairs32<<<dim3(bx, (unsigned)k), 256, 0, s>>>(st, lists, count, cap, k, N, d, planes, mu2);
+  k_pairs32<<<dim3(bx, (unsigned)k), 256, 0, s>>>(st, lists, count, cap, N, d, phi, seed, topk,
+                                                  mu2);
   return cudaGetLastError();
 }
 
