@@ -963,6 +963,47 @@ __device__ __forceinline__ bool gen_column_warp_f32(const float2* phi, int d, in
   return true;
 }
 
+// gen_column_warp_f32 for d <= 32 with two columns per warp: the half-warp
+// h = lane / 16 draws column `col` (its lanes' own), lane 16h + p taking the
+// entries 2p and 2p + 1; each half sums its column's squared entries in
+// gen_column's order from its own lanes.
+__device__ __forceinline__ bool gen_column_halfwarp_f32(const float2* phi, int d, int col,
+                                                        uint64_t seed, uint32_t c, uint32_t t,
+                                                        float delta, int lane, float2& x0,
+                                                        float2& x1) {
+  const int P = (d + 1) >> 1;
+  const int p = lane & 15, base = lane & 16;
+  x0 = x1 = make_float2(0.f, 0.f);
+  if (p < P) {
+    const PhiloxOut u = philox4x32_10((uint32_t)col * (uint32_t)P + (uint32_t)p, c, t, 0u,
+                                      seed_lo(seed), seed_hi(seed));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * p + h;
+      if (i < d) {
+        float zr, zi;
+        cn_draw<float>(u.x[2 * h], u.x[2 * h + 1], zr, zi);
+        const float2 v = phi[(size_t)col * d + i];
+        const float2 x = make_float2(add_rn(v.x, mul_rn(delta, zr)), add_rn(v.y, mul_rn(delta, zi)));
+        if (h == 0) x0 = x; else x1 = x;
+      }
+    }
+  }
+  const float q0 = add_rn(mul_rn(x0.x, x0.x), mul_rn(x0.y, x0.y));
+  const float q1 = add_rn(mul_rn(x1.x, x1.x), mul_rn(x1.y, x1.y));
+  float sq = 0.f;
+  for (int i = 0; i < d; ++i)
+    sq = add_rn(sq, __shfl_sync(0xffffffffu, (i & 1) ? q1 : q0, base + (i >> 1)));
+  if (!(sq > 0.f)) {
+    x0 = x1 = make_float2(0.f, 0.f);
+    return false;
+  }
+  const float nrm = sqrt_rn(sq);
+  x0 = make_float2(div_rn(x0.x, nrm), div_rn(x0.y, nrm));
+  x1 = make_float2(div_rn(x1.x, nrm), div_rn(x1.y, nrm));
+  return true;
+}
+
 __global__ void k_pairs32(DevState* st, const uint2* lists, const uint32_t* count,
                           uint32_t cap, int N, int d, const float2* phi, uint64_t seed,
                           const uint32_t* topk, unsigned int* mu2) {
@@ -977,20 +1018,32 @@ __global__ void k_pairs32(DevState* st, const uint2* lists, const uint32_t* coun
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t c = topk[sv], t = st->t + 1u;
   const float delta = (float)st->delta_used;
+  // d <= 32: lanes 0-15 draw column j and lanes 16-31 column k at once
+  const bool halves = d <= 32;
   for (uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n; q += warps) {
     const uint2 jk = lists[(size_t)sv * cap + q];
     float2 a0, a1, b0, b1;
-    const bool okj = gen_column_warp_f32(phi, d, (int)jk.x, seed, c, t, delta, lane, a0, a1);
-    const bool okk = gen_column_warp_f32(phi, d, (int)jk.y, seed, c, t, delta, lane, b0, b1);
-    if ((!okj || !okk) && lane == 0) atomicOr(&st->error, (uint32_t)kErrZeroColumn);
+    int bbase;
+    if (halves) {
+      const int col = lane < 16 ? (int)jk.x : (int)jk.y;
+      const bool ok = gen_column_halfwarp_f32(phi, d, col, seed, c, t, delta, lane, a0, a1);
+      if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(&st->error, (uint32_t)kErrZeroColumn);
+      b0 = a0; b1 = a1;
+      bbase = 16;
+    } else {
+      const bool okj = gen_column_warp_f32(phi, d, (int)jk.x, seed, c, t, delta, lane, a0, a1);
+      const bool okk = gen_column_warp_f32(phi, d, (int)jk.y, seed, c, t, delta, lane, b0, b1);
+      if ((!okj || !okk) && lane == 0) atomicOr(&st->error, (uint32_t)kErrZeroColumn);
+      bbase = 0;
+    }
     float gr = 0.f, gi = 0.f;
     for (int i = 0; i < d; ++i) {
       const int src = i >> 1;
       const bool odd = (i & 1) != 0;
       const float ar = __shfl_sync(0xffffffffu, odd ? a1.x : a0.x, src);
       const float ai = __shfl_sync(0xffffffffu, odd ? a1.y : a0.y, src);
-      const float br = __shfl_sync(0xffffffffu, odd ? b1.x : b0.x, src);
-      const float bi = __shfl_sync(0xffffffffu, odd ? b1.y : b0.y, src);
+      const float br = __shfl_sync(0xffffffffu, odd ? b1.x : b0.x, bbase + src);
+      const float bi = __shfl_sync(0xffffffffu, odd ? b1.y : b0.y, bbase + src);
       gr = fmaf(ar, br, fmaf(ai, bi, gr));
       gi = fmaf(ar, bi, fmaf(-ai, br, gi));
     }
