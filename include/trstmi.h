@@ -218,7 +218,11 @@ int trstmi_coherence(trstmi_handle h, double *mu, double *welch);
 int trstmi_get_phi(trstmi_handle h, double *out);
 
 /* Replaces the frame (host buffer, 2*d*N doubles); columns are renormalised
- * in binary64 and the frame rescored.  A zero column is TRSTMI_EINVAL. */
+ * in binary64 and the frame rescored.  A zero or non-finite column is
+ * TRSTMI_EINVAL (checked on the host; the frame is then unchanged).  Returns
+ * once `in` has been read: the renormalisation and the rescore are enqueued on
+ * the handle's stream ahead of any later call's work, and a device error they
+ * meet is reported by the next call that reads the state. */
 int trstmi_set_phi(trstmi_handle h, const double *in);
 
 /*

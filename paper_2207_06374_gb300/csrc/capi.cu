@@ -139,6 +139,7 @@ struct trstmi_instance {
                                            // drawn once as [i][column] planes (2dN floats each)
   std::map<int, cudaGraphExec_t> graphs;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev_in = nullptr;             // trstmi_set_phi: the caller's frame copied
   // the device state's screen threshold (infinite when the screen is not
   // used); 0 means every iteration ranks with the screen
   double screen_min_delta = std::numeric_limits<double>::infinity();
@@ -470,6 +471,7 @@ void trstmi_destroy(trstmi_handle h) {
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
   h->dmem.release(h->block);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -567,7 +569,8 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   if (o_ptop != (size_t)-1) h->planes_top = (float*)(b + o_ptop);
   if (o_lists != (size_t)-1) h->slists = (uint2*)(b + o_lists);
   if (o_blocks != (size_t)-1) h->sblocks = (unsigned char*)(b + o_blocks);
-  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess) {
     trstmi_destroy(h);
     return TRSTMI_ECUDA;
   }
@@ -738,11 +741,16 @@ int trstmi_set_phi(trstmi_handle h, const double* in) {
   USE_DEVICE(h->opt.device);
   cudaStream_t s = h->stream;
   const size_t bytes = (size_t)h->N * h->d * sizeof(double2);
-  // reject zero or non-finite columns on the host before touching the device
-  // state; four partial sums per column keep the check off one long chain of
-  // dependent additions (a sum of squares is zero exactly when every entry is)
+  // the copy into scratch (not yet the frame) runs while the host checks the
+  // columns; the caller's buffer is read only until ev_in
+  TRY_CUDA(cudaMemcpyAsync(h->scratch64, in, bytes, cudaMemcpyHostToDevice, s));
+  TRY_CUDA(cudaEventRecord(h->ev_in, s));
+  // reject zero or non-finite columns before the device state changes; four
+  // partial sums per column keep the check off one long chain of dependent
+  // additions (a sum of squares is zero exactly when every entry is)
   const int m = 2 * h->d;
-  for (int j = 0; j < h->N; ++j) {
+  bool ok = true;
+  for (int j = 0; j < h->N && ok; ++j) {
     const double* c = in + (size_t)j * m;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int i = 0;
@@ -754,16 +762,18 @@ int trstmi_set_phi(trstmi_handle h, const double* in) {
     }
     for (; i < m; ++i) a0 += c[i] * c[i];
     const double acc = (a0 + a1) + (a2 + a3);
-    if (!(acc > 0.0) || !std::isfinite(acc)) return TRSTMI_EINVAL;
+    ok = acc > 0.0 && std::isfinite(acc);
   }
-  TRY_CUDA(cudaMemcpyAsync(h->scratch64, in, bytes, cudaMemcpyHostToDevice, s));
+  if (!ok) {
+    TRY_CUDA(cudaEventSynchronize(h->ev_in));
+    return TRSTMI_EINVAL;
+  }
+  // renormalise into the frame and rescore, in stream order before any later
+  // call's work; return once the caller's buffer has been read
   TRY_CUDA(launch_normalize64(h->N, h->d, h->scratch64, h->phi64, h->phi32, h->st, s));
-  int rc = enqueue_rescore_current(h);
-  if (rc) return rc;
-  DevState chk;
-  rc = read_state(h, &chk);
-  if (rc) return rc;
-  return device_error_status(chk);
+  const int rc = enqueue_rescore_current(h);
+  TRY_CUDA(cudaEventSynchronize(h->ev_in));
+  return rc;
 }
 
 namespace {
