@@ -140,6 +140,7 @@ struct trstmi_instance {
   std::map<int, cudaGraphExec_t> graphs;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t ev_in = nullptr;             // trstmi_set_phi: the caller's frame copied
+  DevState* st_host = nullptr;             // pinned host copy of the state (read_state)
   // the device state's screen threshold (infinite when the screen is not
   // used); 0 means every iteration ranks with the screen
   double screen_min_delta = std::numeric_limits<double>::infinity();
@@ -396,9 +397,12 @@ int get_graph(trstmi_instance* h, int iters, cudaGraphExec_t* out, bool with_sto
   return TRSTMI_OK;
 }
 
+// The device state, through a pinned host copy (a direct copy, not staged).
 int read_state(trstmi_instance* h, DevState* out) {
-  TRY_CUDA(cudaMemcpyAsync(out, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  TRY_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                           h->stream));
   TRY_CUDA(cudaStreamSynchronize(h->stream));
+  *out = *h->st_host;
   return TRSTMI_OK;
 }
 
@@ -472,6 +476,7 @@ void trstmi_destroy(trstmi_handle h) {
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->st_host) cudaFreeHost(h->st_host);
   h->dmem.release(h->block);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -570,7 +575,8 @@ int trstmi_create(int N, int d, uint64_t seed, const trstmi_options* opt, trstmi
   if (o_lists != (size_t)-1) h->slists = (uint2*)(b + o_lists);
   if (o_blocks != (size_t)-1) h->sblocks = (unsigned char*)(b + o_blocks);
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost((void**)&h->st_host, sizeof(DevState)) != cudaSuccess) {
     trstmi_destroy(h);
     return TRSTMI_ECUDA;
   }
